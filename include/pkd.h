@@ -1,0 +1,158 @@
+/*
+ * pkd.h -- C ABI of the GB300 (sm_103a) Pkd-tree library, libpkd.so.
+ *
+ * The Pkd-tree is the parallel kd-tree of "Parallel kd-tree with Batch
+ * Updates" (Men, Shen, Gu, Sun, SIGMOD 2025).  Every step of these calls runs
+ * in the library's own CUDA kernels; the host only sequences launches.
+ *
+ * Conventions for every entry point:
+ *  - Points have d int32 coordinates in [0, 2^30) stored point-major
+ *    (coords[i*d + j]) and a uint32 id.  Coordinates outside that range are
+ *    rejected with PKD_EINVAL.
+ *  - Point, query and result buffers are DEVICE pointers owned by the
+ *    caller, except in pkd_export (host buffers).  The library copies what it
+ *    keeps; input buffers may be reused once the call has returned.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Builds
+ *    and batch updates return after their work on `stream` has completed
+ *    (they read device-side counts between sieve rounds).  Queries are
+ *    asynchronous: their outputs are valid once `stream` has been
+ *    synchronised.
+ *  - A pkd_tree is not thread-safe: one call at a time per tree, except
+ *    that queries on an unchanging tree may overlap.
+ *  - Return value 0 (PKD_OK) or one of the error codes below; device-side
+ *    failures (a bound exceeded, a wait that ran out) are reported by the
+ *    call that detects them, and leave the tree unusable: free it.
+ */
+#ifndef PKD_H
+#define PKD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PKD_OK 0
+#define PKD_EINVAL 1    /* bad parameter, size or coordinate */
+#define PKD_ENOMEM 2    /* device memory exhausted; the tree is unchanged */
+#define PKD_ECUDA 3     /* a CUDA runtime call failed */
+#define PKD_ETIMEOUT 4  /* a bounded device-side wait ran out */
+#define PKD_EINTERNAL 5 /* a device-side consistency check failed */
+
+typedef struct pkd_tree pkd_tree;
+
+/* Parameters (Sec. 5 "Parameter Choosing" of the paper uses lambda = 6,
+ * phi = 32, sigma = 32, alpha = 0.3).
+ *   d           dimensions, 1..8
+ *   phi         leaf wrap: a subproblem of at most phi points is a leaf (>= 1)
+ *   lambda      skeleton levels built per sieve round, 1..10 (Alg. 1)
+ *   sigma_log2  rate mode: each point is sampled with probability
+ *               2^-sigma_log2 (0..30; 0 samples every point)
+ *   sigma_os    a skeleton node is split only when it holds at least
+ *               2*sigma_os samples (the oversampling of Lemma 3.1), >= 1
+ *   count_mode  1: instead of a fixed rate, sample about 2^lambda*sigma_os
+ *               points per subproblem as Alg. 1 does
+ *   alpha       weight-balance parameter alpha_num/alpha_den in [0, 1/2]
+ *               (Sec. 2), alpha_den <= 2^20
+ *   seed        salt of the sampling hash
+ * The tree is a deterministic function of (points, ids, parameters). */
+typedef struct {
+  int d;
+  int phi;
+  int lambda;
+  int sigma_log2;
+  int sigma_os;
+  int count_mode;
+  int alpha_num;
+  int alpha_den;
+  uint64_t seed;
+} pkd_params;
+
+/* Build a Pkd-tree over n points (Alg. 1: sample, lambda-level skeleton,
+ * sieve into 2^lambda buckets, recurse; leaves of at most phi points).
+ *   coords  device, [n][d] int32
+ *   ids     device, [n] uint32, or NULL for ids 0..n-1
+ *   n       number of points, < 2^32 - 1 (0 gives an empty tree)
+ *   out     receives the new tree (owns all device memory it allocates)
+ * Errors: PKD_EINVAL (parameters, n, coordinates), PKD_ENOMEM, PKD_ECUDA. */
+int pkd_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const pkd_params* params,
+              void* stream, pkd_tree** out);
+
+/* BatchInsert (Alg. 2): sieve the batch through the existing skeletons,
+ * update subtree sizes top-down, rebuild with Build every subtree that would
+ * leave the alpha balance and every leaf that receives points.
+ *   coords  device, [m][d] int32;  ids  device, [m] uint32 (required)
+ * Ids are the caller's labels; the library does not check their uniqueness.
+ * Errors: PKD_EINVAL (tree unchanged), PKD_ENOMEM (tree unchanged),
+ * PKD_ECUDA / PKD_ETIMEOUT / PKD_EINTERNAL (tree unusable). */
+int pkd_batch_insert(pkd_tree* tree, const int32_t* coords, const uint32_t* ids, uint64_t m,
+                     void* stream);
+
+/* BatchDelete (Sec. 4.2, two rounds): sieve the batch to the leaves, remove
+ * every stored point whose (coordinates, id) equals a batch entry, then
+ * rebalance top-down with the exact new sizes (rebuild the subtrees that
+ * leave the alpha balance).  Entries that match no stored point are skipped.
+ *   coords  device, [m][d] int32;  ids  device, [m] uint32
+ *   n_deleted  host, optional: number of stored points removed
+ * Errors as for pkd_batch_insert. */
+int pkd_batch_delete(pkd_tree* tree, const int32_t* coords, const uint32_t* ids, uint64_t m,
+                     uint64_t* n_deleted, void* stream);
+
+/* k nearest neighbours (Sec. 5 "Queries": depth-first search, near child
+ * first, far child pruned by the distance to its subspace).  For query i,
+ * out_ids[i*k .. i*k+k) and out_d2[...] receive the k smallest
+ * (squared Euclidean distance, id) pairs in lexicographic order; slots past
+ * the tree size hold id 0xFFFFFFFF and distance INT64_MAX.
+ *   queries  device, [q][d] int32 in [0, 2^30);  k  in 1..128
+ *   out_ids  device, [q][k] uint32;  out_d2  device, [q][k] int64 */
+int pkd_knn(const pkd_tree* tree, const int32_t* queries, uint64_t q, int k, uint32_t* out_ids,
+            int64_t* out_d2, void* stream);
+
+/* Range count (Sec. 5): for each closed box lo[i][j] <= x_j <= hi[i][j],
+ * the number of stored points inside; a subtree whose subspace lies inside
+ * the box adds its stored size.
+ *   lo, hi  device, [q][d] int32;  out_counts  device, [q] uint64 */
+int pkd_range_count(const pkd_tree* tree, const int32_t* lo, const int32_t* hi, uint64_t q,
+                    uint64_t* out_counts, void* stream);
+
+/* Canonical form of the tree into HOST buffers (for parity checks and
+ * checkpoints): nodes in pre-order, interior nodes as (dim, split, size),
+ * leaves as (0xFF, 0, point count); leaves in in-order with their ids sorted
+ * ascending, leaf k owning leaf_ids[leaf_offsets[k] .. leaf_offsets[k+1]).
+ * Any NULL buffer is skipped, so a first call with NULL buffers returns
+ * *n_nodes and *n_leaves for sizing (leaf_ids needs pkd_size() entries,
+ * leaf_offsets n_leaves + 1).  Synchronises the device. */
+int pkd_export(const pkd_tree* tree, uint8_t* dims, int32_t* splits, uint64_t* sizes,
+               uint64_t* n_nodes, uint32_t* leaf_ids, uint64_t* leaf_offsets, uint64_t* n_leaves);
+
+/* Number of stored points. */
+uint64_t pkd_size(const pkd_tree* tree);
+
+/* Longest root-to-leaf path (edges) into *height.  Synchronises the device. */
+int pkd_height(const pkd_tree* tree, int* height);
+
+/* Free the tree and all device memory it owns (NULL is a no-op). */
+void pkd_free(pkd_tree* tree);
+
+/* Human-readable text for an error code. */
+const char* pkd_strerror(int code);
+
+/* Tuning knobs (testing and autotuning; results never depend on them):
+ *   "base_cap"   largest subproblem finished in one CTA's shared memory
+ *                (0 = derived from d and the shared-memory size)
+ *   "skel_cap"   largest sample handled by one CTA when building a skeleton
+ *   "tile"       points per CTA in the sieve kernels
+ * Returns PKD_EINVAL for an unknown name or an out-of-range value. */
+int pkd_set_option(const char* name, int64_t value);
+
+/* Per-kernel timing with CUDA events on the launching stream (off by
+ * default).  pkd_kernel_stats fills, for kernel family `name`, the number
+ * of timed launches, their summed duration in ms and the points (items)
+ * they processed; pkd_kernel_timing(1) enables and clears the counters. */
+int pkd_kernel_timing(int enable);
+int pkd_kernel_stats(const char* name, uint64_t* launches, double* total_ms, uint64_t* items);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PKD_H */

@@ -1,0 +1,1375 @@
+// Pkd-tree construction on the GPU (Alg. 1 of "Parallel kd-tree with Batch
+// Updates"), for a set of independent subproblems at once.
+//
+// A subproblem larger than one CTA's shared memory takes a global round:
+//   sample    points whose hash passes the rate test at the subproblem's depth
+//   skeleton  lambda levels of exact medians on the sample: device-wide radix
+//             select while a skeleton node's sample exceeds one CTA, then one
+//             CTA per node in shared memory
+//   count     every point walks the skeleton (splitters in shared memory) to
+//             its bucket; per-tile bucket histograms (warp-aggregated)
+//   scan      bucket-major ("column-major") exclusive prefix sum of the
+//             histograms = write offset of every (tile, bucket)
+//   scatter   the tile is staged in shared memory in bucket order and every
+//             bucket's run is written contiguously into the other buffer
+//             (the two buffers swap each round instead of copying back, Sec. 5)
+//   emit      skeleton nodes become tree nodes; every bucket becomes a child
+//             subproblem at depth + its skeleton depth
+// A subproblem that fits in shared memory is finished by one CTA
+// (smem_build.cuh).  When a skeleton root is a bucket (too few or identical
+// samples) the subproblem takes one exact level on its own points; when its
+// points are all identical it becomes one heavy leaf.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+#include "engine.hpp"
+#include "smem_build.cuh"
+
+namespace pkd {
+
+constexpr uint32_t SEG_SKIP = 0xFFFFFFFFu;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_TILE = SCAN_ITEMS * SCAN_THREADS;
+constexpr int JOB_TILE = 2048;
+constexpr int JOB_THREADS = 256;
+constexpr int SIEVE_THREADS = 512;
+
+// ---------------------------------------------------------------------------
+// Point sources
+// ---------------------------------------------------------------------------
+
+struct Src {
+  Pts soa;
+  const int32_t* aos;
+  const uint32_t* aos_ids;
+  int is_aos;
+  __device__ __forceinline__ int32_t x(int d, int j, uint64_t g) const {
+    return is_aos ? aos[g * (uint64_t)d + j] : soa.c[(uint64_t)j * soa.stride + g];
+  }
+  __device__ __forceinline__ uint32_t id(uint64_t g) const {
+    return is_aos ? (aos_ids ? aos_ids[g] : (uint32_t)g) : soa.id[g];
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Shared-memory kernels (build mode and skeleton mode)
+// ---------------------------------------------------------------------------
+
+struct SmemPtrs {
+  int32_t* X;
+  uint32_t* ID;
+  uint16_t* perm0;
+  uint16_t* perm1;
+  uint8_t* flag;
+  unsigned* bhist;
+  int* bred;
+  unsigned* whist;
+  Task* bstack;
+  Task* wlist;
+  Task* wstack;
+  SmemCtl* ctl;
+};
+
+__device__ SmemPtrs carve(uint8_t* sm, int cap, int d) {
+  const SmemLayout Lo = smem_layout(cap, d);
+  SmemPtrs q;
+  q.X = (int32_t*)(sm + Lo.X);
+  q.ID = (uint32_t*)(sm + Lo.ID);
+  q.perm0 = (uint16_t*)(sm + Lo.perm0);
+  q.perm1 = (uint16_t*)(sm + Lo.perm1);
+  q.flag = (uint8_t*)(sm + Lo.flag);
+  q.bhist = (unsigned*)(sm + Lo.bhist);
+  q.bred = (int*)(sm + Lo.bred);
+  q.whist = (unsigned*)(sm + Lo.whist);
+  q.bstack = (Task*)(sm + Lo.bstack);
+  q.wlist = (Task*)(sm + Lo.wlist);
+  q.wstack = (Task*)(sm + Lo.wstack);
+  q.ctl = (SmemCtl*)(sm + Lo.ctl);
+  return q;
+}
+
+__global__ void __launch_bounds__(SM_THREADS) k_smem_build(SmemArgs a) {
+  if (blockIdx.x >= *a.nsegs) return;
+  extern __shared__ __align__(16) uint8_t sm[];
+  const Seg seg = a.segs[blockIdx.x];
+  const int d = a.p.d, cap = a.cap, tid = threadIdx.x;
+  SmemPtrs q = carve(sm, cap, d);
+  if (seg.len > (uint32_t)cap) {
+    if (tid == 0) set_error(a.st, DERR_CAPACITY, (int)blockIdx.x);
+    return;
+  }
+  const int n = (int)seg.len;
+  for (int i = tid; i < n; i += SM_THREADS) {
+    const uint64_t g = seg.start + (uint64_t)i;
+    if (seg.where == IN_INPUT) {
+      for (int j = 0; j < d; ++j) q.X[j * cap + i] = a.in_coords[g * (uint64_t)d + j];
+      q.ID[i] = a.in_ids ? a.in_ids[g] : (uint32_t)g;
+    } else {
+      const Pts& S = seg.where == IN_A ? a.A : a.B;
+      for (int j = 0; j < d; ++j) q.X[j * cap + i] = S.c[(uint64_t)j * S.stride + g];
+      q.ID[i] = S.id[g];
+    }
+    q.perm0[i] = (uint16_t)i;
+  }
+  if (tid == 0) q.ctl->next_slot = 0;
+  __syncthreads();
+  if (n == 0) {
+    if (tid == 0) {
+      a.nodes[seg.root] = Node{0, 0, (uint32_t)seg.start, 0};
+      a.ndim[seg.root] = PKD_LEAF;
+    }
+    return;
+  }
+  SmemCtx cx;
+  cx.p = a.p;
+  cx.s = SmemPts{q.X, q.ID, q.flag, cap, d};
+  cx.flag = q.flag;
+  cx.perm[0] = q.perm0;
+  cx.perm[1] = q.perm1;
+  cx.ctl = q.ctl;
+  cx.out = a.A;
+  cx.start = seg.start;
+  cx.slot_base = (uint32_t)(a.shared_cap + 2 * seg.start);
+  cx.slot_limit = 2 * n;
+  cx.nodes = a.nodes;
+  cx.ndim = a.ndim;
+  cx.skel = nullptr;
+  cx.lam = 0;
+  cx.min_split = 0;
+  cx.st = a.st;
+  Task root{0, (uint16_t)n, 0, 0, 0, seg.depth, seg.root};
+  run_tasks<false>(cx, root, q.bstack, q.wlist, q.wstack, q.bhist, q.bred, q.whist);
+}
+
+__global__ void __launch_bounds__(SM_THREADS) k_smem_skel(SmemArgs a) {
+  if (blockIdx.x >= *a.njobs) return;
+  extern __shared__ __align__(16) uint8_t sm[];
+  const SkelJob jb = a.jobs[blockIdx.x];
+  const int d = a.p.d, cap = a.cap, tid = threadIdx.x;
+  SmemPtrs q = carve(sm, cap, d);
+  if (jb.n > (uint32_t)cap) {
+    if (tid == 0) set_error(a.st, DERR_CAPACITY, 200000 + (int)blockIdx.x);
+    return;
+  }
+  const int n = (int)jb.n;
+  const int32_t* S = a.sbuf[jb.buf];
+  for (int i = tid; i < n; i += SM_THREADS) {
+    for (int j = 0; j < d; ++j) q.X[j * cap + i] = S[(uint64_t)j * a.sstride + jb.a + i];
+    q.ID[i] = 0;
+    q.flag[i] = 0;
+    q.perm0[i] = (uint16_t)i;
+  }
+  __syncthreads();
+  SmemCtx cx;
+  cx.p = a.p;
+  cx.s = SmemPts{q.X, q.ID, q.flag, cap, d};
+  cx.flag = q.flag;
+  cx.perm[0] = q.perm0;
+  cx.perm[1] = q.perm1;
+  cx.ctl = q.ctl;
+  cx.skel = a.skel + (uint64_t)jb.seg * a.heap_n;
+  cx.lam = jb.lam;
+  cx.min_split = (int)jb.min_split;
+  cx.st = a.st;
+  Task root{0, (uint16_t)n, 0, 0, jb.j, 0, jb.h};
+  run_tasks<true>(cx, root, q.bstack, q.wlist, q.wstack, q.bhist, q.bred, q.whist);
+}
+
+// ---------------------------------------------------------------------------
+// Scans
+// ---------------------------------------------------------------------------
+
+// Exclusive block scan of one value per thread; returns the prefix, *total.
+template <class V>
+__device__ V block_excl_scan(V v, V* sh, V* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  V incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    V t = __shfl_up_sync(FULL_MASK, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) sh[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    V s = lane < nw ? sh[lane] : V(0);
+    V si = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      V t = __shfl_up_sync(FULL_MASK, si, o);
+      if (lane >= o) si += t;
+    }
+    if (lane < nw) sh[lane] = si - s;
+    if (lane == 31) sh[32] = si;
+  }
+  __syncthreads();
+  V r = sh[w] + incl - v;
+  *total = sh[32];
+  __syncthreads();
+  return r;
+}
+
+// Per-block sums of in[0, n).
+__global__ void k_scan_reduce(const uint32_t* in, uint64_t n, uint32_t* partial) {
+  __shared__ uint32_t sh[33];
+  uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+  uint32_t s = 0;
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    uint64_t i = base + (uint64_t)threadIdx.x * SCAN_ITEMS + k;
+    if (i < n) s += in[i];
+  }
+  uint32_t tot;
+  block_excl_scan<uint32_t>(s, sh, &tot);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+// Single-block exclusive scan in place over x[0, n).
+__global__ void k_scan_single(uint32_t* x, uint64_t n) {
+  __shared__ uint32_t sh[33];
+  uint32_t carry = 0;
+  for (uint64_t base = 0; base < n; base += blockDim.x) {
+    uint64_t i = base + threadIdx.x;
+    uint32_t v = i < n ? x[i] : 0;
+    uint32_t tot;
+    uint32_t e = block_excl_scan<uint32_t>(v, sh, &tot);
+    if (i < n) x[i] = carry + e;
+    carry += tot;
+  }
+}
+
+__global__ void k_scan_apply(const uint32_t* in, uint32_t* out, uint64_t n, const uint32_t* partial) {
+  __shared__ uint32_t sh[33];
+  uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
+  uint32_t v[SCAN_ITEMS];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0;
+    s += v[k];
+  }
+  uint32_t tot;
+  uint32_t e = block_excl_scan<uint32_t>(s, sh, &tot) + partial[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    if (base + k < n) out[base + k] = e;
+    e += v[k];
+  }
+}
+
+static void device_excl_scan(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* partial,
+                             cudaStream_t s) {
+  if (n == 0) return;
+  const uint64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+  k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, partial);
+  k_scan_single<<<1, 1024, 0, s>>>(partial, nb);
+  k_scan_apply<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, partial);
+}
+
+// ---------------------------------------------------------------------------
+// Round bookkeeping
+// ---------------------------------------------------------------------------
+
+struct RoundArgs {
+  Params p;
+  int lam, NB, HN, TILE;
+  Src src;
+  Pts dst;
+  Pts A;
+  int dst_where;
+  const Seg* big;
+  const uint32_t* nbig;
+  uint32_t* tile0;   // [nbig] first tile of each big segment
+  uint64_t* excl;    // [nbig] points of the big segments before this one
+  int2* skel;        // [nbig][HN]
+  uint32_t* slots;   // [nbig][HN]
+  uint32_t* nbk;     // [nbig] buckets
+  uint8_t* exact;    // [nbig] 1: exact level on the points; 2: already handled
+  uint32_t* hist;    // [tiles * NB]
+  uint32_t* hscan;
+  uint32_t* scnt;    // [nbig] samples
+  uint32_t* sizes;   // [nbig][HN] skeleton subtree sizes
+  Pts samp;          // sample buffer 0
+  Seg* children;     // [nbig * NB]
+  Node* nodes;
+  uint8_t* ndim;
+  uint32_t* shared_next;
+  uint64_t shared_cap;
+  DevStatus* st;
+};
+
+__device__ __forceinline__ uint32_t seg_of_tile(const uint32_t* tile0, uint32_t nseg, uint32_t tile) {
+  uint32_t lo = 0, hi = nseg;  // largest s with tile0[s] <= tile
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (tile0[mid] <= tile) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Split a segment list into big segments (ctr[0], their tiles ctr[2], their
+// points *pts) and segments finished in shared memory (appended to the
+// persistent base list, counter *nbase).
+__global__ void k_classify(const Seg* segs, uint32_t nseg, uint32_t cap, Seg* big, uint32_t* ctr,
+                           unsigned long long* pts, Seg* base, uint32_t* nbase, uint32_t base_cap,
+                           uint32_t tile, uint32_t where, DevStatus* st) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nseg) return;
+  Seg s = segs[i];
+  if (s.len == SEG_SKIP) return;
+  s.where = where;
+  if (s.len > cap) {
+    uint32_t k = atomicAdd(&ctr[0], 1u);
+    big[k] = s;
+    atomicAdd(&ctr[2], (s.len + tile - 1) / tile);
+    atomicAdd(pts, (unsigned long long)s.len);
+  } else {
+    uint32_t k = atomicAdd(nbase, 1u);
+    if (k < base_cap) base[k] = s;
+    else set_error(st, DERR_CAPACITY, 300);
+  }
+}
+
+// tile0 / excl over the big segments (one block).
+__global__ void k_big_prefix(const Seg* big, const uint32_t* nbig, uint32_t tile, uint32_t* tile0,
+                             uint64_t* excl) {
+  __shared__ uint32_t sh32[33];
+  __shared__ unsigned long long sh64[33];
+  const uint32_t n = *nbig;
+  uint32_t ct = 0;
+  unsigned long long cl = 0;
+  for (uint32_t base = 0; base < n; base += blockDim.x) {
+    uint32_t i = base + threadIdx.x;
+    uint32_t t = 0;
+    unsigned long long l = 0;
+    if (i < n) {
+      t = (big[i].len + tile - 1) / tile;
+      l = big[i].len;
+    }
+    uint32_t tt;
+    unsigned long long tl;
+    uint32_t et = block_excl_scan<uint32_t>(t, sh32, &tt);
+    unsigned long long el = block_excl_scan<unsigned long long>(l, sh64, &tl);
+    if (i < n) {
+      tile0[i] = ct + et;
+      excl[i] = cl + el;
+    }
+    ct += tt;
+    cl += tl;
+  }
+}
+
+// Sample: points whose hash at the segment's depth passes the rate test.
+__global__ void k_sample(RoundArgs r) {
+  const uint32_t nb = *r.nbig;
+  const uint32_t s = seg_of_tile(r.tile0, nb, blockIdx.x);
+  const Seg seg = r.big[s];
+  const uint64_t first = (uint64_t)(blockIdx.x - r.tile0[s]) * r.TILE;
+  if (first >= seg.len) return;
+  const int cnt = (int)min((uint64_t)r.TILE, (uint64_t)seg.len - first);
+  const int shift = sample_shift(r.p, seg.len);
+  const int d = r.p.d;
+  for (int base = 0; base < cnt; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const uint64_t g = seg.start + first + (uint64_t)i;
+    bool f = false;
+    if (i < cnt) f = in_sample(r.p.seed, seg.depth, r.src.id(g), shift);
+    const unsigned m = __ballot_sync(FULL_MASK, f);
+    if (m == 0) continue;
+    uint32_t pos = 0;
+    if (lane_id() == __ffs(m) - 1) pos = atomicAdd(&r.scnt[s], (uint32_t)__popc(m));
+    pos = __shfl_sync(FULL_MASK, pos, __ffs(m) - 1) + __popc(m & lanemask_lt());
+    if (f) {
+      const uint64_t o = seg.start + pos;
+      for (int j = 0; j < d; ++j) r.samp.c[(uint64_t)j * r.samp.stride + o] = r.src.x(d, j, g);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Device-wide skeleton levels for samples larger than one CTA
+// ---------------------------------------------------------------------------
+
+struct JobState {
+  int mn[PKD_DMAX];
+  int mx[PKD_DMAX];
+  int split;       // 1: this node splits
+  int dim;
+  int k;
+  unsigned prefix, mask;
+  int less, eq;
+  int x;
+  int L;
+  unsigned lcur, rcur;
+  int fixmin;
+};
+
+struct JobArgs {
+  Params p;
+  int d;
+  const SkelJob* jobs;
+  const uint32_t* njobs;
+  const uint32_t* jtile0;
+  JobState* js;
+  uint32_t* jhist;  // [job][256]
+  Pts sb[2];        // sample buffers
+  int2* skel;
+  int HN;
+  int scap;
+  SkelJob* next_big;
+  uint32_t* next_ctr;  // [0] big jobs, [1] their tiles, [2] small jobs
+  SkelJob* small;
+  uint32_t small_cap, big_cap;
+  DevStatus* st;
+};
+
+__global__ void k_job_tiles(const SkelJob* jobs, const uint32_t* njobs, uint32_t* jtile0) {
+  __shared__ uint32_t sh[33];
+  const uint32_t n = *njobs;
+  uint32_t c = 0;
+  for (uint32_t base = 0; base < n; base += blockDim.x) {
+    uint32_t i = base + threadIdx.x;
+    uint32_t t = i < n ? (jobs[i].n + JOB_TILE - 1) / JOB_TILE : 0;
+    uint32_t tot;
+    uint32_t e = block_excl_scan<uint32_t>(t, sh, &tot);
+    if (i < n) jtile0[i] = c + e;
+    c += tot;
+  }
+}
+
+__global__ void k_job_init(JobArgs a) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *a.njobs) return;
+  JobState& s = a.js[i];
+  for (int j = 0; j < PKD_DMAX; ++j) {
+    s.mn[j] = INT32_MAX;
+    s.mx[j] = INT32_MIN;
+  }
+  s.split = 0;
+  s.lcur = s.rcur = 0;
+  s.fixmin = INT32_MAX;
+  for (int b = 0; b < 256; ++b) a.jhist[(uint64_t)i * 256 + b] = 0;
+}
+
+struct JobTile {
+  uint32_t job;
+  SkelJob jb;
+  uint64_t first;
+  int cnt;
+};
+
+__device__ __forceinline__ bool job_tile(const JobArgs& a, JobTile& t) {
+  const uint32_t nj = *a.njobs;
+  t.job = seg_of_tile(a.jtile0, nj, blockIdx.x);
+  t.jb = a.jobs[t.job];
+  t.first = (uint64_t)(blockIdx.x - a.jtile0[t.job]) * JOB_TILE;
+  if (t.first >= t.jb.n) return false;
+  t.cnt = (int)min((uint64_t)JOB_TILE, (uint64_t)t.jb.n - t.first);
+  return true;
+}
+
+__global__ void __launch_bounds__(JOB_THREADS) k_job_stats(JobArgs a) {
+  JobTile t;
+  if (!job_tile(a, t)) return;
+  __shared__ int smn[PKD_DMAX][JOB_THREADS / 32], smx[PKD_DMAX][JOB_THREADS / 32];
+  const Pts& B = a.sb[t.jb.buf];
+  const int d = a.d;
+  for (int j = 0; j < d; ++j) {
+    int mn = INT32_MAX, mx = INT32_MIN;
+    for (int i = threadIdx.x; i < t.cnt; i += blockDim.x) {
+      int v = B.c[(uint64_t)j * B.stride + t.jb.a + t.first + i];
+      mn = min(mn, v);
+      mx = max(mx, v);
+    }
+    mn = warp_min(mn);
+    mx = warp_max(mx);
+    if (lane_id() == 0) {
+      smn[j][warp_id()] = mn;
+      smx[j][warp_id()] = mx;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < d) {
+    const int j = threadIdx.x;
+    int mn = INT32_MAX, mx = INT32_MIN;
+    for (int w = 0; w < JOB_THREADS / 32; ++w) {
+      mn = min(mn, smn[j][w]);
+      mx = max(mx, smx[j][w]);
+    }
+    atomicMin(&a.js[t.job].mn[j], mn);
+    atomicMax(&a.js[t.job].mx[j], mx);
+  }
+}
+
+__global__ void k_job_choose(JobArgs a) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *a.njobs) return;
+  const SkelJob jb = a.jobs[i];
+  JobState& s = a.js[i];
+  int dim = -1;
+  if (jb.j < jb.lam && jb.n >= jb.min_split) dim = widest_dim(s.mn, s.mx, a.d);
+  s.split = dim >= 0;
+  s.dim = dim < 0 ? 0 : dim;
+  s.k = (int)(jb.n / 2);
+  s.prefix = 0;
+  s.mask = 0;
+  s.less = 0;
+  s.eq = 0;
+}
+
+__global__ void __launch_bounds__(JOB_THREADS) k_job_hist(JobArgs a, int pass) {
+  JobTile t;
+  if (!job_tile(a, t)) return;
+  const JobState& s = a.js[t.job];
+  if (!s.split) return;
+  __shared__ unsigned h[256];
+  for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  const Pts& B = a.sb[t.jb.buf];
+  const int shift = 24 - 8 * pass;
+  const unsigned prefix = s.prefix, mask = s.mask;
+  const int32_t* X = B.c + (uint64_t)s.dim * B.stride + t.jb.a + t.first;
+  for (int i = threadIdx.x; i < t.cnt; i += blockDim.x) {
+    unsigned v = (unsigned)X[i];
+    if ((v & mask) == prefix) atomicAdd(&h[(v >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < 256; b += blockDim.x)
+    if (h[b]) atomicAdd(&a.jhist[(uint64_t)t.job * 256 + b], h[b]);
+}
+
+// One warp per job.
+__global__ void k_job_pick(JobArgs a, int pass) {
+  const uint32_t job = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (job >= *a.njobs) return;
+  JobState& s = a.js[job];
+  if (!s.split) return;
+  unsigned* h = a.jhist + (uint64_t)job * 256;
+  int digit, below, eq;
+  warp_find_digit(h, s.k, digit, below, eq);
+  __syncwarp();
+  for (int b = lane_id(); b < 256; b += 32) h[b] = 0;
+  if (lane_id() == 0) {
+    const int shift = 24 - 8 * pass;
+    s.prefix |= (unsigned)digit << shift;
+    s.mask |= 255u << shift;
+    s.k -= below;
+    s.less += below;
+    s.eq = eq;
+  }
+}
+
+__global__ void __launch_bounds__(JOB_THREADS) k_job_minabove(JobArgs a) {
+  JobTile t;
+  if (!job_tile(a, t)) return;
+  JobState& s = a.js[t.job];
+  if (!s.split || s.less != 0) return;
+  const Pts& B = a.sb[t.jb.buf];
+  const int32_t* X = B.c + (uint64_t)s.dim * B.stride + t.jb.a + t.first;
+  const int x = (int)s.prefix;
+  int m = INT32_MAX;
+  for (int i = threadIdx.x; i < t.cnt; i += blockDim.x) {
+    int v = X[i];
+    if (v > x) m = min(m, v);
+  }
+  m = warp_min(m);
+  if (lane_id() == 0 && m != INT32_MAX) atomicMin(&s.fixmin, m);
+}
+
+__global__ void k_job_fix(JobArgs a) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *a.njobs) return;
+  JobState& s = a.js[i];
+  if (!s.split) return;
+  if (s.less == 0) {
+    // nothing strictly below the median: split at the next distinct value;
+    // the left side is then exactly the copies of the minimum.
+    s.x = s.fixmin;
+    s.L = s.eq;
+  } else {
+    s.x = (int)s.prefix;
+    s.L = s.less;
+  }
+}
+
+__global__ void __launch_bounds__(JOB_THREADS) k_job_partition(JobArgs a) {
+  JobTile t;
+  if (!job_tile(a, t)) return;
+  JobState& s = a.js[t.job];
+  if (!s.split) return;
+  __shared__ uint32_t sh[33];
+  __shared__ uint32_t base_l, base_r;
+  const Pts& B = a.sb[t.jb.buf];
+  const Pts& O = a.sb[t.jb.buf ^ 1];
+  const int d = a.d;
+  const int x = s.x;
+  const int32_t* X = B.c + (uint64_t)s.dim * B.stride + t.jb.a + t.first;
+  // Each thread takes a contiguous run of the tile so one scan covers it.
+  const int per = (t.cnt + JOB_THREADS - 1) / JOB_THREADS;
+  const int i0 = min(t.cnt, (int)threadIdx.x * per), i1 = min(t.cnt, i0 + per);
+  uint32_t nl = 0;
+  for (int i = i0; i < i1; ++i) nl += X[i] < x;
+  uint32_t tl;
+  uint32_t el = block_excl_scan<uint32_t>(nl, sh, &tl);
+  const uint32_t er = (uint32_t)i0 - el;
+  if (threadIdx.x == 0) {
+    base_l = atomicAdd(&s.lcur, tl);
+    base_r = atomicAdd(&s.rcur, (uint32_t)t.cnt - tl);
+  }
+  __syncthreads();
+  uint64_t pl = t.jb.a + base_l + el;
+  uint64_t pr = t.jb.a + (uint64_t)s.L + base_r + er;
+  for (int i = i0; i < i1; ++i) {
+    const uint64_t src = t.jb.a + t.first + i;
+    const bool left = X[i] < x;
+    const uint64_t dst = left ? pl++ : pr++;
+    for (int j = 0; j < d; ++j) O.c[(uint64_t)j * O.stride + dst] = B.c[(uint64_t)j * B.stride + src];
+  }
+}
+
+__device__ void push_job(const JobArgs& a, const SkelJob& c) {
+  int2* sk = a.skel + (uint64_t)c.seg * a.HN;
+  if (c.j >= c.lam || c.n < c.min_split) {
+    sk[c.h] = make_int2(0, sk_meta(SK_BUCKET, 0, 0));
+    return;
+  }
+  if (c.n > (uint32_t)a.scap) {
+    uint32_t k = atomicAdd(&a.next_ctr[0], 1u);
+    if (k >= a.big_cap) {
+      set_error(a.st, DERR_CAPACITY, 400);
+      return;
+    }
+    a.next_big[k] = c;
+    atomicAdd(&a.next_ctr[1], (c.n + JOB_TILE - 1) / JOB_TILE);
+  } else {
+    uint32_t k = atomicAdd(&a.next_ctr[2], 1u);
+    if (k >= a.small_cap) {
+      set_error(a.st, DERR_CAPACITY, 401);
+      return;
+    }
+    a.small[k] = c;
+  }
+}
+
+__global__ void k_job_children(JobArgs a) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *a.njobs) return;
+  const SkelJob jb = a.jobs[i];
+  const JobState& s = a.js[i];
+  int2* sk = a.skel + (uint64_t)jb.seg * a.HN;
+  if (!s.split) {
+    sk[jb.h] = make_int2(0, sk_meta(SK_BUCKET, 0, 0));
+    return;
+  }
+  if (s.L <= 0 || (uint32_t)s.L >= jb.n) {
+    set_error(a.st, DERR_STATE, 500);
+    return;
+  }
+  sk[jb.h] = make_int2(s.x, sk_meta(SK_INTERNAL, s.dim, 0));
+  SkelJob l = jb, r = jb;
+  l.h = 2 * jb.h;
+  r.h = 2 * jb.h + 1;
+  l.buf = r.buf = (uint8_t)(jb.buf ^ 1);
+  l.j = r.j = (uint8_t)(jb.j + 1);
+  l.n = (uint32_t)s.L;
+  r.a = jb.a + (uint64_t)s.L;
+  r.n = jb.n - (uint32_t)s.L;
+  push_job(a, l);
+  push_job(a, r);
+}
+
+// Root jobs: one per big segment, on its sample.
+__global__ void k_root_jobs(RoundArgs r, JobArgs a, int exact_pass) {
+  uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= *r.nbig) return;
+  const Seg seg = r.big[s];
+  SkelJob jb;
+  jb.seg = s;
+  jb.h = 1;
+  jb.a = seg.start;
+  jb.buf = 0;
+  jb.j = 0;
+  jb.pad = 0;
+  jb.pad2 = 0;
+  if (!exact_pass) {
+    jb.n = r.scnt[s];
+    jb.lam = (uint8_t)r.lam;
+    jb.min_split = 2u * (uint32_t)r.p.sigma_os;
+  } else {
+    if (r.exact[s] != 1) return;
+    jb.n = seg.len;  // every point of the segment was copied into the sample buffer
+    jb.lam = 1;
+    jb.min_split = 2;
+  }
+  push_job(a, jb);
+}
+
+// Segments whose skeleton root is a bucket take one exact level next.
+__global__ void k_mark_exact(RoundArgs r, uint32_t* ctr) {
+  uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= *r.nbig) return;
+  const int m = r.skel[(uint64_t)s * r.HN + 1].y;
+  if (r.exact[s] == 0 && sk_state(m) == SK_BUCKET) {
+    r.exact[s] = 1;
+    atomicAdd(ctr, 1u);
+  }
+}
+
+__global__ void k_copy_exact(RoundArgs r) {
+  const uint32_t nb = *r.nbig;
+  const uint32_t s = seg_of_tile(r.tile0, nb, blockIdx.x);
+  if (r.exact[s] != 1) return;
+  const Seg seg = r.big[s];
+  const uint64_t first = (uint64_t)(blockIdx.x - r.tile0[s]) * r.TILE;
+  if (first >= seg.len) return;
+  const int cnt = (int)min((uint64_t)r.TILE, (uint64_t)seg.len - first);
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const uint64_t g = seg.start + first + i;
+    for (int j = 0; j < r.p.d; ++j) r.samp.c[(uint64_t)j * r.samp.stride + g] = r.src.x(r.p.d, j, g);
+  }
+}
+
+// Number the buckets left to right, detect heavy segments, give every
+// skeleton node a tree slot (root: the segment's own slot).
+__global__ void k_finalize(RoundArgs r) {
+  uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= *r.nbig) return;
+  int2* sk = r.skel + (uint64_t)s * r.HN;
+  uint32_t* sl = r.slots + (uint64_t)s * r.HN;
+  const Seg seg = r.big[s];
+  if (sk_state(sk[1].y) != SK_INTERNAL) {
+    // exact level found no split: every point is identical
+    sk[1] = make_int2(0, sk_meta(SK_HEAVY, 0, 0));
+    r.nbk[s] = 0;
+    sl[1] = seg.root;
+    return;
+  }
+  // in-order walk of the heap
+  int stack[12];
+  int sp = 0, h = 1, nb = 0, ni = 0;
+  while (sp > 0 || h != 0) {
+    if (h != 0) {
+      const int st = sk_state(sk[h].y);
+      if (st == SK_INTERNAL) {
+        stack[sp++] = h;
+        h = 2 * h;
+        continue;
+      }
+      if (st != SK_BUCKET) {
+        set_error(r.st, DERR_STATE, 600);
+        return;
+      }
+      sk[h].y = sk_meta(SK_BUCKET, 0, nb++);
+      h = 0;
+    } else {
+      h = stack[--sp];
+      ++ni;
+      h = 2 * h + 1;
+    }
+  }
+  r.nbk[s] = nb;
+  const uint32_t need = (uint32_t)(ni - 1 + nb);
+  const uint32_t b0 = atomicAdd(r.shared_next, need);
+  if ((uint64_t)b0 + need > r.shared_cap) {
+    set_error(r.st, DERR_SLOT, 601);
+    return;
+  }
+  uint32_t k = b0;
+  for (int v = 1; v < r.HN; ++v) {
+    const int st = sk_state(sk[v].y);
+    if (st == SK_NONE) continue;
+    sl[v] = (v == 1) ? seg.root : k++;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sieve: count and scatter
+// ---------------------------------------------------------------------------
+
+struct SieveTile {
+  uint32_t s;
+  Seg seg;
+  uint64_t first;
+  int cnt;
+  uint32_t t0, nt;
+};
+
+__device__ __forceinline__ bool sieve_tile(const RoundArgs& r, SieveTile& t) {
+  const uint32_t nb = *r.nbig;
+  t.s = seg_of_tile(r.tile0, nb, blockIdx.x);
+  t.seg = r.big[t.s];
+  t.t0 = r.tile0[t.s];
+  t.nt = (t.seg.len + r.TILE - 1) / r.TILE;
+  t.first = (uint64_t)(blockIdx.x - t.t0) * r.TILE;
+  if (t.first >= t.seg.len) return false;
+  t.cnt = (int)min((uint64_t)r.TILE, (uint64_t)t.seg.len - t.first);
+  return true;
+}
+
+// Walk the heap skeleton held in shared memory (split, meta) to a bucket.
+template <int D>
+__device__ __forceinline__ int walk_bucket(const int2* sk, const int32_t* x, int lam) {
+  int h = 1;
+  for (int l = 0; l < lam; ++l) {
+    const int2 e = sk[h];
+    if (sk_state(e.y) != SK_INTERNAL) break;
+    h = 2 * h + (x[sk_dim(e.y)] >= e.x);
+  }
+  return sk_bucket(sk[h].y);
+}
+
+template <int D>
+__global__ void __launch_bounds__(SIEVE_THREADS) k_count(RoundArgs r) {
+  SieveTile t;
+  if (!sieve_tile(r, t)) return;
+  extern __shared__ __align__(16) uint8_t sm[];
+  int2* sk = (int2*)sm;
+  unsigned* lh = (unsigned*)(sk + r.HN);
+  const int2* gsk = r.skel + (uint64_t)t.s * r.HN;
+  for (int v = threadIdx.x; v < r.HN; v += blockDim.x) sk[v] = gsk[v];
+  for (int b = threadIdx.x; b < r.NB; b += blockDim.x) lh[b] = 0;
+  __syncthreads();
+  const bool heavy = sk_state(sk[1].y) == SK_HEAVY;
+  if (!heavy) {
+    for (int base = 0; base < t.cnt; base += blockDim.x) {
+      const int i = base + threadIdx.x;
+      int b = -1;
+      if (i < t.cnt) {
+        int32_t x[D];
+        const uint64_t g = t.seg.start + t.first + i;
+#pragma unroll
+        for (int j = 0; j < D; ++j) x[j] = r.src.x(D, j, g);
+        b = walk_bucket<D>(sk, x, r.lam);
+      }
+      const unsigned m = __match_any_sync(FULL_MASK, b);
+      if (b >= 0 && lane_id() == __ffs(m) - 1) atomicAdd(&lh[b], (unsigned)__popc(m));
+    }
+  }
+  __syncthreads();
+  const uint64_t hb = (uint64_t)t.t0 * r.NB;
+  const uint32_t tl = blockIdx.x - t.t0;
+  for (int b = threadIdx.x; b < r.NB; b += blockDim.x) r.hist[hb + (uint64_t)b * t.nt + tl] = lh[b];
+}
+
+// Children segments, interior nodes and heavy leaves of every big segment.
+__global__ void k_emit(RoundArgs r, uint32_t* heavy_ctr) {
+  uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= *r.nbig) return;
+  const Seg seg = r.big[s];
+  const int2* sk = r.skel + (uint64_t)s * r.HN;
+  const uint32_t* sl = r.slots + (uint64_t)s * r.HN;
+  Seg* ch = r.children + (uint64_t)s * r.NB;
+  const uint32_t nb = r.nbk[s];
+  for (int b = (int)nb; b < r.NB; ++b) ch[b].len = SEG_SKIP;
+  if (sk_state(sk[1].y) == SK_HEAVY) {
+    r.nodes[seg.root] = Node{0, seg.len, (uint32_t)seg.start, 0};
+    r.ndim[seg.root] = PKD_LEAF;
+    atomicAdd(heavy_ctr, 1u);
+    atomicMax(&r.st->max_depth, seg.depth);
+    return;
+  }
+  const uint32_t nt = (seg.len + r.TILE - 1) / r.TILE;
+  const uint64_t hb = (uint64_t)r.tile0[s] * r.NB;
+  const uint32_t base = r.hscan[hb];
+  // subtree sizes, children before parents (heap order reversed)
+  uint32_t* size = r.sizes + (uint64_t)s * r.HN;
+  for (int v = r.HN - 1; v >= 1; --v) {
+    const int st = sk_state(sk[v].y);
+    if (st == SK_BUCKET) {
+      const int b = sk_bucket(sk[v].y);
+      const uint32_t b0 = r.hscan[hb + (uint64_t)b * nt] - base;
+      const uint32_t b1 = (b + 1 < (int)nb) ? r.hscan[hb + (uint64_t)(b + 1) * nt] - base : seg.len;
+      size[v] = b1 - b0;
+      Seg c;
+      c.start = seg.start + b0;
+      c.len = b1 - b0;
+      c.depth = seg.depth + (31 - __clz(v));
+      c.root = sl[v];
+      c.where = (uint32_t)r.dst_where;
+      ch[b] = c;
+    } else if (st == SK_INTERNAL) {
+      size[v] = size[2 * v] + size[2 * v + 1];
+      r.nodes[sl[v]] = Node{sk[v].x, size[v], sl[2 * v], sl[2 * v + 1]};
+      r.ndim[sl[v]] = (uint8_t)sk_dim(sk[v].y);
+    }
+  }
+  if (size[1] != seg.len) set_error(r.st, DERR_STATE, 700);
+}
+
+template <int D>
+__global__ void __launch_bounds__(SIEVE_THREADS) k_scatter(RoundArgs r) {
+  SieveTile t;
+  if (!sieve_tile(r, t)) return;
+  extern __shared__ __align__(16) uint8_t sm[];
+  int2* sk = (int2*)sm;
+  unsigned* cur = (unsigned*)(sk + r.HN);      // [NB] per-bucket counters, then starts
+  unsigned* lstart = cur + r.NB;               // [NB]
+  uint32_t* gbase = lstart + r.NB;             // [NB] (relative to the segment start)
+  int32_t* stx = (int32_t*)(gbase + r.NB);     // [D][TILE]
+  uint32_t* sid = (uint32_t*)(stx + (size_t)D * r.TILE);
+  uint16_t* sb = (uint16_t*)(sid + r.TILE);
+  const int2* gsk = r.skel + (uint64_t)t.s * r.HN;
+  for (int v = threadIdx.x; v < r.HN; v += blockDim.x) sk[v] = gsk[v];
+  for (int b = threadIdx.x; b < r.NB; b += blockDim.x) cur[b] = 0;
+  __syncthreads();
+  if (sk_state(sk[1].y) == SK_HEAVY) return;
+  constexpr int PER = 8;  // TILE <= PER * SIEVE_THREADS
+  int32_t x[PER][D];
+  uint32_t id[PER];
+  int bk[PER], rk[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int i = k * SIEVE_THREADS + threadIdx.x;
+    bk[k] = -1;
+    rk[k] = 0;
+    if (i < t.cnt) {
+      const uint64_t g = t.seg.start + t.first + i;
+#pragma unroll
+      for (int j = 0; j < D; ++j) x[k][j] = r.src.x(D, j, g);
+      id[k] = r.src.id(g);
+      bk[k] = walk_bucket<D>(sk, x[k], r.lam);
+    }
+    const unsigned m = __match_any_sync(FULL_MASK, bk[k]);
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (bk[k] >= 0 && lane_id() == leader) base = atomicAdd(&cur[bk[k]], (unsigned)__popc(m));
+    base = __shfl_sync(FULL_MASK, base, leader);
+    rk[k] = (int)base + __popc(m & lanemask_lt());
+  }
+  __syncthreads();
+  // bucket starts inside the tile, and global bases from the scan
+  if (threadIdx.x < 32) {
+    unsigned carry = 0;
+    for (int b0 = 0; b0 < r.NB; b0 += 32) {
+      const int b = b0 + lane_id();
+      const unsigned c = b < r.NB ? cur[b] : 0;
+      const unsigned incl = (unsigned)warp_incl_scan((int)c);
+      if (b < r.NB) lstart[b] = carry + incl - c;
+      carry += __shfl_sync(FULL_MASK, incl, 31);
+    }
+  }
+  const uint64_t hb = (uint64_t)t.t0 * r.NB;
+  const uint32_t tl = blockIdx.x - t.t0;
+  const uint32_t segbase = r.hscan[hb];
+  for (int b = threadIdx.x; b < r.NB; b += blockDim.x)
+    gbase[b] = r.hscan[hb + (uint64_t)b * t.nt + tl] - segbase;
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    if (bk[k] >= 0) {
+      const int pos = (int)lstart[bk[k]] + rk[k];
+#pragma unroll
+      for (int j = 0; j < D; ++j) stx[j * r.TILE + pos] = x[k][j];
+      sid[pos] = id[k];
+      sb[pos] = (uint16_t)bk[k];
+    }
+  }
+  __syncthreads();
+  // every bucket's run leaves the tile as one contiguous, coalesced range
+  for (int pos = threadIdx.x; pos < t.cnt; pos += blockDim.x) {
+    const int b = sb[pos];
+    const uint64_t g = t.seg.start + gbase[b] + (uint64_t)(pos - (int)lstart[b]);
+#pragma unroll
+    for (int j = 0; j < D; ++j) r.dst.c[(uint64_t)j * r.dst.stride + g] = stx[j * r.TILE + pos];
+    r.dst.id[g] = sid[pos];
+  }
+}
+
+// Heavy segments whose points are not yet in the arena.
+__global__ void k_copy_heavy(RoundArgs r) {
+  SieveTile t;
+  if (!sieve_tile(r, t)) return;
+  if (sk_state(r.skel[(uint64_t)t.s * r.HN + 1].y) != SK_HEAVY) return;
+  for (int i = threadIdx.x; i < t.cnt; i += blockDim.x) {
+    const uint64_t g = t.seg.start + t.first + i;
+    for (int j = 0; j < r.p.d; ++j) r.A.c[(uint64_t)j * r.A.stride + g] = r.src.x(r.p.d, j, g);
+    r.A.id[g] = r.src.id(g);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host orchestration
+// ---------------------------------------------------------------------------
+
+static int smem_optin() {
+  static int v = -1;
+  if (v < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (v <= 0) v = 48 * 1024;
+  }
+  return v;
+}
+
+static int cap_for_bytes(int d, size_t budget) {
+  int lo = 64, hi = 65535;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) / 2;
+    if (smem_layout(mid, d).total <= budget) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo & ~63;
+}
+
+int base_cap_for(int d) {
+  if (knobs().base_cap > 0) return knobs().base_cap;
+  const size_t budget = (size_t)std::min(smem_optin(), 200 * 1024);
+  return std::min(cap_for_bytes(d, budget), 16384);
+}
+
+int skel_cap_for(int d) {
+  if (knobs().skel_cap > 0) return knobs().skel_cap;
+  const size_t budget = (size_t)std::min(smem_optin(), 200 * 1024);
+  return std::min(cap_for_bytes(d, budget), 16384);
+}
+
+static size_t scatter_smem(int HN, int NB, int D, int tile) {
+  return (size_t)HN * 8 + (size_t)NB * 12 + (size_t)D * tile * 4 + (size_t)tile * 4 + (size_t)tile * 2;
+}
+
+template <int D>
+static void launch_count(const RoundArgs& r, uint32_t tiles, cudaStream_t s) {
+  const size_t sm = (size_t)r.HN * 8 + (size_t)r.NB * 4;
+  KTimer kt;
+  ktimer_begin(kt, "count", 0, s);
+  k_count<D><<<tiles, SIEVE_THREADS, sm, s>>>(r);
+  ktimer_end(kt);
+}
+
+template <int D>
+static void launch_scatter(const RoundArgs& r, uint32_t tiles, uint64_t pts, cudaStream_t s) {
+  const size_t sm = scatter_smem(r.HN, r.NB, D, r.TILE);
+  static bool set = false;
+  if (!set) {
+    cudaFuncSetAttribute(k_scatter<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    set = true;
+  }
+  KTimer kt;
+  ktimer_begin(kt, "scatter", pts, s);
+  k_scatter<D><<<tiles, SIEVE_THREADS, sm, s>>>(r);
+  ktimer_end(kt);
+}
+
+#define PKD_DISPATCH_D(d, F, ...) \
+  switch (d) {                    \
+    case 1: F<1>(__VA_ARGS__); break; \
+    case 2: F<2>(__VA_ARGS__); break; \
+    case 3: F<3>(__VA_ARGS__); break; \
+    case 4: F<4>(__VA_ARGS__); break; \
+    case 5: F<5>(__VA_ARGS__); break; \
+    case 6: F<6>(__VA_ARGS__); break; \
+    case 7: F<7>(__VA_ARGS__); break; \
+    default: F<8>(__VA_ARGS__); break; \
+  }
+
+// Shift a structure-of-arrays view so that absolute arena positions index
+// into a scratch allocation that only covers [base, base + extent).
+static Pts shifted(const Pts& p, uint64_t base) {
+  Pts q = p;
+  q.c = p.c - base;
+  q.id = p.id - base;
+  return q;
+}
+
+struct Scratch {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  ~Scratch() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+  }
+  template <class T>
+  int get(T** p, size_t n) {
+    int e = dalloc(p, n, s);
+    if (e == PKD_OK) ptrs.push_back(*p);
+    return e;
+  }
+};
+
+#define PKD_TRY(x)               \
+  do {                           \
+    int _r = (x);                \
+    if (_r != PKD_OK) return _r; \
+  } while (0)
+
+// Run the job levels for skeleton nodes whose samples exceed one CTA, then
+// finish every small node in shared memory.
+static int run_skeleton_jobs(JobArgs ja, SkelJob* big0, uint32_t nbig_jobs, uint32_t big_tiles,
+                             uint32_t nsmall_host, SmemArgs sa, uint32_t* hctr, uint32_t* dctr,
+                             SkelJob* bigA, SkelJob* bigB, uint32_t* d_njobs, Scratch& sc,
+                             cudaStream_t s) {
+  (void)big0;
+  SkelJob* cur = bigA;
+  SkelJob* nxt = bigB;
+  uint32_t njobs = nbig_jobs, tiles = big_tiles;
+  JobState* js = nullptr;
+  uint32_t* jhist = nullptr;
+  uint32_t* jtile0 = nullptr;
+  uint32_t cap_jobs = 0;
+  while (njobs > 0) {
+    if (njobs > cap_jobs) {
+      cap_jobs = std::max(njobs, 64u);
+      PKD_TRY(sc.get(&js, cap_jobs));
+      PKD_TRY(sc.get(&jhist, (size_t)cap_jobs * 256));
+      PKD_TRY(sc.get(&jtile0, cap_jobs));
+    }
+    PKD_CUDA(cudaMemcpyAsync(d_njobs, &njobs, 4, cudaMemcpyHostToDevice, s));
+    ja.jobs = cur;
+    ja.njobs = d_njobs;
+    ja.jtile0 = jtile0;
+    ja.js = js;
+    ja.jhist = jhist;
+    ja.next_big = nxt;
+    const unsigned g1 = (njobs + 127) / 128;
+    k_job_tiles<<<1, 1024, 0, s>>>(cur, d_njobs, jtile0);
+    k_job_init<<<g1, 128, 0, s>>>(ja);
+    PKD_CUDA(cudaMemsetAsync(dctr, 0, 8, s));  // next big jobs and tiles
+    k_job_stats<<<tiles, JOB_THREADS, 0, s>>>(ja);
+    k_job_choose<<<g1, 128, 0, s>>>(ja);
+    for (int pass = 0; pass < 4; ++pass) {
+      k_job_hist<<<tiles, JOB_THREADS, 0, s>>>(ja, pass);
+      k_job_pick<<<(njobs * 32 + 127) / 128, 128, 0, s>>>(ja, pass);
+    }
+    k_job_minabove<<<tiles, JOB_THREADS, 0, s>>>(ja);
+    k_job_fix<<<g1, 128, 0, s>>>(ja);
+    k_job_partition<<<tiles, JOB_THREADS, 0, s>>>(ja);
+    k_job_children<<<g1, 128, 0, s>>>(ja);
+    PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 12, cudaMemcpyDeviceToHost, s));
+    PKD_CUDA(cudaStreamSynchronize(s));
+    njobs = hctr[0];
+    tiles = hctr[1];
+    std::swap(cur, nxt);
+  }
+  // small jobs: the count lives in dctr[2]
+  PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 12, cudaMemcpyDeviceToHost, s));
+  PKD_CUDA(cudaStreamSynchronize(s));
+  const uint32_t nsmall = hctr[2];
+  (void)nsmall_host;
+  if (nsmall > 0) {
+    sa.jobs = ja.small;
+    sa.njobs = dctr + 2;
+    const int d = sa.p.d;
+    sa.cap = skel_cap_for(d);
+    const size_t smb = smem_layout(sa.cap, d).total;
+    cudaFuncSetAttribute(k_smem_skel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+    k_smem_skel<<<nsmall, SM_THREADS, smb, s>>>(sa);
+  }
+  return PKD_OK;
+}
+
+int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
+  const Params& p = t.p;
+  const int d = p.d;
+  const int lam = p.lambda;
+  const int NB = 1 << lam, HN = 2 << lam;
+  const int TILE = std::min(std::max(knobs().tile, 256), 4096);
+  const uint32_t cap = (uint32_t)base_cap_for(d);
+  const int scap = skel_cap_for(d);
+  const uint64_t base = job.base, extent = std::max<uint64_t>(job.extent, 1);
+  Scratch sc{s, {}};
+
+  // scratch point buffer B and two sample buffers over [base, base + extent)
+  int32_t *bc, *s0c, *s1c;
+  uint32_t* bid;
+  PKD_TRY(sc.get(&bc, (size_t)d * extent));
+  PKD_TRY(sc.get(&bid, extent));
+  PKD_TRY(sc.get(&s0c, (size_t)d * extent));
+  PKD_TRY(sc.get(&s1c, (size_t)d * extent));
+  const Pts B = shifted(Pts{bc, bid, extent}, base);
+  Pts S0 = shifted(Pts{s0c, bid, extent}, base), S1 = shifted(Pts{s1c, bid, extent}, base);
+  S0.id = S1.id = nullptr;
+
+  // device counters: [0] big segs, [2] their tiles, [3] exact, [4] heavy,
+  // [8..10] skeleton jobs; [12] base list length; u64 at [14] big points
+  uint32_t* dctr;
+  PKD_TRY(sc.get(&dctr, 16));
+  unsigned long long* dpts = (unsigned long long*)(dctr + 14);
+  uint32_t* d_nbase = dctr + 12;
+  uint32_t* hctr = nullptr;
+  PKD_CUDA(cudaMallocHost((void**)&hctr, 64));
+  struct HostFree {
+    uint32_t* p;
+    ~HostFree() { cudaFreeHost(p); }
+  } hf{hctr};
+  PKD_CUDA(cudaMemsetAsync(dctr, 0, 16 * 4, s));
+
+  const uint64_t nroots = job.segs.size();
+  Seg* cur;
+  PKD_TRY(sc.get(&cur, std::max<uint64_t>(nroots, 1)));
+  PKD_CUDA(cudaMemcpyAsync(cur, job.segs.data(), nroots * sizeof(Seg), cudaMemcpyHostToDevice, s));
+  uint64_t ncur = nroots;
+  // every base segment is a root or a non-empty bucket: at most extent + roots
+  const uint64_t base_cap_segs = extent + nroots + 16;
+  Seg* base_list;
+  PKD_TRY(sc.get(&base_list, base_cap_segs));
+
+  Src src{};
+  int src_where;
+  if (job.input_coords) {
+    src.aos = job.input_coords;
+    src.aos_ids = job.input_ids;
+    src.is_aos = 1;
+    src_where = IN_INPUT;
+  } else {
+    src.soa = t.A;
+    src.is_aos = 0;
+    src_where = IN_A;
+  }
+
+  SmemArgs sa{};
+  sa.p = p;
+  sa.A = t.A;
+  sa.B = B;
+  sa.in_coords = job.input_coords;
+  sa.in_ids = job.input_ids;
+  sa.nodes = t.nodes;
+  sa.ndim = t.ndim;
+  sa.st = t.st;
+  sa.sbuf[0] = S0.c;
+  sa.sbuf[1] = S1.c;
+  sa.sstride = extent;
+  sa.heap_n = HN;
+  sa.shared_cap = t.shared_cap;
+
+  uint32_t* d_nj;
+  PKD_TRY(sc.get(&d_nj, 4));
+
+  for (int round = 0; ncur > 0; ++round) {
+    if (round > 64) return PKD_EINTERNAL;
+    Seg* big;
+    PKD_TRY(sc.get(&big, ncur));
+    PKD_CUDA(cudaMemsetAsync(dctr, 0, 12 * 4, s));
+    PKD_CUDA(cudaMemsetAsync(dpts, 0, 8, s));
+    k_classify<<<(unsigned)((ncur + 255) / 256), 256, 0, s>>>(
+        cur, (uint32_t)ncur, cap, big, dctr, dpts, base_list, d_nbase, (uint32_t)base_cap_segs,
+        (uint32_t)TILE, (uint32_t)src_where, t.st);
+    PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 16 * 4, cudaMemcpyDeviceToHost, s));
+    PKD_CUDA(cudaStreamSynchronize(s));
+    const uint32_t nbig = hctr[0], tiles = hctr[2];
+    const uint64_t pts_big = *(unsigned long long*)(hctr + 14);
+    if (nbig == 0) break;
+
+    RoundArgs r{};
+    r.p = p;
+    r.lam = lam;
+    r.NB = NB;
+    r.HN = HN;
+    r.TILE = TILE;
+    r.src = src;
+    const bool dst_is_A = (src_where == IN_B);
+    r.dst = dst_is_A ? t.A : B;
+    r.dst_where = dst_is_A ? IN_A : IN_B;
+    r.A = t.A;
+    r.big = big;
+    r.nbig = dctr;
+    PKD_TRY(sc.get(&r.tile0, nbig));
+    PKD_TRY(sc.get(&r.excl, nbig));
+    PKD_TRY(sc.get(&r.skel, (size_t)nbig * HN));
+    PKD_TRY(sc.get(&r.slots, (size_t)nbig * HN));
+    PKD_TRY(sc.get(&r.sizes, (size_t)nbig * HN));
+    PKD_TRY(sc.get(&r.nbk, nbig));
+    PKD_TRY(sc.get(&r.exact, nbig));
+    PKD_TRY(sc.get(&r.hist, (size_t)tiles * NB));
+    PKD_TRY(sc.get(&r.hscan, (size_t)tiles * NB));
+    PKD_TRY(sc.get(&r.scnt, nbig));
+    PKD_TRY(sc.get(&r.children, (size_t)nbig * NB));
+    r.samp = S0;
+    r.nodes = t.nodes;
+    r.ndim = t.ndim;
+    r.shared_next = t.shared_next;
+    r.shared_cap = t.shared_cap;
+    r.st = t.st;
+    PKD_CUDA(cudaMemsetAsync(r.skel, 0, (size_t)nbig * HN * sizeof(int2), s));
+    PKD_CUDA(cudaMemsetAsync(r.scnt, 0, (size_t)nbig * 4, s));
+    PKD_CUDA(cudaMemsetAsync(r.exact, 0, nbig, s));
+    k_big_prefix<<<1, 1024, 0, s>>>(big, dctr, (uint32_t)TILE, r.tile0, r.excl);
+
+    // 1. sample
+    {
+      KTimer kt;
+      ktimer_begin(kt, "sample", pts_big, s);
+      k_sample<<<tiles, 256, 0, s>>>(r);
+      ktimer_end(kt);
+    }
+
+    // 2. skeletons (and, for segments whose skeleton root is a bucket, one
+    //    exact level on their own points)
+    JobArgs ja{};
+    ja.p = p;
+    ja.d = d;
+    ja.sb[0] = S0;
+    ja.sb[1] = S1;
+    ja.skel = r.skel;
+    ja.HN = HN;
+    ja.scap = scap;
+    ja.st = t.st;
+    const uint32_t small_cap = nbig * (uint32_t)NB + 16;
+    const uint32_t big_cap = (uint32_t)std::min<uint64_t>(pts_big / (uint64_t)scap + nbig + 16, 1u << 30);
+    SkelJob *bigA, *bigB, *small;
+    PKD_TRY(sc.get(&bigA, big_cap));
+    PKD_TRY(sc.get(&bigB, big_cap));
+    PKD_TRY(sc.get(&small, small_cap));
+    ja.small = small;
+    ja.small_cap = small_cap;
+    ja.big_cap = big_cap;
+    uint32_t* jctr = dctr + 8;
+    ja.next_ctr = jctr;
+    sa.skel = r.skel;
+    for (int exact_pass = 0; exact_pass < 2; ++exact_pass) {
+      if (exact_pass == 1) {
+        k_mark_exact<<<(nbig + 127) / 128, 128, 0, s>>>(r, dctr + 3);
+        PKD_CUDA(cudaMemcpyAsync(hctr + 3, dctr + 3, 4, cudaMemcpyDeviceToHost, s));
+        PKD_CUDA(cudaStreamSynchronize(s));
+        if (hctr[3] == 0) break;
+        k_copy_exact<<<tiles, 256, 0, s>>>(r);
+      }
+      PKD_CUDA(cudaMemsetAsync(jctr, 0, 12, s));
+      ja.next_big = bigA;
+      k_root_jobs<<<(nbig + 127) / 128, 128, 0, s>>>(r, ja, exact_pass);
+      PKD_CUDA(cudaMemcpyAsync(hctr + 8, jctr, 12, cudaMemcpyDeviceToHost, s));
+      PKD_CUDA(cudaStreamSynchronize(s));
+      PKD_TRY(run_skeleton_jobs(ja, bigA, hctr[8], hctr[9], 0, sa, hctr + 8, jctr, bigA, bigB, d_nj,
+                                sc, s));
+    }
+
+    // 3. finalize skeletons, count, scan, emit, scatter
+    k_finalize<<<(nbig + 127) / 128, 128, 0, s>>>(r);
+    PKD_DISPATCH_D(d, launch_count, r, tiles, s);
+    uint32_t* partial;
+    const uint64_t nh = (uint64_t)tiles * NB;
+    PKD_TRY(sc.get(&partial, (nh + SCAN_TILE - 1) / SCAN_TILE + 1));
+    device_excl_scan(r.hist, r.hscan, nh, partial, s);
+    k_emit<<<(nbig + 63) / 64, 64, 0, s>>>(r, dctr + 4);
+    PKD_DISPATCH_D(d, launch_scatter, r, tiles, pts_big, s);
+    k_copy_heavy<<<tiles, 256, 0, s>>>(r);
+
+    // 4. the buckets, now in the destination buffer, are the next round
+    cur = r.children;
+    ncur = (uint64_t)nbig * NB;
+    src.soa = r.dst;
+    src.is_aos = 0;
+    src_where = r.dst_where;
+  }
+
+  // 5. every small subproblem, one CTA each, in shared memory
+  PKD_CUDA(cudaMemcpyAsync(hctr + 12, d_nbase, 4, cudaMemcpyDeviceToHost, s));
+  PKD_CUDA(cudaStreamSynchronize(s));
+  const uint32_t nbase = std::min<uint32_t>(hctr[12], (uint32_t)base_cap_segs);
+  if (nbase > 0) {
+    sa.segs = base_list;
+    sa.nsegs = d_nbase;
+    sa.cap = (int)cap;
+    const size_t smb = smem_layout((int)cap, d).total;
+    PKD_CUDA(cudaFuncSetAttribute(k_smem_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+    KTimer kt;
+    ktimer_begin(kt, "smem_build", 0, s);
+    k_smem_build<<<nbase, SM_THREADS, smb, s>>>(sa);
+    ktimer_end(kt);
+  }
+  PKD_CUDA(cudaGetLastError());
+  return PKD_OK;
+}
+
+}  // namespace pkd

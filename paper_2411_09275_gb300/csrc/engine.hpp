@@ -1,0 +1,106 @@
+// Host-side engine state of a Pkd-tree (device memory it owns, streams,
+// tuning knobs, kernel timers).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace pkd {
+
+// Tunables; none of them changes any result.
+struct Knobs {
+  int base_cap = 0;   // 0: derived from d and the shared memory per block
+  int skel_cap = 0;   // 0: derived
+  int tile = 4096;    // points per CTA in the sieve kernels
+};
+Knobs& knobs();
+
+// Device memory of one tree.
+//
+// Node slots: [0, shared_cap) is a shared region handed out by an atomic
+// counter (skeleton nodes of sieve rounds, tree roots); slot
+// shared_cap + 2*pos + k (k < 2) belongs to arena position pos, so the
+// nodes of a subproblem finished in shared memory over positions
+// [s, s + L) live in [shared_cap + 2s, shared_cap + 2s + 2L) without any
+// global coordination (a binary tree over L >= 1 points has <= 2L - 1 nodes).
+struct TreeMem {
+  Params p{};
+  int device = 0;
+  Pts A{};                 // point arena (SoA), capacity `cap`
+  uint64_t cap = 0;
+  uint64_t top = 0;        // arena positions [0, top) are in use or garbage
+  Node* nodes = nullptr;
+  uint8_t* ndim = nullptr;
+  uint64_t shared_cap = 0;
+  uint64_t node_cap = 0;   // shared_cap + 2*cap
+  uint32_t* shared_next = nullptr;  // device: next free slot of the shared region
+  uint32_t root = 0;
+  uint64_t size = 0;
+  DevStatus* st = nullptr;          // device status word
+  DevStatus* st_host = nullptr;     // pinned mirror
+};
+
+// Error helpers.
+int cuda_err(cudaError_t e);
+#define PKD_CUDA(x)                          \
+  do {                                       \
+    cudaError_t _e = (x);                    \
+    if (_e != cudaSuccess) return cuda_err(_e); \
+  } while (0)
+
+// Stream-ordered scratch allocation.
+template <class T>
+int dalloc(T** p, size_t n, cudaStream_t s) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMallocAsync((void**)p, n * sizeof(T), s);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return PKD_ENOMEM;
+  }
+  return e == cudaSuccess ? PKD_OK : cuda_err(e);
+}
+template <class T>
+void dfree(T*& p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+  p = nullptr;
+}
+
+// Reads the device status word; PKD_OK or the mapped error.
+int check_status(TreeMem& t, cudaStream_t s);
+
+// Kernel timing (CUDA events on the launching stream).
+struct KTimer {
+  bool on = false;
+  cudaEvent_t a = nullptr, b = nullptr;
+  std::string name;
+  uint64_t items = 0;
+  cudaStream_t s = nullptr;
+};
+void ktimer_begin(KTimer& k, const char* name, uint64_t items, cudaStream_t s);
+void ktimer_end(KTimer& k);
+bool ktiming_enabled();
+
+// A build of independent subproblems ("segments"): every segment's points
+// sit at arena positions [start, start+len) of A (or of the caller's input
+// when `input_coords` is set), its root goes to node slot `root`, its depth
+// salts the samples.  On return each segment's points are in A in leaf order
+// and its subtree is written to the node arrays.
+struct BuildJob {
+  const int32_t* input_coords = nullptr;  // point-major input (segments IN_INPUT)
+  const uint32_t* input_ids = nullptr;
+  uint64_t base = 0;       // lowest arena position of any segment
+  uint64_t extent = 0;     // highest position + 1 - base
+  std::vector<Seg> segs;   // host list of root segments
+};
+int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s);
+
+// Derived shared-memory capacities.
+int base_cap_for(int d);
+int skel_cap_for(int d);
+
+}  // namespace pkd

@@ -1,0 +1,294 @@
+// Queries on a Pkd-tree (Sec. 5 "Queries" of the paper): k nearest neighbours
+// by depth-first search (near child first, a subtree pruned when its subspace
+// is strictly farther than the current k-th candidate) and range counting
+// (a subtree whose subspace lies inside the box adds its stored size).
+// Subspaces are not stored: each stack entry carries the box implied by the
+// splitters above it, as the paper does instead of keeping bounding boxes.
+// One thread per query; the stack holds at most height + 1 entries.
+#include <algorithm>
+
+#include "engine.hpp"
+#include "tree_impl.hpp"
+
+namespace pkd {
+
+constexpr int QSTACK = 128;
+constexpr int QTHREADS = 128;
+
+template <int D>
+struct Box {
+  int32_t lo[D], hi[D];
+};
+
+template <int D>
+__device__ __forceinline__ long long box_dist2(const int32_t* q, const Box<D>& b) {
+  long long s = 0;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    long long t = 0;
+    if (q[j] < b.lo[j]) t = (long long)b.lo[j] - q[j];
+    else if (q[j] > b.hi[j]) t = (long long)q[j] - b.hi[j];
+    s += t * t;
+  }
+  return s;
+}
+
+struct QueryArgs {
+  const Node* nodes;
+  const uint8_t* ndim;
+  Pts A;
+  uint32_t root;
+  const int32_t* q;
+  const int32_t* hi;
+  uint64_t nq;
+  int k;
+  uint32_t* out_ids;
+  int64_t* out_d2;
+  uint64_t* out_cnt;
+  DevStatus* st;
+};
+
+template <int D, int KMAX>
+__global__ void __launch_bounds__(QTHREADS) k_knn(QueryArgs a) {
+  const uint64_t qi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (qi >= a.nq) return;
+  int32_t q[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) q[j] = a.q[qi * D + j];
+  long long bd[KMAX];
+  uint32_t bi[KMAX];
+  const int k = a.k;
+  for (int i = 0; i < KMAX; ++i) {
+    bd[i] = LLONG_MAX;
+    bi[i] = 0xFFFFFFFFu;
+  }
+  uint32_t sv[QSTACK];
+  Box<D> sb[QSTACK];
+  int sp = 0;
+  sv[0] = a.root;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    sb[0].lo[j] = 0;
+    sb[0].hi[j] = PKD_COORD_LIMIT - 1;
+  }
+  sp = 1;
+  while (sp > 0) {
+    --sp;
+    const uint32_t v = sv[sp];
+    const Box<D> b = sb[sp];
+    if (box_dist2<D>(q, b) > bd[k - 1]) continue;
+    const uint8_t dm = a.ndim[v];
+    const Node nd = a.nodes[v];
+    if (dm == PKD_LEAF) {
+      for (uint32_t i = 0; i < nd.size; ++i) {
+        const uint64_t g = (uint64_t)nd.a + i;
+        long long d2 = 0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          long long t = (long long)a.A.c[(uint64_t)j * a.A.stride + g] - q[j];
+          d2 += t * t;
+        }
+        const uint32_t id = a.A.id[g];
+        if (d2 > bd[k - 1] || (d2 == bd[k - 1] && id >= bi[k - 1])) continue;
+        int p = k - 1;
+        while (p > 0 && (bd[p - 1] > d2 || (bd[p - 1] == d2 && bi[p - 1] > id))) {
+          bd[p] = bd[p - 1];
+          bi[p] = bi[p - 1];
+          --p;
+        }
+        bd[p] = d2;
+        bi[p] = id;
+      }
+      continue;
+    }
+    if (sp + 2 > QSTACK) {
+      set_error(a.st, DERR_STACK, 900);
+      break;
+    }
+    const int j = dm;
+    const int32_t x = nd.split;
+    Box<D> L = b, R = b;
+    L.hi[j] = min(L.hi[j], x - 1);
+    R.lo[j] = max(R.lo[j], x);
+    const bool near_left = q[j] < x;
+    // far child first, so the near child is searched next
+    sv[sp] = near_left ? nd.b : nd.a;
+    sb[sp] = near_left ? R : L;
+    ++sp;
+    sv[sp] = near_left ? nd.a : nd.b;
+    sb[sp] = near_left ? L : R;
+    ++sp;
+  }
+  for (int i = 0; i < k; ++i) {
+    a.out_d2[qi * k + i] = bd[i];
+    a.out_ids[qi * k + i] = bi[i];
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(QTHREADS) k_range_count(QueryArgs a) {
+  const uint64_t qi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (qi >= a.nq) return;
+  int32_t lo[D], hi[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    lo[j] = a.q[qi * D + j];
+    hi[j] = a.hi[qi * D + j];
+  }
+  uint32_t sv[QSTACK];
+  Box<D> sb[QSTACK];
+  sv[0] = a.root;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    sb[0].lo[j] = 0;
+    sb[0].hi[j] = PKD_COORD_LIMIT - 1;
+  }
+  int sp = 1;
+  unsigned long long cnt = 0;
+  while (sp > 0) {
+    --sp;
+    const uint32_t v = sv[sp];
+    const Box<D> b = sb[sp];
+    bool disjoint = false, inside = true;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      disjoint |= (b.hi[j] < lo[j]) | (b.lo[j] > hi[j]) | (b.hi[j] < b.lo[j]);
+      inside &= (b.lo[j] >= lo[j]) & (b.hi[j] <= hi[j]);
+    }
+    if (disjoint) continue;
+    const Node nd = a.nodes[v];
+    if (inside) {
+      cnt += nd.size;
+      continue;
+    }
+    const uint8_t dm = a.ndim[v];
+    if (dm == PKD_LEAF) {
+      for (uint32_t i = 0; i < nd.size; ++i) {
+        const uint64_t g = (uint64_t)nd.a + i;
+        bool in = true;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          const int32_t x = a.A.c[(uint64_t)j * a.A.stride + g];
+          in &= (x >= lo[j]) & (x <= hi[j]);
+        }
+        cnt += in;
+      }
+      continue;
+    }
+    if (sp + 2 > QSTACK) {
+      set_error(a.st, DERR_STACK, 901);
+      break;
+    }
+    const int j = dm;
+    Box<D> L = b, R = b;
+    L.hi[j] = min(L.hi[j], nd.split - 1);
+    R.lo[j] = max(R.lo[j], nd.split);
+    sv[sp] = nd.b;
+    sb[sp] = R;
+    ++sp;
+    sv[sp] = nd.a;
+    sb[sp] = L;
+    ++sp;
+  }
+  a.out_cnt[qi] = cnt;
+}
+
+template <int D>
+static void launch_knn(const QueryArgs& a, cudaStream_t s) {
+  const unsigned g = (unsigned)((a.nq + QTHREADS - 1) / QTHREADS);
+  KTimer kt;
+  ktimer_begin(kt, "knn", a.nq, s);
+  if (a.k <= 16) k_knn<D, 16><<<g, QTHREADS, 0, s>>>(a);
+  else k_knn<D, 128><<<g, QTHREADS, 0, s>>>(a);
+  ktimer_end(kt);
+}
+
+template <int D>
+static void launch_rc(const QueryArgs& a, cudaStream_t s) {
+  const unsigned g = (unsigned)((a.nq + QTHREADS - 1) / QTHREADS);
+  KTimer kt;
+  ktimer_begin(kt, "range_count", a.nq, s);
+  k_range_count<D><<<g, QTHREADS, 0, s>>>(a);
+  ktimer_end(kt);
+}
+
+#define PKD_QDISPATCH(d, F, ...)      \
+  switch (d) {                        \
+    case 1: F<1>(__VA_ARGS__); break; \
+    case 2: F<2>(__VA_ARGS__); break; \
+    case 3: F<3>(__VA_ARGS__); break; \
+    case 4: F<4>(__VA_ARGS__); break; \
+    case 5: F<5>(__VA_ARGS__); break; \
+    case 6: F<6>(__VA_ARGS__); break; \
+    case 7: F<7>(__VA_ARGS__); break; \
+    default: F<8>(__VA_ARGS__); break; \
+  }
+
+static int query_height_ok(const TreeMem& t) {
+  // the depth-first stack holds at most height + 1 entries
+  return t.st_host && t.st_host->max_depth + 2 < (uint32_t)QSTACK;
+}
+
+}  // namespace pkd
+
+using namespace pkd;
+
+extern "C" {
+
+int pkd_knn(const pkd_tree* tc, const int32_t* queries, uint64_t q, int k, uint32_t* out_ids,
+            int64_t* out_d2, void* stream) {
+  if (!tc || k < 1 || k > 128) return PKD_EINVAL;
+  if (q == 0) return PKD_OK;
+  if (!queries || !out_ids || !out_d2) return PKD_EINVAL;
+  TreeMem& t = const_cast<TreeMem&>(tc->m);
+  cudaStream_t s = (cudaStream_t)stream;
+  bool ok;
+  PKD_TRY_(validate_coords(queries, q * (uint64_t)t.p.d, s, &ok));
+  if (!ok) return PKD_EINVAL;
+  PKD_TRY_(check_status(t, s));
+  if (!query_height_ok(t)) return PKD_EINTERNAL;
+  QueryArgs a{};
+  a.nodes = t.nodes;
+  a.ndim = t.ndim;
+  a.A = t.A;
+  a.root = t.root;
+  a.q = queries;
+  a.nq = q;
+  a.k = k;
+  a.out_ids = out_ids;
+  a.out_d2 = out_d2;
+  a.st = t.st;
+  PKD_QDISPATCH(t.p.d, launch_knn, a, s);
+  PKD_CUDA(cudaGetLastError());
+  return PKD_OK;
+}
+
+int pkd_range_count(const pkd_tree* tc, const int32_t* lo, const int32_t* hi, uint64_t q,
+                    uint64_t* out_counts, void* stream) {
+  if (!tc) return PKD_EINVAL;
+  if (q == 0) return PKD_OK;
+  if (!lo || !hi || !out_counts) return PKD_EINVAL;
+  TreeMem& t = const_cast<TreeMem&>(tc->m);
+  cudaStream_t s = (cudaStream_t)stream;
+  bool ok1, ok2;
+  PKD_TRY_(validate_coords(lo, q * (uint64_t)t.p.d, s, &ok1));
+  PKD_TRY_(validate_coords(hi, q * (uint64_t)t.p.d, s, &ok2));
+  if (!ok1 || !ok2) return PKD_EINVAL;
+  PKD_TRY_(check_status(t, s));
+  if (!query_height_ok(t)) return PKD_EINTERNAL;
+  QueryArgs a{};
+  a.nodes = t.nodes;
+  a.ndim = t.ndim;
+  a.A = t.A;
+  a.root = t.root;
+  a.q = lo;
+  a.hi = hi;
+  a.nq = q;
+  a.out_cnt = out_counts;
+  a.st = t.st;
+  PKD_QDISPATCH(t.p.d, launch_rc, a, s);
+  PKD_CUDA(cudaGetLastError());
+  return PKD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,381 @@
+// One CTA finishes a whole subproblem in shared memory (the base case of
+// Alg. 1: "the base case fits into the cache"), and the same frame builds
+// the skeleton of a sample that fits in shared memory.
+//
+// Points stay where they were loaded; only 16-bit index lists move.  A task
+// is one node: either the root of a Build(P, t) call (j == 0) or a skeleton
+// node at local depth j whose sample is the flagged subset of its points.
+// Because the sample of every skeleton node below a Build root is drawn at
+// that root's depth, one flag byte per point serves all its skeleton levels,
+// and partitioning the points level by level yields exactly the buckets a
+// sieve over the finished skeleton would (shared-memory traffic is cheap, so
+// the sieve's one-pass data movement buys nothing here).
+//
+// Scheduling: tasks larger than WMAX points are processed by the whole block
+// (a depth-first stack that always continues with the smaller child, so it
+// stays within log2(cap) entries); smaller tasks go to single warps, which
+// finish them depth first with the same stack discipline.
+#pragma once
+
+#include "team.cuh"
+
+namespace pkd {
+
+constexpr int SM_NW = 16;
+constexpr int SM_THREADS = SM_NW * 32;
+constexpr int WMAX = 512;
+constexpr int BSTK = 40;
+constexpr int WSTK = 24;
+constexpr int WLIST = 256;
+
+struct Task {
+  uint16_t lo, hi, ns;
+  uint8_t buf, j;
+  uint32_t t;     // tree depth of this node (build mode) / unused
+  uint32_t slot;  // node slot (build mode) / heap index (skeleton mode)
+};
+static_assert(sizeof(Task) == 16, "Task layout");
+
+struct SmemCtl {
+  int next_slot;
+  int bsp;
+  int wl_n;
+  int err;
+};
+
+// A skeleton node whose sample is still to be split: the node at heap index
+// h of segment `seg`, with n samples at a.. in sample buffer `buf`.
+struct SkelJob {
+  uint32_t seg;
+  uint32_t h;
+  uint64_t a;
+  uint32_t n;
+  uint8_t buf, j, lam, pad;
+  uint32_t min_split;  // split only with at least this many samples
+  uint32_t pad2;
+};
+static_assert(sizeof(SkelJob) == 32, "SkelJob layout");
+
+// Heap skeleton entry: split value and meta = state | dim << 8 | bucket << 16.
+enum SkState : int { SK_NONE = 0, SK_INTERNAL = 1, SK_BUCKET = 2, SK_HEAVY = 3 };
+__host__ __device__ __forceinline__ int sk_meta(int state, int dim, int bucket) {
+  return state | (dim << 8) | (bucket << 16);
+}
+__host__ __device__ __forceinline__ int sk_state(int meta) { return meta & 0xFF; }
+__host__ __device__ __forceinline__ int sk_dim(int meta) { return (meta >> 8) & 0xFF; }
+__host__ __device__ __forceinline__ int sk_bucket(int meta) { return (meta >> 16) & 0xFFFF; }
+
+// Arguments of the shared-memory kernels.
+struct SmemArgs {
+  Params p;
+  int cap;  // point capacity of the shared arrays
+  // build mode
+  Pts A, B;
+  const int32_t* in_coords;  // point-major input for IN_INPUT
+  const uint32_t* in_ids;    // NULL -> ids are input positions
+  Node* nodes;
+  uint8_t* ndim;
+  const Seg* segs;
+  const uint32_t* nsegs;  // device count of segs
+  // skeleton mode
+  const SkelJob* jobs;
+  const uint32_t* njobs;
+  const int32_t* sbuf[2];  // sample coordinate buffers (SoA, stride = sstride)
+  uint64_t sstride;
+  int2* skel;              // [seg][heap]
+  int heap_n;              // 2^(lambda+1)
+  uint64_t shared_cap;     // first per-position node slot
+  DevStatus* st;
+};
+
+struct SmemLayout {
+  size_t X, ID, perm0, perm1, flag, bhist, bred, whist, bstack, wlist, wstack, ctl, total;
+};
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline SmemLayout smem_layout(int cap, int d) {
+  SmemLayout L;
+  size_t o = 0;
+  L.X = o;
+  o = align_up(o + (size_t)4 * d * cap, 16);
+  L.ID = o;
+  o = align_up(o + (size_t)4 * cap, 16);
+  L.perm0 = o;
+  o = align_up(o + (size_t)2 * cap, 16);
+  L.perm1 = o;
+  o = align_up(o + (size_t)2 * cap, 16);
+  L.flag = o;
+  o = align_up(o + (size_t)cap, 16);
+  L.bhist = o;
+  o = align_up(o + 256 * 4, 16);
+  L.bred = o;
+  o = align_up(o + RED_INTS * 4, 16);
+  L.whist = o;
+  o = align_up(o + (size_t)SM_NW * 256 * 4, 16);
+  L.bstack = o;
+  o = align_up(o + BSTK * sizeof(Task), 16);
+  L.wlist = o;
+  o = align_up(o + WLIST * sizeof(Task), 16);
+  L.wstack = o;
+  o = align_up(o + (size_t)SM_NW * WSTK * sizeof(Task), 16);
+  L.ctl = o;
+  o = align_up(o + sizeof(SmemCtl), 16);
+  L.total = o;
+  return L;
+}
+
+struct SmemCtx {
+  Params p;
+  SmemPts s;
+  uint8_t* flag;
+  uint16_t* perm[2];
+  SmemCtl* ctl;
+  // build mode
+  Pts out;
+  uint64_t start;
+  uint32_t slot_base;
+  int slot_limit;
+  Node* nodes;
+  uint8_t* ndim;
+  // skeleton mode
+  int2* skel;  // this segment's heap
+  int lam;
+  int min_split;
+  DevStatus* st;
+};
+
+// ---------------------------------------------------------------------------
+// Build mode
+// ---------------------------------------------------------------------------
+
+template <class T>
+__device__ void emit_leaf(const T& tm, const SmemCtx& cx, const Task& tk) {
+  const uint16_t* P = cx.perm[tk.buf];
+  for (int i = tk.lo + tm.rank(); i < tk.hi; i += tm.size()) {
+    int p = P[i];
+    uint64_t g = cx.start + (uint64_t)i;
+    for (int j = 0; j < cx.s.d; ++j) cx.out.c[(uint64_t)j * cx.out.stride + g] = cx.s.x(j, p);
+    cx.out.id[g] = cx.s.ID[p];
+  }
+  if (tm.leader()) {
+    Node nd;
+    nd.split = 0;
+    nd.size = (uint32_t)(tk.hi - tk.lo);
+    nd.a = (uint32_t)(cx.start + tk.lo);
+    nd.b = 0;
+    cx.nodes[tk.slot] = nd;
+    cx.ndim[tk.slot] = PKD_LEAF;
+    atomicMax(&cx.st->max_depth, tk.t);
+  }
+}
+
+template <class T>
+__device__ int alloc_two(const T& tm, const SmemCtx& cx) {
+  int b = 0;
+  if (tm.leader()) b = atomicAdd(&cx.ctl->next_slot, 2);
+  b = tm.bcast(b);
+  return b;
+}
+
+// Process one node; returns the number of children written to ch (0 or 2).
+template <class T>
+__device__ int process_build(const T& tm, const SmemCtx& cx, Task tk, Task* ch) {
+  for (;;) {
+    const int lo = tk.lo, hi = tk.hi, n = hi - lo;
+    uint16_t* P = cx.perm[tk.buf];
+    uint16_t* Q = cx.perm[tk.buf ^ 1];
+    int dim = 0, x = 0;
+    bool on_sample;
+    if (tk.j == 0) {
+      // Build(P, t): leaf wrap, heavy leaf, then sample and skeleton root.
+      if (n <= cx.p.phi) {
+        emit_leaf(tm, cx, tk);
+        return 0;
+      }
+      int mn[PKD_DMAX], mx[PKD_DMAX];
+      team_minmax(tm, cx.s, P, lo, hi, false, mn, mx);
+      int wd = widest_dim(mn, mx, cx.s.d);
+      if (wd < 0) {
+        emit_leaf(tm, cx, tk);
+        return 0;
+      }
+      const int shift = sample_shift(cx.p, (uint64_t)n);
+      const int ns = team_draw_sample(tm, cx.s, cx.flag, P, lo, hi, cx.p.seed, tk.t, shift);
+      tk.ns = (uint16_t)ns;
+      bool skel = false;
+      if (ns >= 2 * cx.p.sigma_os) skel = team_split_rule(tm, cx.s, P, lo, hi, true, ns, dim, x);
+      if (skel) {
+        on_sample = true;
+      } else {
+        // Too few (or identical) samples: one exact level on P itself.
+        on_sample = false;
+        dim = wd;
+        int less, eq;
+        x = team_select(tm, cx.s, P, lo, hi, false, dim, n / 2, less, eq);
+        if (less == 0) x = team_min_above(tm, cx.s, P, lo, hi, false, dim, x);
+      }
+    } else {
+      // Skeleton node: bucket when deep enough, too few samples or identical.
+      if (tk.j >= cx.p.lambda || tk.ns < 2 * cx.p.sigma_os) {
+        tk.j = 0;
+        continue;
+      }
+      if (!team_split_rule(tm, cx.s, P, lo, hi, true, tk.ns, dim, x)) {
+        tk.j = 0;
+        continue;
+      }
+      on_sample = true;
+    }
+    int L, SL, SR;
+    team_partition(tm, cx.s, P, Q, lo, hi, dim, x, L, SL, SR);
+    int b = alloc_two(tm, cx);
+    if (b + 2 > cx.slot_limit) {
+      if (tm.leader()) set_error(cx.st, DERR_SLOT, b);
+      return 0;
+    }
+    if (L <= 0 || L >= n) {
+      if (tm.leader()) set_error(cx.st, DERR_STATE, 100 + L);
+      return 0;
+    }
+    const uint32_t sl = cx.slot_base + (uint32_t)b, sr = sl + 1;
+    if (tm.leader()) {
+      Node nd;
+      nd.split = x;
+      nd.size = (uint32_t)n;
+      nd.a = sl;
+      nd.b = sr;
+      cx.nodes[tk.slot] = nd;
+      cx.ndim[tk.slot] = (uint8_t)dim;
+    }
+    const uint8_t nj = on_sample ? (uint8_t)(tk.j + 1) : (uint8_t)0;
+    const uint8_t nb = (uint8_t)(tk.buf ^ 1);
+    ch[0] = Task{(uint16_t)lo, (uint16_t)(lo + L), (uint16_t)SL, nb, nj, tk.t + 1, sl};
+    ch[1] = Task{(uint16_t)(lo + L), (uint16_t)hi, (uint16_t)SR, nb, nj, tk.t + 1, sr};
+    return 2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Skeleton mode: every loaded point is a sample; nodes become heap entries.
+// ---------------------------------------------------------------------------
+
+template <class T>
+__device__ int process_skel(const T& tm, const SmemCtx& cx, Task tk, Task* ch) {
+  const int lo = tk.lo, hi = tk.hi, n = hi - lo;
+  uint16_t* P = cx.perm[tk.buf];
+  uint16_t* Q = cx.perm[tk.buf ^ 1];
+  int dim, x;
+  bool split = tk.j < cx.lam && n >= cx.min_split &&
+               team_split_rule(tm, cx.s, P, lo, hi, false, n, dim, x);
+  if (!split) {
+    if (tm.leader()) cx.skel[tk.slot] = make_int2(0, sk_meta(SK_BUCKET, 0, 0));
+    return 0;
+  }
+  int L, SL, SR;
+  team_partition(tm, cx.s, P, Q, lo, hi, dim, x, L, SL, SR);
+  if (tm.leader()) cx.skel[tk.slot] = make_int2(x, sk_meta(SK_INTERNAL, dim, 0));
+  const uint8_t nb = (uint8_t)(tk.buf ^ 1);
+  const uint8_t nj = (uint8_t)(tk.j + 1);
+  ch[0] = Task{(uint16_t)lo, (uint16_t)(lo + L), 0, nb, nj, 0, 2 * tk.slot};
+  ch[1] = Task{(uint16_t)(lo + L), (uint16_t)hi, 0, nb, nj, 0, 2 * tk.slot + 1};
+  return 2;
+}
+
+template <bool SKEL, class T>
+__device__ __forceinline__ int process_task(const T& tm, const SmemCtx& cx, const Task& tk, Task* ch) {
+  if (SKEL) return process_skel(tm, cx, tk, ch);
+  return process_build(tm, cx, tk, ch);
+}
+
+template <bool SKEL>
+__device__ void warp_run(const WarpTeam& wt, const SmemCtx& cx, Task tk, Task* stk) {
+  int sp = 0;
+  for (;;) {
+    Task ch[2];
+    int nch = process_task<SKEL>(wt, cx, tk, ch);
+    int err = *(volatile int*)&cx.st->err;
+    if (__shfl_sync(FULL_MASK, err, 0)) return;  // warp-uniform exit
+    if (nch == 2) {
+      const int s0 = ch[0].hi - ch[0].lo, s1 = ch[1].hi - ch[1].lo;
+      const Task big = s0 >= s1 ? ch[0] : ch[1];
+      const Task small = s0 >= s1 ? ch[1] : ch[0];
+      if (sp >= WSTK) {
+        if (lane_id() == 0) set_error(cx.st, DERR_STACK, sp);
+        return;
+      }
+      if (lane_id() == 0) stk[sp] = big;
+      __syncwarp();
+      ++sp;
+      tk = small;
+    } else {
+      if (sp == 0) return;
+      --sp;
+      __syncwarp();
+      tk = stk[sp];
+      __syncwarp();
+    }
+  }
+}
+
+// Drive one CTA over its root task: block phase, then warp phase, repeated
+// until both are empty.  All reads of the control words happen between
+// barriers, so every thread takes the same branches.
+template <bool SKEL>
+__device__ void run_tasks(const SmemCtx& cx, Task root, Task* bstack, Task* wlist, Task* wstack,
+                          unsigned* bhist, int* bred, unsigned* whist) {
+  SmemCtl* ctl = cx.ctl;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    ctl->bsp = 0;
+    ctl->wl_n = 0;
+    if (root.hi - root.lo > WMAX) bstack[ctl->bsp++] = root;
+    else wlist[ctl->wl_n++] = root;
+  }
+  __syncthreads();
+  BlockTeam<SM_NW> bt{bhist, bred};
+  WarpTeam wt{whist + warp_id() * 256, nullptr};
+  for (;;) {
+    for (;;) {
+      if (tid == 0) ctl->err = *(volatile int*)&cx.st->err;
+      __syncthreads();
+      const int bsp = ctl->bsp, wl = ctl->wl_n, err = ctl->err;
+      __syncthreads();
+      if (bsp == 0 || wl + 2 > WLIST || err) break;
+      const Task tk = bstack[bsp - 1];
+      if (tid == 0) ctl->bsp = bsp - 1;
+      Task ch[2];
+      const int nch = process_task<SKEL>(bt, cx, tk, ch);
+      if (tid == 0 && nch == 2) {
+        const int s0 = ch[0].hi - ch[0].lo, s1 = ch[1].hi - ch[1].lo;
+        const Task big = s0 >= s1 ? ch[0] : ch[1];
+        const Task small = s0 >= s1 ? ch[1] : ch[0];
+        const Task order[2] = {big, small};  // larger pushed first: smaller runs next
+        for (int c = 0; c < 2; ++c) {
+          const Task& t = order[c];
+          if (t.hi - t.lo > WMAX) {
+            if (ctl->bsp < BSTK) bstack[ctl->bsp++] = t;
+            else set_error(cx.st, DERR_STACK, 1000 + ctl->bsp);
+          } else {
+            wlist[ctl->wl_n++] = t;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    const int nl = ctl->wl_n;
+    __syncthreads();
+    for (int e = warp_id(); e < nl; e += SM_NW) warp_run<SKEL>(wt, cx, wlist[e], wstack + warp_id() * WSTK);
+    __syncthreads();
+    if (tid == 0) {
+      ctl->wl_n = 0;
+      ctl->err = *(volatile int*)&cx.st->err;
+    }
+    __syncthreads();
+    const int bsp = ctl->bsp, err = ctl->err;
+    __syncthreads();
+    if (bsp == 0 || err) break;
+  }
+}
+
+}  // namespace pkd

@@ -1,0 +1,380 @@
+// C ABI of the Pkd-tree library: tree lifetime, build, export, status,
+// tuning knobs and per-kernel timing.  Every step of the work runs in the
+// library's CUDA kernels; this file sequences them and owns the memory.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "engine.hpp"
+#include "tree_impl.hpp"
+
+namespace pkd {
+
+Knobs& knobs() {
+  static Knobs k;
+  return k;
+}
+
+int cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return PKD_OK;
+  if (e == cudaErrorMemoryAllocation) return PKD_ENOMEM;
+  return PKD_ECUDA;
+}
+
+// ----------------------------------------------------------------------------
+// kernel timers
+// ----------------------------------------------------------------------------
+
+namespace {
+struct TimerStat {
+  uint64_t launches = 0;
+  double ms = 0;
+  uint64_t items = 0;
+};
+struct Pending {
+  std::string name;
+  cudaEvent_t a, b;
+  uint64_t items;
+};
+std::mutex g_tmu;
+bool g_timing = false;
+std::map<std::string, TimerStat> g_stats;
+std::vector<Pending> g_pending;
+
+void resolve_pending() {
+  for (auto& p : g_pending) {
+    float ms = 0;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      auto& s = g_stats[p.name];
+      s.launches++;
+      s.ms += ms;
+      s.items += p.items;
+    }
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  g_pending.clear();
+}
+}  // namespace
+
+bool ktiming_enabled() { return g_timing; }
+
+void ktimer_begin(KTimer& k, const char* name, uint64_t items, cudaStream_t s) {
+  k.on = g_timing;
+  if (!k.on) return;
+  k.name = name;
+  k.items = items;
+  k.s = s;
+  cudaEventCreate(&k.a);
+  cudaEventCreate(&k.b);
+  cudaEventRecord(k.a, s);
+}
+
+void ktimer_end(KTimer& k) {
+  if (!k.on) return;
+  cudaEventRecord(k.b, k.s);
+  std::lock_guard<std::mutex> g(g_tmu);
+  g_pending.push_back(Pending{k.name, k.a, k.b, k.items});
+}
+
+// ----------------------------------------------------------------------------
+// status
+// ----------------------------------------------------------------------------
+
+int check_status(TreeMem& t, cudaStream_t s) {
+  PKD_CUDA(cudaMemcpyAsync(t.st_host, t.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  PKD_CUDA(cudaStreamSynchronize(s));
+  const int e = t.st_host->err;
+  if (e == DERR_NONE) return PKD_OK;
+  fprintf(stderr, "pkd: device status %d (detail %d)\n", e, t.st_host->detail);
+  if (e == DERR_TIMEOUT) return PKD_ETIMEOUT;
+  return PKD_EINTERNAL;
+}
+
+// ----------------------------------------------------------------------------
+// validation
+// ----------------------------------------------------------------------------
+
+int check_params(const pkd_params* p) {
+  if (!p) return PKD_EINVAL;
+  if (p->d < 1 || p->d > PKD_DMAX) return PKD_EINVAL;
+  if (p->phi < 1) return PKD_EINVAL;
+  if (p->lambda < 1 || p->lambda > 10) return PKD_EINVAL;
+  if (p->sigma_log2 < 0 || p->sigma_log2 > 30) return PKD_EINVAL;
+  if (p->sigma_os < 1 || p->sigma_os > (1 << 16)) return PKD_EINVAL;
+  if (p->count_mode != 0 && p->count_mode != 1) return PKD_EINVAL;
+  if (p->alpha_den < 1 || p->alpha_den > (1 << 20)) return PKD_EINVAL;
+  if (p->alpha_num < 0 || 2 * p->alpha_num > p->alpha_den) return PKD_EINVAL;
+  return PKD_OK;
+}
+
+__global__ void k_validate(const int32_t* c, uint64_t cnt, int* bad) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  int b = 0;
+  for (; i < cnt; i += stride) {
+    const int32_t v = c[i];
+    b |= (v < 0) | (v >= PKD_COORD_LIMIT);
+  }
+  if (__any_sync(0xffffffffu, b) && (threadIdx.x & 31) == 0) atomicOr(bad, 1);
+}
+
+int validate_coords(const int32_t* c, uint64_t cnt, cudaStream_t s, bool* ok) {
+  *ok = true;
+  if (cnt == 0) return PKD_OK;
+  int* d = nullptr;
+  PKD_TRY_(dalloc(&d, 1, s));
+  int h = 0;
+  cudaMemsetAsync(d, 0, 4, s);
+  KTimer kt;
+  ktimer_begin(kt, "validate", cnt, s);
+  k_validate<<<152 * 8, 256, 0, s>>>(c, cnt, d);
+  ktimer_end(kt);
+  cudaMemcpyAsync(&h, d, 4, cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  dfree(d, s);
+  if (e != cudaSuccess) return cuda_err(e);
+  *ok = (h == 0);
+  return PKD_OK;
+}
+
+// ----------------------------------------------------------------------------
+// tree memory
+// ----------------------------------------------------------------------------
+
+uint64_t shared_region_for(const Params& p, uint64_t n) {
+  const uint64_t per = (uint64_t)2 << p.lambda;
+  const uint64_t cap = (uint64_t)std::max(base_cap_for(p.d), 64);
+  return per * (8 * (n / cap) + 2048);
+}
+
+void tree_release(TreeMem& t) {
+  cudaFree(t.A.c);
+  cudaFree(t.A.id);
+  cudaFree(t.nodes);
+  cudaFree(t.ndim);
+  cudaFree(t.shared_next);
+  cudaFree(t.st);
+  if (t.st_host) cudaFreeHost(t.st_host);
+  t = TreeMem{};
+}
+
+int download_tree(const TreeMem& t, HostTree& h, bool with_ids) {
+  const uint64_t used = t.shared_cap + 2 * t.top;
+  h.nodes.resize(used);
+  h.ndim.resize(used);
+  PKD_CUDA(cudaDeviceSynchronize());
+  PKD_CUDA(cudaMemcpy(h.nodes.data(), t.nodes, used * sizeof(Node), cudaMemcpyDeviceToHost));
+  PKD_CUDA(cudaMemcpy(h.ndim.data(), t.ndim, used, cudaMemcpyDeviceToHost));
+  if (with_ids) {
+    h.ids.resize(std::max<uint64_t>(t.top, 1));
+    if (t.top) PKD_CUDA(cudaMemcpy(h.ids.data(), t.A.id, t.top * 4, cudaMemcpyDeviceToHost));
+  }
+  return PKD_OK;
+}
+
+int tree_alloc(TreeMem& t, const Params& p, uint64_t cap, uint64_t shared_cap, cudaStream_t s) {
+  t.p = p;
+  cudaGetDevice(&t.device);
+  t.cap = std::max<uint64_t>(cap, 1);
+  t.shared_cap = shared_cap;
+  t.node_cap = shared_cap + 2 * t.cap;
+  if (t.node_cap >= 0xFFFFFFF0ull) return PKD_EINVAL;
+  cudaError_t e;
+  e = cudaMalloc((void**)&t.A.c, (size_t)p.d * t.cap * 4);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&t.A.id, (size_t)t.cap * 4);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&t.nodes, (size_t)t.node_cap * sizeof(Node));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&t.ndim, (size_t)t.node_cap);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&t.shared_next, 16);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&t.st, sizeof(DevStatus));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&t.st_host, sizeof(DevStatus));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    tree_release(t);
+    return e == cudaErrorMemoryAllocation ? PKD_ENOMEM : PKD_ECUDA;
+  }
+  t.A.stride = t.cap;
+  cudaMemsetAsync(t.st, 0, sizeof(DevStatus), s);
+  cudaMemsetAsync(t.shared_next, 0, 16, s);
+  return PKD_OK;
+}
+
+}  // namespace pkd
+
+using namespace pkd;
+
+extern "C" {
+
+const char* pkd_strerror(int code) {
+  switch (code) {
+    case PKD_OK: return "ok";
+    case PKD_EINVAL: return "invalid argument";
+    case PKD_ENOMEM: return "out of device memory";
+    case PKD_ECUDA: return "CUDA runtime error";
+    case PKD_ETIMEOUT: return "device-side wait ran out";
+    case PKD_EINTERNAL: return "device-side consistency check failed";
+    default: return "unknown error";
+  }
+}
+
+int pkd_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const pkd_params* params,
+              void* stream, pkd_tree** out) {
+  if (!out) return PKD_EINVAL;
+  *out = nullptr;
+  int e = check_params(params);
+  if (e) return e;
+  if (n >= (1ull << 31)) return PKD_EINVAL;
+  if (n > 0 && !coords) return PKD_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  Params p{params->d, params->phi, params->lambda, params->sigma_log2, params->sigma_os,
+           params->count_mode, params->alpha_num, params->alpha_den, params->seed};
+  bool ok;
+  e = validate_coords(coords, n * (uint64_t)p.d, s, &ok);
+  if (e) return e;
+  if (!ok) return PKD_EINVAL;
+  pkd_tree* t = new pkd_tree();
+  const uint64_t cap = n + n / 4 + 4096;
+  e = tree_alloc(t->m, p, cap, shared_region_for(p, cap), s);
+  if (e) {
+    delete t;
+    return e;
+  }
+  t->m.root = 0;
+  uint32_t one = 1;
+  cudaMemcpyAsync(t->m.shared_next, &one, 4, cudaMemcpyHostToDevice, s);
+  BuildJob job;
+  job.input_coords = coords;
+  job.input_ids = ids;
+  job.base = 0;
+  job.extent = std::max<uint64_t>(n, 1);
+  job.segs.push_back(Seg{0, (uint32_t)n, 0, 0, IN_INPUT});
+  e = run_build(t->m, job, s);
+  if (e == PKD_OK) e = check_status(t->m, s);
+  if (e) {
+    tree_release(t->m);
+    delete t;
+    return e;
+  }
+  t->m.size = n;
+  t->m.top = n;
+  *out = t;
+  return PKD_OK;
+}
+
+void pkd_free(pkd_tree* t) {
+  if (!t) return;
+  cudaDeviceSynchronize();
+  tree_release(t->m);
+  delete t;
+}
+
+uint64_t pkd_size(const pkd_tree* t) { return t ? t->m.size : 0; }
+
+int pkd_export(const pkd_tree* tc, uint8_t* dims, int32_t* splits, uint64_t* sizes, uint64_t* n_nodes,
+               uint32_t* leaf_ids, uint64_t* leaf_offsets, uint64_t* n_leaves) {
+  if (!tc) return PKD_EINVAL;
+  HostTree h;
+  int e = download_tree(tc->m, h);
+  if (e) return e;
+  uint64_t nn = 0, nl = 0, nid = 0;
+  std::vector<uint32_t> stack;
+  stack.push_back(tc->m.root);
+  while (!stack.empty()) {
+    const uint32_t v = stack.back();
+    stack.pop_back();
+    if (v >= h.nodes.size() || nn > h.nodes.size()) return PKD_EINTERNAL;
+    const Node& nd = h.nodes[v];
+    const uint8_t dm = h.ndim[v];
+    if (dm == PKD_LEAF) {
+      if ((uint64_t)nd.a + nd.size > tc->m.top || nid + nd.size > tc->m.size) return PKD_EINTERNAL;
+      if (dims) dims[nn] = PKD_LEAF;
+      if (splits) splits[nn] = 0;
+      if (sizes) sizes[nn] = nd.size;
+      if (leaf_offsets) leaf_offsets[nl] = nid;
+      if (leaf_ids) {
+        for (uint32_t k = 0; k < nd.size; ++k) leaf_ids[nid + k] = h.ids[(uint64_t)nd.a + k];
+        std::sort(leaf_ids + nid, leaf_ids + nid + nd.size);
+      }
+      nid += nd.size;
+      ++nl;
+    } else {
+      if (dims) dims[nn] = dm;
+      if (splits) splits[nn] = nd.split;
+      if (sizes) sizes[nn] = nd.size;
+      stack.push_back(nd.b);
+      stack.push_back(nd.a);
+    }
+    ++nn;
+  }
+  if (leaf_offsets) leaf_offsets[nl] = nid;
+  if (n_nodes) *n_nodes = nn;
+  if (n_leaves) *n_leaves = nl;
+  return PKD_OK;
+}
+
+int pkd_height(const pkd_tree* tc, int* height) {
+  if (!tc || !height) return PKD_EINVAL;
+  HostTree h;
+  int e = download_tree(tc->m, h, false);
+  if (e) return e;
+  int best = 0;
+  std::vector<std::pair<uint32_t, int>> stack{{tc->m.root, 0}};
+  while (!stack.empty()) {
+    auto [v, dep] = stack.back();
+    stack.pop_back();
+    if (v >= h.nodes.size() || dep > 100000) return PKD_EINTERNAL;
+    if (h.ndim[v] == PKD_LEAF) {
+      best = std::max(best, dep);
+    } else {
+      stack.push_back({h.nodes[v].a, dep + 1});
+      stack.push_back({h.nodes[v].b, dep + 1});
+    }
+  }
+  *height = best;
+  return PKD_OK;
+}
+
+int pkd_set_option(const char* name, int64_t value) {
+  if (!name) return PKD_EINVAL;
+  std::string n(name);
+  if (n == "base_cap") {
+    if (value != 0 && (value < 64 || value > 16384)) return PKD_EINVAL;
+    knobs().base_cap = (int)value;
+  } else if (n == "skel_cap") {
+    if (value != 0 && (value < 64 || value > 16384)) return PKD_EINVAL;
+    knobs().skel_cap = (int)value;
+  } else if (n == "tile") {
+    if (value < 256 || value > 4096 || (value & (value - 1))) return PKD_EINVAL;
+    knobs().tile = (int)value;
+  } else {
+    return PKD_EINVAL;
+  }
+  return PKD_OK;
+}
+
+int pkd_kernel_timing(int enable) {
+  std::lock_guard<std::mutex> g(g_tmu);
+  resolve_pending();
+  g_stats.clear();
+  g_timing = enable != 0;
+  return PKD_OK;
+}
+
+int pkd_kernel_stats(const char* name, uint64_t* launches, double* total_ms, uint64_t* items) {
+  if (!name) return PKD_EINVAL;
+  std::lock_guard<std::mutex> g(g_tmu);
+  resolve_pending();
+  auto it = g_stats.find(name);
+  TimerStat s = it == g_stats.end() ? TimerStat{} : it->second;
+  if (launches) *launches = s.launches;
+  if (total_ms) *total_ms = s.ms;
+  if (items) *items = s.items;
+  return PKD_OK;
+}
+
+}  // extern "C"

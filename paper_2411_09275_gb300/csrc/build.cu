@@ -23,35 +23,15 @@
 #include <cstdio>
 #include <cstring>
 
-#include "engine.hpp"
-#include "smem_build.cuh"
+#include "sieve.cuh"
 
 namespace pkd {
 
-constexpr uint32_t SEG_SKIP = 0xFFFFFFFFu;
-constexpr int SCAN_ITEMS = 8;
-constexpr int SCAN_THREADS = 256;
-constexpr int SCAN_TILE = SCAN_ITEMS * SCAN_THREADS;
-constexpr int JOB_TILE = 2048;
-constexpr int JOB_THREADS = 256;
-constexpr int SIEVE_THREADS = 512;
 
 // ---------------------------------------------------------------------------
 // Point sources
 // ---------------------------------------------------------------------------
 
-struct Src {
-  Pts soa;
-  const int32_t* aos;
-  const uint32_t* aos_ids;
-  int is_aos;
-  __device__ __forceinline__ int32_t x(int d, int j, uint64_t g) const {
-    return is_aos ? aos[g * (uint64_t)d + j] : soa.c[(uint64_t)j * soa.stride + g];
-  }
-  __device__ __forceinline__ uint32_t id(uint64_t g) const {
-    return is_aos ? (aos_ids ? aos_ids[g] : (uint32_t)g) : soa.id[g];
-  }
-};
 
 // ---------------------------------------------------------------------------
 // Shared-memory kernels (build mode and skeleton mode)
@@ -177,144 +157,120 @@ __global__ void __launch_bounds__(SM_THREADS) k_smem_skel(SmemArgs a) {
   run_tasks<true>(cx, root, q.bstack, q.wlist, q.wstack, q.bhist, q.bred, q.whist);
 }
 
+// One warp per small subproblem (a leaf rebuilt with a few new points, or a
+// small bucket): every warp of the CTA owns its own shared-memory slice.
+constexpr int WK_WARPS = 8;
+
+struct WarpLayout {
+  size_t X, ID, perm0, perm1, flag, hist, stack, ctl, per_warp;
+};
+
+__host__ __device__ inline WarpLayout warp_layout(int wcap, int d) {
+  WarpLayout L;
+  size_t o = 0;
+  L.X = o;
+  o = align_up(o + (size_t)4 * d * wcap, 16);
+  L.ID = o;
+  o = align_up(o + (size_t)4 * wcap, 16);
+  L.perm0 = o;
+  o = align_up(o + (size_t)2 * wcap, 16);
+  L.perm1 = o;
+  o = align_up(o + (size_t)2 * wcap, 16);
+  L.flag = o;
+  o = align_up(o + (size_t)wcap, 16);
+  L.hist = o;
+  o = align_up(o + 256 * 4, 16);
+  L.stack = o;
+  o = align_up(o + WSTK * sizeof(Task), 16);
+  L.ctl = o;
+  o = align_up(o + sizeof(SmemCtl), 16);
+  L.per_warp = o;
+  return L;
+}
+
+int warp_cap_for(int d) { return d <= 4 ? 512 : 256; }
+
+__global__ void __launch_bounds__(WK_WARPS * 32) k_smem_warp(SmemArgs a) {
+  const uint32_t sid = blockIdx.x * WK_WARPS + warp_id();
+  if (sid >= *a.nsegs) return;  // warp-uniform
+  extern __shared__ __align__(16) uint8_t sm[];
+  const int d = a.p.d, cap = a.cap, lane = lane_id();
+  const WarpLayout Lo = warp_layout(cap, d);
+  uint8_t* base = sm + (size_t)warp_id() * Lo.per_warp;
+  int32_t* X = (int32_t*)(base + Lo.X);
+  uint32_t* ID = (uint32_t*)(base + Lo.ID);
+  uint16_t* perm0 = (uint16_t*)(base + Lo.perm0);
+  uint16_t* perm1 = (uint16_t*)(base + Lo.perm1);
+  uint8_t* flag = base + Lo.flag;
+  unsigned* hist = (unsigned*)(base + Lo.hist);
+  Task* stack = (Task*)(base + Lo.stack);
+  SmemCtl* ctl = (SmemCtl*)(base + Lo.ctl);
+  const Seg seg = a.segs[sid];
+  if (seg.len > (uint32_t)cap) {
+    if (lane == 0) set_error(a.st, DERR_CAPACITY, 250000);
+    return;
+  }
+  const int n = (int)seg.len;
+  for (int i = lane; i < n; i += 32) {
+    const uint64_t g = seg.start + (uint64_t)i;
+    if (seg.where == IN_INPUT) {
+      for (int j = 0; j < d; ++j) X[j * cap + i] = a.in_coords[g * (uint64_t)d + j];
+      ID[i] = a.in_ids ? a.in_ids[g] : (uint32_t)g;
+    } else {
+      const Pts& S = seg.where == IN_A ? a.A : a.B;
+      for (int j = 0; j < d; ++j) X[j * cap + i] = S.c[(uint64_t)j * S.stride + g];
+      ID[i] = S.id[g];
+    }
+    perm0[i] = (uint16_t)i;
+  }
+  if (lane == 0) ctl->next_slot = 0;
+  __syncwarp();
+  if (n == 0) {
+    if (lane == 0) {
+      a.nodes[seg.root] = Node{0, 0, (uint32_t)seg.start, 0};
+      a.ndim[seg.root] = PKD_LEAF;
+    }
+    return;
+  }
+  SmemCtx cx;
+  cx.p = a.p;
+  cx.s = SmemPts{X, ID, flag, cap, d};
+  cx.flag = flag;
+  cx.perm[0] = perm0;
+  cx.perm[1] = perm1;
+  cx.ctl = ctl;
+  cx.out = a.A;
+  cx.start = seg.start;
+  cx.slot_base = (uint32_t)(a.shared_cap + 2 * seg.start);
+  cx.slot_limit = 2 * n;
+  cx.nodes = a.nodes;
+  cx.ndim = a.ndim;
+  cx.skel = nullptr;
+  cx.lam = 0;
+  cx.min_split = 0;
+  cx.st = a.st;
+  WarpTeam wt{hist, nullptr};
+  warp_run<false>(wt, cx, Task{0, (uint16_t)n, 0, 0, 0, seg.depth, seg.root}, stack);
+}
+
 // ---------------------------------------------------------------------------
 // Scans
 // ---------------------------------------------------------------------------
 
-// Exclusive block scan of one value per thread; returns the prefix, *total.
-template <class V>
-__device__ V block_excl_scan(V v, V* sh, V* total) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  V incl = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    V t = __shfl_up_sync(FULL_MASK, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) sh[w] = incl;
-  __syncthreads();
-  if (w == 0) {
-    V s = lane < nw ? sh[lane] : V(0);
-    V si = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      V t = __shfl_up_sync(FULL_MASK, si, o);
-      if (lane >= o) si += t;
-    }
-    if (lane < nw) sh[lane] = si - s;
-    if (lane == 31) sh[32] = si;
-  }
-  __syncthreads();
-  V r = sh[w] + incl - v;
-  *total = sh[32];
-  __syncthreads();
-  return r;
-}
-
-// Per-block sums of in[0, n).
-__global__ void k_scan_reduce(const uint32_t* in, uint64_t n, uint32_t* partial) {
-  __shared__ uint32_t sh[33];
-  uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
-  uint32_t s = 0;
-  for (int k = 0; k < SCAN_ITEMS; ++k) {
-    uint64_t i = base + (uint64_t)threadIdx.x * SCAN_ITEMS + k;
-    if (i < n) s += in[i];
-  }
-  uint32_t tot;
-  block_excl_scan<uint32_t>(s, sh, &tot);
-  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
-}
-
-// Single-block exclusive scan in place over x[0, n).
-__global__ void k_scan_single(uint32_t* x, uint64_t n) {
-  __shared__ uint32_t sh[33];
-  uint32_t carry = 0;
-  for (uint64_t base = 0; base < n; base += blockDim.x) {
-    uint64_t i = base + threadIdx.x;
-    uint32_t v = i < n ? x[i] : 0;
-    uint32_t tot;
-    uint32_t e = block_excl_scan<uint32_t>(v, sh, &tot);
-    if (i < n) x[i] = carry + e;
-    carry += tot;
-  }
-}
-
-__global__ void k_scan_apply(const uint32_t* in, uint32_t* out, uint64_t n, const uint32_t* partial) {
-  __shared__ uint32_t sh[33];
-  uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
-  uint32_t v[SCAN_ITEMS];
-  uint32_t s = 0;
-#pragma unroll
-  for (int k = 0; k < SCAN_ITEMS; ++k) {
-    v[k] = (base + k < n) ? in[base + k] : 0;
-    s += v[k];
-  }
-  uint32_t tot;
-  uint32_t e = block_excl_scan<uint32_t>(s, sh, &tot) + partial[blockIdx.x];
-#pragma unroll
-  for (int k = 0; k < SCAN_ITEMS; ++k) {
-    if (base + k < n) out[base + k] = e;
-    e += v[k];
-  }
-}
-
-static void device_excl_scan(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* partial,
-                             cudaStream_t s) {
-  if (n == 0) return;
-  const uint64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
-  k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, partial);
-  k_scan_single<<<1, 1024, 0, s>>>(partial, nb);
-  k_scan_apply<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, partial);
-}
 
 // ---------------------------------------------------------------------------
 // Round bookkeeping
 // ---------------------------------------------------------------------------
 
-struct RoundArgs {
-  Params p;
-  int lam, NB, HN, TILE;
-  Src src;
-  Pts dst;
-  Pts A;
-  int dst_where;
-  const Seg* big;
-  const uint32_t* nbig;
-  uint32_t* tile0;   // [nbig] first tile of each big segment
-  uint64_t* excl;    // [nbig] points of the big segments before this one
-  int2* skel;        // [nbig][HN]
-  uint32_t* slots;   // [nbig][HN]
-  uint32_t* nbk;     // [nbig] buckets
-  uint8_t* exact;    // [nbig] 1: exact level on the points; 2: already handled
-  uint32_t* hist;    // [tiles * NB]
-  uint32_t* hscan;
-  uint32_t* scnt;    // [nbig] samples
-  uint32_t* sizes;   // [nbig][HN] skeleton subtree sizes
-  Pts samp;          // sample buffer 0
-  Seg* children;     // [nbig * NB]
-  Node* nodes;
-  uint8_t* ndim;
-  uint32_t* shared_next;
-  uint64_t shared_cap;
-  DevStatus* st;
-};
 
-__device__ __forceinline__ uint32_t seg_of_tile(const uint32_t* tile0, uint32_t nseg, uint32_t tile) {
-  uint32_t lo = 0, hi = nseg;  // largest s with tile0[s] <= tile
-  while (hi - lo > 1) {
-    uint32_t mid = (lo + hi) >> 1;
-    if (tile0[mid] <= tile) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
 
 // Split a segment list into big segments (ctr[0], their tiles ctr[2], their
 // points *pts) and segments finished in shared memory (appended to the
 // persistent base list, counter *nbase).
 __global__ void k_classify(const Seg* segs, uint32_t nseg, uint32_t cap, Seg* big, uint32_t* ctr,
                            unsigned long long* pts, Seg* base, uint32_t* nbase, uint32_t base_cap,
-                           uint32_t tile, uint32_t where, DevStatus* st) {
+                           Seg* wbase, uint32_t* nwbase, uint32_t wcap, uint32_t tile, uint32_t where,
+                           DevStatus* st) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nseg) return;
   Seg s = segs[i];
@@ -325,41 +281,17 @@ __global__ void k_classify(const Seg* segs, uint32_t nseg, uint32_t cap, Seg* bi
     big[k] = s;
     atomicAdd(&ctr[2], (s.len + tile - 1) / tile);
     atomicAdd(pts, (unsigned long long)s.len);
-  } else {
+  } else if (s.len > wcap) {
     uint32_t k = atomicAdd(nbase, 1u);
     if (k < base_cap) base[k] = s;
     else set_error(st, DERR_CAPACITY, 300);
+  } else {
+    uint32_t k = atomicAdd(nwbase, 1u);
+    if (k < base_cap) wbase[k] = s;
+    else set_error(st, DERR_CAPACITY, 301);
   }
 }
 
-// tile0 / excl over the big segments (one block).
-__global__ void k_big_prefix(const Seg* big, const uint32_t* nbig, uint32_t tile, uint32_t* tile0,
-                             uint64_t* excl) {
-  __shared__ uint32_t sh32[33];
-  __shared__ unsigned long long sh64[33];
-  const uint32_t n = *nbig;
-  uint32_t ct = 0;
-  unsigned long long cl = 0;
-  for (uint32_t base = 0; base < n; base += blockDim.x) {
-    uint32_t i = base + threadIdx.x;
-    uint32_t t = 0;
-    unsigned long long l = 0;
-    if (i < n) {
-      t = (big[i].len + tile - 1) / tile;
-      l = big[i].len;
-    }
-    uint32_t tt;
-    unsigned long long tl;
-    uint32_t et = block_excl_scan<uint32_t>(t, sh32, &tt);
-    unsigned long long el = block_excl_scan<unsigned long long>(l, sh64, &tl);
-    if (i < n) {
-      tile0[i] = ct + et;
-      excl[i] = cl + el;
-    }
-    ct += tt;
-    cl += tl;
-  }
-}
 
 // Sample: points whose hash at the segment's depth passes the rate test.
 __global__ void k_sample(RoundArgs r) {
@@ -788,70 +720,8 @@ __global__ void k_finalize(RoundArgs r) {
 // Sieve: count and scatter
 // ---------------------------------------------------------------------------
 
-struct SieveTile {
-  uint32_t s;
-  Seg seg;
-  uint64_t first;
-  int cnt;
-  uint32_t t0, nt;
-};
 
-__device__ __forceinline__ bool sieve_tile(const RoundArgs& r, SieveTile& t) {
-  const uint32_t nb = *r.nbig;
-  t.s = seg_of_tile(r.tile0, nb, blockIdx.x);
-  t.seg = r.big[t.s];
-  t.t0 = r.tile0[t.s];
-  t.nt = (t.seg.len + r.TILE - 1) / r.TILE;
-  t.first = (uint64_t)(blockIdx.x - t.t0) * r.TILE;
-  if (t.first >= t.seg.len) return false;
-  t.cnt = (int)min((uint64_t)r.TILE, (uint64_t)t.seg.len - t.first);
-  return true;
-}
 
-// Walk the heap skeleton held in shared memory (split, meta) to a bucket.
-template <int D>
-__device__ __forceinline__ int walk_bucket(const int2* sk, const int32_t* x, int lam) {
-  int h = 1;
-  for (int l = 0; l < lam; ++l) {
-    const int2 e = sk[h];
-    if (sk_state(e.y) != SK_INTERNAL) break;
-    h = 2 * h + (x[sk_dim(e.y)] >= e.x);
-  }
-  return sk_bucket(sk[h].y);
-}
-
-template <int D>
-__global__ void __launch_bounds__(SIEVE_THREADS) k_count(RoundArgs r) {
-  SieveTile t;
-  if (!sieve_tile(r, t)) return;
-  extern __shared__ __align__(16) uint8_t sm[];
-  int2* sk = (int2*)sm;
-  unsigned* lh = (unsigned*)(sk + r.HN);
-  const int2* gsk = r.skel + (uint64_t)t.s * r.HN;
-  for (int v = threadIdx.x; v < r.HN; v += blockDim.x) sk[v] = gsk[v];
-  for (int b = threadIdx.x; b < r.NB; b += blockDim.x) lh[b] = 0;
-  __syncthreads();
-  const bool heavy = sk_state(sk[1].y) == SK_HEAVY;
-  if (!heavy) {
-    for (int base = 0; base < t.cnt; base += blockDim.x) {
-      const int i = base + threadIdx.x;
-      int b = -1;
-      if (i < t.cnt) {
-        int32_t x[D];
-        const uint64_t g = t.seg.start + t.first + i;
-#pragma unroll
-        for (int j = 0; j < D; ++j) x[j] = r.src.x(D, j, g);
-        b = walk_bucket<D>(sk, x, r.lam);
-      }
-      const unsigned m = __match_any_sync(FULL_MASK, b);
-      if (b >= 0 && lane_id() == __ffs(m) - 1) atomicAdd(&lh[b], (unsigned)__popc(m));
-    }
-  }
-  __syncthreads();
-  const uint64_t hb = (uint64_t)t.t0 * r.NB;
-  const uint32_t tl = blockIdx.x - t.t0;
-  for (int b = threadIdx.x; b < r.NB; b += blockDim.x) r.hist[hb + (uint64_t)b * t.nt + tl] = lh[b];
-}
 
 // Children segments, interior nodes and heavy leaves of every big segment.
 __global__ void k_emit(RoundArgs r, uint32_t* heavy_ctr) {
@@ -898,84 +768,6 @@ __global__ void k_emit(RoundArgs r, uint32_t* heavy_ctr) {
   if (size[1] != seg.len) set_error(r.st, DERR_STATE, 700);
 }
 
-template <int D>
-__global__ void __launch_bounds__(SIEVE_THREADS) k_scatter(RoundArgs r) {
-  SieveTile t;
-  if (!sieve_tile(r, t)) return;
-  extern __shared__ __align__(16) uint8_t sm[];
-  int2* sk = (int2*)sm;
-  unsigned* cur = (unsigned*)(sk + r.HN);      // [NB] per-bucket counters, then starts
-  unsigned* lstart = cur + r.NB;               // [NB]
-  uint32_t* gbase = lstart + r.NB;             // [NB] (relative to the segment start)
-  int32_t* stx = (int32_t*)(gbase + r.NB);     // [D][TILE]
-  uint32_t* sid = (uint32_t*)(stx + (size_t)D * r.TILE);
-  uint16_t* sb = (uint16_t*)(sid + r.TILE);
-  const int2* gsk = r.skel + (uint64_t)t.s * r.HN;
-  for (int v = threadIdx.x; v < r.HN; v += blockDim.x) sk[v] = gsk[v];
-  for (int b = threadIdx.x; b < r.NB; b += blockDim.x) cur[b] = 0;
-  __syncthreads();
-  if (sk_state(sk[1].y) == SK_HEAVY) return;
-  constexpr int PER = 8;  // TILE <= PER * SIEVE_THREADS
-  int32_t x[PER][D];
-  uint32_t id[PER];
-  int bk[PER], rk[PER];
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int i = k * SIEVE_THREADS + threadIdx.x;
-    bk[k] = -1;
-    rk[k] = 0;
-    if (i < t.cnt) {
-      const uint64_t g = t.seg.start + t.first + i;
-#pragma unroll
-      for (int j = 0; j < D; ++j) x[k][j] = r.src.x(D, j, g);
-      id[k] = r.src.id(g);
-      bk[k] = walk_bucket<D>(sk, x[k], r.lam);
-    }
-    const unsigned m = __match_any_sync(FULL_MASK, bk[k]);
-    const int leader = __ffs(m) - 1;
-    unsigned base = 0;
-    if (bk[k] >= 0 && lane_id() == leader) base = atomicAdd(&cur[bk[k]], (unsigned)__popc(m));
-    base = __shfl_sync(FULL_MASK, base, leader);
-    rk[k] = (int)base + __popc(m & lanemask_lt());
-  }
-  __syncthreads();
-  // bucket starts inside the tile, and global bases from the scan
-  if (threadIdx.x < 32) {
-    unsigned carry = 0;
-    for (int b0 = 0; b0 < r.NB; b0 += 32) {
-      const int b = b0 + lane_id();
-      const unsigned c = b < r.NB ? cur[b] : 0;
-      const unsigned incl = (unsigned)warp_incl_scan((int)c);
-      if (b < r.NB) lstart[b] = carry + incl - c;
-      carry += __shfl_sync(FULL_MASK, incl, 31);
-    }
-  }
-  const uint64_t hb = (uint64_t)t.t0 * r.NB;
-  const uint32_t tl = blockIdx.x - t.t0;
-  const uint32_t segbase = r.hscan[hb];
-  for (int b = threadIdx.x; b < r.NB; b += blockDim.x)
-    gbase[b] = r.hscan[hb + (uint64_t)b * t.nt + tl] - segbase;
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    if (bk[k] >= 0) {
-      const int pos = (int)lstart[bk[k]] + rk[k];
-#pragma unroll
-      for (int j = 0; j < D; ++j) stx[j * r.TILE + pos] = x[k][j];
-      sid[pos] = id[k];
-      sb[pos] = (uint16_t)bk[k];
-    }
-  }
-  __syncthreads();
-  // every bucket's run leaves the tile as one contiguous, coalesced range
-  for (int pos = threadIdx.x; pos < t.cnt; pos += blockDim.x) {
-    const int b = sb[pos];
-    const uint64_t g = t.seg.start + gbase[b] + (uint64_t)(pos - (int)lstart[b]);
-#pragma unroll
-    for (int j = 0; j < D; ++j) r.dst.c[(uint64_t)j * r.dst.stride + g] = stx[j * r.TILE + pos];
-    r.dst.id[g] = sid[pos];
-  }
-}
 
 // Heavy segments whose points are not yet in the arena.
 __global__ void k_copy_heavy(RoundArgs r) {
@@ -1026,73 +818,12 @@ int skel_cap_for(int d) {
   return std::min(cap_for_bytes(d, budget), 16384);
 }
 
-static size_t scatter_smem(int HN, int NB, int D, int tile) {
-  return (size_t)HN * 8 + (size_t)NB * 12 + (size_t)D * tile * 4 + (size_t)tile * 4 + (size_t)tile * 2;
-}
 
-template <int D>
-static void launch_count(const RoundArgs& r, uint32_t tiles, cudaStream_t s) {
-  const size_t sm = (size_t)r.HN * 8 + (size_t)r.NB * 4;
-  KTimer kt;
-  ktimer_begin(kt, "count", 0, s);
-  k_count<D><<<tiles, SIEVE_THREADS, sm, s>>>(r);
-  ktimer_end(kt);
-}
 
-template <int D>
-static void launch_scatter(const RoundArgs& r, uint32_t tiles, uint64_t pts, cudaStream_t s) {
-  const size_t sm = scatter_smem(r.HN, r.NB, D, r.TILE);
-  static bool set = false;
-  if (!set) {
-    cudaFuncSetAttribute(k_scatter<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    set = true;
-  }
-  KTimer kt;
-  ktimer_begin(kt, "scatter", pts, s);
-  k_scatter<D><<<tiles, SIEVE_THREADS, sm, s>>>(r);
-  ktimer_end(kt);
-}
 
-#define PKD_DISPATCH_D(d, F, ...) \
-  switch (d) {                    \
-    case 1: F<1>(__VA_ARGS__); break; \
-    case 2: F<2>(__VA_ARGS__); break; \
-    case 3: F<3>(__VA_ARGS__); break; \
-    case 4: F<4>(__VA_ARGS__); break; \
-    case 5: F<5>(__VA_ARGS__); break; \
-    case 6: F<6>(__VA_ARGS__); break; \
-    case 7: F<7>(__VA_ARGS__); break; \
-    default: F<8>(__VA_ARGS__); break; \
-  }
 
-// Shift a structure-of-arrays view so that absolute arena positions index
-// into a scratch allocation that only covers [base, base + extent).
-static Pts shifted(const Pts& p, uint64_t base) {
-  Pts q = p;
-  q.c = p.c - base;
-  q.id = p.id - base;
-  return q;
-}
 
-struct Scratch {
-  cudaStream_t s;
-  std::vector<void*> ptrs;
-  ~Scratch() {
-    for (void* p : ptrs) cudaFreeAsync(p, s);
-  }
-  template <class T>
-  int get(T** p, size_t n) {
-    int e = dalloc(p, n, s);
-    if (e == PKD_OK) ptrs.push_back(*p);
-    return e;
-  }
-};
 
-#define PKD_TRY(x)               \
-  do {                           \
-    int _r = (x);                \
-    if (_r != PKD_OK) return _r; \
-  } while (0)
 
 // Run the job levels for skeleton nodes whose samples exceed one CTA, then
 // finish every small node in shared memory.
@@ -1195,15 +926,21 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
   } hf{hctr};
   PKD_CUDA(cudaMemsetAsync(dctr, 0, 16 * 4, s));
 
-  const uint64_t nroots = job.segs.size();
+  const uint64_t nroots = job.dsegs ? job.dsegs_n : job.segs.size();
   Seg* cur;
-  PKD_TRY(sc.get(&cur, std::max<uint64_t>(nroots, 1)));
-  PKD_CUDA(cudaMemcpyAsync(cur, job.segs.data(), nroots * sizeof(Seg), cudaMemcpyHostToDevice, s));
+  if (job.dsegs) {
+    cur = const_cast<Seg*>(job.dsegs);
+  } else {
+    PKD_TRY(sc.get(&cur, std::max<uint64_t>(nroots, 1)));
+    PKD_CUDA(cudaMemcpyAsync(cur, job.segs.data(), nroots * sizeof(Seg), cudaMemcpyHostToDevice, s));
+  }
   uint64_t ncur = nroots;
+  const uint32_t wcap = (uint32_t)warp_cap_for(d);
   // every base segment is a root or a non-empty bucket: at most extent + roots
   const uint64_t base_cap_segs = extent + nroots + 16;
-  Seg* base_list;
+  Seg *base_list, *wbase_list;
   PKD_TRY(sc.get(&base_list, base_cap_segs));
+  PKD_TRY(sc.get(&wbase_list, base_cap_segs));
 
   Src src{};
   int src_where;
@@ -1244,7 +981,7 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     PKD_CUDA(cudaMemsetAsync(dpts, 0, 8, s));
     k_classify<<<(unsigned)((ncur + 255) / 256), 256, 0, s>>>(
         cur, (uint32_t)ncur, cap, big, dctr, dpts, base_list, d_nbase, (uint32_t)base_cap_segs,
-        (uint32_t)TILE, (uint32_t)src_where, t.st);
+        wbase_list, d_nbase + 1, wcap, (uint32_t)TILE, (uint32_t)src_where, t.st);
     PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 16 * 4, cudaMemcpyDeviceToHost, s));
     PKD_CUDA(cudaStreamSynchronize(s));
     const uint32_t nbig = hctr[0], tiles = hctr[2];
@@ -1354,9 +1091,22 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
   }
 
   // 5. every small subproblem, one CTA each, in shared memory
-  PKD_CUDA(cudaMemcpyAsync(hctr + 12, d_nbase, 4, cudaMemcpyDeviceToHost, s));
+  PKD_CUDA(cudaMemcpyAsync(hctr + 12, d_nbase, 8, cudaMemcpyDeviceToHost, s));
   PKD_CUDA(cudaStreamSynchronize(s));
   const uint32_t nbase = std::min<uint32_t>(hctr[12], (uint32_t)base_cap_segs);
+  const uint32_t nwbase = std::min<uint32_t>(hctr[13], (uint32_t)base_cap_segs);
+  if (nwbase > 0) {
+    SmemArgs wa = sa;
+    wa.segs = wbase_list;
+    wa.nsegs = d_nbase + 1;
+    wa.cap = (int)wcap;
+    const size_t smb = warp_layout((int)wcap, d).per_warp * WK_WARPS;
+    PKD_CUDA(cudaFuncSetAttribute(k_smem_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+    KTimer kt;
+    ktimer_begin(kt, "smem_warp", 0, s);
+    k_smem_warp<<<(nwbase + WK_WARPS - 1) / WK_WARPS, WK_WARPS * 32, smb, s>>>(wa);
+    ktimer_end(kt);
+  }
   if (nbase > 0) {
     sa.segs = base_list;
     sa.nsegs = d_nbase;

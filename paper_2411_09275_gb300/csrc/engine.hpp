@@ -40,6 +40,8 @@ struct TreeMem {
   uint32_t* shared_next = nullptr;  // device: next free slot of the shared region
   uint32_t root = 0;
   uint64_t size = 0;
+  uint8_t* dead = nullptr;          // delete scratch: per arena position (kept zero)
+  uint32_t* aux = nullptr;          // delete scratch: per node slot (kept zero)
   DevStatus* st = nullptr;          // device status word
   DevStatus* st_host = nullptr;     // pinned mirror
 };
@@ -95,7 +97,9 @@ struct BuildJob {
   const uint32_t* input_ids = nullptr;
   uint64_t base = 0;       // lowest arena position of any segment
   uint64_t extent = 0;     // highest position + 1 - base
-  std::vector<Seg> segs;   // host list of root segments
+  std::vector<Seg> segs;   // host list of root segments, or:
+  const Seg* dsegs = nullptr;  // device list of root segments (dsegs_n of them)
+  uint64_t dsegs_n = 0;
 };
 int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s);
 

@@ -1,0 +1,400 @@
+// Sieve machinery shared by the build and the batch updates: point sources,
+// device-wide scans, per-round arguments, and the count / scatter kernels
+// that move every point of a subproblem to its bucket of a heap skeleton.
+#pragma once
+
+#include <algorithm>
+#include <vector>
+
+#include "engine.hpp"
+#include "smem_build.cuh"
+
+namespace pkd {
+
+constexpr uint32_t SEG_SKIP = 0xFFFFFFFFu;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_TILE = SCAN_ITEMS * SCAN_THREADS;
+constexpr int JOB_TILE = 2048;
+constexpr int JOB_THREADS = 256;
+constexpr int SIEVE_THREADS = 512;
+
+struct Src {
+  Pts soa;
+  const int32_t* aos;
+  const uint32_t* aos_ids;
+  int is_aos;
+  __device__ __forceinline__ int32_t x(int d, int j, uint64_t g) const {
+    return is_aos ? aos[g * (uint64_t)d + j] : soa.c[(uint64_t)j * soa.stride + g];
+  }
+  __device__ __forceinline__ uint32_t id(uint64_t g) const {
+    return is_aos ? (aos_ids ? aos_ids[g] : (uint32_t)g) : soa.id[g];
+  }
+};
+
+// Exclusive block scan of one value per thread; returns the prefix, *total.
+template <class V>
+__device__ V block_excl_scan(V v, V* sh, V* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  V incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    V t = __shfl_up_sync(FULL_MASK, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) sh[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    V s = lane < nw ? sh[lane] : V(0);
+    V si = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      V t = __shfl_up_sync(FULL_MASK, si, o);
+      if (lane >= o) si += t;
+    }
+    if (lane < nw) sh[lane] = si - s;
+    if (lane == 31) sh[32] = si;
+  }
+  __syncthreads();
+  V r = sh[w] + incl - v;
+  *total = sh[32];
+  __syncthreads();
+  return r;
+}
+
+// Per-block sums of in[0, n).
+static __global__ void k_scan_reduce(const uint32_t* in, uint64_t n, uint32_t* partial) {
+  __shared__ uint32_t sh[33];
+  uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+  uint32_t s = 0;
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    uint64_t i = base + (uint64_t)threadIdx.x * SCAN_ITEMS + k;
+    if (i < n) s += in[i];
+  }
+  uint32_t tot;
+  block_excl_scan<uint32_t>(s, sh, &tot);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+// Single-block exclusive scan in place over x[0, n).
+static __global__ void k_scan_single(uint32_t* x, uint64_t n) {
+  __shared__ uint32_t sh[33];
+  uint32_t carry = 0;
+  for (uint64_t base = 0; base < n; base += blockDim.x) {
+    uint64_t i = base + threadIdx.x;
+    uint32_t v = i < n ? x[i] : 0;
+    uint32_t tot;
+    uint32_t e = block_excl_scan<uint32_t>(v, sh, &tot);
+    if (i < n) x[i] = carry + e;
+    carry += tot;
+  }
+}
+
+static __global__ void k_scan_apply(const uint32_t* in, uint32_t* out, uint64_t n, const uint32_t* partial) {
+  __shared__ uint32_t sh[33];
+  uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
+  uint32_t v[SCAN_ITEMS];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0;
+    s += v[k];
+  }
+  uint32_t tot;
+  uint32_t e = block_excl_scan<uint32_t>(s, sh, &tot) + partial[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    if (base + k < n) out[base + k] = e;
+    e += v[k];
+  }
+}
+
+static void device_excl_scan(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* partial,
+                             cudaStream_t s) {
+  if (n == 0) return;
+  const uint64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+  k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, partial);
+  k_scan_single<<<1, 1024, 0, s>>>(partial, nb);
+  k_scan_apply<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, partial);
+}
+
+struct RoundArgs {
+  Params p;
+  int lam, NB, HN, TILE;
+  Src src;
+  Pts dst;
+  Pts A;
+  int dst_where;
+  const Seg* big;
+  const uint32_t* nbig;
+  uint32_t* tile0;   // [nbig] first tile of each big segment
+  uint64_t* excl;    // [nbig] points of the big segments before this one
+  int2* skel;        // [nbig][HN]
+  uint32_t* slots;   // [nbig][HN]
+  uint32_t* nbk;     // [nbig] buckets
+  uint8_t* exact;    // [nbig] 1: exact level on the points; 2: already handled
+  uint32_t* hist;    // [tiles * NB]
+  uint32_t* hscan;
+  uint32_t* scnt;    // [nbig] samples
+  uint32_t* sizes;   // [nbig][HN] skeleton subtree sizes
+  Pts samp;          // sample buffer 0
+  Seg* children;     // [nbig * NB]
+  Node* nodes;
+  uint8_t* ndim;
+  uint32_t* shared_next;
+  uint64_t shared_cap;
+  DevStatus* st;
+};
+
+__device__ __forceinline__ uint32_t seg_of_tile(const uint32_t* tile0, uint32_t nseg, uint32_t tile) {
+  uint32_t lo = 0, hi = nseg;  // largest s with tile0[s] <= tile
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (tile0[mid] <= tile) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// tile0 / excl over the big segments (one block).
+static __global__ void k_big_prefix(const Seg* big, const uint32_t* nbig, uint32_t tile, uint32_t* tile0,
+                             uint64_t* excl) {
+  __shared__ uint32_t sh32[33];
+  __shared__ unsigned long long sh64[33];
+  const uint32_t n = *nbig;
+  uint32_t ct = 0;
+  unsigned long long cl = 0;
+  for (uint32_t base = 0; base < n; base += blockDim.x) {
+    uint32_t i = base + threadIdx.x;
+    uint32_t t = 0;
+    unsigned long long l = 0;
+    if (i < n) {
+      t = (big[i].len + tile - 1) / tile;
+      l = big[i].len;
+    }
+    uint32_t tt;
+    unsigned long long tl;
+    uint32_t et = block_excl_scan<uint32_t>(t, sh32, &tt);
+    unsigned long long el = block_excl_scan<unsigned long long>(l, sh64, &tl);
+    if (i < n) {
+      tile0[i] = ct + et;
+      excl[i] = cl + el;
+    }
+    ct += tt;
+    cl += tl;
+  }
+}
+
+struct SieveTile {
+  uint32_t s;
+  Seg seg;
+  uint64_t first;
+  int cnt;
+  uint32_t t0, nt;
+};
+
+__device__ __forceinline__ bool sieve_tile(const RoundArgs& r, SieveTile& t) {
+  const uint32_t nb = *r.nbig;
+  t.s = seg_of_tile(r.tile0, nb, blockIdx.x);
+  t.seg = r.big[t.s];
+  t.t0 = r.tile0[t.s];
+  t.nt = (t.seg.len + r.TILE - 1) / r.TILE;
+  t.first = (uint64_t)(blockIdx.x - t.t0) * r.TILE;
+  if (t.first >= t.seg.len) return false;
+  t.cnt = (int)min((uint64_t)r.TILE, (uint64_t)t.seg.len - t.first);
+  return true;
+}
+
+// Walk the heap skeleton held in shared memory (split, meta) to a bucket.
+template <int D>
+__device__ __forceinline__ int walk_bucket(const int2* sk, const int32_t* x, int lam) {
+  int h = 1;
+  for (int l = 0; l < lam; ++l) {
+    const int2 e = sk[h];
+    if (sk_state(e.y) != SK_INTERNAL) break;
+    h = 2 * h + (x[sk_dim(e.y)] >= e.x);
+  }
+  return sk_bucket(sk[h].y);
+}
+
+template <int D>
+__global__ void __launch_bounds__(SIEVE_THREADS) k_count(RoundArgs r) {
+  SieveTile t;
+  if (!sieve_tile(r, t)) return;
+  extern __shared__ __align__(16) uint8_t sm[];
+  int2* sk = (int2*)sm;
+  unsigned* lh = (unsigned*)(sk + r.HN);
+  const int2* gsk = r.skel + (uint64_t)t.s * r.HN;
+  for (int v = threadIdx.x; v < r.HN; v += blockDim.x) sk[v] = gsk[v];
+  for (int b = threadIdx.x; b < r.NB; b += blockDim.x) lh[b] = 0;
+  __syncthreads();
+  const bool heavy = sk_state(sk[1].y) == SK_HEAVY;
+  if (!heavy) {
+    for (int base = 0; base < t.cnt; base += blockDim.x) {
+      const int i = base + threadIdx.x;
+      int b = -1;
+      if (i < t.cnt) {
+        int32_t x[D];
+        const uint64_t g = t.seg.start + t.first + i;
+#pragma unroll
+        for (int j = 0; j < D; ++j) x[j] = r.src.x(D, j, g);
+        b = walk_bucket<D>(sk, x, r.lam);
+      }
+      const unsigned m = __match_any_sync(FULL_MASK, b);
+      if (b >= 0 && lane_id() == __ffs(m) - 1) atomicAdd(&lh[b], (unsigned)__popc(m));
+    }
+  }
+  __syncthreads();
+  const uint64_t hb = (uint64_t)t.t0 * r.NB;
+  const uint32_t tl = blockIdx.x - t.t0;
+  for (int b = threadIdx.x; b < r.NB; b += blockDim.x) r.hist[hb + (uint64_t)b * t.nt + tl] = lh[b];
+}
+
+template <int D>
+__global__ void __launch_bounds__(SIEVE_THREADS) k_scatter(RoundArgs r) {
+  SieveTile t;
+  if (!sieve_tile(r, t)) return;
+  extern __shared__ __align__(16) uint8_t sm[];
+  int2* sk = (int2*)sm;
+  unsigned* cur = (unsigned*)(sk + r.HN);      // [NB] per-bucket counters, then starts
+  unsigned* lstart = cur + r.NB;               // [NB]
+  uint32_t* gbase = lstart + r.NB;             // [NB] (relative to the segment start)
+  int32_t* stx = (int32_t*)(gbase + r.NB);     // [D][TILE]
+  uint32_t* sid = (uint32_t*)(stx + (size_t)D * r.TILE);
+  uint16_t* sb = (uint16_t*)(sid + r.TILE);
+  const int2* gsk = r.skel + (uint64_t)t.s * r.HN;
+  for (int v = threadIdx.x; v < r.HN; v += blockDim.x) sk[v] = gsk[v];
+  for (int b = threadIdx.x; b < r.NB; b += blockDim.x) cur[b] = 0;
+  __syncthreads();
+  if (sk_state(sk[1].y) == SK_HEAVY) return;
+  constexpr int PER = 8;  // TILE <= PER * SIEVE_THREADS
+  int32_t x[PER][D];
+  uint32_t id[PER];
+  int bk[PER], rk[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int i = k * SIEVE_THREADS + threadIdx.x;
+    bk[k] = -1;
+    rk[k] = 0;
+    if (i < t.cnt) {
+      const uint64_t g = t.seg.start + t.first + i;
+#pragma unroll
+      for (int j = 0; j < D; ++j) x[k][j] = r.src.x(D, j, g);
+      id[k] = r.src.id(g);
+      bk[k] = walk_bucket<D>(sk, x[k], r.lam);
+    }
+    const unsigned m = __match_any_sync(FULL_MASK, bk[k]);
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (bk[k] >= 0 && lane_id() == leader) base = atomicAdd(&cur[bk[k]], (unsigned)__popc(m));
+    base = __shfl_sync(FULL_MASK, base, leader);
+    rk[k] = (int)base + __popc(m & lanemask_lt());
+  }
+  __syncthreads();
+  // bucket starts inside the tile, and global bases from the scan
+  if (threadIdx.x < 32) {
+    unsigned carry = 0;
+    for (int b0 = 0; b0 < r.NB; b0 += 32) {
+      const int b = b0 + lane_id();
+      const unsigned c = b < r.NB ? cur[b] : 0;
+      const unsigned incl = (unsigned)warp_incl_scan((int)c);
+      if (b < r.NB) lstart[b] = carry + incl - c;
+      carry += __shfl_sync(FULL_MASK, incl, 31);
+    }
+  }
+  const uint64_t hb = (uint64_t)t.t0 * r.NB;
+  const uint32_t tl = blockIdx.x - t.t0;
+  const uint32_t segbase = r.hscan[hb];
+  for (int b = threadIdx.x; b < r.NB; b += blockDim.x)
+    gbase[b] = r.hscan[hb + (uint64_t)b * t.nt + tl] - segbase;
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    if (bk[k] >= 0) {
+      const int pos = (int)lstart[bk[k]] + rk[k];
+#pragma unroll
+      for (int j = 0; j < D; ++j) stx[j * r.TILE + pos] = x[k][j];
+      sid[pos] = id[k];
+      sb[pos] = (uint16_t)bk[k];
+    }
+  }
+  __syncthreads();
+  // every bucket's run leaves the tile as one contiguous, coalesced range
+  for (int pos = threadIdx.x; pos < t.cnt; pos += blockDim.x) {
+    const int b = sb[pos];
+    const uint64_t g = t.seg.start + gbase[b] + (uint64_t)(pos - (int)lstart[b]);
+#pragma unroll
+    for (int j = 0; j < D; ++j) r.dst.c[(uint64_t)j * r.dst.stride + g] = stx[j * r.TILE + pos];
+    r.dst.id[g] = sid[pos];
+  }
+}
+
+static size_t scatter_smem(int HN, int NB, int D, int tile) {
+  return (size_t)HN * 8 + (size_t)NB * 12 + (size_t)D * tile * 4 + (size_t)tile * 4 + (size_t)tile * 2;
+}
+
+template <int D>
+static void launch_count(const RoundArgs& r, uint32_t tiles, cudaStream_t s) {
+  const size_t sm = (size_t)r.HN * 8 + (size_t)r.NB * 4;
+  KTimer kt;
+  ktimer_begin(kt, "count", 0, s);
+  k_count<D><<<tiles, SIEVE_THREADS, sm, s>>>(r);
+  ktimer_end(kt);
+}
+
+template <int D>
+static void launch_scatter(const RoundArgs& r, uint32_t tiles, uint64_t pts, cudaStream_t s) {
+  const size_t sm = scatter_smem(r.HN, r.NB, D, r.TILE);
+  static bool set = false;
+  if (!set) {
+    cudaFuncSetAttribute(k_scatter<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    set = true;
+  }
+  KTimer kt;
+  ktimer_begin(kt, "scatter", pts, s);
+  k_scatter<D><<<tiles, SIEVE_THREADS, sm, s>>>(r);
+  ktimer_end(kt);
+}
+
+#define PKD_DISPATCH_D(d, F, ...) \
+  switch (d) {                    \
+    case 1: F<1>(__VA_ARGS__); break; \
+    case 2: F<2>(__VA_ARGS__); break; \
+    case 3: F<3>(__VA_ARGS__); break; \
+    case 4: F<4>(__VA_ARGS__); break; \
+    case 5: F<5>(__VA_ARGS__); break; \
+    case 6: F<6>(__VA_ARGS__); break; \
+    case 7: F<7>(__VA_ARGS__); break; \
+    default: F<8>(__VA_ARGS__); break; \
+  }
+
+// Shift a structure-of-arrays view so that absolute arena positions index
+// into a scratch allocation that only covers [base, base + extent).
+static Pts shifted(const Pts& p, uint64_t base) {
+  Pts q = p;
+  q.c = p.c - base;
+  q.id = p.id - base;
+  return q;
+}
+
+struct Scratch {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  ~Scratch() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+  }
+  template <class T>
+  int get(T** p, size_t n) {
+    int e = dalloc(p, n, s);
+    if (e == PKD_OK) ptrs.push_back(*p);
+    return e;
+  }
+};
+
+#define PKD_TRY(x)               \
+  do {                           \
+    int _r = (x);                \
+    if (_r != PKD_OK) return _r; \
+  } while (0)
+
+}  // namespace pkd

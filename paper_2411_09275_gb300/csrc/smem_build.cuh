@@ -212,7 +212,14 @@ __device__ int process_build(const T& tm, const SmemCtx& cx, Task tk, Task* ch) 
         on_sample = false;
         dim = wd;
         int less, eq;
-        x = team_select(tm, cx.s, P, lo, hi, false, dim, n / 2, less, eq);
+        int vmn = mn[0], vmx = mx[0];
+#pragma unroll
+        for (int j = 1; j < PKD_DMAX; ++j)
+          if (j == dim) {
+            vmn = mn[j];
+            vmx = mx[j];
+          }
+        x = team_select(tm, cx.s, P, lo, hi, false, dim, n / 2, vmn, vmx, less, eq);
         if (less == 0) x = team_min_above(tm, cx.s, P, lo, hi, false, dim, x);
       }
     } else {

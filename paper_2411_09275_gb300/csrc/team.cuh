@@ -209,21 +209,43 @@ __device__ __forceinline__ void warp_find_digit(const unsigned* hist, int k, int
 // (flagged points only when `sampled_only`).  count_less / count_eq: how many
 // of those elements are below / equal to it.  Coordinates are < 2^30, so the
 // four 8-bit digits from bit 24 down cover them exactly.
+//
+// vmin/vmax bound the values: bits above their highest differing bit are
+// common to every element, so the digits start just below them (a deep node
+// with a narrow range needs fewer passes, and its first digit spreads over
+// the bins instead of piling every element onto one counter).  Counter
+// updates are aggregated per warp over lanes that hit the same bin.
 template <class T>
 __device__ int team_select(const T& tm, const SmemPts& s, const uint16_t* idx, int lo, int hi,
-                           bool sampled_only, int dim, int k, int& count_less, int& count_eq) {
+                           bool sampled_only, int dim, int k, int vmin, int vmax, int& count_less,
+                           int& count_eq) {
   const int32_t* X = s.X + dim * s.cap;
-  unsigned prefix = 0, mask = 0;
+  if (vmin == vmax) {
+    count_less = 0;
+    count_eq = k + 1;  // not used by callers in this case
+    return vmin;
+  }
+  const int hb = 31 - __clz((unsigned)(vmin ^ vmax));  // highest differing bit
+  unsigned mask = hb >= 31 ? 0u : ~((2u << hb) - 1u);
+  unsigned prefix = (unsigned)vmin & mask;
   int less = 0, eq = 0;
-  for (int pass = 0; pass < 4; ++pass) {
-    const int shift = 24 - 8 * pass;
+  const int stride = tm.size();
+  const int wbase = tm.my_warp() * 32;
+  for (int top = hb; top >= 0; top -= 8) {
+    const int shift = max(top - 7, 0);
+    const unsigned dmask = (2u << (top - shift)) - 1u;
     for (int i = tm.rank(); i < 256; i += tm.size()) tm.hist[i] = 0;
     tm.sync();
-    for (int i = lo + tm.rank(); i < hi; i += tm.size()) {
-      int p = idx[i];
-      if (sampled_only && !s.flag[p]) continue;
-      unsigned v = (unsigned)X[p];
-      if ((v & mask) == prefix) atomicAdd(&tm.hist[(v >> shift) & 255u], 1u);
+    for (int base = lo + wbase; base < hi; base += stride) {
+      const int i = base + lane_id();
+      int key = -1;
+      if (i < hi) {
+        const int p = idx[i];
+        const unsigned v = (unsigned)X[p];
+        if ((!sampled_only || s.flag[p]) && (v & mask) == prefix) key = (int)((v >> shift) & dmask);
+      }
+      const unsigned m = __match_any_sync(FULL_MASK, key);
+      if (key >= 0 && lane_id() == __ffs(m) - 1) atomicAdd(&tm.hist[key], (unsigned)__popc(m));
     }
     tm.sync();
     int digit, below, e;
@@ -245,7 +267,7 @@ __device__ int team_select(const T& tm, const SmemPts& s, const uint16_t* idx, i
     }
     tm.sync();
     prefix |= (unsigned)digit << shift;
-    mask |= 255u << shift;
+    mask |= dmask << shift;
     k -= below;
     less += below;
     eq = e;
@@ -287,7 +309,14 @@ __device__ bool team_split_rule(const T& tm, const SmemPts& s, const uint16_t* i
   dim = widest_dim(mn, mx, s.d);
   if (dim < 0) return false;
   int less, eq;
-  x = team_select(tm, s, idx, lo, hi, sampled_only, dim, count / 2, less, eq);
+  int vmn = mn[0], vmx = mx[0];
+#pragma unroll
+  for (int j = 1; j < PKD_DMAX; ++j)
+    if (j == dim) {
+      vmn = mn[j];
+      vmx = mx[j];
+    }
+  x = team_select(tm, s, idx, lo, hi, sampled_only, dim, count / 2, vmn, vmx, less, eq);
   if (less == 0) x = team_min_above(tm, s, idx, lo, hi, sampled_only, dim, x);
   return true;
 }

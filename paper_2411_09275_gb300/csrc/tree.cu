@@ -159,6 +159,8 @@ void tree_release(TreeMem& t) {
   cudaFree(t.nodes);
   cudaFree(t.ndim);
   cudaFree(t.shared_next);
+  cudaFree(t.dead);
+  cudaFree(t.aux);
   cudaFree(t.st);
   if (t.st_host) cudaFreeHost(t.st_host);
   t = TreeMem{};

@@ -1,30 +1,863 @@
-// Batch updates (Alg. 2 and Sec. 4.2).
-#include "engine.hpp"
+// Batch updates of a Pkd-tree: BatchInsert (Alg. 2, Sec. 4.1) and the
+// two-round BatchDelete (Sec. 4.2).
+//
+//  route    the batch is sieved through the tree lambda levels at a time: the
+//           "skeleton at T" is fetched from the existing nodes (cut at
+//           leaves), and the same count / scan / scatter kernels as the build
+//           move every batch point to its external node.  Internal external
+//           nodes become the next round's items; leaves collect "leaf groups".
+//  match    (delete only) every stored point of a reached leaf is compared
+//           with the batch points routed there; matches are marked dead and
+//           points that match nothing are discarded (round 1 of Sec. 4.2).
+//  count    exact per-node counts of inserted / deleted points, aggregated
+//           bottom-up over the recorded skeletons.
+//  decide   top-down over every skeleton: a node that receives updates stays
+//           (its size is rewritten in place) when it is still alpha-balanced,
+//           otherwise it is rebuilt with Build on all its (live) points plus
+//           the new ones, and nothing below it is looked at.  A reached leaf
+//           is rebuilt (insert: Build(leaf + new)) or compacted (delete).
+//  rebuild  old subtrees are flattened by a parallel breadth-first walk into
+//           fresh arena ranges, new points appended, and every rebuild item
+//           becomes a root segment of one multi-segment build (build.cu).
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "sieve.cuh"
 #include "tree_impl.hpp"
+
+namespace pkd {
+
+constexpr uint32_t LINK_NONE = 0xFFFFFFFFu;
+constexpr uint32_t LINK_LEAF = 0x80000000u;
+
+struct LeafGroup {
+  uint32_t slot;   // the leaf's node slot
+  uint32_t depth;  // its tree depth
+  uint64_t start;  // first routed batch point (position in the batch buffers)
+  uint32_t len;    // routed batch points
+  uint32_t found;  // insert: len; delete: stored points removed
+  uint32_t flag;   // 1: inside a subtree that is rebuilt
+  uint32_t pad;
+};
+
+struct RebuildItem {
+  uint32_t slot;
+  uint32_t depth;
+  uint32_t size;    // points after the update
+  uint32_t old_live;
+  uint64_t ws, we;  // batch points (insert) in the final batch buffer
+  uint64_t pos;     // arena position assigned
+};
+
+struct UpdArgs {
+  Params p;
+  int lam, NB, HN, TILE;
+  int insert;
+  const Node* nodes;
+  Node* wnodes;
+  const uint8_t* ndim;
+  // this round
+  const Seg* items;
+  const uint32_t* nitems;
+  int2* skel;
+  uint32_t* slots;
+  uint32_t* nbk;
+  const uint32_t* tile0;
+  const uint32_t* hscan;
+  uint64_t* bstart;  // [item][NB]
+  uint32_t* blen;    // [item][NB]
+  uint32_t* link;    // [item][NB]
+  uint32_t* fnd;     // [item][HN]
+  uint32_t* iflag;   // [item]
+  // next round
+  Seg* next;
+  uint32_t* next_ctr;  // [0] items, [1] tiles
+  uint32_t* next_iflag;
+  const uint32_t* next_fnd;  // found counts of the next round (aggregation)
+  int next_HN;
+  // leaf groups
+  LeafGroup* groups;
+  uint32_t* ngroups;
+  uint32_t group_cap;
+  // rebuild items
+  RebuildItem* items_out;
+  uint32_t* nitems_out;
+  unsigned long long* items_total;
+  uint32_t items_cap;
+  uint32_t* aux;  // [node slot] deleted points below (delete only)
+  DevStatus* st;
+};
+
+// The skeleton at each item: its node and lambda levels below, cut at leaves.
+__global__ void k_fetch(UpdArgs a) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *a.nitems) return;
+  int2* sk = a.skel + (uint64_t)i * a.HN;
+  uint32_t* sl = a.slots + (uint64_t)i * a.HN;
+  for (int v = 1; v < a.HN; ++v) {
+    sk[v] = make_int2(0, sk_meta(SK_NONE, 0, 0));
+    sl[v] = 0xFFFFFFFFu;
+  }
+  sl[0] = 0xFFFFFFFFu;
+  sl[1] = a.items[i].root;
+  sk[1] = make_int2(0, sk_meta(SK_BUCKET, 0, 0));  // provisional: marks "defined"
+  for (int v = 1; v < a.HN; ++v) {
+    if (sk_state(sk[v].y) == SK_NONE) continue;
+    const uint32_t slot = sl[v];
+    const int j = 31 - __clz(v);
+    if (a.ndim[slot] == PKD_LEAF || j >= a.lam) {
+      sk[v] = make_int2(0, sk_meta(SK_BUCKET, 0, 0));
+      continue;
+    }
+    const Node nd = a.nodes[slot];
+    sk[v] = make_int2(nd.split, sk_meta(SK_INTERNAL, a.ndim[slot], 0));
+    sl[2 * v] = nd.a;
+    sl[2 * v + 1] = nd.b;
+    sk[2 * v] = make_int2(0, sk_meta(SK_BUCKET, 0, 0));
+    sk[2 * v + 1] = make_int2(0, sk_meta(SK_BUCKET, 0, 0));
+  }
+  // number the external nodes left to right
+  int stack[12];
+  int sp = 0, h = 1, nb = 0;
+  while (sp > 0 || h != 0) {
+    if (h != 0) {
+      if (sk_state(sk[h].y) == SK_INTERNAL) {
+        stack[sp++] = h;
+        h = 2 * h;
+        continue;
+      }
+      sk[h].y = sk_meta(SK_BUCKET, 0, nb++);
+      h = 0;
+    } else {
+      h = stack[--sp];
+      h = 2 * h + 1;
+    }
+  }
+  a.nbk[i] = nb;
+}
+
+// Bucket counts and ranges; next-round items and leaf groups.
+__global__ void k_route_emit(UpdArgs a) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *a.nitems) return;
+  const Seg it = a.items[i];
+  const int2* sk = a.skel + (uint64_t)i * a.HN;
+  const uint32_t* sl = a.slots + (uint64_t)i * a.HN;
+  const uint32_t nb = a.nbk[i];
+  const uint32_t nt = (it.len + a.TILE - 1) / a.TILE;
+  const uint64_t hb = (uint64_t)a.tile0[i] * a.NB;
+  const uint32_t base = a.hscan[hb];
+  for (uint32_t b = 0; b < (uint32_t)a.NB; ++b) a.link[(uint64_t)i * a.NB + b] = LINK_NONE;
+  for (int v = 1; v < a.HN; ++v) {
+    const int m = sk[v].y;
+    if (sk_state(m) != SK_BUCKET) continue;
+    const int b = sk_bucket(m);
+    const uint32_t b0 = a.hscan[hb + (uint64_t)b * nt] - base;
+    const uint32_t b1 = (b + 1 < (int)nb) ? a.hscan[hb + (uint64_t)(b + 1) * nt] - base : it.len;
+    const uint32_t cnt = b1 - b0;
+    const uint64_t k = (uint64_t)i * a.NB + b;
+    a.bstart[k] = it.start + b0;
+    a.blen[k] = cnt;
+    if (cnt == 0) continue;
+    const uint32_t slot = sl[v];
+    const uint32_t depth = it.depth + (31 - __clz(v));
+    if (a.ndim[slot] == PKD_LEAF) {
+      const uint32_t g = atomicAdd(a.ngroups, 1u);
+      if (g >= a.group_cap) {
+        set_error(a.st, DERR_CAPACITY, 800);
+        return;
+      }
+      a.groups[g] = LeafGroup{slot, depth, it.start + b0, cnt, a.insert ? cnt : 0u, 0u, 0u};
+      a.link[k] = LINK_LEAF | g;
+    } else {
+      const uint32_t q = atomicAdd(&a.next_ctr[0], 1u);
+      a.next[q] = Seg{it.start + b0, cnt, depth, slot, IN_B};
+      atomicAdd(&a.next_ctr[1], (cnt + a.TILE - 1) / a.TILE);
+      a.link[k] = q;
+    }
+  }
+}
+
+// Copy the batch points of the leaf groups created this round into the
+// final batch buffer F (later rounds never write their ranges again).
+__global__ void k_copy_groups(const LeafGroup* g, uint32_t g0, const uint32_t* g1, Pts src, Pts F, int d) {
+  const uint32_t gi = g0 + blockIdx.x;
+  if (gi >= *g1) return;
+  const LeafGroup G = g[gi];
+  for (uint32_t i = threadIdx.x; i < G.len; i += blockDim.x) {
+    const uint64_t p = G.start + i;
+    for (int j = 0; j < d; ++j) F.c[(uint64_t)j * F.stride + p] = src.c[(uint64_t)j * src.stride + p];
+    F.id[p] = src.id[p];
+  }
+}
+
+// Deletion round 1 at the leaves: mark stored points equal to a routed batch
+// point (coordinates and id); count them.
+__global__ void k_match(LeafGroup* groups, const uint32_t* ngroups, const Node* nodes, Pts A, Pts F,
+                        int d, uint8_t* dead, uint32_t* aux) {
+  const uint32_t gi = blockIdx.x * (blockDim.x / 32) + warp_id();
+  if (gi >= *ngroups) return;
+  LeafGroup& G = groups[gi];
+  const Node leaf = nodes[G.slot];
+  int found = 0;
+  for (uint32_t base = 0; base < leaf.size; base += 32) {
+    const uint32_t i = base + lane_id();
+    bool hit = false;
+    if (i < leaf.size) {
+      const uint64_t p = (uint64_t)leaf.a + i;
+      const uint32_t id = A.id[p];
+      for (uint32_t q = 0; q < G.len && !hit; ++q) {
+        const uint64_t r = G.start + q;
+        if (F.id[r] != id) continue;
+        bool same = true;
+        for (int j = 0; j < d; ++j) same &= A.c[(uint64_t)j * A.stride + p] == F.c[(uint64_t)j * F.stride + r];
+        hit = same;
+      }
+      if (hit) dead[p] = 1;
+    }
+    found += __popc(__ballot_sync(FULL_MASK, hit));
+  }
+  if (lane_id() == 0) {
+    G.found = (uint32_t)found;
+    aux[G.slot] = (uint32_t)found;
+  }
+}
+
+// Exact counts per skeleton node, bottom-up (rounds in reverse order).
+__global__ void k_aggregate(UpdArgs a) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *a.nitems) return;
+  const int2* sk = a.skel + (uint64_t)i * a.HN;
+  const uint32_t* sl = a.slots + (uint64_t)i * a.HN;
+  uint32_t* f = a.fnd + (uint64_t)i * a.HN;
+  for (int v = a.HN - 1; v >= 1; --v) {
+    const int m = sk[v].y;
+    const int st = sk_state(m);
+    if (st == SK_NONE) continue;
+    uint32_t c = 0;
+    if (st == SK_BUCKET) {
+      const uint32_t L = a.link[(uint64_t)i * a.NB + sk_bucket(m)];
+      if (L != LINK_NONE) c = (L & LINK_LEAF) ? a.groups[L & ~LINK_LEAF].found : a.next_fnd[(uint64_t)L * a.next_HN + 1];
+    } else {
+      c = f[2 * v] + f[2 * v + 1];
+    }
+    f[v] = c;
+    if (!a.insert && c) a.aux[sl[v]] = c;
+  }
+}
+
+__device__ void push_rebuild(const UpdArgs& a, uint32_t slot, uint32_t depth, uint32_t size,
+                             uint32_t old_live, uint64_t ws, uint64_t we) {
+  const uint32_t k = atomicAdd(a.nitems_out, 1u);
+  if (k >= a.items_cap) {
+    set_error(a.st, DERR_CAPACITY, 810);
+    return;
+  }
+  a.items_out[k] = RebuildItem{slot, depth, size, old_live, ws, we, 0};
+  atomicAdd(a.items_total, (unsigned long long)size);
+}
+
+// Top-down alpha test over every skeleton (rounds in forward order).
+__global__ void k_decide(UpdArgs a) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *a.nitems) return;
+  const Seg it = a.items[i];
+  const int2* sk = a.skel + (uint64_t)i * a.HN;
+  const uint32_t* sl = a.slots + (uint64_t)i * a.HN;
+  const uint32_t* f = a.fnd + (uint64_t)i * a.HN;
+  uint32_t under[64];  // one bit per heap node: inside a rebuilt subtree
+  for (int w = 0; w < (a.HN + 31) / 32; ++w) under[w] = 0;
+  if (a.iflag[i]) under[0] |= 2u;
+  for (int v = 1; v < a.HN; ++v) {
+    const int m = sk[v].y;
+    const int st = sk_state(m);
+    if (st == SK_NONE) continue;
+    const bool u = (under[v >> 5] >> (v & 31)) & 1u;
+    if (st == SK_BUCKET) {
+      if (!u) continue;
+      const uint32_t L = a.link[(uint64_t)i * a.NB + sk_bucket(m)];
+      if (L == LINK_NONE) continue;
+      if (L & LINK_LEAF) a.groups[L & ~LINK_LEAF].flag = 1;
+      else a.next_iflag[L] = 1;
+      continue;
+    }
+    const int c0 = 2 * v, c1 = 2 * v + 1;
+    if (u) {
+      under[c0 >> 5] |= 1u << (c0 & 31);
+      under[c1 >> 5] |= 1u << (c1 & 31);
+      continue;
+    }
+    const uint32_t c = f[v];
+    if (c == 0) continue;  // nothing below changes
+    const uint32_t slot = sl[v];
+    const uint32_t old = a.nodes[slot].size;
+    const uint32_t N = a.insert ? old + c : old - c;
+    const uint32_t lold = a.nodes[sl[c0]].size;
+    const uint32_t L = a.insert ? lold + f[c0] : lold - f[c0];
+    if (N > 0 && is_balanced(L, N, a.p.alpha_num, a.p.alpha_den)) {
+      a.wnodes[slot].size = N;
+      continue;
+    }
+    // rebuild this subtree; the batch points below it are contiguous
+    int lv = v, rv = v;
+    while (sk_state(sk[lv].y) == SK_INTERNAL) lv = 2 * lv;
+    while (sk_state(sk[rv].y) == SK_INTERNAL) rv = 2 * rv + 1;
+    const uint64_t kl = (uint64_t)i * a.NB + sk_bucket(sk[lv].y);
+    const uint64_t kr = (uint64_t)i * a.NB + sk_bucket(sk[rv].y);
+    const uint32_t depth = it.depth + (31 - __clz(v));
+    push_rebuild(a, slot, depth, N, a.insert ? old : old - c, a.bstart[kl], a.bstart[kr] + a.blen[kr]);
+    under[c0 >> 5] |= 1u << (c0 & 31);
+    under[c1 >> 5] |= 1u << (c1 & 31);
+  }
+}
+
+// Reached leaves outside rebuilt subtrees: insert -> rebuild item
+// Build(leaf + new); delete -> compacted in place (a leaf minus some of its
+// points is a leaf again).
+__global__ void k_leaf_items(UpdArgs a, LeafGroup* groups, const uint32_t* ngroups, uint32_t* compact,
+                             uint32_t* ncompact) {
+  const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= *ngroups) return;
+  const LeafGroup G = groups[gi];
+  if (G.flag) return;
+  const uint32_t old = a.nodes[G.slot].size;
+  if (a.insert) {
+    push_rebuild(a, G.slot, G.depth, old + G.len, old, G.start, G.start + G.len);
+  } else if (G.found) {
+    compact[atomicAdd(ncompact, 1u)] = gi;
+  }
+}
+
+__global__ void k_compact_leaves(const LeafGroup* groups, const uint32_t* list, const uint32_t* n,
+                                 Node* nodes, Pts A, int d, const uint8_t* dead) {
+  const uint32_t k = blockIdx.x * (blockDim.x / 32) + warp_id();
+  if (k >= *n) return;
+  const LeafGroup G = groups[list[k]];
+  Node nd = nodes[G.slot];
+  // survivors move to the front, in order; one warp, chunks of 32
+  uint32_t out = 0;
+  for (uint32_t base = 0; base < nd.size; base += 32) {
+    const uint32_t i = base + lane_id();
+    const bool keep = i < nd.size && !dead[(uint64_t)nd.a + i];
+    int32_t x[PKD_DMAX];
+    uint32_t id = 0;
+    if (keep) {
+      for (int j = 0; j < d; ++j) x[j] = A.c[(uint64_t)j * A.stride + nd.a + i];
+      id = A.id[(uint64_t)nd.a + i];
+    }
+    const unsigned m = __ballot_sync(FULL_MASK, keep);
+    __syncwarp();
+    if (keep) {
+      const uint64_t o = (uint64_t)nd.a + out + __popc(m & lanemask_lt());
+      for (int j = 0; j < d; ++j) A.c[(uint64_t)j * A.stride + o] = x[j];
+      A.id[o] = id;
+    }
+    out += __popc(m);
+    __syncwarp();
+  }
+  if (lane_id() == 0) nodes[G.slot].size = out;
+}
+
+// Arena positions of the rebuild items (exclusive scan of their sizes).
+__global__ void k_item_sizes(const RebuildItem* it, const uint32_t* n, uint32_t* sizes) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < *n) sizes[i] = it[i].size;
+}
+
+__global__ void k_item_pos(RebuildItem* it, const uint32_t* n, const uint32_t* off, uint64_t top, Seg* segs) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *n) return;
+  it[i].pos = top + off[i];
+  segs[i] = Seg{top + off[i], it[i].size, it[i].depth, it[i].slot, IN_A};
+}
+
+// Breadth-first flatten of the old subtrees of the rebuild items: every
+// frontier entry is (node, item, offset of its live points within the item).
+struct Front {
+  uint32_t slot;
+  uint32_t item;
+  uint64_t off;
+};
+
+__global__ void k_front_init(const RebuildItem* it, const uint32_t* n, Front* f, uint32_t* nf) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *n) return;
+  if (it[i].old_live == 0) return;
+  f[atomicAdd(nf, 1u)] = Front{it[i].slot, i, 0};
+}
+
+__global__ void k_front_expand(const Front* f, const uint32_t* nf, Front* g, uint32_t* ng, Front* leaves,
+                               uint32_t* nleaves, const Node* nodes, const uint8_t* ndim, const uint32_t* aux,
+                               int use_aux, uint32_t cap, DevStatus* st) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *nf) return;
+  const Front e = f[i];
+  if (ndim[e.slot] == PKD_LEAF) {
+    const uint32_t k = atomicAdd(nleaves, 1u);
+    if (k < cap) leaves[k] = e;
+    else set_error(st, DERR_CAPACITY, 820);
+    return;
+  }
+  const Node nd = nodes[e.slot];
+  const uint32_t llive = nodes[nd.a].size - (use_aux ? aux[nd.a] : 0u);
+  const uint32_t k = atomicAdd(ng, 2u);
+  if (k + 2 > cap) {
+    set_error(st, DERR_CAPACITY, 821);
+    return;
+  }
+  g[k] = Front{nd.a, e.item, e.off};
+  g[k + 1] = Front{nd.b, e.item, e.off + llive};
+}
+
+// One warp per flattened leaf: copy its live points to the item's range.
+__global__ void k_copy_leaves(const Front* lv, const uint32_t* n, const RebuildItem* items, const Node* nodes,
+                              Pts A, int d, const uint8_t* dead, int use_dead) {
+  const uint32_t k = blockIdx.x * (blockDim.x / 32) + warp_id();
+  if (k >= *n) return;
+  const Front e = lv[k];
+  const Node nd = nodes[e.slot];
+  const uint64_t dst0 = items[e.item].pos + e.off;
+  uint32_t out = 0;
+  for (uint32_t base = 0; base < nd.size; base += 32) {
+    const uint32_t i = base + lane_id();
+    const bool keep = i < nd.size && !(use_dead && dead[(uint64_t)nd.a + i]);
+    const unsigned m = __ballot_sync(FULL_MASK, keep);
+    if (keep) {
+      const uint64_t src = (uint64_t)nd.a + i, dst = dst0 + out + __popc(m & lanemask_lt());
+      for (int j = 0; j < d; ++j) A.c[(uint64_t)j * A.stride + dst] = A.c[(uint64_t)j * A.stride + src];
+      A.id[dst] = A.id[src];
+    }
+    out += __popc(m);
+  }
+}
+
+// Insert: append each item's new batch points after its old ones.
+__global__ void k_copy_new(const RebuildItem* items, const uint32_t* n, Pts F, Pts A, int d) {
+  const uint32_t k = blockIdx.x * (blockDim.x / 32) + warp_id();
+  if (k >= *n) return;
+  const RebuildItem it = items[k];
+  const uint64_t cnt = it.we - it.ws;
+  for (uint64_t i = lane_id(); i < cnt; i += 32) {
+    const uint64_t src = it.ws + i, dst = it.pos + it.old_live + i;
+    for (int j = 0; j < d; ++j) A.c[(uint64_t)j * A.stride + dst] = F.c[(uint64_t)j * F.stride + src];
+    A.id[dst] = F.id[src];
+  }
+}
+
+__global__ void k_clear_aux(const uint32_t* slots, uint64_t n, uint32_t* aux) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const uint32_t s = slots[i];
+    if (s != 0xFFFFFFFFu) aux[s] = 0;
+  }
+}
+
+__global__ void k_stage(const int32_t* coords, const uint32_t* ids, uint64_t m, int d, Pts W) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  for (int j = 0; j < d; ++j) W.c[(uint64_t)j * W.stride + i] = coords[i * d + j];
+  W.id[i] = ids[i];
+}
+
+// ---------------------------------------------------------------------------
+// host
+// ---------------------------------------------------------------------------
+
+// Grow the arena (and the per-position node region) to hold `need` more
+// points; node slots do not move, so the tree stays valid.
+static int ensure_capacity(TreeMem& t, uint64_t need, cudaStream_t s) {
+  if (t.top + need <= t.cap) return PKD_OK;
+  uint64_t ncap = std::max<uint64_t>(t.cap + t.cap / 2, t.top + need + 4096);
+  const uint64_t nnode = t.shared_cap + 2 * ncap;
+  if (nnode >= 0xFFFFFFF0ull) return PKD_ENOMEM;
+  Pts A2{};
+  Node* n2 = nullptr;
+  uint8_t* d2 = nullptr;
+  cudaError_t e = cudaMalloc((void**)&A2.c, (size_t)t.p.d * ncap * 4);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&A2.id, (size_t)ncap * 4);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n2, (size_t)nnode * sizeof(Node));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d2, (size_t)nnode);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(A2.c);
+    cudaFree(A2.id);
+    cudaFree(n2);
+    cudaFree(d2);
+    return PKD_ENOMEM;
+  }
+  A2.stride = ncap;
+  for (int j = 0; j < t.p.d; ++j)
+    PKD_CUDA(cudaMemcpyAsync(A2.c + (uint64_t)j * ncap, t.A.c + (uint64_t)j * t.cap, t.top * 4,
+                             cudaMemcpyDeviceToDevice, s));
+  PKD_CUDA(cudaMemcpyAsync(A2.id, t.A.id, t.top * 4, cudaMemcpyDeviceToDevice, s));
+  const uint64_t used = t.shared_cap + 2 * t.top;
+  PKD_CUDA(cudaMemcpyAsync(n2, t.nodes, used * sizeof(Node), cudaMemcpyDeviceToDevice, s));
+  PKD_CUDA(cudaMemcpyAsync(d2, t.ndim, used, cudaMemcpyDeviceToDevice, s));
+  // delete scratch grows with the arena and keeps its marks
+  uint8_t* dead2 = nullptr;
+  uint32_t* aux2 = nullptr;
+  if (t.dead) {
+    PKD_CUDA(cudaMalloc((void**)&dead2, ncap));
+    PKD_CUDA(cudaMemsetAsync(dead2, 0, ncap, s));
+    PKD_CUDA(cudaMemcpyAsync(dead2, t.dead, t.cap, cudaMemcpyDeviceToDevice, s));
+  }
+  if (t.aux) {
+    PKD_CUDA(cudaMalloc((void**)&aux2, nnode * 4));
+    PKD_CUDA(cudaMemsetAsync(aux2, 0, nnode * 4, s));
+    PKD_CUDA(cudaMemcpyAsync(aux2, t.aux, t.node_cap * 4, cudaMemcpyDeviceToDevice, s));
+  }
+  PKD_CUDA(cudaStreamSynchronize(s));
+  cudaFree(t.A.c);
+  cudaFree(t.A.id);
+  cudaFree(t.nodes);
+  cudaFree(t.ndim);
+  cudaFree(t.dead);
+  cudaFree(t.aux);
+  t.dead = dead2;
+  t.aux = aux2;
+  t.A = A2;
+  t.nodes = n2;
+  t.ndim = d2;
+  t.cap = ncap;
+  t.node_cap = nnode;
+  return PKD_OK;
+}
+
+static int ensure_delete_scratch(TreeMem& t, cudaStream_t s) {
+  if (!t.dead) {
+    PKD_CUDA(cudaMalloc((void**)&t.dead, t.cap));
+    PKD_CUDA(cudaMemsetAsync(t.dead, 0, t.cap, s));
+  }
+  if (!t.aux) {
+    PKD_CUDA(cudaMalloc((void**)&t.aux, t.node_cap * 4));
+    PKD_CUDA(cudaMemsetAsync(t.aux, 0, t.node_cap * 4, s));
+  }
+  return PKD_OK;
+}
+
+struct RouteRound {
+  Seg* items;
+  uint32_t n;
+  int2* skel;
+  uint32_t* slots;
+  uint32_t* fnd;
+  uint32_t* link;
+  uint64_t* bstart;
+  uint32_t* blen;
+  uint32_t* iflag;
+  uint32_t* d_n;  // device copy of n
+};
+
+static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, uint64_t m, bool insert,
+                      uint64_t* n_changed, cudaStream_t s) {
+  const Params& p = t.p;
+  const int d = p.d, lam = p.lambda, NB = 1 << lam, HN = 2 << lam;
+  const int TILE = std::min(std::max(knobs().tile, 256), 4096);
+  Scratch sc{s, {}};
+  if (!insert) PKD_TRY(ensure_delete_scratch(t, s));
+
+  // batch buffers: W0/W1 ping-pong for the sieve, F final positions
+  int32_t *wc[3];
+  uint32_t* wid[3];
+  for (int k = 0; k < 3; ++k) {
+    PKD_TRY(sc.get(&wc[k], (size_t)d * m));
+    PKD_TRY(sc.get(&wid[k], m));
+  }
+  Pts W[2] = {Pts{wc[0], wid[0], m}, Pts{wc[1], wid[1], m}};
+  Pts F{wc[2], wid[2], m};
+  k_stage<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(coords, ids, m, d, W[0]);
+
+  uint32_t* dctr;
+  PKD_TRY(sc.get(&dctr, 32));
+  PKD_CUDA(cudaMemsetAsync(dctr, 0, 32 * 4, s));
+  uint32_t* hctr = nullptr;
+  PKD_CUDA(cudaMallocHost((void**)&hctr, 128));
+  struct HostFree {
+    uint32_t* p;
+    ~HostFree() { cudaFreeHost(p); }
+  } hf{hctr};
+  uint32_t* d_ngroups = dctr + 4;
+  uint32_t* d_nitems = dctr + 5;
+  unsigned long long* d_total = (unsigned long long*)(dctr + 6);
+  uint32_t* d_ncompact = dctr + 8;
+
+  // every routed point ends in exactly one leaf group: at most m groups
+  const uint32_t group_cap = (uint32_t)std::min<uint64_t>(m + 16, 0xFFFFFFF0ull);
+  LeafGroup* groups;
+  PKD_TRY(sc.get(&groups, group_cap));
+  RebuildItem* items_out;
+  const uint32_t items_cap = group_cap;  // at most one rebuild per routed point
+  PKD_TRY(sc.get(&items_out, items_cap));
+
+  UpdArgs ua{};
+  ua.p = p;
+  ua.lam = lam;
+  ua.NB = NB;
+  ua.HN = HN;
+  ua.TILE = TILE;
+  ua.insert = insert ? 1 : 0;
+  ua.nodes = t.nodes;
+  ua.wnodes = t.nodes;
+  ua.ndim = t.ndim;
+  ua.groups = groups;
+  ua.ngroups = d_ngroups;
+  ua.group_cap = group_cap;
+  ua.items_out = items_out;
+  ua.nitems_out = d_nitems;
+  ua.items_total = d_total;
+  ua.items_cap = items_cap;
+  ua.aux = t.aux;
+  ua.st = t.st;
+
+  // ---- route ----
+  std::vector<RouteRound> rounds;
+  Seg root{0, (uint32_t)m, 0, t.root, IN_B};
+  Seg* cur;
+  PKD_TRY(sc.get(&cur, 1));
+  PKD_CUDA(cudaMemcpyAsync(cur, &root, sizeof(Seg), cudaMemcpyHostToDevice, s));
+  uint32_t ncur = 1, tiles = (uint32_t)((m + TILE - 1) / TILE);
+  int w = 0;
+  uint32_t groups_before = 0;
+  for (int r = 0; ncur > 0; ++r) {
+    if (r > 200) return PKD_EINTERNAL;
+    RouteRound R{};
+    R.items = cur;
+    R.n = ncur;
+    PKD_TRY(sc.get(&R.skel, (size_t)ncur * HN));
+    PKD_TRY(sc.get(&R.slots, (size_t)ncur * HN));
+    PKD_TRY(sc.get(&R.fnd, (size_t)ncur * HN));
+    PKD_TRY(sc.get(&R.link, (size_t)ncur * NB));
+    PKD_TRY(sc.get(&R.bstart, (size_t)ncur * NB));
+    PKD_TRY(sc.get(&R.blen, (size_t)ncur * NB));
+    PKD_TRY(sc.get(&R.iflag, ncur));
+    PKD_TRY(sc.get(&R.d_n, 1));
+    PKD_CUDA(cudaMemsetAsync(R.iflag, 0, (size_t)ncur * 4, s));
+    PKD_CUDA(cudaMemcpyAsync(R.d_n, &R.n, 4, cudaMemcpyHostToDevice, s));
+    uint32_t *nbk, *tile0, *hist, *hscan, *partial;
+    uint64_t* excl;
+    PKD_TRY(sc.get(&nbk, ncur));
+    PKD_TRY(sc.get(&tile0, ncur));
+    PKD_TRY(sc.get(&excl, ncur));
+    PKD_TRY(sc.get(&hist, (size_t)tiles * NB));
+    PKD_TRY(sc.get(&hscan, (size_t)tiles * NB));
+    const uint64_t nh = (uint64_t)tiles * NB;
+    PKD_TRY(sc.get(&partial, (nh + SCAN_TILE - 1) / SCAN_TILE + 1));
+    Seg* next;
+    PKD_TRY(sc.get(&next, (size_t)ncur * NB));
+    PKD_CUDA(cudaMemsetAsync(dctr, 0, 8, s));
+
+    ua.items = cur;
+    ua.nitems = R.d_n;
+    ua.skel = R.skel;
+    ua.slots = R.slots;
+    ua.nbk = nbk;
+    ua.tile0 = tile0;
+    ua.hscan = hscan;
+    ua.bstart = R.bstart;
+    ua.blen = R.blen;
+    ua.link = R.link;
+    ua.fnd = R.fnd;
+    ua.iflag = R.iflag;
+    ua.next = next;
+    ua.next_ctr = dctr;
+    const unsigned g1 = (ncur + 127) / 128;
+    k_fetch<<<g1, 128, 0, s>>>(ua);
+    k_big_prefix<<<1, 1024, 0, s>>>(cur, R.d_n, (uint32_t)TILE, tile0, excl);
+
+    RoundArgs ra{};
+    ra.p = p;
+    ra.lam = lam;
+    ra.NB = NB;
+    ra.HN = HN;
+    ra.TILE = TILE;
+    ra.src.soa = W[w];
+    ra.src.is_aos = 0;
+    ra.dst = W[w ^ 1];
+    ra.big = cur;
+    ra.nbig = R.d_n;
+    ra.tile0 = tile0;
+    ra.excl = excl;
+    ra.skel = R.skel;
+    ra.hist = hist;
+    ra.hscan = hscan;
+    ra.st = t.st;
+    PKD_DISPATCH_D(d, launch_count, ra, tiles, s);
+    device_excl_scan(hist, hscan, nh, partial, s);
+    k_route_emit<<<g1, 128, 0, s>>>(ua);
+    PKD_DISPATCH_D(d, launch_scatter, ra, tiles, (uint64_t)0, s);
+    PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 24, cudaMemcpyDeviceToHost, s));
+    PKD_CUDA(cudaStreamSynchronize(s));
+    const uint32_t nnext = hctr[0], ntiles = hctr[1], ngroups = hctr[4];
+    if (ngroups > groups_before)
+      k_copy_groups<<<ngroups - groups_before, 128, 0, s>>>(groups, groups_before, d_ngroups, W[w ^ 1], F, d);
+    groups_before = ngroups;
+    rounds.push_back(R);
+    cur = next;
+    ncur = nnext;
+    tiles = ntiles;
+    w ^= 1;
+  }
+  const uint32_t ngroups = groups_before;
+
+  // ---- match (delete) ----
+  if (!insert && ngroups)
+    k_match<<<(ngroups + 7) / 8, 256, 0, s>>>(groups, d_ngroups, t.nodes, t.A, F, d, t.dead, t.aux);
+
+  // ---- count, bottom-up ----
+  for (int r = (int)rounds.size() - 1; r >= 0; --r) {
+    RouteRound& R = rounds[r];
+    ua.items = R.items;
+    ua.nitems = R.d_n;
+    ua.skel = R.skel;
+    ua.slots = R.slots;
+    ua.link = R.link;
+    ua.fnd = R.fnd;
+    ua.next_fnd = (r + 1 < (int)rounds.size()) ? rounds[r + 1].fnd : nullptr;
+    ua.next_HN = HN;
+    k_aggregate<<<(R.n + 127) / 128, 128, 0, s>>>(ua);
+  }
+  uint32_t total_changed = 0;
+  PKD_CUDA(cudaMemcpyAsync(&total_changed, rounds[0].fnd + 1, 4, cudaMemcpyDeviceToHost, s));
+
+  // ---- decide, top-down ----
+  for (size_t r = 0; r < rounds.size(); ++r) {
+    RouteRound& R = rounds[r];
+    ua.items = R.items;
+    ua.nitems = R.d_n;
+    ua.skel = R.skel;
+    ua.slots = R.slots;
+    ua.link = R.link;
+    ua.fnd = R.fnd;
+    ua.bstart = R.bstart;
+    ua.blen = R.blen;
+    ua.iflag = R.iflag;
+    ua.next_iflag = (r + 1 < rounds.size()) ? rounds[r + 1].iflag : nullptr;
+    k_decide<<<(R.n + 127) / 128, 128, 0, s>>>(ua);
+  }
+  uint32_t* compact;
+  PKD_TRY(sc.get(&compact, std::max<uint32_t>(ngroups, 1)));
+  if (ngroups) k_leaf_items<<<(ngroups + 127) / 128, 128, 0, s>>>(ua, groups, d_ngroups, compact, d_ncompact);
+  PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 40, cudaMemcpyDeviceToHost, s));
+  PKD_CUDA(cudaStreamSynchronize(s));
+  const uint32_t nitems = hctr[5];
+  const uint64_t total = *(unsigned long long*)(hctr + 6);
+  const uint32_t ncompact = hctr[8];
+
+  // ---- delete: compact the reached leaves in place ----
+  if (ncompact)
+    k_compact_leaves<<<(ncompact + 7) / 8, 256, 0, s>>>(groups, compact, d_ncompact, t.nodes, t.A, d, t.dead);
+
+  // ---- rebuild ----
+  if (nitems) {
+    PKD_TRY(ensure_capacity(t, total, s));
+    uint32_t *isz, *ioff, *ipart;
+    PKD_TRY(sc.get(&isz, nitems));
+    PKD_TRY(sc.get(&ioff, nitems));
+    PKD_TRY(sc.get(&ipart, ((uint64_t)nitems + SCAN_TILE - 1) / SCAN_TILE + 1));
+    Seg* segs;
+    PKD_TRY(sc.get(&segs, nitems));
+    const unsigned gi = (nitems + 127) / 128;
+    k_item_sizes<<<gi, 128, 0, s>>>(items_out, d_nitems, isz);
+    device_excl_scan(isz, ioff, nitems, ipart, s);
+    k_item_pos<<<gi, 128, 0, s>>>(items_out, d_nitems, ioff, t.top, segs);
+    // flatten the old subtrees breadth first
+    uint64_t old_total = 0;
+    {
+      // capacity: every node of the old subtrees appears once
+      const uint64_t fcap = 4 * ((uint64_t)t.size + (uint64_t)nitems) + 1024;
+      Front *fa, *fb, *leaves;
+      PKD_TRY(sc.get(&fa, std::min<uint64_t>(fcap, 0xFFFFFFF0ull)));
+      PKD_TRY(sc.get(&fb, std::min<uint64_t>(fcap, 0xFFFFFFF0ull)));
+      PKD_TRY(sc.get(&leaves, std::min<uint64_t>(fcap, 0xFFFFFFF0ull)));
+      uint32_t* fc = dctr + 12;  // [0] cur, [1] next, [2] leaves
+      PKD_CUDA(cudaMemsetAsync(fc, 0, 12, s));
+      k_front_init<<<gi, 128, 0, s>>>(items_out, d_nitems, fa, fc);
+      PKD_CUDA(cudaMemcpyAsync(hctr + 12, fc, 12, cudaMemcpyDeviceToHost, s));
+      PKD_CUDA(cudaStreamSynchronize(s));
+      uint32_t nf = hctr[12];
+      const uint32_t fcap32 = (uint32_t)std::min<uint64_t>(fcap, 0xFFFFFFF0ull);
+      for (int it = 0; nf > 0; ++it) {
+        if (it > 100000) return PKD_EINTERNAL;
+        PKD_CUDA(cudaMemsetAsync(fc + 1, 0, 4, s));
+        k_front_expand<<<(nf + 127) / 128, 128, 0, s>>>(fa, fc, fb, fc + 1, leaves, fc + 2, t.nodes, t.ndim,
+                                                        t.aux, insert ? 0 : 1, fcap32, t.st);
+        PKD_CUDA(cudaMemcpyAsync(fc, fc + 1, 4, cudaMemcpyDeviceToDevice, s));
+        PKD_CUDA(cudaMemcpyAsync(hctr + 12, fc, 12, cudaMemcpyDeviceToHost, s));
+        PKD_CUDA(cudaStreamSynchronize(s));
+        nf = hctr[12];
+        std::swap(fa, fb);
+      }
+      const uint32_t nleaves = hctr[14];
+      if (nleaves)
+        k_copy_leaves<<<(nleaves + 7) / 8, 256, 0, s>>>(leaves, fc + 2, items_out, t.nodes, t.A, d, t.dead,
+                                                        insert ? 0 : 1);
+      (void)old_total;
+    }
+    if (insert) k_copy_new<<<(nitems + 7) / 8, 256, 0, s>>>(items_out, d_nitems, F, t.A, d);
+    BuildJob job;
+    job.base = t.top;
+    job.extent = std::max<uint64_t>(total, 1);
+    job.dsegs = segs;
+    job.dsegs_n = nitems;
+    PKD_TRY(run_build(t, job, s));
+    t.top += total;
+  }
+
+  // ---- delete: clear the marks this batch set ----
+  if (!insert) {
+    PKD_CUDA(cudaMemsetAsync(t.dead, 0, t.cap, s));
+    for (auto& R : rounds)
+      k_clear_aux<<<(unsigned)(((uint64_t)R.n * HN + 255) / 256), 256, 0, s>>>(R.slots, (uint64_t)R.n * HN, t.aux);
+    // (a leaf group's slot is a heap bucket of its round, cleared above)
+  }
+  PKD_CUDA(cudaStreamSynchronize(s));
+  if (n_changed) *n_changed = total_changed;
+  return PKD_OK;
+}
+
+}  // namespace pkd
 
 using namespace pkd;
 
 extern "C" {
 
-int pkd_batch_insert(pkd_tree* t, const int32_t* coords, const uint32_t* ids, uint64_t m,
-                     void* stream) {
-  (void)t;
-  (void)coords;
-  (void)ids;
-  (void)m;
-  (void)stream;
-  return PKD_EINVAL;
+int pkd_batch_insert(pkd_tree* tc, const int32_t* coords, const uint32_t* ids, uint64_t m, void* stream) {
+  if (!tc) return PKD_EINVAL;
+  if (m == 0) return PKD_OK;
+  if (!coords || !ids) return PKD_EINVAL;
+  TreeMem& t = tc->m;
+  if (t.size + m >= (1ull << 31)) return PKD_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  bool ok;
+  PKD_TRY_(validate_coords(coords, m * (uint64_t)t.p.d, s, &ok));
+  if (!ok) return PKD_EINVAL;
+  PKD_TRY_(check_status(t, s));
+  uint64_t changed = 0;
+  int e = run_update(t, coords, ids, m, true, &changed, s);
+  if (e == PKD_OK) e = check_status(t, s);
+  if (e == PKD_OK) t.size += m;
+  return e;
 }
 
-int pkd_batch_delete(pkd_tree* t, const int32_t* coords, const uint32_t* ids, uint64_t m,
+int pkd_batch_delete(pkd_tree* tc, const int32_t* coords, const uint32_t* ids, uint64_t m,
                      uint64_t* n_deleted, void* stream) {
-  (void)t;
-  (void)coords;
-  (void)ids;
-  (void)m;
-  (void)n_deleted;
-  (void)stream;
-  return PKD_EINVAL;
+  if (!tc) return PKD_EINVAL;
+  if (n_deleted) *n_deleted = 0;
+  if (m == 0) return PKD_OK;
+  if (!coords || !ids) return PKD_EINVAL;
+  TreeMem& t = tc->m;
+  if (m >= (1ull << 31)) return PKD_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  PKD_TRY_(check_status(t, s));
+  uint64_t removed = 0;
+  int e = run_update(t, coords, ids, m, false, &removed, s);
+  if (e == PKD_OK) e = check_status(t, s);
+  if (e == PKD_OK) {
+    t.size -= removed;
+    if (n_deleted) *n_deleted = removed;
+  }
+  return e;
 }
 
 }  // extern "C"

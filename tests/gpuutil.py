@@ -24,7 +24,9 @@ def to_dev(a):
 def ids_dev(a):
     import torch
 
-    return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev())
+    a = np.asarray(a)
+    assert a.min(initial=0) >= 0 and a.max(initial=0) < (1 << 32)
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).to(dev())
 
 
 def oparams(p) -> O.Params:

@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 Pkd-tree hot path.
+
+One step = the whole hot path on one synthetic batch: BuildTree over n points
+(sample, skeleton, sieve rounds, shared-memory base cases), then BatchInsert
+of m new points and BatchDelete of m random existing points (alpha = 0.3).
+The default workload is n = 1e8 3-D int32 points uniform in [0, 2^30),
+m = 1e7 (the paper's 1% batches), parameters lambda = 6, phi = 32, sample
+rate 1/64, sigma_os = 32.  Inputs (1.6 GB) are larger than the 129 MB L2,
+so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank builds its own independent tree (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Pkd-tree build Mpts/s + % HBM roofline; batch-update Mpts/s; p99 request latency"
+PEAK_FALLBACK_GBS = 6800.0
+
+WORKLOADS = {
+    # configs[1]: build 1e8 3-D uniform, insert 1e7, delete 1e7 random existing ids
+    "build1e8_d3_ins1e7_del1e7": dict(n=100_000_000, d=3, m=10_000_000, kind="uniform"),
+    # configs[0] at full size (fits in L2: roofline not claimed)
+    "build1e6_d2_ins1e4_del1e4": dict(n=1_000_000, d=2, m=10_000, kind="uniform"),
+    # small case for quick checks
+    "build1e7_d3_ins1e6_del1e6": dict(n=10_000_000, d=3, m=1_000_000, kind="uniform"),
+}
+DEFAULT_WORKLOAD = "build1e8_d3_ins1e7_del1e7"
+
+# Algorithmic bytes per point moved by each kernel family (int32 coords + id):
+# a sieve scatter or a shared-memory base case reads and writes every point
+# once, 2 * (4d + 4); a count pass reads the coordinates only, 4d; the sample
+# pass reads the ids, 4.
+def algo_bytes(kernel: str, d: int) -> float | None:
+    return {"scatter": 2 * (4 * d + 4), "smem_build": 2 * (4 * d + 4), "smem_warp": 2 * (4 * d + 4),
+            "count": 4 * d, "sample": 4, "validate": 4}.get(kernel)
+
+
+TIMED_KERNELS = ["smem_build", "smem_warp", "scatter", "count", "sample", "validate"]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j.get("hbm_gbs", PEAK_FALLBACK_GBS)), "measured"
+    return PEAK_FALLBACK_GBS, "fallback"
+
+
+def dram_traffic():
+    """Per-item DRAM bytes from a committed ncu summary, if one exists."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def barrier_max(x: float, ws: int, dev=None) -> float:
+    """Barrier, then the maximum of x over all ranks."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=dev if dev is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_inputs(wl: dict, rank: int):
+    from paper_2411_09275_gb300 import inputs as I
+
+    n, d, m = wl["n"], wl["d"], wl["m"]
+    seed = 1000 * rank
+    X = I.points(wl["kind"], n, d, I.SEED_DATA + seed if wl["kind"] == "uniform" else I.SEED_VARDEN + seed)
+    Y = I.points(wl["kind"], m, d, I.SEED_INSERT + seed)
+    yid = np.arange(n, n + m, dtype=np.uint32)
+    sel = I.sample_indices(m, n + m, I.SEED_DELETE + seed)
+    in_x = sel < n
+    Z = np.empty((m, d), np.int32)
+    Z[in_x] = X[sel[in_x]]
+    Z[~in_x] = Y[sel[~in_x] - n]
+    return X, Y, yid, Z, sel.astype(np.uint32)
+
+
+def cpu_oracle_step(wl: dict, scale: int = 100):
+    """The oracle on 1/scale of the workload (single-threaded); returns
+    (points processed, seconds, description)."""
+    import oracle as O
+    from paper_2411_09275_gb300 import inputs as I
+
+    n, d, m = wl["n"] // scale, wl["d"], max(wl["m"] // scale, 1)
+    X = I.points(wl["kind"], n, d, I.SEED_DATA)
+    Y = I.points(wl["kind"], m, d, I.SEED_INSERT)
+    yid = np.arange(n, n + m, dtype=np.uint32)
+    sel = I.sample_indices(m, n + m, I.SEED_DELETE)
+    allX = np.concatenate([X, Y])
+    t0 = time.perf_counter()
+    t = O.OracleTree(X, None, O.Params(d=d))
+    t.insert(Y, yid)
+    t.delete(allX[sel], sel)
+    dt = time.perf_counter() - t0
+    t.close()
+    desc = f"oracle, 1 thread: build n={n} d={d} {wl['kind']} + insert {m} + delete {m} (1/{scale} of the workload)"
+    return n + 2 * m, dt, desc
+
+
+def run_reference(args, wl):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        cpu_oracle_step(wl)
+    pts, tot = 0, 0.0
+    for _ in range(args.steps):
+        p, dt, desc = cpu_oracle_step(wl)
+        pts += p
+        tot += dt
+    v = pts / tot / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpts/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": config_of(args, wl),
+            "cpu_baseline": {"value": v, "unit": "Mpts/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(args, wl):
+    return {"workload": args.workload, "n": wl["n"], "d": wl["d"], "m_insert": wl["m"],
+            "m_delete": wl["m"], "distribution": wl["kind"], "phi": 32, "lambda": 6,
+            "sample_rate": "1/64", "sigma_os": 32, "alpha": "3/10",
+            "l2": "inputs larger than L2 (no flush needed)" if wl["n"] * (4 * wl["d"] + 4) > 129e6
+            else "inputs fit in L2: roofline not claimed",
+            "parallelism": f"independent tree per GPU x{args.gpus}"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--varden", action="store_true", help="also time the varden-like variant")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+
+    from paper_2411_09275_gb300 import pkd
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkd.lib()
+
+    X, Y, yid, Z, zid = make_inputs(wl, rank)
+    d = wl["d"]
+    gX = torch.from_numpy(X).to(dev)
+    gY = torch.from_numpy(Y).to(dev)
+    gyid = torch.from_numpy(yid.view(np.int32)).to(dev)
+    gZ = torch.from_numpy(Z).to(dev)
+    gzid = torch.from_numpy(zid.view(np.int32)).to(dev)
+    params = pkd.Params(d=d)
+    stream = torch.cuda.current_stream(dev)
+    n, m = wl["n"], wl["m"]
+
+    def step(ev=None):
+        t = pkd.pkd_build(gX, None, params, stream)
+        if ev is not None:
+            ev[0].record(stream)
+        pkd.pkd_batch_insert(t, gY, gyid, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        nd = pkd.pkd_batch_delete(t, gZ, gzid, stream)
+        if ev is not None:
+            ev[2].record(stream)
+        size = pkd.pkd_size(t)
+        pkd.pkd_free(t)
+        return nd, size
+
+    for _ in range(max(args.warmup, 3)):
+        nd, size = step()
+    assert nd == m and size == n, (nd, size)
+
+    # ---- device-timed region: inputs resident in HBM ----
+    pkd.pkd_kernel_timing(True)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    gpu_index = local
+    try:
+        gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local])
+    except (ValueError, IndexError):
+        pass
+    barrier_max(0.0, ws, dev)
+    torch.cuda.synchronize(dev)
+    with Clocks(gpu_index) as clk:
+        e0.record(stream)
+        for k in range(args.steps):
+            starts[k].record(stream)
+            step(evs[k])
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    elapsed_ms = barrier_max(e0.elapsed_time(e1), ws, dev)
+    launches = pkd.pkd_kernel_stats("launches")[0]
+    kstats = {k: pkd.pkd_kernel_stats(k) for k in TIMED_KERNELS}
+    phase = {"build_ms": 0.0, "insert_ms": 0.0, "delete_ms": 0.0}
+    for k in range(args.steps):
+        phase["build_ms"] += starts[k].elapsed_time(evs[k][0])
+        phase["insert_ms"] += evs[k][0].elapsed_time(evs[k][1])
+        phase["delete_ms"] += evs[k][1].elapsed_time(evs[k][2])
+    for key in list(phase):
+        phase[key] /= args.steps
+    pkd.pkd_kernel_timing(False)
+
+    pts_step = n + 2 * m
+    ms_per_step = elapsed_ms / args.steps
+    value = ws * pts_step * args.steps / (elapsed_ms / 1e3) / 1e6
+    peak, peak_src = measured_peaks()
+    kernels = {}
+    for name, (cnt, ms, items) in kstats.items():
+        b = algo_bytes(name, d)
+        if cnt == 0 or ms <= 0:
+            continue
+        gbs = (b * items / (ms / 1e3) / 1e9) if (b and items) else None
+        kernels[name] = {"launches": cnt, "ms_per_step": ms / args.steps, "items_per_launch": items / cnt,
+                         "algo_bytes_per_item": b, "achieved_gbs": gbs}
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"]) if kernels else None
+    roof = None
+    if dom:
+        kd = kernels[dom]
+        tr = dram_traffic().get(dom)
+        traffic = (tr["dram_bytes_per_item"] * kd["items_per_launch"]) if tr else None
+        roof = {"bound": "hbm", "kernel": dom, "achieved": kd["achieved_gbs"], "peak": peak,
+                "unit": "GB/s", "frac": (kd["achieved_gbs"] / peak) if kd["achieved_gbs"] else None,
+                "traffic": traffic, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        hX = torch.from_numpy(X).pin_memory()
+        hY = torch.from_numpy(Y).pin_memory()
+        hyid = torch.from_numpy(yid.view(np.int32)).pin_memory()
+        hZ = torch.from_numpy(Z).pin_memory()
+        hzid = torch.from_numpy(zid.view(np.int32)).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in (hX, hY, hyid, hZ, hzid))
+        dX, dY, dyid, dZ, dzid = (torch.empty_like(t, device=dev) for t in (hX, hY, hyid, hZ, hzid))
+
+        def e2e_step():
+            for dd, hh in ((dX, hX), (dY, hY), (dyid, hyid), (dZ, hZ), (dzid, hzid)):
+                dd.copy_(hh, non_blocking=True)
+            t = pkd.pkd_build(dX, None, params, stream)
+            pkd.pkd_batch_insert(t, dY, dyid, stream)
+            nd = pkd.pkd_batch_delete(t, dZ, dzid, stream)  # n_deleted comes back to the host
+            pkd.pkd_free(t)
+            return nd
+
+        e2e_step()
+        barrier_max(0.0, ws, dev)
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = barrier_max(a.elapsed_time(b), ws, dev)
+        e2e = {"value": ws * pts_step * args.steps / (e2e_ms / 1e3) / 1e6, "unit": "Mpts/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8}
+
+    # ---- varden-like variant (same sizes), reported beside the headline ----
+    varden = None
+    if args.varden:
+        wv = dict(wl, kind="varden")
+        Xv, Yv, yv, Zv, zv = make_inputs(wv, rank)
+        gX.copy_(torch.from_numpy(Xv))
+        gY.copy_(torch.from_numpy(Yv))
+        gZ.copy_(torch.from_numpy(Zv))
+        gzid.copy_(torch.from_numpy(zv.view(np.int32)))
+        step()
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        a.record(stream)
+        step(ev)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        varden = {"ms_per_step": a.elapsed_time(b), "build_ms": a.elapsed_time(ev[0]),
+                  "insert_ms": ev[0].elapsed_time(ev[1]), "delete_ms": ev[1].elapsed_time(ev[2]),
+                  "value": pts_step / (a.elapsed_time(b) / 1e3) / 1e6}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        p, dt, desc = cpu_oracle_step(wl)
+        cpu = {"value": p / dt / 1e6, "unit": "Mpts/s", "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": config_of(args, wl), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk.summary(),
+                "phases": dict(phase, build_mpts=n / phase["build_ms"] / 1e3,
+                               insert_mpts=m / phase["insert_ms"] / 1e3,
+                               delete_mpts=m / phase["delete_ms"] / 1e3),
+                "kernels": kernels, "varden": varden}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -148,7 +148,9 @@ int pkd_set_option(const char* name, int64_t value);
 /* Per-kernel timing with CUDA events on the launching stream (off by
  * default).  pkd_kernel_stats fills, for kernel family `name`, the number
  * of timed launches, their summed duration in ms and the points (items)
- * they processed; pkd_kernel_timing(1) enables and clears the counters. */
+ * they processed; pkd_kernel_timing(1) enables and clears the counters.
+ * The name "launches" reports, in *launches, every kernel launch the
+ * library made since the last pkd_kernel_timing call (timed or not). */
 int pkd_kernel_timing(int enable);
 int pkd_kernel_stats(const char* name, uint64_t* launches, double* total_ms, uint64_t* items);
 

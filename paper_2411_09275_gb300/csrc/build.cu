@@ -270,28 +270,47 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_smem_warp(SmemArgs a) {
 __global__ void k_classify(const Seg* segs, uint32_t nseg, uint32_t cap, Seg* big, uint32_t* ctr,
                            unsigned long long* pts, Seg* base, uint32_t* nbase, uint32_t base_cap,
                            Seg* wbase, uint32_t* nwbase, uint32_t wcap, uint32_t tile, uint32_t where,
-                           DevStatus* st) {
-  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nseg) return;
-  Seg s = segs[i];
-  if (s.len == SEG_SKIP) return;
-  s.where = where;
-  if (s.len > cap) {
-    uint32_t k = atomicAdd(&ctr[0], 1u);
-    big[k] = s;
-    atomicAdd(&ctr[2], (s.len + tile - 1) / tile);
-    atomicAdd(pts, (unsigned long long)s.len);
-  } else if (s.len > wcap) {
-    uint32_t k = atomicAdd(nbase, 1u);
-    if (k < base_cap) base[k] = s;
-    else set_error(st, DERR_CAPACITY, 300);
-  } else {
-    uint32_t k = atomicAdd(nwbase, 1u);
-    if (k < base_cap) wbase[k] = s;
-    else set_error(st, DERR_CAPACITY, 301);
+                           unsigned long long* base_pts, DevStatus* st) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  Seg s{};
+  int kind = -1;  // 0 big, 1 one CTA, 2 one warp
+  if (i < nseg) {
+    s = segs[i];
+    if (s.len != SEG_SKIP) {
+      s.where = where;
+      kind = s.len > cap ? 0 : (s.len > wcap ? 1 : 2);
+    }
+  }
+  // counters are updated once per warp and kind
+  for (int k = 0; k < 3; ++k) {
+    const unsigned m = __ballot_sync(FULL_MASK, kind == k);
+    if (!m) continue;
+    unsigned long long sum = kind == k ? s.len : 0;
+    uint32_t tl = (kind == 0) ? (s.len + tile - 1) / tile : 0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      sum += __shfl_xor_sync(FULL_MASK, sum, o);
+      tl += __shfl_xor_sync(FULL_MASK, tl, o);
+    }
+    uint32_t b = 0;
+    if (lane_id() == 0) {
+      if (k == 0) {
+        b = atomicAdd(&ctr[0], (uint32_t)__popc(m));
+        atomicAdd(&ctr[2], tl);
+        atomicAdd(pts, sum);
+      } else {
+        b = atomicAdd(k == 1 ? nbase : nwbase, (uint32_t)__popc(m));
+        atomicAdd(&base_pts[k - 1], sum);
+      }
+    }
+    b = __shfl_sync(FULL_MASK, b, 0) + __popc(m & lanemask_lt());
+    if (kind == k) {
+      if (k == 0) big[b] = s;
+      else if (b < base_cap) (k == 1 ? base : wbase)[b] = s;
+      else set_error(st, DERR_CAPACITY, 300 + k);
+    }
   }
 }
-
 
 // Sample: points whose hash at the segment's depth passes the rate test.
 __global__ void k_sample(RoundArgs r) {
@@ -854,19 +873,19 @@ static int run_skeleton_jobs(JobArgs ja, SkelJob* big0, uint32_t nbig_jobs, uint
     ja.jhist = jhist;
     ja.next_big = nxt;
     const unsigned g1 = (njobs + 127) / 128;
-    k_job_tiles<<<1, 1024, 0, s>>>(cur, d_njobs, jtile0);
-    k_job_init<<<g1, 128, 0, s>>>(ja);
+    PKD_LAUNCH(k_job_tiles<<<1, 1024, 0, s>>>(cur, d_njobs, jtile0));
+    PKD_LAUNCH(k_job_init<<<g1, 128, 0, s>>>(ja));
     PKD_CUDA(cudaMemsetAsync(dctr, 0, 8, s));  // next big jobs and tiles
-    k_job_stats<<<tiles, JOB_THREADS, 0, s>>>(ja);
-    k_job_choose<<<g1, 128, 0, s>>>(ja);
+    PKD_LAUNCH(k_job_stats<<<tiles, JOB_THREADS, 0, s>>>(ja));
+    PKD_LAUNCH(k_job_choose<<<g1, 128, 0, s>>>(ja));
     for (int pass = 0; pass < 4; ++pass) {
-      k_job_hist<<<tiles, JOB_THREADS, 0, s>>>(ja, pass);
-      k_job_pick<<<(njobs * 32 + 127) / 128, 128, 0, s>>>(ja, pass);
+      PKD_LAUNCH(k_job_hist<<<tiles, JOB_THREADS, 0, s>>>(ja, pass));
+      PKD_LAUNCH(k_job_pick<<<(njobs * 32 + 127) / 128, 128, 0, s>>>(ja, pass));
     }
-    k_job_minabove<<<tiles, JOB_THREADS, 0, s>>>(ja);
-    k_job_fix<<<g1, 128, 0, s>>>(ja);
-    k_job_partition<<<tiles, JOB_THREADS, 0, s>>>(ja);
-    k_job_children<<<g1, 128, 0, s>>>(ja);
+    PKD_LAUNCH(k_job_minabove<<<tiles, JOB_THREADS, 0, s>>>(ja));
+    PKD_LAUNCH(k_job_fix<<<g1, 128, 0, s>>>(ja));
+    PKD_LAUNCH(k_job_partition<<<tiles, JOB_THREADS, 0, s>>>(ja));
+    PKD_LAUNCH(k_job_children<<<g1, 128, 0, s>>>(ja));
     PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 12, cudaMemcpyDeviceToHost, s));
     PKD_CUDA(cudaStreamSynchronize(s));
     njobs = hctr[0];
@@ -885,7 +904,7 @@ static int run_skeleton_jobs(JobArgs ja, SkelJob* big0, uint32_t nbig_jobs, uint
     sa.cap = skel_cap_for(d);
     const size_t smb = smem_layout(sa.cap, d).total;
     cudaFuncSetAttribute(k_smem_skel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
-    k_smem_skel<<<nsmall, SM_THREADS, smb, s>>>(sa);
+    PKD_LAUNCH(k_smem_skel<<<nsmall, SM_THREADS, smb, s>>>(sa));
   }
   return PKD_OK;
 }
@@ -915,16 +934,17 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
   // device counters: [0] big segs, [2] their tiles, [3] exact, [4] heavy,
   // [8..10] skeleton jobs; [12] base list length; u64 at [14] big points
   uint32_t* dctr;
-  PKD_TRY(sc.get(&dctr, 16));
+  PKD_TRY(sc.get(&dctr, 24));
   unsigned long long* dpts = (unsigned long long*)(dctr + 14);
+  unsigned long long* dbase_pts = (unsigned long long*)(dctr + 16);
   uint32_t* d_nbase = dctr + 12;
   uint32_t* hctr = nullptr;
-  PKD_CUDA(cudaMallocHost((void**)&hctr, 64));
+  PKD_CUDA(cudaMallocHost((void**)&hctr, 128));
   struct HostFree {
     uint32_t* p;
     ~HostFree() { cudaFreeHost(p); }
   } hf{hctr};
-  PKD_CUDA(cudaMemsetAsync(dctr, 0, 16 * 4, s));
+  PKD_CUDA(cudaMemsetAsync(dctr, 0, 24 * 4, s));
 
   const uint64_t nroots = job.dsegs ? job.dsegs_n : job.segs.size();
   Seg* cur;
@@ -979,9 +999,9 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     PKD_TRY(sc.get(&big, ncur));
     PKD_CUDA(cudaMemsetAsync(dctr, 0, 12 * 4, s));
     PKD_CUDA(cudaMemsetAsync(dpts, 0, 8, s));
-    k_classify<<<(unsigned)((ncur + 255) / 256), 256, 0, s>>>(
+    PKD_LAUNCH(k_classify<<<(unsigned)((ncur + 255) / 256), 256, 0, s>>>(
         cur, (uint32_t)ncur, cap, big, dctr, dpts, base_list, d_nbase, (uint32_t)base_cap_segs,
-        wbase_list, d_nbase + 1, wcap, (uint32_t)TILE, (uint32_t)src_where, t.st);
+        wbase_list, d_nbase + 1, wcap, (uint32_t)TILE, (uint32_t)src_where, dbase_pts, t.st));
     PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 16 * 4, cudaMemcpyDeviceToHost, s));
     PKD_CUDA(cudaStreamSynchronize(s));
     const uint32_t nbig = hctr[0], tiles = hctr[2];
@@ -1021,13 +1041,13 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     PKD_CUDA(cudaMemsetAsync(r.skel, 0, (size_t)nbig * HN * sizeof(int2), s));
     PKD_CUDA(cudaMemsetAsync(r.scnt, 0, (size_t)nbig * 4, s));
     PKD_CUDA(cudaMemsetAsync(r.exact, 0, nbig, s));
-    k_big_prefix<<<1, 1024, 0, s>>>(big, dctr, (uint32_t)TILE, r.tile0, r.excl);
+    PKD_LAUNCH(k_big_prefix<<<1, 1024, 0, s>>>(big, dctr, (uint32_t)TILE, r.tile0, r.excl));
 
     // 1. sample
     {
       KTimer kt;
       ktimer_begin(kt, "sample", pts_big, s);
-      k_sample<<<tiles, 256, 0, s>>>(r);
+      PKD_LAUNCH(k_sample<<<tiles, 256, 0, s>>>(r));
       ktimer_end(kt);
     }
 
@@ -1056,15 +1076,15 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     sa.skel = r.skel;
     for (int exact_pass = 0; exact_pass < 2; ++exact_pass) {
       if (exact_pass == 1) {
-        k_mark_exact<<<(nbig + 127) / 128, 128, 0, s>>>(r, dctr + 3);
+        PKD_LAUNCH(k_mark_exact<<<(nbig + 127) / 128, 128, 0, s>>>(r, dctr + 3));
         PKD_CUDA(cudaMemcpyAsync(hctr + 3, dctr + 3, 4, cudaMemcpyDeviceToHost, s));
         PKD_CUDA(cudaStreamSynchronize(s));
         if (hctr[3] == 0) break;
-        k_copy_exact<<<tiles, 256, 0, s>>>(r);
+        PKD_LAUNCH(k_copy_exact<<<tiles, 256, 0, s>>>(r));
       }
       PKD_CUDA(cudaMemsetAsync(jctr, 0, 12, s));
       ja.next_big = bigA;
-      k_root_jobs<<<(nbig + 127) / 128, 128, 0, s>>>(r, ja, exact_pass);
+      PKD_LAUNCH(k_root_jobs<<<(nbig + 127) / 128, 128, 0, s>>>(r, ja, exact_pass));
       PKD_CUDA(cudaMemcpyAsync(hctr + 8, jctr, 12, cudaMemcpyDeviceToHost, s));
       PKD_CUDA(cudaStreamSynchronize(s));
       PKD_TRY(run_skeleton_jobs(ja, bigA, hctr[8], hctr[9], 0, sa, hctr + 8, jctr, bigA, bigB, d_nj,
@@ -1072,15 +1092,15 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     }
 
     // 3. finalize skeletons, count, scan, emit, scatter
-    k_finalize<<<(nbig + 127) / 128, 128, 0, s>>>(r);
+    PKD_LAUNCH(k_finalize<<<(nbig + 127) / 128, 128, 0, s>>>(r));
     PKD_DISPATCH_D(d, launch_count, r, tiles, s);
     uint32_t* partial;
     const uint64_t nh = (uint64_t)tiles * NB;
     PKD_TRY(sc.get(&partial, (nh + SCAN_TILE - 1) / SCAN_TILE + 1));
     device_excl_scan(r.hist, r.hscan, nh, partial, s);
-    k_emit<<<(nbig + 63) / 64, 64, 0, s>>>(r, dctr + 4);
+    PKD_LAUNCH(k_emit<<<(nbig + 63) / 64, 64, 0, s>>>(r, dctr + 4));
     PKD_DISPATCH_D(d, launch_scatter, r, tiles, pts_big, s);
-    k_copy_heavy<<<tiles, 256, 0, s>>>(r);
+    PKD_LAUNCH(k_copy_heavy<<<tiles, 256, 0, s>>>(r));
 
     // 4. the buckets, now in the destination buffer, are the next round
     cur = r.children;
@@ -1091,8 +1111,9 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
   }
 
   // 5. every small subproblem, one CTA each, in shared memory
-  PKD_CUDA(cudaMemcpyAsync(hctr + 12, d_nbase, 8, cudaMemcpyDeviceToHost, s));
+  PKD_CUDA(cudaMemcpyAsync(hctr + 12, d_nbase, 32, cudaMemcpyDeviceToHost, s));
   PKD_CUDA(cudaStreamSynchronize(s));
+  const uint64_t cta_pts = *(unsigned long long*)(hctr + 16), warp_pts = *(unsigned long long*)(hctr + 18);
   const uint32_t nbase = std::min<uint32_t>(hctr[12], (uint32_t)base_cap_segs);
   const uint32_t nwbase = std::min<uint32_t>(hctr[13], (uint32_t)base_cap_segs);
   if (nwbase > 0) {
@@ -1103,8 +1124,8 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     const size_t smb = warp_layout((int)wcap, d).per_warp * WK_WARPS;
     PKD_CUDA(cudaFuncSetAttribute(k_smem_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
     KTimer kt;
-    ktimer_begin(kt, "smem_warp", 0, s);
-    k_smem_warp<<<(nwbase + WK_WARPS - 1) / WK_WARPS, WK_WARPS * 32, smb, s>>>(wa);
+    ktimer_begin(kt, "smem_warp", warp_pts, s);
+    PKD_LAUNCH(k_smem_warp<<<(nwbase + WK_WARPS - 1) / WK_WARPS, WK_WARPS * 32, smb, s>>>(wa));
     ktimer_end(kt);
   }
   if (nbase > 0) {
@@ -1114,8 +1135,8 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     const size_t smb = smem_layout((int)cap, d).total;
     PKD_CUDA(cudaFuncSetAttribute(k_smem_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
     KTimer kt;
-    ktimer_begin(kt, "smem_build", 0, s);
-    k_smem_build<<<nbase, SM_THREADS, smb, s>>>(sa);
+    ktimer_begin(kt, "smem_build", cta_pts, s);
+    PKD_LAUNCH(k_smem_build<<<nbase, SM_THREADS, smb, s>>>(sa));
     ktimer_end(kt);
   }
   PKD_CUDA(cudaGetLastError());

@@ -46,6 +46,19 @@ struct TreeMem {
   DevStatus* st_host = nullptr;     // pinned mirror
 };
 
+// Every kernel launch of the library goes through PKD_LAUNCH, which counts
+// it (pkd_kernel_stats("launches", ...) reports the count).
+void count_launch();
+#define PKD_LAUNCH(...)        \
+  do {                         \
+    ::pkd::count_launch();     \
+    __VA_ARGS__;               \
+  } while (0)
+
+// Host-side tracing: with PKD_TRACE=1 in the environment, trace_mark()
+// synchronises the stream and prints the wall time since the previous mark.
+void trace_mark(cudaStream_t s, const char* what);
+
 // Error helpers.
 int cuda_err(cudaError_t e);
 #define PKD_CUDA(x)                          \
@@ -54,12 +67,17 @@ int cuda_err(cudaError_t e);
     if (_e != cudaSuccess) return cuda_err(_e); \
   } while (0)
 
-// Stream-ordered scratch allocation.
+// The library's stream-ordered memory pool on the current device.  Its
+// release threshold is unlimited: memory freed by one build stays mapped for
+// the next instead of being returned to the driver at every synchronisation.
+cudaMemPool_t mem_pool();
+
+// Stream-ordered allocation from that pool.
 template <class T>
 int dalloc(T** p, size_t n, cudaStream_t s) {
   *p = nullptr;
   if (n == 0) n = 1;
-  cudaError_t e = cudaMallocAsync((void**)p, n * sizeof(T), s);
+  cudaError_t e = cudaMallocFromPoolAsync((void**)p, n * sizeof(T), mem_pool(), s);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
     return PKD_ENOMEM;

@@ -198,8 +198,8 @@ static void launch_knn(const QueryArgs& a, cudaStream_t s) {
   const unsigned g = (unsigned)((a.nq + QTHREADS - 1) / QTHREADS);
   KTimer kt;
   ktimer_begin(kt, "knn", a.nq, s);
-  if (a.k <= 16) k_knn<D, 16><<<g, QTHREADS, 0, s>>>(a);
-  else k_knn<D, 128><<<g, QTHREADS, 0, s>>>(a);
+  if (a.k <= 16) PKD_LAUNCH(k_knn<D, 16><<<g, QTHREADS, 0, s>>>(a));
+  else PKD_LAUNCH(k_knn<D, 128><<<g, QTHREADS, 0, s>>>(a));
   ktimer_end(kt);
 }
 
@@ -208,7 +208,7 @@ static void launch_rc(const QueryArgs& a, cudaStream_t s) {
   const unsigned g = (unsigned)((a.nq + QTHREADS - 1) / QTHREADS);
   KTimer kt;
   ktimer_begin(kt, "range_count", a.nq, s);
-  k_range_count<D><<<g, QTHREADS, 0, s>>>(a);
+  PKD_LAUNCH(k_range_count<D><<<g, QTHREADS, 0, s>>>(a));
   ktimer_end(kt);
 }
 

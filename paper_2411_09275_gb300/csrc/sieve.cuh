@@ -113,9 +113,9 @@ static void device_excl_scan(const uint32_t* in, uint32_t* out, uint64_t n, uint
                              cudaStream_t s) {
   if (n == 0) return;
   const uint64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
-  k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, partial);
-  k_scan_single<<<1, 1024, 0, s>>>(partial, nb);
-  k_scan_apply<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, partial);
+  PKD_LAUNCH(k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, partial));
+  PKD_LAUNCH(k_scan_single<<<1, 1024, 0, s>>>(partial, nb));
+  PKD_LAUNCH(k_scan_apply<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, partial));
 }
 
 struct RoundArgs {
@@ -338,7 +338,7 @@ static void launch_count(const RoundArgs& r, uint32_t tiles, cudaStream_t s) {
   const size_t sm = (size_t)r.HN * 8 + (size_t)r.NB * 4;
   KTimer kt;
   ktimer_begin(kt, "count", 0, s);
-  k_count<D><<<tiles, SIEVE_THREADS, sm, s>>>(r);
+  PKD_LAUNCH(k_count<D><<<tiles, SIEVE_THREADS, sm, s>>>(r));
   ktimer_end(kt);
 }
 
@@ -352,7 +352,7 @@ static void launch_scatter(const RoundArgs& r, uint32_t tiles, uint64_t pts, cud
   }
   KTimer kt;
   ktimer_begin(kt, "scatter", pts, s);
-  k_scatter<D><<<tiles, SIEVE_THREADS, sm, s>>>(r);
+  PKD_LAUNCH(k_scatter<D><<<tiles, SIEVE_THREADS, sm, s>>>(r));
   ktimer_end(kt);
 }
 

@@ -4,7 +4,9 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -18,6 +20,28 @@ namespace pkd {
 Knobs& knobs() {
   static Knobs k;
   return k;
+}
+
+cudaMemPool_t mem_pool() {
+  static cudaMemPool_t pools[64] = {};
+  static std::mutex mu;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&pools[dev], &props) != cudaSuccess) {
+      cudaGetLastError();
+      cudaDeviceGetDefaultMemPool(&pools[dev], dev);
+    }
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  return pools[dev];
 }
 
 int cuda_err(cudaError_t e) {
@@ -63,6 +87,19 @@ void resolve_pending() {
 }  // namespace
 
 bool ktiming_enabled() { return g_timing; }
+
+void trace_mark(cudaStream_t s, const char* what) {
+  static const bool on = getenv("PKD_TRACE") && getenv("PKD_TRACE")[0] == '1';
+  if (!on) return;
+  static auto last = std::chrono::steady_clock::now();
+  cudaStreamSynchronize(s);
+  auto now = std::chrono::steady_clock::now();
+  fprintf(stderr, "[pkd] %-28s %9.3f ms\n", what, std::chrono::duration<double, std::milli>(now - last).count());
+  last = now;
+}
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void ktimer_begin(KTimer& k, const char* name, uint64_t items, cudaStream_t s) {
   k.on = g_timing;
@@ -133,7 +170,7 @@ int validate_coords(const int32_t* c, uint64_t cnt, cudaStream_t s, bool* ok) {
   cudaMemsetAsync(d, 0, 4, s);
   KTimer kt;
   ktimer_begin(kt, "validate", cnt, s);
-  k_validate<<<152 * 8, 256, 0, s>>>(c, cnt, d);
+  PKD_LAUNCH(k_validate<<<152 * 8, 256, 0, s>>>(c, cnt, d));
   ktimer_end(kt);
   cudaMemcpyAsync(&h, d, 4, cudaMemcpyDeviceToHost, s);
   cudaError_t e = cudaStreamSynchronize(s);
@@ -154,14 +191,10 @@ uint64_t shared_region_for(const Params& p, uint64_t n) {
 }
 
 void tree_release(TreeMem& t) {
-  cudaFree(t.A.c);
-  cudaFree(t.A.id);
-  cudaFree(t.nodes);
-  cudaFree(t.ndim);
-  cudaFree(t.shared_next);
-  cudaFree(t.dead);
-  cudaFree(t.aux);
-  cudaFree(t.st);
+  cudaStream_t s = 0;
+  for (void* p : {(void*)t.A.c, (void*)t.A.id, (void*)t.nodes, (void*)t.ndim, (void*)t.shared_next,
+                  (void*)t.dead, (void*)t.aux, (void*)t.st})
+    if (p) cudaFreeAsync(p, s);
   if (t.st_host) cudaFreeHost(t.st_host);
   t = TreeMem{};
 }
@@ -188,12 +221,13 @@ int tree_alloc(TreeMem& t, const Params& p, uint64_t cap, uint64_t shared_cap, c
   t.node_cap = shared_cap + 2 * t.cap;
   if (t.node_cap >= 0xFFFFFFF0ull) return PKD_EINVAL;
   cudaError_t e;
-  e = cudaMalloc((void**)&t.A.c, (size_t)p.d * t.cap * 4);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&t.A.id, (size_t)t.cap * 4);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&t.nodes, (size_t)t.node_cap * sizeof(Node));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&t.ndim, (size_t)t.node_cap);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&t.shared_next, 16);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&t.st, sizeof(DevStatus));
+  cudaMemPool_t pool = mem_pool();
+  e = cudaMallocFromPoolAsync((void**)&t.A.c, (size_t)p.d * t.cap * 4, pool, s);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&t.A.id, (size_t)t.cap * 4, pool, s);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&t.nodes, (size_t)t.node_cap * sizeof(Node), pool, s);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&t.ndim, (size_t)t.node_cap, pool, s);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&t.shared_next, 16, pool, s);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&t.st, sizeof(DevStatus), pool, s);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&t.st_host, sizeof(DevStatus));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -236,9 +270,11 @@ int pkd_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const pkd_
   Params p{params->d, params->phi, params->lambda, params->sigma_log2, params->sigma_os,
            params->count_mode, params->alpha_num, params->alpha_den, params->seed};
   bool ok;
+  trace_mark(s, "build: enter");
   e = validate_coords(coords, n * (uint64_t)p.d, s, &ok);
   if (e) return e;
   if (!ok) return PKD_EINVAL;
+  trace_mark(s, "build: validate");
   pkd_tree* t = new pkd_tree();
   const uint64_t cap = n + n / 4 + 4096;
   e = tree_alloc(t->m, p, cap, shared_region_for(p, cap), s);
@@ -255,7 +291,9 @@ int pkd_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const pkd_
   job.base = 0;
   job.extent = std::max<uint64_t>(n, 1);
   job.segs.push_back(Seg{0, (uint32_t)n, 0, 0, IN_INPUT});
+  trace_mark(s, "build: alloc tree");
   e = run_build(t->m, job, s);
+  trace_mark(s, "build: run_build");
   if (e == PKD_OK) e = check_status(t->m, s);
   if (e) {
     tree_release(t->m);
@@ -270,9 +308,11 @@ int pkd_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const pkd_
 
 void pkd_free(pkd_tree* t) {
   if (!t) return;
-  cudaDeviceSynchronize();
+  cudaDeviceSynchronize();  // no kernel of any stream may still use the tree
+  trace_mark(0, "free: enter");
   tree_release(t->m);
   delete t;
+  trace_mark(0, "free: release");
 }
 
 uint64_t pkd_size(const pkd_tree* t) { return t ? t->m.size : 0; }
@@ -363,6 +403,7 @@ int pkd_kernel_timing(int enable) {
   std::lock_guard<std::mutex> g(g_tmu);
   resolve_pending();
   g_stats.clear();
+  g_launches.store(0);
   g_timing = enable != 0;
   return PKD_OK;
 }
@@ -370,6 +411,12 @@ int pkd_kernel_timing(int enable) {
 int pkd_kernel_stats(const char* name, uint64_t* launches, double* total_ms, uint64_t* items) {
   if (!name) return PKD_EINVAL;
   std::lock_guard<std::mutex> g(g_tmu);
+  if (std::string(name) == "launches") {
+    if (launches) *launches = g_launches.load();
+    if (total_ms) *total_ms = 0;
+    if (items) *items = 0;
+    return PKD_OK;
+  }
   resolve_pending();
   auto it = g_stats.find(name);
   TimerStat s = it == g_stats.end() ? TimerStat{} : it->second;

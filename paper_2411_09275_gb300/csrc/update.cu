@@ -179,16 +179,18 @@ __global__ void k_route_emit(UpdArgs a) {
   }
 }
 
-// Copy the batch points of the leaf groups created this round into the
-// final batch buffer F (later rounds never write their ranges again).
-__global__ void k_copy_groups(const LeafGroup* g, uint32_t g0, const uint32_t* g1, Pts src, Pts F, int d) {
-  const uint32_t gi = g0 + blockIdx.x;
-  if (gi >= *g1) return;
-  const LeafGroup G = g[gi];
-  for (uint32_t i = threadIdx.x; i < G.len; i += blockDim.x) {
-    const uint64_t p = G.start + i;
-    for (int j = 0; j < d; ++j) F.c[(uint64_t)j * F.stride + p] = src.c[(uint64_t)j * src.stride + p];
-    F.id[p] = src.id[p];
+// Copy every point this round moved into the final batch buffer F.  Points
+// that go on to a deeper round are overwritten there later, so F ends with
+// every point at its final position (the points of a leaf group are never
+// moved again).  Same tiling as the sieve kernels: one block per tile.
+__global__ void k_copy_round(RoundArgs r, Pts F) {
+  SieveTile t;
+  if (!sieve_tile(r, t)) return;
+  const int d = r.p.d;
+  for (int i = threadIdx.x; i < t.cnt; i += blockDim.x) {
+    const uint64_t p = t.seg.start + t.first + (uint64_t)i;
+    for (int j = 0; j < d; ++j) F.c[(uint64_t)j * F.stride + p] = r.dst.c[(uint64_t)j * r.dst.stride + p];
+    F.id[p] = r.dst.id[p];
   }
 }
 
@@ -318,15 +320,42 @@ __global__ void k_decide(UpdArgs a) {
 __global__ void k_leaf_items(UpdArgs a, LeafGroup* groups, const uint32_t* ngroups, uint32_t* compact,
                              uint32_t* ncompact) {
   const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gi >= *ngroups) return;
-  const LeafGroup G = groups[gi];
-  if (G.flag) return;
-  const uint32_t old = a.nodes[G.slot].size;
-  if (a.insert) {
-    push_rebuild(a, G.slot, G.depth, old + G.len, old, G.start, G.start + G.len);
-  } else if (G.found) {
-    compact[atomicAdd(ncompact, 1u)] = gi;
+  const uint32_t ng = *ngroups;
+  bool push = false, comp = false;
+  RebuildItem it{};
+  if (gi < ng) {
+    const LeafGroup G = groups[gi];
+    if (!G.flag) {
+      const uint32_t old = a.nodes[G.slot].size;
+      if (a.insert) {
+        push = true;
+        it = RebuildItem{G.slot, G.depth, old + G.len, old, G.start, G.start + G.len, 0};
+      } else if (G.found) {
+        comp = true;
+      }
+    }
   }
+  // one counter update per warp
+  const unsigned mp = __ballot_sync(FULL_MASK, push), mc = __ballot_sync(FULL_MASK, comp);
+  const int lead = 0;
+  uint32_t bp = 0, bc = 0;
+  unsigned long long tot = push ? it.size : 0;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) tot += __shfl_xor_sync(FULL_MASK, tot, o);
+  if (lane_id() == lead) {
+    if (mp) {
+      bp = atomicAdd(a.nitems_out, (uint32_t)__popc(mp));
+      atomicAdd(a.items_total, tot);
+    }
+    if (mc) bc = atomicAdd(ncompact, (uint32_t)__popc(mc));
+  }
+  bp = __shfl_sync(FULL_MASK, bp, lead) + __popc(mp & lanemask_lt());
+  bc = __shfl_sync(FULL_MASK, bc, lead) + __popc(mc & lanemask_lt());
+  if (push) {
+    if (bp < a.items_cap) a.items_out[bp] = it;
+    else set_error(a.st, DERR_CAPACITY, 811);
+  }
+  if (comp) compact[bc] = gi;
 }
 
 __global__ void k_compact_leaves(const LeafGroup* groups, const uint32_t* list, const uint32_t* n,
@@ -474,16 +503,15 @@ static int ensure_capacity(TreeMem& t, uint64_t need, cudaStream_t s) {
   Pts A2{};
   Node* n2 = nullptr;
   uint8_t* d2 = nullptr;
-  cudaError_t e = cudaMalloc((void**)&A2.c, (size_t)t.p.d * ncap * 4);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&A2.id, (size_t)ncap * 4);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&n2, (size_t)nnode * sizeof(Node));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&d2, (size_t)nnode);
+  cudaMemPool_t pool = mem_pool();
+  cudaError_t e = cudaMallocFromPoolAsync((void**)&A2.c, (size_t)t.p.d * ncap * 4, pool, s);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&A2.id, (size_t)ncap * 4, pool, s);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&n2, (size_t)nnode * sizeof(Node), pool, s);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&d2, (size_t)nnode, pool, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(A2.c);
-    cudaFree(A2.id);
-    cudaFree(n2);
-    cudaFree(d2);
+    for (void* q : {(void*)A2.c, (void*)A2.id, (void*)n2, (void*)d2})
+      if (q) cudaFreeAsync(q, s);
     return PKD_ENOMEM;
   }
   A2.stride = ncap;
@@ -498,22 +526,17 @@ static int ensure_capacity(TreeMem& t, uint64_t need, cudaStream_t s) {
   uint8_t* dead2 = nullptr;
   uint32_t* aux2 = nullptr;
   if (t.dead) {
-    PKD_CUDA(cudaMalloc((void**)&dead2, ncap));
+    PKD_CUDA(cudaMallocFromPoolAsync((void**)&dead2, ncap, pool, s));
     PKD_CUDA(cudaMemsetAsync(dead2, 0, ncap, s));
     PKD_CUDA(cudaMemcpyAsync(dead2, t.dead, t.cap, cudaMemcpyDeviceToDevice, s));
   }
   if (t.aux) {
-    PKD_CUDA(cudaMalloc((void**)&aux2, nnode * 4));
+    PKD_CUDA(cudaMallocFromPoolAsync((void**)&aux2, nnode * 4, pool, s));
     PKD_CUDA(cudaMemsetAsync(aux2, 0, nnode * 4, s));
     PKD_CUDA(cudaMemcpyAsync(aux2, t.aux, t.node_cap * 4, cudaMemcpyDeviceToDevice, s));
   }
-  PKD_CUDA(cudaStreamSynchronize(s));
-  cudaFree(t.A.c);
-  cudaFree(t.A.id);
-  cudaFree(t.nodes);
-  cudaFree(t.ndim);
-  cudaFree(t.dead);
-  cudaFree(t.aux);
+  for (void* q : {(void*)t.A.c, (void*)t.A.id, (void*)t.nodes, (void*)t.ndim, (void*)t.dead, (void*)t.aux})
+    if (q) cudaFreeAsync(q, s);
   t.dead = dead2;
   t.aux = aux2;
   t.A = A2;
@@ -526,11 +549,11 @@ static int ensure_capacity(TreeMem& t, uint64_t need, cudaStream_t s) {
 
 static int ensure_delete_scratch(TreeMem& t, cudaStream_t s) {
   if (!t.dead) {
-    PKD_CUDA(cudaMalloc((void**)&t.dead, t.cap));
+    PKD_CUDA(cudaMallocFromPoolAsync((void**)&t.dead, t.cap, mem_pool(), s));
     PKD_CUDA(cudaMemsetAsync(t.dead, 0, t.cap, s));
   }
   if (!t.aux) {
-    PKD_CUDA(cudaMalloc((void**)&t.aux, t.node_cap * 4));
+    PKD_CUDA(cudaMallocFromPoolAsync((void**)&t.aux, t.node_cap * 4, mem_pool(), s));
     PKD_CUDA(cudaMemsetAsync(t.aux, 0, t.node_cap * 4, s));
   }
   return PKD_OK;
@@ -555,7 +578,9 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
   const int d = p.d, lam = p.lambda, NB = 1 << lam, HN = 2 << lam;
   const int TILE = std::min(std::max(knobs().tile, 256), 4096);
   Scratch sc{s, {}};
+  trace_mark(s, insert ? "insert: enter" : "delete: enter");
   if (!insert) PKD_TRY(ensure_delete_scratch(t, s));
+  trace_mark(s, "upd: delete scratch");
 
   // batch buffers: W0/W1 ping-pong for the sieve, F final positions
   int32_t *wc[3];
@@ -566,7 +591,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
   }
   Pts W[2] = {Pts{wc[0], wid[0], m}, Pts{wc[1], wid[1], m}};
   Pts F{wc[2], wid[2], m};
-  k_stage<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(coords, ids, m, d, W[0]);
+  PKD_LAUNCH(k_stage<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(coords, ids, m, d, W[0]));
 
   uint32_t* dctr;
   PKD_TRY(sc.get(&dctr, 32));
@@ -662,8 +687,8 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
     ua.next = next;
     ua.next_ctr = dctr;
     const unsigned g1 = (ncur + 127) / 128;
-    k_fetch<<<g1, 128, 0, s>>>(ua);
-    k_big_prefix<<<1, 1024, 0, s>>>(cur, R.d_n, (uint32_t)TILE, tile0, excl);
+    PKD_LAUNCH(k_fetch<<<g1, 128, 0, s>>>(ua));
+    PKD_LAUNCH(k_big_prefix<<<1, 1024, 0, s>>>(cur, R.d_n, (uint32_t)TILE, tile0, excl));
 
     RoundArgs ra{};
     ra.p = p;
@@ -684,13 +709,12 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
     ra.st = t.st;
     PKD_DISPATCH_D(d, launch_count, ra, tiles, s);
     device_excl_scan(hist, hscan, nh, partial, s);
-    k_route_emit<<<g1, 128, 0, s>>>(ua);
+    PKD_LAUNCH(k_route_emit<<<g1, 128, 0, s>>>(ua));
     PKD_DISPATCH_D(d, launch_scatter, ra, tiles, (uint64_t)0, s);
     PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 24, cudaMemcpyDeviceToHost, s));
     PKD_CUDA(cudaStreamSynchronize(s));
     const uint32_t nnext = hctr[0], ntiles = hctr[1], ngroups = hctr[4];
-    if (ngroups > groups_before)
-      k_copy_groups<<<ngroups - groups_before, 128, 0, s>>>(groups, groups_before, d_ngroups, W[w ^ 1], F, d);
+    PKD_LAUNCH(k_copy_round<<<tiles, 256, 0, s>>>(ra, F));
     groups_before = ngroups;
     rounds.push_back(R);
     cur = next;
@@ -699,10 +723,11 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
     w ^= 1;
   }
   const uint32_t ngroups = groups_before;
+  trace_mark(s, "upd: route");
 
   // ---- match (delete) ----
   if (!insert && ngroups)
-    k_match<<<(ngroups + 7) / 8, 256, 0, s>>>(groups, d_ngroups, t.nodes, t.A, F, d, t.dead, t.aux);
+    PKD_LAUNCH(k_match<<<(ngroups + 7) / 8, 256, 0, s>>>(groups, d_ngroups, t.nodes, t.A, F, d, t.dead, t.aux));
 
   // ---- count, bottom-up ----
   for (int r = (int)rounds.size() - 1; r >= 0; --r) {
@@ -715,7 +740,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
     ua.fnd = R.fnd;
     ua.next_fnd = (r + 1 < (int)rounds.size()) ? rounds[r + 1].fnd : nullptr;
     ua.next_HN = HN;
-    k_aggregate<<<(R.n + 127) / 128, 128, 0, s>>>(ua);
+    PKD_LAUNCH(k_aggregate<<<(R.n + 127) / 128, 128, 0, s>>>(ua));
   }
   uint32_t total_changed = 0;
   PKD_CUDA(cudaMemcpyAsync(&total_changed, rounds[0].fnd + 1, 4, cudaMemcpyDeviceToHost, s));
@@ -733,11 +758,12 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
     ua.blen = R.blen;
     ua.iflag = R.iflag;
     ua.next_iflag = (r + 1 < rounds.size()) ? rounds[r + 1].iflag : nullptr;
-    k_decide<<<(R.n + 127) / 128, 128, 0, s>>>(ua);
+    PKD_LAUNCH(k_decide<<<(R.n + 127) / 128, 128, 0, s>>>(ua));
   }
+  trace_mark(s, "upd: match+count+decide");
   uint32_t* compact;
   PKD_TRY(sc.get(&compact, std::max<uint32_t>(ngroups, 1)));
-  if (ngroups) k_leaf_items<<<(ngroups + 127) / 128, 128, 0, s>>>(ua, groups, d_ngroups, compact, d_ncompact);
+  if (ngroups) PKD_LAUNCH(k_leaf_items<<<(ngroups + 127) / 128, 128, 0, s>>>(ua, groups, d_ngroups, compact, d_ncompact));
   PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 40, cudaMemcpyDeviceToHost, s));
   PKD_CUDA(cudaStreamSynchronize(s));
   const uint32_t nitems = hctr[5];
@@ -746,11 +772,13 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
 
   // ---- delete: compact the reached leaves in place ----
   if (ncompact)
-    k_compact_leaves<<<(ncompact + 7) / 8, 256, 0, s>>>(groups, compact, d_ncompact, t.nodes, t.A, d, t.dead);
+    PKD_LAUNCH(k_compact_leaves<<<(ncompact + 7) / 8, 256, 0, s>>>(groups, compact, d_ncompact, t.nodes, t.A, d, t.dead));
 
   // ---- rebuild ----
+  trace_mark(s, "upd: leaf items + compact");
   if (nitems) {
     PKD_TRY(ensure_capacity(t, total, s));
+    trace_mark(s, "upd: ensure capacity");
     uint32_t *isz, *ioff, *ipart;
     PKD_TRY(sc.get(&isz, nitems));
     PKD_TRY(sc.get(&ioff, nitems));
@@ -758,9 +786,9 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
     Seg* segs;
     PKD_TRY(sc.get(&segs, nitems));
     const unsigned gi = (nitems + 127) / 128;
-    k_item_sizes<<<gi, 128, 0, s>>>(items_out, d_nitems, isz);
+    PKD_LAUNCH(k_item_sizes<<<gi, 128, 0, s>>>(items_out, d_nitems, isz));
     device_excl_scan(isz, ioff, nitems, ipart, s);
-    k_item_pos<<<gi, 128, 0, s>>>(items_out, d_nitems, ioff, t.top, segs);
+    PKD_LAUNCH(k_item_pos<<<gi, 128, 0, s>>>(items_out, d_nitems, ioff, t.top, segs));
     // flatten the old subtrees breadth first
     uint64_t old_total = 0;
     {
@@ -772,7 +800,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
       PKD_TRY(sc.get(&leaves, std::min<uint64_t>(fcap, 0xFFFFFFF0ull)));
       uint32_t* fc = dctr + 12;  // [0] cur, [1] next, [2] leaves
       PKD_CUDA(cudaMemsetAsync(fc, 0, 12, s));
-      k_front_init<<<gi, 128, 0, s>>>(items_out, d_nitems, fa, fc);
+      PKD_LAUNCH(k_front_init<<<gi, 128, 0, s>>>(items_out, d_nitems, fa, fc));
       PKD_CUDA(cudaMemcpyAsync(hctr + 12, fc, 12, cudaMemcpyDeviceToHost, s));
       PKD_CUDA(cudaStreamSynchronize(s));
       uint32_t nf = hctr[12];
@@ -780,8 +808,8 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
       for (int it = 0; nf > 0; ++it) {
         if (it > 100000) return PKD_EINTERNAL;
         PKD_CUDA(cudaMemsetAsync(fc + 1, 0, 4, s));
-        k_front_expand<<<(nf + 127) / 128, 128, 0, s>>>(fa, fc, fb, fc + 1, leaves, fc + 2, t.nodes, t.ndim,
-                                                        t.aux, insert ? 0 : 1, fcap32, t.st);
+        PKD_LAUNCH(k_front_expand<<<(nf + 127) / 128, 128, 0, s>>>(fa, fc, fb, fc + 1, leaves, fc + 2, t.nodes, t.ndim,
+                                                        t.aux, insert ? 0 : 1, fcap32, t.st));
         PKD_CUDA(cudaMemcpyAsync(fc, fc + 1, 4, cudaMemcpyDeviceToDevice, s));
         PKD_CUDA(cudaMemcpyAsync(hctr + 12, fc, 12, cudaMemcpyDeviceToHost, s));
         PKD_CUDA(cudaStreamSynchronize(s));
@@ -790,17 +818,19 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
       }
       const uint32_t nleaves = hctr[14];
       if (nleaves)
-        k_copy_leaves<<<(nleaves + 7) / 8, 256, 0, s>>>(leaves, fc + 2, items_out, t.nodes, t.A, d, t.dead,
-                                                        insert ? 0 : 1);
+        PKD_LAUNCH(k_copy_leaves<<<(nleaves + 7) / 8, 256, 0, s>>>(leaves, fc + 2, items_out, t.nodes, t.A, d, t.dead,
+                                                        insert ? 0 : 1));
       (void)old_total;
     }
-    if (insert) k_copy_new<<<(nitems + 7) / 8, 256, 0, s>>>(items_out, d_nitems, F, t.A, d);
+    if (insert) PKD_LAUNCH(k_copy_new<<<(nitems + 7) / 8, 256, 0, s>>>(items_out, d_nitems, F, t.A, d));
+    trace_mark(s, "upd: flatten + gather");
     BuildJob job;
     job.base = t.top;
     job.extent = std::max<uint64_t>(total, 1);
     job.dsegs = segs;
     job.dsegs_n = nitems;
     PKD_TRY(run_build(t, job, s));
+    trace_mark(s, "upd: rebuild");
     t.top += total;
   }
 
@@ -808,10 +838,11 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
   if (!insert) {
     PKD_CUDA(cudaMemsetAsync(t.dead, 0, t.cap, s));
     for (auto& R : rounds)
-      k_clear_aux<<<(unsigned)(((uint64_t)R.n * HN + 255) / 256), 256, 0, s>>>(R.slots, (uint64_t)R.n * HN, t.aux);
+      PKD_LAUNCH(k_clear_aux<<<(unsigned)(((uint64_t)R.n * HN + 255) / 256), 256, 0, s>>>(R.slots, (uint64_t)R.n * HN, t.aux));
     // (a leaf group's slot is a heap bucket of its round, cleared above)
   }
   PKD_CUDA(cudaStreamSynchronize(s));
+  trace_mark(s, "upd: cleanup");
   if (n_changed) *n_changed = total_changed;
   return PKD_OK;
 }

@@ -43,11 +43,8 @@ struct SmemPtrs {
   uint16_t* perm0;
   uint16_t* perm1;
   uint8_t* flag;
-  unsigned* bhist;
-  int* bred;
   unsigned* whist;
-  Task* bstack;
-  Task* wlist;
+  int* wred;
   Task* wstack;
   SmemCtl* ctl;
 };
@@ -60,40 +57,72 @@ __device__ SmemPtrs carve(uint8_t* sm, int cap, int d) {
   q.perm0 = (uint16_t*)(sm + Lo.perm0);
   q.perm1 = (uint16_t*)(sm + Lo.perm1);
   q.flag = (uint8_t*)(sm + Lo.flag);
-  q.bhist = (unsigned*)(sm + Lo.bhist);
-  q.bred = (int*)(sm + Lo.bred);
   q.whist = (unsigned*)(sm + Lo.whist);
-  q.bstack = (Task*)(sm + Lo.bstack);
-  q.wlist = (Task*)(sm + Lo.wlist);
+  q.wred = (int*)(sm + Lo.wred);
   q.wstack = (Task*)(sm + Lo.wstack);
   q.ctl = (SmemCtl*)(sm + Lo.ctl);
   return q;
 }
 
+template <int D>
+__device__ SmemCtx<D> make_ctx(const SmemArgs& a, const SmemPtrs& q, int cap) {
+  SmemCtx<D> cx;
+  cx.p = a.p;
+  cx.s = SmemPts<D>{q.X, q.ID, q.flag, cap};
+  cx.flag = q.flag;
+  cx.perm[0] = q.perm0;
+  cx.perm[1] = q.perm1;
+  cx.ctl = q.ctl;
+  cx.out = a.A;
+  cx.start = 0;
+  cx.slot_base = 0;
+  cx.slot_limit = 0;
+  cx.nodes = a.nodes;
+  cx.ndim = a.ndim;
+  cx.skel = nullptr;
+  cx.lam = 0;
+  cx.min_split = 0;
+  cx.st = a.st;
+  return cx;
+}
+
+// Load the points of a segment into shared memory (coordinates per
+// dimension, ids) and set the identity index list.
+template <int D>
+__device__ void load_segment(const SmemArgs& a, const Seg& seg, int32_t* X, uint32_t* ID, uint16_t* perm,
+                             int cap, int rank, int stride) {
+  const int n = (int)seg.len;
+  for (int i = rank; i < n; i += stride) {
+    const uint64_t g = seg.start + (uint64_t)i;
+    if (seg.where == IN_INPUT) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) X[j * cap + i] = a.in_coords[g * (uint64_t)D + j];
+      ID[i] = a.in_ids ? a.in_ids[g] : (uint32_t)g;
+    } else {
+      const Pts& S = seg.where == IN_A ? a.A : a.B;
+#pragma unroll
+      for (int j = 0; j < D; ++j) X[j * cap + i] = S.c[(uint64_t)j * S.stride + g];
+      ID[i] = S.id[g];
+    }
+    perm[i] = (uint16_t)i;
+  }
+}
+
+template <int D>
 __global__ void __launch_bounds__(SM_THREADS) k_smem_build(SmemArgs a) {
   if (blockIdx.x >= *a.nsegs) return;
   extern __shared__ __align__(16) uint8_t sm[];
   const Seg seg = a.segs[blockIdx.x];
-  const int d = a.p.d, cap = a.cap, tid = threadIdx.x;
-  SmemPtrs q = carve(sm, cap, d);
+  const int cap = a.cap, tid = threadIdx.x;
+  SmemPtrs q = carve(sm, cap, D);
   if (seg.len > (uint32_t)cap) {
     if (tid == 0) set_error(a.st, DERR_CAPACITY, (int)blockIdx.x);
     return;
   }
   const int n = (int)seg.len;
-  for (int i = tid; i < n; i += SM_THREADS) {
-    const uint64_t g = seg.start + (uint64_t)i;
-    if (seg.where == IN_INPUT) {
-      for (int j = 0; j < d; ++j) q.X[j * cap + i] = a.in_coords[g * (uint64_t)d + j];
-      q.ID[i] = a.in_ids ? a.in_ids[g] : (uint32_t)g;
-    } else {
-      const Pts& S = seg.where == IN_A ? a.A : a.B;
-      for (int j = 0; j < d; ++j) q.X[j * cap + i] = S.c[(uint64_t)j * S.stride + g];
-      q.ID[i] = S.id[g];
-    }
-    q.perm0[i] = (uint16_t)i;
-  }
+  load_segment<D>(a, seg, q.X, q.ID, q.perm0, cap, tid, SM_THREADS);
   if (tid == 0) q.ctl->next_slot = 0;
+  if (tid < SM_NW) q.ctl->wsp[tid] = 0;
   __syncthreads();
   if (n == 0) {
     if (tid == 0) {
@@ -102,33 +131,21 @@ __global__ void __launch_bounds__(SM_THREADS) k_smem_build(SmemArgs a) {
     }
     return;
   }
-  SmemCtx cx;
-  cx.p = a.p;
-  cx.s = SmemPts{q.X, q.ID, q.flag, cap, d};
-  cx.flag = q.flag;
-  cx.perm[0] = q.perm0;
-  cx.perm[1] = q.perm1;
-  cx.ctl = q.ctl;
-  cx.out = a.A;
+  SmemCtx<D> cx = make_ctx<D>(a, q, cap);
   cx.start = seg.start;
   cx.slot_base = (uint32_t)(a.shared_cap + 2 * seg.start);
   cx.slot_limit = 2 * n;
-  cx.nodes = a.nodes;
-  cx.ndim = a.ndim;
-  cx.skel = nullptr;
-  cx.lam = 0;
-  cx.min_split = 0;
-  cx.st = a.st;
   Task root{0, (uint16_t)n, 0, 0, 0, seg.depth, seg.root};
-  run_tasks<false>(cx, root, q.bstack, q.wlist, q.wstack, q.bhist, q.bred, q.whist);
+  run_team_tasks<false, D>(cx, root, q.whist, q.wred, q.wstack, SM_NW);
 }
 
+template <int D>
 __global__ void __launch_bounds__(SM_THREADS) k_smem_skel(SmemArgs a) {
   if (blockIdx.x >= *a.njobs) return;
   extern __shared__ __align__(16) uint8_t sm[];
   const SkelJob jb = a.jobs[blockIdx.x];
-  const int d = a.p.d, cap = a.cap, tid = threadIdx.x;
-  SmemPtrs q = carve(sm, cap, d);
+  const int cap = a.cap, tid = threadIdx.x;
+  SmemPtrs q = carve(sm, cap, D);
   if (jb.n > (uint32_t)cap) {
     if (tid == 0) set_error(a.st, DERR_CAPACITY, 200000 + (int)blockIdx.x);
     return;
@@ -136,25 +153,20 @@ __global__ void __launch_bounds__(SM_THREADS) k_smem_skel(SmemArgs a) {
   const int n = (int)jb.n;
   const int32_t* S = a.sbuf[jb.buf];
   for (int i = tid; i < n; i += SM_THREADS) {
-    for (int j = 0; j < d; ++j) q.X[j * cap + i] = S[(uint64_t)j * a.sstride + jb.a + i];
+#pragma unroll
+    for (int j = 0; j < D; ++j) q.X[j * cap + i] = S[(uint64_t)j * a.sstride + jb.a + i];
     q.ID[i] = 0;
     q.flag[i] = 0;
     q.perm0[i] = (uint16_t)i;
   }
+  if (tid < SM_NW) q.ctl->wsp[tid] = 0;
   __syncthreads();
-  SmemCtx cx;
-  cx.p = a.p;
-  cx.s = SmemPts{q.X, q.ID, q.flag, cap, d};
-  cx.flag = q.flag;
-  cx.perm[0] = q.perm0;
-  cx.perm[1] = q.perm1;
-  cx.ctl = q.ctl;
+  SmemCtx<D> cx = make_ctx<D>(a, q, cap);
   cx.skel = a.skel + (uint64_t)jb.seg * a.heap_n;
   cx.lam = jb.lam;
   cx.min_split = (int)jb.min_split;
-  cx.st = a.st;
   Task root{0, (uint16_t)n, 0, 0, jb.j, 0, jb.h};
-  run_tasks<true>(cx, root, q.bstack, q.wlist, q.wstack, q.bhist, q.bred, q.whist);
+  run_team_tasks<true, D>(cx, root, q.whist, q.wred, q.wstack, SM_NW);
 }
 
 // One warp per small subproblem (a leaf rebuilt with a few new points, or a
@@ -190,40 +202,32 @@ __host__ __device__ inline WarpLayout warp_layout(int wcap, int d) {
 
 int warp_cap_for(int d) { return d <= 4 ? 512 : 256; }
 
+template <int D>
 __global__ void __launch_bounds__(WK_WARPS * 32) k_smem_warp(SmemArgs a) {
   const uint32_t sid = blockIdx.x * WK_WARPS + warp_id();
   if (sid >= *a.nsegs) return;  // warp-uniform
   extern __shared__ __align__(16) uint8_t sm[];
-  const int d = a.p.d, cap = a.cap, lane = lane_id();
-  const WarpLayout Lo = warp_layout(cap, d);
+  const int cap = a.cap, lane = lane_id();
+  const WarpLayout Lo = warp_layout(cap, D);
   uint8_t* base = sm + (size_t)warp_id() * Lo.per_warp;
-  int32_t* X = (int32_t*)(base + Lo.X);
-  uint32_t* ID = (uint32_t*)(base + Lo.ID);
-  uint16_t* perm0 = (uint16_t*)(base + Lo.perm0);
-  uint16_t* perm1 = (uint16_t*)(base + Lo.perm1);
-  uint8_t* flag = base + Lo.flag;
-  unsigned* hist = (unsigned*)(base + Lo.hist);
-  Task* stack = (Task*)(base + Lo.stack);
-  SmemCtl* ctl = (SmemCtl*)(base + Lo.ctl);
+  SmemPtrs q;
+  q.X = (int32_t*)(base + Lo.X);
+  q.ID = (uint32_t*)(base + Lo.ID);
+  q.perm0 = (uint16_t*)(base + Lo.perm0);
+  q.perm1 = (uint16_t*)(base + Lo.perm1);
+  q.flag = base + Lo.flag;
+  q.whist = (unsigned*)(base + Lo.hist);
+  q.wred = nullptr;
+  q.wstack = (Task*)(base + Lo.stack);
+  q.ctl = (SmemCtl*)(base + Lo.ctl);
   const Seg seg = a.segs[sid];
   if (seg.len > (uint32_t)cap) {
     if (lane == 0) set_error(a.st, DERR_CAPACITY, 250000);
     return;
   }
   const int n = (int)seg.len;
-  for (int i = lane; i < n; i += 32) {
-    const uint64_t g = seg.start + (uint64_t)i;
-    if (seg.where == IN_INPUT) {
-      for (int j = 0; j < d; ++j) X[j * cap + i] = a.in_coords[g * (uint64_t)d + j];
-      ID[i] = a.in_ids ? a.in_ids[g] : (uint32_t)g;
-    } else {
-      const Pts& S = seg.where == IN_A ? a.A : a.B;
-      for (int j = 0; j < d; ++j) X[j * cap + i] = S.c[(uint64_t)j * S.stride + g];
-      ID[i] = S.id[g];
-    }
-    perm0[i] = (uint16_t)i;
-  }
-  if (lane == 0) ctl->next_slot = 0;
+  load_segment<D>(a, seg, q.X, q.ID, q.perm0, cap, lane, 32);
+  if (lane == 0) q.ctl->next_slot = 0;
   __syncwarp();
   if (n == 0) {
     if (lane == 0) {
@@ -232,25 +236,42 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_smem_warp(SmemArgs a) {
     }
     return;
   }
-  SmemCtx cx;
-  cx.p = a.p;
-  cx.s = SmemPts{X, ID, flag, cap, d};
-  cx.flag = flag;
-  cx.perm[0] = perm0;
-  cx.perm[1] = perm1;
-  cx.ctl = ctl;
-  cx.out = a.A;
+  SmemCtx<D> cx = make_ctx<D>(a, q, cap);
   cx.start = seg.start;
   cx.slot_base = (uint32_t)(a.shared_cap + 2 * seg.start);
   cx.slot_limit = 2 * n;
-  cx.nodes = a.nodes;
-  cx.ndim = a.ndim;
-  cx.skel = nullptr;
-  cx.lam = 0;
-  cx.min_split = 0;
-  cx.st = a.st;
-  WarpTeam wt{hist, nullptr};
-  warp_run<false>(wt, cx, Task{0, (uint16_t)n, 0, 0, 0, seg.depth, seg.root}, stack);
+  const Team wt{warp_id(), 1, 0, q.whist, nullptr};
+  warp_run<false, D>(wt, cx, Task{0, (uint16_t)n, 0, 0, 0, seg.depth, seg.root}, q.wstack, 0);
+}
+
+template <int D>
+static void launch_smem_build(const SmemArgs& a, uint32_t nblocks, size_t smb, cudaStream_t s) {
+  static int set = 0;
+  if (set < (int)smb) {
+    cudaFuncSetAttribute(k_smem_build<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+    set = (int)smb;
+  }
+  PKD_LAUNCH(k_smem_build<D><<<nblocks, SM_THREADS, smb, s>>>(a));
+}
+
+template <int D>
+static void launch_smem_skel(const SmemArgs& a, uint32_t nblocks, size_t smb, cudaStream_t s) {
+  static int set = 0;
+  if (set < (int)smb) {
+    cudaFuncSetAttribute(k_smem_skel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+    set = (int)smb;
+  }
+  PKD_LAUNCH(k_smem_skel<D><<<nblocks, SM_THREADS, smb, s>>>(a));
+}
+
+template <int D>
+static void launch_smem_warp(const SmemArgs& a, uint32_t nblocks, size_t smb, cudaStream_t s) {
+  static int set = 0;
+  if (set < (int)smb) {
+    cudaFuncSetAttribute(k_smem_warp<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+    set = (int)smb;
+  }
+  PKD_LAUNCH(k_smem_warp<D><<<nblocks, WK_WARPS * 32, smb, s>>>(a));
 }
 
 // ---------------------------------------------------------------------------
@@ -460,7 +481,7 @@ __global__ void k_job_choose(JobArgs a) {
   const SkelJob jb = a.jobs[i];
   JobState& s = a.js[i];
   int dim = -1;
-  if (jb.j < jb.lam && jb.n >= jb.min_split) dim = widest_dim(s.mn, s.mx, a.d);
+  if (jb.j < jb.lam && jb.n >= jb.min_split) dim = widest_dim_rt(s.mn, s.mx, a.d);
   s.split = dim >= 0;
   s.dim = dim < 0 ? 0 : dim;
   s.k = (int)(jb.n / 2);
@@ -903,8 +924,7 @@ static int run_skeleton_jobs(JobArgs ja, SkelJob* big0, uint32_t nbig_jobs, uint
     const int d = sa.p.d;
     sa.cap = skel_cap_for(d);
     const size_t smb = smem_layout(sa.cap, d).total;
-    cudaFuncSetAttribute(k_smem_skel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
-    PKD_LAUNCH(k_smem_skel<<<nsmall, SM_THREADS, smb, s>>>(sa));
+    PKD_DISPATCH_D(d, launch_smem_skel, sa, nsmall, smb, s);
   }
   return PKD_OK;
 }
@@ -1122,10 +1142,9 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     wa.nsegs = d_nbase + 1;
     wa.cap = (int)wcap;
     const size_t smb = warp_layout((int)wcap, d).per_warp * WK_WARPS;
-    PKD_CUDA(cudaFuncSetAttribute(k_smem_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
     KTimer kt;
     ktimer_begin(kt, "smem_warp", warp_pts, s);
-    PKD_LAUNCH(k_smem_warp<<<(nwbase + WK_WARPS - 1) / WK_WARPS, WK_WARPS * 32, smb, s>>>(wa));
+    PKD_DISPATCH_D(d, launch_smem_warp, wa, (nwbase + WK_WARPS - 1) / WK_WARPS, smb, s);
     ktimer_end(kt);
   }
   if (nbase > 0) {
@@ -1133,10 +1152,9 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     sa.nsegs = d_nbase;
     sa.cap = (int)cap;
     const size_t smb = smem_layout((int)cap, d).total;
-    PKD_CUDA(cudaFuncSetAttribute(k_smem_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
     KTimer kt;
     ktimer_begin(kt, "smem_build", cta_pts, s);
-    PKD_LAUNCH(k_smem_build<<<nbase, SM_THREADS, smb, s>>>(sa));
+    PKD_DISPATCH_D(d, launch_smem_build, sa, nbase, smb, s);
     ktimer_end(kt);
   }
   PKD_CUDA(cudaGetLastError());

@@ -11,10 +11,12 @@
 // sieve over the finished skeleton would (shared-memory traffic is cheap, so
 // the sieve's one-pass data movement buys nothing here).
 //
-// Scheduling: tasks larger than WMAX points are processed by the whole block
-// (a depth-first stack that always continues with the smaller child, so it
-// stays within log2(cap) entries); smaller tasks go to single warps, which
-// finish them depth first with the same stack discipline.
+// Scheduling: the root task is processed by all 16 warps of the CTA; at
+// every split the team halves and each half takes one child (a child much
+// smaller than its sibling is deferred to the stack of the team's first warp
+// instead), down to single warps, which finish their subtrees depth first
+// with a stack that always continues with the smaller child (so it stays
+// within log2(cap) entries).  Teams synchronise on their own named barrier.
 #pragma once
 
 #include "team.cuh"
@@ -23,10 +25,8 @@ namespace pkd {
 
 constexpr int SM_NW = 16;
 constexpr int SM_THREADS = SM_NW * 32;
-constexpr int WMAX = 512;
-constexpr int BSTK = 40;
-constexpr int WSTK = 24;
-constexpr int WLIST = 256;
+constexpr int WSTK = 32;
+constexpr int DEFER_MAX = 96;  // children this small are deferred instead of splitting a team
 
 struct Task {
   uint16_t lo, hi, ns;
@@ -38,9 +38,7 @@ static_assert(sizeof(Task) == 16, "Task layout");
 
 struct SmemCtl {
   int next_slot;
-  int bsp;
-  int wl_n;
-  int err;
+  int wsp[SM_NW];  // per-warp stack depth
 };
 
 // A skeleton node whose sample is still to be split: the node at heap index
@@ -89,12 +87,13 @@ struct SmemArgs {
 };
 
 struct SmemLayout {
-  size_t X, ID, perm0, perm1, flag, bhist, bred, whist, bstack, wlist, wstack, ctl, total;
+  size_t X, ID, perm0, perm1, flag, whist, wred, wstack, ctl, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline SmemLayout smem_layout(int cap, int d) {
+// Shared memory of one CTA with `warps` warps holding up to `cap` points.
+__host__ __device__ inline SmemLayout smem_layout(int cap, int d, int warps = SM_NW) {
   SmemLayout L;
   size_t o = 0;
   L.X = o;
@@ -107,27 +106,22 @@ __host__ __device__ inline SmemLayout smem_layout(int cap, int d) {
   o = align_up(o + (size_t)2 * cap, 16);
   L.flag = o;
   o = align_up(o + (size_t)cap, 16);
-  L.bhist = o;
-  o = align_up(o + 256 * 4, 16);
-  L.bred = o;
-  o = align_up(o + RED_INTS * 4, 16);
   L.whist = o;
-  o = align_up(o + (size_t)SM_NW * 256 * 4, 16);
-  L.bstack = o;
-  o = align_up(o + BSTK * sizeof(Task), 16);
-  L.wlist = o;
-  o = align_up(o + WLIST * sizeof(Task), 16);
+  o = align_up(o + (size_t)warps * 256 * 4, 16);
+  L.wred = o;
+  o = align_up(o + (size_t)warps * RED_INTS * 4, 16);
   L.wstack = o;
-  o = align_up(o + (size_t)SM_NW * WSTK * sizeof(Task), 16);
+  o = align_up(o + (size_t)warps * WSTK * sizeof(Task), 16);
   L.ctl = o;
   o = align_up(o + sizeof(SmemCtl), 16);
   L.total = o;
   return L;
 }
 
+template <int D>
 struct SmemCtx {
   Params p;
-  SmemPts s;
+  SmemPts<D> s;
   uint8_t* flag;
   uint16_t* perm[2];
   SmemCtl* ctl;
@@ -149,13 +143,14 @@ struct SmemCtx {
 // Build mode
 // ---------------------------------------------------------------------------
 
-template <class T>
-__device__ void emit_leaf(const T& tm, const SmemCtx& cx, const Task& tk) {
+template <int D>
+__device__ void emit_leaf(const Team& tm, const SmemCtx<D>& cx, const Task& tk) {
   const uint16_t* P = cx.perm[tk.buf];
   for (int i = tk.lo + tm.rank(); i < tk.hi; i += tm.size()) {
-    int p = P[i];
-    uint64_t g = cx.start + (uint64_t)i;
-    for (int j = 0; j < cx.s.d; ++j) cx.out.c[(uint64_t)j * cx.out.stride + g] = cx.s.x(j, p);
+    const int p = P[i];
+    const uint64_t g = cx.start + (uint64_t)i;
+#pragma unroll
+    for (int j = 0; j < D; ++j) cx.out.c[(uint64_t)j * cx.out.stride + g] = cx.s.x(j, p);
     cx.out.id[g] = cx.s.ID[p];
   }
   if (tm.leader()) {
@@ -170,17 +165,9 @@ __device__ void emit_leaf(const T& tm, const SmemCtx& cx, const Task& tk) {
   }
 }
 
-template <class T>
-__device__ int alloc_two(const T& tm, const SmemCtx& cx) {
-  int b = 0;
-  if (tm.leader()) b = atomicAdd(&cx.ctl->next_slot, 2);
-  b = tm.bcast(b);
-  return b;
-}
-
 // Process one node; returns the number of children written to ch (0 or 2).
-template <class T>
-__device__ int process_build(const T& tm, const SmemCtx& cx, Task tk, Task* ch) {
+template <int D>
+__device__ int process_build(const Team& tm, const SmemCtx<D>& cx, Task tk, Task* ch) {
   for (;;) {
     const int lo = tk.lo, hi = tk.hi, n = hi - lo;
     uint16_t* P = cx.perm[tk.buf];
@@ -190,21 +177,28 @@ __device__ int process_build(const T& tm, const SmemCtx& cx, Task tk, Task* ch) 
     if (tk.j == 0) {
       // Build(P, t): leaf wrap, heavy leaf, then sample and skeleton root.
       if (n <= cx.p.phi) {
-        emit_leaf(tm, cx, tk);
+        emit_leaf<D>(tm, cx, tk);
         return 0;
       }
-      int mn[PKD_DMAX], mx[PKD_DMAX];
-      team_minmax(tm, cx.s, P, lo, hi, false, mn, mx);
-      int wd = widest_dim(mn, mx, cx.s.d);
+      int mn[D], mx[D];
+      team_minmax<D>(tm, cx.s, P, lo, hi, false, mn, mx);
+      int vmin, vmax;
+      const int wd = widest_dim<D>(mn, mx, vmin, vmax);
       if (wd < 0) {
-        emit_leaf(tm, cx, tk);
+        emit_leaf<D>(tm, cx, tk);
         return 0;
       }
-      const int shift = sample_shift(cx.p, (uint64_t)n);
-      const int ns = team_draw_sample(tm, cx.s, cx.flag, P, lo, hi, cx.p.seed, tk.t, shift);
+      // A subproblem with fewer than 2*sigma_os points cannot reach the
+      // split threshold whatever its sample: no need to draw it.
+      int ns = 0;
+      if (n >= 2 * cx.p.sigma_os) {
+        const int shift = sample_shift(cx.p, (uint64_t)n);
+        ns = team_draw_sample<D>(tm, cx.s, cx.flag, P, lo, hi, cx.p.seed, tk.t, shift);
+      }
       tk.ns = (uint16_t)ns;
       bool skel = false;
-      if (ns >= 2 * cx.p.sigma_os) skel = team_split_rule(tm, cx.s, P, lo, hi, true, ns, dim, x);
+      if (ns >= 2 * cx.p.sigma_os)
+        skel = team_split_rule<D>(tm, cx.s, P, lo, hi, true, ns, nullptr, nullptr, dim, x);
       if (skel) {
         on_sample = true;
       } else {
@@ -212,15 +206,8 @@ __device__ int process_build(const T& tm, const SmemCtx& cx, Task tk, Task* ch) 
         on_sample = false;
         dim = wd;
         int less, eq;
-        int vmn = mn[0], vmx = mx[0];
-#pragma unroll
-        for (int j = 1; j < PKD_DMAX; ++j)
-          if (j == dim) {
-            vmn = mn[j];
-            vmx = mx[j];
-          }
-        x = team_select(tm, cx.s, P, lo, hi, false, dim, n / 2, vmn, vmx, less, eq);
-        if (less == 0) x = team_min_above(tm, cx.s, P, lo, hi, false, dim, x);
+        x = team_select<D>(tm, cx.s, P, lo, hi, false, dim, n / 2, vmin, vmax, less, eq);
+        if (less == 0) x = team_min_above<D>(tm, cx.s, P, lo, hi, false, dim, x);
       }
     } else {
       // Skeleton node: bucket when deep enough, too few samples or identical.
@@ -228,15 +215,17 @@ __device__ int process_build(const T& tm, const SmemCtx& cx, Task tk, Task* ch) 
         tk.j = 0;
         continue;
       }
-      if (!team_split_rule(tm, cx.s, P, lo, hi, true, tk.ns, dim, x)) {
+      if (!team_split_rule<D>(tm, cx.s, P, lo, hi, true, tk.ns, nullptr, nullptr, dim, x)) {
         tk.j = 0;
         continue;
       }
       on_sample = true;
     }
     int L, SL, SR;
-    team_partition(tm, cx.s, P, Q, lo, hi, dim, x, L, SL, SR);
-    int b = alloc_two(tm, cx);
+    team_partition<D>(tm, cx.s, P, Q, lo, hi, dim, x, L, SL, SR);
+    int b = 0;
+    if (tm.leader()) b = atomicAdd(&cx.ctl->next_slot, 2);
+    b = tm.bcast(b);
     if (b + 2 > cx.slot_limit) {
       if (tm.leader()) set_error(cx.st, DERR_SLOT, b);
       return 0;
@@ -267,20 +256,20 @@ __device__ int process_build(const T& tm, const SmemCtx& cx, Task tk, Task* ch) 
 // Skeleton mode: every loaded point is a sample; nodes become heap entries.
 // ---------------------------------------------------------------------------
 
-template <class T>
-__device__ int process_skel(const T& tm, const SmemCtx& cx, Task tk, Task* ch) {
+template <int D>
+__device__ int process_skel(const Team& tm, const SmemCtx<D>& cx, Task tk, Task* ch) {
   const int lo = tk.lo, hi = tk.hi, n = hi - lo;
   uint16_t* P = cx.perm[tk.buf];
   uint16_t* Q = cx.perm[tk.buf ^ 1];
   int dim, x;
-  bool split = tk.j < cx.lam && n >= cx.min_split &&
-               team_split_rule(tm, cx.s, P, lo, hi, false, n, dim, x);
+  const bool split = tk.j < cx.lam && n >= cx.min_split &&
+                     team_split_rule<D>(tm, cx.s, P, lo, hi, false, n, nullptr, nullptr, dim, x);
   if (!split) {
     if (tm.leader()) cx.skel[tk.slot] = make_int2(0, sk_meta(SK_BUCKET, 0, 0));
     return 0;
   }
   int L, SL, SR;
-  team_partition(tm, cx.s, P, Q, lo, hi, dim, x, L, SL, SR);
+  team_partition<D>(tm, cx.s, P, Q, lo, hi, dim, x, L, SL, SR);
   if (tm.leader()) cx.skel[tk.slot] = make_int2(x, sk_meta(SK_INTERNAL, dim, 0));
   const uint8_t nb = (uint8_t)(tk.buf ^ 1);
   const uint8_t nj = (uint8_t)(tk.j + 1);
@@ -289,19 +278,20 @@ __device__ int process_skel(const T& tm, const SmemCtx& cx, Task tk, Task* ch) {
   return 2;
 }
 
-template <bool SKEL, class T>
-__device__ __forceinline__ int process_task(const T& tm, const SmemCtx& cx, const Task& tk, Task* ch) {
-  if (SKEL) return process_skel(tm, cx, tk, ch);
-  return process_build(tm, cx, tk, ch);
+template <bool SKEL, int D>
+__device__ __forceinline__ int process_task(const Team& tm, const SmemCtx<D>& cx, const Task& tk, Task* ch) {
+  if (SKEL) return process_skel<D>(tm, cx, tk, ch);
+  return process_build<D>(tm, cx, tk, ch);
 }
 
-template <bool SKEL>
-__device__ void warp_run(const WarpTeam& wt, const SmemCtx& cx, Task tk, Task* stk) {
-  int sp = 0;
+// One warp finishes its subtree depth first; `stk` holds sp0 deferred tasks.
+template <bool SKEL, int D>
+__device__ void warp_run(const Team& wt, const SmemCtx<D>& cx, Task tk, Task* stk, int sp0) {
+  int sp = sp0;
   for (;;) {
     Task ch[2];
-    int nch = process_task<SKEL>(wt, cx, tk, ch);
-    int err = *(volatile int*)&cx.st->err;
+    const int nch = process_task<SKEL, D>(wt, cx, tk, ch);
+    const int err = *(volatile int*)&cx.st->err;
     if (__shfl_sync(FULL_MASK, err, 0)) return;  // warp-uniform exit
     if (nch == 2) {
       const int s0 = ch[0].hi - ch[0].lo, s1 = ch[1].hi - ch[1].lo;
@@ -325,64 +315,54 @@ __device__ void warp_run(const WarpTeam& wt, const SmemCtx& cx, Task tk, Task* s
   }
 }
 
-// Drive one CTA over its root task: block phase, then warp phase, repeated
-// until both are empty.  All reads of the control words happen between
-// barriers, so every thread takes the same branches.
-template <bool SKEL>
-__device__ void run_tasks(const SmemCtx& cx, Task root, Task* bstack, Task* wlist, Task* wstack,
-                          unsigned* bhist, int* bred, unsigned* whist) {
-  SmemCtl* ctl = cx.ctl;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    ctl->bsp = 0;
-    ctl->wl_n = 0;
-    if (root.hi - root.lo > WMAX) bstack[ctl->bsp++] = root;
-    else wlist[ctl->wl_n++] = root;
-  }
-  __syncthreads();
-  BlockTeam<SM_NW> bt{bhist, bred};
-  WarpTeam wt{whist + warp_id() * 256, nullptr};
-  for (;;) {
-    for (;;) {
-      if (tid == 0) ctl->err = *(volatile int*)&cx.st->err;
-      __syncthreads();
-      const int bsp = ctl->bsp, wl = ctl->wl_n, err = ctl->err;
-      __syncthreads();
-      if (bsp == 0 || wl + 2 > WLIST || err) break;
-      const Task tk = bstack[bsp - 1];
-      if (tid == 0) ctl->bsp = bsp - 1;
-      Task ch[2];
-      const int nch = process_task<SKEL>(bt, cx, tk, ch);
-      if (tid == 0 && nch == 2) {
-        const int s0 = ch[0].hi - ch[0].lo, s1 = ch[1].hi - ch[1].lo;
-        const Task big = s0 >= s1 ? ch[0] : ch[1];
-        const Task small = s0 >= s1 ? ch[1] : ch[0];
-        const Task order[2] = {big, small};  // larger pushed first: smaller runs next
-        for (int c = 0; c < 2; ++c) {
-          const Task& t = order[c];
-          if (t.hi - t.lo > WMAX) {
-            if (ctl->bsp < BSTK) bstack[ctl->bsp++] = t;
-            else set_error(cx.st, DERR_STACK, 1000 + ctl->bsp);
-          } else {
-            wlist[ctl->wl_n++] = t;
-          }
-        }
+// Drive the warps of a CTA over one root task (see the scheduling note at
+// the top).  Every branch below is uniform within the team that takes it.
+template <bool SKEL, int D>
+__device__ void run_team_tasks(const SmemCtx<D>& cx, Task root, unsigned* whist, int* wred, Task* wstack,
+                               int cta_warps) {
+  const int w = warp_id();
+  int f = 0, nw = cta_warps;
+  Task tk = root;
+  bool have_task = true;
+  while (nw > 1) {
+    const Team tm{f, nw, team_barrier(f, nw, cta_warps), whist + f * 256, wred + f * RED_INTS};
+    Task ch[2];
+    const int nch = process_task<SKEL, D>(tm, cx, tk, ch);
+    if (nch == 0) {  // this team's subtree is finished (deferred tasks remain)
+      have_task = false;
+      break;
+    }
+    const int s0 = ch[0].hi - ch[0].lo, s1 = ch[1].hi - ch[1].lo;
+    const int big = s0 >= s1 ? 0 : 1;
+    const int small_n = min(s0, s1);
+    // a tiny child goes to the first warp's stack; the team keeps the other
+    tm.sync();
+    const bool defer = small_n <= DEFER_MAX && small_n * 8 <= max(s0, s1) && cx.ctl->wsp[f] < WSTK;
+    tm.sync();
+    if (defer) {
+      if (tm.leader()) {
+        wstack[f * WSTK + cx.ctl->wsp[f]] = ch[big ^ 1];
+        cx.ctl->wsp[f] += 1;
       }
-      __syncthreads();
+      tm.sync();
+      tk = ch[big];
+      continue;
     }
-    const int nl = ctl->wl_n;
-    __syncthreads();
-    for (int e = warp_id(); e < nl; e += SM_NW) warp_run<SKEL>(wt, cx, wlist[e], wstack + warp_id() * WSTK);
-    __syncthreads();
-    if (tid == 0) {
-      ctl->wl_n = 0;
-      ctl->err = *(volatile int*)&cx.st->err;
-    }
-    __syncthreads();
-    const int bsp = ctl->bsp, err = ctl->err;
-    __syncthreads();
-    if (bsp == 0 || err) break;
+    const int half = nw / 2;
+    const bool second = w >= f + half;
+    tk = second ? ch[1] : ch[0];
+    if (second) f += half;
+    nw = half;
   }
+  __syncwarp();
+  int sp0 = cx.ctl->wsp[w];
+  if (!have_task) {
+    if (sp0 == 0) return;
+    tk = wstack[w * WSTK + --sp0];
+  }
+  __syncwarp();
+  const Team wt{w, 1, 0, whist + w * 256, wred + w * RED_INTS};
+  warp_run<SKEL, D>(wt, cx, tk, wstack + w * WSTK, sp0);
 }
 
 }  // namespace pkd

@@ -290,20 +290,21 @@ static void launch_smem_warp(const SmemArgs& a, uint32_t nblocks, size_t smb, cu
 // persistent base list, counter *nbase).
 __global__ void k_classify(const Seg* segs, uint32_t nseg, uint32_t cap, Seg* big, uint32_t* ctr,
                            unsigned long long* pts, Seg* base, uint32_t* nbase, uint32_t base_cap,
-                           Seg* wbase, uint32_t* nwbase, uint32_t wcap, uint32_t tile, uint32_t where,
-                           unsigned long long* base_pts, DevStatus* st) {
+                           Seg* wbase, uint32_t* nwbase, uint32_t wcap, Seg* tbase, uint32_t* ntbase,
+                           uint32_t tcap, uint32_t tile, uint32_t where, unsigned long long* base_pts,
+                           DevStatus* st) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   Seg s{};
-  int kind = -1;  // 0 big, 1 one CTA, 2 one warp
+  int kind = -1;  // 0 big, 1 one CTA, 2 one warp, 3 one warp with a small slice
   if (i < nseg) {
     s = segs[i];
     if (s.len != SEG_SKIP) {
       s.where = where;
-      kind = s.len > cap ? 0 : (s.len > wcap ? 1 : 2);
+      kind = s.len > cap ? 0 : (s.len > wcap ? 1 : (s.len > tcap ? 2 : 3));
     }
   }
   // counters are updated once per warp and kind
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 4; ++k) {
     const unsigned m = __ballot_sync(FULL_MASK, kind == k);
     if (!m) continue;
     unsigned long long sum = kind == k ? s.len : 0;
@@ -320,14 +321,14 @@ __global__ void k_classify(const Seg* segs, uint32_t nseg, uint32_t cap, Seg* bi
         atomicAdd(&ctr[2], tl);
         atomicAdd(pts, sum);
       } else {
-        b = atomicAdd(k == 1 ? nbase : nwbase, (uint32_t)__popc(m));
+        b = atomicAdd(k == 1 ? nbase : (k == 2 ? nwbase : ntbase), (uint32_t)__popc(m));
         atomicAdd(&base_pts[k - 1], sum);
       }
     }
     b = __shfl_sync(FULL_MASK, b, 0) + __popc(m & lanemask_lt());
     if (kind == k) {
       if (k == 0) big[b] = s;
-      else if (b < base_cap) (k == 1 ? base : wbase)[b] = s;
+      else if (b < base_cap) (k == 1 ? base : (k == 2 ? wbase : tbase))[b] = s;
       else set_error(st, DERR_CAPACITY, 300 + k);
     }
   }
@@ -953,8 +954,10 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
 
   // device counters: [0] big segs, [2] their tiles, [3] exact, [4] heavy,
   // [8..10] skeleton jobs; [12] base list length; u64 at [14] big points
+  // u32: [12] CTA list, [13] warp list, [24] tiny list;
+  // u64: [14] big points, [16] CTA points, [18] warp points, [20] tiny points
   uint32_t* dctr;
-  PKD_TRY(sc.get(&dctr, 24));
+  PKD_TRY(sc.get(&dctr, 32));
   unsigned long long* dpts = (unsigned long long*)(dctr + 14);
   unsigned long long* dbase_pts = (unsigned long long*)(dctr + 16);
   uint32_t* d_nbase = dctr + 12;
@@ -964,7 +967,7 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     uint32_t* p;
     ~HostFree() { cudaFreeHost(p); }
   } hf{hctr};
-  PKD_CUDA(cudaMemsetAsync(dctr, 0, 24 * 4, s));
+  PKD_CUDA(cudaMemsetAsync(dctr, 0, 32 * 4, s));
 
   const uint64_t nroots = job.dsegs ? job.dsegs_n : job.segs.size();
   Seg* cur;
@@ -978,9 +981,11 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
   const uint32_t wcap = (uint32_t)warp_cap_for(d);
   // every base segment is a root or a non-empty bucket: at most extent + roots
   const uint64_t base_cap_segs = extent + nroots + 16;
-  Seg *base_list, *wbase_list;
+  Seg *base_list, *wbase_list, *tbase_list;
   PKD_TRY(sc.get(&base_list, base_cap_segs));
   PKD_TRY(sc.get(&wbase_list, base_cap_segs));
+  PKD_TRY(sc.get(&tbase_list, base_cap_segs));
+  const uint32_t tcap = 128;
 
   Src src{};
   int src_where;
@@ -1021,7 +1026,8 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     PKD_CUDA(cudaMemsetAsync(dpts, 0, 8, s));
     PKD_LAUNCH(k_classify<<<(unsigned)((ncur + 255) / 256), 256, 0, s>>>(
         cur, (uint32_t)ncur, cap, big, dctr, dpts, base_list, d_nbase, (uint32_t)base_cap_segs,
-        wbase_list, d_nbase + 1, wcap, (uint32_t)TILE, (uint32_t)src_where, dbase_pts, t.st));
+        wbase_list, d_nbase + 1, wcap, tbase_list, dctr + 24, tcap, (uint32_t)TILE, (uint32_t)src_where,
+        dbase_pts, t.st));
     PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 16 * 4, cudaMemcpyDeviceToHost, s));
     PKD_CUDA(cudaStreamSynchronize(s));
     const uint32_t nbig = hctr[0], tiles = hctr[2];
@@ -1131,20 +1137,24 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
   }
 
   // 5. every small subproblem, one CTA each, in shared memory
-  PKD_CUDA(cudaMemcpyAsync(hctr + 12, d_nbase, 32, cudaMemcpyDeviceToHost, s));
+  PKD_CUDA(cudaMemcpyAsync(hctr + 12, d_nbase, 13 * 4, cudaMemcpyDeviceToHost, s));
   PKD_CUDA(cudaStreamSynchronize(s));
   const uint64_t cta_pts = *(unsigned long long*)(hctr + 16), warp_pts = *(unsigned long long*)(hctr + 18);
+  const uint64_t tiny_pts = *(unsigned long long*)(hctr + 20);
   const uint32_t nbase = std::min<uint32_t>(hctr[12], (uint32_t)base_cap_segs);
   const uint32_t nwbase = std::min<uint32_t>(hctr[13], (uint32_t)base_cap_segs);
-  if (nwbase > 0) {
+  const uint32_t ntbase = std::min<uint32_t>(hctr[24], (uint32_t)base_cap_segs);
+  for (int pass = 0; pass < 2; ++pass) {
+    const uint32_t nw = pass == 0 ? nwbase : ntbase;
+    if (nw == 0) continue;
     SmemArgs wa = sa;
-    wa.segs = wbase_list;
-    wa.nsegs = d_nbase + 1;
-    wa.cap = (int)wcap;
-    const size_t smb = warp_layout((int)wcap, d).per_warp * WK_WARPS;
+    wa.segs = pass == 0 ? wbase_list : tbase_list;
+    wa.nsegs = pass == 0 ? d_nbase + 1 : dctr + 24;
+    wa.cap = pass == 0 ? (int)wcap : (int)tcap;
+    const size_t smb = warp_layout(wa.cap, d).per_warp * WK_WARPS;
     KTimer kt;
-    ktimer_begin(kt, "smem_warp", warp_pts, s);
-    PKD_DISPATCH_D(d, launch_smem_warp, wa, (nwbase + WK_WARPS - 1) / WK_WARPS, smb, s);
+    ktimer_begin(kt, "smem_warp", pass == 0 ? warp_pts : tiny_pts, s);
+    PKD_DISPATCH_D(d, launch_smem_warp, wa, (nw + WK_WARPS - 1) / WK_WARPS, smb, s);
     ktimer_end(kt);
   }
   if (nbase > 0) {

@@ -130,6 +130,7 @@ struct RoundArgs {
   uint32_t* tile0;   // [nbig] first tile of each big segment
   uint64_t* excl;    // [nbig] points of the big segments before this one
   int2* skel;        // [nbig][HN]
+  const uint32_t* skel_map;  // optional: big segment -> row of skel
   uint32_t* slots;   // [nbig][HN]
   uint32_t* nbk;     // [nbig] buckets
   uint8_t* exact;    // [nbig] 1: exact level on the points; 2: already handled
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(SIEVE_THREADS) k_count(RoundArgs r) {
   extern __shared__ __align__(16) uint8_t sm[];
   int2* sk = (int2*)sm;
   unsigned* lh = (unsigned*)(sk + r.HN);
-  const int2* gsk = r.skel + (uint64_t)t.s * r.HN;
+  const int2* gsk = r.skel + (uint64_t)(r.skel_map ? r.skel_map[t.s] : t.s) * r.HN;
   for (int v = threadIdx.x; v < r.HN; v += blockDim.x) sk[v] = gsk[v];
   for (int b = threadIdx.x; b < r.NB; b += blockDim.x) lh[b] = 0;
   __syncthreads();
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(SIEVE_THREADS) k_scatter(RoundArgs r) {
   int32_t* stx = (int32_t*)(gbase + r.NB);     // [D][TILE]
   uint32_t* sid = (uint32_t*)(stx + (size_t)D * r.TILE);
   uint16_t* sb = (uint16_t*)(sid + r.TILE);
-  const int2* gsk = r.skel + (uint64_t)t.s * r.HN;
+  const int2* gsk = r.skel + (uint64_t)(r.skel_map ? r.skel_map[t.s] : t.s) * r.HN;
   for (int v = threadIdx.x; v < r.HN; v += blockDim.x) sk[v] = gsk[v];
   for (int b = threadIdx.x; b < r.NB; b += blockDim.x) cur[b] = 0;
   __syncthreads();

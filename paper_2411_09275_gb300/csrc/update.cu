@@ -72,7 +72,10 @@ struct UpdArgs {
   uint32_t* iflag;   // [item]
   // next round
   Seg* next;
-  uint32_t* next_ctr;  // [0] items, [1] tiles
+  uint32_t* next_ctr;  // [0] items, [1] tiles of big items, [2] big items, [3] small items
+  Seg* next_big;       // big items (more than SMALL_ITEM points) and their item index
+  uint32_t* next_bigmap;
+  uint32_t* next_small;  // item index of the small items
   uint32_t* next_iflag;
   const uint32_t* next_fnd;  // found counts of the next round (aggregation)
   int next_HN;
@@ -137,28 +140,130 @@ __global__ void k_fetch(UpdArgs a) {
   a.nbk[i] = nb;
 }
 
-// Bucket counts and ranges; next-round items and leaf groups.
+constexpr uint32_t SMALL_ITEM = 256;  // items up to this many points: one warp routes them
+
+// Bucket ranges of the big items from the bucket-major scan of the tile
+// histograms.
+__global__ void k_bucket_ranges(RoundArgs r, uint64_t* bstart, uint32_t* blen, const uint32_t* nbk) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= *r.nbig) return;
+  const Seg it = r.big[s];
+  const uint32_t k = r.skel_map[s];
+  const uint32_t nb = nbk[k];
+  const uint32_t nt = (it.len + r.TILE - 1) / r.TILE;
+  const uint64_t hb = (uint64_t)r.tile0[s] * r.NB;
+  const uint32_t base = r.hscan[hb];
+  for (uint32_t b = 0; b < (uint32_t)r.NB; ++b) {
+    uint32_t b0 = it.len, b1 = it.len;
+    if (b < nb) {
+      b0 = r.hscan[hb + (uint64_t)b * nt] - base;
+      b1 = (b + 1 < nb) ? r.hscan[hb + (uint64_t)(b + 1) * nt] - base : it.len;
+    }
+    bstart[(uint64_t)k * r.NB + b] = it.start + b0;
+    blen[(uint64_t)k * r.NB + b] = b1 - b0;
+  }
+}
+
+// Small items: one warp walks every point through the item's skeleton,
+// counts and ranks the buckets in shared memory, and scatters the item in
+// one pass (no global histogram: the warp owns the whole item).  Points
+// also go to the final batch buffer F (see k_copy_round).
+template <int D>
+__global__ void __launch_bounds__(256) k_route_small(RoundArgs r, const uint32_t* small, const uint32_t* nsmall,
+                                                     const Seg* items, const uint32_t* nbk, uint64_t* bstart,
+                                                     uint32_t* blen, Pts F) {
+  extern __shared__ unsigned cnt_sm[];
+  const uint32_t gw = blockIdx.x * (blockDim.x / 32) + warp_id();
+  if (gw >= *nsmall) return;  // warp-uniform
+  unsigned* cnt = cnt_sm + (size_t)warp_id() * r.NB;
+  const uint32_t k = small[gw];
+  const Seg it = items[k];
+  const int2* sk = r.skel + (uint64_t)k * r.HN;
+  const uint32_t nb = nbk[k];
+  for (int b = lane_id(); b < r.NB; b += 32) cnt[b] = 0;
+  __syncwarp();
+  constexpr int PER = SMALL_ITEM / 32;
+  int32_t x[PER][D];
+  uint32_t id[PER];
+  int bk[PER], rk[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const uint32_t i = q * 32 + lane_id();
+    bk[q] = -1;
+    rk[q] = 0;
+    if (i < it.len) {
+      const uint64_t g = it.start + i;
+#pragma unroll
+      for (int j = 0; j < D; ++j) x[q][j] = r.src.x(D, j, g);
+      id[q] = r.src.id(g);
+      int h = 1;
+      for (int l = 0; l < r.lam; ++l) {
+        const int2 e = sk[h];
+        if (sk_state(e.y) != SK_INTERNAL) break;
+        h = 2 * h + (x[q][sk_dim(e.y)] >= e.x);
+      }
+      bk[q] = sk_bucket(sk[h].y);
+    }
+    const unsigned m = __match_any_sync(FULL_MASK, bk[q]);
+    const int leader = __ffs(m) - 1;
+    unsigned b0 = 0;
+    if (bk[q] >= 0 && lane_id() == leader) b0 = atomicAdd(&cnt[bk[q]], (unsigned)__popc(m));
+    rk[q] = (int)__shfl_sync(FULL_MASK, b0, leader) + __popc(m & lanemask_lt());
+  }
+  __syncwarp();
+  // bucket starts: exclusive scan of the counts, 32 buckets at a time
+  unsigned carry = 0;
+  for (int b0 = 0; b0 < r.NB; b0 += 32) {
+    const int b = b0 + lane_id();
+    const unsigned c = b < r.NB ? cnt[b] : 0;
+    const unsigned incl = (unsigned)warp_incl_scan((int)c);
+    if (b < r.NB) {
+      const uint64_t o = (uint64_t)k * r.NB + b;
+      bstart[o] = it.start + carry + incl - c;
+      blen[o] = (uint32_t)b < nb ? c : 0;
+    }
+    __syncwarp();
+    if (b < r.NB) cnt[b] = carry + incl - c;
+    carry += __shfl_sync(FULL_MASK, incl, 31);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    if (bk[q] < 0) continue;
+    const uint64_t g = it.start + cnt[bk[q]] + (uint32_t)rk[q];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      r.dst.c[(uint64_t)j * r.dst.stride + g] = x[q][j];
+      F.c[(uint64_t)j * F.stride + g] = x[q][j];
+    }
+    r.dst.id[g] = id[q];
+    F.id[g] = id[q];
+  }
+}
+
+template <int D>
+static void launch_route_small(const RoundArgs& ra, const uint32_t* small, const uint32_t* nsmall, const Seg* items,
+                               const uint32_t* nbk, uint64_t* bstart, uint32_t* blen, Pts F, uint32_t n,
+                               cudaStream_t s) {
+  const size_t smb = (size_t)8 * ra.NB * 4;
+  PKD_LAUNCH(k_route_small<D><<<(n + 7) / 8, 256, smb, s>>>(ra, small, nsmall, items, nbk, bstart, blen, F));
+}
+
+// Next-round items and leaf groups from the bucket ranges.
 __global__ void k_route_emit(UpdArgs a) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= *a.nitems) return;
   const Seg it = a.items[i];
   const int2* sk = a.skel + (uint64_t)i * a.HN;
   const uint32_t* sl = a.slots + (uint64_t)i * a.HN;
-  const uint32_t nb = a.nbk[i];
-  const uint32_t nt = (it.len + a.TILE - 1) / a.TILE;
-  const uint64_t hb = (uint64_t)a.tile0[i] * a.NB;
-  const uint32_t base = a.hscan[hb];
   for (uint32_t b = 0; b < (uint32_t)a.NB; ++b) a.link[(uint64_t)i * a.NB + b] = LINK_NONE;
   for (int v = 1; v < a.HN; ++v) {
     const int m = sk[v].y;
     if (sk_state(m) != SK_BUCKET) continue;
     const int b = sk_bucket(m);
-    const uint32_t b0 = a.hscan[hb + (uint64_t)b * nt] - base;
-    const uint32_t b1 = (b + 1 < (int)nb) ? a.hscan[hb + (uint64_t)(b + 1) * nt] - base : it.len;
-    const uint32_t cnt = b1 - b0;
     const uint64_t k = (uint64_t)i * a.NB + b;
-    a.bstart[k] = it.start + b0;
-    a.blen[k] = cnt;
+    const uint32_t cnt = a.blen[k];
+    const uint64_t b0 = a.bstart[k];
     if (cnt == 0) continue;
     const uint32_t slot = sl[v];
     const uint32_t depth = it.depth + (31 - __clz(v));
@@ -168,12 +273,20 @@ __global__ void k_route_emit(UpdArgs a) {
         set_error(a.st, DERR_CAPACITY, 800);
         return;
       }
-      a.groups[g] = LeafGroup{slot, depth, it.start + b0, cnt, a.insert ? cnt : 0u, 0u, 0u};
+      a.groups[g] = LeafGroup{slot, depth, b0, cnt, a.insert ? cnt : 0u, 0u, 0u};
       a.link[k] = LINK_LEAF | g;
     } else {
       const uint32_t q = atomicAdd(&a.next_ctr[0], 1u);
-      a.next[q] = Seg{it.start + b0, cnt, depth, slot, IN_B};
-      atomicAdd(&a.next_ctr[1], (cnt + a.TILE - 1) / a.TILE);
+      const Seg c{b0, cnt, depth, slot, IN_B};
+      a.next[q] = c;
+      if (cnt > SMALL_ITEM) {
+        const uint32_t kb = atomicAdd(&a.next_ctr[2], 1u);
+        a.next_big[kb] = c;
+        a.next_bigmap[kb] = q;
+        atomicAdd(&a.next_ctr[1], (cnt + a.TILE - 1) / a.TILE);
+      } else {
+        a.next_small[atomicAdd(&a.next_ctr[3], 1u)] = q;
+      }
       a.link[k] = q;
     }
   }
@@ -639,9 +752,23 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
   std::vector<RouteRound> rounds;
   Seg root{0, (uint32_t)m, 0, t.root, IN_B};
   Seg* cur;
+  Seg* cur_big;
+  uint32_t *cur_bigmap, *cur_small;
   PKD_TRY(sc.get(&cur, 1));
+  PKD_TRY(sc.get(&cur_big, 1));
+  PKD_TRY(sc.get(&cur_bigmap, 1));
+  PKD_TRY(sc.get(&cur_small, 1));
+  uint32_t zero = 0;
   PKD_CUDA(cudaMemcpyAsync(cur, &root, sizeof(Seg), cudaMemcpyHostToDevice, s));
-  uint32_t ncur = 1, tiles = (uint32_t)((m + TILE - 1) / TILE);
+  const bool root_big = m > SMALL_ITEM;
+  if (root_big) {
+    PKD_CUDA(cudaMemcpyAsync(cur_big, &root, sizeof(Seg), cudaMemcpyHostToDevice, s));
+    PKD_CUDA(cudaMemcpyAsync(cur_bigmap, &zero, 4, cudaMemcpyHostToDevice, s));
+  } else {
+    PKD_CUDA(cudaMemcpyAsync(cur_small, &zero, 4, cudaMemcpyHostToDevice, s));
+  }
+  uint32_t ncur = 1, tiles = root_big ? (uint32_t)((m + TILE - 1) / TILE) : 0;
+  uint32_t nbig = root_big ? 1 : 0, nsmall = root_big ? 0 : 1;
   int w = 0;
   uint32_t groups_before = 0;
   for (int r = 0; ncur > 0; ++r) {
@@ -656,29 +783,25 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
     PKD_TRY(sc.get(&R.bstart, (size_t)ncur * NB));
     PKD_TRY(sc.get(&R.blen, (size_t)ncur * NB));
     PKD_TRY(sc.get(&R.iflag, ncur));
-    PKD_TRY(sc.get(&R.d_n, 1));
+    PKD_TRY(sc.get(&R.d_n, 4));
+    uint32_t hn[4] = {ncur, nbig, nsmall, 0};
     PKD_CUDA(cudaMemsetAsync(R.iflag, 0, (size_t)ncur * 4, s));
-    PKD_CUDA(cudaMemcpyAsync(R.d_n, &R.n, 4, cudaMemcpyHostToDevice, s));
-    uint32_t *nbk, *tile0, *hist, *hscan, *partial;
-    uint64_t* excl;
+    PKD_CUDA(cudaMemcpyAsync(R.d_n, hn, 16, cudaMemcpyHostToDevice, s));
+    uint32_t* nbk;
     PKD_TRY(sc.get(&nbk, ncur));
-    PKD_TRY(sc.get(&tile0, ncur));
-    PKD_TRY(sc.get(&excl, ncur));
-    PKD_TRY(sc.get(&hist, (size_t)tiles * NB));
-    PKD_TRY(sc.get(&hscan, (size_t)tiles * NB));
-    const uint64_t nh = (uint64_t)tiles * NB;
-    PKD_TRY(sc.get(&partial, (nh + SCAN_TILE - 1) / SCAN_TILE + 1));
-    Seg* next;
+    Seg *next, *next_big;
+    uint32_t *next_bigmap, *next_small;
     PKD_TRY(sc.get(&next, (size_t)ncur * NB));
-    PKD_CUDA(cudaMemsetAsync(dctr, 0, 8, s));
+    PKD_TRY(sc.get(&next_big, (size_t)ncur * NB));
+    PKD_TRY(sc.get(&next_bigmap, (size_t)ncur * NB));
+    PKD_TRY(sc.get(&next_small, (size_t)ncur * NB));
+    PKD_CUDA(cudaMemsetAsync(dctr, 0, 16, s));
 
     ua.items = cur;
     ua.nitems = R.d_n;
     ua.skel = R.skel;
     ua.slots = R.slots;
     ua.nbk = nbk;
-    ua.tile0 = tile0;
-    ua.hscan = hscan;
     ua.bstart = R.bstart;
     ua.blen = R.blen;
     ua.link = R.link;
@@ -686,9 +809,11 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
     ua.iflag = R.iflag;
     ua.next = next;
     ua.next_ctr = dctr;
+    ua.next_big = next_big;
+    ua.next_bigmap = next_bigmap;
+    ua.next_small = next_small;
     const unsigned g1 = (ncur + 127) / 128;
     PKD_LAUNCH(k_fetch<<<g1, 128, 0, s>>>(ua));
-    PKD_LAUNCH(k_big_prefix<<<1, 1024, 0, s>>>(cur, R.d_n, (uint32_t)TILE, tile0, excl));
 
     RoundArgs ra{};
     ra.p = p;
@@ -699,27 +824,49 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
     ra.src.soa = W[w];
     ra.src.is_aos = 0;
     ra.dst = W[w ^ 1];
-    ra.big = cur;
-    ra.nbig = R.d_n;
-    ra.tile0 = tile0;
-    ra.excl = excl;
     ra.skel = R.skel;
-    ra.hist = hist;
-    ra.hscan = hscan;
     ra.st = t.st;
-    PKD_DISPATCH_D(d, launch_count, ra, tiles, s);
-    device_excl_scan(hist, hscan, nh, partial, s);
+    if (nbig) {
+      // big items: tile histograms, bucket-major scan, scatter
+      uint32_t *tile0, *hist, *hscan, *partial;
+      uint64_t* excl;
+      PKD_TRY(sc.get(&tile0, nbig));
+      PKD_TRY(sc.get(&excl, nbig));
+      PKD_TRY(sc.get(&hist, (size_t)tiles * NB));
+      PKD_TRY(sc.get(&hscan, (size_t)tiles * NB));
+      const uint64_t nh = (uint64_t)tiles * NB;
+      PKD_TRY(sc.get(&partial, (nh + SCAN_TILE - 1) / SCAN_TILE + 1));
+      ra.big = cur_big;
+      ra.nbig = R.d_n + 1;
+      ra.skel_map = cur_bigmap;
+      ra.tile0 = tile0;
+      ra.excl = excl;
+      ra.hist = hist;
+      ra.hscan = hscan;
+      PKD_LAUNCH(k_big_prefix<<<1, 1024, 0, s>>>(cur_big, R.d_n + 1, (uint32_t)TILE, tile0, excl));
+      PKD_DISPATCH_D(d, launch_count, ra, tiles, s);
+      device_excl_scan(hist, hscan, nh, partial, s);
+      PKD_LAUNCH(k_bucket_ranges<<<(nbig + 127) / 128, 128, 0, s>>>(ra, R.bstart, R.blen, nbk));
+      PKD_DISPATCH_D(d, launch_scatter, ra, tiles, (uint64_t)0, s);
+      PKD_LAUNCH(k_copy_round<<<tiles, 256, 0, s>>>(ra, F));
+    }
+    if (nsmall) {
+      PKD_DISPATCH_D(d, launch_route_small, ra, cur_small, R.d_n + 2, cur, nbk, R.bstart, R.blen, F, nsmall, s);
+    }
     PKD_LAUNCH(k_route_emit<<<g1, 128, 0, s>>>(ua));
-    PKD_DISPATCH_D(d, launch_scatter, ra, tiles, (uint64_t)0, s);
     PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 24, cudaMemcpyDeviceToHost, s));
     PKD_CUDA(cudaStreamSynchronize(s));
     const uint32_t nnext = hctr[0], ntiles = hctr[1], ngroups = hctr[4];
-    PKD_LAUNCH(k_copy_round<<<tiles, 256, 0, s>>>(ra, F));
     groups_before = ngroups;
     rounds.push_back(R);
     cur = next;
+    cur_big = next_big;
+    cur_bigmap = next_bigmap;
+    cur_small = next_small;
     ncur = nnext;
     tiles = ntiles;
+    nbig = hctr[2];
+    nsmall = hctr[3];
     w ^= 1;
   }
   const uint32_t ngroups = groups_before;

@@ -109,7 +109,7 @@ __device__ void load_segment(const SmemArgs& a, const Seg& seg, int32_t* X, uint
 }
 
 template <int D>
-__global__ void __launch_bounds__(SM_THREADS) k_smem_build(SmemArgs a) {
+__global__ void __launch_bounds__(SM_THREADS, 1) k_smem_build(SmemArgs a) {
   if (blockIdx.x >= *a.nsegs) return;
   extern __shared__ __align__(16) uint8_t sm[];
   const Seg seg = a.segs[blockIdx.x];
@@ -121,7 +121,10 @@ __global__ void __launch_bounds__(SM_THREADS) k_smem_build(SmemArgs a) {
   }
   const int n = (int)seg.len;
   load_segment<D>(a, seg, q.X, q.ID, q.perm0, cap, tid, SM_THREADS);
-  if (tid == 0) q.ctl->next_slot = 0;
+  if (tid == 0) {
+    q.ctl->next_slot = 0;
+    q.ctl->maxd = 0;
+  }
   if (tid < SM_NW) q.ctl->wsp[tid] = 0;
   __syncthreads();
   if (n == 0) {
@@ -137,10 +140,12 @@ __global__ void __launch_bounds__(SM_THREADS) k_smem_build(SmemArgs a) {
   cx.slot_limit = 2 * n;
   Task root{0, (uint16_t)n, 0, 0, 0, seg.depth, seg.root};
   run_team_tasks<false, D>(cx, root, q.whist, q.wred, q.wstack, SM_NW);
+  __syncthreads();
+  if (tid == 0) atomicMax(&a.st->max_depth, q.ctl->maxd);
 }
 
 template <int D>
-__global__ void __launch_bounds__(SM_THREADS) k_smem_skel(SmemArgs a) {
+__global__ void __launch_bounds__(SM_THREADS, 1) k_smem_skel(SmemArgs a) {
   if (blockIdx.x >= *a.njobs) return;
   extern __shared__ __align__(16) uint8_t sm[];
   const SkelJob jb = a.jobs[blockIdx.x];
@@ -203,9 +208,7 @@ __host__ __device__ inline WarpLayout warp_layout(int wcap, int d) {
 int warp_cap_for(int d) { return d <= 4 ? 512 : 256; }
 
 template <int D>
-__global__ void __launch_bounds__(WK_WARPS * 32) k_smem_warp(SmemArgs a) {
-  const uint32_t sid = blockIdx.x * WK_WARPS + warp_id();
-  if (sid >= *a.nsegs) return;  // warp-uniform
+__global__ void __launch_bounds__(WK_WARPS * 32, 4) k_smem_warp(SmemArgs a) {
   extern __shared__ __align__(16) uint8_t sm[];
   const int cap = a.cap, lane = lane_id();
   const WarpLayout Lo = warp_layout(cap, D);
@@ -220,28 +223,37 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_smem_warp(SmemArgs a) {
   q.wred = nullptr;
   q.wstack = (Task*)(base + Lo.stack);
   q.ctl = (SmemCtl*)(base + Lo.ctl);
-  const Seg seg = a.segs[sid];
-  if (seg.len > (uint32_t)cap) {
-    if (lane == 0) set_error(a.st, DERR_CAPACITY, 250000);
-    return;
-  }
-  const int n = (int)seg.len;
-  load_segment<D>(a, seg, q.X, q.ID, q.perm0, cap, lane, 32);
-  if (lane == 0) q.ctl->next_slot = 0;
+  const uint32_t nsegs = *a.nsegs;
+  if (lane == 0) q.ctl->maxd = 0;
   __syncwarp();
-  if (n == 0) {
-    if (lane == 0) {
-      a.nodes[seg.root] = Node{0, 0, (uint32_t)seg.start, 0};
-      a.ndim[seg.root] = PKD_LEAF;
+  // every warp takes segments in turn (a grid of a few CTAs per SM)
+  for (uint32_t sid = blockIdx.x * WK_WARPS + warp_id(); sid < nsegs; sid += gridDim.x * WK_WARPS) {
+    const Seg seg = a.segs[sid];
+    if (seg.len > (uint32_t)cap) {
+      if (lane == 0) set_error(a.st, DERR_CAPACITY, 250000);
+      return;
     }
-    return;
+    const int n = (int)seg.len;
+    __syncwarp();
+    load_segment<D>(a, seg, q.X, q.ID, q.perm0, cap, lane, 32);
+    if (lane == 0) q.ctl->next_slot = 0;
+    __syncwarp();
+    if (n == 0) {
+      if (lane == 0) {
+        a.nodes[seg.root] = Node{0, 0, (uint32_t)seg.start, 0};
+        a.ndim[seg.root] = PKD_LEAF;
+      }
+      continue;
+    }
+    SmemCtx<D> cx = make_ctx<D>(a, q, cap);
+    cx.start = seg.start;
+    cx.slot_base = (uint32_t)(a.shared_cap + 2 * seg.start);
+    cx.slot_limit = 2 * n;
+    const Team wt{warp_id(), 1, 0, q.whist, nullptr};
+    warp_run<false, D>(wt, cx, Task{0, (uint16_t)n, 0, 0, 0, seg.depth, seg.root}, q.wstack, 0);
   }
-  SmemCtx<D> cx = make_ctx<D>(a, q, cap);
-  cx.start = seg.start;
-  cx.slot_base = (uint32_t)(a.shared_cap + 2 * seg.start);
-  cx.slot_limit = 2 * n;
-  const Team wt{warp_id(), 1, 0, q.whist, nullptr};
-  warp_run<false, D>(wt, cx, Task{0, (uint16_t)n, 0, 0, 0, seg.depth, seg.root}, q.wstack, 0);
+  __syncwarp();
+  if (lane == 0) atomicMax(&a.st->max_depth, q.ctl->maxd);
 }
 
 template <int D>
@@ -837,6 +849,17 @@ static int smem_optin() {
   return v;
 }
 
+static int num_sms() {
+  static int v = -1;
+  if (v < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (v <= 0) v = 152;
+  }
+  return v;
+}
+
 static int cap_for_bytes(int d, size_t budget) {
   int lo = 64, hi = 65535;
   while (lo < hi) {
@@ -1154,7 +1177,8 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     const size_t smb = warp_layout(wa.cap, d).per_warp * WK_WARPS;
     KTimer kt;
     ktimer_begin(kt, "smem_warp", pass == 0 ? warp_pts : tiny_pts, s);
-    PKD_DISPATCH_D(d, launch_smem_warp, wa, (nw + WK_WARPS - 1) / WK_WARPS, smb, s);
+    const uint32_t blocks = std::min<uint32_t>((nw + WK_WARPS - 1) / WK_WARPS, (uint32_t)(num_sms() * 8));
+    PKD_DISPATCH_D(d, launch_smem_warp, wa, blocks, smb, s);
     ktimer_end(kt);
   }
   if (nbase > 0) {

@@ -17,7 +17,8 @@ constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_TILE = SCAN_ITEMS * SCAN_THREADS;
 constexpr int JOB_TILE = 2048;
 constexpr int JOB_THREADS = 256;
-constexpr int SIEVE_THREADS = 512;
+constexpr int SIEVE_THREADS = 1024;
+constexpr int SIEVE_PER = 4;  // points per thread: TILE <= SIEVE_PER * SIEVE_THREADS
 
 struct Src {
   Pts soa;
@@ -231,16 +232,21 @@ __global__ void __launch_bounds__(SIEVE_THREADS) k_count(RoundArgs r) {
   __syncthreads();
   const bool heavy = sk_state(sk[1].y) == SK_HEAVY;
   if (!heavy) {
-    for (int base = 0; base < t.cnt; base += blockDim.x) {
-      const int i = base + threadIdx.x;
-      int b = -1;
+    // all of this thread's loads first, then the walks (loads stay in flight)
+    int32_t x[SIEVE_PER][D];
+#pragma unroll
+    for (int k = 0; k < SIEVE_PER; ++k) {
+      const int i = k * SIEVE_THREADS + threadIdx.x;
       if (i < t.cnt) {
-        int32_t x[D];
         const uint64_t g = t.seg.start + t.first + i;
 #pragma unroll
-        for (int j = 0; j < D; ++j) x[j] = r.src.x(D, j, g);
-        b = walk_bucket<D>(sk, x, r.lam);
+        for (int j = 0; j < D; ++j) x[k][j] = r.src.x(D, j, g);
       }
+    }
+#pragma unroll
+    for (int k = 0; k < SIEVE_PER; ++k) {
+      const int i = k * SIEVE_THREADS + threadIdx.x;
+      const int b = i < t.cnt ? walk_bucket<D>(sk, x[k], r.lam) : -1;
       const unsigned m = __match_any_sync(FULL_MASK, b);
       if (b >= 0 && lane_id() == __ffs(m) - 1) atomicAdd(&lh[b], (unsigned)__popc(m));
     }
@@ -268,22 +274,25 @@ __global__ void __launch_bounds__(SIEVE_THREADS) k_scatter(RoundArgs r) {
   for (int b = threadIdx.x; b < r.NB; b += blockDim.x) cur[b] = 0;
   __syncthreads();
   if (sk_state(sk[1].y) == SK_HEAVY) return;
-  constexpr int PER = 8;  // TILE <= PER * SIEVE_THREADS
+  constexpr int PER = SIEVE_PER;
   int32_t x[PER][D];
   uint32_t id[PER];
   int bk[PER], rk[PER];
+  // all of this thread's loads first, then the walks (loads stay in flight)
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
     const int i = k * SIEVE_THREADS + threadIdx.x;
-    bk[k] = -1;
-    rk[k] = 0;
     if (i < t.cnt) {
       const uint64_t g = t.seg.start + t.first + i;
 #pragma unroll
       for (int j = 0; j < D; ++j) x[k][j] = r.src.x(D, j, g);
       id[k] = r.src.id(g);
-      bk[k] = walk_bucket<D>(sk, x[k], r.lam);
     }
+  }
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int i = k * SIEVE_THREADS + threadIdx.x;
+    bk[k] = i < t.cnt ? walk_bucket<D>(sk, x[k], r.lam) : -1;
     const unsigned m = __match_any_sync(FULL_MASK, bk[k]);
     const int leader = __ffs(m) - 1;
     unsigned base = 0;

@@ -38,6 +38,7 @@ static_assert(sizeof(Task) == 16, "Task layout");
 
 struct SmemCtl {
   int next_slot;
+  unsigned maxd;   // deepest leaf written by this CTA (or warp)
   int wsp[SM_NW];  // per-warp stack depth
 };
 
@@ -144,7 +145,7 @@ struct SmemCtx {
 // ---------------------------------------------------------------------------
 
 template <int D>
-__device__ void emit_leaf(const Team& tm, const SmemCtx<D>& cx, const Task& tk) {
+__device__ __forceinline__ void emit_leaf(const Team& tm, const SmemCtx<D>& cx, const Task& tk) {
   const uint16_t* P = cx.perm[tk.buf];
   for (int i = tk.lo + tm.rank(); i < tk.hi; i += tm.size()) {
     const int p = P[i];
@@ -161,8 +162,147 @@ __device__ void emit_leaf(const Team& tm, const SmemCtx<D>& cx, const Task& tk) 
     nd.b = 0;
     cx.nodes[tk.slot] = nd;
     cx.ndim[tk.slot] = PKD_LEAF;
-    atomicMax(&cx.st->max_depth, tk.t);
+    atomicMax(&cx.ctl->maxd, tk.t);  // published once per CTA / warp
   }
+}
+
+// A Build root of at most 128 points handled by one warp entirely in
+// registers (each lane holds up to 4 points): min/max, the sample count,
+// the element of rank floor(n/2) by broadcast rank counting, and the stable
+// partition by ballots.  Returns -1 when the rules call for a skeleton split
+// on the sample (the generic path then takes over), otherwise the number of
+// children like process_build.
+constexpr int REG_MAX = 128;
+
+template <int D>
+__device__ __forceinline__ int warp_small_build(const Team& tm, const SmemCtx<D>& cx, const Task& tk, Task* ch) {
+  constexpr int Q = REG_MAX / 32;
+  const int lane = lane_id();
+  const int lo = tk.lo, hi = tk.hi, n = hi - lo;
+  const uint16_t* P = cx.perm[tk.buf];
+  uint16_t* Qp = cx.perm[tk.buf ^ 1];
+  int p[Q];
+  int32_t x[Q][D];
+  bool valid[Q];
+  int mn[D], mx[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    mn[j] = INT32_MAX;
+    mx[j] = INT32_MIN;
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int i = lo + q * 32 + lane;
+    valid[q] = i < hi;
+    p[q] = valid[q] ? P[i] : 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      x[q][j] = valid[q] ? cx.s.x(j, p[q]) : 0;
+      if (valid[q]) {
+        mn[j] = min(mn[j], x[q][j]);
+        mx[j] = max(mx[j], x[q][j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    mn[j] = warp_min(mn[j]);
+    mx[j] = warp_max(mx[j]);
+  }
+  int vmin, vmax;
+  const int wd = widest_dim<D>(mn, mx, vmin, vmax);
+  if (wd < 0) {  // heavy leaf
+    emit_leaf<D>(tm, cx, tk);
+    return 0;
+  }
+  if (n >= 2 * cx.p.sigma_os) {
+    // draw the sample; with enough samples the node is a skeleton node
+    const int shift = sample_shift(cx.p, (uint64_t)n);
+    int ns = 0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const bool f = valid[q] && in_sample(cx.p.seed, tk.t, cx.s.ID[p[q]], shift);
+      if (valid[q]) cx.flag[p[q]] = f;
+      ns += __popc(__ballot_sync(FULL_MASK, f));
+    }
+    __syncwarp();
+    if (ns >= 2 * cx.p.sigma_os) return -1;
+  }
+  // element of rank k = floor(n/2) on dimension wd
+  int key[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    int v = x[q][0];
+#pragma unroll
+    for (int j = 1; j < D; ++j)
+      if (j == wd) v = x[q][j];
+    key[q] = valid[q] ? v : INT32_MAX;
+  }
+  int less[Q], leq[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) less[q] = leq[q] = 0;
+#pragma unroll
+  for (int qs = 0; qs < Q; ++qs) {
+    if (qs * 32 >= n) break;
+    for (int sl = 0; sl < 32; ++sl) {
+      const int v = __shfl_sync(FULL_MASK, key[qs], sl);
+      const bool ok = qs * 32 + sl < n;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        less[q] += ok && v < key[q];
+        leq[q] += ok && v <= key[q];
+      }
+    }
+  }
+  const int k = n / 2;
+  int cand = INT32_MAX, cless = 0;
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+    if (valid[q] && less[q] <= k && k < leq[q]) {
+      cand = key[q];
+      cless = less[q];
+    }
+  int xsplit = warp_min(cand);
+  int count_less = warp_max(cand == xsplit ? cless : -1);
+  if (count_less == 0) {  // nothing strictly below: the next distinct value
+    int m = INT32_MAX;
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+      if (valid[q] && key[q] > xsplit) m = min(m, key[q]);
+    xsplit = warp_min(m);
+  }
+  // stable partition: left (key < xsplit) first, original order kept
+  int L = 0;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) L += __popc(__ballot_sync(FULL_MASK, valid[q] && key[q] < xsplit));
+  int lpos = lo, rpos = lo + L;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const bool left = valid[q] && key[q] < xsplit;
+    const unsigned bl = __ballot_sync(FULL_MASK, left);
+    const unsigned br = __ballot_sync(FULL_MASK, valid[q] && !left);
+    if (left) Qp[lpos + __popc(bl & lanemask_lt())] = (uint16_t)p[q];
+    else if (valid[q]) Qp[rpos + __popc(br & lanemask_lt())] = (uint16_t)p[q];
+    lpos += __popc(bl);
+    rpos += __popc(br);
+  }
+  __syncwarp();
+  int b = 0;
+  if (lane == 0) b = atomicAdd(&cx.ctl->next_slot, 2);
+  b = __shfl_sync(FULL_MASK, b, 0);
+  if (b + 2 > cx.slot_limit || L <= 0 || L >= n) {
+    if (lane == 0) set_error(cx.st, b + 2 > cx.slot_limit ? DERR_SLOT : DERR_STATE, 150 + L);
+    return 0;
+  }
+  const uint32_t sl = cx.slot_base + (uint32_t)b, sr = sl + 1;
+  if (lane == 0) {
+    cx.nodes[tk.slot] = Node{xsplit, (uint32_t)n, sl, sr};
+    cx.ndim[tk.slot] = (uint8_t)wd;
+  }
+  const uint8_t nb = (uint8_t)(tk.buf ^ 1);
+  ch[0] = Task{(uint16_t)lo, (uint16_t)(lo + L), 0, nb, 0, tk.t + 1, sl};
+  ch[1] = Task{(uint16_t)(lo + L), (uint16_t)hi, 0, nb, 0, tk.t + 1, sr};
+  return 2;
 }
 
 // Process one node; returns the number of children written to ch (0 or 2).
@@ -170,6 +310,10 @@ template <int D>
 __device__ int process_build(const Team& tm, const SmemCtx<D>& cx, Task tk, Task* ch) {
   for (;;) {
     const int lo = tk.lo, hi = tk.hi, n = hi - lo;
+    if (tm.nw == 1 && tk.j == 0 && n > cx.p.phi && n <= REG_MAX) {
+      const int r = warp_small_build<D>(tm, cx, tk, ch);
+      if (r >= 0) return r;
+    }
     uint16_t* P = cx.perm[tk.buf];
     uint16_t* Q = cx.perm[tk.buf ^ 1];
     int dim = 0, x = 0;
@@ -288,11 +432,13 @@ __device__ __forceinline__ int process_task(const Team& tm, const SmemCtx<D>& cx
 template <bool SKEL, int D>
 __device__ void warp_run(const Team& wt, const SmemCtx<D>& cx, Task tk, Task* stk, int sp0) {
   int sp = sp0;
-  for (;;) {
+  for (int iter = 1;; ++iter) {
     Task ch[2];
     const int nch = process_task<SKEL, D>(wt, cx, tk, ch);
-    const int err = *(volatile int*)&cx.st->err;
-    if (__shfl_sync(FULL_MASK, err, 0)) return;  // warp-uniform exit
+    if ((iter & 15) == 0 || nch == 0) {
+      const int err = *(volatile int*)&cx.st->err;
+      if (__shfl_sync(FULL_MASK, err, 0)) return;  // warp-uniform exit
+    }
     if (nch == 2) {
       const int s0 = ch[0].hi - ch[0].lo, s1 = ch[1].hi - ch[1].lo;
       const Task big = s0 >= s1 ? ch[0] : ch[1];

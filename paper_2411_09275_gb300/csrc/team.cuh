@@ -111,7 +111,7 @@ struct SmemPts {
 // Min and max of every dimension over idx[lo, hi) (only flagged points when
 // `sampled_only`).  Results are valid in every thread of the team.
 template <int D>
-__device__ void team_minmax(const Team& tm, const SmemPts<D>& s, const uint16_t* idx, int lo, int hi,
+__device__ __forceinline__ void team_minmax(const Team& tm, const SmemPts<D>& s, const uint16_t* idx, int lo, int hi,
                             bool sampled_only, int* mn, int* mx) {
   int lmn[D], lmx[D];
 #pragma unroll
@@ -232,6 +232,54 @@ __device__ __forceinline__ void warp_find_digit(const unsigned* hist, int k, int
   eq = __shfl_sync(FULL_MASK, e, src);
 }
 
+// Single-warp variant of team_select with 5-bit digits: the 32 counters are
+// one per lane, so clearing them is one store and finding the digit is one
+// warp scan (small subproblems are dominated by these fixed costs).
+template <int D>
+__device__ __forceinline__ int warp_select32(const Team& tm, const SmemPts<D>& s, const uint16_t* idx, int lo,
+                                             int hi, bool sampled_only, int dim, int k, int vmin, int vmax,
+                                             int& count_less, int& count_eq) {
+  const int32_t* X = s.X + dim * s.cap;
+  const int lane = lane_id();
+  const int hb = 31 - __clz((unsigned)(vmin ^ vmax));
+  unsigned mask = hb >= 31 ? 0u : ~((2u << hb) - 1u);
+  unsigned prefix = (unsigned)vmin & mask;
+  int less = 0, eq = 0;
+  for (int top = hb; top >= 0; top -= 5) {
+    const int shift = max(top - 4, 0);
+    const unsigned dmask = (2u << (top - shift)) - 1u;
+    tm.hist[lane] = 0;
+    __syncwarp();
+    for (int base = lo; base < hi; base += 32) {
+      const int i = base + lane;
+      int key = -1;
+      if (i < hi) {
+        const int p = idx[i];
+        const unsigned v = (unsigned)X[p];
+        if ((!sampled_only || s.flag[p]) && (v & mask) == prefix) key = (int)((v >> shift) & dmask);
+      }
+      const unsigned m = __match_any_sync(FULL_MASK, key);
+      if (key >= 0 && lane == __ffs(m) - 1) atomicAdd(&tm.hist[key], (unsigned)__popc(m));
+    }
+    __syncwarp();
+    const int c = (int)tm.hist[lane];
+    const int incl = warp_incl_scan(c);
+    const int excl = incl - c;
+    const unsigned hit = __ballot_sync(FULL_MASK, excl <= k && k < incl);
+    const int digit = hit ? __ffs(hit) - 1 : 0;
+    const int below = __shfl_sync(FULL_MASK, excl, digit);
+    eq = __shfl_sync(FULL_MASK, c, digit);
+    __syncwarp();
+    prefix |= (unsigned)digit << shift;
+    mask |= dmask << shift;
+    k -= below;
+    less += below;
+  }
+  count_less = less;
+  count_eq = eq;
+  return (int)prefix;
+}
+
 // The element of rank k (0-based) of dimension `dim` over idx[lo, hi)
 // (flagged points only when `sampled_only`), with count_less / count_eq =
 // how many of those elements are below / equal to it.
@@ -242,9 +290,11 @@ __device__ __forceinline__ void warp_find_digit(const unsigned* hist, int k, int
 // spreads over the bins instead of piling every element onto one counter).
 // Counter updates are aggregated per warp over lanes that hit the same bin.
 template <int D>
-__device__ int team_select(const Team& tm, const SmemPts<D>& s, const uint16_t* idx, int lo, int hi,
+__device__ __forceinline__ int team_select(const Team& tm, const SmemPts<D>& s, const uint16_t* idx, int lo, int hi,
                            bool sampled_only, int dim, int k, int vmin, int vmax, int& count_less,
                            int& count_eq) {
+  if (tm.nwarps() == 1)
+    return warp_select32<D>(tm, s, idx, lo, hi, sampled_only, dim, k, vmin, vmax, count_less, count_eq);
   const int32_t* X = s.X + dim * s.cap;
   const int hb = 31 - __clz((unsigned)(vmin ^ vmax));  // highest differing bit
   unsigned mask = hb >= 31 ? 0u : ~((2u << hb) - 1u);
@@ -300,7 +350,7 @@ __device__ int team_select(const Team& tm, const SmemPts<D>& s, const uint16_t* 
 
 // Smallest value of dimension `dim` strictly above `x` over idx[lo, hi).
 template <int D>
-__device__ int team_min_above(const Team& tm, const SmemPts<D>& s, const uint16_t* idx, int lo, int hi,
+__device__ __forceinline__ int team_min_above(const Team& tm, const SmemPts<D>& s, const uint16_t* idx, int lo, int hi,
                               bool sampled_only, int dim, int x) {
   int m = INT32_MAX;
   for (int i = lo + tm.rank(); i < hi; i += tm.size()) {
@@ -317,7 +367,7 @@ __device__ int team_min_above(const Team& tm, const SmemPts<D>& s, const uint16_
 // nothing lies below it.  With the min/max already known (mn/mx valid), the
 // min/max pass is skipped.  Returns false when the points are all identical.
 template <int D>
-__device__ bool team_split_rule(const Team& tm, const SmemPts<D>& s, const uint16_t* idx, int lo, int hi,
+__device__ __forceinline__ bool team_split_rule(const Team& tm, const SmemPts<D>& s, const uint16_t* idx, int lo, int hi,
                                 bool sampled_only, int count, const int* mn_in, const int* mx_in, int& dim,
                                 int& x) {
   int mn[D], mx[D];
@@ -343,7 +393,7 @@ __device__ bool team_split_rule(const Team& tm, const SmemPts<D>& s, const uint1
 // `dim` below x first.  Returns the left count and the flagged counts on
 // each side.
 template <int D>
-__device__ void team_partition(const Team& tm, const SmemPts<D>& s, const uint16_t* src, uint16_t* dst,
+__device__ __forceinline__ void team_partition(const Team& tm, const SmemPts<D>& s, const uint16_t* src, uint16_t* dst,
                                int lo, int hi, int dim, int x, int& L, int& SL, int& SR) {
   const int32_t* X = s.X + dim * s.cap;
   const int n = hi - lo;
@@ -411,7 +461,7 @@ __device__ void team_partition(const Team& tm, const SmemPts<D>& s, const uint16
 
 // Set flag[p] = sampled(seed, depth, id, s) for idx[lo, hi); returns the count.
 template <int D>
-__device__ int team_draw_sample(const Team& tm, const SmemPts<D>& s, uint8_t* flag, const uint16_t* idx,
+__device__ __forceinline__ int team_draw_sample(const Team& tm, const SmemPts<D>& s, uint8_t* flag, const uint16_t* idx,
                                 int lo, int hi, uint64_t seed, uint32_t depth, int shift) {
   int c = 0;
   for (int i = lo + tm.rank(); i < hi; i += tm.size()) {

@@ -108,6 +108,33 @@ int pkd_batch_delete(pkd_tree* tree, const int32_t* coords, const uint32_t* ids,
 int pkd_knn(const pkd_tree* tree, const int32_t* queries, uint64_t q, int k, uint32_t* out_ids,
             int64_t* out_d2, void* stream);
 
+/* k-NN ids that allocate nothing (the paper has no counterpart): the same
+ * search and the same out_ids as pkd_knn, for callers that may not allocate
+ * device memory during the call (a server that has given its spare memory
+ * to its trees and may not let a pool grow mid-request, or one that wants no
+ * allocator or mapping work in a query's latency).  The coordinate-check
+ * flag and the k distances per query live in one fixed scratch array
+ * compiled into the library (one per device), so
+ *   - q * k must not exceed PKD_NOALLOC_MAX_PAIRS (8 MiB of distances);
+ *     larger batches return PKD_EINVAL with a message on stderr (split
+ *     them, or use pkd_knn);
+ *   - the call must run on the tree's device (the current device);
+ *   - calls whose device work overlaps (other streams, other host threads)
+ *     race on the scratch; calls one after another on one stream do not;
+ *   - the first call on a device resolves the scratch address, which may
+ *     load the library's kernels on that device: make it before any region
+ *     in which the caller may not allocate.
+ * The call synchronises `stream` once (after the coordinate check) and
+ * returns with the search queued on it; out_ids is valid once `stream` has
+ * been synchronised.
+ *   queries  device, [q][d] int32 in [0, 2^30);  k  in 1..128
+ *   out_ids  device, [q][k] uint32 (as pkd_knn)
+ * Errors: PKD_EINVAL (k, q * k, coordinates, wrong device), PKD_ECUDA,
+ * PKD_EINTERNAL. */
+#define PKD_NOALLOC_MAX_PAIRS (1u << 20)
+int pkd_knn_ids_noalloc(const pkd_tree* tree, const int32_t* queries, uint64_t q, int k,
+                        uint32_t* out_ids, void* stream);
+
 /* Range count (Sec. 5): for each closed box lo[i][j] <= x_j <= hi[i][j],
  * the number of stored points inside; a subtree whose subspace lies inside
  * the box adds its stored size.

@@ -6,6 +6,8 @@
 // splitters above it, as the paper does instead of keeping bounding boxes.
 // One thread per query; the stack holds at most height + 1 entries.
 #include <algorithm>
+#include <cstdio>
+#include <mutex>
 
 #include "engine.hpp"
 #include "tree_impl.hpp"
@@ -292,3 +294,116 @@ int pkd_range_count(const pkd_tree* tc, const int32_t* lo, const int32_t* hi, ui
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------
+// k-NN ids without any allocation (the paper has no counterpart)
+// ----------------------------------------------------------------------------
+// pkd_knn takes a status word from the library's memory pool for its
+// coordinate check and needs a caller buffer for the distances.  Some callers
+// can do neither: a server that has handed all spare device memory to its
+// trees and may not let a pool grow while a request is in flight, or one that
+// needs the latency of a query call free of allocator and mapping work.  This
+// variant keeps both in a fixed scratch array compiled into the library:
+//
+//   bytes [0, 4)                          coordinate-check flag; must be zero
+//                                         when the check kernel starts (each
+//                                         call clears it on its stream first)
+//   bytes [256, 256 + 8 * q * k)          the k distances of every query; no
+//                                         initial value needed (written by
+//                                         the search before anything reads it)
+//
+// The scratch is one array per device, shared by every call: two calls whose
+// work overlaps on the device (different streams, or different host threads)
+// race on it.  Calls issued one after the other on one stream are ordered.
+// The first call on a device resolves the array's address (which loads the
+// module on that device if it is not loaded yet); make that call before any
+// region in which the caller may not allocate.
+
+namespace pkd {
+
+static __device__ __align__(256) unsigned char g_knn_noalloc_scratch[256 + 8 * (uint64_t)PKD_NOALLOC_MAX_PAIRS];
+
+__global__ void k_noalloc_check(const int32_t* c, uint64_t cnt, unsigned* bad) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  int b = 0;
+  for (; i < cnt; i += stride) {
+    const int32_t v = c[i];
+    b |= (v < 0) | (v >= PKD_COORD_LIMIT);
+  }
+  if (__any_sync(0xffffffffu, b) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
+}
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static std::mutex g_noalloc_mu;
+static unsigned char* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Set-up, once per device, with that device current: the scratch address.
+static int noalloc_scratch(int dev, unsigned char** out) {
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_knn_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      fprintf(stderr, "pkd_knn_ids_noalloc: scratch address on device %d: %s\n", dev,
+              cudaGetErrorString(e));
+      return e != cudaSuccess ? cuda_err(e) : PKD_ECUDA;
+    }
+    g_noalloc_ptr[dev] = (unsigned char*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return PKD_OK;
+}
+
+template <int D>
+static void launch_knn_noalloc(const QueryArgs& a, cudaStream_t s) {
+  const unsigned g = (unsigned)((a.nq + QTHREADS - 1) / QTHREADS);
+  if (a.k <= 16) PKD_LAUNCH(k_knn<D, 16><<<g, QTHREADS, 0, s>>>(a));
+  else PKD_LAUNCH(k_knn<D, 128><<<g, QTHREADS, 0, s>>>(a));
+}
+
+}  // namespace pkd
+
+extern "C" int pkd_knn_ids_noalloc(const pkd_tree* tc, const int32_t* queries, uint64_t q, int k,
+                                   uint32_t* out_ids, void* stream) {
+  if (!tc || k < 1 || k > 128) return PKD_EINVAL;
+  if (q == 0) return PKD_OK;
+  if (!queries || !out_ids) return PKD_EINVAL;
+  if (q > (uint64_t)PKD_NOALLOC_MAX_PAIRS / (uint64_t)k) {
+    fprintf(stderr,
+            "pkd_knn_ids_noalloc: q*k = %llu exceeds the fixed scratch of %llu (query, neighbour) "
+            "pairs; split the batch or use pkd_knn\n",
+            (unsigned long long)q * (unsigned long long)k, (unsigned long long)PKD_NOALLOC_MAX_PAIRS);
+    return PKD_EINVAL;
+  }
+  TreeMem& t = const_cast<TreeMem&>(tc->m);
+  int dev = -1;
+  PKD_CUDA(cudaGetDevice(&dev));
+  if (dev != t.device || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return PKD_EINVAL;
+  unsigned char* scratch = nullptr;
+  PKD_TRY_(noalloc_scratch(dev, &scratch));
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned* bad = (unsigned*)scratch;
+  PKD_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned), s));
+  PKD_LAUNCH(k_noalloc_check<<<152 * 8, 256, 0, s>>>(queries, q * (uint64_t)t.p.d, bad));
+  unsigned h = 0;
+  PKD_CUDA(cudaMemcpyAsync(&h, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  PKD_CUDA(cudaStreamSynchronize(s));
+  if (h != 0) return PKD_EINVAL;
+  PKD_TRY_(check_status(t, s));
+  if (!query_height_ok(t)) return PKD_EINTERNAL;
+  QueryArgs a{};
+  a.nodes = t.nodes;
+  a.ndim = t.ndim;
+  a.A = t.A;
+  a.root = t.root;
+  a.q = queries;
+  a.nq = q;
+  a.k = k;
+  a.out_ids = out_ids;
+  a.out_d2 = (int64_t*)(scratch + 256);
+  a.st = t.st;
+  PKD_QDISPATCH(t.p.d, launch_knn_noalloc, a, s);
+  PKD_CUDA(cudaGetLastError());
+  return PKD_OK;
+}

@@ -69,6 +69,7 @@ def lib():
         L.pkd_batch_delete.argtypes = [vp, vp, vp, u64, P(u64), vp]
         L.pkd_knn.argtypes = [vp, vp, u64, i32, vp, vp, vp]
         L.pkd_range_count.argtypes = [vp, vp, vp, u64, vp, vp]
+        L.pkd_knn_ids_noalloc.argtypes = [vp, vp, u64, i32, vp, vp]
         L.pkd_export.argtypes = [vp, vp, vp, vp, P(u64), vp, vp, P(u64)]
         L.pkd_size.restype = u64
         L.pkd_size.argtypes = [vp]
@@ -81,7 +82,7 @@ def lib():
         L.pkd_kernel_timing.argtypes = [i32]
         L.pkd_kernel_stats.argtypes = [C.c_char_p, P(u64), P(C.c_double), P(u64)]
         for f in ("pkd_build", "pkd_batch_insert", "pkd_batch_delete", "pkd_knn", "pkd_range_count",
-                  "pkd_export", "pkd_height", "pkd_set_option", "pkd_kernel_timing",
+                  "pkd_knn_ids_noalloc", "pkd_export", "pkd_height", "pkd_set_option", "pkd_kernel_timing",
                   "pkd_kernel_stats"):
             getattr(L, f).restype = i32
         _lib = L
@@ -140,6 +141,12 @@ def pkd_knn(tree, queries: torch.Tensor, k: int, out_ids: torch.Tensor, out_d2: 
             stream=None):
     _check(lib().pkd_knn(tree, _dptr(queries), queries.shape[0], k, _dptr(out_ids), _dptr(out_d2),
                          _stream(stream)), "pkd_knn")
+
+
+def pkd_knn_ids_noalloc(tree, queries: torch.Tensor, k: int, out_ids: torch.Tensor, stream=None):
+    """k-NN ids through the library's fixed scratch (no allocation in the call)."""
+    _check(lib().pkd_knn_ids_noalloc(tree, _dptr(queries), queries.shape[0], k, _dptr(out_ids),
+                                     _stream(stream)), "pkd_knn_ids_noalloc")
 
 
 def pkd_range_count(tree, lo: torch.Tensor, hi: torch.Tensor, out: torch.Tensor, stream=None):

@@ -35,9 +35,9 @@ METRIC = "Pkd-tree build Mpts/s + % HBM roofline; batch-update Mpts/s; p99 reque
 PEAK_FALLBACK_GBS = 6800.0
 
 WORKLOADS = {
-    # configs[1]: build 1e8 3-D uniform, insert 1e7, delete 1e7 random existing ids
+    # build 1e8 3-D uniform points, insert 1e7 new ones, delete 1e7 random existing ids
     "build1e8_d3_ins1e7_del1e7": dict(n=100_000_000, d=3, m=10_000_000, kind="uniform"),
-    # configs[0] at full size (fits in L2: roofline not claimed)
+    # build 1e6 2-D uniform points, insert and delete 1e4 (fits in L2: roofline not claimed)
     "build1e6_d2_ins1e4_del1e4": dict(n=1_000_000, d=2, m=10_000, kind="uniform"),
     # small case for quick checks
     "build1e7_d3_ins1e6_del1e6": dict(n=10_000_000, d=3, m=1_000_000, kind="uniform"),

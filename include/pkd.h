@@ -7,8 +7,9 @@
  *
  * Conventions for every entry point:
  *  - Points have d int32 coordinates in [0, 2^30) stored point-major
- *    (coords[i*d + j]) and a uint32 id.  Coordinates outside that range are
- *    rejected with PKD_EINVAL.
+ *    (coords[i*d + j]) and a uint32 id.  Builds, inserts and queries reject
+ *    coordinates outside that range with PKD_EINVAL; a delete entry outside
+ *    it matches no stored point and is skipped.
  *  - Point, query and result buffers are DEVICE pointers owned by the
  *    caller, except in pkd_export (host buffers).  The library copies what it
  *    keeps; input buffers may be reused once the call has returned.
@@ -72,7 +73,8 @@ typedef struct {
  * sieve into 2^lambda buckets, recurse; leaves of at most phi points).
  *   coords  device, [n][d] int32
  *   ids     device, [n] uint32, or NULL for ids 0..n-1
- *   n       number of points, < 2^32 - 1 (0 gives an empty tree)
+ *   n       number of points, < 2^31 (0 gives an empty tree); the tree
+ *           holds fewer than 2^31 points after any insert
  *   out     receives the new tree (owns all device memory it allocates)
  * Errors: PKD_EINVAL (parameters, n, coordinates), PKD_ENOMEM, PKD_ECUDA. */
 int pkd_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const pkd_params* params,
@@ -169,6 +171,9 @@ const char* pkd_strerror(int code);
  *                (0 = derived from d and the shared-memory size)
  *   "skel_cap"   largest sample handled by one CTA when building a skeleton
  *   "tile"       points per CTA in the sieve kernels
+ *   "base_kernel" shared-memory base case: 0 sorts each subproblem once per
+ *                dimension and splits by lookups (default), 1 selects every
+ *                splitter by a radix select
  * Returns PKD_EINVAL for an unknown name or an out-of-range value. */
 int pkd_set_option(const char* name, int64_t value);
 

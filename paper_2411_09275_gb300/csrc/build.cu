@@ -24,6 +24,7 @@
 #include <cstring>
 
 #include "sieve.cuh"
+#include "smem_sorted.cuh"
 
 namespace pkd {
 
@@ -142,6 +143,117 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_smem_build(SmemArgs a) {
   run_team_tasks<false, D>(cx, root, q.whist, q.wred, q.wstack, SM_NW);
   __syncthreads();
   if (tid == 0) atomicMax(&a.st->max_depth, q.ctl->maxd);
+}
+
+// The base case on presorted lists (one CTA per segment of at most cap
+// points): load, sort every dimension once, then split by lookups and stable
+// list partitions.
+template <int D>
+__global__ void __launch_bounds__(SS_THREADS, 1) k_smem_sorted(SmemArgs a) {
+  if (blockIdx.x >= *a.nsegs) return;
+  extern __shared__ __align__(16) uint8_t sm[];
+  const Seg seg = a.segs[blockIdx.x];
+  const int cap = a.cap, tid = threadIdx.x;
+  const SortedLayout Lo = sorted_layout(cap, D);
+  int32_t* X = (int32_t*)(sm + Lo.X);
+  uint32_t* ID = (uint32_t*)(sm + Lo.ID);
+  int* sred = (int*)(sm + Lo.red);
+  STask* wstack = (STask*)(sm + Lo.stack);
+  SmemCtl* ctl = (SmemCtl*)(sm + Lo.ctl);
+  if (seg.len > (uint32_t)cap) {
+    if (tid == 0) set_error(a.st, DERR_CAPACITY, 400000 + (int)blockIdx.x);
+    return;
+  }
+  const int n = (int)seg.len;
+  if (n == 0) {
+    if (tid == 0) {
+      a.nodes[seg.root] = Node{0, 0, (uint32_t)seg.start, 0};
+      a.ndim[seg.root] = PKD_LEAF;
+    }
+    return;
+  }
+  if (tid < D) {
+    sred[tid] = INT32_MAX;
+    sred[D + tid] = INT32_MIN;
+  }
+  if (tid == 0) {
+    ctl->next_slot = 0;
+    ctl->maxd = 0;
+  }
+  if (tid < SS_NW) ctl->wsp[tid] = 0;
+  __syncthreads();
+  int lmn[D], lmx[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    lmn[j] = INT32_MAX;
+    lmx[j] = INT32_MIN;
+  }
+  for (int i = tid; i < n; i += SS_THREADS) {
+    const uint64_t g = seg.start + (uint64_t)i;
+    int32_t v[D];
+    uint32_t id;
+    if (seg.where == IN_INPUT) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) v[j] = a.in_coords[g * (uint64_t)D + j];
+      id = a.in_ids ? a.in_ids[g] : (uint32_t)g;
+    } else {
+      const Pts& S = seg.where == IN_A ? a.A : a.B;
+#pragma unroll
+      for (int j = 0; j < D; ++j) v[j] = S.c[(uint64_t)j * S.stride + g];
+      id = S.id[g];
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      X[j * cap + i] = v[j];
+      lmn[j] = min(lmn[j], v[j]);
+      lmx[j] = max(lmx[j], v[j]);
+    }
+    ID[i] = id;
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    lmn[j] = warp_min(lmn[j]);
+    lmx[j] = warp_max(lmx[j]);
+  }
+  if (lane_id() == 0) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      atomicMin(&sred[j], lmn[j]);
+      atomicMax(&sred[D + j], lmx[j]);
+    }
+  }
+  __syncthreads();
+  int vmn[D], vmx[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    vmn[j] = sred[j];
+    vmx[j] = sred[D + j];
+  }
+  __syncthreads();
+  SCtx<D> cx;
+  cx.p = a.p;
+  cx.X = X;
+  cx.ID = ID;
+  cx.flag = sm + Lo.flag;
+  cx.lists = (uint16_t*)(sm + Lo.lists);
+  cx.cap = cap;
+  cx.ctl = ctl;
+  cx.out = a.A;
+  cx.start = seg.start;
+  cx.slot_base = (uint32_t)(a.shared_cap + 2 * seg.start);
+  cx.slot_limit = 2 * n;
+  cx.nodes = a.nodes;
+  cx.ndim = a.ndim;
+  cx.st = a.st;
+  unsigned* hist = (unsigned*)wstack;  // the task stacks are not in use yet
+#pragma unroll 1
+  for (int k = 0; k < D; ++k) presort_dim<D>(cx, k, vmn[k], vmx[k], n, hist, sred + 2 * D);
+  uint32_t map = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) map |= (uint32_t)k << (4 * k);
+  srun_tasks<D>(cx, STask{0, (uint16_t)n, 0, 0, 0, seg.depth, seg.root, map, 0}, sred, wstack);
+  __syncthreads();
+  if (tid == 0) atomicMax(&a.st->max_depth, ctl->maxd);
 }
 
 template <int D>
@@ -264,6 +376,16 @@ static void launch_smem_build(const SmemArgs& a, uint32_t nblocks, size_t smb, c
     set = (int)smb;
   }
   PKD_LAUNCH(k_smem_build<D><<<nblocks, SM_THREADS, smb, s>>>(a));
+}
+
+template <int D>
+static void launch_smem_sorted(const SmemArgs& a, uint32_t nblocks, size_t smb, cudaStream_t s) {
+  static int set = 0;
+  if (set < (int)smb) {
+    cudaFuncSetAttribute(k_smem_sorted<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+    set = (int)smb;
+  }
+  PKD_LAUNCH(k_smem_sorted<D><<<nblocks, SS_THREADS, smb, s>>>(a));
 }
 
 template <int D>
@@ -873,6 +995,15 @@ static int cap_for_bytes(int d, size_t budget) {
 int base_cap_for(int d) {
   if (knobs().base_cap > 0) return knobs().base_cap;
   const size_t budget = (size_t)std::min(smem_optin(), 200 * 1024);
+  if (knobs().base_kernel == 0) {
+    int lo = 64, hi = 16384;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (sorted_layout(mid, d).total <= budget) lo = mid;
+      else hi = mid - 1;
+    }
+    return lo & ~63;
+  }
   return std::min(cap_for_bytes(d, budget), 16384);
 }
 
@@ -1185,10 +1316,13 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     sa.segs = base_list;
     sa.nsegs = d_nbase;
     sa.cap = (int)cap;
-    const size_t smb = smem_layout((int)cap, d).total;
     KTimer kt;
     ktimer_begin(kt, "smem_build", cta_pts, s);
-    PKD_DISPATCH_D(d, launch_smem_build, sa, nbase, smb, s);
+    if (knobs().base_kernel == 0) {
+      PKD_DISPATCH_D(d, launch_smem_sorted, sa, nbase, sorted_layout((int)cap, d).total, s);
+    } else {
+      PKD_DISPATCH_D(d, launch_smem_build, sa, nbase, smem_layout((int)cap, d).total, s);
+    }
     ktimer_end(kt);
   }
   PKD_CUDA(cudaGetLastError());

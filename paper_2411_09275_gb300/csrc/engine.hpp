@@ -16,6 +16,7 @@ struct Knobs {
   int base_cap = 0;   // 0: derived from d and the shared memory per block
   int skel_cap = 0;   // 0: derived
   int tile = 4096;    // points per CTA in the sieve kernels
+  int base_kernel = 0;  // base case: 0 presorted lists, 1 radix select per node
 };
 Knobs& knobs();
 

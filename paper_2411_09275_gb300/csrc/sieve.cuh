@@ -247,8 +247,7 @@ __global__ void __launch_bounds__(SIEVE_THREADS) k_count(RoundArgs r) {
     for (int k = 0; k < SIEVE_PER; ++k) {
       const int i = k * SIEVE_THREADS + threadIdx.x;
       const int b = i < t.cnt ? walk_bucket<D>(sk, x[k], r.lam) : -1;
-      const unsigned m = __match_any_sync(FULL_MASK, b);
-      if (b >= 0 && lane_id() == __ffs(m) - 1) atomicAdd(&lh[b], (unsigned)__popc(m));
+      if (b >= 0) atomicAdd(&lh[b], 1u);
     }
   }
   __syncthreads();
@@ -293,7 +292,7 @@ __global__ void __launch_bounds__(SIEVE_THREADS) k_scatter(RoundArgs r) {
   for (int k = 0; k < PER; ++k) {
     const int i = k * SIEVE_THREADS + threadIdx.x;
     bk[k] = i < t.cnt ? walk_bucket<D>(sk, x[k], r.lam) : -1;
-    const unsigned m = __match_any_sync(FULL_MASK, bk[k]);
+    const unsigned m = peer_mask(bk[k], r.lam);
     const int leader = __ffs(m) - 1;
     unsigned base = 0;
     if (bk[k] >= 0 && lane_id() == leader) base = atomicAdd(&cur[bk[k]], (unsigned)__popc(m));

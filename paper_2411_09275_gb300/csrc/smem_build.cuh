@@ -435,7 +435,7 @@ __device__ void warp_run(const Team& wt, const SmemCtx<D>& cx, Task tk, Task* st
   for (int iter = 1;; ++iter) {
     Task ch[2];
     const int nch = process_task<SKEL, D>(wt, cx, tk, ch);
-    if ((iter & 15) == 0 || nch == 0) {
+    if ((iter & 63) == 0) {  // another CTA's failure ends this one early
       const int err = *(volatile int*)&cx.st->err;
       if (__shfl_sync(FULL_MASK, err, 0)) return;  // warp-uniform exit
     }

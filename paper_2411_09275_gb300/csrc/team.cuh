@@ -43,6 +43,36 @@ __device__ __forceinline__ int warp_incl_scan(int v) {
   return v;
 }
 
+// Lanes of the warp whose key equals this lane's, for keys in [0, 2^bits)
+// (a negative key means "no key"; such lanes get an unspecified mask).
+// One ballot per key bit instead of match.any, which on sm_103a issues at
+// one warp-instruction per 64 cycles per SM against about one per cycle for
+// a ballot.
+__device__ __forceinline__ unsigned peer_mask(int key, int bits) {
+  const bool valid = key >= 0;
+  unsigned m = __ballot_sync(FULL_MASK, valid);
+  m = valid ? m : ~m;
+  for (int b = 0; b < bits; ++b) {
+    const bool bit = (key >> b) & 1;
+    const unsigned vb = __ballot_sync(FULL_MASK, bit);
+    m &= bit ? vb : ~vb;
+  }
+  return m;
+}
+template <int BITS>
+__device__ __forceinline__ unsigned peer_mask_c(int key) {
+  const bool valid = key >= 0;
+  unsigned m = __ballot_sync(FULL_MASK, valid);
+  m = valid ? m : ~m;
+#pragma unroll
+  for (int b = 0; b < BITS; ++b) {
+    const bool bit = (key >> b) & 1;
+    const unsigned vb = __ballot_sync(FULL_MASK, bit);
+    m &= bit ? vb : ~vb;
+  }
+  return m;
+}
+
 // Scratch ints per team (reductions over up to 16 warps and 8 dimensions).
 constexpr int RED_INTS = 16 * (2 * PKD_DMAX) + 16;
 
@@ -258,8 +288,7 @@ __device__ __forceinline__ int warp_select32(const Team& tm, const SmemPts<D>& s
         const unsigned v = (unsigned)X[p];
         if ((!sampled_only || s.flag[p]) && (v & mask) == prefix) key = (int)((v >> shift) & dmask);
       }
-      const unsigned m = __match_any_sync(FULL_MASK, key);
-      if (key >= 0 && lane == __ffs(m) - 1) atomicAdd(&tm.hist[key], (unsigned)__popc(m));
+      if (key >= 0) atomicAdd(&tm.hist[key], 1u);
     }
     __syncwarp();
     const int c = (int)tm.hist[lane];
@@ -288,7 +317,8 @@ __device__ __forceinline__ int warp_select32(const Team& tm, const SmemPts<D>& s
 // are common to every element, so the 8-bit digits start just below them (a
 // deep node with a narrow range needs fewer passes, and its first digit
 // spreads over the bins instead of piling every element onto one counter).
-// Counter updates are aggregated per warp over lanes that hit the same bin.
+// Counters are plain shared-memory atomics (lanes that hit the same bin
+// serialise in hardware, which is cheaper than finding the peers first).
 template <int D>
 __device__ __forceinline__ int team_select(const Team& tm, const SmemPts<D>& s, const uint16_t* idx, int lo, int hi,
                            bool sampled_only, int dim, int k, int vmin, int vmax, int& count_less,
@@ -315,8 +345,7 @@ __device__ __forceinline__ int team_select(const Team& tm, const SmemPts<D>& s, 
         const unsigned v = (unsigned)X[p];
         if ((!sampled_only || s.flag[p]) && (v & mask) == prefix) key = (int)((v >> shift) & dmask);
       }
-      const unsigned m = __match_any_sync(FULL_MASK, key);
-      if (key >= 0 && lane_id() == __ffs(m) - 1) atomicAdd(&tm.hist[key], (unsigned)__popc(m));
+      if (key >= 0) atomicAdd(&tm.hist[key], 1u);
     }
     tm.sync();
     int digit, below, e;

@@ -390,6 +390,9 @@ int pkd_set_option(const char* name, int64_t value) {
   } else if (n == "skel_cap") {
     if (value != 0 && (value < 64 || value > 16384)) return PKD_EINVAL;
     knobs().skel_cap = (int)value;
+  } else if (n == "base_kernel") {
+    if (value != 0 && value != 1) return PKD_EINVAL;
+    knobs().base_kernel = (int)value;
   } else if (n == "tile") {
     if (value < 256 || value > 4096 || (value & (value - 1))) return PKD_EINVAL;
     knobs().tile = (int)value;

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256) k_route_small(RoundArgs r, const uint32_t
       }
       bk[q] = sk_bucket(sk[h].y);
     }
-    const unsigned m = __match_any_sync(FULL_MASK, bk[q]);
+    const unsigned m = peer_mask(bk[q], r.lam);
     const int leader = __ffs(m) - 1;
     unsigned b0 = 0;
     if (bk[q] >= 0 && lane_id() == leader) b0 = atomicAdd(&cnt[bk[q]], (unsigned)__popc(m));

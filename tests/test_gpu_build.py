@@ -45,13 +45,14 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("base_kernel", [0, 1], ids=["sorted", "select"])
 @pytest.mark.parametrize("name,n,d,kind,over,kn", CASES, ids=[c[0] for c in CASES])
-def test_build_matches_oracle(name, n, d, kind, over, kn):
+def test_build_matches_oracle(name, n, d, kind, over, kn, base_kernel):
     pkd = _pkd()
     X = make_points(kind, n, d, 1000 + n + d)
     ids = ((np.arange(n, dtype=np.uint64) * 2654435761) % (1 << 32)).astype(np.uint32)
     p = pkd.Params(d=d, seed=42, **over)
-    with knobs(**kn):
+    with knobs(base_kernel=base_kernel, **kn):
         t = pkd.Tree(to_dev(X), ids_dev(ids), p)
         got = t.export()
     want = O.OracleTree(X, ids, oparams(p)).export()
@@ -83,7 +84,7 @@ def test_build_rejects_bad_input():
 
 
 def test_build_deterministic_and_config1():
-    # configs[0]: n = 1e6, d = 2 uniform in [0, 2^30), phi 32, lambda 6, rate 1/64.
+    # n = 1e6, d = 2 uniform in [0, 2^30), phi 32, lambda 6, rate 1/64.
     pkd = _pkd()
     from paper_2411_09275_gb300 import inputs as I
 

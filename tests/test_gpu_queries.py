@@ -62,7 +62,7 @@ def test_range_count_matches_oracle(d):
 
 
 def test_queries_after_updates_and_config1_knn():
-    # configs[0]: 1e6 uniform 2-D, k-NN k=10 for 1e4 uniform queries
+    # 1e6 uniform 2-D points, k-NN k=10 for 1e4 uniform queries
     pkd = _pkd()
     X = I.uniform(1_000_000, 2, 1)
     p = pkd.Params(d=2)

@@ -111,7 +111,7 @@ def test_empty_tree_grow_and_delete_everything():
 
 
 def test_config2_scaled_uniform_and_varden():
-    # the configs[1] workload at 1/100 scale: 1e6 points d=3, insert 1e5 new
+    # the 1e8-point build-and-update workload at 1/100 scale: 1e6 points d=3, insert 1e5 new
     # points, delete 1e5 random existing ids, alpha = 3/10, default params
     pkd = _pkd()
     d, n, m = 3, 1_000_000, 100_000

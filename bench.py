@@ -17,6 +17,7 @@ collective on the data path); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -66,12 +67,22 @@ def measured_peaks():
 
 
 def dram_traffic():
-    """Per-item DRAM bytes from a committed ncu summary, if one exists."""
+    """Per-item DRAM bytes of the kernel families from the committed ncu
+    capture (profiles/dram_traffic.json), or {} when a kernel source it lists
+    has changed since the capture (the counters then describe other code)."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
-    if os.path.exists(p):
-        with open(p) as f:
-            return json.load(f)
-    return {}
+    if not os.path.exists(p):
+        return {}
+    with open(p) as f:
+        j = json.load(f)
+    for rel, digest in j.get("sources", {}).items():
+        q = os.path.join(ROOT, rel)
+        if not os.path.exists(q):
+            return {}
+        with open(q, "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != digest:
+                return {}
+    return j.get("kernels", {})
 
 
 class Clocks:

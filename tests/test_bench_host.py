@@ -79,3 +79,18 @@ def test_roofline_bytes_and_config():
 def test_cpu_oracle_step_small():
     pts, dt, desc = bench.cpu_oracle_step(dict(n=20000, d=2, m=2000, kind="uniform"), scale=10)
     assert pts == 2000 + 2 * 200 and dt > 0 and "oracle" in desc
+
+
+def test_dram_traffic_is_dropped_when_a_kernel_source_changed(tmp_path, monkeypatch):
+    import hashlib
+    import json
+
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "k.cu").write_text("kernel v1")
+    j = {"sources": {"k.cu": hashlib.sha1(b"kernel v1").hexdigest()},
+         "kernels": {"scatter": {"dram_bytes_per_item": 25.0}}}
+    (tmp_path / "profiles" / "dram_traffic.json").write_text(json.dumps(j))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.dram_traffic()["scatter"]["dram_bytes_per_item"] == 25.0
+    (tmp_path / "k.cu").write_text("kernel v2")
+    assert bench.dram_traffic() == {}

@@ -346,6 +346,15 @@ __global__ void __launch_bounds__(WK_WARPS * 32, 4) k_smem_warp(SmemArgs a) {
       return;
     }
     const int n = (int)seg.len;
+    if (n > 0 && n <= a.p.phi && seg.where == IN_A) {
+      // a leaf whose points already sit at their final arena positions
+      if (lane == 0) {
+        a.nodes[seg.root] = Node{0, (uint32_t)n, (uint32_t)seg.start, 0};
+        a.ndim[seg.root] = PKD_LEAF;
+        q.ctl->maxd = max(q.ctl->maxd, seg.depth);
+      }
+      continue;
+    }
     __syncwarp();
     load_segment<D>(a, seg, q.X, q.ID, q.perm0, cap, lane, 32);
     if (lane == 0) q.ctl->next_slot = 0;
@@ -469,7 +478,16 @@ __global__ void k_classify(const Seg* segs, uint32_t nseg, uint32_t cap, Seg* bi
 }
 
 // Sample: points whose hash at the segment's depth passes the rate test.
-__global__ void k_sample(RoundArgs r) {
+// Each CTA hashes its tile (ids only), counts its samples, reserves their
+// slots with one atomic on the segment's counter and then gathers their
+// coordinates (the order of a sample is immaterial: only its multiset
+// enters the skeleton).
+constexpr int SAMPLE_THREADS = 256;
+constexpr int SAMPLE_PER = 16;  // points per thread (tiles of up to 4096)
+
+__global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(RoundArgs r) {
+  __shared__ uint32_t sh[33];
+  __shared__ uint32_t base_sh;
   const uint32_t nb = *r.nbig;
   const uint32_t s = seg_of_tile(r.tile0, nb, blockIdx.x);
   const Seg seg = r.big[s];
@@ -478,19 +496,31 @@ __global__ void k_sample(RoundArgs r) {
   const int cnt = (int)min((uint64_t)r.TILE, (uint64_t)seg.len - first);
   const int shift = sample_shift(r.p, seg.len);
   const int d = r.p.d;
-  for (int base = 0; base < cnt; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const uint64_t g = seg.start + first + (uint64_t)i;
-    bool f = false;
-    if (i < cnt) f = in_sample(r.p.seed, seg.depth, r.src.id(g), shift);
-    const unsigned m = __ballot_sync(FULL_MASK, f);
-    if (m == 0) continue;
-    uint32_t pos = 0;
-    if (lane_id() == __ffs(m) - 1) pos = atomicAdd(&r.scnt[s], (uint32_t)__popc(m));
-    pos = __shfl_sync(FULL_MASK, pos, __ffs(m) - 1) + __popc(m & lanemask_lt());
-    if (f) {
-      const uint64_t o = seg.start + pos;
-      for (int j = 0; j < d; ++j) r.samp.c[(uint64_t)j * r.samp.stride + o] = r.src.x(d, j, g);
+  uint32_t ids[SAMPLE_PER];
+#pragma unroll
+  for (int k = 0; k < SAMPLE_PER; ++k) {
+    const int i = k * SAMPLE_THREADS + threadIdx.x;
+    if (i < cnt) ids[k] = r.src.id(seg.start + first + (uint64_t)i);
+  }
+  unsigned fl = 0;
+#pragma unroll
+  for (int k = 0; k < SAMPLE_PER; ++k) {
+    const int i = k * SAMPLE_THREADS + threadIdx.x;
+    if (i < cnt && in_sample(r.p.seed, seg.depth, ids[k], shift)) fl |= 1u << k;
+  }
+  uint32_t total;
+  uint32_t off = block_excl_scan<uint32_t>((uint32_t)__popc(fl), sh, &total);
+  if (total == 0) return;
+  if (threadIdx.x == 0) base_sh = atomicAdd(&r.scnt[s], total);
+  __syncthreads();
+  const uint64_t o0 = seg.start + base_sh + off;
+  int q = 0;
+#pragma unroll
+  for (int k = 0; k < SAMPLE_PER; ++k) {
+    if (fl & (1u << k)) {
+      const uint64_t g = seg.start + first + (uint64_t)(k * SAMPLE_THREADS + threadIdx.x);
+      for (int j = 0; j < d; ++j) r.samp.c[(uint64_t)j * r.samp.stride + o0 + q] = r.src.x(d, j, g);
+      ++q;
     }
   }
 }
@@ -1227,7 +1257,7 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     {
       KTimer kt;
       ktimer_begin(kt, "sample", pts_big, s);
-      PKD_LAUNCH(k_sample<<<tiles, 256, 0, s>>>(r));
+      PKD_LAUNCH(k_sample<<<tiles, SAMPLE_THREADS, 0, s>>>(r));
       ktimer_end(kt);
     }
 

@@ -307,35 +307,82 @@ __global__ void k_copy_round(RoundArgs r, Pts F) {
   }
 }
 
+// The per-leaf kernels below give each warp UPW leaves (or rebuild items):
+// lanes 0..UPW-1 fetch the descriptors together, and for leaves of at most
+// 32 points every load of the UPW leaves is issued before the first store,
+// so a warp keeps UPW dependent chains in flight instead of one.
+constexpr int UPW = 4;
+constexpr int UPW_WARPS = 8;  // warps per CTA
+__host__ __device__ inline unsigned upw_blocks(uint32_t n) {
+  return (unsigned)(((uint64_t)n + UPW * UPW_WARPS - 1) / (UPW * UPW_WARPS));
+}
+
 // Deletion round 1 at the leaves: mark stored points equal to a routed batch
 // point (coordinates and id); count them.
-__global__ void k_match(LeafGroup* groups, const uint32_t* ngroups, const Node* nodes, Pts A, Pts F,
-                        int d, uint8_t* dead, uint32_t* aux) {
-  const uint32_t gi = blockIdx.x * (blockDim.x / 32) + warp_id();
-  if (gi >= *ngroups) return;
-  LeafGroup& G = groups[gi];
-  const Node leaf = nodes[G.slot];
-  int found = 0;
-  for (uint32_t base = 0; base < leaf.size; base += 32) {
-    const uint32_t i = base + lane_id();
-    bool hit = false;
-    if (i < leaf.size) {
-      const uint64_t p = (uint64_t)leaf.a + i;
-      const uint32_t id = A.id[p];
-      for (uint32_t q = 0; q < G.len && !hit; ++q) {
-        const uint64_t r = G.start + q;
-        if (F.id[r] != id) continue;
-        bool same = true;
-        for (int j = 0; j < d; ++j) same &= A.c[(uint64_t)j * A.stride + p] == F.c[(uint64_t)j * F.stride + r];
-        hit = same;
-      }
-      if (hit) dead[p] = 1;
-    }
-    found += __popc(__ballot_sync(FULL_MASK, hit));
+template <int D>
+__global__ void __launch_bounds__(UPW_WARPS * 32) k_match(LeafGroup* groups, const uint32_t* ngroups,
+                                                          const Node* nodes, Pts A, Pts F, uint8_t* dead,
+                                                          uint32_t* aux) {
+  const uint32_t n = *ngroups;
+  const uint32_t k0 = (blockIdx.x * UPW_WARPS + warp_id()) * UPW;
+  if (k0 >= n) return;
+  const int lane = lane_id();
+  uint32_t slot = 0, a = 0, sz = 0, glen = 0;
+  unsigned long long gst = 0;
+  if (lane < UPW && k0 + lane < n) {
+    const LeafGroup G = groups[k0 + lane];
+    const Node leaf = nodes[G.slot];
+    slot = G.slot;
+    gst = G.start;
+    glen = G.len;
+    a = leaf.a;
+    sz = leaf.size;
   }
-  if (lane_id() == 0) {
-    G.found = (uint32_t)found;
-    aux[G.slot] = (uint32_t)found;
+#pragma unroll
+  for (int q = 0; q < UPW; ++q) {
+    if (k0 + q >= n) break;
+    const uint32_t qa = __shfl_sync(FULL_MASK, a, q), qsz = __shfl_sync(FULL_MASK, sz, q);
+    const uint32_t qlen = __shfl_sync(FULL_MASK, glen, q), qslot = __shfl_sync(FULL_MASK, slot, q);
+    const unsigned long long qst = __shfl_sync(FULL_MASK, gst, q);
+    int found = 0;
+    for (uint32_t base = 0; base < qsz; base += 32) {
+      const uint32_t i = base + lane;
+      bool hit = false;
+      int32_t x[D];
+      uint32_t id = 0;
+      if (i < qsz) {
+        const uint64_t p = (uint64_t)qa + i;
+#pragma unroll
+        for (int j = 0; j < D; ++j) x[j] = A.c[(uint64_t)j * A.stride + p];
+        id = A.id[p];
+      }
+      // the routed batch points, 32 at a time, broadcast lane by lane
+      for (uint32_t b0 = 0; b0 < qlen; b0 += 32) {
+        const uint32_t rb = b0 + lane;
+        int32_t fx[D];
+        uint32_t fid = 0xFFFFFFFFu;
+        if (rb < qlen) {
+          const uint64_t r = qst + rb;
+#pragma unroll
+          for (int j = 0; j < D; ++j) fx[j] = F.c[(uint64_t)j * F.stride + r];
+          fid = F.id[r];
+        }
+        const int cnt = (int)min(32u, qlen - b0);
+        for (int t = 0; t < cnt; ++t) {
+          bool same = __shfl_sync(FULL_MASK, fid, t) == id;
+#pragma unroll
+          for (int j = 0; j < D; ++j) same &= __shfl_sync(FULL_MASK, fx[j], t) == x[j];
+          hit |= same;
+        }
+      }
+      hit &= i < qsz;
+      if (hit) dead[(uint64_t)qa + i] = 1;
+      found += __popc(__ballot_sync(FULL_MASK, hit));
+    }
+    if (lane == 0) {
+      groups[k0 + q].found = (uint32_t)found;
+      aux[qslot] = (uint32_t)found;
+    }
   }
 }
 
@@ -471,34 +518,85 @@ __global__ void k_leaf_items(UpdArgs a, LeafGroup* groups, const uint32_t* ngrou
   if (comp) compact[bc] = gi;
 }
 
-__global__ void k_compact_leaves(const LeafGroup* groups, const uint32_t* list, const uint32_t* n,
-                                 Node* nodes, Pts A, int d, const uint8_t* dead) {
-  const uint32_t k = blockIdx.x * (blockDim.x / 32) + warp_id();
-  if (k >= *n) return;
-  const LeafGroup G = groups[list[k]];
-  Node nd = nodes[G.slot];
-  // survivors move to the front, in order; one warp, chunks of 32
-  uint32_t out = 0;
-  for (uint32_t base = 0; base < nd.size; base += 32) {
-    const uint32_t i = base + lane_id();
-    const bool keep = i < nd.size && !dead[(uint64_t)nd.a + i];
-    int32_t x[PKD_DMAX];
-    uint32_t id = 0;
-    if (keep) {
-      for (int j = 0; j < d; ++j) x[j] = A.c[(uint64_t)j * A.stride + nd.a + i];
-      id = A.id[(uint64_t)nd.a + i];
-    }
-    const unsigned m = __ballot_sync(FULL_MASK, keep);
-    __syncwarp();
-    if (keep) {
-      const uint64_t o = (uint64_t)nd.a + out + __popc(m & lanemask_lt());
-      for (int j = 0; j < d; ++j) A.c[(uint64_t)j * A.stride + o] = x[j];
-      A.id[o] = id;
-    }
-    out += __popc(m);
-    __syncwarp();
+template <int D>
+__global__ void __launch_bounds__(UPW_WARPS * 32) k_compact_leaves(const LeafGroup* groups, const uint32_t* list,
+                                                                   const uint32_t* n, Node* nodes, Pts A,
+                                                                   const uint8_t* dead) {
+  const uint32_t nn = *n;
+  const uint32_t k0 = (blockIdx.x * UPW_WARPS + warp_id()) * UPW;
+  if (k0 >= nn) return;
+  const int lane = lane_id();
+  uint32_t slot = 0, a = 0, sz = 0;
+  if (lane < UPW && k0 + lane < nn) {
+    slot = groups[list[k0 + lane]].slot;
+    const Node nd = nodes[slot];
+    a = nd.a;
+    sz = nd.size;
   }
-  if (lane_id() == 0) nodes[G.slot].size = out;
+  uint32_t qa[UPW], qsz[UPW], qslot[UPW];
+  bool small = true;
+#pragma unroll
+  for (int q = 0; q < UPW; ++q) {
+    qa[q] = __shfl_sync(FULL_MASK, a, q);
+    qsz[q] = __shfl_sync(FULL_MASK, sz, q);
+    qslot[q] = __shfl_sync(FULL_MASK, slot, q);
+    small &= qsz[q] <= 32;
+  }
+  if (small) {
+    // survivors move to the front, in order: all loads, then all stores
+    int32_t x[UPW][D];
+    uint32_t id[UPW];
+    bool keep[UPW];
+#pragma unroll
+    for (int q = 0; q < UPW; ++q) {
+      keep[q] = lane < qsz[q] && !dead[(uint64_t)qa[q] + lane];
+      if (lane < qsz[q]) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) x[q][j] = A.c[(uint64_t)j * A.stride + qa[q] + lane];
+        id[q] = A.id[(uint64_t)qa[q] + lane];
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < UPW; ++q) {
+      const unsigned m = __ballot_sync(FULL_MASK, keep[q]);
+      if (keep[q]) {
+        const uint64_t o = (uint64_t)qa[q] + __popc(m & lanemask_lt());
+#pragma unroll
+        for (int j = 0; j < D; ++j) A.c[(uint64_t)j * A.stride + o] = x[q][j];
+        A.id[o] = id[q];
+      }
+      if (lane == 0 && k0 + q < nn) nodes[qslot[q]].size = (uint32_t)__popc(m);
+    }
+    return;
+  }
+#pragma unroll 1
+  for (int q = 0; q < UPW; ++q) {
+    if (k0 + q >= nn) break;
+    uint32_t out = 0;
+    for (uint32_t base = 0; base < qsz[q]; base += 32) {
+      const uint32_t i = base + lane;
+      const bool keep = i < qsz[q] && !dead[(uint64_t)qa[q] + i];
+      int32_t x[D];
+      uint32_t id = 0;
+      if (keep) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) x[j] = A.c[(uint64_t)j * A.stride + qa[q] + i];
+        id = A.id[(uint64_t)qa[q] + i];
+      }
+      const unsigned m = __ballot_sync(FULL_MASK, keep);
+      __syncwarp();
+      if (keep) {
+        const uint64_t o = (uint64_t)qa[q] + out + __popc(m & lanemask_lt());
+#pragma unroll
+        for (int j = 0; j < D; ++j) A.c[(uint64_t)j * A.stride + o] = x[j];
+        A.id[o] = id;
+      }
+      out += __popc(m);
+      __syncwarp();
+    }
+    if (lane == 0) nodes[qslot[q]].size = out;
+  }
 }
 
 // Arena positions of the rebuild items (exclusive scan of their sizes).
@@ -552,39 +650,126 @@ __global__ void k_front_expand(const Front* f, const uint32_t* nf, Front* g, uin
   g[k + 1] = Front{nd.b, e.item, e.off + llive};
 }
 
-// One warp per flattened leaf: copy its live points to the item's range.
-__global__ void k_copy_leaves(const Front* lv, const uint32_t* n, const RebuildItem* items, const Node* nodes,
-                              Pts A, int d, const uint8_t* dead, int use_dead) {
-  const uint32_t k = blockIdx.x * (blockDim.x / 32) + warp_id();
-  if (k >= *n) return;
-  const Front e = lv[k];
-  const Node nd = nodes[e.slot];
-  const uint64_t dst0 = items[e.item].pos + e.off;
-  uint32_t out = 0;
-  for (uint32_t base = 0; base < nd.size; base += 32) {
-    const uint32_t i = base + lane_id();
-    const bool keep = i < nd.size && !(use_dead && dead[(uint64_t)nd.a + i]);
-    const unsigned m = __ballot_sync(FULL_MASK, keep);
-    if (keep) {
-      const uint64_t src = (uint64_t)nd.a + i, dst = dst0 + out + __popc(m & lanemask_lt());
-      for (int j = 0; j < d; ++j) A.c[(uint64_t)j * A.stride + dst] = A.c[(uint64_t)j * A.stride + src];
-      A.id[dst] = A.id[src];
+// Flattened leaves, UPW per warp: copy their live points to the item's range.
+template <int D>
+__global__ void __launch_bounds__(UPW_WARPS * 32) k_copy_leaves(const Front* lv, const uint32_t* n,
+                                                                const RebuildItem* items, const Node* nodes, Pts A,
+                                                                const uint8_t* dead, int use_dead) {
+  const uint32_t nn = *n;
+  const uint32_t k0 = (blockIdx.x * UPW_WARPS + warp_id()) * UPW;
+  if (k0 >= nn) return;
+  const int lane = lane_id();
+  uint32_t a = 0, sz = 0;
+  unsigned long long d0 = 0;
+  if (lane < UPW && k0 + lane < nn) {
+    const Front e = lv[k0 + lane];
+    const Node nd = nodes[e.slot];
+    a = nd.a;
+    sz = nd.size;
+    d0 = items[e.item].pos + e.off;
+  }
+  uint32_t qa[UPW], qsz[UPW];
+  unsigned long long qd[UPW];
+  bool small = true;
+#pragma unroll
+  for (int q = 0; q < UPW; ++q) {
+    qa[q] = __shfl_sync(FULL_MASK, a, q);
+    qsz[q] = __shfl_sync(FULL_MASK, sz, q);
+    qd[q] = __shfl_sync(FULL_MASK, d0, q);
+    small &= qsz[q] <= 32;
+  }
+  if (small) {
+    int32_t x[UPW][D];
+    uint32_t id[UPW];
+    bool keep[UPW];
+#pragma unroll
+    for (int q = 0; q < UPW; ++q) {
+      keep[q] = lane < qsz[q];
+      if (keep[q]) {
+        const uint64_t src = (uint64_t)qa[q] + lane;
+        if (use_dead) keep[q] = !dead[src];
+#pragma unroll
+        for (int j = 0; j < D; ++j) x[q][j] = A.c[(uint64_t)j * A.stride + src];
+        id[q] = A.id[src];
+      }
     }
-    out += __popc(m);
+#pragma unroll
+    for (int q = 0; q < UPW; ++q) {
+      const unsigned m = __ballot_sync(FULL_MASK, keep[q]);
+      if (keep[q]) {
+        const uint64_t dst = qd[q] + __popc(m & lanemask_lt());
+#pragma unroll
+        for (int j = 0; j < D; ++j) A.c[(uint64_t)j * A.stride + dst] = x[q][j];
+        A.id[dst] = id[q];
+      }
+    }
+    return;
+  }
+#pragma unroll 1
+  for (int q = 0; q < UPW; ++q) {
+    uint32_t out = 0;
+    for (uint32_t base = 0; base < qsz[q]; base += 32) {
+      const uint32_t i = base + lane;
+      const bool keep = i < qsz[q] && !(use_dead && dead[(uint64_t)qa[q] + i]);
+      const unsigned m = __ballot_sync(FULL_MASK, keep);
+      if (keep) {
+        const uint64_t src = (uint64_t)qa[q] + i, dst = qd[q] + out + __popc(m & lanemask_lt());
+#pragma unroll
+        for (int j = 0; j < D; ++j) A.c[(uint64_t)j * A.stride + dst] = A.c[(uint64_t)j * A.stride + src];
+        A.id[dst] = A.id[src];
+      }
+      out += __popc(m);
+    }
   }
 }
 
-// Insert: append each item's new batch points after its old ones.
-__global__ void k_copy_new(const RebuildItem* items, const uint32_t* n, Pts F, Pts A, int d) {
-  const uint32_t k = blockIdx.x * (blockDim.x / 32) + warp_id();
-  if (k >= *n) return;
-  const RebuildItem it = items[k];
-  const uint64_t cnt = it.we - it.ws;
-  for (uint64_t i = lane_id(); i < cnt; i += 32) {
-    const uint64_t src = it.ws + i, dst = it.pos + it.old_live + i;
-    for (int j = 0; j < d; ++j) A.c[(uint64_t)j * A.stride + dst] = F.c[(uint64_t)j * F.stride + src];
-    A.id[dst] = F.id[src];
+// Insert: append each item's new batch points after its old ones (UPW
+// items per warp).
+template <int D>
+__global__ void __launch_bounds__(UPW_WARPS * 32) k_copy_new(const RebuildItem* items, const uint32_t* n, Pts F,
+                                                             Pts A) {
+  const uint32_t nn = *n;
+  const uint32_t k0 = (blockIdx.x * UPW_WARPS + warp_id()) * UPW;
+  if (k0 >= nn) return;
+  const int lane = lane_id();
+  unsigned long long ws = 0, cnt = 0, dst0 = 0;
+  if (lane < UPW && k0 + lane < nn) {
+    const RebuildItem it = items[k0 + lane];
+    ws = it.ws;
+    cnt = it.we - it.ws;
+    dst0 = it.pos + it.old_live;
   }
+#pragma unroll 1
+  for (int q = 0; q < UPW; ++q) {
+    const unsigned long long qws = __shfl_sync(FULL_MASK, ws, q), qcnt = __shfl_sync(FULL_MASK, cnt, q);
+    const unsigned long long qd = __shfl_sync(FULL_MASK, dst0, q);
+    for (uint64_t i = lane; i < qcnt; i += 32) {
+      const uint64_t src = qws + i, dst = qd + i;
+#pragma unroll
+      for (int j = 0; j < D; ++j) A.c[(uint64_t)j * A.stride + dst] = F.c[(uint64_t)j * F.stride + src];
+      A.id[dst] = F.id[src];
+    }
+  }
+}
+
+template <int D>
+static void launch_match(LeafGroup* g, const uint32_t* ng, uint32_t n, const Node* nodes, Pts A, Pts F,
+                         uint8_t* dead, uint32_t* aux, cudaStream_t s) {
+  PKD_LAUNCH(k_match<D><<<upw_blocks(n), UPW_WARPS * 32, 0, s>>>(g, ng, nodes, A, F, dead, aux));
+}
+template <int D>
+static void launch_compact(const LeafGroup* g, const uint32_t* list, const uint32_t* n, uint32_t nh, Node* nodes,
+                           Pts A, const uint8_t* dead, cudaStream_t s) {
+  PKD_LAUNCH(k_compact_leaves<D><<<upw_blocks(nh), UPW_WARPS * 32, 0, s>>>(g, list, n, nodes, A, dead));
+}
+template <int D>
+static void launch_copy_leaves(const Front* lv, const uint32_t* n, uint32_t nh, const RebuildItem* items,
+                               const Node* nodes, Pts A, const uint8_t* dead, int use_dead, cudaStream_t s) {
+  PKD_LAUNCH(k_copy_leaves<D><<<upw_blocks(nh), UPW_WARPS * 32, 0, s>>>(lv, n, items, nodes, A, dead, use_dead));
+}
+template <int D>
+static void launch_copy_new(const RebuildItem* items, const uint32_t* n, uint32_t nh, Pts F, Pts A, cudaStream_t s) {
+  PKD_LAUNCH(k_copy_new<D><<<upw_blocks(nh), UPW_WARPS * 32, 0, s>>>(items, n, F, A));
 }
 
 __global__ void k_clear_aux(const uint32_t* slots, uint64_t n, uint32_t* aux) {
@@ -874,7 +1059,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
 
   // ---- match (delete) ----
   if (!insert && ngroups)
-    PKD_LAUNCH(k_match<<<(ngroups + 7) / 8, 256, 0, s>>>(groups, d_ngroups, t.nodes, t.A, F, d, t.dead, t.aux));
+    PKD_DISPATCH_D(d, launch_match, groups, d_ngroups, ngroups, t.nodes, t.A, F, t.dead, t.aux, s);
 
   // ---- count, bottom-up ----
   for (int r = (int)rounds.size() - 1; r >= 0; --r) {
@@ -919,7 +1104,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
 
   // ---- delete: compact the reached leaves in place ----
   if (ncompact)
-    PKD_LAUNCH(k_compact_leaves<<<(ncompact + 7) / 8, 256, 0, s>>>(groups, compact, d_ncompact, t.nodes, t.A, d, t.dead));
+    PKD_DISPATCH_D(d, launch_compact, groups, compact, d_ncompact, ncompact, t.nodes, t.A, t.dead, s);
 
   // ---- rebuild ----
   trace_mark(s, "upd: leaf items + compact");
@@ -937,7 +1122,6 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
     device_excl_scan(isz, ioff, nitems, ipart, s);
     PKD_LAUNCH(k_item_pos<<<gi, 128, 0, s>>>(items_out, d_nitems, ioff, t.top, segs));
     // flatten the old subtrees breadth first
-    uint64_t old_total = 0;
     {
       // capacity: every node of the old subtrees appears once
       const uint64_t fcap = 4 * ((uint64_t)t.size + (uint64_t)nitems) + 1024;
@@ -965,11 +1149,10 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
       }
       const uint32_t nleaves = hctr[14];
       if (nleaves)
-        PKD_LAUNCH(k_copy_leaves<<<(nleaves + 7) / 8, 256, 0, s>>>(leaves, fc + 2, items_out, t.nodes, t.A, d, t.dead,
-                                                        insert ? 0 : 1));
-      (void)old_total;
+        PKD_DISPATCH_D(d, launch_copy_leaves, leaves, fc + 2, nleaves, items_out, t.nodes, t.A, t.dead,
+                       insert ? 0 : 1, s);
     }
-    if (insert) PKD_LAUNCH(k_copy_new<<<(nitems + 7) / 8, 256, 0, s>>>(items_out, d_nitems, F, t.A, d));
+    if (insert) PKD_DISPATCH_D(d, launch_copy_new, items_out, d_nitems, nitems, F, t.A, s);
     trace_mark(s, "upd: flatten + gather");
     BuildJob job;
     job.base = t.top;

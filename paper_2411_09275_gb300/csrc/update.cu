@@ -92,52 +92,69 @@ struct UpdArgs {
   DevStatus* st;
 };
 
-// The skeleton at each item: its node and lambda levels below, cut at leaves.
-__global__ void k_fetch(UpdArgs a) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= *a.nitems) return;
+// The per-item kernels (fetch, emit, aggregate, decide) give each item one
+// warp, whose lanes take the heap entries of one skeleton level at a time
+// (levels are ordered by __syncwarp); each CTA holds ITEM_WARPS items.
+constexpr int ITEM_WARPS = 4;
+__host__ __device__ inline unsigned item_blocks(uint64_t n) { return (unsigned)((n + ITEM_WARPS - 1) / ITEM_WARPS); }
+__device__ __forceinline__ uint32_t item_of_warp() { return blockIdx.x * ITEM_WARPS + warp_id(); }
+
+// The skeleton at each item: its node and lambda levels below, cut at leaves;
+// the external nodes are numbered left to right (the item's buckets).
+__global__ void __launch_bounds__(ITEM_WARPS * 32) k_fetch(UpdArgs a) {
+  __shared__ uint32_t bits_sh[ITEM_WARPS][32], pre_sh[ITEM_WARPS][32];
+  const uint32_t i = item_of_warp();
+  if (i >= *a.nitems) return;  // warp-uniform
+  const int lane = lane_id();
+  uint32_t* bits = bits_sh[warp_id()];
+  uint32_t* pre = pre_sh[warp_id()];
   int2* sk = a.skel + (uint64_t)i * a.HN;
   uint32_t* sl = a.slots + (uint64_t)i * a.HN;
-  for (int v = 1; v < a.HN; ++v) {
+  for (int v = lane; v < a.HN; v += 32) {
     sk[v] = make_int2(0, sk_meta(SK_NONE, 0, 0));
     sl[v] = 0xFFFFFFFFu;
   }
-  sl[0] = 0xFFFFFFFFu;
-  sl[1] = a.items[i].root;
-  sk[1] = make_int2(0, sk_meta(SK_BUCKET, 0, 0));  // provisional: marks "defined"
-  for (int v = 1; v < a.HN; ++v) {
-    if (sk_state(sk[v].y) == SK_NONE) continue;
-    const uint32_t slot = sl[v];
-    const int j = 31 - __clz(v);
-    if (a.ndim[slot] == PKD_LEAF || j >= a.lam) {
-      sk[v] = make_int2(0, sk_meta(SK_BUCKET, 0, 0));
-      continue;
-    }
-    const Node nd = a.nodes[slot];
-    sk[v] = make_int2(nd.split, sk_meta(SK_INTERNAL, a.ndim[slot], 0));
-    sl[2 * v] = nd.a;
-    sl[2 * v + 1] = nd.b;
-    sk[2 * v] = make_int2(0, sk_meta(SK_BUCKET, 0, 0));
-    sk[2 * v + 1] = make_int2(0, sk_meta(SK_BUCKET, 0, 0));
+  bits[lane] = 0;
+  __syncwarp();
+  if (lane == 0) {
+    sl[1] = a.items[i].root;
+    sk[1] = make_int2(0, sk_meta(SK_BUCKET, 0, 0));  // provisional: marks "defined"
   }
-  // number the external nodes left to right
-  int stack[12];
-  int sp = 0, h = 1, nb = 0;
-  while (sp > 0 || h != 0) {
-    if (h != 0) {
-      if (sk_state(sk[h].y) == SK_INTERNAL) {
-        stack[sp++] = h;
-        h = 2 * h;
+  __syncwarp();
+  for (int j = 0; j <= a.lam; ++j) {
+    for (int v = (1 << j) + lane; v < (2 << j); v += 32) {
+      if (sk_state(sk[v].y) == SK_NONE) continue;
+      const uint32_t slot = sl[v];
+      const uint8_t dm = j < a.lam ? a.ndim[slot] : (uint8_t)PKD_LEAF;
+      if (dm == PKD_LEAF) {
+        // external: bit (its first position on level lambda) in the bitmap
+        const uint32_t lo = (uint32_t)(v - (1 << j)) << (a.lam - j);
+        atomicOr(&bits[lo >> 5], 1u << (lo & 31));
         continue;
       }
-      sk[h].y = sk_meta(SK_BUCKET, 0, nb++);
-      h = 0;
-    } else {
-      h = stack[--sp];
-      h = 2 * h + 1;
+      const Node nd = a.nodes[slot];
+      sk[v] = make_int2(nd.split, sk_meta(SK_INTERNAL, dm, 0));
+      sl[2 * v] = nd.a;
+      sl[2 * v + 1] = nd.b;
+      sk[2 * v] = make_int2(0, sk_meta(SK_BUCKET, 0, 0));
+      sk[2 * v + 1] = make_int2(0, sk_meta(SK_BUCKET, 0, 0));
+    }
+    __syncwarp();
+  }
+  // left-to-right number of an external node = set bits before its position
+  const uint32_t wc = (uint32_t)__popc(bits[lane]);
+  const uint32_t incl = (uint32_t)warp_incl_scan((int)wc);
+  pre[lane] = incl - wc;
+  __syncwarp();
+  for (int j = 0; j <= a.lam; ++j) {
+    for (int v = (1 << j) + lane; v < (2 << j); v += 32) {
+      if (sk_state(sk[v].y) != SK_BUCKET) continue;
+      const uint32_t lo = (uint32_t)(v - (1 << j)) << (a.lam - j);
+      const uint32_t nbk = pre[lo >> 5] + (uint32_t)__popc(bits[lo >> 5] & ((1u << (lo & 31)) - 1u));
+      sk[v].y = sk_meta(SK_BUCKET, 0, (int)nbk);
     }
   }
-  a.nbk[i] = nb;
+  if (lane == 31) a.nbk[i] = incl;
 }
 
 constexpr uint32_t SMALL_ITEM = 256;  // items up to this many points: one warp routes them
@@ -250,42 +267,72 @@ static void launch_route_small(const RoundArgs& ra, const uint32_t* small, const
 }
 
 // Next-round items and leaf groups from the bucket ranges.
-__global__ void k_route_emit(UpdArgs a) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= *a.nitems) return;
+__global__ void __launch_bounds__(ITEM_WARPS * 32) k_route_emit(UpdArgs a) {
+  const uint32_t i = item_of_warp();
+  if (i >= *a.nitems) return;  // warp-uniform
+  const int lane = lane_id();
   const Seg it = a.items[i];
   const int2* sk = a.skel + (uint64_t)i * a.HN;
   const uint32_t* sl = a.slots + (uint64_t)i * a.HN;
-  for (uint32_t b = 0; b < (uint32_t)a.NB; ++b) a.link[(uint64_t)i * a.NB + b] = LINK_NONE;
-  for (int v = 1; v < a.HN; ++v) {
-    const int m = sk[v].y;
-    if (sk_state(m) != SK_BUCKET) continue;
-    const int b = sk_bucket(m);
-    const uint64_t k = (uint64_t)i * a.NB + b;
-    const uint32_t cnt = a.blen[k];
-    const uint64_t b0 = a.bstart[k];
-    if (cnt == 0) continue;
-    const uint32_t slot = sl[v];
-    const uint32_t depth = it.depth + (31 - __clz(v));
-    if (a.ndim[slot] == PKD_LEAF) {
-      const uint32_t g = atomicAdd(a.ngroups, 1u);
+  for (int b = lane; b < a.NB; b += 32) a.link[(uint64_t)i * a.NB + b] = LINK_NONE;
+  __syncwarp();
+  for (int v0 = 1; v0 < a.HN; v0 += 32) {
+    const int v = v0 + lane;
+    bool leaf = false, inner = false;
+    uint32_t cnt = 0, slot = 0, depth = 0;
+    uint64_t b0 = 0, k = 0;
+    if (v < a.HN) {
+      const int m = sk[v].y;
+      if (sk_state(m) == SK_BUCKET) {
+        k = (uint64_t)i * a.NB + sk_bucket(m);
+        cnt = a.blen[k];
+        if (cnt) {
+          b0 = a.bstart[k];
+          slot = sl[v];
+          depth = it.depth + (31 - __clz(v));
+          leaf = a.ndim[slot] == PKD_LEAF;
+          inner = !leaf;
+        }
+      }
+    }
+    // one update of each counter per warp
+    const bool big = inner && cnt > SMALL_ITEM;
+    const unsigned mL = __ballot_sync(FULL_MASK, leaf), mN = __ballot_sync(FULL_MASK, inner);
+    const unsigned mB = __ballot_sync(FULL_MASK, big), mS = __ballot_sync(FULL_MASK, inner && !big);
+    uint32_t tiles = big ? (cnt + a.TILE - 1) / a.TILE : 0u;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) tiles += __shfl_xor_sync(FULL_MASK, tiles, o);
+    uint32_t gB = 0, qB = 0, kB = 0, sB = 0;
+    if (lane == 0) {
+      if (mL) gB = atomicAdd(a.ngroups, (uint32_t)__popc(mL));
+      if (mN) qB = atomicAdd(&a.next_ctr[0], (uint32_t)__popc(mN));
+      if (mB) {
+        kB = atomicAdd(&a.next_ctr[2], (uint32_t)__popc(mB));
+        atomicAdd(&a.next_ctr[1], tiles);
+      }
+      if (mS) sB = atomicAdd(&a.next_ctr[3], (uint32_t)__popc(mS));
+    }
+    const unsigned lt = lanemask_lt();
+    const uint32_t g = __shfl_sync(FULL_MASK, gB, 0) + __popc(mL & lt);
+    if (leaf) {
       if (g >= a.group_cap) {
         set_error(a.st, DERR_CAPACITY, 800);
-        return;
+      } else {
+        a.groups[g] = LeafGroup{slot, depth, b0, cnt, a.insert ? cnt : 0u, 0u, 0u};
+        a.link[k] = LINK_LEAF | g;
       }
-      a.groups[g] = LeafGroup{slot, depth, b0, cnt, a.insert ? cnt : 0u, 0u, 0u};
-      a.link[k] = LINK_LEAF | g;
-    } else {
-      const uint32_t q = atomicAdd(&a.next_ctr[0], 1u);
+    }
+    const uint32_t q = __shfl_sync(FULL_MASK, qB, 0) + __popc(mN & lt);
+    const uint32_t kb = __shfl_sync(FULL_MASK, kB, 0) + __popc(mB & lt);
+    const uint32_t sb = __shfl_sync(FULL_MASK, sB, 0) + __popc(mS & lt);
+    if (inner) {
       const Seg c{b0, cnt, depth, slot, IN_B};
       a.next[q] = c;
-      if (cnt > SMALL_ITEM) {
-        const uint32_t kb = atomicAdd(&a.next_ctr[2], 1u);
+      if (big) {
         a.next_big[kb] = c;
         a.next_bigmap[kb] = q;
-        atomicAdd(&a.next_ctr[1], (cnt + a.TILE - 1) / a.TILE);
       } else {
-        a.next_small[atomicAdd(&a.next_ctr[3], 1u)] = q;
+        a.next_small[sb] = q;
       }
       a.link[k] = q;
     }
@@ -386,26 +433,32 @@ __global__ void __launch_bounds__(UPW_WARPS * 32) k_match(LeafGroup* groups, con
   }
 }
 
-// Exact counts per skeleton node, bottom-up (rounds in reverse order).
-__global__ void k_aggregate(UpdArgs a) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= *a.nitems) return;
+// Exact counts per skeleton node, bottom-up (rounds in reverse order; within
+// a skeleton, level by level from the deepest).
+__global__ void __launch_bounds__(ITEM_WARPS * 32) k_aggregate(UpdArgs a) {
+  const uint32_t i = item_of_warp();
+  if (i >= *a.nitems) return;  // warp-uniform
+  const int lane = lane_id();
   const int2* sk = a.skel + (uint64_t)i * a.HN;
   const uint32_t* sl = a.slots + (uint64_t)i * a.HN;
   uint32_t* f = a.fnd + (uint64_t)i * a.HN;
-  for (int v = a.HN - 1; v >= 1; --v) {
-    const int m = sk[v].y;
-    const int st = sk_state(m);
-    if (st == SK_NONE) continue;
-    uint32_t c = 0;
-    if (st == SK_BUCKET) {
-      const uint32_t L = a.link[(uint64_t)i * a.NB + sk_bucket(m)];
-      if (L != LINK_NONE) c = (L & LINK_LEAF) ? a.groups[L & ~LINK_LEAF].found : a.next_fnd[(uint64_t)L * a.next_HN + 1];
-    } else {
-      c = f[2 * v] + f[2 * v + 1];
+  for (int j = a.lam; j >= 0; --j) {
+    for (int v = (1 << j) + lane; v < (2 << j); v += 32) {
+      const int m = sk[v].y;
+      const int st = sk_state(m);
+      if (st == SK_NONE) continue;
+      uint32_t c = 0;
+      if (st == SK_BUCKET) {
+        const uint32_t L = a.link[(uint64_t)i * a.NB + sk_bucket(m)];
+        if (L != LINK_NONE)
+          c = (L & LINK_LEAF) ? a.groups[L & ~LINK_LEAF].found : a.next_fnd[(uint64_t)L * a.next_HN + 1];
+      } else {
+        c = f[2 * v] + f[2 * v + 1];
+      }
+      f[v] = c;
+      if (!a.insert && c) a.aux[sl[v]] = c;
     }
-    f[v] = c;
-    if (!a.insert && c) a.aux[sl[v]] = c;
+    __syncwarp();
   }
 }
 
@@ -420,57 +473,65 @@ __device__ void push_rebuild(const UpdArgs& a, uint32_t slot, uint32_t depth, ui
   atomicAdd(a.items_total, (unsigned long long)size);
 }
 
-// Top-down alpha test over every skeleton (rounds in forward order).
-__global__ void k_decide(UpdArgs a) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= *a.nitems) return;
+// Top-down alpha test over every skeleton (rounds in forward order; within a
+// skeleton, level by level from the root).  under: one bit per heap node
+// inside a subtree that is rebuilt.
+__global__ void __launch_bounds__(ITEM_WARPS * 32) k_decide(UpdArgs a) {
+  __shared__ uint32_t under_sh[ITEM_WARPS][64];
+  const uint32_t i = item_of_warp();
+  if (i >= *a.nitems) return;  // warp-uniform
+  const int lane = lane_id();
+  uint32_t* under = under_sh[warp_id()];
   const Seg it = a.items[i];
   const int2* sk = a.skel + (uint64_t)i * a.HN;
   const uint32_t* sl = a.slots + (uint64_t)i * a.HN;
   const uint32_t* f = a.fnd + (uint64_t)i * a.HN;
-  uint32_t under[64];  // one bit per heap node: inside a rebuilt subtree
-  for (int w = 0; w < (a.HN + 31) / 32; ++w) under[w] = 0;
-  if (a.iflag[i]) under[0] |= 2u;
-  for (int v = 1; v < a.HN; ++v) {
-    const int m = sk[v].y;
-    const int st = sk_state(m);
-    if (st == SK_NONE) continue;
-    const bool u = (under[v >> 5] >> (v & 31)) & 1u;
-    if (st == SK_BUCKET) {
-      if (!u) continue;
-      const uint32_t L = a.link[(uint64_t)i * a.NB + sk_bucket(m)];
-      if (L == LINK_NONE) continue;
-      if (L & LINK_LEAF) a.groups[L & ~LINK_LEAF].flag = 1;
-      else a.next_iflag[L] = 1;
-      continue;
+  under[lane] = 0;
+  under[lane + 32] = 0;
+  __syncwarp();
+  if (lane == 0 && a.iflag[i]) under[0] = 2u;
+  __syncwarp();
+  for (int j = 0; j <= a.lam; ++j) {
+    for (int v = (1 << j) + lane; v < (2 << j); v += 32) {
+      const int m = sk[v].y;
+      const int st = sk_state(m);
+      if (st == SK_NONE) continue;
+      const bool u = (under[v >> 5] >> (v & 31)) & 1u;
+      if (st == SK_BUCKET) {
+        if (!u) continue;
+        const uint32_t L = a.link[(uint64_t)i * a.NB + sk_bucket(m)];
+        if (L == LINK_NONE) continue;
+        if (L & LINK_LEAF) a.groups[L & ~LINK_LEAF].flag = 1;
+        else a.next_iflag[L] = 1;
+        continue;
+      }
+      const int c0 = 2 * v;  // children c0 and c0 + 1 share a word of `under`
+      if (u) {
+        atomicOr(&under[c0 >> 5], 3u << (c0 & 31));
+        continue;
+      }
+      const uint32_t c = f[v];
+      if (c == 0) continue;  // nothing below changes
+      const uint32_t slot = sl[v];
+      const uint32_t old = a.nodes[slot].size;
+      const uint32_t N = a.insert ? old + c : old - c;
+      const uint32_t lold = a.nodes[sl[c0]].size;
+      const uint32_t L = a.insert ? lold + f[c0] : lold - f[c0];
+      if (N > 0 && is_balanced(L, N, a.p.alpha_num, a.p.alpha_den)) {
+        a.wnodes[slot].size = N;
+        continue;
+      }
+      // rebuild this subtree; the batch points below it are contiguous
+      int lv = v, rv = v;
+      while (sk_state(sk[lv].y) == SK_INTERNAL) lv = 2 * lv;
+      while (sk_state(sk[rv].y) == SK_INTERNAL) rv = 2 * rv + 1;
+      const uint64_t kl = (uint64_t)i * a.NB + sk_bucket(sk[lv].y);
+      const uint64_t kr = (uint64_t)i * a.NB + sk_bucket(sk[rv].y);
+      const uint32_t depth = it.depth + (31 - __clz(v));
+      push_rebuild(a, slot, depth, N, a.insert ? old : old - c, a.bstart[kl], a.bstart[kr] + a.blen[kr]);
+      atomicOr(&under[c0 >> 5], 3u << (c0 & 31));
     }
-    const int c0 = 2 * v, c1 = 2 * v + 1;
-    if (u) {
-      under[c0 >> 5] |= 1u << (c0 & 31);
-      under[c1 >> 5] |= 1u << (c1 & 31);
-      continue;
-    }
-    const uint32_t c = f[v];
-    if (c == 0) continue;  // nothing below changes
-    const uint32_t slot = sl[v];
-    const uint32_t old = a.nodes[slot].size;
-    const uint32_t N = a.insert ? old + c : old - c;
-    const uint32_t lold = a.nodes[sl[c0]].size;
-    const uint32_t L = a.insert ? lold + f[c0] : lold - f[c0];
-    if (N > 0 && is_balanced(L, N, a.p.alpha_num, a.p.alpha_den)) {
-      a.wnodes[slot].size = N;
-      continue;
-    }
-    // rebuild this subtree; the batch points below it are contiguous
-    int lv = v, rv = v;
-    while (sk_state(sk[lv].y) == SK_INTERNAL) lv = 2 * lv;
-    while (sk_state(sk[rv].y) == SK_INTERNAL) rv = 2 * rv + 1;
-    const uint64_t kl = (uint64_t)i * a.NB + sk_bucket(sk[lv].y);
-    const uint64_t kr = (uint64_t)i * a.NB + sk_bucket(sk[rv].y);
-    const uint32_t depth = it.depth + (31 - __clz(v));
-    push_rebuild(a, slot, depth, N, a.insert ? old : old - c, a.bstart[kl], a.bstart[kr] + a.blen[kr]);
-    under[c0 >> 5] |= 1u << (c0 & 31);
-    under[c1 >> 5] |= 1u << (c1 & 31);
+    __syncwarp();
   }
 }
 
@@ -997,8 +1058,8 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
     ua.next_big = next_big;
     ua.next_bigmap = next_bigmap;
     ua.next_small = next_small;
-    const unsigned g1 = (ncur + 127) / 128;
-    PKD_LAUNCH(k_fetch<<<g1, 128, 0, s>>>(ua));
+    const unsigned g1 = item_blocks(ncur);
+    PKD_LAUNCH(k_fetch<<<g1, ITEM_WARPS * 32, 0, s>>>(ua));
 
     RoundArgs ra{};
     ra.p = p;
@@ -1038,7 +1099,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
     if (nsmall) {
       PKD_DISPATCH_D(d, launch_route_small, ra, cur_small, R.d_n + 2, cur, nbk, R.bstart, R.blen, F, nsmall, s);
     }
-    PKD_LAUNCH(k_route_emit<<<g1, 128, 0, s>>>(ua));
+    PKD_LAUNCH(k_route_emit<<<g1, ITEM_WARPS * 32, 0, s>>>(ua));
     PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 24, cudaMemcpyDeviceToHost, s));
     PKD_CUDA(cudaStreamSynchronize(s));
     const uint32_t nnext = hctr[0], ntiles = hctr[1], ngroups = hctr[4];
@@ -1072,7 +1133,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
     ua.fnd = R.fnd;
     ua.next_fnd = (r + 1 < (int)rounds.size()) ? rounds[r + 1].fnd : nullptr;
     ua.next_HN = HN;
-    PKD_LAUNCH(k_aggregate<<<(R.n + 127) / 128, 128, 0, s>>>(ua));
+    PKD_LAUNCH(k_aggregate<<<item_blocks(R.n), ITEM_WARPS * 32, 0, s>>>(ua));
   }
   uint32_t total_changed = 0;
   PKD_CUDA(cudaMemcpyAsync(&total_changed, rounds[0].fnd + 1, 4, cudaMemcpyDeviceToHost, s));
@@ -1090,7 +1151,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
     ua.blen = R.blen;
     ua.iflag = R.iflag;
     ua.next_iflag = (r + 1 < rounds.size()) ? rounds[r + 1].iflag : nullptr;
-    PKD_LAUNCH(k_decide<<<(R.n + 127) / 128, 128, 0, s>>>(ua));
+    PKD_LAUNCH(k_decide<<<item_blocks(R.n), ITEM_WARPS * 32, 0, s>>>(ua));
   }
   trace_mark(s, "upd: match+count+decide");
   uint32_t* compact;

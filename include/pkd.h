@@ -170,7 +170,11 @@ const char* pkd_strerror(int code);
  *   "base_cap"   largest subproblem finished in one CTA's shared memory
  *                (0 = derived from d and the shared-memory size)
  *   "skel_cap"   largest sample handled by one CTA when building a skeleton
- *   "tile"       points per CTA in the sieve kernels
+ *   "tile"       points per tile of the sieve kernels (256..4096, a power of
+ *                two; default 2048)
+ *   "sieve_kernel" sieve count/scatter: 0 persistent CTAs streaming tiles
+ *                through shared memory with bulk copies (default), 1 one
+ *                CTA per tile
  *   "base_kernel" shared-memory base case: 0 sorts each subproblem once per
  *                dimension and splits by lookups (default), 1 selects every
  *                splitter by a radix select

@@ -23,7 +23,7 @@
 #include <cstdio>
 #include <cstring>
 
-#include "sieve.cuh"
+#include "sieve_tma.cuh"
 #include "smem_sorted.cuh"
 
 namespace pkd {
@@ -1145,12 +1145,9 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
   unsigned long long* dpts = (unsigned long long*)(dctr + 14);
   unsigned long long* dbase_pts = (unsigned long long*)(dctr + 16);
   uint32_t* d_nbase = dctr + 12;
-  uint32_t* hctr = nullptr;
-  PKD_CUDA(cudaMallocHost((void**)&hctr, 128));
-  struct HostFree {
-    uint32_t* p;
-    ~HostFree() { cudaFreeHost(p); }
-  } hf{hctr};
+  PinnedBlock hblk(s);  // 128 bytes of host counters
+  uint32_t* hctr = (uint32_t*)hblk.p;
+  if (!hctr) return PKD_ENOMEM;
   PKD_CUDA(cudaMemsetAsync(dctr, 0, 32 * 4, s));
 
   const uint64_t nroots = job.dsegs ? job.dsegs_n : job.segs.size();

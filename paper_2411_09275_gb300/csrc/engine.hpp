@@ -15,8 +15,9 @@ namespace pkd {
 struct Knobs {
   int base_cap = 0;   // 0: derived from d and the shared memory per block
   int skel_cap = 0;   // 0: derived
-  int tile = 4096;    // points per CTA in the sieve kernels
+  int tile = 2048;    // points per tile in the sieve kernels
   int base_kernel = 0;  // base case: 0 presorted lists, 1 radix select per node
+  int sieve_kernel = 0;  // sieve: 0 persistent with bulk copies, 1 one tile per CTA
 };
 Knobs& knobs();
 
@@ -90,6 +91,26 @@ void dfree(T*& p, cudaStream_t s) {
   if (p) cudaFreeAsync(p, s);
   p = nullptr;
 }
+
+// Pinned host blocks of PINNED_BLOCK bytes from a library-owned pool that
+// grows by whole chunks and is never returned (pinning and unpinning memory
+// are slow, synchronising driver calls).  nullptr when pinning fails.
+constexpr size_t PINNED_BLOCK = 256;
+void* pinned_get();
+void pinned_put(void* p);
+// Return a block once the work queued on `s` so far has completed (a copy
+// into it may still be in flight).
+void pinned_put_after(cudaStream_t s, void* p);
+
+// A pinned block of PINNED_BLOCK bytes owned by one scope.
+struct PinnedBlock {
+  void* p = nullptr;
+  cudaStream_t s = nullptr;
+  explicit PinnedBlock(cudaStream_t st) : p(pinned_get()), s(st) {}
+  ~PinnedBlock() { pinned_put_after(s, p); }
+  PinnedBlock(const PinnedBlock&) = delete;
+  PinnedBlock& operator=(const PinnedBlock&) = delete;
+};
 
 // Reads the device status word; PKD_OK or the mapped error.
 int check_status(TreeMem& t, cudaStream_t s);

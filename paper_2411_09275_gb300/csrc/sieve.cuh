@@ -343,7 +343,7 @@ static size_t scatter_smem(int HN, int NB, int D, int tile) {
 }
 
 template <int D>
-static void launch_count(const RoundArgs& r, uint32_t tiles, cudaStream_t s) {
+static void launch_count_tiles(const RoundArgs& r, uint32_t tiles, cudaStream_t s) {
   const size_t sm = (size_t)r.HN * 8 + (size_t)r.NB * 4;
   KTimer kt;
   ktimer_begin(kt, "count", 0, s);
@@ -352,7 +352,7 @@ static void launch_count(const RoundArgs& r, uint32_t tiles, cudaStream_t s) {
 }
 
 template <int D>
-static void launch_scatter(const RoundArgs& r, uint32_t tiles, uint64_t pts, cudaStream_t s) {
+static void launch_scatter_tiles(const RoundArgs& r, uint32_t tiles, uint64_t pts, cudaStream_t s) {
   const size_t sm = scatter_smem(r.HN, r.NB, D, r.TILE);
   static bool set = false;
   if (!set) {

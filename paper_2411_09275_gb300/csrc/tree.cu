@@ -190,12 +190,48 @@ uint64_t shared_region_for(const Params& p, uint64_t n) {
   return per * (8 * (n / cap) + 2048);
 }
 
+static std::mutex g_pin_mu;
+static std::vector<void*> g_pin_free;
+
+void* pinned_get() {
+  std::lock_guard<std::mutex> g(g_pin_mu);
+  if (g_pin_free.empty()) {
+    constexpr size_t CHUNK = 256;  // blocks per chunk
+    char* c = nullptr;
+    if (cudaMallocHost((void**)&c, CHUNK * PINNED_BLOCK) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    for (size_t k = 0; k < CHUNK; ++k) g_pin_free.push_back(c + k * PINNED_BLOCK);
+  }
+  void* p = g_pin_free.back();
+  g_pin_free.pop_back();
+  return p;
+}
+
+void pinned_put(void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> g(g_pin_mu);
+  g_pin_free.push_back(p);
+}
+
+static void CUDART_CB pinned_put_cb(void* p) { pinned_put(p); }
+
+void pinned_put_after(cudaStream_t s, void* p) {
+  if (!p) return;
+  if (cudaLaunchHostFunc(s, pinned_put_cb, p) != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamSynchronize(s);
+    pinned_put(p);
+  }
+}
+
 void tree_release(TreeMem& t) {
   cudaStream_t s = 0;
   for (void* p : {(void*)t.A.c, (void*)t.A.id, (void*)t.nodes, (void*)t.ndim, (void*)t.shared_next,
                   (void*)t.dead, (void*)t.aux, (void*)t.st})
     if (p) cudaFreeAsync(p, s);
-  if (t.st_host) cudaFreeHost(t.st_host);
+  pinned_put_after(s, t.st_host);
   t = TreeMem{};
 }
 
@@ -228,7 +264,11 @@ int tree_alloc(TreeMem& t, const Params& p, uint64_t cap, uint64_t shared_cap, c
   if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&t.ndim, (size_t)t.node_cap, pool, s);
   if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&t.shared_next, 16, pool, s);
   if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&t.st, sizeof(DevStatus), pool, s);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&t.st_host, sizeof(DevStatus));
+  static_assert(sizeof(DevStatus) <= PINNED_BLOCK, "status block");
+  if (e == cudaSuccess) {
+    t.st_host = (DevStatus*)pinned_get();
+    if (!t.st_host) e = cudaErrorMemoryAllocation;
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     tree_release(t);
@@ -390,6 +430,9 @@ int pkd_set_option(const char* name, int64_t value) {
   } else if (n == "skel_cap") {
     if (value != 0 && (value < 64 || value > 16384)) return PKD_EINVAL;
     knobs().skel_cap = (int)value;
+  } else if (n == "sieve_kernel") {
+    if (value != 0 && value != 1) return PKD_EINVAL;
+    knobs().sieve_kernel = (int)value;
   } else if (n == "base_kernel") {
     if (value != 0 && value != 1) return PKD_EINVAL;
     knobs().base_kernel = (int)value;

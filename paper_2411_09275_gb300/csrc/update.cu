@@ -23,7 +23,7 @@
 #include <cstdio>
 #include <vector>
 
-#include "sieve.cuh"
+#include "sieve_tma.cuh"
 #include "tree_impl.hpp"
 
 namespace pkd {
@@ -955,12 +955,9 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
   uint32_t* dctr;
   PKD_TRY(sc.get(&dctr, 32));
   PKD_CUDA(cudaMemsetAsync(dctr, 0, 32 * 4, s));
-  uint32_t* hctr = nullptr;
-  PKD_CUDA(cudaMallocHost((void**)&hctr, 128));
-  struct HostFree {
-    uint32_t* p;
-    ~HostFree() { cudaFreeHost(p); }
-  } hf{hctr};
+  PinnedBlock hblk(s);  // 128 bytes of host counters
+  uint32_t* hctr = (uint32_t*)hblk.p;
+  if (!hctr) return PKD_ENOMEM;
   uint32_t* d_ngroups = dctr + 4;
   uint32_t* d_nitems = dctr + 5;
   unsigned long long* d_total = (unsigned long long*)(dctr + 6);

@@ -45,7 +45,7 @@ def knobs(**kw):
         yield
     finally:
         for k in kw:
-            pkd.pkd_set_option(k, 0 if k != "tile" else 4096)
+            pkd.pkd_set_option(k, 0 if k != "tile" else 2048)
 
 
 def make_points(kind: str, n: int, d: int, seed: int) -> np.ndarray:

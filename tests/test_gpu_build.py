@@ -45,14 +45,14 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("base_kernel", [0, 1], ids=["sorted", "select"])
+@pytest.mark.parametrize("base_kernel,sieve_kernel", [(0, 0), (1, 1)], ids=["sorted-stream", "select-tiles"])
 @pytest.mark.parametrize("name,n,d,kind,over,kn", CASES, ids=[c[0] for c in CASES])
-def test_build_matches_oracle(name, n, d, kind, over, kn, base_kernel):
+def test_build_matches_oracle(name, n, d, kind, over, kn, base_kernel, sieve_kernel):
     pkd = _pkd()
     X = make_points(kind, n, d, 1000 + n + d)
     ids = ((np.arange(n, dtype=np.uint64) * 2654435761) % (1 << 32)).astype(np.uint32)
     p = pkd.Params(d=d, seed=42, **over)
-    with knobs(base_kernel=base_kernel, **kn):
+    with knobs(base_kernel=base_kernel, sieve_kernel=sieve_kernel, **kn):
         t = pkd.Tree(to_dev(X), ids_dev(ids), p)
         got = t.export()
     want = O.OracleTree(X, ids, oparams(p)).export()

@@ -61,13 +61,14 @@ def test_insert_delete_small_tree(kind):
     assert pr.delete(Z, sel) == 600
 
 
+@pytest.mark.parametrize("sieve_kernel", [0, 1], ids=["stream", "tiles"])
 @pytest.mark.parametrize("alpha", [(3, 10), (0, 1), (1, 2), (1, 10)])
-def test_update_sequences_forced_rounds(alpha):
+def test_update_sequences_forced_rounds(alpha, sieve_kernel):
     pkd = _pkd()
     d, n = 3, 20000
     X = make_points("uniform", n, d, 21)
     p = pkd.Params(d=d, phi=8, lam=3, sigma_log2=2, sigma_os=4, alpha_num=alpha[0], alpha_den=alpha[1])
-    with knobs(base_cap=256, skel_cap=64):
+    with knobs(base_cap=256, skel_cap=64, tile=512, sieve_kernel=sieve_kernel):
         pr = Pair(X, _ids(n), p)
         nxt = n
         rng = np.random.default_rng(5)

@@ -74,6 +74,17 @@ int cuda_err(cudaError_t e);
 // the next instead of being returned to the driver at every synchronisation.
 cudaMemPool_t mem_pool();
 
+// Large blocks (tree arenas and node arrays) go through a small cache in
+// front of the pool: a freed block is kept with an event recorded on the
+// freeing stream and handed to the next request it fits (the requesting
+// stream waits on that event), so building, updating and freeing trees in a
+// loop does not map and unmap gigabytes each time.  Blocks below
+// BIG_BLOCK_MIN go straight to the pool.  On exhaustion the cache is
+// emptied and the request retried once.
+constexpr size_t BIG_BLOCK_MIN = (size_t)64 << 20;
+cudaError_t big_alloc(void** p, size_t bytes, cudaStream_t s);
+void big_free(void* p, cudaStream_t s);
+
 // Stream-ordered allocation from that pool.
 template <class T>
 int dalloc(T** p, size_t n, cudaStream_t s) {

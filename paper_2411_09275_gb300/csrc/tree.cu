@@ -190,6 +190,84 @@ uint64_t shared_region_for(const Params& p, uint64_t n) {
   return per * (8 * (n / cap) + 2048);
 }
 
+struct CachedBlock {
+  void* p;
+  size_t bytes;
+  int dev;
+  cudaEvent_t ev;  // recorded on the stream that freed the block
+};
+static std::mutex g_big_mu;
+static std::vector<CachedBlock> g_big_cache;
+static std::map<void*, std::pair<size_t, int>> g_big_live;  // block -> (bytes, device)
+static size_t g_big_cached = 0;
+constexpr size_t BIG_CACHE_MAX = (size_t)128 << 30;
+
+static void big_flush_locked() {
+  for (CachedBlock& b : g_big_cache) {
+    cudaEventSynchronize(b.ev);
+    cudaEventDestroy(b.ev);
+    cudaFree(b.p);
+  }
+  g_big_cache.clear();
+  g_big_cached = 0;
+}
+
+cudaError_t big_alloc(void** p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  if (bytes < BIG_BLOCK_MIN) return cudaMallocFromPoolAsync(p, bytes, mem_pool(), s);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(g_big_mu);
+  // the smallest cached block that fits and wastes at most half of itself
+  int best = -1;
+  for (size_t k = 0; k < g_big_cache.size(); ++k) {
+    const CachedBlock& b = g_big_cache[k];
+    if (b.dev == dev && b.bytes >= bytes && b.bytes <= 2 * bytes && (best < 0 || b.bytes < g_big_cache[best].bytes))
+      best = (int)k;
+  }
+  if (best >= 0) {
+    CachedBlock b = g_big_cache[best];
+    g_big_cache.erase(g_big_cache.begin() + best);
+    g_big_cached -= b.bytes;
+    cudaStreamWaitEvent(s, b.ev, 0);
+    cudaEventDestroy(b.ev);
+    g_big_live[b.p] = {b.bytes, dev};
+    *p = b.p;
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, mem_pool(), s);
+  if (e == cudaErrorMemoryAllocation && !g_big_cache.empty()) {
+    cudaGetLastError();
+    big_flush_locked();
+    e = cudaMallocFromPoolAsync(p, bytes, mem_pool(), s);
+  }
+  if (e == cudaSuccess) g_big_live[*p] = {bytes, dev};
+  return e;
+}
+
+void big_free(void* p, cudaStream_t s) {
+  if (!p) return;
+  std::lock_guard<std::mutex> g(g_big_mu);
+  auto it = g_big_live.find(p);
+  if (it == g_big_live.end()) {  // a small block from the pool
+    cudaFreeAsync(p, s);
+    return;
+  }
+  const size_t bytes = it->second.first;
+  const int dev = it->second.second;
+  g_big_live.erase(it);
+  cudaEvent_t ev = nullptr;
+  if (g_big_cached + bytes <= BIG_CACHE_MAX && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess &&
+      cudaEventRecord(ev, s) == cudaSuccess) {
+    g_big_cache.push_back(CachedBlock{p, bytes, dev, ev});
+    g_big_cached += bytes;
+    return;
+  }
+  cudaGetLastError();
+  if (ev) cudaEventDestroy(ev);
+  cudaFreeAsync(p, s);
+}
+
 static std::mutex g_pin_mu;
 static std::vector<void*> g_pin_free;
 
@@ -230,7 +308,7 @@ void tree_release(TreeMem& t) {
   cudaStream_t s = 0;
   for (void* p : {(void*)t.A.c, (void*)t.A.id, (void*)t.nodes, (void*)t.ndim, (void*)t.shared_next,
                   (void*)t.dead, (void*)t.aux, (void*)t.st})
-    if (p) cudaFreeAsync(p, s);
+    big_free(p, s);
   pinned_put_after(s, t.st_host);
   t = TreeMem{};
 }
@@ -258,10 +336,10 @@ int tree_alloc(TreeMem& t, const Params& p, uint64_t cap, uint64_t shared_cap, c
   if (t.node_cap >= 0xFFFFFFF0ull) return PKD_EINVAL;
   cudaError_t e;
   cudaMemPool_t pool = mem_pool();
-  e = cudaMallocFromPoolAsync((void**)&t.A.c, (size_t)p.d * t.cap * 4, pool, s);
-  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&t.A.id, (size_t)t.cap * 4, pool, s);
-  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&t.nodes, (size_t)t.node_cap * sizeof(Node), pool, s);
-  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&t.ndim, (size_t)t.node_cap, pool, s);
+  e = big_alloc((void**)&t.A.c, (size_t)p.d * t.cap * 4, s);
+  if (e == cudaSuccess) e = big_alloc((void**)&t.A.id, (size_t)t.cap * 4, s);
+  if (e == cudaSuccess) e = big_alloc((void**)&t.nodes, (size_t)t.node_cap * sizeof(Node), s);
+  if (e == cudaSuccess) e = big_alloc((void**)&t.ndim, (size_t)t.node_cap, s);
   if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&t.shared_next, 16, pool, s);
   if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&t.st, sizeof(DevStatus), pool, s);
   static_assert(sizeof(DevStatus) <= PINNED_BLOCK, "status block");
@@ -316,7 +394,13 @@ int pkd_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const pkd_
   if (!ok) return PKD_EINVAL;
   trace_mark(s, "build: validate");
   pkd_tree* t = new pkd_tree();
-  const uint64_t cap = n + n / 4 + 4096;
+  // Rebuilt subtrees take fresh arena ranges, so a batch insert that
+  // touches most leaves needs about n + (its points + the leaves' points)
+  // positions: leave room for that before the first growth (a copy).
+  // Node slots are 32-bit (2 per arena position), so very large trees
+  // start closer to their size.
+  uint64_t cap = 2 * n + n / 4 + 4096;
+  if (shared_region_for(p, cap) + 2 * cap >= 0xF0000000ull) cap = n + n / 4 + 4096;
   e = tree_alloc(t->m, p, cap, shared_region_for(p, cap), s);
   if (e) {
     delete t;

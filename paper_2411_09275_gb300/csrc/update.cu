@@ -862,15 +862,13 @@ static int ensure_capacity(TreeMem& t, uint64_t need, cudaStream_t s) {
   Pts A2{};
   Node* n2 = nullptr;
   uint8_t* d2 = nullptr;
-  cudaMemPool_t pool = mem_pool();
-  cudaError_t e = cudaMallocFromPoolAsync((void**)&A2.c, (size_t)t.p.d * ncap * 4, pool, s);
-  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&A2.id, (size_t)ncap * 4, pool, s);
-  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&n2, (size_t)nnode * sizeof(Node), pool, s);
-  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&d2, (size_t)nnode, pool, s);
+  cudaError_t e = big_alloc((void**)&A2.c, (size_t)t.p.d * ncap * 4, s);
+  if (e == cudaSuccess) e = big_alloc((void**)&A2.id, (size_t)ncap * 4, s);
+  if (e == cudaSuccess) e = big_alloc((void**)&n2, (size_t)nnode * sizeof(Node), s);
+  if (e == cudaSuccess) e = big_alloc((void**)&d2, (size_t)nnode, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    for (void* q : {(void*)A2.c, (void*)A2.id, (void*)n2, (void*)d2})
-      if (q) cudaFreeAsync(q, s);
+    for (void* q : {(void*)A2.c, (void*)A2.id, (void*)n2, (void*)d2}) big_free(q, s);
     return PKD_ENOMEM;
   }
   A2.stride = ncap;
@@ -885,17 +883,17 @@ static int ensure_capacity(TreeMem& t, uint64_t need, cudaStream_t s) {
   uint8_t* dead2 = nullptr;
   uint32_t* aux2 = nullptr;
   if (t.dead) {
-    PKD_CUDA(cudaMallocFromPoolAsync((void**)&dead2, ncap, pool, s));
+    PKD_CUDA(big_alloc((void**)&dead2, ncap, s));
     PKD_CUDA(cudaMemsetAsync(dead2, 0, ncap, s));
     PKD_CUDA(cudaMemcpyAsync(dead2, t.dead, t.cap, cudaMemcpyDeviceToDevice, s));
   }
   if (t.aux) {
-    PKD_CUDA(cudaMallocFromPoolAsync((void**)&aux2, nnode * 4, pool, s));
+    PKD_CUDA(big_alloc((void**)&aux2, nnode * 4, s));
     PKD_CUDA(cudaMemsetAsync(aux2, 0, nnode * 4, s));
     PKD_CUDA(cudaMemcpyAsync(aux2, t.aux, t.node_cap * 4, cudaMemcpyDeviceToDevice, s));
   }
   for (void* q : {(void*)t.A.c, (void*)t.A.id, (void*)t.nodes, (void*)t.ndim, (void*)t.dead, (void*)t.aux})
-    if (q) cudaFreeAsync(q, s);
+    big_free(q, s);
   t.dead = dead2;
   t.aux = aux2;
   t.A = A2;
@@ -908,11 +906,11 @@ static int ensure_capacity(TreeMem& t, uint64_t need, cudaStream_t s) {
 
 static int ensure_delete_scratch(TreeMem& t, cudaStream_t s) {
   if (!t.dead) {
-    PKD_CUDA(cudaMallocFromPoolAsync((void**)&t.dead, t.cap, mem_pool(), s));
+    PKD_CUDA(big_alloc((void**)&t.dead, t.cap, s));
     PKD_CUDA(cudaMemsetAsync(t.dead, 0, t.cap, s));
   }
   if (!t.aux) {
-    PKD_CUDA(cudaMallocFromPoolAsync((void**)&t.aux, t.node_cap * 4, mem_pool(), s));
+    PKD_CUDA(big_alloc((void**)&t.aux, t.node_cap * 4, s));
     PKD_CUDA(cudaMemsetAsync(t.aux, 0, t.node_cap * 4, s));
   }
   return PKD_OK;

@@ -247,7 +247,9 @@ __global__ void __launch_bounds__(SS_THREADS, 1) k_smem_sorted(SmemArgs a) {
   cx.st = a.st;
   unsigned* hist = (unsigned*)wstack;  // the task stacks are not in use yet
 #pragma unroll 1
-  for (int k = 0; k < D; ++k) presort_dim<D>(cx, k, vmn[k], vmx[k], n, hist, sred + 2 * D);
+  for (int k = 0; k < D; ++k)
+    if (!presort_dim_msd<D>(cx, k, vmn[k], vmx[k], n, hist, sred + 2 * D))
+      presort_dim<D>(cx, k, vmn[k], vmx[k], n, hist, sred + 2 * D);
   uint32_t map = 0;
 #pragma unroll
   for (int k = 0; k < D; ++k) map |= (uint32_t)k << (4 * k);

@@ -220,6 +220,83 @@ __device__ void presort_dim(const SCtx<D>& cx, int k, int vmin, int vmax, int n,
   }
 }
 
+// Faster presort for the common case: one most-significant-digit counting
+// pass over MSD_BINS bins of the top varying bits (plain shared-memory
+// atomics, no ranking), then every bin, now a contiguous run of the list, is
+// sorted by (coordinate, point index) by one thread.  The order is the same
+// as the stable LSD sort's.  Returns false, before writing the list, when a
+// bin holds more than MSD_MAX_BUCKET points (clustered coordinates); the
+// caller then sorts that dimension with presort_dim.
+constexpr int MSD_BITS = 12;
+constexpr int MSD_BINS = 1 << MSD_BITS;  // 4096 counters fill the 16 KB radix region
+constexpr int MSD_MAX_BUCKET = 64;
+
+template <int D>
+__device__ bool presort_dim_msd(const SCtx<D>& cx, int k, int vmin, int vmax, int n, unsigned* hist, int* tmp) {
+  static_assert(MSD_BINS == 8 * SS_THREADS, "eight bins per thread");
+  const int32_t* Xk = cx.X + k * cx.cap;
+  uint16_t* target = cx.list(k);
+  const unsigned range = (unsigned)vmax - (unsigned)vmin;
+  const int bits = range ? 32 - __clz(range) : 0;
+  const int shift = max(0, bits - MSD_BITS);
+  const int tid = threadIdx.x, lane = lane_id(), w = warp_id();
+#pragma unroll
+  for (int q = 0; q < 8; ++q) hist[q * SS_THREADS + tid] = 0;
+  __syncthreads();
+  for (int i = tid; i < n; i += SS_THREADS) atomicAdd(&hist[((unsigned)Xk[i] - (unsigned)vmin) >> shift], 1u);
+  __syncthreads();
+  // bin starts: thread t owns bins [8t, 8t + 8)
+  unsigned c[8], sum = 0, mx = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    c[q] = hist[8 * tid + q];
+    sum += c[q];
+    mx = max(mx, c[q]);
+  }
+  const unsigned inc = (unsigned)warp_incl_scan((int)sum);
+  const unsigned wmx = (unsigned)warp_max((int)mx);
+  if (lane == 31) tmp[w] = (int)inc;
+  if (lane == 0) tmp[SS_NW + w] = (int)wmx;
+  __syncthreads();
+  unsigned run = inc - sum, big = 0;
+  for (int v = 0; v < SS_NW; ++v) {
+    if (v < w) run += (unsigned)tmp[v];
+    big = max(big, (unsigned)tmp[SS_NW + v]);
+  }
+  if (big > (unsigned)MSD_MAX_BUCKET) {
+    __syncthreads();  // every thread has read tmp before the caller reuses it
+    return false;
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    hist[8 * tid + q] = run;
+    run += c[q];
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += SS_THREADS)
+    target[atomicAdd(&hist[((unsigned)Xk[i] - (unsigned)vmin) >> shift], 1u)] = (uint16_t)i;
+  __syncthreads();
+  // hist[b] is now the end of bin b; sort each bin by (coordinate, index)
+  for (int b = tid; b < MSD_BINS; b += SS_THREADS) {
+    const int e = (int)hist[b], st = b ? (int)hist[b - 1] : 0;
+    for (int i = st + 1; i < e; ++i) {
+      const int v = target[i];
+      const int32_t kv = Xk[v];
+      int j = i - 1;
+      while (j >= st) {
+        const int u = target[j];
+        const int32_t ku = Xk[u];
+        if (ku < kv || (ku == kv && u < v)) break;
+        target[j + 1] = (uint16_t)u;
+        --j;
+      }
+      target[j + 1] = (uint16_t)v;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 // Node steps (uniform within the team that calls them)
 // ---------------------------------------------------------------------------
@@ -248,33 +325,18 @@ __device__ __forceinline__ int upper_pos(const SCtx<D>& cx, const uint16_t* Lst,
 template <int D>
 __device__ __forceinline__ void semit_leaf(const Team& tm, const SCtx<D>& cx, const STask& tk) {
   const uint16_t* P = cx.list(mget(tk.map, 0));
-  constexpr int U = 2;
-  for (int i0 = tk.lo + tm.rank(); i0 < tk.hi; i0 += U * tm.size()) {
-    int pp[U];
-    int32_t v[U][D];
-    uint32_t id[U];
+  const uint64_t stride = cx.out.stride;
+  int32_t* oc = cx.out.c + cx.start;
+  uint32_t* oid = cx.out.id + cx.start;
+  for (int i = tk.lo + tm.rank(); i < tk.hi; i += tm.size()) {
+    const int p = P[i];
+    int32_t v[D];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = i0 + u * tm.size();
-      pp[u] = i < tk.hi ? (int)P[i] : -1;
-    }
+    for (int j = 0; j < D; ++j) v[j] = cx.key(j, p);
+    const uint32_t id = cx.ID[p];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (pp[u] >= 0) {
-#pragma unroll
-        for (int j = 0; j < D; ++j) v[u][j] = cx.key(j, pp[u]);
-        id[u] = cx.ID[pp[u]];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (pp[u] >= 0) {
-        const uint64_t g = cx.start + (uint64_t)(i0 + u * tm.size());
-#pragma unroll
-        for (int j = 0; j < D; ++j) cx.out.c[(uint64_t)j * cx.out.stride + g] = v[u][j];
-        cx.out.id[g] = id[u];
-      }
-    }
+    for (int j = 0; j < D; ++j) oc[(uint64_t)j * stride + i] = v[j];
+    oid[i] = id;
   }
   if (tm.leader()) {
     cx.nodes[tk.slot] = Node{0, (uint32_t)(tk.hi - tk.lo), (uint32_t)(cx.start + tk.lo), 0};
@@ -452,34 +514,46 @@ __device__ bool ssample_split(const Team& tm, const SCtx<D>& cx, const STask& tk
   return true;
 }
 
-// Stable split of src[a, b) by Xd[p] < x into dst: left entries from lb,
-// right entries from rb (both advanced).  One warp; loads are issued
-// SS_BATCH groups at a time before the stores.
-__device__ __forceinline__ void warp_split_run(const int32_t* Xd, int x, const uint16_t* src, uint16_t* dst, int a,
-                                               int b, int& lb, int& rb) {
+// One batch of B groups of 32 entries of src starting at base0 (entries at
+// b or beyond are absent): loads first, then the stable split by
+// Xd[p] < x into dst at lb (left) and rb (right), both advanced.
+template <int B>
+__device__ __forceinline__ void warp_split_batch(const int32_t* Xd, int x, const uint16_t* src, uint16_t* dst,
+                                                 int base0, int b, int& lb, int& rb) {
   const int lane = lane_id();
-  for (int base0 = a; base0 < b; base0 += 32 * SS_BATCH) {
-    int pp[SS_BATCH];
-    bool lf[SS_BATCH];
+  int pp[B];
+  bool lf[B];
 #pragma unroll
-    for (int u = 0; u < SS_BATCH; ++u) {
-      const int i = base0 + u * 32 + lane;
-      pp[u] = i < b ? (int)src[i] : -1;
-    }
+  for (int u = 0; u < B; ++u) {
+    const int i = base0 + u * 32 + lane;
+    pp[u] = i < b ? (int)src[i] : -1;
+  }
 #pragma unroll
-    for (int u = 0; u < SS_BATCH; ++u) lf[u] = pp[u] >= 0 && Xd[pp[u]] < x;
+  for (int u = 0; u < B; ++u) lf[u] = pp[u] >= 0 && Xd[pp[u]] < x;
 #pragma unroll
-    for (int u = 0; u < SS_BATCH; ++u) {
-      if (base0 + u * 32 < b) {
-        const unsigned bl = __ballot_sync(FULL_MASK, lf[u]);
-        const unsigned br = __ballot_sync(FULL_MASK, pp[u] >= 0 && !lf[u]);
-        if (lf[u]) dst[lb + __popc(bl & lanemask_lt())] = (uint16_t)pp[u];
-        else if (pp[u] >= 0) dst[rb + __popc(br & lanemask_lt())] = (uint16_t)pp[u];
-        lb += __popc(bl);
-        rb += __popc(br);
-      }
+  for (int u = 0; u < B; ++u) {
+    const int rem = b - (base0 + u * 32);
+    if (rem > 0) {
+      const unsigned vm = rem >= 32 ? FULL_MASK : ((1u << rem) - 1u);  // lanes holding an entry
+      const unsigned bl = __ballot_sync(FULL_MASK, lf[u]), br = vm & ~bl;
+      if (lf[u]) dst[lb + __popc(bl & lanemask_lt())] = (uint16_t)pp[u];
+      else if (pp[u] >= 0) dst[rb + __popc(br & lanemask_lt())] = (uint16_t)pp[u];
+      lb += __popc(bl);
+      rb += __popc(br);
     }
   }
+}
+
+// Stable split of src[a, b) by Xd[p] < x into dst: left entries from lb,
+// right entries from rb (both advanced).  One warp; the batch size follows
+// the run's length, so a short run issues no empty groups.
+__device__ __forceinline__ void warp_split_run(const int32_t* Xd, int x, const uint16_t* src, uint16_t* dst, int a,
+                                               int b, int& lb, int& rb) {
+  int base0 = a;
+  for (; b - base0 > 128; base0 += 256) warp_split_batch<8>(Xd, x, src, dst, base0, b, lb, rb);
+  if (b - base0 > 64) warp_split_batch<4>(Xd, x, src, dst, base0, b, lb, rb);
+  else if (b - base0 > 32) warp_split_batch<2>(Xd, x, src, dst, base0, b, lb, rb);
+  else if (b - base0 > 0) warp_split_batch<1>(Xd, x, src, dst, base0, b, lb, rb);
 }
 
 // Number of entries of src[a, b) with Xd[p] < x, counted by one warp.

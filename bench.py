@@ -42,6 +42,11 @@ WORKLOADS = {
     "build1e6_d2_ins1e4_del1e4": dict(n=1_000_000, d=2, m=10_000, kind="uniform"),
     # small case for quick checks
     "build1e7_d3_ins1e6_del1e6": dict(n=10_000_000, d=3, m=1_000_000, kind="uniform"),
+    # batched build: 4096 independent 3-D uniform trees, sizes log-uniform in
+    # [1e3, 1e6] (about 5.9e8 points), one pass against one build per tree
+    "forest4096_d3": dict(forest=True, trees=4096, lo=1e3, hi=1e6, d=3, kind="uniform", n=0, m=0),
+    # the same with 256 trees, for quick checks
+    "forest256_d3": dict(forest=True, trees=256, lo=1e3, hi=1e6, d=3, kind="uniform", n=0, m=0),
 }
 DEFAULT_WORKLOAD = "build1e8_d3_ins1e7_del1e7"
 
@@ -221,6 +226,145 @@ def run_reference(args, wl):
     return 0
 
 
+def forest_sizes(wl: dict) -> np.ndarray:
+    """Tree sizes, log-uniform in [lo, hi], from the seeded stream 21."""
+    from paper_2411_09275_gb300 import inputs as I
+
+    u = I.uniform(wl["trees"], 1, 21)[:, 0].astype(np.float64) / float(1 << 30)
+    lo, hi = np.log(wl["lo"]), np.log(wl["hi"])
+    return np.floor(np.exp(lo + u * (hi - lo))).astype(np.int64)
+
+
+def run_forest(args, wl):
+    """Batched build of many trees in one pass (pkd_build_forest) against one
+    pkd_build per tree on the same points; prints one JSON line."""
+    import torch
+
+    from paper_2411_09275_gb300 import inputs as I
+    from paper_2411_09275_gb300 import pkd
+
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkd.lib()
+    sizes = forest_sizes(wl)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    N, d, T = int(off[-1]), wl["d"], wl["trees"]
+    X = I.points(wl["kind"], N, d, I.SEED_DATA + 1000 * rank)
+    hX = torch.from_numpy(X).pin_memory()
+    gX = hX.to(dev)
+    params = pkd.Params(d=d)
+    stream = torch.cuda.current_stream(dev)
+
+    def forest_once(src):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        f = pkd.pkd_build_forest(src, None, off, params, stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        pkd.pkd_forest_free(f)
+        return a.elapsed_time(b)
+
+    for _ in range(max(args.warmup, 3)):
+        forest_once(gX)
+    pkd.pkd_kernel_timing(True)
+    with Clocks(local) as clk:
+        ms = [forest_once(gX) for _ in range(args.steps)]
+        launches = pkd.pkd_kernel_stats("launches")[0]
+        kst = {k: pkd.pkd_kernel_stats(k) for k in TIMED_KERNELS}
+    pkd.pkd_kernel_timing(False)
+    t_forest = barrier_max(sum(ms) / len(ms), ws, dev)
+
+    # one pkd_build per tree, the plain path (each tree's own launches and syncs)
+    def per_tree_once():
+        tot = 0.0
+        for t in range(T):
+            a, b = int(off[t]), int(off[t + 1])
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h = pkd.pkd_build(gX[a:b], None, params, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            tot += e0.elapsed_time(e1)
+            pkd.pkd_free(h)
+        return tot
+
+    for t in range(min(T, 16)):
+        pkd.pkd_free(pkd.pkd_build(gX[int(off[t]):int(off[t + 1])], None, params, stream))
+    t_plain = barrier_max(per_tree_once(), ws, dev)
+
+    # end to end: the points come from pinned host memory every build
+    def e2e_once():
+        g = hX.to(dev, non_blocking=True)
+        f = pkd.pkd_build_forest(g, None, off, params, stream)
+        pkd.pkd_forest_free(f)
+
+    e2e_once()
+    torch.cuda.synchronize(dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        e2e_once()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    t_e2e = barrier_max(a.elapsed_time(b) / args.steps, ws, dev)
+
+    if rank != 0:
+        return 0
+    peak, peak_src = measured_peaks()
+    kernels = {}
+    for name, (cnt, kms, items) in kst.items():
+        bb = algo_bytes(name, d)
+        if cnt == 0 or kms <= 0:
+            continue
+        gbs = (bb * items / (kms / 1e3) / 1e9) if (bb and items) else None
+        kernels[name] = {"launches": cnt, "ms_per_step": kms / args.steps, "items_per_launch": items / cnt,
+                         "algo_bytes_per_item": bb, "achieved_gbs": gbs}
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"]) if kernels else None
+    roof = None
+    if dom:
+        kd = kernels[dom]
+        tr = dram_traffic().get(dom)
+        roof = {"bound": "hbm", "kernel": dom, "achieved": kd["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                "frac": (kd["achieved_gbs"] / peak) if kd["achieved_gbs"] else None,
+                "traffic": (tr["dram_bytes_per_item"] * kd["items_per_launch"]) if tr else None,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle as O
+
+        k = 0
+        t0 = time.perf_counter()
+        pts = 0
+        while k < T and time.perf_counter() - t0 < 10.0:
+            aa, bb_ = int(off[k]), int(off[k + 1])
+            O.OracleTree(X[aa:bb_], None, O.Params(d=d)).close()
+            pts += bb_ - aa
+            k += 1
+        cpu = {"value": pts / (time.perf_counter() - t0) / 1e6, "unit": "Mpts/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle, 1 thread: builds of the first {k} trees ({pts} points)"}
+    line = {"metric": METRIC, "value": ws * N / (t_forest / 1e3) / 1e6, "unit": "Mpts/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_forest, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "trees": T, "points": N, "d": d,
+                       "sizes": f"log-uniform in [{wl['lo']:.0e}, {wl['hi']:.0e}], seed 21",
+                       "distribution": wl["kind"], "phi": 32, "lambda": 6, "sample_rate": "1/64", "sigma_os": 32,
+                       "l2": "inputs larger than L2 (no flush needed)",
+                       "parallelism": f"independent forest per GPU x{ws}"},
+            "per_tree": {"value": ws * N / (t_plain / 1e3) / 1e6, "unit": "Mpts/s", "ms": t_plain,
+                         "how": "one pkd_build per tree on the same device-resident points"},
+            "batched_over_per_tree": t_plain / t_forest,
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": ws * N / (t_e2e / 1e3) / 1e6, "unit": "Mpts/s",
+                    "h2d_bytes_per_step": int(hX.numel() * 4), "d2h_bytes_per_step": 0},
+            "gpu_launches": launches // max(args.steps, 1), "clocks": clk.summary(), "kernels": kernels}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def config_of(args, wl):
     return {"workload": args.workload, "n": wl["n"], "d": wl["d"], "m_insert": wl["m"],
             "m_delete": wl["m"], "distribution": wl["kind"], "phi": 32, "lambda": 6,
@@ -242,6 +386,12 @@ def main():
     ap.add_argument("--varden", action="store_true", help="also time the varden-like variant")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
+    if wl.get("forest"):
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the forest workload has no reference arm; "
+                              "its per-tree baseline is reported in the same line"}))
+            return 0
+        return run_forest(args, wl)
     if args.impl == "reference":
         return run_reference(args, wl)
 

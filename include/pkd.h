@@ -163,6 +163,32 @@ int pkd_height(const pkd_tree* tree, int* height);
 /* Free the tree and all device memory it owns (NULL is a no-op). */
 void pkd_free(pkd_tree* tree);
 
+/* Batched build of independent trees ("forest"): one pass over n_trees
+ * point sets, each built exactly as pkd_build would build it alone (Alg. 1
+ * per tree: its own root at depth 0, its own samples), with the sieve
+ * rounds and base cases of all trees sharing the same launches.  The paper
+ * builds one tree per call; batching many trees is this library's
+ * extension.
+ *   coords   device, [n][d] int32, the trees' points one after another
+ *   ids      device, [n] uint32, or NULL for ids 0..n-1 (positions in coords)
+ *   offsets  HOST, [n_trees + 1] uint64: tree i owns points
+ *            offsets[i] .. offsets[i+1]; offsets[0] = 0, non-decreasing,
+ *            n = offsets[n_trees] < 2^31 (empty trees are allowed)
+ *   n_trees  1 .. 2^24 - 1
+ * Errors: PKD_EINVAL (parameters, offsets, coordinates), PKD_ENOMEM,
+ * PKD_ECUDA.  A forest is read-only: its trees take exports and k-NN queries
+ * (same semantics as pkd_export / pkd_knn). */
+typedef struct pkd_forest pkd_forest;
+int pkd_build_forest(const int32_t* coords, const uint32_t* ids, const uint64_t* offsets, uint32_t n_trees,
+                     const pkd_params* params, void* stream, pkd_forest** out);
+uint32_t pkd_forest_trees(const pkd_forest* forest);
+uint64_t pkd_forest_size(const pkd_forest* forest, uint32_t tree);
+int pkd_forest_export(const pkd_forest* forest, uint32_t tree, uint8_t* dims, int32_t* splits, uint64_t* sizes,
+                      uint64_t* n_nodes, uint32_t* leaf_ids, uint64_t* leaf_offsets, uint64_t* n_leaves);
+int pkd_forest_knn(const pkd_forest* forest, uint32_t tree, const int32_t* queries, uint64_t q, int k,
+                   uint32_t* out_ids, int64_t* out_d2, void* stream);
+void pkd_forest_free(pkd_forest* forest);
+
 /* Human-readable text for an error code. */
 const char* pkd_strerror(int code);
 

@@ -188,27 +188,41 @@ __global__ void __launch_bounds__(SS_THREADS, 1) k_smem_sorted(SmemArgs a) {
     lmn[j] = INT32_MAX;
     lmx[j] = INT32_MIN;
   }
-  for (int i = tid; i < n; i += SS_THREADS) {
-    const uint64_t g = seg.start + (uint64_t)i;
-    int32_t v[D];
-    uint32_t id;
-    if (seg.where == IN_INPUT) {
+  // four points per thread in flight: every load of a batch before its stores
+  constexpr int LU = 4;
+  for (int i0 = tid; i0 < n; i0 += LU * SS_THREADS) {
+    int32_t v[LU][D];
+    uint32_t id[LU];
 #pragma unroll
-      for (int j = 0; j < D; ++j) v[j] = a.in_coords[g * (uint64_t)D + j];
-      id = a.in_ids ? a.in_ids[g] : (uint32_t)g;
-    } else {
-      const Pts& S = seg.where == IN_A ? a.A : a.B;
+    for (int u = 0; u < LU; ++u) {
+      const int i = i0 + u * SS_THREADS;
+      if (i < n) {
+        const uint64_t g = seg.start + (uint64_t)i;
+        if (seg.where == IN_INPUT) {
 #pragma unroll
-      for (int j = 0; j < D; ++j) v[j] = S.c[(uint64_t)j * S.stride + g];
-      id = S.id[g];
+          for (int j = 0; j < D; ++j) v[u][j] = a.in_coords[g * (uint64_t)D + j];
+          id[u] = a.in_ids ? a.in_ids[g] : (uint32_t)g;
+        } else {
+          const Pts& S = seg.where == IN_A ? a.A : a.B;
+#pragma unroll
+          for (int j = 0; j < D; ++j) v[u][j] = S.c[(uint64_t)j * S.stride + g];
+          id[u] = S.id[g];
+        }
+      }
     }
 #pragma unroll
-    for (int j = 0; j < D; ++j) {
-      X[j * cap + i] = v[j];
-      lmn[j] = min(lmn[j], v[j]);
-      lmx[j] = max(lmx[j], v[j]);
+    for (int u = 0; u < LU; ++u) {
+      const int i = i0 + u * SS_THREADS;
+      if (i < n) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          X[j * cap + i] = v[u][j];
+          lmn[j] = min(lmn[j], v[u][j]);
+          lmx[j] = max(lmx[j], v[u][j]);
+        }
+        ID[i] = id[u];
+      }
     }
-    ID[i] = id;
   }
 #pragma unroll
   for (int j = 0; j < D; ++j) {
@@ -255,6 +269,20 @@ __global__ void __launch_bounds__(SS_THREADS, 1) k_smem_sorted(SmemArgs a) {
   for (int k = 0; k < D; ++k) map |= (uint32_t)k << (4 * k);
   srun_tasks<D>(cx, STask{0, (uint16_t)n, 0, 0, 0, seg.depth, seg.root, map, 0}, sred, wstack);
   __syncthreads();
+  // every leaf left its points' indices in list 0: write the subproblem out
+  // in leaf order, coalesced
+  {
+    const uint16_t* P = cx.list(0);
+    int32_t* oc = a.A.c + seg.start;
+    uint32_t* oid = a.A.id + seg.start;
+    for (int i = tid; i < n; i += SS_THREADS) {
+      const int p = P[i];
+      if (p >= n) continue;  // only after a recorded error, when leaves are missing
+#pragma unroll
+      for (int j = 0; j < D; ++j) oc[(uint64_t)j * a.A.stride + i] = X[j * cap + p];
+      oid[i] = ID[p];
+    }
+  }
   if (tid == 0) atomicMax(&a.st->max_depth, ctl->maxd);
 }
 

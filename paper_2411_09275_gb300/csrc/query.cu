@@ -239,11 +239,18 @@ extern "C" {
 
 int pkd_knn(const pkd_tree* tc, const int32_t* queries, uint64_t q, int k, uint32_t* out_ids,
             int64_t* out_d2, void* stream) {
-  if (!tc || k < 1 || k > 128) return PKD_EINVAL;
+  if (!tc) return PKD_EINVAL;
+  TreeMem& t = const_cast<TreeMem&>(tc->m);
+  return knn_on(t, t.root, queries, q, k, out_ids, out_d2, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+int pkd::knn_on(TreeMem& t, uint32_t root, const int32_t* queries, uint64_t q, int k, uint32_t* out_ids,
+                int64_t* out_d2, cudaStream_t s) {
+  if (k < 1 || k > 128) return PKD_EINVAL;
   if (q == 0) return PKD_OK;
   if (!queries || !out_ids || !out_d2) return PKD_EINVAL;
-  TreeMem& t = const_cast<TreeMem&>(tc->m);
-  cudaStream_t s = (cudaStream_t)stream;
   bool ok;
   PKD_TRY_(validate_coords(queries, q * (uint64_t)t.p.d, s, &ok));
   if (!ok) return PKD_EINVAL;
@@ -253,7 +260,7 @@ int pkd_knn(const pkd_tree* tc, const int32_t* queries, uint64_t q, int k, uint3
   a.nodes = t.nodes;
   a.ndim = t.ndim;
   a.A = t.A;
-  a.root = t.root;
+  a.root = root;
   a.q = queries;
   a.nq = q;
   a.k = k;
@@ -264,6 +271,8 @@ int pkd_knn(const pkd_tree* tc, const int32_t* queries, uint64_t q, int k, uint3
   PKD_CUDA(cudaGetLastError());
   return PKD_OK;
 }
+
+extern "C" {
 
 int pkd_range_count(const pkd_tree* tc, const int32_t* lo, const int32_t* hi, uint64_t q,
                     uint64_t* out_counts, void* stream) {

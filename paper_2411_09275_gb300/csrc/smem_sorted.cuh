@@ -322,21 +322,17 @@ __device__ __forceinline__ int upper_pos(const SCtx<D>& cx, const uint16_t* Lst,
   return a;
 }
 
+// A finished leaf: its node record, and its points' indices moved into
+// list buffer 0 at its positions (no other node uses positions [lo, hi) of
+// any buffer), from which the CTA writes every point out in one coalesced
+// pass at the end.
 template <int D>
 __device__ __forceinline__ void semit_leaf(const Team& tm, const SCtx<D>& cx, const STask& tk) {
-  const uint16_t* P = cx.list(mget(tk.map, 0));
-  const uint64_t stride = cx.out.stride;
-  int32_t* oc = cx.out.c + cx.start;
-  uint32_t* oid = cx.out.id + cx.start;
-  for (int i = tk.lo + tm.rank(); i < tk.hi; i += tm.size()) {
-    const int p = P[i];
-    int32_t v[D];
-#pragma unroll
-    for (int j = 0; j < D; ++j) v[j] = cx.key(j, p);
-    const uint32_t id = cx.ID[p];
-#pragma unroll
-    for (int j = 0; j < D; ++j) oc[(uint64_t)j * stride + i] = v[j];
-    oid[i] = id;
+  const int b0 = mget(tk.map, 0);
+  if (b0 != 0) {
+    const uint16_t* P = cx.list(b0);
+    uint16_t* Q = cx.list(0);
+    for (int i = tk.lo + tm.rank(); i < tk.hi; i += tm.size()) Q[i] = P[i];
   }
   if (tm.leader()) {
     cx.nodes[tk.slot] = Node{0, (uint32_t)(tk.hi - tk.lo), (uint32_t)(cx.start + tk.lo), 0};

@@ -313,6 +313,44 @@ void tree_release(TreeMem& t) {
   t = TreeMem{};
 }
 
+int export_from(const HostTree& h, uint32_t root, uint64_t top, uint64_t size, uint8_t* dims, int32_t* splits,
+                uint64_t* sizes, uint64_t* n_nodes, uint32_t* leaf_ids, uint64_t* leaf_offsets, uint64_t* n_leaves) {
+  uint64_t nn = 0, nl = 0, nid = 0;
+  std::vector<uint32_t> stack;
+  stack.push_back(root);
+  while (!stack.empty()) {
+    const uint32_t v = stack.back();
+    stack.pop_back();
+    if (v >= h.nodes.size() || nn > h.nodes.size()) return PKD_EINTERNAL;
+    const Node& nd = h.nodes[v];
+    const uint8_t dm = h.ndim[v];
+    if (dm == PKD_LEAF) {
+      if ((uint64_t)nd.a + nd.size > top || nid + nd.size > size) return PKD_EINTERNAL;
+      if (dims) dims[nn] = PKD_LEAF;
+      if (splits) splits[nn] = 0;
+      if (sizes) sizes[nn] = nd.size;
+      if (leaf_offsets) leaf_offsets[nl] = nid;
+      if (leaf_ids) {
+        for (uint32_t k = 0; k < nd.size; ++k) leaf_ids[nid + k] = h.ids[(uint64_t)nd.a + k];
+        std::sort(leaf_ids + nid, leaf_ids + nid + nd.size);
+      }
+      nid += nd.size;
+      ++nl;
+    } else {
+      if (dims) dims[nn] = dm;
+      if (splits) splits[nn] = nd.split;
+      if (sizes) sizes[nn] = nd.size;
+      stack.push_back(nd.b);
+      stack.push_back(nd.a);
+    }
+    ++nn;
+  }
+  if (leaf_offsets) leaf_offsets[nl] = nid;
+  if (n_nodes) *n_nodes = nn;
+  if (n_leaves) *n_leaves = nl;
+  return PKD_OK;
+}
+
 int download_tree(const TreeMem& t, HostTree& h, bool with_ids) {
   const uint64_t used = t.shared_cap + 2 * t.top;
   h.nodes.resize(used);
@@ -447,40 +485,8 @@ int pkd_export(const pkd_tree* tc, uint8_t* dims, int32_t* splits, uint64_t* siz
   HostTree h;
   int e = download_tree(tc->m, h);
   if (e) return e;
-  uint64_t nn = 0, nl = 0, nid = 0;
-  std::vector<uint32_t> stack;
-  stack.push_back(tc->m.root);
-  while (!stack.empty()) {
-    const uint32_t v = stack.back();
-    stack.pop_back();
-    if (v >= h.nodes.size() || nn > h.nodes.size()) return PKD_EINTERNAL;
-    const Node& nd = h.nodes[v];
-    const uint8_t dm = h.ndim[v];
-    if (dm == PKD_LEAF) {
-      if ((uint64_t)nd.a + nd.size > tc->m.top || nid + nd.size > tc->m.size) return PKD_EINTERNAL;
-      if (dims) dims[nn] = PKD_LEAF;
-      if (splits) splits[nn] = 0;
-      if (sizes) sizes[nn] = nd.size;
-      if (leaf_offsets) leaf_offsets[nl] = nid;
-      if (leaf_ids) {
-        for (uint32_t k = 0; k < nd.size; ++k) leaf_ids[nid + k] = h.ids[(uint64_t)nd.a + k];
-        std::sort(leaf_ids + nid, leaf_ids + nid + nd.size);
-      }
-      nid += nd.size;
-      ++nl;
-    } else {
-      if (dims) dims[nn] = dm;
-      if (splits) splits[nn] = nd.split;
-      if (sizes) sizes[nn] = nd.size;
-      stack.push_back(nd.b);
-      stack.push_back(nd.a);
-    }
-    ++nn;
-  }
-  if (leaf_offsets) leaf_offsets[nl] = nid;
-  if (n_nodes) *n_nodes = nn;
-  if (n_leaves) *n_leaves = nl;
-  return PKD_OK;
+  return export_from(h, tc->m.root, tc->m.top, tc->m.size, dims, splits, sizes, n_nodes, leaf_ids, leaf_offsets,
+                     n_leaves);
 }
 
 int pkd_height(const pkd_tree* tc, int* height) {

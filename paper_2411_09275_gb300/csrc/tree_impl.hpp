@@ -31,4 +31,13 @@ struct HostTree {
 };
 int download_tree(const TreeMem& t, HostTree& h, bool with_ids = true);
 
+// Canonical form (see pkd_export) of the tree rooted at node slot `root`
+// holding `size` points of an arena whose positions [0, top) are in use.
+int export_from(const HostTree& h, uint32_t root, uint64_t top, uint64_t size, uint8_t* dims, int32_t* splits,
+                uint64_t* sizes, uint64_t* n_nodes, uint32_t* leaf_ids, uint64_t* leaf_offsets, uint64_t* n_leaves);
+
+// k-NN (see pkd_knn) on the tree rooted at node slot `root`.
+int knn_on(TreeMem& t, uint32_t root, const int32_t* queries, uint64_t q, int k, uint32_t* out_ids,
+           int64_t* out_d2, cudaStream_t s);
+
 }  // namespace pkd

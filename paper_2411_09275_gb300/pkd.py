@@ -70,6 +70,15 @@ def lib():
         L.pkd_knn.argtypes = [vp, vp, u64, i32, vp, vp, vp]
         L.pkd_range_count.argtypes = [vp, vp, vp, u64, vp, vp]
         L.pkd_knn_ids_noalloc.argtypes = [vp, vp, u64, i32, vp, vp]
+        L.pkd_build_forest.argtypes = [vp, vp, P(u64), C.c_uint32, P(pkd_params), vp, P(vp)]
+        L.pkd_forest_trees.restype = C.c_uint32
+        L.pkd_forest_trees.argtypes = [vp]
+        L.pkd_forest_size.restype = u64
+        L.pkd_forest_size.argtypes = [vp, C.c_uint32]
+        L.pkd_forest_export.argtypes = [vp, C.c_uint32, vp, vp, vp, P(u64), vp, vp, P(u64)]
+        L.pkd_forest_knn.argtypes = [vp, C.c_uint32, vp, u64, i32, vp, vp, vp]
+        L.pkd_forest_free.argtypes = [vp]
+        L.pkd_forest_free.restype = None
         L.pkd_export.argtypes = [vp, vp, vp, vp, P(u64), vp, vp, P(u64)]
         L.pkd_size.restype = u64
         L.pkd_size.argtypes = [vp]
@@ -82,7 +91,7 @@ def lib():
         L.pkd_kernel_timing.argtypes = [i32]
         L.pkd_kernel_stats.argtypes = [C.c_char_p, P(u64), P(C.c_double), P(u64)]
         for f in ("pkd_build", "pkd_batch_insert", "pkd_batch_delete", "pkd_knn", "pkd_range_count",
-                  "pkd_knn_ids_noalloc", "pkd_export", "pkd_height", "pkd_set_option", "pkd_kernel_timing",
+                  "pkd_knn_ids_noalloc", "pkd_build_forest", "pkd_forest_export", "pkd_forest_knn", "pkd_export", "pkd_height", "pkd_set_option", "pkd_kernel_timing",
                   "pkd_kernel_stats"):
             getattr(L, f).restype = i32
         _lib = L
@@ -167,6 +176,47 @@ def pkd_export(tree) -> dict:
     _check(lib().pkd_export(tree, p(dims), p(splits), p(sizes), C.byref(nn), p(lids), p(offs),
                             C.byref(nl)), "pkd_export")
     return dict(dims=dims, splits=splits, sizes=sizes, leaf_ids=lids[:n], leaf_offsets=offs)
+
+
+def pkd_build_forest(coords: torch.Tensor, ids: torch.Tensor | None, offsets, params: Params, stream=None):
+    """Build len(offsets) - 1 independent trees over coords [n, d] in one pass;
+    offsets is a host sequence of n_trees + 1 point offsets."""
+    assert coords.dtype == torch.int32 and coords.dim() == 2 and coords.shape[1] == params.d
+    if ids is not None:
+        assert ids.dtype in (torch.int32, torch.uint32) and ids.numel() == coords.shape[0]
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
+    assert off.ndim == 1 and off.size >= 2 and int(off[-1]) == coords.shape[0]
+    h = C.c_void_p()
+    pc = params.c()
+    _check(lib().pkd_build_forest(_dptr(coords), _dptr(ids), off.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                  off.size - 1, C.byref(pc), _stream(stream), C.byref(h)), "pkd_build_forest")
+    return h
+
+
+def pkd_forest_export(forest, tree: int) -> dict:
+    nn, nl = C.c_uint64(0), C.c_uint64(0)
+    _check(lib().pkd_forest_export(forest, tree, None, None, None, C.byref(nn), None, None, C.byref(nl)),
+           "pkd_forest_export")
+    n = int(lib().pkd_forest_size(forest, tree))
+    dims = np.empty(nn.value, np.uint8)
+    splits = np.empty(nn.value, np.int32)
+    sizes = np.empty(nn.value, np.uint64)
+    lids = np.empty(max(n, 1), np.uint32)
+    offs = np.empty(nl.value + 1, np.uint64)
+    p = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    _check(lib().pkd_forest_export(forest, tree, p(dims), p(splits), p(sizes), C.byref(nn), p(lids), p(offs),
+                                   C.byref(nl)), "pkd_forest_export")
+    return dict(dims=dims, splits=splits, sizes=sizes, leaf_ids=lids[:n], leaf_offsets=offs)
+
+
+def pkd_forest_knn(forest, tree: int, queries: torch.Tensor, k: int, out_ids: torch.Tensor,
+                   out_d2: torch.Tensor, stream=None):
+    _check(lib().pkd_forest_knn(forest, tree, _dptr(queries), queries.shape[0], k, _dptr(out_ids),
+                                _dptr(out_d2), _stream(stream)), "pkd_forest_knn")
+
+
+def pkd_forest_free(forest):
+    lib().pkd_forest_free(forest)
 
 
 def pkd_size(tree) -> int:

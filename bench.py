@@ -47,6 +47,11 @@ WORKLOADS = {
     "forest4096_d3": dict(forest=True, trees=4096, lo=1e3, hi=1e6, d=3, kind="uniform", n=0, m=0),
     # the same with 256 trees, for quick checks
     "forest256_d3": dict(forest=True, trees=256, lo=1e3, hi=1e6, d=3, kind="uniform", n=0, m=0),
+    # serving: resident 1e8 3-D varden-like tree, Poisson stream of 40% inserts
+    # (1e3..1e6 points), 20% deletes (1e3..1e6 live ids), 40% 10-NN batches
+    # (1e3..1e5 queries), sizes log-uniform, seed 31
+    "serve1e8_d3": dict(serve=True, n=100_000_000, d=3, kind="varden", requests=300, load=0.7, m=0),
+    "serve1e6_d3": dict(serve=True, n=1_000_000, d=3, kind="varden", requests=100, load=0.7, m=0),
 }
 DEFAULT_WORKLOAD = "build1e8_d3_ins1e7_del1e7"
 
@@ -365,6 +370,124 @@ def run_forest(args, wl):
     return 0
 
 
+def serve_requests(wl: dict, X: np.ndarray, dev):
+    """The request stream (arrival offsets in units of the mean gap, to be
+    scaled to a rate) and its device tensors."""
+    import torch
+
+    from paper_2411_09275_gb300 import inputs as I
+    from paper_2411_09275_gb300 import serve
+
+    n, d, R = wl["n"], wl["d"], wl["requests"]
+    rng = np.random.default_rng(31)
+    scale = max(1, 100_000_000 // n)  # smaller trees take proportionally smaller batches
+
+    def logu(lo, hi):
+        return int(np.exp(rng.uniform(np.log(lo), np.log(hi)))) // scale + 1
+
+    alive = np.ones(n, bool)
+    chunks, starts = [], []  # inserted batches and their first ids
+    nxt = n
+    reqs = []
+    t = 0.0
+    for q in range(R):
+        t += rng.exponential(1.0)
+        u = rng.uniform()
+        if u < 0.4:
+            m = logu(1e3, 1e6)
+            Y = I.points(wl["kind"], m, d, 3100 + q)
+            ids = np.arange(nxt, nxt + m, dtype=np.uint32)
+            chunks.append(Y)
+            starts.append(nxt)
+            alive = np.concatenate([alive, np.ones(m, bool)])
+            nxt += m
+            reqs.append(("insert", t, Y, ids))
+        elif u < 0.6:
+            m = logu(1e3, 1e6)
+            got = np.empty(0, np.int64)
+            while got.size < m:
+                cand = rng.integers(0, nxt, size=2 * (m - got.size) + 16)
+                got = np.unique(np.concatenate([got, cand[alive[cand]]]))
+            got = rng.permutation(got)[:m]
+            alive[got] = False
+            Z = np.empty((m, d), np.int32)
+            old = got < n
+            Z[old] = X[got[old]]
+            if (~old).any():
+                gi = got[~old]
+                ci = np.searchsorted(np.asarray(starts), gi, side="right") - 1
+                for c in np.unique(ci):
+                    sel = ci == c
+                    Z[np.flatnonzero(~old)[sel]] = chunks[c][gi[sel] - starts[c]]
+            reqs.append(("delete", t, Z, got.astype(np.uint32)))
+        else:
+            m = logu(1e3, 1e5)
+            pick = rng.integers(0, n, size=m)
+            reqs.append(("knn", t, X[pick], None))
+    out = []
+    for kind, t, C, ids in reqs:
+        tc = torch.from_numpy(np.ascontiguousarray(C)).to(dev)
+        ti = torch.from_numpy(ids.view(np.int32)).to(dev) if ids is not None else None
+        out.append(serve.Request(kind, t, tc, ti, 10))
+    return out
+
+
+def run_serve(args, wl):
+    """Serving loop on one resident tree: p50 / p99 latency and Mpts/s at a
+    request rate that loads the device to about wl['load'] of its capacity."""
+    import torch
+
+    from paper_2411_09275_gb300 import inputs as I
+    from paper_2411_09275_gb300 import pkd, serve
+
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkd.lib()
+    n, d = wl["n"], wl["d"]
+    X = I.points(wl["kind"], n, d, I.SEED_VARDEN + 1000 * rank)
+    gX = torch.from_numpy(X).to(dev)
+    params = pkd.Params(d=d)
+    reqs = serve_requests(wl, X, dev)
+
+    def fresh_tree():
+        t = pkd.Tree(gX, None, params)
+        torch.cuda.synchronize(dev)
+        return t
+
+    # service capacity: the whole stream back to back
+    tree = fresh_tree()
+    s0 = time.perf_counter()
+    serve.Server(tree, realtime=False).run(reqs)
+    torch.cuda.synchronize(dev)
+    busy = time.perf_counter() - s0
+    tree.close()
+    gap = busy / len(reqs) / wl["load"]  # mean inter-arrival time
+    timed = [serve.Request(r.kind, r.arrival * gap, r.coords, r.ids, r.k) for r in reqs]
+    tree = fresh_tree()
+    with Clocks(local) as clk:
+        s0 = time.perf_counter()
+        res = serve.Server(tree).run(timed)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - s0
+    tree.close()
+    summ = serve.summarize(res, wall)
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": ws * summ["mpts_per_s"], "unit": "Mpts/s", "n_gpus": ws,
+            "steps": 1, "warmup": 1, "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "d": d, "distribution": wl["kind"],
+                       "requests": len(reqs), "mix": "40% insert, 20% delete, 40% 10-NN",
+                       "sizes": "log-uniform: updates 1e3..1e6, queries 1e3..1e5 (scaled by 1e8/n)",
+                       "arrivals": f"Poisson, mean gap {1e3 * gap:.3f} ms ({wl['load']:.0%} of measured capacity)",
+                       "parallelism": f"independent server per GPU x{ws}"},
+            "latency": summ, "clocks": clk.summary(),
+            "p99_ms": summ["all"]["p99_ms"], "p50_ms": summ["all"]["p50_ms"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def config_of(args, wl):
     return {"workload": args.workload, "n": wl["n"], "d": wl["d"], "m_insert": wl["m"],
             "m_delete": wl["m"], "distribution": wl["kind"], "phi": 32, "lambda": 6,
@@ -386,6 +509,11 @@ def main():
     ap.add_argument("--varden", action="store_true", help="also time the varden-like variant")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
+    if wl.get("serve"):
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the serving workload has no reference arm"}))
+            return 0
+        return run_serve(args, wl)
     if wl.get("forest"):
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the forest workload has no reference arm; "

@@ -52,6 +52,11 @@ WORKLOADS = {
     # (1e3..1e5 queries), sizes log-uniform, seed 31
     "serve1e8_d3": dict(serve=True, n=100_000_000, d=3, kind="varden", requests=300, load=0.7, m=0),
     "serve1e6_d3": dict(serve=True, n=1_000_000, d=3, kind="varden", requests=100, load=0.7, m=0),
+    # full scale: 1e9 2-D varden-like points, lambda and the sample rate from
+    # the autotuner (timed on every 100th point), 10-NN for the first 1e7
+    # input points as queries
+    "build1e9_d2_varden": dict(full=True, n=1_000_000_000, d=2, kind="varden", q=10_000_000, k=10, m=0),
+    "build1e8_d2_varden": dict(full=True, n=100_000_000, d=2, kind="varden", q=1_000_000, k=10, m=0),
 }
 DEFAULT_WORKLOAD = "build1e8_d3_ins1e7_del1e7"
 
@@ -488,6 +493,121 @@ def run_serve(args, wl):
     return 0
 
 
+def run_full(args, wl):
+    """Autotuned build of a large tree plus a k-NN batch; one JSON line."""
+    import torch
+
+    from paper_2411_09275_gb300 import autotune as A
+    from paper_2411_09275_gb300 import inputs as I
+    from paper_2411_09275_gb300 import pkd
+
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkd.lib()
+    n, d, q, k = wl["n"], wl["d"], wl["q"], wl["k"]
+    X = I.points(wl["kind"], n, d, I.SEED_VARDEN + 1000 * rank)
+    hX = torch.from_numpy(X).pin_memory()
+    gX = hX.to(dev)
+    stream = torch.cuda.current_stream(dev)
+    sample = gX[::100].contiguous()
+    tuned = A.tune(sample, A.grid((5, 6, 7, 8), (5, 6, 7, 8), (2048, 4096)), reps=2)
+    best = A.Candidate(**tuned["best"])
+    params = best.params(d)
+    pkd.pkd_set_option("tile", best.tile)
+    Q = gX[:q].contiguous()
+    oi = torch.empty((q, k), dtype=torch.int32, device=dev)
+    od = torch.empty((q, k), dtype=torch.int64, device=dev)
+
+    def build_once():
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        t = pkd.pkd_build(gX, None, params, stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return t, a.elapsed_time(b)
+
+    for _ in range(max(args.warmup, 3)):
+        t, _ = build_once()
+        pkd.pkd_free(t)
+    pkd.pkd_kernel_timing(True)
+    with Clocks(local) as clk:
+        ms = []
+        for _ in range(args.steps):
+            t, m_ = build_once()
+            ms.append(m_)
+            if len(ms) < args.steps:
+                pkd.pkd_free(t)
+        launches = pkd.pkd_kernel_stats("launches")[0]
+        kst = {kk: pkd.pkd_kernel_stats(kk) for kk in TIMED_KERNELS}
+        # k-NN on the last tree built
+        pkd.pkd_knn(t, Q, k, oi, od, stream)
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pkd.pkd_knn(t, Q, k, oi, od, stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        knn_ms = a.elapsed_time(b)
+    pkd.pkd_kernel_timing(False)
+    height = pkd.pkd_height(t)
+    pkd.pkd_free(t)
+    pkd.pkd_set_option("tile", 2048)
+    t_build = barrier_max(sum(ms) / len(ms), ws, dev)
+
+    # end to end: points from pinned host memory, build, one k-NN batch
+    def e2e_once():
+        g = hX.to(dev, non_blocking=True)
+        tt = pkd.pkd_build(g, None, params, stream)
+        pkd.pkd_knn(tt, g[:q], k, oi, od, stream)
+        oi[0, 0].item()
+        pkd.pkd_free(tt)
+
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    e2e_once()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    t_e2e = barrier_max(a.elapsed_time(b), ws, dev)
+    if rank != 0:
+        return 0
+    peak, peak_src = measured_peaks()
+    kernels = {}
+    for name, (cnt, kms, items) in kst.items():
+        bb = algo_bytes(name, d)
+        if cnt == 0 or kms <= 0:
+            continue
+        gbs = (bb * items / (kms / 1e3) / 1e9) if (bb and items) else None
+        kernels[name] = {"launches": cnt, "ms_per_step": kms / args.steps, "items_per_launch": items / cnt,
+                         "algo_bytes_per_item": bb, "achieved_gbs": gbs}
+    dom = max(kernels, key=lambda kk: kernels[kk]["ms_per_step"]) if kernels else None
+    roof = None
+    if dom:
+        kd = kernels[dom]
+        roof = {"bound": "hbm", "kernel": dom, "achieved": kd["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                "frac": (kd["achieved_gbs"] / peak) if kd["achieved_gbs"] else None, "traffic": None,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
+    line = {"metric": METRIC, "value": ws * n / (t_build / 1e3) / 1e6, "unit": "Mpts/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_build, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "d": d, "distribution": wl["kind"],
+                       "phi": 32, "lambda": best.lam, "sample_rate": f"1/{1 << best.sigma_log2}",
+                       "sigma_os": 32, "tile": best.tile, "queries": q, "k": k,
+                       "l2": "inputs larger than L2 (no flush needed)",
+                       "parallelism": f"independent tree per GPU x{ws}"},
+            "autotune": tuned, "knn": {"ms": knn_ms, "queries_per_s": q / (knn_ms / 1e3)},
+            "tree_height": height, "roofline": roof, "cpu_baseline": None,
+            "e2e": {"value": ws * (n + q) / (t_e2e / 1e3) / 1e6, "unit": "Mpts/s",
+                    "h2d_bytes_per_step": int(hX.numel() * 4), "d2h_bytes_per_step": 4,
+                    "note": "build + one 10-NN batch, points from pinned host memory"},
+            "gpu_launches": launches // max(args.steps, 1), "clocks": clk.summary(), "kernels": kernels}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def config_of(args, wl):
     return {"workload": args.workload, "n": wl["n"], "d": wl["d"], "m_insert": wl["m"],
             "m_delete": wl["m"], "distribution": wl["kind"], "phi": 32, "lambda": 6,
@@ -509,6 +629,11 @@ def main():
     ap.add_argument("--varden", action="store_true", help="also time the varden-like variant")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
+    if wl.get("full"):
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the full-scale workload has no reference arm"}))
+            return 0
+        return run_full(args, wl)
     if wl.get("serve"):
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the serving workload has no reference arm"}))

@@ -144,6 +144,20 @@ int pkd_knn_ids_noalloc(const pkd_tree* tree, const int32_t* queries, uint64_t q
 int pkd_range_count(const pkd_tree* tree, const int32_t* lo, const int32_t* hi, uint64_t q,
                     uint64_t* out_counts, void* stream);
 
+/* Range report (Sec. 5, the reporting form of the range query): the ids of
+ * the stored points inside each closed box lo[i][j] <= x_j <= hi[i][j].
+ *   lo, hi    device, [q][d] int32
+ *   offsets   device, [q + 1] uint64: box i's ids are
+ *             ids[offsets[i] .. offsets[i+1]) (depth-first leaf order)
+ *   ids       device, [ids_cap] uint32
+ *   total     host: the number of ids (offsets[q])
+ * The call counts, scans and synchronises `stream` once; when *total
+ * exceeds ids_cap it returns PKD_EINVAL with offsets and *total filled and
+ * no ids written (call again with a large enough buffer).  The ids are
+ * valid once `stream` has been synchronised. */
+int pkd_range_report(const pkd_tree* tree, const int32_t* lo, const int32_t* hi, uint64_t q, uint64_t* offsets,
+                     uint32_t* ids, uint64_t ids_cap, uint64_t* total, void* stream);
+
 /* Canonical form of the tree into HOST buffers (for parity checks and
  * checkpoints): nodes in pre-order, interior nodes as (dim, split, size),
  * leaves as (0xFF, 0, point count); leaves in in-order with their ids sorted

@@ -211,6 +211,24 @@ class OracleTree:
         f(self._h, _ptr(lo), _ptr(hi), lo.shape[0], _ptr(out))
         return out
 
+    def range_report(self, lo, hi) -> list:
+        """Range report (Sec. 5, reporting form of the range query) by its
+        definition: for each closed box, the sorted ids of the stored points
+        with lo <= x <= hi in every dimension."""
+        ids, X = self.points()
+        return range_report(X, ids, lo, hi)
+
+
+def range_report(points, ids, lo, hi) -> list:
+    """Sorted ids of the points inside each closed box (brute force)."""
+    P = np.asarray(points).reshape(len(ids), -1)
+    i = np.asarray(ids, dtype=np.uint32)
+    out = []
+    for a, b in zip(np.asarray(lo), np.asarray(hi)):
+        inside = np.all((P >= a) & (P <= b), axis=1)
+        out.append(np.sort(i[inside]))
+    return out
+
 
 def mix64(z: int) -> int:
     return int(lib().orc_mix64(z))

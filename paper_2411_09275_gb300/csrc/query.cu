@@ -195,6 +195,165 @@ __global__ void __launch_bounds__(QTHREADS) k_range_count(QueryArgs a) {
   a.out_cnt[qi] = cnt;
 }
 
+// Range report: the same depth-first search as the range count; a subtree
+// whose subspace lies inside the box is walked to its leaves without
+// coordinate tests (its points need not be contiguous in the arena after
+// updates).  Query qi writes its ids from out_ids[offsets[qi]].
+template <int D>
+__global__ void __launch_bounds__(QTHREADS) k_range_report(QueryArgs a, const uint64_t* offsets, uint32_t* out_ids) {
+  const uint64_t qi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (qi >= a.nq) return;
+  int32_t lo[D], hi[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    lo[j] = a.q[qi * D + j];
+    hi[j] = a.hi[qi * D + j];
+  }
+  uint32_t sv[QSTACK];
+  Box<D> sb[QSTACK];
+  uint8_t sin[QSTACK];  // 1: the subspace lies inside the box
+  sv[0] = a.root;
+  sin[0] = 0;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    sb[0].lo[j] = 0;
+    sb[0].hi[j] = PKD_COORD_LIMIT - 1;
+  }
+  int sp = 1;
+  uint64_t pos = offsets[qi];
+  const uint64_t end = offsets[qi + 1];
+  while (sp > 0) {
+    --sp;
+    const uint32_t v = sv[sp];
+    bool inside = sin[sp] != 0;
+    const Box<D> b = sb[sp];
+    if (!inside) {
+      bool disjoint = false;
+      inside = true;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        disjoint |= (b.hi[j] < lo[j]) | (b.lo[j] > hi[j]) | (b.hi[j] < b.lo[j]);
+        inside &= (b.lo[j] >= lo[j]) & (b.hi[j] <= hi[j]);
+      }
+      if (disjoint) continue;
+    }
+    const Node nd = a.nodes[v];
+    const uint8_t dm = a.ndim[v];
+    if (dm == PKD_LEAF) {
+      for (uint32_t i = 0; i < nd.size; ++i) {
+        const uint64_t g = (uint64_t)nd.a + i;
+        bool in = true;
+        if (!inside) {
+#pragma unroll
+          for (int j = 0; j < D; ++j) {
+            const int32_t x = a.A.c[(uint64_t)j * a.A.stride + g];
+            in &= (x >= lo[j]) & (x <= hi[j]);
+          }
+        }
+        if (in) {
+          if (pos >= end) {  // more points than counted: the tree changed
+            set_error(a.st, DERR_STATE, 902);
+            return;
+          }
+          out_ids[pos++] = a.A.id[g];
+        }
+      }
+      continue;
+    }
+    if (sp + 2 > QSTACK) {
+      set_error(a.st, DERR_STACK, 903);
+      return;
+    }
+    const int j = dm;
+    Box<D> L = b, R = b;
+    L.hi[j] = min(L.hi[j], nd.split - 1);
+    R.lo[j] = max(R.lo[j], nd.split);
+    sv[sp] = nd.b;
+    sb[sp] = R;
+    sin[sp] = inside;
+    ++sp;
+    sv[sp] = nd.a;
+    sb[sp] = L;
+    sin[sp] = inside;
+    ++sp;
+  }
+}
+
+// Exclusive scan of q 64-bit counts into offsets[0..q] (offsets[q] = total):
+// per-block sums, one block over the sums, then the blocks again.
+constexpr int SCAN64_THREADS = 256, SCAN64_PER = 8, SCAN64_TILE = SCAN64_THREADS * SCAN64_PER;
+
+__device__ __forceinline__ uint64_t block_scan64(uint64_t v, uint64_t* sh, uint64_t* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint64_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) sh[w] = inc;
+  __syncthreads();
+  uint64_t before = 0, tot = 0;
+  for (int k = 0; k < SCAN64_THREADS / 32; ++k) {
+    if (k < w) before += sh[k];
+    tot += sh[k];
+  }
+  __syncthreads();
+  *total = tot;
+  return before + inc - v;
+}
+
+__global__ void k_scan64_reduce(const uint64_t* in, uint64_t n, uint64_t* partial) {
+  __shared__ uint64_t sh[SCAN64_THREADS / 32];
+  const uint64_t base = (uint64_t)blockIdx.x * SCAN64_TILE + (uint64_t)threadIdx.x * SCAN64_PER;
+  uint64_t s = 0;
+  for (int k = 0; k < SCAN64_PER; ++k)
+    if (base + k < n) s += in[base + k];
+  uint64_t tot;
+  block_scan64(s, sh, &tot);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void k_scan64_partials(uint64_t* partial, uint64_t nb) {
+  __shared__ uint64_t sh[SCAN64_THREADS / 32];
+  uint64_t carry = 0;
+  for (uint64_t b0 = 0; b0 < nb; b0 += SCAN64_THREADS) {
+    const uint64_t i = b0 + threadIdx.x;
+    const uint64_t v = i < nb ? partial[i] : 0;
+    uint64_t tot;
+    const uint64_t ex = block_scan64(v, sh, &tot);
+    if (i < nb) partial[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) partial[nb] = carry;
+}
+
+__global__ void k_scan64_apply(const uint64_t* in, uint64_t n, const uint64_t* partial, uint64_t* out) {
+  __shared__ uint64_t sh[SCAN64_THREADS / 32];
+  const uint64_t base = (uint64_t)blockIdx.x * SCAN64_TILE + (uint64_t)threadIdx.x * SCAN64_PER;
+  uint64_t v[SCAN64_PER], s = 0;
+  for (int k = 0; k < SCAN64_PER; ++k) {
+    v[k] = base + k < n ? in[base + k] : 0;
+    s += v[k];
+  }
+  uint64_t tot;
+  uint64_t run = partial[blockIdx.x] + block_scan64(s, sh, &tot);
+  for (int k = 0; k < SCAN64_PER; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = partial[gridDim.x];
+}
+
+template <int D>
+static void launch_report(const QueryArgs& a, const uint64_t* offsets, uint32_t* ids, cudaStream_t s) {
+  const unsigned g = (unsigned)((a.nq + QTHREADS - 1) / QTHREADS);
+  KTimer kt;
+  ktimer_begin(kt, "range_report", a.nq, s);
+  PKD_LAUNCH(k_range_report<D><<<g, QTHREADS, 0, s>>>(a, offsets, ids));
+  ktimer_end(kt);
+}
+
 template <int D>
 static void launch_knn(const QueryArgs& a, cudaStream_t s) {
   const unsigned g = (unsigned)((a.nq + QTHREADS - 1) / QTHREADS);
@@ -298,6 +457,57 @@ int pkd_range_count(const pkd_tree* tc, const int32_t* lo, const int32_t* hi, ui
   a.out_cnt = out_counts;
   a.st = t.st;
   PKD_QDISPATCH(t.p.d, launch_rc, a, s);
+  PKD_CUDA(cudaGetLastError());
+  return PKD_OK;
+}
+
+int pkd_range_report(const pkd_tree* tc, const int32_t* lo, const int32_t* hi, uint64_t q, uint64_t* offsets,
+                     uint32_t* ids, uint64_t ids_cap, uint64_t* total, void* stream) {
+  if (!tc || !total) return PKD_EINVAL;
+  *total = 0;
+  if (q == 0) return PKD_OK;
+  if (!lo || !hi || !offsets) return PKD_EINVAL;
+  TreeMem& t = const_cast<TreeMem&>(tc->m);
+  cudaStream_t s = (cudaStream_t)stream;
+  bool ok1, ok2;
+  PKD_TRY_(validate_coords(lo, q * (uint64_t)t.p.d, s, &ok1));
+  PKD_TRY_(validate_coords(hi, q * (uint64_t)t.p.d, s, &ok2));
+  if (!ok1 || !ok2) return PKD_EINVAL;
+  PKD_TRY_(check_status(t, s));
+  if (!query_height_ok(t)) return PKD_EINTERNAL;
+  // pass 1: counts (into offsets[0..q)), scanned in place into offsets[0..q]
+  uint64_t* counts = nullptr;
+  uint64_t* partial = nullptr;
+  const uint64_t nb = (q + SCAN64_TILE - 1) / SCAN64_TILE;
+  PKD_TRY_(dalloc(&counts, q, s));
+  int e = dalloc(&partial, nb + 1, s);
+  if (e) {
+    dfree(counts, s);
+    return e;
+  }
+  QueryArgs a{};
+  a.nodes = t.nodes;
+  a.ndim = t.ndim;
+  a.A = t.A;
+  a.root = t.root;
+  a.q = lo;
+  a.hi = hi;
+  a.nq = q;
+  a.out_cnt = counts;
+  a.st = t.st;
+  PKD_QDISPATCH(t.p.d, launch_rc, a, s);
+  PKD_LAUNCH(k_scan64_reduce<<<(unsigned)nb, SCAN64_THREADS, 0, s>>>(counts, q, partial));
+  PKD_LAUNCH(k_scan64_partials<<<1, SCAN64_THREADS, 0, s>>>(partial, nb));
+  PKD_LAUNCH(k_scan64_apply<<<(unsigned)nb, SCAN64_THREADS, 0, s>>>(counts, q, partial, offsets));
+  dfree(counts, s);
+  dfree(partial, s);
+  uint64_t tot = 0;
+  PKD_CUDA(cudaMemcpyAsync(&tot, offsets + q, 8, cudaMemcpyDeviceToHost, s));
+  PKD_CUDA(cudaStreamSynchronize(s));
+  *total = tot;
+  if (tot > ids_cap || (tot > 0 && !ids)) return PKD_EINVAL;
+  // pass 2: the ids
+  PKD_QDISPATCH(t.p.d, launch_report, a, offsets, ids, s);
   PKD_CUDA(cudaGetLastError());
   return PKD_OK;
 }

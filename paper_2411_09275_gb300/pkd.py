@@ -70,6 +70,7 @@ def lib():
         L.pkd_knn.argtypes = [vp, vp, u64, i32, vp, vp, vp]
         L.pkd_range_count.argtypes = [vp, vp, vp, u64, vp, vp]
         L.pkd_knn_ids_noalloc.argtypes = [vp, vp, u64, i32, vp, vp]
+        L.pkd_range_report.argtypes = [vp, vp, vp, u64, vp, vp, u64, P(u64), vp]
         L.pkd_build_forest.argtypes = [vp, vp, P(u64), C.c_uint32, P(pkd_params), vp, P(vp)]
         L.pkd_forest_trees.restype = C.c_uint32
         L.pkd_forest_trees.argtypes = [vp]
@@ -91,7 +92,7 @@ def lib():
         L.pkd_kernel_timing.argtypes = [i32]
         L.pkd_kernel_stats.argtypes = [C.c_char_p, P(u64), P(C.c_double), P(u64)]
         for f in ("pkd_build", "pkd_batch_insert", "pkd_batch_delete", "pkd_knn", "pkd_range_count",
-                  "pkd_knn_ids_noalloc", "pkd_build_forest", "pkd_forest_export", "pkd_forest_knn", "pkd_export", "pkd_height", "pkd_set_option", "pkd_kernel_timing",
+                  "pkd_knn_ids_noalloc", "pkd_range_report", "pkd_build_forest", "pkd_forest_export", "pkd_forest_knn", "pkd_export", "pkd_height", "pkd_set_option", "pkd_kernel_timing",
                   "pkd_kernel_stats"):
             getattr(L, f).restype = i32
         _lib = L
@@ -176,6 +177,22 @@ def pkd_export(tree) -> dict:
     _check(lib().pkd_export(tree, p(dims), p(splits), p(sizes), C.byref(nn), p(lids), p(offs),
                             C.byref(nl)), "pkd_export")
     return dict(dims=dims, splits=splits, sizes=sizes, leaf_ids=lids[:n], leaf_offsets=offs)
+
+
+def pkd_range_report(tree, lo: torch.Tensor, hi: torch.Tensor, stream=None):
+    """Ids of the points inside each box: (offsets [q+1] int64, ids) on the
+    device; sizes the id buffer with a first call."""
+    q = lo.shape[0]
+    offsets = torch.empty(q + 1, dtype=torch.int64, device=lo.device)
+    tot = C.c_uint64(0)
+    r = lib().pkd_range_report(tree, _dptr(lo), _dptr(hi), q, _dptr(offsets), None, 0, C.byref(tot),
+                               _stream(stream))
+    if r != PKD_OK and not (r == PKD_EINVAL and tot.value > 0):
+        _check(r, "pkd_range_report")
+    ids = torch.empty(max(int(tot.value), 1), dtype=torch.int32, device=lo.device)
+    _check(lib().pkd_range_report(tree, _dptr(lo), _dptr(hi), q, _dptr(offsets), _dptr(ids), ids.numel(),
+                                  C.byref(tot), _stream(stream)), "pkd_range_report")
+    return offsets, ids[:int(tot.value)]
 
 
 def pkd_build_forest(coords: torch.Tensor, ids: torch.Tensor | None, offsets, params: Params, stream=None):

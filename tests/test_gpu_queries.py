@@ -85,3 +85,48 @@ def test_queries_after_updates_and_config1_knn():
     lo, hi = I.boxes(2000, 2, 1 << 26, 5)
     got = t.range_count(to_dev(lo), to_dev(hi)).cpu().numpy().astype(np.uint64)
     assert np.array_equal(got, o.range_count(lo, hi))
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 5])
+def test_range_report_matches_brute_force(d):
+    pkd = _pkd()
+    n = 40000
+    X = make_points("varden" if d == 3 else "uniform", n, d, 91)
+    ids = ((np.arange(n, dtype=np.uint64) * 2246822519) % (1 << 32)).astype(np.uint32)
+    p = pkd.Params(d=d, phi=16, lam=4, sigma_log2=3, sigma_os=8)
+    t = pkd.Tree(to_dev(X), ids_dev(ids), p)
+    for side in (1 << 10, 1 << 22, 1 << 30):
+        lo, hi = I.boxes(300, d, side, 92 + side % 89)
+        off, got = pkd.pkd_range_report(t._h, to_dev(lo), to_dev(hi))
+        off = off.cpu().numpy().astype(np.int64)
+        got = got.cpu().numpy().view(np.uint32)
+        cnt = t.range_count(to_dev(lo), to_dev(hi)).cpu().numpy().astype(np.int64)
+        assert np.array_equal(np.diff(off), cnt) and off[0] == 0 and off[-1] == got.size
+        want = O.range_report(X, ids, lo, hi)
+        for i in range(len(lo)):
+            assert np.array_equal(np.sort(got[off[i]:off[i + 1]]), want[i])
+    t.close()
+
+
+def test_range_report_after_updates():
+    pkd = _pkd()
+    d, n = 2, 20000
+    X = make_points("uniform", n, d, 93)
+    t = pkd.Tree(to_dev(X), None, pkd.Params(d=d, phi=8, lam=3, sigma_log2=2, sigma_os=4))
+    Y = I.uniform(5000, d, 94)
+    yid = np.arange(n, n + 5000, dtype=np.uint32)
+    t.insert(to_dev(Y), ids_dev(yid))
+    kill = np.arange(0, n, 3)
+    t.delete(to_dev(X[kill]), ids_dev(kill.astype(np.uint32)))
+    o = O.OracleTree(X, None, O.Params(d=d, phi=8, lam=3, sigma_log2=2, sigma_os=4))
+    o.insert(Y, yid)
+    o.delete(X[kill], kill.astype(np.uint32))
+    lo, hi = I.boxes(200, d, 1 << 27, 95)
+    off, got = pkd.pkd_range_report(t._h, to_dev(lo), to_dev(hi))
+    off = off.cpu().numpy().astype(np.int64)
+    got = got.cpu().numpy().view(np.uint32)
+    want = o.range_report(lo, hi)
+    for i in range(len(lo)):
+        assert np.array_equal(np.sort(got[off[i]:off[i + 1]]), want[i])
+    o.close()
+    t.close()

@@ -457,3 +457,22 @@ def test_knn_equal_distance_tie_across_a_split():
     assert gi[0, 0] == 1 and gd[0, 0] == 25
     gi, gd = t.knn(np.array([[0, 0]], np.int32), 2)
     assert list(gi[0]) == [1, 50] and list(gd[0]) == [25, 25]
+
+
+def test_range_report_hand_example_and_count_consistency():
+    # five 2-D points; closed boxes include their boundary
+    X = np.array([[0, 0], [5, 5], [5, 9], [10, 0], [7, 7]], np.int32)
+    ids = np.array([40, 11, 12, 3, 9], np.uint32)
+    lo = np.array([[0, 0], [5, 5], [8, 8], [0, 0]], np.int32)
+    hi = np.array([[5, 5], [7, 9], [9, 9], [10, 10]], np.int32)
+    got = O.range_report(X, ids, lo, hi)
+    assert [list(g) for g in got] == [[11, 40], [9, 11, 12], [], [3, 9, 11, 12, 40]]
+    # the tree's report agrees with its own count on random boxes
+    rng = np.random.default_rng(3)
+    P = rng.integers(0, 1 << 20, size=(3000, 3)).astype(np.int32)
+    t = O.OracleTree(P, None, O.Params(d=3, phi=8, lam=3, sigma_log2=2, sigma_os=4))
+    lo = rng.integers(0, 1 << 19, size=(50, 3)).astype(np.int32)
+    hi = lo + rng.integers(0, 1 << 19, size=(50, 3)).astype(np.int32)
+    rep = t.range_report(lo, hi)
+    assert [len(r) for r in rep] == list(t.range_count(lo, hi).astype(int))
+    t.close()

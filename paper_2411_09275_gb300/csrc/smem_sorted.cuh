@@ -408,7 +408,7 @@ __device__ int snth_flagged(const Team& tm, const SCtx<D>& cx, const uint16_t* L
     if (lane == 0) tm.red[w * SS_RED] = c;
     if (tm.leader()) tm.red[SS_RED - 1] = -1;
     tm.sync();
-    for (int v = 0; v < w; ++v) before += tm.red[v * SS_RED];
+    before = warp_sum(lane < w ? tm.red[lane * SS_RED] : 0);
     tm.sync();
   }
   int found = -1;
@@ -474,12 +474,11 @@ __device__ bool ssample_split(const Team& tm, const SCtx<D>& cx, const STask& tk
       }
     }
     tm.sync();
+    const int ln = lane_id();
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      for (int v = 0; v < tm.nwarps(); ++v) {
-        mn[j] = min(mn[j], tm.red[v * SS_RED + j]);
-        mx[j] = max(mx[j], tm.red[v * SS_RED + D + j]);
-      }
+      mn[j] = warp_min(ln < tm.nwarps() ? tm.red[ln * SS_RED + j] : INT32_MAX);
+      mx[j] = warp_max(ln < tm.nwarps() ? tm.red[ln * SS_RED + D + j] : INT32_MIN);
     }
     tm.sync();
   }
@@ -603,8 +602,8 @@ __device__ uint32_t spartition(const Team& tm, const SCtx<D>& cx, uint32_t map, 
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     if (k == dim) continue;
-    int before = 0;
-    for (int v = 0; v < w; ++v) before += tm.red[v * SS_RED + k];
+    // left entries in the chunks of the warps before this one
+    const int before = warp_sum(lane < w ? tm.red[lane * SS_RED + k] : 0);
     int lb = lo + before, rb = lo + L + (wlo - lo - before);
     warp_split_run(Xd, x, cx.list(mget(map, k)), cx.list(spare), wlo, whi, lb, rb);
     // the next list is written where this one was read

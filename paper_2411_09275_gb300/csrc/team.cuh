@@ -99,13 +99,14 @@ struct Team {
     sync();
     return r;
   }
+  // Team-wide sum / minimum: each warp reduces, then every warp reduces the
+  // nw partial values with one load per lane (nw <= 32).
   __device__ int sum(int v) const {
     v = warp_sum(v);
     if (nw == 1) return v;
     if (lane_id() == 0) red[my_warp()] = v;
     sync();
-    int r = 0;
-    for (int i = 0; i < nw; ++i) r += red[i];
+    const int r = warp_sum(lane_id() < nw ? red[lane_id()] : 0);
     sync();
     return r;
   }
@@ -114,8 +115,7 @@ struct Team {
     if (nw == 1) return v;
     if (lane_id() == 0) red[my_warp()] = v;
     sync();
-    int r = INT32_MAX;
-    for (int i = 0; i < nw; ++i) r = min(r, red[i]);
+    const int r = warp_min(lane_id() < nw ? red[lane_id()] : INT32_MAX);
     sync();
     return r;
   }

@@ -753,30 +753,51 @@ def main():
         hZ = torch.from_numpy(Z).pin_memory()
         hzid = torch.from_numpy(zid.view(np.int32)).pin_memory()
         h2d = sum(t.numel() * t.element_size() for t in (hX, hY, hyid, hZ, hzid))
-        dX, dY, dyid, dZ, dzid = (torch.empty_like(t, device=dev) for t in (hX, hY, hyid, hZ, hzid))
+        hs = (hX, hY, hyid, hZ, hzid)
+        # two device sets: step k+1's inputs travel on a copy stream while step
+        # k runs its updates (every byte of every step is still copied inside
+        # the timed region)
+        sets = [tuple(torch.empty_like(t, device=dev) for t in hs) for _ in range(2)]
+        copy_stream = torch.cuda.Stream(dev)
+        ready = [torch.cuda.Event() for _ in range(2)]
 
-        def e2e_step():
-            for dd, hh in ((dX, hX), (dY, hY), (dyid, hyid), (dZ, hZ), (dzid, hzid)):
-                dd.copy_(hh, non_blocking=True)
+        def upload(k):
+            with torch.cuda.stream(copy_stream):
+                for dd, hh in zip(sets[k % 2], hs):
+                    dd.copy_(hh, non_blocking=True)
+                ready[k % 2].record(copy_stream)
+
+        def e2e_step(k, last):
+            dX, dY, dyid, dZ, dzid = sets[k % 2]
+            stream.wait_event(ready[k % 2])
             t = pkd.pkd_build(dX, None, params, stream)
+            if not last:
+                upload(k + 1)
             pkd.pkd_batch_insert(t, dY, dyid, stream)
             nd = pkd.pkd_batch_delete(t, dZ, dzid, stream)  # n_deleted comes back to the host
             pkd.pkd_free(t)
             return nd
 
-        e2e_step()
+        def e2e_run(steps):
+            upload(0)
+            for k in range(steps):
+                e2e_step(k, k == steps - 1)
+
+        e2e_run(2)
         barrier_max(0.0, ws, dev)
         torch.cuda.synchronize(dev)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
+        copy_stream.wait_event(a)
+        e2e_run(args.steps)
         b.record(stream)
         torch.cuda.synchronize(dev)
         e2e_ms = barrier_max(a.elapsed_time(b), ws, dev)
         e2e = {"value": ws * pts_step * args.steps / (e2e_ms / 1e3) / 1e6, "unit": "Mpts/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8,
+               "note": "inputs copied from pinned host memory every step; the next step's copy overlaps "
+                       "this step's updates on a second stream"}
 
     # ---- varden-like variant (same sizes), reported beside the headline ----
     varden = None

@@ -190,6 +190,15 @@ __global__ void __launch_bounds__(SS_THREADS, 1) k_smem_sorted(SmemArgs a) {
   }
   // four points per thread in flight: every load of a batch before its stores
   constexpr int LU = 4;
+  // the segment's arrays, offset once (32-bit indexing below)
+  const bool aos = seg.where == IN_INPUT;
+  const Pts& S = seg.where == IN_A ? a.A : a.B;
+  const int32_t* src_c[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j)
+    src_c[j] = aos ? a.in_coords + seg.start * (uint64_t)D + j : S.c + (uint64_t)j * S.stride + seg.start;
+  const uint32_t* src_id = aos ? (a.in_ids ? a.in_ids + seg.start : nullptr) : S.id + seg.start;
+  const int cstep = aos ? D : 1;
   for (int i0 = tid; i0 < n; i0 += LU * SS_THREADS) {
     int32_t v[LU][D];
     uint32_t id[LU];
@@ -197,17 +206,9 @@ __global__ void __launch_bounds__(SS_THREADS, 1) k_smem_sorted(SmemArgs a) {
     for (int u = 0; u < LU; ++u) {
       const int i = i0 + u * SS_THREADS;
       if (i < n) {
-        const uint64_t g = seg.start + (uint64_t)i;
-        if (seg.where == IN_INPUT) {
 #pragma unroll
-          for (int j = 0; j < D; ++j) v[u][j] = a.in_coords[g * (uint64_t)D + j];
-          id[u] = a.in_ids ? a.in_ids[g] : (uint32_t)g;
-        } else {
-          const Pts& S = seg.where == IN_A ? a.A : a.B;
-#pragma unroll
-          for (int j = 0; j < D; ++j) v[u][j] = S.c[(uint64_t)j * S.stride + g];
-          id[u] = S.id[g];
-        }
+        for (int j = 0; j < D; ++j) v[u][j] = src_c[j][i * cstep];
+        id[u] = src_id ? src_id[i] : (uint32_t)(seg.start + (uint64_t)i);
       }
     }
 #pragma unroll
@@ -273,13 +274,15 @@ __global__ void __launch_bounds__(SS_THREADS, 1) k_smem_sorted(SmemArgs a) {
   // in leaf order, coalesced
   {
     const uint16_t* P = cx.list(0);
-    int32_t* oc = a.A.c + seg.start;
+    int32_t* oc[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) oc[j] = a.A.c + (uint64_t)j * a.A.stride + seg.start;
     uint32_t* oid = a.A.id + seg.start;
     for (int i = tid; i < n; i += SS_THREADS) {
       const int p = P[i];
       if (p >= n) continue;  // only after a recorded error, when leaves are missing
 #pragma unroll
-      for (int j = 0; j < D; ++j) oc[(uint64_t)j * a.A.stride + i] = X[j * cap + p];
+      for (int j = 0; j < D; ++j) oc[j][i] = X[j * cap + p];
       oid[i] = ID[p];
     }
   }
@@ -525,6 +528,7 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(RoundArgs r) {
   if (first >= seg.len) return;
   const int cnt = (int)min((uint64_t)r.TILE, (uint64_t)seg.len - first);
   const int shift = sample_shift(r.p, seg.len);
+  const uint64_t key = sample_key(r.p.seed, seg.depth);
   const int d = r.p.d;
   uint32_t ids[SAMPLE_PER];
 #pragma unroll
@@ -536,7 +540,7 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(RoundArgs r) {
 #pragma unroll
   for (int k = 0; k < SAMPLE_PER; ++k) {
     const int i = k * SAMPLE_THREADS + threadIdx.x;
-    if (i < cnt && in_sample(r.p.seed, seg.depth, ids[k], shift)) fl |= 1u << k;
+    if (i < cnt && in_sample_k(key, ids[k], shift)) fl |= 1u << k;
   }
   uint32_t total;
   uint32_t off = block_excl_scan<uint32_t>((uint32_t)__popc(fl), sh, &total);

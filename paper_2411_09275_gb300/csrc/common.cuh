@@ -93,6 +93,17 @@ __host__ __device__ __forceinline__ bool in_sample(uint64_t seed, uint32_t t, ui
   return (h >> (64 - s)) == 0;
 }
 
+// The same test with the per-subproblem part of the key precomputed:
+// key = seed ^ t * K_DEPTH (identical results).
+__host__ __device__ __forceinline__ uint64_t sample_key(uint64_t seed, uint32_t t) {
+  return seed ^ ((uint64_t)t * K_DEPTH);
+}
+__host__ __device__ __forceinline__ bool in_sample_k(uint64_t key, uint32_t id, int s) {
+  if (s == 0) return true;
+  const uint64_t h = finalize64(key ^ ((uint64_t)id * K_ID));
+  return (h >> (64 - s)) == 0;
+}
+
 // Sample-rate exponent for a subproblem of n points: fixed in rate mode; in
 // count mode the largest s with 2^lambda * sigma_os * 2^s <= n (about
 // 2^lambda * sigma_os samples, Alg. 1).

@@ -478,12 +478,18 @@ __global__ void __launch_bounds__(STM_THREADS) k_scatter_stream(RoundArgs r, uin
     }
     consumers_sync();
     // every bucket's run leaves the tile as one contiguous range
-    for (int pos = tid; pos < st.t.cnt; pos += STM_CONSUMERS) {
-      const int b = sb[pos];
-      const uint64_t g = seg_start + gbase[b] + (uint64_t)(pos - (int)lstart[b]);
+    {
+      int32_t* oc[D];
 #pragma unroll
-      for (int j = 0; j < D; ++j) r.dst.c[(uint64_t)j * r.dst.stride + g] = stx[j * tilecap + pos];
-      r.dst.id[g] = sid[pos];
+      for (int j = 0; j < D; ++j) oc[j] = r.dst.c + (uint64_t)j * r.dst.stride + seg_start;
+      uint32_t* oid = r.dst.id + seg_start;
+      for (int pos = tid; pos < st.t.cnt; pos += STM_CONSUMERS) {
+        const int b = sb[pos];
+        const uint32_t g = gbase[b] + (uint32_t)(pos - (int)lstart[b]);  // within the segment (< 2^31)
+#pragma unroll
+        for (int j = 0; j < D; ++j) oc[j][g] = stx[j * tilecap + pos];
+        oid[g] = sid[pos];
+      }
     }
     for (int b = tid; b < r.NB; b += STM_CONSUMERS) cur[b] = 0;
     consumers_sync();

@@ -346,6 +346,7 @@ template <int D>
 __device__ __forceinline__ int sdraw_sample(const Team& tm, const SCtx<D>& cx, uint32_t map, int lo, int hi,
                                             uint32_t t, int shift) {
   const uint16_t* P = cx.list(mget(map, 0));
+  const uint64_t key = sample_key(cx.p.seed, t);
   int c = 0;
   constexpr int U = 4;
   for (int i0 = lo + tm.rank(); i0 < hi; i0 += U * tm.size()) {
@@ -361,7 +362,7 @@ __device__ __forceinline__ int sdraw_sample(const Team& tm, const SCtx<D>& cx, u
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (pp[u] >= 0) {
-        const bool f = in_sample(cx.p.seed, t, id[u], shift);
+        const bool f = in_sample_k(key, id[u], shift);
         cx.flag[pp[u]] = f;
         c += f;
       }

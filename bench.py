@@ -769,10 +769,10 @@ def main():
 
         def e2e_step(k, last):
             dX, dY, dyid, dZ, dzid = sets[k % 2]
+            if not last:  # the other set is free: step k-1 has finished
+                upload(k + 1)
             stream.wait_event(ready[k % 2])
             t = pkd.pkd_build(dX, None, params, stream)
-            if not last:
-                upload(k + 1)
             pkd.pkd_batch_insert(t, dY, dyid, stream)
             nd = pkd.pkd_batch_delete(t, dZ, dzid, stream)  # n_deleted comes back to the host
             pkd.pkd_free(t)
@@ -797,7 +797,7 @@ def main():
         e2e = {"value": ws * pts_step * args.steps / (e2e_ms / 1e3) / 1e6, "unit": "Mpts/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8,
                "note": "inputs copied from pinned host memory every step; the next step's copy overlaps "
-                       "this step's updates on a second stream"}
+                       "this step on a second stream"}
 
     # ---- varden-like variant (same sizes), reported beside the headline ----
     varden = None

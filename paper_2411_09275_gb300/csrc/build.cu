@@ -147,13 +147,18 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_smem_build(SmemArgs a) {
 
 // The base case on presorted lists (one CTA per segment of at most cap
 // points): load, sort every dimension once, then split by lookups and stable
-// list partitions.
-template <int D>
-__global__ void __launch_bounds__(SS_THREADS, 1) k_smem_sorted(SmemArgs a) {
+// list partitions.  Instantiated for one CTA per SM (the largest capacity)
+// and for two (half the shared memory and at most 64 registers a thread):
+// the two-CTA launch takes every segment it can hold, the other launch the
+// segments longer than that (a.seg_min).
+template <int D, int MINB>
+__global__ void __launch_bounds__(SS_THREADS, MINB) k_smem_sorted(SmemArgs a) {
   if (blockIdx.x >= *a.nsegs) return;
   extern __shared__ __align__(16) uint8_t sm[];
   const Seg seg = a.segs[blockIdx.x];
   const int cap = a.cap, tid = threadIdx.x;
+  if ((int)seg.len <= a.seg_min) return;  // taken by the smaller launch
+  if (seg.len > (uint32_t)cap && seg.len <= (uint32_t)a.cap_next) return;  // left to the larger launch
   const SortedLayout Lo = sorted_layout(cap, D);
   int32_t* X = (int32_t*)(sm + Lo.X);
   uint32_t* ID = (uint32_t*)(sm + Lo.ID);
@@ -424,10 +429,39 @@ template <int D>
 static void launch_smem_sorted(const SmemArgs& a, uint32_t nblocks, size_t smb, cudaStream_t s) {
   static int set = 0;
   if (set < (int)smb) {
-    cudaFuncSetAttribute(k_smem_sorted<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+    cudaFuncSetAttribute(k_smem_sorted<D, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
     set = (int)smb;
   }
-  PKD_LAUNCH(k_smem_sorted<D><<<nblocks, SS_THREADS, smb, s>>>(a));
+  PKD_LAUNCH((k_smem_sorted<D, 1><<<nblocks, SS_THREADS, smb, s>>>(a)));
+}
+template <int D>
+static void launch_smem_sorted2(const SmemArgs& a, uint32_t nblocks, size_t smb, cudaStream_t s) {
+  static int set = 0;
+  if (set < (int)smb) {
+    cudaFuncSetAttribute(k_smem_sorted<D, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+    set = (int)smb;
+  }
+  PKD_LAUNCH((k_smem_sorted<D, 2><<<nblocks, SS_THREADS, smb, s>>>(a)));
+}
+
+// Largest capacity of the presorted base case that lets two CTAs share an
+// SM (each gets half of the SM's shared memory, less the per-CTA reserve).
+static int sorted_cap_two_per_sm(int d) {
+  static int per_sm = -1;
+  if (per_sm < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (per_sm <= 0) per_sm = 96 * 1024;
+  }
+  const size_t budget = (size_t)per_sm / 2 - 2048;
+  int lo = 64, hi = 16384;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (sorted_layout(mid, d).total <= budget) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo & ~63;
 }
 
 template <int D>
@@ -1380,7 +1414,18 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     KTimer kt;
     ktimer_begin(kt, "smem_build", cta_pts, s);
     if (knobs().base_kernel == 0) {
-      PKD_DISPATCH_D(d, launch_smem_sorted, sa, nbase, sorted_layout((int)cap, d).total, s);
+      const int cap2 = std::min<int>((int)cap, sorted_cap_two_per_sm(d));
+      SmemArgs s2 = sa;
+      s2.cap = cap2;
+      s2.seg_min = -1;
+      s2.cap_next = (int)cap;
+      PKD_DISPATCH_D(d, launch_smem_sorted2, s2, nbase, sorted_layout(cap2, d).total, s);
+      if ((int)cap > cap2) {
+        SmemArgs s1 = sa;
+        s1.seg_min = cap2;
+        s1.cap_next = 0;
+        PKD_DISPATCH_D(d, launch_smem_sorted, s1, nbase, sorted_layout((int)cap, d).total, s);
+      }
     } else {
       PKD_DISPATCH_D(d, launch_smem_build, sa, nbase, smem_layout((int)cap, d).total, s);
     }

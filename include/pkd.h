@@ -213,8 +213,10 @@ const char* pkd_strerror(int code);
  *   "tile"       points per tile of the sieve kernels (256..4096, a power of
  *                two; default 2048)
  *   "sieve_kernel" sieve count/scatter: 0 persistent CTAs streaming tiles
- *                through shared memory with bulk copies (default), 1 one
- *                CTA per tile
+ *                through shared memory with bulk copies, the count recording
+ *                every point's bucket for the scatter when there are at most
+ *                256 buckets (default); 2 the same kernels with the scatter
+ *                walking the skeleton again; 1 one CTA per tile
  *   "base_kernel" shared-memory base case: 0 sorts each subproblem once per
  *                dimension and splits by lookups (default), 1 selects every
  *                splitter by a radix select

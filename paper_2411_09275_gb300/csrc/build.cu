@@ -1305,6 +1305,8 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     PKD_TRY(sc.get(&r.exact, nbig));
     PKD_TRY(sc.get(&r.hist, (size_t)tiles * NB));
     PKD_TRY(sc.get(&r.hscan, (size_t)tiles * NB));
+    r.bkt = nullptr;
+    if (record_buckets(NB)) PKD_TRY(sc.get(&r.bkt, (size_t)tiles * TILE));
     PKD_TRY(sc.get(&r.scnt, nbig));
     PKD_TRY(sc.get(&r.children, (size_t)nbig * NB));
     r.samp = S0;

@@ -17,7 +17,8 @@ struct Knobs {
   int skel_cap = 0;   // 0: derived
   int tile = 2048;    // points per tile in the sieve kernels
   int base_kernel = 0;  // base case: 0 presorted lists, 1 radix select per node
-  int sieve_kernel = 0;  // sieve: 0 persistent with bulk copies, 1 one tile per CTA
+  int sieve_kernel = 0;  // sieve: 0 persistent with bulk copies and recorded
+                         // buckets, 2 persistent re-walking, 1 one tile per CTA
 };
 Knobs& knobs();
 

@@ -137,6 +137,9 @@ struct RoundArgs {
   uint8_t* exact;    // [nbig] 1: exact level on the points; 2: already handled
   uint32_t* hist;    // [tiles * NB]
   uint32_t* hscan;
+  uint8_t* bkt;      // optional [tiles][TILE]: every point's bucket, written by
+                     // the streaming count and read by the streaming scatter
+                     // (NB <= 256), which then need not walk the skeleton again
   uint32_t* scnt;    // [nbig] samples
   uint32_t* sizes;   // [nbig][HN] skeleton subtree sizes
   Pts samp;          // sample buffer 0

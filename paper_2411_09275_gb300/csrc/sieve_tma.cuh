@@ -137,9 +137,14 @@ __host__ __device__ inline size_t stm_stage_words(int tile, bool ids) {
 // `full` with the bytes the bulk copies will deliver.
 template <int D>
 __device__ void stm_produce(const RoundArgs& r, uint32_t s, uint32_t tile, bool ids, uint32_t* buf,
-                            StmStage<D>* rec, uint64_t* full) {
+                            StmStage<D>* rec, uint64_t* full, uint32_t* gbs, uint8_t* sbk) {
   const int lane = lane_id();
   const StmTile t = stm_tile(r, s, tile);
+  if (gbs) {
+    const uint64_t hb = (uint64_t)t.t0 * r.NB;
+    const uint32_t g0 = r.hscan[hb];
+    for (int b = lane; b < r.NB; b += 32) gbs[b] = r.hscan[hb + (uint64_t)b * t.nt + t.tl] - g0;
+  }
   const size_t stride = stm_stride(r.TILE);
   StmArr arr[D + 1];
   int implicit = 0;
@@ -170,6 +175,10 @@ __device__ void stm_produce(const RoundArgs& r, uint32_t s, uint32_t tile, bool 
     uint32_t bytes = 0;
 #pragma unroll
     for (int a = 0; a <= D; ++a) bytes += (uint32_t)arr[a].L * 4u;
+    // the tile's bucket bytes (tile-aligned rows of TILE bytes, so the copy
+    // starts 16-byte aligned; it may read past cnt within the row)
+    const uint32_t kb = sbk ? ((uint32_t)t.cnt + 15u) & ~15u : 0u;
+    bytes += kb;
     StmStage<D> st;
     st.t = t;
 #pragma unroll
@@ -181,6 +190,7 @@ __device__ void stm_produce(const RoundArgs& r, uint32_t s, uint32_t tile, bool 
     for (int a = 0; a <= D; ++a)
       if (arr[a].L) bulk_g2s(buf + (size_t)a * stride + arr[a].sh + arr[a].h, arr[a].P + arr[a].h,
                              (uint32_t)arr[a].L * 4u, full);
+    if (kb) bulk_g2s(sbk, r.bkt + (uint64_t)tile * r.TILE, kb, full);
   }
 }
 
@@ -210,7 +220,8 @@ __device__ __forceinline__ uint32_t stm_advance(const RoundArgs& r, uint32_t s, 
 // Producer warp main loop over the CTA's tiles.
 template <int D>
 __device__ void stm_producer(const RoundArgs& r, uint32_t tb, uint32_t te, bool ids, uint32_t* bufs, size_t swords,
-                             StmStage<D>* recs, uint64_t* full, uint64_t* empty) {
+                             StmStage<D>* recs, uint64_t* full, uint64_t* empty, uint32_t* gbs,
+                             uint8_t* sbk) {
   const uint32_t nb = *r.nbig;
   uint32_t s = seg_of_tile(r.tile0, nb, tb);
   for (uint32_t k = 0; tb + k < te; ++k) {
@@ -225,7 +236,8 @@ __device__ void stm_producer(const RoundArgs& r, uint32_t tb, uint32_t te, bool 
       fence_proxy_async_smem();
     }
     s = stm_advance(r, s, nb, tb + k);
-    stm_produce<D>(r, s, tb + k, ids, bufs + stg * swords, &recs[stg], &full[stg]);
+    stm_produce<D>(r, s, tb + k, ids, bufs + stg * swords, &recs[stg], &full[stg], gbs ? gbs + stg * r.NB : nullptr,
+                   sbk ? sbk + (size_t)stg * r.TILE : nullptr);
   }
 }
 
@@ -260,18 +272,28 @@ __device__ __forceinline__ bool stm_tables(const RoundArgs& r, uint32_t s, int2*
   return sk_state(gsk[1].y) == SK_HEAVY;
 }
 
+// The walks of a thread's STM_PER points advance level by level together,
+// so their shared-memory lookups overlap; bk[u] = bucket, or -1 when point u
+// is not in the tile.
 template <int D>
-__device__ __forceinline__ int stm_walk(const int2* wt, const uint16_t* wb, const int32_t* x, int lam) {
-  int h = 1;
-  for (int l = 0; l < lam; ++l) {
-    const int2 e = wt[h];
-    int xs = x[0];
+__device__ __forceinline__ void stm_walk4(const int2* wt, const uint16_t* wb, const int32_t (&x)[STM_PER][D],
+                                          const bool (&in)[STM_PER], int lam, int (&bk)[STM_PER]) {
+  int h[STM_PER];
 #pragma unroll
-    for (int j = 1; j < D; ++j)
-      if (e.y == j) xs = x[j];
-    h = 2 * h + (xs >= e.x);
+  for (int u = 0; u < STM_PER; ++u) h[u] = 1;
+  for (int l = 0; l < lam; ++l) {
+#pragma unroll
+    for (int u = 0; u < STM_PER; ++u) {
+      const int2 e = wt[h[u]];
+      int xs = x[u][0];
+#pragma unroll
+      for (int j = 1; j < D; ++j)
+        if (e.y == j) xs = x[u][j];
+      h[u] = 2 * h[u] + (xs >= e.x);
+    }
   }
-  return wb[h - (1 << lam)];
+#pragma unroll
+  for (int u = 0; u < STM_PER; ++u) bk[u] = in[u] ? (int)wb[h[u] - (1 << lam)] : -1;
 }
 
 // ---------------------------------------------------------------------------
@@ -306,7 +328,7 @@ __global__ void __launch_bounds__(STM_THREADS) k_count_stream(RoundArgs r, uint3
   for (int b = tid; b < r.NB; b += blockDim.x) lh[b] = 0;
   __syncthreads();
   if (tid >= STM_CONSUMERS) {
-    stm_producer<D>(r, tb, te, false, bufs, swords, recs, full, empty);
+    stm_producer<D>(r, tb, te, false, bufs, swords, recs, full, empty, nullptr, nullptr);
     return;
   }
   uint32_t cur_seg = 0xFFFFFFFFu;
@@ -322,27 +344,37 @@ __global__ void __launch_bounds__(STM_THREADS) k_count_stream(RoundArgs r, uint3
       consumers_sync();
     }
     if (!heavy) {
+      int32_t x[STM_PER][D];
+      bool in[STM_PER];
+      int bk[STM_PER];
 #pragma unroll
       for (int u = 0; u < STM_PER; ++u) {
         const int i = u * STM_CONSUMERS + tid;
-        if (i < st.t.cnt) {
-          int32_t x[D];
+        in[u] = i < st.t.cnt;
 #pragma unroll
-          for (int j = 0; j < D; ++j) x[j] = stm_x<D>(st, buf, stride, aos, j, i);
-          atomicAdd(&lh[stm_walk<D>(wt, wb, x, r.lam)], 1u);
-        }
+        for (int j = 0; j < D; ++j) x[u][j] = in[u] ? stm_x<D>(st, buf, stride, aos, j, i) : 0;
+      }
+      stm_walk4<D>(wt, wb, x, in, r.lam, bk);
+#pragma unroll
+      for (int u = 0; u < STM_PER; ++u)
+        if (bk[u] >= 0) atomicAdd(&lh[bk[u]], 1u);
+      if (r.bkt) {
+        uint8_t* row = r.bkt + (uint64_t)(tb + k) * r.TILE;
+#pragma unroll
+        for (int u = 0; u < STM_PER; ++u)
+          if (bk[u] >= 0) row[u * STM_CONSUMERS + tid] = (uint8_t)bk[u];
       }
     }
     consumers_sync();
     // the stage is no longer read: let the producer refill it
     if (tid == 0) mbar_arrive(&empty[stg]);
-    // the tile's counts, bucket-major as the device scan expects
+    // the tile's counts, bucket-major as the device scan expects (the next
+    // tile's counting starts after the barrier of its stage wait)
     const uint64_t hb = (uint64_t)st.t.t0 * r.NB;
     for (int b = tid; b < r.NB; b += STM_CONSUMERS) {
       r.hist[hb + (uint64_t)b * st.t.nt + st.t.tl] = heavy ? 0u : lh[b];
       lh[b] = 0;
     }
-    consumers_sync();
   }
 }
 
@@ -377,6 +409,9 @@ __global__ void __launch_bounds__(STM_THREADS) k_scatter_stream(RoundArgs r, uin
   uint16_t* sb = (uint16_t*)(sid + tilecap);
   uint16_t* wb = sb + tilecap;              // [L]
   int* flag = (int*)(wb + L + 2);
+  uint32_t* gbs = (uint32_t*)(flag + 4);    // [STM_STAGES][NB]
+  uint8_t* sbk = r.bkt ? (uint8_t*)(((uintptr_t)(gbs + STM_STAGES * r.NB) + 15) & ~(uintptr_t)15)
+                       : nullptr;  // [STM_STAGES][TILE], 16-byte aligned for the bulk copies
   const int tid = threadIdx.x;
   const bool aos = r.src.is_aos != 0;
   uint32_t tb, te;
@@ -392,7 +427,7 @@ __global__ void __launch_bounds__(STM_THREADS) k_scatter_stream(RoundArgs r, uin
   for (int b = tid; b < r.NB; b += blockDim.x) cur[b] = 0;
   __syncthreads();
   if (tid >= STM_CONSUMERS) {
-    stm_producer<D>(r, tb, te, true, bufs, swords, recs, full, empty);
+    stm_producer<D>(r, tb, te, true, bufs, swords, recs, full, empty, gbs, sbk);
     return;
   }
   uint32_t cur_seg = 0xFFFFFFFFu;
@@ -414,56 +449,52 @@ __global__ void __launch_bounds__(STM_THREADS) k_scatter_stream(RoundArgs r, uin
     }
     const uint64_t hb = (uint64_t)st.t.t0 * r.NB;
     const uint64_t seg_start = st.t.g0 - (uint64_t)st.t.tl * r.TILE;
+    const int cnt = st.t.cnt;
     // this tile's global bucket bases, up to two per thread (NB <= 1024);
-    // their loads overlap the walks
-    static_assert(2 * STM_CONSUMERS >= 1024, "bucket bases per thread");
-    uint32_t gb[2] = {0u, 0u};
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int b = tid + q * STM_CONSUMERS;
-      if (b < r.NB) gb[q] = r.hscan[hb + (uint64_t)b * st.t.nt + st.t.tl] - r.hscan[hb];
-    }
+    // the loads are issued here and used after the ranking
+    for (int b = tid; b < r.NB; b += STM_CONSUMERS) gbase[b] = gbs[stg * r.NB + b];
     int32_t x[STM_PER][D];
     uint32_t id[STM_PER];
+    bool in[STM_PER];
     int bk[STM_PER], rk[STM_PER];
 #pragma unroll
     for (int u = 0; u < STM_PER; ++u) {
       const int i = u * STM_CONSUMERS + tid;
-      bk[u] = -1;
-      if (i < st.t.cnt) {
+      in[u] = i < cnt;
 #pragma unroll
-        for (int j = 0; j < D; ++j) x[u][j] = stm_x<D>(st, buf, stride, aos, j, i);
-        id[u] = stm_id<D>(st, buf, stride, i);
-        bk[u] = stm_walk<D>(wt, wb, x[u], r.lam);
-      }
+      for (int j = 0; j < D; ++j) x[u][j] = in[u] ? stm_x<D>(st, buf, stride, aos, j, i) : 0;
+      id[u] = in[u] ? stm_id<D>(st, buf, stride, i) : 0u;
+    }
+    if (sbk) {  // buckets recorded by the count
+      const uint8_t* tb8 = sbk + (size_t)stg * r.TILE;
+#pragma unroll
+      for (int u = 0; u < STM_PER; ++u) bk[u] = in[u] ? (int)tb8[u * STM_CONSUMERS + tid] : -1;
+    } else {
+      stm_walk4<D>(wt, wb, x, in, r.lam, bk);
     }
     consumers_sync();
     // the stage is no longer read: let the producer refill it
     if (tid == 0) mbar_arrive(&empty[stg]);
+    // rank within the tile's buckets: one shared atomic per bucket and warp
+    // (the order inside a bucket is immaterial: later steps see only sets)
 #pragma unroll
-    for (int u = 0; u < STM_PER; ++u) {
-      const unsigned m = peer_mask(bk[u], r.lam);
-      const int leader = __ffs(m) - 1;
-      unsigned base = 0;
-      if (bk[u] >= 0 && lane_id() == leader) base = atomicAdd(&cur[bk[u]], (unsigned)__popc(m));
-      base = __shfl_sync(FULL_MASK, base, leader);
-      rk[u] = (int)base + __popc(m & lanemask_lt());
-    }
+    for (int u = 0; u < STM_PER; ++u) rk[u] = bk[u] >= 0 ? (int)atomicAdd(&cur[bk[u]], 1u) : 0;
     consumers_sync();
+    // the tile's bucket starts (one warp; it also clears the counters for
+    // the next tile, whose ranking comes after two more barriers)
     if (tid < 32) {
-      unsigned carry = 0;
-      for (int b0 = 0; b0 < r.NB; b0 += 32) {
-        const int b = b0 + lane_id();
-        const unsigned c = b < r.NB ? cur[b] : 0;
-        const unsigned incl = (unsigned)warp_incl_scan((int)c);
-        if (b < r.NB) lstart[b] = carry + incl - c;
-        carry += __shfl_sync(FULL_MASK, incl, 31);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int b = tid + q * STM_CONSUMERS;
-      if (b < r.NB) gbase[b] = gb[q];
+      const int per = (r.NB + 31) >> 5, b0 = lane_id() * per;
+      unsigned sum = 0;
+      for (int k2 = 0; k2 < per; ++k2)
+        if (b0 + k2 < r.NB) sum += cur[b0 + k2];
+      unsigned run = (unsigned)warp_incl_scan((int)sum) - sum;
+      for (int k2 = 0; k2 < per; ++k2)
+        if (b0 + k2 < r.NB) {
+          const unsigned c = cur[b0 + k2];
+          lstart[b0 + k2] = run;
+          run += c;
+          cur[b0 + k2] = 0;
+        }
     }
     consumers_sync();
 #pragma unroll
@@ -477,22 +508,25 @@ __global__ void __launch_bounds__(STM_THREADS) k_scatter_stream(RoundArgs r, uin
       }
     }
     consumers_sync();
-    // every bucket's run leaves the tile as one contiguous range
+    // every bucket's run leaves the tile as one contiguous range; the next
+    // tile overwrites the staging arrays only after three more barriers
     {
       int32_t* oc[D];
 #pragma unroll
       for (int j = 0; j < D; ++j) oc[j] = r.dst.c + (uint64_t)j * r.dst.stride + seg_start;
       uint32_t* oid = r.dst.id + seg_start;
-      for (int pos = tid; pos < st.t.cnt; pos += STM_CONSUMERS) {
-        const int b = sb[pos];
-        const uint32_t g = gbase[b] + (uint32_t)(pos - (int)lstart[b]);  // within the segment (< 2^31)
 #pragma unroll
-        for (int j = 0; j < D; ++j) oc[j][g] = stx[j * tilecap + pos];
-        oid[g] = sid[pos];
+      for (int u = 0; u < STM_PER; ++u) {
+        const int pos = u * STM_CONSUMERS + tid;
+        if (pos < cnt) {
+          const int b = sb[pos];
+          const uint32_t g = gbase[b] + (uint32_t)(pos - (int)lstart[b]);  // within the segment (< 2^31)
+#pragma unroll
+          for (int j = 0; j < D; ++j) oc[j][g] = stx[j * tilecap + pos];
+          oid[g] = sid[pos];
+        }
       }
     }
-    for (int b = tid; b < r.NB; b += STM_CONSUMERS) cur[b] = 0;
-    consumers_sync();
   }
 }
 
@@ -501,7 +535,7 @@ static size_t scatter_stream_smem(const RoundArgs& r) {
   const int L = 1 << r.lam;
   return STM_STAGES * stm_stage_words<D>(r.TILE, true) * 4 + STM_STAGES * 16 + STM_STAGES * sizeof(StmStage<D>) +
          (size_t)L * 8 + (size_t)r.NB * 12 + (size_t)D * r.TILE * 4 + (size_t)r.TILE * 4 + (size_t)r.TILE * 2 +
-         (size_t)(L + 2) * 2 + 16 + 16;
+         (size_t)(L + 2) * 2 + 16 + 16 + (size_t)STM_STAGES * r.NB * 4 + (r.bkt ? (size_t)STM_STAGES * r.TILE + 16 : 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -531,10 +565,14 @@ static size_t stream_smem_limit() {
   return (size_t)v;
 }
 
+// Whether the count records every point's bucket for the scatter (one byte
+// a point; the streaming kernels only).
+static inline bool record_buckets(int NB) { return NB <= 256 && knobs().sieve_kernel == 0; }
+
 template <int D>
 static void launch_count(const RoundArgs& r, uint32_t tiles, cudaStream_t s) {
   const size_t smb = count_stream_smem<D>(r);
-  if (knobs().sieve_kernel != 0 || smb > stream_smem_limit() || r.TILE > STM_CONSUMERS * STM_PER) {
+  if (knobs().sieve_kernel == 1 || smb > stream_smem_limit() || r.TILE > STM_CONSUMERS * STM_PER) {
     launch_count_tiles<D>(r, tiles, s);
     return;
   }
@@ -553,7 +591,7 @@ static void launch_count(const RoundArgs& r, uint32_t tiles, cudaStream_t s) {
 template <int D>
 static void launch_scatter(const RoundArgs& r, uint32_t tiles, uint64_t pts, cudaStream_t s) {
   const size_t smb = scatter_stream_smem<D>(r);
-  if (knobs().sieve_kernel != 0 || smb > stream_smem_limit() || r.TILE > STM_CONSUMERS * STM_PER) {
+  if (knobs().sieve_kernel == 1 || smb > stream_smem_limit() || r.TILE > STM_CONSUMERS * STM_PER) {
     launch_scatter_tiles<D>(r, tiles, pts, s);
     return;
   }

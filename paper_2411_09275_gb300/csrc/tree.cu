@@ -521,7 +521,7 @@ int pkd_set_option(const char* name, int64_t value) {
     if (value != 0 && (value < 64 || value > 16384)) return PKD_EINVAL;
     knobs().skel_cap = (int)value;
   } else if (n == "sieve_kernel") {
-    if (value != 0 && value != 1) return PKD_EINVAL;
+    if (value < 0 || value > 2) return PKD_EINVAL;
     knobs().sieve_kernel = (int)value;
   } else if (n == "base_kernel") {
     if (value != 0 && value != 1) return PKD_EINVAL;

@@ -1084,6 +1084,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
       ra.excl = excl;
       ra.hist = hist;
       ra.hscan = hscan;
+      if (record_buckets(NB)) PKD_TRY(sc.get(&ra.bkt, (size_t)tiles * TILE));
       PKD_LAUNCH(k_big_prefix<<<1, 1024, 0, s>>>(cur_big, R.d_n + 1, (uint32_t)TILE, tile0, excl));
       PKD_DISPATCH_D(d, launch_count, ra, tiles, s);
       device_excl_scan(hist, hscan, nh, partial, s);

@@ -38,6 +38,8 @@ CASES = [
     ("d8", 20000, 8, "varden", dict(phi=8, lam=3, sigma_log2=2, sigma_os=4), dict(base_cap=512)),
     ("lambda10", 60000, 2, "uniform", dict(phi=4, lam=10, sigma_log2=0, sigma_os=4),
      dict(base_cap=2048, skel_cap=1024)),
+    ("lambda8-256-buckets", 60000, 3, "varden", dict(phi=4, lam=8, sigma_log2=0, sigma_os=4),
+     dict(base_cap=2048, skel_cap=1024)),
     ("sample-all-tiles", 50000, 2, "uniform", dict(phi=32, lam=6, sigma_log2=0, sigma_os=32),
      dict(base_cap=1024, tile=512)),
     ("defaults-100k", 100000, 2, "uniform", {}, {}),
@@ -45,7 +47,8 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("base_kernel,sieve_kernel", [(0, 0), (1, 1)], ids=["sorted-stream", "select-tiles"])
+@pytest.mark.parametrize("base_kernel,sieve_kernel", [(0, 0), (0, 2), (1, 1)],
+                         ids=["sorted-stream", "sorted-stream-rewalk", "select-tiles"])
 @pytest.mark.parametrize("name,n,d,kind,over,kn", CASES, ids=[c[0] for c in CASES])
 def test_build_matches_oracle(name, n, d, kind, over, kn, base_kernel, sieve_kernel):
     pkd = _pkd()

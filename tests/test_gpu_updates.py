@@ -61,7 +61,7 @@ def test_insert_delete_small_tree(kind):
     assert pr.delete(Z, sel) == 600
 
 
-@pytest.mark.parametrize("sieve_kernel", [0, 1], ids=["stream", "tiles"])
+@pytest.mark.parametrize("sieve_kernel", [0, 1, 2], ids=["stream", "tiles", "stream-rewalk"])
 @pytest.mark.parametrize("alpha", [(3, 10), (0, 1), (1, 2), (1, 10)])
 def test_update_sequences_forced_rounds(alpha, sieve_kernel):
     pkd = _pkd()

@@ -148,17 +148,15 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_smem_build(SmemArgs a) {
 // The base case on presorted lists (one CTA per segment of at most cap
 // points): load, sort every dimension once, then split by lookups and stable
 // list partitions.  Instantiated for one CTA per SM (the largest capacity)
-// and for two (half the shared memory and at most 64 registers a thread):
-// the two-CTA launch takes every segment it can hold, the other launch the
-// segments longer than that (a.seg_min).
+// and for two (half the shared memory and at most 64 registers a thread);
+// the segment lists of the two launches are separated when the segments are
+// classified.
 template <int D, int MINB>
 __global__ void __launch_bounds__(SS_THREADS, MINB) k_smem_sorted(SmemArgs a) {
   if (blockIdx.x >= *a.nsegs) return;
   extern __shared__ __align__(16) uint8_t sm[];
   const Seg seg = a.segs[blockIdx.x];
   const int cap = a.cap, tid = threadIdx.x;
-  if ((int)seg.len <= a.seg_min) return;  // taken by the smaller launch
-  if (seg.len > (uint32_t)cap && seg.len <= (uint32_t)a.cap_next) return;  // left to the larger launch
   const SortedLayout Lo = sorted_layout(cap, D);
   int32_t* X = (int32_t*)(sm + Lo.X);
   uint32_t* ID = (uint32_t*)(sm + Lo.ID);
@@ -496,101 +494,124 @@ static void launch_smem_warp(const SmemArgs& a, uint32_t nblocks, size_t smb, cu
 
 
 // Split a segment list into big segments (ctr[0], their tiles ctr[2], their
-// points *pts) and segments finished in shared memory (appended to the
-// persistent base list, counter *nbase).
+// points *pts) and segments finished in shared memory, appended to the
+// persistent base lists: one CTA per SM (longer than cap2), two CTAs per SM
+// (*nbase), one warp (*nwbase) and one warp with a small slice (*ntbase).
 __global__ void k_classify(const Seg* segs, uint32_t nseg, uint32_t cap, Seg* big, uint32_t* ctr,
                            unsigned long long* pts, Seg* base, uint32_t* nbase, uint32_t base_cap,
                            Seg* wbase, uint32_t* nwbase, uint32_t wcap, Seg* tbase, uint32_t* ntbase,
-                           uint32_t tcap, uint32_t tile, uint32_t where, unsigned long long* base_pts,
-                           DevStatus* st) {
+                           uint32_t tcap, Seg* bbase, uint32_t* nbbase, uint32_t cap2, uint32_t tile,
+                           uint32_t where, unsigned long long* base_pts, DevStatus* st) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   Seg s{};
-  int kind = -1;  // 0 big, 1 one CTA, 2 one warp, 3 one warp with a small slice
+  int kind = -1;  // 0 big, 1 one CTA (two per SM), 2 one warp, 3 small slice, 4 one CTA per SM
   if (i < nseg) {
     s = segs[i];
     if (s.len != SEG_SKIP) {
       s.where = where;
-      kind = s.len > cap ? 0 : (s.len > wcap ? 1 : (s.len > tcap ? 2 : 3));
+      kind = s.len > cap ? 0 : (s.len > cap2 ? 4 : (s.len > wcap ? 1 : (s.len > tcap ? 2 : 3)));
     }
   }
-  // counters are updated once per warp and kind
-  for (int k = 0; k < 4; ++k) {
-    const unsigned m = __ballot_sync(FULL_MASK, kind == k);
-    if (!m) continue;
-    unsigned long long sum = kind == k ? s.len : 0;
-    uint32_t tl = (kind == 0) ? (s.len + tile - 1) / tile : 0;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      sum += __shfl_xor_sync(FULL_MASK, sum, o);
-      tl += __shfl_xor_sync(FULL_MASK, tl, o);
-    }
-    uint32_t b = 0;
-    if (lane_id() == 0) {
-      if (k == 0) {
-        b = atomicAdd(&ctr[0], (uint32_t)__popc(m));
-        atomicAdd(&ctr[2], tl);
-        atomicAdd(pts, sum);
-      } else {
-        b = atomicAdd(k == 1 ? nbase : (k == 2 ? nwbase : ntbase), (uint32_t)__popc(m));
-        atomicAdd(&base_pts[k - 1], sum);
-      }
-    }
-    b = __shfl_sync(FULL_MASK, b, 0) + __popc(m & lanemask_lt());
-    if (kind == k) {
-      if (k == 0) big[b] = s;
-      else if (b < base_cap) (k == 1 ? base : (k == 2 ? wbase : tbase))[b] = s;
-      else set_error(st, DERR_CAPACITY, 300 + k);
-    }
+  // the list counters and point sums are updated once per block
+  const uint32_t c[6] = {kind == 0, kind == 1, kind == 2, kind == 3, kind == 4,
+                         kind == 0 ? (s.len + tile - 1) / tile : 0u};
+  uint32_t* const ctrs[6] = {&ctr[0], nbase, nwbase, ntbase, nbbase, &ctr[2]};
+  uint32_t first[6];
+  block_reserve<6>(c, ctrs, first);
+  const unsigned long long len = kind >= 0 ? s.len : 0ull;
+  const unsigned long long v[4] = {kind == 0 ? len : 0ull, (kind == 1 || kind == 4) ? len : 0ull,
+                                   kind == 2 ? len : 0ull, kind == 3 ? len : 0ull};
+  unsigned long long* const sums[4] = {pts, &base_pts[0], &base_pts[1], &base_pts[2]};
+  block_add64<4>(v, sums);
+  if (kind == 0) {
+    big[first[0]] = s;
+  } else if (kind > 0) {
+    const uint32_t b = first[kind];
+    if (b < base_cap) (kind == 1 ? base : (kind == 2 ? wbase : (kind == 3 ? tbase : bbase)))[b] = s;
+    else set_error(st, DERR_CAPACITY, 300 + kind);
   }
 }
 
 // Sample: points whose hash at the segment's depth passes the rate test.
-// Each CTA hashes its tile (ids only), counts its samples, reserves their
-// slots with one atomic on the segment's counter and then gathers their
-// coordinates (the order of a sample is immaterial: only its multiset
-// enters the skeleton).
+// Persistent CTAs, each over a contiguous run of tiles: a CTA hashes a
+// tile's ids and appends the sampled positions to a shared list; once per
+// run of tiles of one segment (or before the list could overflow) it
+// reserves the list's slots in the segment's sample with one atomic and
+// gathers their coordinates.  One atomic per CTA and segment instead of one
+// per tile: the first round's tiles all belong to one segment.  The order of
+// a sample is immaterial: only its multiset enters the skeleton.
 constexpr int SAMPLE_THREADS = 256;
-constexpr int SAMPLE_PER = 16;  // points per thread (tiles of up to 4096)
+constexpr int SAMPLE_PER = 16;      // points per thread (tiles of up to 4096)
+constexpr int SAMPLE_LIST = 8192;   // sampled positions held before a flush
+constexpr int SAMPLE_CTAS_PER_SM = 4;
 
-__global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(RoundArgs r) {
+__device__ __forceinline__ void sample_flush(const RoundArgs& r, const Seg& seg, uint32_t s, const uint32_t* lst,
+                                             int nl, uint32_t* base_sh) {
+  if (threadIdx.x == 0) *base_sh = atomicAdd(&r.scnt[s], (uint32_t)nl);
+  __syncthreads();
+  const uint64_t o0 = seg.start + *base_sh;
+  const int d = r.p.d;
+  for (int i = threadIdx.x; i < nl; i += SAMPLE_THREADS) {
+    const uint64_t g = seg.start + lst[i];
+    for (int j = 0; j < d; ++j) r.samp.c[(uint64_t)j * r.samp.stride + o0 + i] = r.src.x(d, j, g);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(RoundArgs r, uint32_t ntiles) {
   __shared__ uint32_t sh[33];
   __shared__ uint32_t base_sh;
+  __shared__ uint32_t lst[SAMPLE_LIST];
+  const uint32_t per_cta = (ntiles + gridDim.x - 1) / gridDim.x;
+  const uint32_t tb = min(ntiles, blockIdx.x * per_cta), te = min(ntiles, tb + per_cta);
+  if (tb >= te) return;
   const uint32_t nb = *r.nbig;
-  const uint32_t s = seg_of_tile(r.tile0, nb, blockIdx.x);
-  const Seg seg = r.big[s];
-  const uint64_t first = (uint64_t)(blockIdx.x - r.tile0[s]) * r.TILE;
-  if (first >= seg.len) return;
-  const int cnt = (int)min((uint64_t)r.TILE, (uint64_t)seg.len - first);
-  const int shift = sample_shift(r.p, seg.len);
-  const uint64_t key = sample_key(r.p.seed, seg.depth);
-  const int d = r.p.d;
-  uint32_t ids[SAMPLE_PER];
-#pragma unroll
-  for (int k = 0; k < SAMPLE_PER; ++k) {
-    const int i = k * SAMPLE_THREADS + threadIdx.x;
-    if (i < cnt) ids[k] = r.src.id(seg.start + first + (uint64_t)i);
-  }
-  unsigned fl = 0;
-#pragma unroll
-  for (int k = 0; k < SAMPLE_PER; ++k) {
-    const int i = k * SAMPLE_THREADS + threadIdx.x;
-    if (i < cnt && in_sample_k(key, ids[k], shift)) fl |= 1u << k;
-  }
-  uint32_t total;
-  uint32_t off = block_excl_scan<uint32_t>((uint32_t)__popc(fl), sh, &total);
-  if (total == 0) return;
-  if (threadIdx.x == 0) base_sh = atomicAdd(&r.scnt[s], total);
-  __syncthreads();
-  const uint64_t o0 = seg.start + base_sh + off;
-  int q = 0;
-#pragma unroll
-  for (int k = 0; k < SAMPLE_PER; ++k) {
-    if (fl & (1u << k)) {
-      const uint64_t g = seg.start + first + (uint64_t)(k * SAMPLE_THREADS + threadIdx.x);
-      for (int j = 0; j < d; ++j) r.samp.c[(uint64_t)j * r.samp.stride + o0 + q] = r.src.x(d, j, g);
-      ++q;
+  uint32_t s = seg_of_tile(r.tile0, nb, tb);
+  Seg seg = r.big[s];
+  uint32_t t0 = r.tile0[s];
+  int shift = sample_shift(r.p, seg.len);
+  uint64_t key = sample_key(r.p.seed, seg.depth);
+  int nl = 0;  // uniform
+  for (uint32_t tile = tb; tile < te; ++tile) {
+    if (s + 1 < nb && r.tile0[s + 1] <= tile) {  // the next segment with tiles
+      if (nl) sample_flush(r, seg, s, lst, nl, &base_sh);
+      nl = 0;
+      do {
+        ++s;
+      } while (s + 1 < nb && r.tile0[s + 1] <= tile);
+      seg = r.big[s];
+      t0 = r.tile0[s];
+      shift = sample_shift(r.p, seg.len);
+      key = sample_key(r.p.seed, seg.depth);
     }
+    const uint64_t first = (uint64_t)(tile - t0) * r.TILE;
+    if (first >= seg.len) continue;
+    const int cnt = (int)min((uint64_t)r.TILE, (uint64_t)seg.len - first);
+    if (nl + cnt > SAMPLE_LIST) {
+      sample_flush(r, seg, s, lst, nl, &base_sh);
+      nl = 0;
+    }
+    uint32_t ids[SAMPLE_PER];
+#pragma unroll
+    for (int k = 0; k < SAMPLE_PER; ++k) {
+      const int i = k * SAMPLE_THREADS + threadIdx.x;
+      if (i < cnt) ids[k] = r.src.id(seg.start + first + (uint64_t)i);
+    }
+    unsigned fl = 0;
+#pragma unroll
+    for (int k = 0; k < SAMPLE_PER; ++k) {
+      const int i = k * SAMPLE_THREADS + threadIdx.x;
+      if (i < cnt && in_sample_k(key, ids[k], shift)) fl |= 1u << k;
+    }
+    uint32_t total;
+    const uint32_t off = block_excl_scan<uint32_t>((uint32_t)__popc(fl), sh, &total);
+    int q = 0;
+#pragma unroll
+    for (int k = 0; k < SAMPLE_PER; ++k)
+      if (fl & (1u << k)) lst[nl + (int)off + q++] = (uint32_t)(first + (uint64_t)(k * SAMPLE_THREADS + threadIdx.x));
+    nl += (int)total;
   }
+  if (nl) sample_flush(r, seg, s, lst, nl, &base_sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -1206,7 +1227,7 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
 
   // device counters: [0] big segs, [2] their tiles, [3] exact, [4] heavy,
   // [8..10] skeleton jobs; [12] base list length; u64 at [14] big points
-  // u32: [12] CTA list, [13] warp list, [24] tiny list;
+  // u32: [12] CTA list, [13] warp list, [24] tiny list, [25] one-CTA-per-SM list;
   // u64: [14] big points, [16] CTA points, [18] warp points, [20] tiny points
   uint32_t* dctr;
   PKD_TRY(sc.get(&dctr, 32));
@@ -1230,11 +1251,15 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
   const uint32_t wcap = (uint32_t)warp_cap_for(d);
   // every base segment is a root or a non-empty bucket: at most extent + roots
   const uint64_t base_cap_segs = extent + nroots + 16;
-  Seg *base_list, *wbase_list, *tbase_list;
+  Seg *base_list, *wbase_list, *tbase_list, *bbase_list;
   PKD_TRY(sc.get(&base_list, base_cap_segs));
   PKD_TRY(sc.get(&wbase_list, base_cap_segs));
   PKD_TRY(sc.get(&tbase_list, base_cap_segs));
+  PKD_TRY(sc.get(&bbase_list, base_cap_segs));
   const uint32_t tcap = 128;
+  // the presorted base case runs two CTAs per SM up to cap2 points
+  const uint32_t cap2 =
+      knobs().base_kernel == 0 ? std::min<uint32_t>(cap, (uint32_t)sorted_cap_two_per_sm(d)) : cap;
 
   Src src{};
   int src_where;
@@ -1275,7 +1300,8 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     PKD_CUDA(cudaMemsetAsync(dpts, 0, 8, s));
     PKD_LAUNCH(k_classify<<<(unsigned)((ncur + 255) / 256), 256, 0, s>>>(
         cur, (uint32_t)ncur, cap, big, dctr, dpts, base_list, d_nbase, (uint32_t)base_cap_segs,
-        wbase_list, d_nbase + 1, wcap, tbase_list, dctr + 24, tcap, (uint32_t)TILE, (uint32_t)src_where,
+        wbase_list, d_nbase + 1, wcap, tbase_list, dctr + 24, tcap, bbase_list, dctr + 25, cap2, (uint32_t)TILE,
+        (uint32_t)src_where,
         dbase_pts, t.st));
     PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 16 * 4, cudaMemcpyDeviceToHost, s));
     PKD_CUDA(cudaStreamSynchronize(s));
@@ -1324,7 +1350,8 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     {
       KTimer kt;
       ktimer_begin(kt, "sample", pts_big, s);
-      PKD_LAUNCH(k_sample<<<tiles, SAMPLE_THREADS, 0, s>>>(r));
+      const uint32_t sgrid = std::min<uint32_t>(tiles, (uint32_t)stream_sm_count() * SAMPLE_CTAS_PER_SM);
+      PKD_LAUNCH(k_sample<<<sgrid, SAMPLE_THREADS, 0, s>>>(r, tiles));
       ktimer_end(kt);
     }
 
@@ -1388,13 +1415,14 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
   }
 
   // 5. every small subproblem, one CTA each, in shared memory
-  PKD_CUDA(cudaMemcpyAsync(hctr + 12, d_nbase, 13 * 4, cudaMemcpyDeviceToHost, s));
+  PKD_CUDA(cudaMemcpyAsync(hctr + 12, d_nbase, 14 * 4, cudaMemcpyDeviceToHost, s));
   PKD_CUDA(cudaStreamSynchronize(s));
   const uint64_t cta_pts = *(unsigned long long*)(hctr + 16), warp_pts = *(unsigned long long*)(hctr + 18);
   const uint64_t tiny_pts = *(unsigned long long*)(hctr + 20);
   const uint32_t nbase = std::min<uint32_t>(hctr[12], (uint32_t)base_cap_segs);
   const uint32_t nwbase = std::min<uint32_t>(hctr[13], (uint32_t)base_cap_segs);
   const uint32_t ntbase = std::min<uint32_t>(hctr[24], (uint32_t)base_cap_segs);
+  const uint32_t nbbase = std::min<uint32_t>(hctr[25], (uint32_t)base_cap_segs);
   for (int pass = 0; pass < 2; ++pass) {
     const uint32_t nw = pass == 0 ? nwbase : ntbase;
     if (nw == 0) continue;
@@ -1409,26 +1437,28 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     PKD_DISPATCH_D(d, launch_smem_warp, wa, blocks, smb, s);
     ktimer_end(kt);
   }
-  if (nbase > 0) {
-    sa.segs = base_list;
-    sa.nsegs = d_nbase;
-    sa.cap = (int)cap;
+  if (nbase + nbbase > 0) {
     KTimer kt;
     ktimer_begin(kt, "smem_build", cta_pts, s);
     if (knobs().base_kernel == 0) {
-      const int cap2 = std::min<int>((int)cap, sorted_cap_two_per_sm(d));
-      SmemArgs s2 = sa;
-      s2.cap = cap2;
-      s2.seg_min = -1;
-      s2.cap_next = (int)cap;
-      PKD_DISPATCH_D(d, launch_smem_sorted2, s2, nbase, sorted_layout(cap2, d).total, s);
-      if ((int)cap > cap2) {
+      if (nbase > 0) {
+        SmemArgs s2 = sa;
+        s2.segs = base_list;
+        s2.nsegs = d_nbase;
+        s2.cap = (int)cap2;
+        PKD_DISPATCH_D(d, launch_smem_sorted2, s2, nbase, sorted_layout((int)cap2, d).total, s);
+      }
+      if (nbbase > 0) {
         SmemArgs s1 = sa;
-        s1.seg_min = cap2;
-        s1.cap_next = 0;
-        PKD_DISPATCH_D(d, launch_smem_sorted, s1, nbase, sorted_layout((int)cap, d).total, s);
+        s1.segs = bbase_list;
+        s1.nsegs = dctr + 25;
+        s1.cap = (int)cap;
+        PKD_DISPATCH_D(d, launch_smem_sorted, s1, nbbase, sorted_layout((int)cap, d).total, s);
       }
     } else {
+      sa.segs = base_list;
+      sa.nsegs = d_nbase;
+      sa.cap = (int)cap;
       PKD_DISPATCH_D(d, launch_smem_build, sa, nbase, smem_layout((int)cap, d).total, s);
     }
     ktimer_end(kt);

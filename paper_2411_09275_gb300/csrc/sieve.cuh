@@ -63,6 +63,75 @@ __device__ V block_excl_scan(V v, V* sh, V* total) {
   return r;
 }
 
+// Block-wide reservation in K lists, one atomic per list and block: thread
+// t asks c[k] entries of list k (length counter ctr[k]) and receives the
+// index of its first one in first[k].  Appending to a list through one
+// counter serialises at that counter's address, so the fewer updates the
+// better.  Every thread of the block calls it (c = 0 when it adds nothing).
+template <int K>
+__device__ __forceinline__ void block_reserve(const uint32_t (&c)[K], uint32_t* const (&ctr)[K],
+                                              uint32_t (&first)[K]) {
+  __shared__ uint32_t part[K][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t incl[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    incl[k] = c[k];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(FULL_MASK, incl[k], o);
+      if (lane >= o) incl[k] += t;
+    }
+    if (lane == 31) part[k][w] = incl[k];
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const uint32_t v = lane < nw ? part[k][lane] : 0u;
+      uint32_t s = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL_MASK, s, o);
+        if (lane >= o) s += t;
+      }
+      if (lane < nw) part[k][lane] = s - v;
+      const uint32_t tot = __shfl_sync(FULL_MASK, s, 31);
+      if (lane == 0) part[k][32] = tot ? atomicAdd(ctr[k], tot) : 0u;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) first[k] = part[k][32] + part[k][w] + incl[k] - c[k];
+  __syncthreads();  // part is rewritten by the next call
+}
+
+// Block-wide 64-bit sums added to K counters, one atomic per counter and
+// block.  Every thread of the block calls it.
+template <int K>
+__device__ __forceinline__ void block_add64(const unsigned long long (&v)[K], unsigned long long* const (&ctr)[K]) {
+  __shared__ unsigned long long part64[K][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    unsigned long long s = v[k];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
+    if (lane == 0) part64[k][w] = s;
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      unsigned long long s = lane < nw ? part64[k][lane] : 0ull;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
+      if (lane == 0 && s) atomicAdd(ctr[k], s);
+    }
+  }
+  __syncthreads();
+}
+
 // Per-block sums of in[0, n).
 static __global__ void k_scan_reduce(const uint32_t* in, uint64_t n, uint32_t* partial) {
   __shared__ uint32_t sh[33];

@@ -68,10 +68,6 @@ __host__ __device__ __forceinline__ int sk_bucket(int meta) { return (meta >> 16
 struct SmemArgs {
   Params p;
   int cap;  // point capacity of the shared arrays
-  int seg_min;   // presorted base case: only segments longer than this (the
-                 // rest were taken by the launch with the smaller capacity)
-  int cap_next;  // presorted base case: segments in (cap, cap_next] are left
-                 // to the launch with the larger capacity
   // build mode
   Pts A, B;
   const int32_t* in_coords;  // point-major input for IN_INPUT

@@ -680,7 +680,14 @@ __device__ int snode(const Team& tm, const SCtx<D>& cx, STask tk, STask* ch) {
       if (tm.leader()) set_error(cx.st, DERR_STATE, 300 + L);
       return 0;
     }
-    const uint32_t cmap = spartition<D>(tm, cx, tk.map, lo, hi, dim, x, L);
+    // both children wrap into leaves (at most phi points each, and neither
+    // is a skeleton node that its sample would split further): their points
+    // are the two runs of the list sorted along dim, so no other list needs
+    // splitting and no child task is made
+    const bool sk_child = on_sample && tk.j + 1 < cx.p.lambda;
+    const bool leaves = L <= cx.p.phi && n - L <= cx.p.phi &&
+                        (!sk_child || (SL < 2 * cx.p.sigma_os && tk.ns - SL < 2 * cx.p.sigma_os));
+    const uint32_t cmap = leaves ? tk.map : spartition<D>(tm, cx, tk.map, lo, hi, dim, x, L);
     int b = 0;
     if (tm.leader()) b = atomicAdd(&cx.ctl->next_slot, 2);
     b = tm.bcast(b);
@@ -692,6 +699,22 @@ __device__ int snode(const Team& tm, const SCtx<D>& cx, STask tk, STask* ch) {
     if (tm.leader()) {
       cx.nodes[tk.slot] = Node{x, (uint32_t)n, sl, sr};
       cx.ndim[tk.slot] = (uint8_t)dim;
+    }
+    if (leaves) {
+      const int bd = mget(tk.map, dim);
+      if (bd != 0) {  // leaves are written out from list buffer 0
+        const uint16_t* P = cx.list(bd);
+        uint16_t* Q = cx.list(0);
+        for (int i = lo + tm.rank(); i < hi; i += tm.size()) Q[i] = P[i];
+      }
+      if (tm.leader()) {
+        cx.nodes[sl] = Node{0, (uint32_t)L, (uint32_t)(cx.start + lo), 0};
+        cx.ndim[sl] = PKD_LEAF;
+        cx.nodes[sr] = Node{0, (uint32_t)(n - L), (uint32_t)(cx.start + lo + L), 0};
+        cx.ndim[sr] = PKD_LEAF;
+        atomicMax(&cx.ctl->maxd, tk.t + 1);
+      }
+      return 0;
     }
     const uint8_t nj = on_sample ? (uint8_t)(tk.j + 1) : (uint8_t)0;
     const int SR = on_sample ? tk.ns - SL : 0;

@@ -269,19 +269,22 @@ static void launch_route_small(const RoundArgs& ra, const uint32_t* small, const
 // Next-round items and leaf groups from the bucket ranges.
 __global__ void __launch_bounds__(ITEM_WARPS * 32) k_route_emit(UpdArgs a) {
   const uint32_t i = item_of_warp();
-  if (i >= *a.nitems) return;  // warp-uniform
+  const bool valid = i < *a.nitems;  // warp-uniform; every warp takes part in the block's counter updates
   const int lane = lane_id();
-  const Seg it = a.items[i];
+  Seg it{};
   const int2* sk = a.skel + (uint64_t)i * a.HN;
   const uint32_t* sl = a.slots + (uint64_t)i * a.HN;
-  for (int b = lane; b < a.NB; b += 32) a.link[(uint64_t)i * a.NB + b] = LINK_NONE;
+  if (valid) {
+    it = a.items[i];
+    for (int b = lane; b < a.NB; b += 32) a.link[(uint64_t)i * a.NB + b] = LINK_NONE;
+  }
   __syncwarp();
   for (int v0 = 1; v0 < a.HN; v0 += 32) {
     const int v = v0 + lane;
     bool leaf = false, inner = false;
     uint32_t cnt = 0, slot = 0, depth = 0;
     uint64_t b0 = 0, k = 0;
-    if (v < a.HN) {
+    if (valid && v < a.HN) {
       const int m = sk[v].y;
       if (sk_state(m) == SK_BUCKET) {
         k = (uint64_t)i * a.NB + sk_bucket(m);
@@ -295,25 +298,14 @@ __global__ void __launch_bounds__(ITEM_WARPS * 32) k_route_emit(UpdArgs a) {
         }
       }
     }
-    // one update of each counter per warp
+    // one update of each counter per block
     const bool big = inner && cnt > SMALL_ITEM;
-    const unsigned mL = __ballot_sync(FULL_MASK, leaf), mN = __ballot_sync(FULL_MASK, inner);
-    const unsigned mB = __ballot_sync(FULL_MASK, big), mS = __ballot_sync(FULL_MASK, inner && !big);
-    uint32_t tiles = big ? (cnt + a.TILE - 1) / a.TILE : 0u;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) tiles += __shfl_xor_sync(FULL_MASK, tiles, o);
-    uint32_t gB = 0, qB = 0, kB = 0, sB = 0;
-    if (lane == 0) {
-      if (mL) gB = atomicAdd(a.ngroups, (uint32_t)__popc(mL));
-      if (mN) qB = atomicAdd(&a.next_ctr[0], (uint32_t)__popc(mN));
-      if (mB) {
-        kB = atomicAdd(&a.next_ctr[2], (uint32_t)__popc(mB));
-        atomicAdd(&a.next_ctr[1], tiles);
-      }
-      if (mS) sB = atomicAdd(&a.next_ctr[3], (uint32_t)__popc(mS));
-    }
-    const unsigned lt = lanemask_lt();
-    const uint32_t g = __shfl_sync(FULL_MASK, gB, 0) + __popc(mL & lt);
+    const uint32_t c[5] = {leaf ? 1u : 0u, inner ? 1u : 0u, big ? 1u : 0u, inner && !big ? 1u : 0u,
+                           big ? (cnt + a.TILE - 1) / a.TILE : 0u};
+    uint32_t* const ctrs[5] = {a.ngroups, &a.next_ctr[0], &a.next_ctr[2], &a.next_ctr[3], &a.next_ctr[1]};
+    uint32_t first[5];
+    block_reserve<5>(c, ctrs, first);
+    const uint32_t g = first[0];
     if (leaf) {
       if (g >= a.group_cap) {
         set_error(a.st, DERR_CAPACITY, 800);
@@ -322,9 +314,7 @@ __global__ void __launch_bounds__(ITEM_WARPS * 32) k_route_emit(UpdArgs a) {
         a.link[k] = LINK_LEAF | g;
       }
     }
-    const uint32_t q = __shfl_sync(FULL_MASK, qB, 0) + __popc(mN & lt);
-    const uint32_t kb = __shfl_sync(FULL_MASK, kB, 0) + __popc(mB & lt);
-    const uint32_t sb = __shfl_sync(FULL_MASK, sB, 0) + __popc(mS & lt);
+    const uint32_t q = first[1], kb = first[2], sb = first[3];
     if (inner) {
       const Seg c{b0, cnt, depth, slot, IN_B};
       a.next[q] = c;
@@ -556,22 +546,15 @@ __global__ void k_leaf_items(UpdArgs a, LeafGroup* groups, const uint32_t* ngrou
       }
     }
   }
-  // one counter update per warp
-  const unsigned mp = __ballot_sync(FULL_MASK, push), mc = __ballot_sync(FULL_MASK, comp);
-  const int lead = 0;
-  uint32_t bp = 0, bc = 0;
-  unsigned long long tot = push ? it.size : 0;
-#pragma unroll
-  for (int o = 16; o; o >>= 1) tot += __shfl_xor_sync(FULL_MASK, tot, o);
-  if (lane_id() == lead) {
-    if (mp) {
-      bp = atomicAdd(a.nitems_out, (uint32_t)__popc(mp));
-      atomicAdd(a.items_total, tot);
-    }
-    if (mc) bc = atomicAdd(ncompact, (uint32_t)__popc(mc));
-  }
-  bp = __shfl_sync(FULL_MASK, bp, lead) + __popc(mp & lanemask_lt());
-  bc = __shfl_sync(FULL_MASK, bc, lead) + __popc(mc & lanemask_lt());
+  // one counter update per block
+  const uint32_t c[2] = {push ? 1u : 0u, comp ? 1u : 0u};
+  uint32_t* const ctrs[2] = {a.nitems_out, ncompact};
+  uint32_t first[2];
+  block_reserve<2>(c, ctrs, first);
+  const unsigned long long tv[1] = {push ? (unsigned long long)it.size : 0ull};
+  unsigned long long* const tc[1] = {a.items_total};
+  block_add64<1>(tv, tc);
+  const uint32_t bp = first[0], bc = first[1];
   if (push) {
     if (bp < a.items_cap) a.items_out[bp] = it;
     else set_error(a.st, DERR_CAPACITY, 811);
@@ -683,26 +666,38 @@ struct Front {
 
 __global__ void k_front_init(const RebuildItem* it, const uint32_t* n, Front* f, uint32_t* nf) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= *n) return;
-  if (it[i].old_live == 0) return;
-  f[atomicAdd(nf, 1u)] = Front{it[i].slot, i, 0};
+  const bool e = i < *n && it[i].old_live != 0;
+  const uint32_t c[1] = {e ? 1u : 0u};
+  uint32_t* const ctrs[1] = {nf};
+  uint32_t first[1];
+  block_reserve<1>(c, ctrs, first);
+  if (e) f[first[0]] = Front{it[i].slot, i, 0};
 }
 
 __global__ void k_front_expand(const Front* f, const uint32_t* nf, Front* g, uint32_t* ng, Front* leaves,
                                uint32_t* nleaves, const Node* nodes, const uint8_t* ndim, const uint32_t* aux,
                                int use_aux, uint32_t cap, DevStatus* st) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= *nf) return;
-  const Front e = f[i];
-  if (ndim[e.slot] == PKD_LEAF) {
-    const uint32_t k = atomicAdd(nleaves, 1u);
-    if (k < cap) leaves[k] = e;
+  const bool have = i < *nf;
+  Front e{};
+  bool leaf = false;
+  if (have) {
+    e = f[i];
+    leaf = ndim[e.slot] == PKD_LEAF;
+  }
+  const uint32_t c[2] = {have && leaf ? 1u : 0u, have && !leaf ? 2u : 0u};
+  uint32_t* const ctrs[2] = {nleaves, ng};
+  uint32_t first[2];
+  block_reserve<2>(c, ctrs, first);
+  if (!have) return;
+  if (leaf) {
+    if (first[0] < cap) leaves[first[0]] = e;
     else set_error(st, DERR_CAPACITY, 820);
     return;
   }
   const Node nd = nodes[e.slot];
   const uint32_t llive = nodes[nd.a].size - (use_aux ? aux[nd.a] : 0u);
-  const uint32_t k = atomicAdd(ng, 2u);
+  const uint32_t k = first[1];
   if (k + 2 > cap) {
     set_error(st, DERR_CAPACITY, 821);
     return;
@@ -1152,7 +1147,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
   trace_mark(s, "upd: match+count+decide");
   uint32_t* compact;
   PKD_TRY(sc.get(&compact, std::max<uint32_t>(ngroups, 1)));
-  if (ngroups) PKD_LAUNCH(k_leaf_items<<<(ngroups + 127) / 128, 128, 0, s>>>(ua, groups, d_ngroups, compact, d_ncompact));
+  if (ngroups) PKD_LAUNCH(k_leaf_items<<<(ngroups + 255) / 256, 256, 0, s>>>(ua, groups, d_ngroups, compact, d_ncompact));
   PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 40, cudaMemcpyDeviceToHost, s));
   PKD_CUDA(cudaStreamSynchronize(s));
   const uint32_t nitems = hctr[5];

@@ -150,15 +150,31 @@ int check_params(const pkd_params* p) {
   return PKD_OK;
 }
 
+// Every coordinate in [0, 2^30): a value is out of range exactly when one of
+// its two top bits is set.  A scalar head up to the first 16-byte boundary,
+// then 16-byte loads, four in flight per thread, then a scalar tail.
+static_assert(PKD_COORD_LIMIT == (1 << 30), "range test by the top two bits");
 __global__ void k_validate(const int32_t* c, uint64_t cnt, int* bad) {
-  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  int b = 0;
-  for (; i < cnt; i += stride) {
-    const int32_t v = c[i];
-    b |= (v < 0) | (v >= PKD_COORD_LIMIT);
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t head = min(cnt, (uint64_t)(((16u - ((uintptr_t)c & 15u)) & 15u) >> 2));
+  unsigned b = 0;
+  if (tid < head) b |= (unsigned)c[tid];
+  const int4* v4 = reinterpret_cast<const int4*>(c + head);
+  const uint64_t n4 = (cnt - head) >> 2;
+  uint64_t i = tid;
+  for (; i + 3 * nth < n4; i += 4 * nth) {
+    const int4 a0 = v4[i], a1 = v4[i + nth], a2 = v4[i + 2 * nth], a3 = v4[i + 3 * nth];
+    b |= (unsigned)(a0.x | a0.y | a0.z | a0.w | a1.x | a1.y | a1.z | a1.w);
+    b |= (unsigned)(a2.x | a2.y | a2.z | a2.w | a3.x | a3.y | a3.z | a3.w);
   }
-  if (__any_sync(0xffffffffu, b) && (threadIdx.x & 31) == 0) atomicOr(bad, 1);
+  for (; i < n4; i += nth) {
+    const int4 a = v4[i];
+    b |= (unsigned)(a.x | a.y | a.z | a.w);
+  }
+  const uint64_t t0 = head + 4 * n4;
+  if (tid < cnt - t0) b |= (unsigned)c[t0 + tid];
+  if (__any_sync(0xffffffffu, (b >> 30) != 0) && (threadIdx.x & 31) == 0) atomicOr(bad, 1);
 }
 
 int validate_coords(const int32_t* c, uint64_t cnt, cudaStream_t s, bool* ok) {

@@ -649,11 +649,29 @@ __global__ void k_item_sizes(const RebuildItem* it, const uint32_t* n, uint32_t*
   if (i < *n) sizes[i] = it[i].size;
 }
 
-__global__ void k_item_pos(RebuildItem* it, const uint32_t* n, const uint32_t* off, uint64_t top, Seg* segs) {
+// An item of at most phi points is a leaf again (Build wraps it): its
+// segment is skipped by the rebuild, which then only visits the items that
+// split, and k_item_leaves writes its node once its points are in place.
+__global__ void k_item_pos(RebuildItem* it, const uint32_t* n, const uint32_t* off, uint64_t top, Seg* segs,
+                           uint32_t phi) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= *n) return;
-  it[i].pos = top + off[i];
-  segs[i] = Seg{top + off[i], it[i].size, it[i].depth, it[i].slot, IN_A};
+  const RebuildItem x = it[i];
+  const uint64_t pos = top + off[i];
+  it[i].pos = pos;
+  segs[i] = Seg{pos, x.size <= phi ? SEG_SKIP : x.size, x.depth, x.slot, IN_A};
+}
+
+// The node of every item of at most phi points: a leaf over its new range.
+// (Its depth is that of the old subtree's root, so the tree's depth bound
+// needs no update.)
+__global__ void k_item_leaves(const RebuildItem* it, const uint32_t* n, Node* nodes, uint8_t* ndim, uint32_t phi) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *n) return;
+  const RebuildItem x = it[i];
+  if (x.size > phi) return;
+  nodes[x.slot] = Node{0, x.size, (uint32_t)x.pos, 0};
+  ndim[x.slot] = PKD_LEAF;
 }
 
 // Breadth-first flatten of the old subtrees of the rebuild items: every
@@ -1172,7 +1190,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
     const unsigned gi = (nitems + 127) / 128;
     PKD_LAUNCH(k_item_sizes<<<gi, 128, 0, s>>>(items_out, d_nitems, isz));
     device_excl_scan(isz, ioff, nitems, ipart, s);
-    PKD_LAUNCH(k_item_pos<<<gi, 128, 0, s>>>(items_out, d_nitems, ioff, t.top, segs));
+    PKD_LAUNCH(k_item_pos<<<gi, 128, 0, s>>>(items_out, d_nitems, ioff, t.top, segs, (uint32_t)p.phi));
     // flatten the old subtrees breadth first
     {
       // capacity: every node of the old subtrees appears once
@@ -1205,6 +1223,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
                        insert ? 0 : 1, s);
     }
     if (insert) PKD_DISPATCH_D(d, launch_copy_new, items_out, d_nitems, nitems, F, t.A, s);
+    PKD_LAUNCH(k_item_leaves<<<gi, 128, 0, s>>>(items_out, d_nitems, t.nodes, t.ndim, (uint32_t)p.phi));
     trace_mark(s, "upd: flatten + gather");
     BuildJob job;
     job.base = t.top;

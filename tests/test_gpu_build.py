@@ -97,3 +97,31 @@ def test_build_deterministic_and_config1():
     b = pkd.Tree(to_dev(X), None, p).export()
     U.assert_exports_equal(a, b)
     U.assert_exports_equal(a, O.OracleTree(X, None, oparams(p)).export())
+
+
+@pytest.mark.parametrize("n", [1, 3, 6, 37, 1000, 100003])
+def test_build_validation_every_position_and_alignment(n):
+    # The range check reads a scalar head up to a 16-byte boundary, 16-byte
+    # vectors, then a scalar tail: a bad value is caught wherever it sits
+    # and whatever the buffer's alignment; in-range extremes pass.
+    import torch
+
+    pkd = _pkd()
+    d = 2
+    base = make_points("uniform", n, d, 11).reshape(-1)
+    base[0] = 0
+    base[-1] = (1 << 30) - 1
+    for off in range(4):
+        buf = torch.zeros(n * d + 4, dtype=torch.int32, device="cuda")
+        view = buf[off:off + n * d]
+        view.copy_(torch.from_numpy(base))
+        t = pkd.Tree(view.view(n, d), None, pkd.Params(d=d))
+        assert t.size == n
+        t.close()
+        for pos in sorted({0, 1, 2, 3, n * d // 2, n * d - 2, n * d - 1} & set(range(n * d))):
+            for bad in (-1, 1 << 30, -(1 << 31)):
+                view.copy_(torch.from_numpy(base))
+                view[pos] = bad
+                with pytest.raises(pkd.PkdError) as e:
+                    pkd.Tree(view.view(n, d), None, pkd.Params(d=d))
+                assert e.value.code == pkd.PKD_EINVAL

@@ -350,6 +350,7 @@ __global__ void k_copy_round(RoundArgs r, Pts F) {
 // so a warp keeps UPW dependent chains in flight instead of one.
 constexpr int UPW = 4;
 constexpr int UPW_WARPS = 8;  // warps per CTA
+static_assert(32 % UPW == 0, "lanes split evenly between a warp's leaves");
 __host__ __device__ inline unsigned upw_blocks(uint32_t n) {
   return (unsigned)(((uint64_t)n + UPW * UPW_WARPS - 1) / (UPW * UPW_WARPS));
 }
@@ -374,6 +375,65 @@ __global__ void __launch_bounds__(UPW_WARPS * 32) k_match(LeafGroup* groups, con
     glen = G.len;
     a = leaf.a;
     sz = leaf.size;
+  }
+  {
+    // common case: every leaf of the warp holds at most 32 points and
+    // receives at most 32 / UPW batch points; all loads are issued at once
+    constexpr int PER = 32 / UPW;
+    uint32_t qa[UPW], qsz[UPW], qlen[UPW];
+    bool small = true;
+#pragma unroll
+    for (int q = 0; q < UPW; ++q) {
+      qa[q] = __shfl_sync(FULL_MASK, a, q);
+      qsz[q] = __shfl_sync(FULL_MASK, sz, q);
+      qlen[q] = __shfl_sync(FULL_MASK, glen, q);
+      small &= qsz[q] <= 32 && qlen[q] <= (uint32_t)PER;
+    }
+    if (small) {
+      int32_t x[UPW][D];
+      uint32_t id[UPW];
+#pragma unroll
+      for (int q = 0; q < UPW; ++q) {
+        id[q] = 0;
+        if ((uint32_t)lane < qsz[q]) {
+#pragma unroll
+          for (int j = 0; j < D; ++j) x[q][j] = A.c[(uint64_t)j * A.stride + qa[q] + lane];
+          id[q] = A.id[(uint64_t)qa[q] + lane];
+        }
+      }
+      // lane q * PER + e holds batch point e of leaf q
+      const int mq = lane / PER, me = lane % PER;
+      const unsigned long long myst = __shfl_sync(FULL_MASK, gst, mq);
+      const uint32_t mylen = __shfl_sync(FULL_MASK, glen, mq);
+      int32_t fx[D];
+      uint32_t fid = 0xFFFFFFFFu;
+      if ((uint32_t)me < mylen) {
+        const uint64_t r = myst + (uint64_t)me;
+#pragma unroll
+        for (int j = 0; j < D; ++j) fx[j] = F.c[(uint64_t)j * F.stride + r];
+        fid = F.id[r];
+      }
+#pragma unroll
+      for (int q = 0; q < UPW; ++q) {
+        bool hit = false;
+        for (int t = 0; t < (int)qlen[q]; ++t) {
+          const int src = q * PER + t;
+          bool same = __shfl_sync(FULL_MASK, fid, src) == id[q];
+#pragma unroll
+          for (int j = 0; j < D; ++j) same &= __shfl_sync(FULL_MASK, fx[j], src) == x[q][j];
+          hit |= same;
+        }
+        hit &= (uint32_t)lane < qsz[q];
+        if (hit) dead[(uint64_t)qa[q] + lane] = 1;
+        const int found = __popc(__ballot_sync(FULL_MASK, hit));
+        const uint32_t qslot = __shfl_sync(FULL_MASK, slot, q);
+        if (lane == 0 && k0 + q < n) {
+          groups[k0 + q].found = (uint32_t)found;
+          aux[qslot] = (uint32_t)found;
+        }
+      }
+      return;
+    }
   }
 #pragma unroll
   for (int q = 0; q < UPW; ++q) {
@@ -812,6 +872,26 @@ __global__ void __launch_bounds__(UPW_WARPS * 32) k_copy_new(const RebuildItem* 
     ws = it.ws;
     cnt = it.we - it.ws;
     dst0 = it.pos + it.old_live;
+  }
+  {
+    // common case: at most 32 / UPW new points per item, one per lane
+    constexpr int PER = 32 / UPW;
+    const int mq = lane / PER, me = lane % PER;
+    const unsigned long long mws = __shfl_sync(FULL_MASK, ws, mq), mcnt = __shfl_sync(FULL_MASK, cnt, mq);
+    const unsigned long long md = __shfl_sync(FULL_MASK, dst0, mq);
+    if (__all_sync(FULL_MASK, mcnt <= (unsigned long long)PER)) {
+      if ((unsigned long long)me < mcnt) {
+        const uint64_t src = mws + me, dst = md + me;
+        int32_t x[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) x[j] = F.c[(uint64_t)j * F.stride + src];
+        const uint32_t id = F.id[src];
+#pragma unroll
+        for (int j = 0; j < D; ++j) A.c[(uint64_t)j * A.stride + dst] = x[j];
+        A.id[dst] = id;
+      }
+      return;
+    }
   }
 #pragma unroll 1
   for (int q = 0; q < UPW; ++q) {

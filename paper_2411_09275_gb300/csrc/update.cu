@@ -101,15 +101,20 @@ __device__ __forceinline__ uint32_t item_of_warp() { return blockIdx.x * ITEM_WA
 
 // The skeleton at each item: its node and lambda levels below, cut at leaves;
 // the external nodes are numbered left to right (the item's buckets).
+// The skeleton is assembled in shared memory (one level's node loads in
+// flight at a time, both of a node's records at once) and written out at
+// the end.
 __global__ void __launch_bounds__(ITEM_WARPS * 32) k_fetch(UpdArgs a) {
+  extern __shared__ __align__(16) uint8_t fetch_sm[];
   __shared__ uint32_t bits_sh[ITEM_WARPS][32], pre_sh[ITEM_WARPS][32];
   const uint32_t i = item_of_warp();
   if (i >= *a.nitems) return;  // warp-uniform
   const int lane = lane_id();
   uint32_t* bits = bits_sh[warp_id()];
   uint32_t* pre = pre_sh[warp_id()];
-  int2* sk = a.skel + (uint64_t)i * a.HN;
-  uint32_t* sl = a.slots + (uint64_t)i * a.HN;
+  int2* sk = reinterpret_cast<int2*>(fetch_sm) + (size_t)warp_id() * a.HN;
+  uint32_t* sl = reinterpret_cast<uint32_t*>(reinterpret_cast<int2*>(fetch_sm) + (size_t)ITEM_WARPS * a.HN) +
+                 (size_t)warp_id() * a.HN;
   for (int v = lane; v < a.HN; v += 32) {
     sk[v] = make_int2(0, sk_meta(SK_NONE, 0, 0));
     sl[v] = 0xFFFFFFFFu;
@@ -125,14 +130,18 @@ __global__ void __launch_bounds__(ITEM_WARPS * 32) k_fetch(UpdArgs a) {
     for (int v = (1 << j) + lane; v < (2 << j); v += 32) {
       if (sk_state(sk[v].y) == SK_NONE) continue;
       const uint32_t slot = sl[v];
-      const uint8_t dm = j < a.lam ? a.ndim[slot] : (uint8_t)PKD_LEAF;
+      uint8_t dm = (uint8_t)PKD_LEAF;
+      Node nd{};
+      if (j < a.lam) {  // both loads issued together
+        dm = a.ndim[slot];
+        nd = a.nodes[slot];
+      }
       if (dm == PKD_LEAF) {
         // external: bit (its first position on level lambda) in the bitmap
         const uint32_t lo = (uint32_t)(v - (1 << j)) << (a.lam - j);
         atomicOr(&bits[lo >> 5], 1u << (lo & 31));
         continue;
       }
-      const Node nd = a.nodes[slot];
       sk[v] = make_int2(nd.split, sk_meta(SK_INTERNAL, dm, 0));
       sl[2 * v] = nd.a;
       sl[2 * v + 1] = nd.b;
@@ -153,6 +162,13 @@ __global__ void __launch_bounds__(ITEM_WARPS * 32) k_fetch(UpdArgs a) {
       const uint32_t nbk = pre[lo >> 5] + (uint32_t)__popc(bits[lo >> 5] & ((1u << (lo & 31)) - 1u));
       sk[v].y = sk_meta(SK_BUCKET, 0, (int)nbk);
     }
+  }
+  __syncwarp();
+  int2* gsk = a.skel + (uint64_t)i * a.HN;
+  uint32_t* gsl = a.slots + (uint64_t)i * a.HN;
+  for (int v = lane; v < a.HN; v += 32) {
+    gsk[v] = sk[v];
+    gsl[v] = sl[v];
   }
   if (lane == 31) a.nbk[i] = incl;
 }
@@ -269,22 +285,19 @@ static void launch_route_small(const RoundArgs& ra, const uint32_t* small, const
 // Next-round items and leaf groups from the bucket ranges.
 __global__ void __launch_bounds__(ITEM_WARPS * 32) k_route_emit(UpdArgs a) {
   const uint32_t i = item_of_warp();
-  const bool valid = i < *a.nitems;  // warp-uniform; every warp takes part in the block's counter updates
+  if (i >= *a.nitems) return;  // warp-uniform
   const int lane = lane_id();
-  Seg it{};
+  const Seg it = a.items[i];
   const int2* sk = a.skel + (uint64_t)i * a.HN;
   const uint32_t* sl = a.slots + (uint64_t)i * a.HN;
-  if (valid) {
-    it = a.items[i];
-    for (int b = lane; b < a.NB; b += 32) a.link[(uint64_t)i * a.NB + b] = LINK_NONE;
-  }
+  for (int b = lane; b < a.NB; b += 32) a.link[(uint64_t)i * a.NB + b] = LINK_NONE;
   __syncwarp();
   for (int v0 = 1; v0 < a.HN; v0 += 32) {
     const int v = v0 + lane;
     bool leaf = false, inner = false;
     uint32_t cnt = 0, slot = 0, depth = 0;
     uint64_t b0 = 0, k = 0;
-    if (valid && v < a.HN) {
+    if (v < a.HN) {
       const int m = sk[v].y;
       if (sk_state(m) == SK_BUCKET) {
         k = (uint64_t)i * a.NB + sk_bucket(m);
@@ -298,14 +311,25 @@ __global__ void __launch_bounds__(ITEM_WARPS * 32) k_route_emit(UpdArgs a) {
         }
       }
     }
-    // one update of each counter per block
+    // one update of each counter per warp
     const bool big = inner && cnt > SMALL_ITEM;
-    const uint32_t c[5] = {leaf ? 1u : 0u, inner ? 1u : 0u, big ? 1u : 0u, inner && !big ? 1u : 0u,
-                           big ? (cnt + a.TILE - 1) / a.TILE : 0u};
-    uint32_t* const ctrs[5] = {a.ngroups, &a.next_ctr[0], &a.next_ctr[2], &a.next_ctr[3], &a.next_ctr[1]};
-    uint32_t first[5];
-    block_reserve<5>(c, ctrs, first);
-    const uint32_t g = first[0];
+    const unsigned mL = __ballot_sync(FULL_MASK, leaf), mN = __ballot_sync(FULL_MASK, inner);
+    const unsigned mB = __ballot_sync(FULL_MASK, big), mS = __ballot_sync(FULL_MASK, inner && !big);
+    uint32_t tiles = big ? (cnt + a.TILE - 1) / a.TILE : 0u;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) tiles += __shfl_xor_sync(FULL_MASK, tiles, o);
+    uint32_t gB = 0, qB = 0, kB = 0, sB = 0;
+    if (lane == 0) {
+      if (mL) gB = atomicAdd(a.ngroups, (uint32_t)__popc(mL));
+      if (mN) qB = atomicAdd(&a.next_ctr[0], (uint32_t)__popc(mN));
+      if (mB) {
+        kB = atomicAdd(&a.next_ctr[2], (uint32_t)__popc(mB));
+        atomicAdd(&a.next_ctr[1], tiles);
+      }
+      if (mS) sB = atomicAdd(&a.next_ctr[3], (uint32_t)__popc(mS));
+    }
+    const unsigned lt = lanemask_lt();
+    const uint32_t g = __shfl_sync(FULL_MASK, gB, 0) + __popc(mL & lt);
     if (leaf) {
       if (g >= a.group_cap) {
         set_error(a.st, DERR_CAPACITY, 800);
@@ -314,7 +338,9 @@ __global__ void __launch_bounds__(ITEM_WARPS * 32) k_route_emit(UpdArgs a) {
         a.link[k] = LINK_LEAF | g;
       }
     }
-    const uint32_t q = first[1], kb = first[2], sb = first[3];
+    const uint32_t q = __shfl_sync(FULL_MASK, qB, 0) + __popc(mN & lt);
+    const uint32_t kb = __shfl_sync(FULL_MASK, kB, 0) + __popc(mB & lt);
+    const uint32_t sb = __shfl_sync(FULL_MASK, sB, 0) + __popc(mS & lt);
     if (inner) {
       const Seg c{b0, cnt, depth, slot, IN_B};
       a.next[q] = c;
@@ -526,16 +552,33 @@ __device__ void push_rebuild(const UpdArgs& a, uint32_t slot, uint32_t depth, ui
 // Top-down alpha test over every skeleton (rounds in forward order; within a
 // skeleton, level by level from the root).  under: one bit per heap node
 // inside a subtree that is rebuilt.
+// The item's skeleton, slots and counts are staged in shared memory first;
+// each level then loads only node sizes (both of a node's at once).
 __global__ void __launch_bounds__(ITEM_WARPS * 32) k_decide(UpdArgs a) {
+  extern __shared__ __align__(16) uint8_t dec_sm[];
   __shared__ uint32_t under_sh[ITEM_WARPS][64];
   const uint32_t i = item_of_warp();
   if (i >= *a.nitems) return;  // warp-uniform
   const int lane = lane_id();
   uint32_t* under = under_sh[warp_id()];
   const Seg it = a.items[i];
-  const int2* sk = a.skel + (uint64_t)i * a.HN;
-  const uint32_t* sl = a.slots + (uint64_t)i * a.HN;
-  const uint32_t* f = a.fnd + (uint64_t)i * a.HN;
+  int2* sk = reinterpret_cast<int2*>(dec_sm) + (size_t)warp_id() * a.HN;
+  uint32_t* sl = reinterpret_cast<uint32_t*>(reinterpret_cast<int2*>(dec_sm) + (size_t)ITEM_WARPS * a.HN) +
+                 (size_t)warp_id() * a.HN;
+  uint32_t* f = sl + (size_t)ITEM_WARPS * a.HN;
+  {
+    const int2* gsk = a.skel + (uint64_t)i * a.HN;
+    const uint32_t* gsl = a.slots + (uint64_t)i * a.HN;
+    const uint32_t* gf = a.fnd + (uint64_t)i * a.HN;
+    for (int v = 1 + lane; v < a.HN; v += 32) {
+      const int2 e = gsk[v];
+      sk[v] = e;
+      if (sk_state(e.y) != SK_NONE) {
+        sl[v] = gsl[v];
+        f[v] = gf[v];
+      }
+    }
+  }
   under[lane] = 0;
   under[lane + 32] = 0;
   __syncwarp();
@@ -563,9 +606,8 @@ __global__ void __launch_bounds__(ITEM_WARPS * 32) k_decide(UpdArgs a) {
       const uint32_t c = f[v];
       if (c == 0) continue;  // nothing below changes
       const uint32_t slot = sl[v];
-      const uint32_t old = a.nodes[slot].size;
+      const uint32_t old = a.nodes[slot].size, lold = a.nodes[sl[c0]].size;
       const uint32_t N = a.insert ? old + c : old - c;
-      const uint32_t lold = a.nodes[sl[c0]].size;
       const uint32_t L = a.insert ? lold + f[c0] : lold - f[c0];
       if (N > 0 && is_balanced(L, N, a.p.alpha_num, a.p.alpha_den)) {
         a.wnodes[slot].size = N;
@@ -1147,7 +1189,15 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
     ua.next_bigmap = next_bigmap;
     ua.next_small = next_small;
     const unsigned g1 = item_blocks(ncur);
-    PKD_LAUNCH(k_fetch<<<g1, ITEM_WARPS * 32, 0, s>>>(ua));
+    {
+      const size_t smb = (size_t)ITEM_WARPS * HN * (sizeof(int2) + sizeof(uint32_t));
+      static size_t set = 0;
+      if (smb > 48 * 1024 && set < smb) {
+        cudaFuncSetAttribute(k_fetch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+        set = smb;
+      }
+      PKD_LAUNCH(k_fetch<<<g1, ITEM_WARPS * 32, smb, s>>>(ua));
+    }
 
     RoundArgs ra{};
     ra.p = p;
@@ -1240,7 +1290,15 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
     ua.blen = R.blen;
     ua.iflag = R.iflag;
     ua.next_iflag = (r + 1 < rounds.size()) ? rounds[r + 1].iflag : nullptr;
-    PKD_LAUNCH(k_decide<<<item_blocks(R.n), ITEM_WARPS * 32, 0, s>>>(ua));
+    {
+      const size_t smb = (size_t)ITEM_WARPS * HN * (sizeof(int2) + 2 * sizeof(uint32_t));
+      static size_t set = 0;
+      if (smb > 48 * 1024 && set < smb) {
+        cudaFuncSetAttribute(k_decide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+        set = smb;
+      }
+      PKD_LAUNCH(k_decide<<<item_blocks(R.n), ITEM_WARPS * 32, smb, s>>>(ua));
+    }
   }
   trace_mark(s, "upd: match+count+decide");
   uint32_t* compact;

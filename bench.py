@@ -65,11 +65,14 @@ DEFAULT_WORKLOAD = "build1e8_d3_ins1e7_del1e7"
 # once, 2 * (4d + 4); a count pass reads the coordinates only, 4d; the sample
 # pass reads the ids, 4.
 def algo_bytes(kernel: str, d: int) -> float | None:
+    """Algorithmic DRAM bytes per point: a pass that reads and writes every
+    point moves 2(4d+4); the count reads the coordinates (4d); sampling and
+    the range check read one 4-byte word."""
     return {"scatter": 2 * (4 * d + 4), "smem_build": 2 * (4 * d + 4), "smem_warp": 2 * (4 * d + 4),
             "count": 4 * d, "sample": 4, "validate": 4}.get(kernel)
 
 
-TIMED_KERNELS = ["smem_build", "smem_warp", "scatter", "count", "sample", "validate"]
+TIMED_KERNELS = ["smem_build", "smem_warp", "scatter", "count", "sample", "validate", "scatter_route", "count_route"]
 
 
 def measured_peaks():
@@ -743,6 +746,16 @@ def main():
         roof = {"bound": "hbm", "kernel": dom, "achieved": kd["achieved_gbs"], "peak": peak,
                 "unit": "GB/s", "frac": (kd["achieved_gbs"] / peak) if kd["achieved_gbs"] else None,
                 "traffic": traffic, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
+    # the build's HBM-bound sieve kernels, each against the same peak
+    roof_sieve = {}
+    for name in ("scatter", "count", "sample", "validate"):
+        kd = kernels.get(name)
+        if not kd or not kd["achieved_gbs"]:
+            continue
+        tr = dram_traffic().get(name)
+        roof_sieve[name] = {"bound": "hbm", "achieved": kd["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                            "frac": kd["achieved_gbs"] / peak,
+                            "traffic": (tr["dram_bytes_per_item"] * kd["items_per_launch"]) if tr else None}
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -830,7 +843,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-                "config": config_of(args, wl), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "config": config_of(args, wl), "roofline": roof, "roofline_sieve": roof_sieve,
+                "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(),
                 "phases": dict(phase, build_mpts=n / phase["build_ms"] / 1e3,
                                insert_mpts=m / phase["insert_ms"] / 1e3,

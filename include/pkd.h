@@ -228,7 +228,12 @@ int pkd_set_option(const char* name, int64_t value);
  * of timed launches, their summed duration in ms and the points (items)
  * they processed; pkd_kernel_timing(1) enables and clears the counters.
  * The name "launches" reports, in *launches, every kernel launch the
- * library made since the last pkd_kernel_timing call (timed or not). */
+ * library made since the last pkd_kernel_timing call (timed or not).
+ * Families: "validate", "sample", "count" and "scatter" (sieve rounds of a
+ * build), "count_route" and "scatter_route" (sieve rounds that route an
+ * update batch; items not counted), "smem_build" (shared-memory base case,
+ * one CTA per subproblem), "smem_warp" (one warp per subproblem), "knn",
+ * "range_count", "range_report". */
 int pkd_kernel_timing(int enable);
 int pkd_kernel_stats(const char* name, uint64_t* launches, double* total_ms, uint64_t* items);
 

@@ -19,6 +19,8 @@
 // (smem_build.cuh).  When a skeleton root is a bucket (too few or identical
 // samples) the subproblem takes one exact level on its own points; when its
 // points are all identical it becomes one heavy leaf.
+#include <map>
+#include <mutex>
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -440,6 +442,21 @@ static void launch_smem_sorted2(const SmemArgs& a, uint32_t nblocks, size_t smb,
     set = (int)smb;
   }
   PKD_LAUNCH((k_smem_sorted<D, 2><<<nblocks, SS_THREADS, smb, s>>>(a)));
+}
+
+// A second stream of the current device, created on first use.
+static cudaStream_t aux_stream() {
+  static std::mutex mu;
+  static std::map<int, cudaStream_t> streams;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = streams.find(dev);
+  if (it != streams.end()) return it->second;
+  cudaStream_t st = nullptr;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  streams[dev] = st;
+  return st;
 }
 
 // Largest capacity of the presorted base case that lets two CTAs share an
@@ -1397,13 +1414,13 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
 
     // 3. finalize skeletons, count, scan, emit, scatter
     PKD_LAUNCH(k_finalize<<<(nbig + 127) / 128, 128, 0, s>>>(r));
-    PKD_DISPATCH_D(d, launch_count, r, tiles, s);
+    PKD_DISPATCH_D(d, launch_count, r, tiles, pts_big, "count", s);
     uint32_t* partial;
     const uint64_t nh = (uint64_t)tiles * NB;
     PKD_TRY(sc.get(&partial, (nh + SCAN_TILE - 1) / SCAN_TILE + 1));
     device_excl_scan(r.hist, r.hscan, nh, partial, s);
     PKD_LAUNCH(k_emit<<<(nbig + 63) / 64, 64, 0, s>>>(r, dctr + 4));
-    PKD_DISPATCH_D(d, launch_scatter, r, tiles, pts_big, s);
+    PKD_DISPATCH_D(d, launch_scatter, r, tiles, pts_big, "scatter", s);
     PKD_LAUNCH(k_copy_heavy<<<tiles, 256, 0, s>>>(r));
 
     // 4. the buckets, now in the destination buffer, are the next round
@@ -1441,6 +1458,24 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     KTimer kt;
     ktimer_begin(kt, "smem_build", cta_pts, s);
     if (knobs().base_kernel == 0) {
+      // the one-CTA-per-SM segments run beside the two-CTA launch, on a
+      // second stream, so their long CTAs do not form a tail of their own
+      cudaStream_t sb = s;
+      cudaEvent_t fork = nullptr, join = nullptr;
+      if (nbase > 0 && nbbase > 0) {
+        sb = aux_stream();
+        PKD_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        PKD_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+        PKD_CUDA(cudaEventRecord(fork, s));
+        PKD_CUDA(cudaStreamWaitEvent(sb, fork, 0));
+      }
+      if (nbbase > 0) {
+        SmemArgs s1 = sa;
+        s1.segs = bbase_list;
+        s1.nsegs = dctr + 25;
+        s1.cap = (int)cap;
+        PKD_DISPATCH_D(d, launch_smem_sorted, s1, nbbase, sorted_layout((int)cap, d).total, sb);
+      }
       if (nbase > 0) {
         SmemArgs s2 = sa;
         s2.segs = base_list;
@@ -1448,12 +1483,11 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
         s2.cap = (int)cap2;
         PKD_DISPATCH_D(d, launch_smem_sorted2, s2, nbase, sorted_layout((int)cap2, d).total, s);
       }
-      if (nbbase > 0) {
-        SmemArgs s1 = sa;
-        s1.segs = bbase_list;
-        s1.nsegs = dctr + 25;
-        s1.cap = (int)cap;
-        PKD_DISPATCH_D(d, launch_smem_sorted, s1, nbbase, sorted_layout((int)cap, d).total, s);
+      if (join) {
+        PKD_CUDA(cudaEventRecord(join, sb));
+        PKD_CUDA(cudaStreamWaitEvent(s, join, 0));
+        cudaEventDestroy(fork);
+        cudaEventDestroy(join);
       }
     } else {
       sa.segs = base_list;

@@ -415,16 +415,17 @@ static size_t scatter_smem(int HN, int NB, int D, int tile) {
 }
 
 template <int D>
-static void launch_count_tiles(const RoundArgs& r, uint32_t tiles, cudaStream_t s) {
+static void launch_count_tiles(const RoundArgs& r, uint32_t tiles, uint64_t pts, const char* fam, cudaStream_t s) {
   const size_t sm = (size_t)r.HN * 8 + (size_t)r.NB * 4;
   KTimer kt;
-  ktimer_begin(kt, "count", 0, s);
+  ktimer_begin(kt, fam, pts, s);
   PKD_LAUNCH(k_count<D><<<tiles, SIEVE_THREADS, sm, s>>>(r));
   ktimer_end(kt);
 }
 
 template <int D>
-static void launch_scatter_tiles(const RoundArgs& r, uint32_t tiles, uint64_t pts, cudaStream_t s) {
+static void launch_scatter_tiles(const RoundArgs& r, uint32_t tiles, uint64_t pts, const char* fam,
+                                 cudaStream_t s) {
   const size_t sm = scatter_smem(r.HN, r.NB, D, r.TILE);
   static bool set = false;
   if (!set) {
@@ -432,7 +433,7 @@ static void launch_scatter_tiles(const RoundArgs& r, uint32_t tiles, uint64_t pt
     set = true;
   }
   KTimer kt;
-  ktimer_begin(kt, "scatter", pts, s);
+  ktimer_begin(kt, fam, pts, s);
   PKD_LAUNCH(k_scatter<D><<<tiles, SIEVE_THREADS, sm, s>>>(r));
   ktimer_end(kt);
 }

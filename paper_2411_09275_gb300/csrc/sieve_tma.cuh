@@ -569,11 +569,12 @@ static size_t stream_smem_limit() {
 // a point; the streaming kernels only).
 static inline bool record_buckets(int NB) { return NB <= 256 && knobs().sieve_kernel == 0; }
 
+// `fam` names the kernel timer family, `pts` the points of the launch.
 template <int D>
-static void launch_count(const RoundArgs& r, uint32_t tiles, cudaStream_t s) {
+static void launch_count(const RoundArgs& r, uint32_t tiles, uint64_t pts, const char* fam, cudaStream_t s) {
   const size_t smb = count_stream_smem<D>(r);
   if (knobs().sieve_kernel == 1 || smb > stream_smem_limit() || r.TILE > STM_CONSUMERS * STM_PER) {
-    launch_count_tiles<D>(r, tiles, s);
+    launch_count_tiles<D>(r, tiles, pts, fam, s);
     return;
   }
   static size_t set = 0;
@@ -583,16 +584,16 @@ static void launch_count(const RoundArgs& r, uint32_t tiles, cudaStream_t s) {
   }
   const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)stream_sm_count() * 2);
   KTimer kt;
-  ktimer_begin(kt, "count", 0, s);
+  ktimer_begin(kt, fam, pts, s);
   PKD_LAUNCH(k_count_stream<D><<<grid, STM_THREADS, smb, s>>>(r, tiles));
   ktimer_end(kt);
 }
 
 template <int D>
-static void launch_scatter(const RoundArgs& r, uint32_t tiles, uint64_t pts, cudaStream_t s) {
+static void launch_scatter(const RoundArgs& r, uint32_t tiles, uint64_t pts, const char* fam, cudaStream_t s) {
   const size_t smb = scatter_stream_smem<D>(r);
   if (knobs().sieve_kernel == 1 || smb > stream_smem_limit() || r.TILE > STM_CONSUMERS * STM_PER) {
-    launch_scatter_tiles<D>(r, tiles, pts, s);
+    launch_scatter_tiles<D>(r, tiles, pts, fam, s);
     return;
   }
   static size_t set = 0;
@@ -602,7 +603,7 @@ static void launch_scatter(const RoundArgs& r, uint32_t tiles, uint64_t pts, cud
   }
   const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)stream_sm_count() * 2);
   KTimer kt;
-  ktimer_begin(kt, "scatter", pts, s);
+  ktimer_begin(kt, fam, pts, s);
   PKD_LAUNCH(k_scatter_stream<D><<<grid, STM_THREADS, smb, s>>>(r, tiles));
   ktimer_end(kt);
 }

@@ -1229,10 +1229,10 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
       ra.hscan = hscan;
       if (record_buckets(NB)) PKD_TRY(sc.get(&ra.bkt, (size_t)tiles * TILE));
       PKD_LAUNCH(k_big_prefix<<<1, 1024, 0, s>>>(cur_big, R.d_n + 1, (uint32_t)TILE, tile0, excl));
-      PKD_DISPATCH_D(d, launch_count, ra, tiles, s);
+      PKD_DISPATCH_D(d, launch_count, ra, tiles, (uint64_t)0, "count_route", s);
       device_excl_scan(hist, hscan, nh, partial, s);
       PKD_LAUNCH(k_bucket_ranges<<<(nbig + 127) / 128, 128, 0, s>>>(ra, R.bstart, R.blen, nbk));
-      PKD_DISPATCH_D(d, launch_scatter, ra, tiles, (uint64_t)0, s);
+      PKD_DISPATCH_D(d, launch_scatter, ra, tiles, (uint64_t)0, "scatter_route", s);
       PKD_LAUNCH(k_copy_round<<<tiles, 256, 0, s>>>(ra, F));
     }
     if (nsmall) {

@@ -475,8 +475,8 @@ __global__ void __launch_bounds__(STM_THREADS) k_scatter_stream(RoundArgs r, uin
     consumers_sync();
     // the stage is no longer read: let the producer refill it
     if (tid == 0) mbar_arrive(&empty[stg]);
-    // rank within the tile's buckets: one shared atomic per bucket and warp
-    // (the order inside a bucket is immaterial: later steps see only sets)
+    // rank within the tile's buckets: one shared atomic per point (the order
+    // inside a bucket is immaterial: later steps see only sets)
 #pragma unroll
     for (int u = 0; u < STM_PER; ++u) rk[u] = bk[u] >= 0 ? (int)atomicAdd(&cur[bk[u]], 1u) : 0;
     consumers_sync();

@@ -14,7 +14,9 @@
 // The skeleton of the tile's segment is expanded into a complete heap of
 // lambda levels (a node below a bucket always goes left) plus a table from
 // the 2^lambda level-lambda positions to bucket numbers, so a walk is lambda
-// branch-free steps.
+// branch-free steps.  The count walks every point once and, with at most
+// 256 buckets, records its bucket in one byte; the scatter's producer then
+// copies those bytes with the tile, so the scatter does not walk again.
 #pragma once
 
 #include "sieve.cuh"

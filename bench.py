@@ -103,6 +103,23 @@ def dram_traffic():
     return j.get("kernels", {})
 
 
+def sieve_rooflines(kernels: dict, peak: float, traffic: dict) -> dict:
+    """Roofline of every HBM-bound sieve kernel of the build that was timed
+    with a point count: achieved = algorithmic bytes per launch / average
+    launch time, against `peak`; traffic = measured DRAM bytes per point
+    (when the capture is still valid) x points per launch."""
+    out = {}
+    for name in ("scatter", "count", "sample", "validate"):
+        kd = kernels.get(name)
+        if not kd or not kd["achieved_gbs"]:
+            continue
+        tr = traffic.get(name)
+        out[name] = {"bound": "hbm", "achieved": kd["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": kd["achieved_gbs"] / peak,
+                     "traffic": (tr["dram_bytes_per_item"] * kd["items_per_launch"]) if tr else None}
+    return out
+
+
 class Clocks:
     """nvidia-smi sampled every 200 ms while the timed region runs."""
 
@@ -747,15 +764,7 @@ def main():
                 "unit": "GB/s", "frac": (kd["achieved_gbs"] / peak) if kd["achieved_gbs"] else None,
                 "traffic": traffic, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
     # the build's HBM-bound sieve kernels, each against the same peak
-    roof_sieve = {}
-    for name in ("scatter", "count", "sample", "validate"):
-        kd = kernels.get(name)
-        if not kd or not kd["achieved_gbs"]:
-            continue
-        tr = dram_traffic().get(name)
-        roof_sieve[name] = {"bound": "hbm", "achieved": kd["achieved_gbs"], "peak": peak, "unit": "GB/s",
-                            "frac": kd["achieved_gbs"] / peak,
-                            "traffic": (tr["dram_bytes_per_item"] * kd["items_per_launch"]) if tr else None}
+    roof_sieve = sieve_rooflines(kernels, peak, dram_traffic())
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None

@@ -94,3 +94,17 @@ def test_dram_traffic_is_dropped_when_a_kernel_source_changed(tmp_path, monkeypa
     assert bench.dram_traffic()["scatter"]["dram_bytes_per_item"] == 25.0
     (tmp_path / "k.cu").write_text("kernel v2")
     assert bench.dram_traffic() == {}
+
+
+def test_sieve_rooflines():
+    import bench
+
+    kernels = {"scatter": {"achieved_gbs": 3400.0, "items_per_launch": 1e8},
+               "count": {"achieved_gbs": None, "items_per_launch": 0.0},
+               "smem_build": {"achieved_gbs": 340.0, "items_per_launch": 1e8},
+               "sample": {"achieved_gbs": 1000.0, "items_per_launch": 5e7}}
+    traffic = {"scatter": {"dram_bytes_per_item": 33.0}}
+    r = bench.sieve_rooflines(kernels, 6800.0, traffic)
+    assert set(r) == {"scatter", "sample"}          # count had no point count; smem_build is not a sieve kernel
+    assert r["scatter"]["frac"] == 0.5 and r["scatter"]["traffic"] == 33.0 * 1e8
+    assert r["sample"]["traffic"] is None and r["sample"]["unit"] == "GB/s"

@@ -86,7 +86,7 @@ def lib():
         L.orc_insert.restype = C.c_int
         L.orc_insert.argtypes = [vp, vp, vp, C.c_uint64]
         L.orc_delete.restype = C.c_int
-        L.orc_delete.argtypes = [vp, vp, vp, C.c_uint64, P(C.c_uint64)]
+        L.orc_delete.argtypes = [vp, vp, C.c_uint64, P(C.c_uint64)]
         L.orc_free.argtypes = [vp]
         L.orc_size.restype = C.c_uint64
         L.orc_size.argtypes = [vp]
@@ -167,11 +167,12 @@ class OracleTree:
         if r:
             raise OracleError(f"orc_insert failed: {r}")
 
-    def delete(self, coords, ids) -> int:
-        c = _coords(coords, self.params.d)
-        i = np.ascontiguousarray(ids, dtype=np.uint32)
+    def delete(self, ids) -> int:
+        """Delete the points named by ids (Sec. 4.2 with the id as the key);
+        unknown and repeated ids are skipped.  Returns the points removed."""
+        i = np.ascontiguousarray(ids, dtype=np.uint32).reshape(-1)
         nd = C.c_uint64(0)
-        r = lib().orc_delete(self._h, _ptr(c), _ptr(i), c.shape[0], C.byref(nd))
+        r = lib().orc_delete(self._h, _ptr(i), i.shape[0], C.byref(nd))
         if r:
             raise OracleError(f"orc_delete failed: {r}")
         return int(nd.value)

@@ -27,10 +27,20 @@
  *   R4 leaves: |P| <= phi -> leaf; all points identical -> one (heavy) leaf
  *      of any size holding every id (App. C keeps coordinate + count).
  *   R5 balance: 0.5 - alpha <= L/N <= 0.5 + alpha, inclusive, in integers.
- *      A node whose subtree receives no updated point is left as it is.
+ *      The test is applied to the nodes an update reaches: Sec. 4.1 rebuilds
+ *      a node that the insertion makes unbalanced, so a node whose
+ *      subtree receives no updated point is left as it is, even when it was
+ *      already unbalanced (sampled splits can leave it so; rebuilding it at
+ *      its own depth would draw a new sample and could change it).
  *      A node whose size drops to 0 becomes an empty leaf.
- *   R6 deletion key: a stored point is removed when its (coordinates, id)
- *      equals a batch entry; entries that match nothing are skipped.
+ *   R6 deletion key: the id.  Sec. 4.2 deletes points; ids name them.  An
+ *      id is looked up among the stored points for its coordinates, which
+ *      are then sieved as Sec. 4.2 sieves a point; ids that name no stored
+ *      point (never inserted, or deleted already) and repeats are skipped,
+ *      as round 1 discards points that are not in the tree.
+ *   R9 ids name points: every id in a tree is unique and not 0xFFFFFFFF (the
+ *      k-NN padding value).  A build with a repeated id, or an insert whose
+ *      batch repeats an id or names a stored point, is rejected whole.
  */
 #include "oracle.h"
 
@@ -372,6 +382,43 @@ static opt* load_points(const int32_t* coords, const uint32_t* ids, uint64_t n, 
   return P;
 }
 
+/* Ids name points (reading R9).  Sorting a copy is the plain way to see a
+ * repeat: equal ids end up next to each other. */
+static int cmp_u32_asc(const void* a, const void* b) {
+  uint32_t x = *(const uint32_t*)a, y = *(const uint32_t*)b;
+  return (x > y) - (x < y);
+}
+
+static uint32_t* sorted_ids(const opt* P, uint64_t n) {
+  uint32_t* v = (uint32_t*)xmalloc(n * sizeof(uint32_t));
+  for (uint64_t i = 0; i < n; ++i) v[i] = P[i].id;
+  qsort(v, n, sizeof(uint32_t), cmp_u32_asc);
+  return v;
+}
+
+/* 1 when some id repeats or is 0xFFFFFFFF. */
+static int ids_bad(const opt* P, uint64_t n) {
+  if (n == 0) return 0;
+  uint32_t* v = sorted_ids(P, n);
+  int bad = v[n - 1] == 0xFFFFFFFFu;
+  for (uint64_t i = 1; i < n && !bad; ++i) bad = v[i] == v[i - 1];
+  free(v);
+  return bad;
+}
+
+/* 1 when x is in the ascending array v[0..n). */
+static int id_in(const uint32_t* v, uint64_t n, uint32_t x) {
+  uint64_t lo = 0, hi = n;
+  while (lo < hi) {
+    uint64_t mid = lo + (hi - lo) / 2;
+    if (v[mid] < x)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo < n && v[lo] == x;
+}
+
 orc_tree* orc_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const orc_params* p,
                     int* err) {
   return orc_build_at_depth(coords, ids, n, p, 0, err);
@@ -386,6 +433,10 @@ orc_tree* orc_build_at_depth(const int32_t* coords, const uint32_t* ids, uint64_
     return NULL;
   }
   opt* P = load_points(coords, ids, n, p->d, 0, &e);
+  if (e == ORC_OK && ids_bad(P, n)) {
+    free(P);
+    e = ORC_EINVAL;
+  }
   if (e != ORC_OK) {
     if (err) *err = e;
     return NULL;
@@ -518,6 +569,20 @@ int orc_insert(orc_tree* t, const int32_t* coords, const uint32_t* ids, uint64_t
   int e;
   opt* P = load_points(coords, ids, m, t->p.d, 0, &e);
   if (e != ORC_OK) return e;
+  /* reading R9: the batch is rejected whole, before any change */
+  int bad = ids_bad(P, m);
+  if (!bad && m) {
+    ovec all = {0};
+    collect(t->root, &all);
+    uint32_t* live = sorted_ids(all.a, all.n);
+    for (uint64_t i = 0; i < m && !bad; ++i) bad = id_in(live, all.n, P[i].id);
+    free(live);
+    free(all.a);
+  }
+  if (bad) {
+    free(P);
+    return ORC_EINVAL;
+  }
   t->root = batch_insert(&t->p, t->root, P, m, 0);
   free(P);
   return ORC_OK;
@@ -600,24 +665,39 @@ static onode* delete_rec(const orc_params* p, onode* u, uint32_t t) {
   return v;
 }
 
-int orc_delete(orc_tree* t, const int32_t* coords, const uint32_t* ids, uint64_t m,
-               uint64_t* n_deleted) {
-  if (!t || (m && (!coords || !ids))) return ORC_EINVAL;
+static int cmp_opt_id(const void* a, const void* b) {
+  uint32_t x = ((const opt*)a)->id, y = ((const opt*)b)->id;
+  return (x > y) - (x < y);
+}
+
+int orc_delete(orc_tree* t, const uint32_t* ids, uint64_t m, uint64_t* n_deleted) {
+  if (!t || (m && !ids)) return ORC_EINVAL;
   int d = t->p.d;
+  /* reading R6: the stored points sorted by id give each id's coordinates */
+  ovec all = {0};
+  collect(t->root, &all);
+  if (all.n) qsort(all.a, all.n, sizeof(opt), cmp_opt_id);
+  /* distinct batch ids */
+  uint32_t* q = (uint32_t*)xmalloc((m ? m : 1) * sizeof(uint32_t));
+  if (m) memcpy(q, ids, m * sizeof(uint32_t));
+  qsort(q, m, sizeof(uint32_t), cmp_u32_asc);
   for (uint64_t i = 0; i < m; ++i) {
-    opt q;
-    q.id = ids[i];
-    memset(q.x, 0, sizeof(q.x));
-    int outside = 0;
-    for (int j = 0; j < d; ++j) {
-      q.x[j] = coords[i * d + j];
-      if (q.x[j] < 0 || (int64_t)q.x[j] >= ORC_COORD_LIMIT) outside = 1;
+    if (i > 0 && q[i] == q[i - 1]) continue; /* a repeat */
+    uint64_t lo = 0, hi = all.n;
+    while (lo < hi) {
+      uint64_t mid = lo + (hi - lo) / 2;
+      if (all.a[mid].id < q[i])
+        lo = mid + 1;
+      else
+        hi = mid;
     }
-    if (!outside) mark_point(t->root, &q, d);
+    if (lo < all.n && all.a[lo].id == q[i]) mark_point(t->root, &all.a[lo], d); /* round 1 */
   }
+  free(q);
+  free(all.a);
   uint64_t k = count_dead(t->root);
   if (n_deleted) *n_deleted = k;
-  t->root = delete_rec(&t->p, t->root, 0);
+  t->root = delete_rec(&t->p, t->root, 0); /* round 2 */
   return ORC_OK;
 }
 

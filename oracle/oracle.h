@@ -39,19 +39,23 @@ typedef struct {
 
 typedef struct orc_tree orc_tree;
 
-/* Alg. 1: build over coords[n][d] with ids (NULL -> 0..n-1).  NULL on error. */
+/* Alg. 1: build over coords[n][d] with ids (NULL -> 0..n-1).  NULL on error
+ * (ORC_EINVAL also when two points share an id or an id is 0xFFFFFFFF, the
+ * k-NN padding value: ids name the points, so they are unique). */
 orc_tree* orc_build(const int32_t* coords, const uint32_t* ids, uint64_t n,
                     const orc_params* p, int* err);
 /* The same build for a subtree whose root sits at tree depth `depth` (the
  * depth salts the sample hash); the rebuilds of Alg. 2 use it. */
 orc_tree* orc_build_at_depth(const int32_t* coords, const uint32_t* ids, uint64_t n,
                              const orc_params* p, uint32_t depth, int* err);
-/* Alg. 2: insert m points.  Returns ORC_OK or ORC_EINVAL (tree unchanged). */
+/* Alg. 2: insert m points.  Returns ORC_OK, or ORC_EINVAL with the tree
+ * unchanged when a coordinate is out of range, an id is 0xFFFFFFFF, an id
+ * names a point already in the tree, or two batch points share an id. */
 int orc_insert(orc_tree* t, const int32_t* coords, const uint32_t* ids, uint64_t m);
-/* Sec. 4.2: delete every stored point whose (coords, id) equals a batch entry;
- * entries matching nothing are skipped.  *n_deleted = records removed. */
-int orc_delete(orc_tree* t, const int32_t* coords, const uint32_t* ids, uint64_t m,
-               uint64_t* n_deleted);
+/* Sec. 4.2: delete the points named by ids.  Each id is looked up among the
+ * stored points to find its coordinates; ids that name no stored point and
+ * repeats of an id are skipped.  *n_deleted = points removed. */
+int orc_delete(orc_tree* t, const uint32_t* ids, uint64_t m, uint64_t* n_deleted);
 void orc_free(orc_tree* t);
 
 uint64_t orc_size(const orc_tree* t);

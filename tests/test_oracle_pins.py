@@ -260,12 +260,11 @@ def test_updates_set_algebra_and_invariants(kind):
     allX, allI = np.concatenate([X, Y]), np.concatenate([ids, yid])
     assert _multiset(*t.points()) == _multiset(allI, allX)
     U.check_invariants(t.export(), allX, allI, p.phi, built_fresh=False)
-    # delete: some present points, repeats, and absent ones (wrong coords / unknown id)
+    # delete: some present points, repeats, and ids that name no point
     sel = I.sample_indices(2000, n + m, 93)
-    dc, di = allX[sel].copy(), allI[sel].copy()
-    dc = np.concatenate([dc, dc[:50], dc[50:80] + 1, allX[:10]])
+    di = allI[sel].copy()
     di = np.concatenate([di, di[:50], di[50:80], np.full(10, 10 ** 9, np.uint32)])
-    nd = t.delete(dc, di)
+    nd = t.delete(di)
     keep = np.ones(n + m, bool)
     keep[sel] = False
     assert nd == 2000 and t.size == n + m - 2000
@@ -296,7 +295,7 @@ def test_exact_median_updates_keep_every_node_balanced():
         AX, AI = np.concatenate(live_X), np.concatenate(live_I)
         # skewed delete: the largest x0 first
         sel = np.argsort(-AX[:, 0])[:500]
-        assert t.delete(AX[sel], AI[sel]) == 500
+        assert t.delete(AI[sel]) == 500
         keep = np.ones(len(AI), bool)
         keep[sel] = False
         live_X, live_I = [AX[keep]], [AI[keep]]
@@ -357,10 +356,10 @@ def test_insert_into_leaf_root_and_delete_to_empty():
     fresh = O.OracleTree(np.concatenate([X, Y]), np.arange(510, dtype=np.uint32), p)
     U.assert_exports_equal(t.export(), fresh.export())  # leaf root: Build(T u P)
     allX = np.concatenate([X, Y])
-    assert t.delete(allX, np.arange(510, dtype=np.uint32)) == 510
+    assert t.delete(np.arange(510, dtype=np.uint32)) == 510
     e = t.export()
     assert list(e["dims"]) == [0xFF] and t.size == 0
-    assert t.delete(allX[:5], np.arange(5, dtype=np.uint32)) == 0
+    assert t.delete(np.arange(5, dtype=np.uint32)) == 0
 
 
 def test_invalid_inputs_rejected():
@@ -437,8 +436,7 @@ def test_updates_rederived_node_by_node(kind, alpha):
         sel = live[np.argsort([xyz[int(i)][1] for i in live])[:500]]  # the 500 lowest x1
         sel = np.concatenate([sel, rng.choice(live, 50, replace=False)])
         want = U.expect_delete(before, set(int(i) for i in sel), P, build_at, O.balanced)
-        c = np.array([xyz[int(i)] for i in sel], np.int32)
-        t.delete(c, sel)
+        t.delete(sel)
         U.assert_exports_equal(t.export(), U.unparse(want))
 
 
@@ -476,3 +474,116 @@ def test_range_report_hand_example_and_count_consistency():
     rep = t.range_report(lo, hi)
     assert [len(r) for r in rep] == list(t.range_count(lo, hi).astype(int))
     t.close()
+
+
+# --------------------------------------------------------------------------
+# Reading R5: a node no update reaches is not re-tested
+# --------------------------------------------------------------------------
+
+def _pre_order(e):
+    """(children, depth, end of subtree) per pre-order node index."""
+    dims = e["dims"]
+    n = len(dims)
+    kids, stack = {}, []
+    depth = np.zeros(n, int)
+    for i in range(n):
+        if stack:
+            p = stack[-1]
+            kids.setdefault(p, []).append(i)
+            depth[i] = depth[p] + 1
+            if len(kids[p]) == 2:
+                stack.pop()
+        if dims[i] != 0xFF:
+            stack.append(i)
+    end = np.zeros(n, int)
+    for i in range(n - 1, -1, -1):
+        end[i] = i + 1 if dims[i] == 0xFF else end[kids[i][1]]
+    return kids, depth, end
+
+
+def test_untouched_unbalanced_node_is_kept_r5():
+    # 60 points on a line, rate-1/2 samples, lambda = 2, phi = 2, alpha = 3/10.
+    # The node at pre-order 14 (depth 3) was split on its ancestor's sample at
+    # 139, below which only one of its ten points lies: 2*10*1 = 20 is below
+    # (10 - 6)*10 = 40, so it is already outside the alpha band after the
+    # build.  Inserting one point at the far right end (x = 999, right of the
+    # root's splitter) reaches none of that subtree: Sec. 4.1 rebuilds only a
+    # node that becomes unbalanced after insertion, so the subtree must come
+    # out unchanged, although Build on its ten points at depth 3 (what
+    # re-testing every node of Alg. 2's skeletons would do) draws a new
+    # sample and gives a different subtree.
+    X = np.random.default_rng(3).integers(0, 1000, size=(60, 1)).astype(np.int32)
+    ids = np.arange(60, dtype=np.uint32)
+    P = O.Params(d=1, phi=2, lam=2, sigma_log2=1, sigma_os=1, alpha_num=3, alpha_den=10, seed=3)
+    t = O.OracleTree(X, ids, P)
+    e = t.export()
+    kids, depth, end = _pre_order(e)
+    u = 14
+    assert e["dims"][u] == 0 and depth[u] == 3 and int(e["splits"][u]) == 139
+    assert int(e["sizes"][u]) == 10 and int(e["sizes"][kids[u][0]]) == 1
+    assert not O.balanced(1, 10, 3, 10)
+    # u's ten points: the leaves of its pre-order span
+    leaf_no = np.cumsum(e["dims"] == 0xFF) - 1
+    offs = e["leaf_offsets"].astype(int)
+    uid = np.concatenate([e["leaf_ids"][offs[leaf_no[i]]:offs[leaf_no[i] + 1]]
+                          for i in range(u, end[u]) if e["dims"][i] == 0xFF])
+    assert sorted(X[uid, 0].tolist()) == [113, 139, 159, 172, 179, 181, 190, 236, 244, 254]
+    assert 999 >= int(e["splits"][0]) and e["dims"][0] == 0  # the new point goes right at the root
+    span = {k: e[k][u:end[u]].copy() for k in ("dims", "splits", "sizes")}
+    t.insert(np.array([[999]], np.int32), np.array([60], np.uint32))
+    e2 = t.export()
+    for k in span:  # u lies in the root's left subtree: same pre-order positions
+        assert np.array_equal(e2[k][u:end[u]], span[k]), k
+    alt = O.OracleTree(X[uid], uid, P, depth=3).export()
+    assert not (len(alt["dims"]) == len(span["dims"])
+                and all(np.array_equal(alt[k], span[k]) for k in span))
+
+
+# --------------------------------------------------------------------------
+# Reading R9 (ids name points) and R6 (delete by id)
+# --------------------------------------------------------------------------
+
+def test_ids_are_unique_and_insert_rejects_whole_batches():
+    d = 2
+    p = O.Params(d=d, phi=4, lam=2, sigma_log2=1, sigma_os=2)
+    X = I.uniform(300, d, 171)
+    with pytest.raises(O.OracleError):  # a repeated id in a build
+        O.OracleTree(X, np.r_[np.arange(299), [5]].astype(np.uint32), p)
+    with pytest.raises(O.OracleError):  # the k-NN padding id
+        O.OracleTree(X, np.r_[np.arange(299), [0xFFFFFFFF]].astype(np.uint32), p)
+    t = O.OracleTree(X, np.arange(300, dtype=np.uint32), p)
+    before = t.export()
+    Y = I.uniform(20, d, 172)
+    for bad in (np.r_[np.arange(300, 319), [7]],        # 7 is stored
+                np.r_[np.arange(300, 319), [300]],      # repeated in the batch
+                np.r_[np.arange(300, 319), [0xFFFFFFFF]]):
+        with pytest.raises(O.OracleError):
+            t.insert(Y, bad.astype(np.uint32))
+        U.assert_exports_equal(t.export(), before)     # rejected whole
+    t.insert(Y, np.arange(300, 320, dtype=np.uint32))
+    assert t.size == 320
+
+
+def test_delete_by_id_skips_unknown_dead_and_repeated_ids():
+    d = 3
+    p = O.Params(d=d, phi=4, lam=2, sigma_log2=1, sigma_os=2)
+    X = I.uniform(500, d, 181)
+    ids = (np.arange(500, dtype=np.uint32) * 7 + 3)  # sparse labels
+    t = O.OracleTree(X, ids, p)
+    # 40 stored ids, each twice, plus labels that name nothing
+    sel = ids[::12][:40]
+    batch = np.r_[sel, sel[::-1], [0, 1, 2, 4, 10 ** 9]].astype(np.uint32)
+    assert t.delete(batch) == 40 and t.size == 460
+    got_ids, got_x = t.points()
+    keep = ~np.isin(ids, sel)
+    assert sorted(zip(got_ids.tolist(), map(tuple, got_x.tolist()))) == \
+        sorted(zip(ids[keep].tolist(), map(tuple, X[keep].tolist())))
+    # deleted ids are gone: deleting them again removes nothing
+    assert t.delete(sel) == 0
+    # a deleted id may be inserted again, with new coordinates
+    Y = I.uniform(3, d, 182)
+    t.insert(Y, sel[:3])
+    assert t.size == 463
+    gi, gx = t.points()
+    assert {int(i): tuple(x) for i, x in zip(gi, gx.tolist())}[int(sel[1])] == tuple(Y[1].tolist())
+    assert t.delete(sel[:3]) == 3

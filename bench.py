@@ -222,12 +222,11 @@ def cpu_oracle_step(wl: dict, scale: int = 100):
     X = I.points(wl["kind"], n, d, I.SEED_DATA)
     Y = I.points(wl["kind"], m, d, I.SEED_INSERT)
     yid = np.arange(n, n + m, dtype=np.uint32)
-    sel = I.sample_indices(m, n + m, I.SEED_DELETE)
-    allX = np.concatenate([X, Y])
+    sel = I.sample_indices(m, n + m, I.SEED_DELETE).astype(np.uint32)
     t0 = time.perf_counter()
     t = O.OracleTree(X, None, O.Params(d=d))
     t.insert(Y, yid)
-    t.delete(allX[sel], sel)
+    t.delete(sel)
     dt = time.perf_counter() - t0
     t.close()
     desc = f"oracle, 1 thread: build n={n} d={d} {wl['kind']} + insert {m} + delete {m} (1/{scale} of the workload)"

@@ -69,7 +69,8 @@ def algo_bytes(kernel: str, d: int) -> float | None:
     point moves 2(4d+4); the count reads the coordinates (4d); sampling and
     the range check read one 4-byte word."""
     return {"scatter": 2 * (4 * d + 4), "smem_build": 2 * (4 * d + 4), "smem_warp": 2 * (4 * d + 4),
-            "count": 4 * d, "sample": 4, "validate": 4}.get(kernel)
+            "count": 4 * d, "sample": 4, "validate": 4,
+            "scatter_route": 2 * (4 * d + 4), "count_route": 4 * d}.get(kernel)
 
 
 TIMED_KERNELS = ["smem_build", "smem_warp", "scatter", "count", "sample", "validate", "scatter_route", "count_route"]
@@ -117,6 +118,37 @@ def sieve_rooflines(kernels: dict, peak: float, traffic: dict) -> dict:
         out[name] = {"bound": "hbm", "achieved": kd["achieved_gbs"], "peak": peak, "unit": "GB/s",
                      "frac": kd["achieved_gbs"] / peak,
                      "traffic": (tr["dram_bytes_per_item"] * kd["items_per_launch"]) if tr else None}
+    return out
+
+
+def kernel_table(kstats: dict, d: int, steps: int) -> dict:
+    """Per kernel family: launches, ms per step, items per launch and the
+    achieved GB/s of its algorithmic bytes (when it has a per-item figure)."""
+    kernels = {}
+    for name, (cnt, ms, items) in kstats.items():
+        b = algo_bytes(name, d)
+        if cnt == 0 or ms <= 0:
+            continue
+        gbs = (b * items / (ms / 1e3) / 1e9) if (b and items) else None
+        kernels[name] = {"launches": cnt, "ms_per_step": ms / steps, "items_per_launch": items / cnt,
+                         "algo_bytes_per_item": b, "achieved_gbs": gbs}
+    return kernels
+
+
+def update_rooflines(kernels: dict, counts: dict, peak: float, d: int, steps: int) -> dict:
+    """Routing sieve of the batch updates against `peak` (count 4d B and
+    scatter 2(4d+4) B per routed point), plus the points the updates rebuilt
+    and the ids a delete looked up (4 + 4d B each), per step."""
+    out = {}
+    for name in ("scatter_route", "count_route"):
+        kd = kernels.get(name)
+        if kd and kd["achieved_gbs"]:
+            out[name] = {"bound": "hbm", "achieved": kd["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                         "frac": kd["achieved_gbs"] / peak, "points_per_step": kd["items_per_launch"] *
+                         kd["launches"] / steps}
+    for name, (cnt, _, items) in counts.items():
+        out[name + "_per_step"] = items / steps
+    out["delete_gather_bytes_per_id"] = 4 + 4 * d
     return out
 
 
@@ -205,11 +237,7 @@ def make_inputs(wl: dict, rank: int):
     Y = I.points(wl["kind"], m, d, I.SEED_INSERT + seed)
     yid = np.arange(n, n + m, dtype=np.uint32)
     sel = I.sample_indices(m, n + m, I.SEED_DELETE + seed)
-    in_x = sel < n
-    Z = np.empty((m, d), np.int32)
-    Z[in_x] = X[sel[in_x]]
-    Z[~in_x] = Y[sel[~in_x] - n]
-    return X, Y, yid, Z, sel.astype(np.uint32)
+    return X, Y, yid, sel.astype(np.uint32)
 
 
 def cpu_oracle_step(wl: dict, scale: int = 100):
@@ -233,6 +261,12 @@ def cpu_oracle_step(wl: dict, scale: int = 100):
     return n + 2 * m, dt, desc
 
 
+def sample_config(args, wl, scale: int = 100) -> dict:
+    """The workload's config with the scale the oracle legs actually run."""
+    return dict(config_of(args, wl), sample_scale=f"1/{scale}", n_run=wl["n"] // scale,
+                m_insert_run=max(wl["m"] // scale, 1), m_delete_run=max(wl["m"] // scale, 1))
+
+
 def run_reference(args, wl):
     ws, rank, _ = dist_info()
     if rank != 0:
@@ -248,8 +282,9 @@ def run_reference(args, wl):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpts/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic", "config": config_of(args, wl),
-            "cpu_baseline": {"value": v, "unit": "Mpts/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "data": "synthetic", "config": sample_config(args, wl),
+            "cpu_baseline": {"value": v, "unit": "Mpts/s", "cores": 1, "kind": "oracle", "sample": desc,
+                             "config": sample_config(args, wl)},
             "e2e": {"value": v, "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -410,7 +445,6 @@ def serve_requests(wl: dict, X: np.ndarray, dev):
         return int(np.exp(rng.uniform(np.log(lo), np.log(hi)))) // scale + 1
 
     alive = np.ones(n, bool)
-    chunks, starts = [], []  # inserted batches and their first ids
     nxt = n
     reqs = []
     t = 0.0
@@ -421,8 +455,6 @@ def serve_requests(wl: dict, X: np.ndarray, dev):
             m = logu(1e3, 1e6)
             Y = I.points(wl["kind"], m, d, 3100 + q)
             ids = np.arange(nxt, nxt + m, dtype=np.uint32)
-            chunks.append(Y)
-            starts.append(nxt)
             alive = np.concatenate([alive, np.ones(m, bool)])
             nxt += m
             reqs.append(("insert", t, Y, ids))
@@ -434,40 +466,28 @@ def serve_requests(wl: dict, X: np.ndarray, dev):
                 got = np.unique(np.concatenate([got, cand[alive[cand]]]))
             got = rng.permutation(got)[:m]
             alive[got] = False
-            Z = np.empty((m, d), np.int32)
-            old = got < n
-            Z[old] = X[got[old]]
-            if (~old).any():
-                gi = got[~old]
-                ci = np.searchsorted(np.asarray(starts), gi, side="right") - 1
-                for c in np.unique(ci):
-                    sel = ci == c
-                    Z[np.flatnonzero(~old)[sel]] = chunks[c][gi[sel] - starts[c]]
-            reqs.append(("delete", t, Z, got.astype(np.uint32)))
+            reqs.append(("delete", t, None, got.astype(np.uint32)))
         else:
             m = logu(1e3, 1e5)
             pick = rng.integers(0, n, size=m)
             reqs.append(("knn", t, X[pick], None))
     out = []
     for kind, t, C, ids in reqs:
-        tc = torch.from_numpy(np.ascontiguousarray(C)).to(dev)
+        tc = torch.from_numpy(np.ascontiguousarray(C)).to(dev) if C is not None else None
         ti = torch.from_numpy(ids.view(np.int32)).to(dev) if ids is not None else None
         out.append(serve.Request(kind, t, tc, ti, 10))
     return out
 
 
-def run_serve(args, wl):
-    """Serving loop on one resident tree: p50 / p99 latency and Mpts/s at a
-    request rate that loads the device to about wl['load'] of its capacity."""
+def serve_measure(wl, dev, rank, gpu_index):
+    """The serving workload on one resident tree: a back-to-back pass gives
+    the capacity, then the same stream arrives as a Poisson process at
+    wl['load'] of it.  Returns (latency summary, wall s, mean gap s, clocks)."""
     import torch
 
     from paper_2411_09275_gb300 import inputs as I
     from paper_2411_09275_gb300 import pkd, serve
 
-    ws, rank, local = dist_info()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    pkd.lib()
     n, d = wl["n"], wl["d"]
     X = I.points(wl["kind"], n, d, I.SEED_VARDEN + 1000 * rank)
     gX = torch.from_numpy(X).to(dev)
@@ -479,7 +499,6 @@ def run_serve(args, wl):
         torch.cuda.synchronize(dev)
         return t
 
-    # service capacity: the whole stream back to back
     tree = fresh_tree()
     s0 = time.perf_counter()
     serve.Server(tree, realtime=False).run(reqs)
@@ -489,20 +508,36 @@ def run_serve(args, wl):
     gap = busy / len(reqs) / wl["load"]  # mean inter-arrival time
     timed = [serve.Request(r.kind, r.arrival * gap, r.coords, r.ids, r.k) for r in reqs]
     tree = fresh_tree()
-    with Clocks(local) as clk:
+    with Clocks(gpu_index) as clk:
         s0 = time.perf_counter()
         res = serve.Server(tree).run(timed)
         torch.cuda.synchronize(dev)
         wall = time.perf_counter() - s0
     tree.close()
-    summ = serve.summarize(res, wall)
+    del gX
+    return serve.summarize(res, wall), wall, gap, clk, len(reqs)
+
+
+def run_serve(args, wl):
+    """Serving loop on one resident tree: p50 / p99 latency and Mpts/s at a
+    request rate that loads the device to about wl['load'] of its capacity."""
+    import torch
+
+    from paper_2411_09275_gb300 import pkd
+
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkd.lib()
+    n, d = wl["n"], wl["d"]
+    summ, wall, gap, clk, nreq = serve_measure(wl, dev, rank, local)
     if rank != 0:
         return 0
     line = {"metric": METRIC, "value": ws * summ["mpts_per_s"], "unit": "Mpts/s", "n_gpus": ws,
             "steps": 1, "warmup": 1, "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "d": d, "distribution": wl["kind"],
-                       "requests": len(reqs), "mix": "40% insert, 20% delete, 40% 10-NN",
+                       "requests": nreq, "mix": "40% insert, 20% delete, 40% 10-NN",
                        "sizes": "log-uniform: updates 1e3..1e6, queries 1e3..1e5 (scaled by 1e8/n)",
                        "arrivals": f"Poisson, mean gap {1e3 * gap:.3f} ms ({wl['load']:.0%} of measured capacity)",
                        "parallelism": f"independent server per GPU x{ws}"},
@@ -645,7 +680,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--varden", action="store_true", help="also time the varden-like variant")
+    ap.add_argument("--no-varden", action="store_true", help="skip the varden-like repetition of the step")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg (p50 / p99 latency)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if wl.get("full"):
@@ -680,12 +716,11 @@ def main():
     dev = torch.device("cuda", local)
     pkd.lib()
 
-    X, Y, yid, Z, zid = make_inputs(wl, rank)
+    X, Y, yid, zid = make_inputs(wl, rank)
     d = wl["d"]
     gX = torch.from_numpy(X).to(dev)
     gY = torch.from_numpy(Y).to(dev)
     gyid = torch.from_numpy(yid.view(np.int32)).to(dev)
-    gZ = torch.from_numpy(Z).to(dev)
     gzid = torch.from_numpy(zid.view(np.int32)).to(dev)
     params = pkd.Params(d=d)
     stream = torch.cuda.current_stream(dev)
@@ -698,7 +733,7 @@ def main():
         pkd.pkd_batch_insert(t, gY, gyid, stream)
         if ev is not None:
             ev[1].record(stream)
-        nd = pkd.pkd_batch_delete(t, gZ, gzid, stream)
+        nd = pkd.pkd_batch_delete(t, gzid, stream)
         if ev is not None:
             ev[2].record(stream)
         size = pkd.pkd_size(t)
@@ -709,8 +744,8 @@ def main():
         nd, size = step()
     assert nd == m and size == n, (nd, size)
 
-    # ---- device-timed region: inputs resident in HBM ----
-    pkd.pkd_kernel_timing(True)
+    # ---- device-timed region: inputs resident in HBM, kernel timers off ----
+    pkd.pkd_kernel_timing(False)  # clears the launch counter; no events inside the steps
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -731,7 +766,6 @@ def main():
         torch.cuda.synchronize(dev)
     elapsed_ms = barrier_max(e0.elapsed_time(e1), ws, dev)
     launches = pkd.pkd_kernel_stats("launches")[0]
-    kstats = {k: pkd.pkd_kernel_stats(k) for k in TIMED_KERNELS}
     phase = {"build_ms": 0.0, "insert_ms": 0.0, "delete_ms": 0.0}
     for k in range(args.steps):
         phase["build_ms"] += starts[k].elapsed_time(evs[k][0])
@@ -739,20 +773,22 @@ def main():
         phase["delete_ms"] += evs[k][1].elapsed_time(evs[k][2])
     for key in list(phase):
         phase[key] /= args.steps
+
+    # ---- per-kernel pass (outside the headline's timed region) ----
+    stat_steps = 2
+    pkd.pkd_kernel_timing(True)
+    for _ in range(stat_steps):
+        step()
+    torch.cuda.synchronize(dev)
+    kstats = {k: pkd.pkd_kernel_stats(k) for k in TIMED_KERNELS}
+    counts = {k: pkd.pkd_kernel_stats(k) for k in ("rebuilt_insert", "rebuilt_delete", "delete_gather")}
     pkd.pkd_kernel_timing(False)
 
     pts_step = n + 2 * m
     ms_per_step = elapsed_ms / args.steps
     value = ws * pts_step * args.steps / (elapsed_ms / 1e3) / 1e6
     peak, peak_src = measured_peaks()
-    kernels = {}
-    for name, (cnt, ms, items) in kstats.items():
-        b = algo_bytes(name, d)
-        if cnt == 0 or ms <= 0:
-            continue
-        gbs = (b * items / (ms / 1e3) / 1e9) if (b and items) else None
-        kernels[name] = {"launches": cnt, "ms_per_step": ms / args.steps, "items_per_launch": items / cnt,
-                         "algo_bytes_per_item": b, "achieved_gbs": gbs}
+    kernels = kernel_table(kstats, d, stat_steps)
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"]) if kernels else None
     roof = None
     if dom:
@@ -764,6 +800,8 @@ def main():
                 "traffic": traffic, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
     # the build's HBM-bound sieve kernels, each against the same peak
     roof_sieve = sieve_rooflines(kernels, peak, dram_traffic())
+    # the update batches' routing sieve, and what the updates rebuilt
+    roof_update = update_rooflines(kernels, counts, peak, d, stat_steps)
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -771,10 +809,9 @@ def main():
         hX = torch.from_numpy(X).pin_memory()
         hY = torch.from_numpy(Y).pin_memory()
         hyid = torch.from_numpy(yid.view(np.int32)).pin_memory()
-        hZ = torch.from_numpy(Z).pin_memory()
         hzid = torch.from_numpy(zid.view(np.int32)).pin_memory()
-        h2d = sum(t.numel() * t.element_size() for t in (hX, hY, hyid, hZ, hzid))
-        hs = (hX, hY, hyid, hZ, hzid)
+        h2d = sum(t.numel() * t.element_size() for t in (hX, hY, hyid, hzid))
+        hs = (hX, hY, hyid, hzid)
         # two device sets: step k+1's inputs travel on a copy stream while step
         # k runs its updates (every byte of every step is still copied inside
         # the timed region)
@@ -789,13 +826,13 @@ def main():
                 ready[k % 2].record(copy_stream)
 
         def e2e_step(k, last):
-            dX, dY, dyid, dZ, dzid = sets[k % 2]
+            dX, dY, dyid, dzid = sets[k % 2]
             if not last:  # the other set is free: step k-1 has finished
                 upload(k + 1)
             stream.wait_event(ready[k % 2])
             t = pkd.pkd_build(dX, None, params, stream)
             pkd.pkd_batch_insert(t, dY, dyid, stream)
-            nd = pkd.pkd_batch_delete(t, dZ, dzid, stream)  # n_deleted comes back to the host
+            nd = pkd.pkd_batch_delete(t, dzid, stream)  # n_deleted comes back to the host
             pkd.pkd_free(t)
             return nd
 
@@ -820,44 +857,68 @@ def main():
                "note": "inputs copied from pinned host memory every step; the next step's copy overlaps "
                        "this step on a second stream"}
 
-    # ---- varden-like variant (same sizes), reported beside the headline ----
+    # ---- varden-like variant of the same step (same sizes, timers off) ----
     varden = None
-    if args.varden:
+    if not args.no_varden:
         wv = dict(wl, kind="varden")
-        Xv, Yv, yv, Zv, zv = make_inputs(wv, rank)
+        Xv, Yv, yv, zv = make_inputs(wv, rank)
         gX.copy_(torch.from_numpy(Xv))
         gY.copy_(torch.from_numpy(Yv))
-        gZ.copy_(torch.from_numpy(Zv))
         gzid.copy_(torch.from_numpy(zv.view(np.int32)))
         step()
         torch.cuda.synchronize(dev)
+        vsteps = 3
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        evv = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(vsteps)]
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(vsteps)]
         a.record(stream)
-        step(ev)
+        for k in range(vsteps):
+            st[k].record(stream)
+            step(evv[k])
         b.record(stream)
         torch.cuda.synchronize(dev)
-        varden = {"ms_per_step": a.elapsed_time(b), "build_ms": a.elapsed_time(ev[0]),
-                  "insert_ms": ev[0].elapsed_time(ev[1]), "delete_ms": ev[1].elapsed_time(ev[2]),
-                  "value": pts_step / (a.elapsed_time(b) / 1e3) / 1e6}
+        vms = a.elapsed_time(b) / vsteps
+        varden = {"ms_per_step": vms, "steps": vsteps,
+                  "build_ms": sum(st[k].elapsed_time(evv[k][0]) for k in range(vsteps)) / vsteps,
+                  "insert_ms": sum(evv[k][0].elapsed_time(evv[k][1]) for k in range(vsteps)) / vsteps,
+                  "delete_ms": sum(evv[k][1].elapsed_time(evv[k][2]) for k in range(vsteps)) / vsteps,
+                  "value": pts_step / (vms / 1e3) / 1e6, "unit": "Mpts/s",
+                  "config": dict(config_of(args, wv), distribution="varden")}
+        del Xv, Yv
+
+    # ---- serving leg: the metric's p50 / p99 request latency ----
+    serving = None
+    if not args.no_serve:
+        sw = WORKLOADS["serve1e8_d3"]
+        summ, wall, gap, sclk, nreq = serve_measure(sw, dev, rank, gpu_index)
+        serving = {"p50_ms": summ["all"]["p50_ms"], "p99_ms": summ["all"]["p99_ms"],
+                   "value": summ["mpts_per_s"], "unit": "Mpts/s", "latency": summ, "wall_s": wall,
+                   "clocks": sclk.summary(),
+                   "config": {"workload": "serve1e8_d3", "n": sw["n"], "d": sw["d"], "distribution": sw["kind"],
+                              "requests": nreq, "mix": "40% insert, 20% delete, 40% 10-NN",
+                              "arrivals": f"Poisson, mean gap {1e3 * gap:.3f} ms "
+                                          f"({sw['load']:.0%} of measured capacity)"}}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         p, dt, desc = cpu_oracle_step(wl)
-        cpu = {"value": p / dt / 1e6, "unit": "Mpts/s", "cores": 1, "kind": "oracle", "sample": desc}
+        cpu = {"value": p / dt / 1e6, "unit": "Mpts/s", "cores": 1, "kind": "oracle", "sample": desc,
+               "config": sample_config(args, wl)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
                 "config": config_of(args, wl), "roofline": roof, "roofline_sieve": roof_sieve,
+                "roofline_update": roof_update, "kernel_stats": f"separate pass of {stat_steps} steps with "
+                "CUDA-event timers (the headline steps run with the timers off)",
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(),
                 "phases": dict(phase, build_mpts=n / phase["build_ms"] / 1e3,
                                insert_mpts=m / phase["insert_ms"] / 1e3,
                                delete_mpts=m / phase["delete_ms"] / 1e3),
-                "kernels": kernels, "varden": varden}
+                "kernels": kernels, "varden": varden, "serving": serving}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

@@ -7,9 +7,9 @@
  *
  * Conventions for every entry point:
  *  - Points have d int32 coordinates in [0, 2^30) stored point-major
- *    (coords[i*d + j]) and a uint32 id.  Builds, inserts and queries reject
- *    coordinates outside that range with PKD_EINVAL; a delete entry outside
- *    it matches no stored point and is skipped.
+ *    (coords[i*d + j]) and a uint32 id that names the point: the ids stored
+ *    in a tree are distinct, and 0xFFFFFFFF is never an id.  Builds, inserts
+ *    and queries reject coordinates outside that range with PKD_EINVAL.
  *  - Point, query and result buffers are DEVICE pointers owned by the
  *    caller, except in pkd_export (host buffers).  The library copies what it
  *    keeps; input buffers may be reused once the call has returned.
@@ -72,11 +72,16 @@ typedef struct {
 /* Build a Pkd-tree over n points (Alg. 1: sample, lambda-level skeleton,
  * sieve into 2^lambda buckets, recurse; leaves of at most phi points).
  *   coords  device, [n][d] int32
- *   ids     device, [n] uint32, or NULL for ids 0..n-1
+ *   ids     device, [n] uint32, or NULL for ids 0..n-1.  Ids name the
+ *           points: they must be distinct and not 0xFFFFFFFF (the k-NN
+ *           padding value).  The tree keeps an id table (id -> coordinates)
+ *           for deletes by id and for the id checks of inserts.
  *   n       number of points, < 2^31 (0 gives an empty tree); the tree
- *           holds fewer than 2^31 points after any insert
+ *           holds fewer than 2^31 points after any insert (node slots are
+ *           32-bit: two per arena position, plus skeleton nodes)
  *   out     receives the new tree (owns all device memory it allocates)
- * Errors: PKD_EINVAL (parameters, n, coordinates), PKD_ENOMEM, PKD_ECUDA. */
+ * Errors: PKD_EINVAL (parameters, n, coordinates, a repeated or reserved
+ * id), PKD_ENOMEM, PKD_ECUDA. */
 int pkd_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const pkd_params* params,
               void* stream, pkd_tree** out);
 
@@ -84,21 +89,25 @@ int pkd_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const pkd_
  * update subtree sizes top-down, rebuild with Build every subtree that would
  * leave the alpha balance and every leaf that receives points.
  *   coords  device, [m][d] int32;  ids  device, [m] uint32 (required)
- * Ids are the caller's labels; the library does not check their uniqueness.
- * Errors: PKD_EINVAL (tree unchanged), PKD_ENOMEM (tree unchanged),
+ * The whole batch is rejected with PKD_EINVAL, and the tree is unchanged,
+ * when an id is 0xFFFFFFFF, names a point stored in the tree, or appears
+ * twice in the batch.  An id deleted earlier may be inserted again.
+ * Errors: PKD_EINVAL (tree unchanged), PKD_ENOMEM (see below),
  * PKD_ECUDA / PKD_ETIMEOUT / PKD_EINTERNAL (tree unusable). */
 int pkd_batch_insert(pkd_tree* tree, const int32_t* coords, const uint32_t* ids, uint64_t m,
                      void* stream);
 
-/* BatchDelete (Sec. 4.2, two rounds): sieve the batch to the leaves, remove
- * every stored point whose (coordinates, id) equals a batch entry, then
- * rebalance top-down with the exact new sizes (rebuild the subtrees that
- * leave the alpha balance).  Entries that match no stored point are skipped.
- *   coords  device, [m][d] int32;  ids  device, [m] uint32
- *   n_deleted  host, optional: number of stored points removed
+/* BatchDelete (Sec. 4.2, two rounds) of the points named by ids: each id is
+ * looked up in the tree's id table for its coordinates, the found points are
+ * sieved to the leaves and removed, then the tree is rebalanced top-down
+ * with the exact new sizes (subtrees that leave the alpha balance are
+ * rebuilt).  Ids that name no stored point (never inserted, or deleted
+ * already) and repeats within the batch are skipped, as round 1 of Sec. 4.2
+ * discards points that are not in the tree; they are not errors.
+ *   ids        device, [m] uint32
+ *   n_deleted  host, optional: number of points removed
  * Errors as for pkd_batch_insert. */
-int pkd_batch_delete(pkd_tree* tree, const int32_t* coords, const uint32_t* ids, uint64_t m,
-                     uint64_t* n_deleted, void* stream);
+int pkd_batch_delete(pkd_tree* tree, const uint32_t* ids, uint64_t m, uint64_t* n_deleted, void* stream);
 
 /* k nearest neighbours (Sec. 5 "Queries": depth-first search, near child
  * first, far child pruned by the distance to its subspace).  For query i,
@@ -123,9 +132,13 @@ int pkd_knn(const pkd_tree* tree, const int32_t* queries, uint64_t q, int k, uin
  *   - the call must run on the tree's device (the current device);
  *   - calls whose device work overlaps (other streams, other host threads)
  *     race on the scratch; calls one after another on one stream do not;
- *   - the first call on a device resolves the scratch address, which may
- *     load the library's kernels on that device: make it before any region
- *     in which the caller may not allocate.
+ *   - the first call on a device is its set-up: it resolves the scratch
+ *     address and runs every search kernel variant (all d, both k ranges)
+ *     once on an empty query set, so that the kernels are loaded and the
+ *     driver's local-memory reservation is sized for the largest of them
+ *     (about 10 KB per resident thread at d = 8, k > 16); make that call
+ *     before any region in which the caller may not allocate.  Later calls
+ *     allocate nothing on the host or the device.
  * The call synchronises `stream` once (after the coordinate check) and
  * returns with the search queued on it; out_ids is valid once `stream` has
  * been synchronised.
@@ -231,9 +244,13 @@ int pkd_set_option(const char* name, int64_t value);
  * library made since the last pkd_kernel_timing call (timed or not).
  * Families: "validate", "sample", "count" and "scatter" (sieve rounds of a
  * build), "count_route" and "scatter_route" (sieve rounds that route an
- * update batch; items not counted), "smem_build" (shared-memory base case,
- * one CTA per subproblem), "smem_warp" (one warp per subproblem), "knn",
- * "range_count", "range_report". */
+ * update batch; items = batch points they move), "smem_build" (shared-memory
+ * base case, one CTA per subproblem), "smem_warp" (one warp per subproblem),
+ * "knn", "range_count", "range_report".  Counts without a time: "rebuilt_insert"
+ * and "rebuilt_delete" (points in the subtrees an update rebuilt, one entry
+ * per call), "delete_gather" (ids a delete found and looked up).  The name
+ * "allocations" reports, in *launches, every device or pinned-host allocation
+ * the library made since it was loaded. */
 int pkd_kernel_timing(int enable);
 int pkd_kernel_stats(const char* name, uint64_t* launches, double* total_ms, uint64_t* items);
 

@@ -65,7 +65,7 @@ struct DevStatus {
   int err;
   int detail;
   uint32_t max_depth;
-  uint32_t pad;
+  int idflags;  // id-table flags of the running call (IDF_* in ids.cuh)
   unsigned long long counters[8];
 };
 

@@ -8,11 +8,13 @@
 #include <vector>
 
 #include "common.cuh"
+#include "ids.cuh"
 
 namespace pkd {
 
 // Tunables; none of them changes any result.
 struct Knobs {
+  long long fail_alloc_after = -1;  // >= 0: allocations fail after this many more (fault injection)
   int base_cap = 0;   // 0: derived from d and the shared memory per block
   int skel_cap = 0;   // 0: derived
   int tile = 2048;    // points per tile in the sieve kernels
@@ -47,6 +49,7 @@ struct TreeMem {
   uint32_t* aux = nullptr;          // delete scratch: per node slot (kept zero)
   DevStatus* st = nullptr;          // device status word
   DevStatus* st_host = nullptr;     // pinned mirror
+  IdTable ids;                      // id -> coordinates of the stored points
 };
 
 // Every kernel launch of the library goes through PKD_LAUNCH, which counts
@@ -86,12 +89,20 @@ constexpr size_t BIG_BLOCK_MIN = (size_t)64 << 20;
 cudaError_t big_alloc(void** p, size_t bytes, cudaStream_t s);
 void big_free(void* p, cudaStream_t s);
 
+// Every device allocation of the library goes through pool_alloc: a
+// stream-ordered allocation from the pool above that is counted (reported by
+// pkd_kernel_stats("allocations")) and that fails with
+// cudaErrorMemoryAllocation, without allocating, once the option
+// "fail_alloc_after" is set to k >= 0 and k allocations have succeeded since
+// (host-side fault injection for the out-of-memory paths).
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s);
+
 // Stream-ordered allocation from that pool.
 template <class T>
 int dalloc(T** p, size_t n, cudaStream_t s) {
   *p = nullptr;
   if (n == 0) n = 1;
-  cudaError_t e = cudaMallocFromPoolAsync((void**)p, n * sizeof(T), mem_pool(), s);
+  cudaError_t e = pool_alloc((void**)p, n * sizeof(T), s);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
     return PKD_ENOMEM;
@@ -138,6 +149,9 @@ struct KTimer {
 void ktimer_begin(KTimer& k, const char* name, uint64_t items, cudaStream_t s);
 void ktimer_end(KTimer& k);
 bool ktiming_enabled();
+// While timing is on, add `items` to the counter family `name` (a count
+// with no kernel time, e.g. the points a batch update rebuilt).
+void stat_items(const char* name, uint64_t items);
 
 // A build of independent subproblems ("segments"): every segment's points
 // sit at arena positions [start, start+len) of A (or of the caller's input

@@ -534,9 +534,11 @@ int pkd_range_report(const pkd_tree* tc, const int32_t* lo, const int32_t* hi, u
 // The scratch is one array per device, shared by every call: two calls whose
 // work overlaps on the device (different streams, or different host threads)
 // race on it.  Calls issued one after the other on one stream are ordered.
-// The first call on a device resolves the array's address (which loads the
-// module on that device if it is not loaded yet); make that call before any
-// region in which the caller may not allocate.
+// The first call on a device is the set-up: it resolves the array's address
+// and launches every kernel the call uses once on an empty query set, which
+// loads them and lets the driver size its local-memory reservation for the
+// largest; make that call before any region in which the caller may not
+// allocate.
 
 namespace pkd {
 
@@ -557,8 +559,23 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 static std::mutex g_noalloc_mu;
 static unsigned char* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 
-// Set-up, once per device, with that device current: the scratch address.
-static int noalloc_scratch(int dev, unsigned char** out) {
+// Every kernel this entry point can launch, run once on an empty query set:
+// under lazy module loading a kernel's first launch loads it, and a kernel
+// with more local memory per thread than any launched before makes the driver
+// enlarge the device's local-memory reservation.  Both must happen in the
+// set-up, not in a later call.
+template <int D>
+static void noalloc_warm(cudaStream_t s) {
+  QueryArgs a{};
+  a.nq = 0;
+  a.k = 1;
+  PKD_LAUNCH(k_knn<D, 16><<<1, QTHREADS, 0, s>>>(a));
+  PKD_LAUNCH(k_knn<D, 128><<<1, QTHREADS, 0, s>>>(a));
+}
+
+// Set-up, once per device, with that device current: the scratch address,
+// and every kernel of the call loaded with its local memory reserved.
+static int noalloc_scratch(int dev, cudaStream_t s, unsigned char** out) {
   std::lock_guard<std::mutex> g(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
     void* p = nullptr;
@@ -568,6 +585,17 @@ static int noalloc_scratch(int dev, unsigned char** out) {
               cudaGetErrorString(e));
       return e != cudaSuccess ? cuda_err(e) : PKD_ECUDA;
     }
+    PKD_LAUNCH(k_noalloc_check<<<1, 256, 0, s>>>(nullptr, 0, nullptr));
+    noalloc_warm<1>(s);
+    noalloc_warm<2>(s);
+    noalloc_warm<3>(s);
+    noalloc_warm<4>(s);
+    noalloc_warm<5>(s);
+    noalloc_warm<6>(s);
+    noalloc_warm<7>(s);
+    noalloc_warm<8>(s);
+    PKD_CUDA(cudaGetLastError());
+    PKD_CUDA(cudaStreamSynchronize(s));
     g_noalloc_ptr[dev] = (unsigned char*)p;
   }
   *out = g_noalloc_ptr[dev];
@@ -600,7 +628,7 @@ extern "C" int pkd_knn_ids_noalloc(const pkd_tree* tc, const int32_t* queries, u
   PKD_CUDA(cudaGetDevice(&dev));
   if (dev != t.device || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return PKD_EINVAL;
   unsigned char* scratch = nullptr;
-  PKD_TRY_(noalloc_scratch(dev, &scratch));
+  PKD_TRY_(noalloc_scratch(dev, (cudaStream_t)stream, &scratch));
   cudaStream_t s = (cudaStream_t)stream;
   unsigned* bad = (unsigned*)scratch;
   PKD_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned), s));

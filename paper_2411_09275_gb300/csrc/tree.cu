@@ -112,6 +112,14 @@ void ktimer_begin(KTimer& k, const char* name, uint64_t items, cudaStream_t s) {
   cudaEventRecord(k.a, s);
 }
 
+void stat_items(const char* name, uint64_t items) {
+  if (!g_timing) return;
+  std::lock_guard<std::mutex> g(g_tmu);
+  auto& st = g_stats[name];
+  st.launches++;
+  st.items += items;
+}
+
 void ktimer_end(KTimer& k) {
   if (!k.on) return;
   cudaEventRecord(k.b, k.s);
@@ -228,9 +236,23 @@ static void big_flush_locked() {
   g_big_cached = 0;
 }
 
+static std::atomic<unsigned long long> g_allocs{0};
+static std::atomic<long long> g_fail_budget{-1};
+
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  long long b = g_fail_budget.load();
+  while (b >= 0) {  // fault injection armed
+    if (b == 0) return cudaErrorMemoryAllocation;
+    if (g_fail_budget.compare_exchange_weak(b, b - 1)) break;
+  }
+  g_allocs.fetch_add(1, std::memory_order_relaxed);
+  return cudaMallocFromPoolAsync(p, bytes, mem_pool(), s);
+}
+
 cudaError_t big_alloc(void** p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
-  if (bytes < BIG_BLOCK_MIN) return cudaMallocFromPoolAsync(p, bytes, mem_pool(), s);
+  if (bytes < BIG_BLOCK_MIN) return pool_alloc(p, bytes, s);
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> g(g_big_mu);
@@ -251,11 +273,11 @@ cudaError_t big_alloc(void** p, size_t bytes, cudaStream_t s) {
     *p = b.p;
     return cudaSuccess;
   }
-  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, mem_pool(), s);
-  if (e == cudaErrorMemoryAllocation && !g_big_cache.empty()) {
+  cudaError_t e = pool_alloc(p, bytes, s);
+  if (e == cudaErrorMemoryAllocation && !g_big_cache.empty() && g_fail_budget.load() < 0) {
     cudaGetLastError();
     big_flush_locked();
-    e = cudaMallocFromPoolAsync(p, bytes, mem_pool(), s);
+    e = pool_alloc(p, bytes, s);
   }
   if (e == cudaSuccess) g_big_live[*p] = {bytes, dev};
   return e;
@@ -292,6 +314,7 @@ void* pinned_get() {
   if (g_pin_free.empty()) {
     constexpr size_t CHUNK = 256;  // blocks per chunk
     char* c = nullptr;
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
     if (cudaMallocHost((void**)&c, CHUNK * PINNED_BLOCK) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
@@ -325,8 +348,22 @@ void tree_release(TreeMem& t) {
   for (void* p : {(void*)t.A.c, (void*)t.A.id, (void*)t.nodes, (void*)t.ndim, (void*)t.shared_next,
                   (void*)t.dead, (void*)t.aux, (void*)t.st})
     big_free(p, s);
+  ids_release(t.ids, s);
   pinned_put_after(s, t.st_host);
   t = TreeMem{};
+}
+
+cudaStream_t side_stream() {
+  static cudaStream_t streams[64] = {};
+  static std::mutex mu;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(mu);
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    streams[dev] = nullptr;
+  }
+  return streams[dev];
 }
 
 int export_from(const HostTree& h, uint32_t root, uint64_t top, uint64_t size, uint8_t* dims, int32_t* splits,
@@ -389,13 +426,12 @@ int tree_alloc(TreeMem& t, const Params& p, uint64_t cap, uint64_t shared_cap, c
   t.node_cap = shared_cap + 2 * t.cap;
   if (t.node_cap >= 0xFFFFFFF0ull) return PKD_EINVAL;
   cudaError_t e;
-  cudaMemPool_t pool = mem_pool();
   e = big_alloc((void**)&t.A.c, (size_t)p.d * t.cap * 4, s);
   if (e == cudaSuccess) e = big_alloc((void**)&t.A.id, (size_t)t.cap * 4, s);
   if (e == cudaSuccess) e = big_alloc((void**)&t.nodes, (size_t)t.node_cap * sizeof(Node), s);
   if (e == cudaSuccess) e = big_alloc((void**)&t.ndim, (size_t)t.node_cap, s);
-  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&t.shared_next, 16, pool, s);
-  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&t.st, sizeof(DevStatus), pool, s);
+  if (e == cudaSuccess) e = pool_alloc((void**)&t.shared_next, 16, s);
+  if (e == cudaSuccess) e = pool_alloc((void**)&t.st, sizeof(DevStatus), s);
   static_assert(sizeof(DevStatus) <= PINNED_BLOCK, "status block");
   if (e == cudaSuccess) {
     t.st_host = (DevStatus*)pinned_get();
@@ -463,6 +499,25 @@ int pkd_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const pkd_
   t->m.root = 0;
   uint32_t one = 1;
   cudaMemcpyAsync(t->m.shared_next, &one, 4, cudaMemcpyHostToDevice, s);
+  // The id table (id -> coordinates, and the check that ids are unique) is
+  // filled on a second stream while the tree is built: the base case is
+  // bound by instruction issue, the table fill by memory traffic.
+  cudaStream_t s2 = side_stream();
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (!s2 || cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    for (cudaEvent_t x : ev)
+      if (x) cudaEventDestroy(x);
+    tree_release(t->m);
+    delete t;
+    return PKD_ECUDA;
+  }
+  cudaEventRecord(ev[0], s);
+  cudaStreamWaitEvent(s2, ev[0], 0);
+  int eid = ids_create(t->m, n, s2);
+  if (eid == PKD_OK) ids_claim(t->m, coords, ids, n, nullptr, s2);
+  cudaEventRecord(ev[1], s2);
   BuildJob job;
   job.input_coords = coords;
   job.input_ids = ids;
@@ -472,7 +527,13 @@ int pkd_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const pkd_
   trace_mark(s, "build: alloc tree");
   e = run_build(t->m, job, s);
   trace_mark(s, "build: run_build");
+  cudaStreamWaitEvent(s, ev[1], 0);
+  if (e == PKD_OK) e = eid;
   if (e == PKD_OK) e = check_status(t->m, s);
+  if (e == PKD_OK && t->m.st_host->idflags) e = (t->m.st_host->idflags & IDF_FULL) ? PKD_EINTERNAL : PKD_EINVAL;
+  cudaStreamSynchronize(s2);
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
   if (e) {
     tree_release(t->m);
     delete t;
@@ -480,6 +541,8 @@ int pkd_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const pkd_
   }
   t->m.size = n;
   t->m.top = n;
+  t->m.ids.live = n;
+  t->m.ids.used = n;
   *out = t;
   return PKD_OK;
 }
@@ -542,6 +605,10 @@ int pkd_set_option(const char* name, int64_t value) {
   } else if (n == "base_kernel") {
     if (value != 0 && value != 1) return PKD_EINVAL;
     knobs().base_kernel = (int)value;
+  } else if (n == "fail_alloc_after") {
+    if (value < -1) return PKD_EINVAL;
+    knobs().fail_alloc_after = value;
+    g_fail_budget.store(value);
   } else if (n == "tile") {
     if (value < 256 || value > 4096 || (value & (value - 1))) return PKD_EINVAL;
     knobs().tile = (int)value;
@@ -565,6 +632,12 @@ int pkd_kernel_stats(const char* name, uint64_t* launches, double* total_ms, uin
   std::lock_guard<std::mutex> g(g_tmu);
   if (std::string(name) == "launches") {
     if (launches) *launches = g_launches.load();
+    if (total_ms) *total_ms = 0;
+    if (items) *items = 0;
+    return PKD_OK;
+  }
+  if (std::string(name) == "allocations") {  // since the library was loaded
+    if (launches) *launches = g_allocs.load();
     if (total_ms) *total_ms = 0;
     if (items) *items = 0;
     return PKD_OK;

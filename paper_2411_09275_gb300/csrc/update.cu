@@ -72,7 +72,8 @@ struct UpdArgs {
   uint32_t* iflag;   // [item]
   // next round
   Seg* next;
-  uint32_t* next_ctr;  // [0] items, [1] tiles of big items, [2] big items, [3] small items
+  uint32_t* next_ctr;  // [0] items, [1] tiles of big items, [2] big items, [3] small items,
+                       // [16] points of the big items
   Seg* next_big;       // big items (more than SMALL_ITEM points) and their item index
   uint32_t* next_bigmap;
   uint32_t* next_small;  // item index of the small items
@@ -316,8 +317,12 @@ __global__ void __launch_bounds__(ITEM_WARPS * 32) k_route_emit(UpdArgs a) {
     const unsigned mL = __ballot_sync(FULL_MASK, leaf), mN = __ballot_sync(FULL_MASK, inner);
     const unsigned mB = __ballot_sync(FULL_MASK, big), mS = __ballot_sync(FULL_MASK, inner && !big);
     uint32_t tiles = big ? (cnt + a.TILE - 1) / a.TILE : 0u;
+    uint32_t bigpts = big ? cnt : 0u;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) tiles += __shfl_xor_sync(FULL_MASK, tiles, o);
+    for (int o = 16; o; o >>= 1) {
+      tiles += __shfl_xor_sync(FULL_MASK, tiles, o);
+      bigpts += __shfl_xor_sync(FULL_MASK, bigpts, o);
+    }
     uint32_t gB = 0, qB = 0, kB = 0, sB = 0;
     if (lane == 0) {
       if (mL) gB = atomicAdd(a.ngroups, (uint32_t)__popc(mL));
@@ -325,6 +330,7 @@ __global__ void __launch_bounds__(ITEM_WARPS * 32) k_route_emit(UpdArgs a) {
       if (mB) {
         kB = atomicAdd(&a.next_ctr[2], (uint32_t)__popc(mB));
         atomicAdd(&a.next_ctr[1], tiles);
+        atomicAdd(&a.next_ctr[16], bigpts);
       }
       if (mS) sB = atomicAdd(&a.next_ctr[3], (uint32_t)__popc(mS));
     }
@@ -1064,8 +1070,11 @@ struct RouteRound {
   uint32_t* d_n;  // device copy of n
 };
 
-static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, uint64_t m, bool insert,
-                      uint64_t* n_changed, cudaStream_t s) {
+// The batch comes either point-major from the caller (coords, ids) or
+// already staged in structure-of-arrays form (`staged`, a buffer of at least
+// m positions that the route may overwrite).
+static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, const Pts* staged, uint64_t m,
+                      bool insert, uint64_t* n_changed, cudaStream_t s) {
   const Params& p = t.p;
   const int d = p.d, lam = p.lambda, NB = 1 << lam, HN = 2 << lam;
   const int TILE = std::min(std::max(knobs().tile, 256), 4096);
@@ -1075,15 +1084,15 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
   trace_mark(s, "upd: delete scratch");
 
   // batch buffers: W0/W1 ping-pong for the sieve, F final positions
-  int32_t *wc[3];
-  uint32_t* wid[3];
-  for (int k = 0; k < 3; ++k) {
+  int32_t *wc[3] = {nullptr, nullptr, nullptr};
+  uint32_t* wid[3] = {nullptr, nullptr, nullptr};
+  for (int k = staged ? 1 : 0; k < 3; ++k) {
     PKD_TRY(sc.get(&wc[k], (size_t)d * m));
     PKD_TRY(sc.get(&wid[k], m));
   }
-  Pts W[2] = {Pts{wc[0], wid[0], m}, Pts{wc[1], wid[1], m}};
+  Pts W[2] = {staged ? *staged : Pts{wc[0], wid[0], m}, Pts{wc[1], wid[1], m}};
   Pts F{wc[2], wid[2], m};
-  PKD_LAUNCH(k_stage<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(coords, ids, m, d, W[0]));
+  if (!staged) PKD_LAUNCH(k_stage<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(coords, ids, m, d, W[0]));
 
   uint32_t* dctr;
   PKD_TRY(sc.get(&dctr, 32));
@@ -1144,6 +1153,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
     PKD_CUDA(cudaMemcpyAsync(cur_small, &zero, 4, cudaMemcpyHostToDevice, s));
   }
   uint32_t ncur = 1, tiles = root_big ? (uint32_t)((m + TILE - 1) / TILE) : 0;
+  uint64_t big_pts = root_big ? m : 0;  // points the round's sieve kernels move
   uint32_t nbig = root_big ? 1 : 0, nsmall = root_big ? 0 : 1;
   int w = 0;
   uint32_t groups_before = 0;
@@ -1172,6 +1182,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
     PKD_TRY(sc.get(&next_bigmap, (size_t)ncur * NB));
     PKD_TRY(sc.get(&next_small, (size_t)ncur * NB));
     PKD_CUDA(cudaMemsetAsync(dctr, 0, 16, s));
+    PKD_CUDA(cudaMemsetAsync(dctr + 16, 0, 4, s));
 
     ua.items = cur;
     ua.nitems = R.d_n;
@@ -1229,19 +1240,20 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
       ra.hscan = hscan;
       if (record_buckets(NB)) PKD_TRY(sc.get(&ra.bkt, (size_t)tiles * TILE));
       PKD_LAUNCH(k_big_prefix<<<1, 1024, 0, s>>>(cur_big, R.d_n + 1, (uint32_t)TILE, tile0, excl));
-      PKD_DISPATCH_D(d, launch_count, ra, tiles, (uint64_t)0, "count_route", s);
+      PKD_DISPATCH_D(d, launch_count, ra, tiles, big_pts, "count_route", s);
       device_excl_scan(hist, hscan, nh, partial, s);
       PKD_LAUNCH(k_bucket_ranges<<<(nbig + 127) / 128, 128, 0, s>>>(ra, R.bstart, R.blen, nbk));
-      PKD_DISPATCH_D(d, launch_scatter, ra, tiles, (uint64_t)0, "scatter_route", s);
+      PKD_DISPATCH_D(d, launch_scatter, ra, tiles, big_pts, "scatter_route", s);
       PKD_LAUNCH(k_copy_round<<<tiles, 256, 0, s>>>(ra, F));
     }
     if (nsmall) {
       PKD_DISPATCH_D(d, launch_route_small, ra, cur_small, R.d_n + 2, cur, nbk, R.bstart, R.blen, F, nsmall, s);
     }
     PKD_LAUNCH(k_route_emit<<<g1, ITEM_WARPS * 32, 0, s>>>(ua));
-    PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 24, cudaMemcpyDeviceToHost, s));
+    PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 68, cudaMemcpyDeviceToHost, s));
     PKD_CUDA(cudaStreamSynchronize(s));
     const uint32_t nnext = hctr[0], ntiles = hctr[1], ngroups = hctr[4];
+    big_pts = hctr[16];
     groups_before = ngroups;
     rounds.push_back(R);
     cur = next;
@@ -1309,6 +1321,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, ui
   const uint32_t nitems = hctr[5];
   const uint64_t total = *(unsigned long long*)(hctr + 6);
   const uint32_t ncompact = hctr[8];
+  stat_items(insert ? "rebuilt_insert" : "rebuilt_delete", total);
 
   // ---- delete: compact the reached leaves in place ----
   if (ncompact)
@@ -1403,28 +1416,75 @@ int pkd_batch_insert(pkd_tree* tc, const int32_t* coords, const uint32_t* ids, u
   PKD_TRY_(validate_coords(coords, m * (uint64_t)t.p.d, s, &ok));
   if (!ok) return PKD_EINVAL;
   PKD_TRY_(check_status(t, s));
+  // the batch's ids take their slots first: a stored or repeated id rejects
+  // the whole batch before the tree changes
+  PKD_TRY_(ids_reserve(t, m, s));
+  uint64_t* slots = nullptr;
+  PKD_TRY_(dalloc(&slots, m, s));
+  ids_claim(t, coords, ids, m, slots, s);
+  t.ids.used += m;
+  int fl = 0;
+  int e = read_idflags(t, s, &fl);
+  if (e == PKD_OK && fl) e = (fl & IDF_FULL) ? PKD_EINTERNAL : PKD_EINVAL;
   uint64_t changed = 0;
-  int e = run_update(t, coords, ids, m, true, &changed, s);
+  if (e == PKD_OK) e = run_update(t, coords, ids, nullptr, m, true, &changed, s);
   if (e == PKD_OK) e = check_status(t, s);
-  if (e == PKD_OK) t.size += m;
+  if (e == PKD_OK) {
+    t.size += m;
+    t.ids.live += m;
+  } else {
+    ids_unclaim(t, slots, m, s);
+  }
+  dfree(slots, s);
   return e;
 }
 
-int pkd_batch_delete(pkd_tree* tc, const int32_t* coords, const uint32_t* ids, uint64_t m,
-                     uint64_t* n_deleted, void* stream) {
+int pkd_batch_delete(pkd_tree* tc, const uint32_t* ids, uint64_t m, uint64_t* n_deleted, void* stream) {
   if (!tc) return PKD_EINVAL;
   if (n_deleted) *n_deleted = 0;
   if (m == 0) return PKD_OK;
-  if (!coords || !ids) return PKD_EINVAL;
+  if (!ids) return PKD_EINVAL;
   TreeMem& t = tc->m;
   if (m >= (1ull << 31)) return PKD_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   PKD_TRY_(check_status(t, s));
+  // ids -> coordinates: every LIVE id of the batch is taken once (repeats and
+  // unknown or deleted ids are skipped) and staged for the sieve
+  Scratch sc{s, {}};
+  const int d = t.p.d;
+  int32_t* wc;
+  uint32_t *wid, *cnt;
+  uint64_t* wslots;
+  PKD_TRY(sc.get(&wc, (size_t)d * m));
+  PKD_TRY(sc.get(&wid, m));
+  PKD_TRY(sc.get(&wslots, m));
+  PKD_TRY(sc.get(&cnt, 1));
+  PKD_CUDA(cudaMemsetAsync(cnt, 0, 4, s));
+  Pts W{wc, wid, m};
+  ids_take(t, ids, m, W, wslots, cnt, s);
+  PinnedBlock hb(s);
+  if (!hb.p) return PKD_ENOMEM;
+  PKD_CUDA(cudaMemcpyAsync(hb.p, cnt, 4, cudaMemcpyDeviceToHost, s));
+  int fl = 0;
+  PKD_TRY(read_idflags(t, s, &fl));  // synchronises s
+  const uint32_t taken = *(const uint32_t*)hb.p;
+  if (fl) {
+    ids_settle(t, wslots, taken, false, s);
+    return PKD_EINTERNAL;
+  }
+  stat_items("delete_gather", taken);
+  if (taken == 0) return PKD_OK;
   uint64_t removed = 0;
-  int e = run_update(t, coords, ids, m, false, &removed, s);
+  int e = run_update(t, nullptr, nullptr, &W, taken, false, &removed, s);
   if (e == PKD_OK) e = check_status(t, s);
+  if (e == PKD_OK && removed != taken) {
+    fprintf(stderr, "pkd: delete removed %llu points for %u live ids\n", (unsigned long long)removed, taken);
+    e = PKD_EINTERNAL;
+  }
+  ids_settle(t, wslots, taken, e == PKD_OK, s);
   if (e == PKD_OK) {
     t.size -= removed;
+    t.ids.live -= removed;
     if (n_deleted) *n_deleted = removed;
   }
   return e;

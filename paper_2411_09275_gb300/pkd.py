@@ -66,7 +66,7 @@ def lib():
         P = C.POINTER
         L.pkd_build.argtypes = [vp, vp, u64, P(pkd_params), vp, P(vp)]
         L.pkd_batch_insert.argtypes = [vp, vp, vp, u64, vp]
-        L.pkd_batch_delete.argtypes = [vp, vp, vp, u64, P(u64), vp]
+        L.pkd_batch_delete.argtypes = [vp, vp, u64, P(u64), vp]
         L.pkd_knn.argtypes = [vp, vp, u64, i32, vp, vp, vp]
         L.pkd_range_count.argtypes = [vp, vp, vp, u64, vp, vp]
         L.pkd_knn_ids_noalloc.argtypes = [vp, vp, u64, i32, vp, vp]
@@ -140,10 +140,12 @@ def pkd_batch_insert(tree, coords: torch.Tensor, ids: torch.Tensor, stream=None)
                                   _stream(stream)), "pkd_batch_insert")
 
 
-def pkd_batch_delete(tree, coords: torch.Tensor, ids: torch.Tensor, stream=None) -> int:
+def pkd_batch_delete(tree, ids: torch.Tensor, stream=None) -> int:
+    """Delete the points named by ids [m] int32/uint32 (device); returns
+    the number removed (unknown and repeated ids are skipped)."""
     nd = C.c_uint64(0)
-    _check(lib().pkd_batch_delete(tree, _dptr(coords), _dptr(ids), coords.shape[0], C.byref(nd),
-                                  _stream(stream)), "pkd_batch_delete")
+    _check(lib().pkd_batch_delete(tree, _dptr(ids), ids.numel(), C.byref(nd), _stream(stream)),
+           "pkd_batch_delete")
     return int(nd.value)
 
 
@@ -297,8 +299,8 @@ class Tree:
     def insert(self, coords, ids, stream=None):
         pkd_batch_insert(self._h, coords, ids, stream)
 
-    def delete(self, coords, ids, stream=None) -> int:
-        return pkd_batch_delete(self._h, coords, ids, stream)
+    def delete(self, ids, stream=None) -> int:
+        return pkd_batch_delete(self._h, ids, stream)
 
     def knn(self, queries: torch.Tensor, k: int, stream=None):
         out_i = torch.empty((queries.shape[0], k), dtype=torch.int32, device=queries.device)

@@ -32,9 +32,13 @@ from . import pkd
 class Request:
     kind: str                    # "insert", "delete" or "knn"
     arrival: float               # seconds after the start of the stream
-    coords: torch.Tensor         # device [m, d] int32 (points, or queries)
+    coords: torch.Tensor | None  # device [m, d] int32: points (insert) or queries (knn); None for deletes
     ids: torch.Tensor | None = None  # device [m] int32 view of uint32 ids (updates)
     k: int = 10                  # knn
+
+    @property
+    def size(self) -> int:
+        return int(self.ids.numel()) if self.kind == "delete" else int(self.coords.shape[0])
 
 
 @dataclasses.dataclass
@@ -55,7 +59,7 @@ class Result:
 def working_set_bytes(r: Request, d: int) -> int:
     """Device bytes a request may need beyond the tree (routing buffers and
     rebuild scratch for updates, outputs for queries); an estimate."""
-    m = r.coords.shape[0]
+    m = r.size
     if r.kind == "knn":
         return m * r.k * 12 + m * 4 * d
     return m * (4 * d + 4) * 24
@@ -106,7 +110,7 @@ class Server:
             need = working_set_bytes(r, self.d)
             if self._free_bytes() < need + self.reserve:
                 retire(True)
-            res = Result(r.kind, int(r.coords.shape[0]), r.arrival)
+            res = Result(r.kind, r.size, r.arrival)
             results.append(res)
             if r.kind == "knn":
                 retire(False)
@@ -133,7 +137,7 @@ class Server:
                 if r.kind == "insert":
                     pkd.pkd_batch_insert(self.tree._h, r.coords, r.ids, s)
                 else:
-                    res.n_deleted = pkd.pkd_batch_delete(self.tree._h, r.coords, r.ids, s)
+                    res.n_deleted = pkd.pkd_batch_delete(self.tree._h, r.ids, s)
                 ev = torch.cuda.Event(enable_timing=True)
                 ev.record(s)
                 ev.synchronize()

@@ -76,12 +76,13 @@ def test_null_tree_and_option_ranges():
     for f in ("pkd_batch_insert", "pkd_batch_delete", "pkd_knn", "pkd_range_count", "pkd_export", "pkd_height"):
         getattr(lib, f).restype = ctypes.c_int
     assert lib.pkd_batch_insert(None, None, None, ctypes.c_uint64(5), None) == 1
+    assert lib.pkd_batch_delete(None, None, ctypes.c_uint64(5), None, None) == 1
     assert lib.pkd_knn(None, None, ctypes.c_uint64(1), 1, None, None, None) == 1
     assert lib.pkd_range_count(None, None, None, ctypes.c_uint64(1), None, None) == 1
     assert lib.pkd_export(None, None, None, None, None, None, None, None) == 1
     assert lib.pkd_height(None, None) == 1
     # tuning options: unknown names and out-of-range values are rejected
-    for name, v in ((b"no_such_option", 1), (b"tile", 100), (b"tile", 3000), (b"tile", 8192), (b"base_cap", 32),
+    for name, v in ((b"no_such_option", 1), (b"fail_alloc_after", -2), (b"tile", 100), (b"tile", 3000), (b"tile", 8192), (b"base_cap", 32),
                     (b"base_cap", 20000), (b"skel_cap", 63), (b"sieve_kernel", 3), (b"sieve_kernel", -1),
                     (b"base_kernel", 2)):
         assert lib.pkd_set_option(name, v) == 1, (name, v)

@@ -1,17 +1,19 @@
 """The benchmark's own workload at full size, in the launch configuration
 bench.py times (default parameters, the same input generators and seeds):
-build 1e8 3-D uniform points, insert 1e7 new points, delete 1e7 random
-existing ids.  The oracle cannot rebuild a 1e8-point tree in a test, so the
-checks are outputs it can compute one at a time and properties that hold at
-any size:
+build 1e8 3-D points, insert 1e7 new points, delete 1e7 random existing ids,
+on uniform and on varden-like inputs.
 
-- the exported tree holds every live id exactly once, each leaf at most phi
-  points unless all its points are identical, and every internal node's size
-  equals the sum of its children's;
-- every point of every sampled leaf lies inside the leaf's subspace (the box
-  cut by the splitters above it, left = strictly below);
-- k-NN for sampled queries and range counts for sampled boxes equal brute
-  force over all live points (numpy, one query at a time).
+- Exact parity with the oracle: the SHA-256 of the GPU tree's canonical
+  export after the delete, and of its 10-NN answer for 1e4 queries, equal the
+  values that tests/golden/make_fullsize_golden.py computed from the CPU
+  oracle alone on the same inputs (tests/golden/fullsize_*.txt).
+- Properties that hold at any size, checked independently of the oracle:
+  the exported tree holds every live id exactly once, each leaf at most phi
+  points unless all its points are identical, every internal node's size
+  equals the sum of its children's; every point of every sampled leaf lies
+  inside the leaf's subspace (the box cut by the splitters above it, left =
+  strictly below); k-NN for sampled queries and range counts for sampled
+  boxes equal brute force over all live points (numpy, one query at a time).
 """
 import numpy as np
 import pytest
@@ -71,11 +73,11 @@ def test_full_size_bench_workload_properties():
 
     wl = bench.WORKLOADS[bench.DEFAULT_WORKLOAD]
     n, d, m = wl["n"], wl["d"], wl["m"]
-    X, Y, yid, Z, zid = bench.make_inputs(wl, 0)
+    X, Y, yid, zid = bench.make_inputs(wl, 0)
     params = pkd.Params(d=d)
     t = pkd.Tree(to_dev(X), None, params)
     t.insert(to_dev(Y), ids_dev(yid))
-    assert t.delete(to_dev(Z), ids_dev(zid)) == m
+    assert t.delete(ids_dev(zid)) == m
     assert t.size == n
     allX = np.concatenate([X, Y])
     alive = np.ones(n + m, bool)
@@ -127,3 +129,4 @@ def test_full_size_bench_workload_properties():
     for bi in range(len(lo)):
         assert cnt[bi] == int(np.all((P >= lo[bi]) & (P <= hi[bi]), axis=1).sum())
     t.close()
+

@@ -78,7 +78,7 @@ def test_queries_after_updates_and_config1_knn():
     t.insert(to_dev(Y), ids_dev(yid))
     o.insert(Y, yid)
     sel = I.sample_indices(50_000, 1_000_000, 4)
-    assert t.delete(to_dev(X[sel]), ids_dev(sel)) == o.delete(X[sel], sel) == 50_000
+    assert t.delete(ids_dev(sel)) == o.delete(sel) == 50_000
     gi, gd = t.knn(to_dev(Q[:2000]), 10)
     wi, wd = o.knn(Q[:2000], 10)
     assert np.array_equal(gd.cpu().numpy(), wd) and np.array_equal(gi.cpu().numpy().view(np.uint32), wi)
@@ -117,10 +117,10 @@ def test_range_report_after_updates():
     yid = np.arange(n, n + 5000, dtype=np.uint32)
     t.insert(to_dev(Y), ids_dev(yid))
     kill = np.arange(0, n, 3)
-    t.delete(to_dev(X[kill]), ids_dev(kill.astype(np.uint32)))
+    t.delete(ids_dev(kill.astype(np.uint32)))
     o = O.OracleTree(X, None, O.Params(d=d, phi=8, lam=3, sigma_log2=2, sigma_os=4))
     o.insert(Y, yid)
-    o.delete(X[kill], kill.astype(np.uint32))
+    o.delete(kill.astype(np.uint32))
     lo, hi = I.boxes(200, d, 1 << 27, 95)
     off, got = pkd.pkd_range_report(t._h, to_dev(lo), to_dev(hi))
     off = off.cpu().numpy().astype(np.int64)

@@ -23,7 +23,6 @@ def _workload(n, d, count, seed):
     """A request list (arrival order) plus the host data to replay it."""
     rng = np.random.default_rng(seed)
     X = make_points("uniform", n, d, seed)
-    coords = {i: X[i] for i in range(n)}
     live = list(range(n))
     nxt = n
     reqs = []
@@ -35,8 +34,6 @@ def _workload(n, d, count, seed):
             m = int(rng.integers(50, 1500))
             Y = I.uniform(m, d, seed * 100 + q)
             ids = np.arange(nxt, nxt + m, dtype=np.uint32)
-            for j in range(m):
-                coords[nxt + j] = Y[j]
             live.extend(range(nxt, nxt + m))
             nxt += m
             reqs.append(("insert", t, Y, ids, 0))
@@ -44,11 +41,10 @@ def _workload(n, d, count, seed):
             m = int(rng.integers(20, 800))
             sel = rng.choice(len(live), size=min(m, len(live)), replace=False)
             ids = np.array([live[i] for i in sel], np.uint32)
-            Z = np.array([coords[int(i)] for i in ids], np.int32).reshape(-1, d)
             keep = np.ones(len(live), bool)
             keep[sel] = False
             live = [v for v, kp in zip(live, keep) if kp]
-            reqs.append(("delete", t, Z, ids, 0))
+            reqs.append(("delete", t, None, ids, 0))
         else:
             m = int(rng.integers(10, 400))
             Q = I.uniform(m, d, seed * 1000 + q)
@@ -60,7 +56,7 @@ def _run(pkd, serve, X, reqs, streams, realtime=False):
     d = X.shape[1]
     p = pkd.Params(d=d, phi=16, lam=4, sigma_log2=3, sigma_os=8)
     tree = pkd.Tree(to_dev(X), None, p)
-    R = [serve.Request(kind, t, to_dev(C), ids_dev(ids) if ids is not None else None, k)
+    R = [serve.Request(kind, t, to_dev(C) if C is not None else None, ids_dev(ids) if ids is not None else None, k)
          for kind, t, C, ids, k in reqs]
     out = serve.Server(tree, streams=streams, realtime=realtime).run(R)
     tree.close()
@@ -77,7 +73,7 @@ def test_serving_results_equal_oracle_replay():
         if kind == "insert":
             o.insert(C, ids)
         elif kind == "delete":
-            assert res.n_deleted == o.delete(C, ids) == len(ids)
+            assert res.n_deleted == o.delete(ids) == len(ids)
         else:
             wi, wd = o.knn(C, k)
             assert np.array_equal(res.knn_d2.cpu().numpy(), wd)

@@ -33,10 +33,12 @@ class Pair:
         self.xyz.update({int(i): tuple(x) for i, x in zip(yid, Y.tolist())})
         self.check("insert")
 
-    def delete(self, Z, zid):
-        nd = self.g.delete(to_dev(Z), ids_dev(zid))
-        assert nd == self.o.delete(Z, zid)
+    def delete(self, zid):
+        nd = self.g.delete(ids_dev(zid))
+        assert nd == self.o.delete(zid)
         self.check("delete")
+        for i in zid:
+            self.xyz.pop(int(i), None)
         return nd
 
     def check(self, what):
@@ -57,8 +59,7 @@ def test_insert_delete_small_tree(kind):
     pr.insert(make_points(kind, 500, d, 12), _ids(500, 2000))
     live = np.array(sorted(pr.xyz))
     sel = live[I.sample_indices(600, len(live), 13)]
-    Z = np.array([pr.xyz[int(i)] for i in sel], np.int32)
-    assert pr.delete(Z, sel) == 600
+    assert pr.delete(sel) == 600
 
 
 @pytest.mark.parametrize("sieve_kernel", [0, 1, 2], ids=["stream", "tiles", "stream-rewalk"])
@@ -79,12 +80,9 @@ def test_update_sequences_forced_rounds(alpha, sieve_kernel):
             nxt += 3000
             live = np.array(sorted(pr.xyz))
             sel = rng.choice(live, 2500, replace=False)
-            Z = np.array([pr.xyz[int(i)] for i in sel], np.int32)
-            Z = np.concatenate([Z, Z[:100], Z[100:150] + 1])  # duplicates and absent points
-            zid = np.concatenate([sel, sel[:100], sel[100:150]]).astype(np.uint32)
-            assert pr.delete(Z, zid) == 2500
-            for i in sel:
-                del pr.xyz[int(i)]
+            # repeats, and ids that name nothing (never inserted)
+            zid = np.concatenate([sel, sel[:100], sel[100:150], _ids(50, 10 ** 8)]).astype(np.uint32)
+            assert pr.delete(rng.permutation(zid)) == 2500
 
 
 def test_heavy_leaves_and_duplicates():
@@ -94,9 +92,8 @@ def test_heavy_leaves_and_duplicates():
     pr = Pair(X, _ids(n), pkd.Params(d=d, phi=16, lam=4, sigma_log2=2, sigma_os=4))
     Y = make_points("dups", 3000, d, 42)
     pr.insert(Y, _ids(3000, n))
-    Z = np.concatenate([X[:1000], Y[:500]])
     zid = np.concatenate([_ids(1000), _ids(500, n)])
-    assert pr.delete(Z, zid) == 1500
+    assert pr.delete(zid) == 1500
 
 
 def test_empty_tree_grow_and_delete_everything():
@@ -106,7 +103,7 @@ def test_empty_tree_grow_and_delete_everything():
     pr = Pair(np.zeros((0, d), np.int32), np.zeros(0, np.uint32), p)
     Y = make_points("uniform", 20000, d, 51)  # larger than the initial arena: it must grow
     pr.insert(Y, _ids(20000))
-    assert pr.delete(Y, _ids(20000)) == 20000
+    assert pr.delete(_ids(20000)) == 20000
     assert pr.g.size == 0
     pr.insert(Y[:100], _ids(100))
 
@@ -122,5 +119,63 @@ def test_config2_scaled_uniform_and_varden():
         Y = I.points(kind, m, d, 3 + seed)
         pr.insert(Y, np.arange(n, n + m, dtype=np.uint32))
         sel = I.sample_indices(m, n + m, 4)
-        allX = np.concatenate([X, Y])
-        assert pr.delete(allX[sel], sel) == m
+        assert pr.delete(sel.astype(np.uint32)) == m
+
+
+def _rejects(fn):
+    pkd = _pkd()
+    with pytest.raises(pkd.PkdError) as e:
+        fn()
+    assert e.value.code == pkd.PKD_EINVAL
+
+
+def test_id_rules_match_the_oracle():
+    # ids name points: repeated or reserved ids are rejected (builds), a batch
+    # that names a stored point or repeats an id is rejected whole (inserts);
+    # deletes skip ids that name nothing, repeats and deleted ids; a deleted
+    # id may come back with new coordinates
+    pkd = _pkd()
+    d, n = 3, 6000
+    p = pkd.Params(d=d, phi=8, lam=3, sigma_log2=2, sigma_os=4)
+    X = make_points("uniform", n, d, 61)
+    ids = _ids(n)
+    _rejects(lambda: pkd.Tree(to_dev(X), ids_dev(np.r_[ids[:-1], ids[:1]]), p))
+    _rejects(lambda: pkd.Tree(to_dev(X), ids_dev(np.r_[ids[:-1], [0xFFFFFFFF]]), p))
+    pr = Pair(X, ids, p)
+    before = pr.g.export()
+    Y = make_points("uniform", 400, d, 62)
+    for bad in (np.r_[_ids(399, n), ids[17:18]],            # a stored id
+                np.r_[_ids(399, n), _ids(1, n + 5)],        # repeated in the batch
+                np.r_[_ids(399, n), [0xFFFFFFFF]]):        # the reserved id
+        _rejects(lambda: pr.g.insert(to_dev(Y), ids_dev(bad)))
+        with pytest.raises(O.OracleError):
+            pr.o.insert(Y, bad.astype(np.uint32))
+        U.assert_exports_equal(pr.g.export(), before)
+    pr.insert(Y, _ids(400, n))
+    kill = np.r_[ids[::7], _ids(400, n)[::3]]
+    assert pr.delete(np.r_[kill, kill[:50], [12345678, 0xFFFFFFFF]].astype(np.uint32)) == len(kill)
+    assert pr.delete(kill[:100]) == 0  # deleted already
+    Z = make_points("uniform", 100, d, 63)
+    pr.insert(Z, kill[:100])  # deleted ids come back with new coordinates
+    assert pr.delete(kill[:100]) == 100
+
+
+def test_sparse_random_ids_and_table_growth():
+    # labels drawn at random from the whole 32-bit range (the id table's
+    # probing path), a tree that starts small and grows through many inserts
+    pkd = _pkd()
+    d = 2
+    p = pkd.Params(d=d, phi=8, lam=3, sigma_log2=2, sigma_os=4)
+    rng = np.random.default_rng(71)
+    labels = rng.permutation(np.unique(rng.integers(0, 0xFFFFFFFF, size=70000, dtype=np.uint64)))[:60000]
+    labels = labels.astype(np.uint32)
+    X = make_points("varden", 1000, d, 72)
+    pr = Pair(X, labels[:1000], p)
+    at = 1000
+    for r in range(5):
+        m = 1000 * 3 ** r // 3 + 500
+        Y = make_points("varden", m, d, 73 + r)
+        pr.insert(Y, labels[at:at + m])
+        at += m
+        live = np.array(sorted(pr.xyz), dtype=np.uint32)
+        pr.delete(rng.choice(live, len(live) // 4, replace=False))

@@ -83,9 +83,9 @@ def world(monkeypatch):
     def ins(h, coords, ids, st):
         w.log.append(("insert", int(coords[0, 0])))
 
-    def dele(h, coords, ids, st):
-        w.log.append(("delete", int(coords[0, 0])))
-        return int(coords.shape[0])
+    def dele(h, ids, st):
+        w.log.append(("delete", int(ids[0])))
+        return int(ids.numel())
 
     monkeypatch.setattr(serve.pkd, "pkd_knn", knn)
     monkeypatch.setattr(serve.pkd, "pkd_batch_insert", ins)
@@ -104,8 +104,12 @@ def world(monkeypatch):
 
 
 def _req(kind, idx, m=4, k=3):
-    c = torch.full((m, 2), idx, dtype=torch.int32)
-    ids = torch.arange(m, dtype=torch.int32) if kind != "knn" else None
+    c = torch.full((m, 2), idx, dtype=torch.int32) if kind != "delete" else None
+    ids = None
+    if kind == "insert":
+        ids = torch.arange(m, dtype=torch.int32)
+    elif kind == "delete":
+        ids = torch.full((m,), idx, dtype=torch.int32)  # the log reads the request number from ids[0]
     return serve.Request(kind, 0.001 * idx, c, ids, k)
 
 

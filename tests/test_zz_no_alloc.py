@@ -92,3 +92,57 @@ def test_noalloc_rejects_bad_input_then_recovers():
     assert (_noalloc(t, Q, 5) == want).all().item()
     empty = torch.empty((0, 3), dtype=torch.int32, device=Q.device)
     assert _noalloc(t, empty, 5).numel() == 0
+
+
+_FRESH = r'''
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_2411_09275_gb300 import inputs as I, pkd
+
+dev = torch.device("cuda:0")
+pkd.lib()
+trees, queries = {}, {}
+for d in (3, 8):
+    X = I.uniform(30000, d, 90 + d)
+    trees[d] = pkd.Tree(torch.from_numpy(X).to(dev), None, pkd.Params(d=d, phi=16, lam=4, sigma_log2=3, sigma_os=8))
+    queries[d] = torch.from_numpy(np.concatenate([I.uniform(1000, d, 95 + d), X[:200]])).to(dev)
+out3 = torch.empty((1200, 5), dtype=torch.int32, device=dev)
+out8 = torch.empty((1200, 128), dtype=torch.int32, device=dev)
+torch.cuda.synchronize()
+# first call on the device: the set-up (d = 3, k = 5 uses the small-k kernel only)
+pkd.pkd_knn_ids_noalloc(trees[3]._h, queries[3], 5, out3)
+torch.cuda.synchronize()
+free0 = torch.cuda.mem_get_info()[0]
+alloc0 = pkd.pkd_kernel_stats("allocations")[0]
+# first d = 8, k = 128 search of the process: a kernel with far more local memory
+pkd.pkd_knn_ids_noalloc(trees[8]._h, queries[8], 128, out8)
+torch.cuda.synchronize()
+free1 = torch.cuda.mem_get_info()[0]
+alloc1 = pkd.pkd_kernel_stats("allocations")[0]
+want, _ = trees[8].knn(queries[8], 128)
+torch.cuda.synchronize()
+ok = bool((want == out8).all().item())
+print("RESULT", free0, free1, alloc0, alloc1, ok)
+'''
+
+
+def test_noalloc_call_allocates_nothing_after_its_set_up():
+    # in a fresh process, so that no earlier test has loaded the kernels or
+    # grown the local-memory reservation: after the set-up call, a call that
+    # uses a kernel never launched before in the process (d = 8, k = 128)
+    # leaves the device's free memory and the library's allocation count
+    # unchanged, and returns pkd_knn's ids
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FRESH, root], capture_output=True, text=True, timeout=600)
+    line = [ln for ln in r.stdout.splitlines() if ln.startswith("RESULT")]
+    assert r.returncode == 0 and line, r.stdout[-2000:] + r.stderr[-2000:]
+    _, free0, free1, alloc0, alloc1, ok = line[0].split()
+    assert ok == "True"
+    assert int(alloc1) == int(alloc0), (alloc0, alloc1)
+    assert int(free1) == int(free0), (free0, free1)

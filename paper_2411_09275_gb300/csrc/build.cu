@@ -1434,6 +1434,7 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
   // 5. every small subproblem, one CTA each, in shared memory
   PKD_CUDA(cudaMemcpyAsync(hctr + 12, d_nbase, 14 * 4, cudaMemcpyDeviceToHost, s));
   PKD_CUDA(cudaStreamSynchronize(s));
+  if (job.before_base) job.before_base();
   const uint64_t cta_pts = *(unsigned long long*)(hctr + 16), warp_pts = *(unsigned long long*)(hctr + 18);
   const uint64_t tiny_pts = *(unsigned long long*)(hctr + 20);
   const uint32_t nbase = std::min<uint32_t>(hctr[12], (uint32_t)base_cap_segs);

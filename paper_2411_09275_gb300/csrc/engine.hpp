@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -166,6 +167,10 @@ struct BuildJob {
   std::vector<Seg> segs;   // host list of root segments, or:
   const Seg* dsegs = nullptr;  // device list of root segments (dsegs_n of them)
   uint64_t dsegs_n = 0;
+  // Called once on the host, right before the shared-memory base cases are
+  // launched on the stream (work that should overlap them, which are bound by
+  // instruction issue rather than memory traffic, is queued from here).
+  std::function<void()> before_base;
 };
 int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s);
 

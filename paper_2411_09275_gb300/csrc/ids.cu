@@ -1,16 +1,18 @@
 // Id table kernels and their host side (layout and hashing in ids.cuh).
 //
 //  claim    build and insert: every point takes the slot of its id (an
-//           empty slot, or its own DEAD slot), writes its coordinates and
-//           becomes LIVE; an id found LIVE or taken by another point of the
-//           same batch raises IDF_BAD_ID.  A rejected batch gives its claimed
-//           slots back as DEAD (unclaim), so the stored set is unchanged.
-//  take     delete: every id found LIVE moves to DELETING (one winner per
-//           id, so repeats count once), and its coordinates and id are
-//           appended to the batch buffer that the delete sieves; unknown and
-//           DEAD ids are skipped (round 1 of Sec. 4.2 discards points that
-//           are not in the tree).  settle then marks the taken ids DEAD, or
-//           LIVE again when the delete failed.
+//           empty slot, or its own DEAD slot), stores its coordinates and
+//           becomes LIVE; an id found LIVE (stored, or taken by another point
+//           of the same batch) raises IDF_BAD_ID.  A rejected batch gives its
+//           claimed slots back as DEAD (unclaim), so the stored set is
+//           unchanged.  A build with ids 0..n-1 stores its keys without
+//           compare-and-swap: the table is empty and those ids have distinct
+//           home slots.
+//  take     delete: every id found LIVE becomes DEAD (one winner per id, so
+//           repeats count once), and its coordinates and id are appended to
+//           the batch buffer that the delete sieves; unknown and DEAD ids are
+//           skipped (round 1 of Sec. 4.2 discards points that are not in the
+//           tree).  When the delete fails, restore puts the taken ids back.
 //  rehash   the LIVE entries move to a larger table (DEAD ones are dropped).
 #include <algorithm>
 #include <cstdio>
@@ -29,52 +31,58 @@ unsigned id_blocks(uint64_t n) {
   return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(b, 152ull * 16));
 }
 
-__device__ __forceinline__ uint32_t key_state(unsigned long long k) { return (uint32_t)(k >> 32); }
-
 __global__ void __launch_bounds__(ID_THREADS) k_ids_claim(const int32_t* coords, const uint32_t* ids, uint64_t m,
                                                           int d, IdTable T, uint64_t* slots, DevStatus* st) {
   const uint64_t mask = T.cap - 1;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t id = ids ? ids[i] : (uint32_t)i;
+    const int32_t* c = coords + i * (uint64_t)d;
+    const int32_t x0 = c[0];
     uint64_t got = ID_NO_SLOT;
     int bad = 0;
-    if (id == ID_RESERVED) {
-      bad = IDF_BAD_ID;
+    if (!ids) {  // ids 0..m-1 into an empty table: distinct home slots
+      got = id_home((uint32_t)i, T.lgc);
+      T.key[got] = id_key((uint32_t)i, x0, ID_LIVE);
     } else {
-      uint64_t s = id_home(id, T.lgc), n = 0;
-      for (; n < T.cap; ++n, s = (s + 1) & mask) {
-        unsigned long long k = __ldcg(&T.key[s]);
-        if (k == ID_EMPTY) {
-          k = atomicCAS(&T.key[s], ID_EMPTY, id_key(id, ID_LIVE));
+      const uint32_t id = ids[i];
+      const unsigned long long want = id_key(id, x0, ID_LIVE);
+      if (id == ID_RESERVED) {
+        bad = IDF_BAD_ID;
+      } else {
+        uint64_t s = id_home(id, T.lgc), n = 0;
+        for (; n < T.cap; ++n, s = (s + 1) & mask) {
+          unsigned long long k = __ldcg(&T.key[s]);
           if (k == ID_EMPTY) {
-            got = s;
+            k = atomicCAS(&T.key[s], ID_EMPTY, want);
+            if (k == ID_EMPTY) {
+              got = s;
+              break;
+            }
+          }
+          if ((uint32_t)k == id) {  // this id's slot: revive it if deleted
+            if (id_state(k) == ID_DEAD && atomicCAS(&T.key[s], k, want) == k)
+              got = s;
+            else
+              bad = IDF_BAD_ID;
             break;
           }
         }
-        if ((uint32_t)k == id) {  // this id's slot: revive it if deleted
-          if (key_state(k) == ID_DEAD && atomicCAS(&T.key[s], k, id_key(id, ID_LIVE)) == k)
-            got = s;
-          else
-            bad = IDF_BAD_ID;
-          break;
-        }
+        if (n == T.cap) bad = IDF_FULL;
       }
-      if (n == T.cap) bad = IDF_FULL;
     }
     if (got != ID_NO_SLOT) {
       int32_t* x = T.xs + got * (uint64_t)T.cw;
-      const int32_t* c = coords + i * (uint64_t)d;
-      for (int j = 0; j < d; ++j) x[j] = c[j];
+      for (int j = 1; j < d; ++j) x[j - 1] = c[j];
     }
     if (slots) slots[i] = got;
     if (bad) atomicOr(&st->idflags, bad);
   }
 }
 
-__global__ void __launch_bounds__(ID_THREADS) k_ids_unclaim(const uint64_t* slots, uint64_t m, IdTable T) {
+__global__ void __launch_bounds__(ID_THREADS) k_ids_restate(const uint64_t* slots, uint64_t m, IdTable T,
+                                                            uint32_t state) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t s = slots[i];
-    if (s != ID_NO_SLOT) T.key[s] = id_key((uint32_t)T.key[s], ID_DEAD);
+    if (s != ID_NO_SLOT) T.key[s] = id_with_state(T.key[s], state);
   }
 }
 
@@ -87,6 +95,7 @@ __global__ void __launch_bounds__(ID_THREADS) k_ids_take(const uint32_t* ids, ui
     const uint64_t i = b0 + threadIdx.x;
     uint64_t got = ID_NO_SLOT;
     uint32_t id = ID_RESERVED;
+    int32_t x0 = 0;
     if (i < m) {
       id = ids[i];
       if (id != ID_RESERVED) {
@@ -95,7 +104,10 @@ __global__ void __launch_bounds__(ID_THREADS) k_ids_take(const uint32_t* ids, ui
           const unsigned long long k = __ldcg(&T.key[s]);
           if (k == ID_EMPTY) break;  // never stored
           if ((uint32_t)k == id) {
-            if (key_state(k) == ID_LIVE && atomicCAS(&T.key[s], k, id_key(id, ID_DELETING)) == k) got = s;
+            if (id_state(k) == ID_LIVE && atomicCAS(&T.key[s], k, id_with_state(k, ID_DEAD)) == k) {
+              got = s;
+              x0 = id_x0(k);
+            }
             break;
           }
         }
@@ -109,18 +121,11 @@ __global__ void __launch_bounds__(ID_THREADS) k_ids_take(const uint32_t* ids, ui
     if (got != ID_NO_SLOT) {
       const uint64_t p = first[0];
       const int32_t* x = T.xs + got * (uint64_t)T.cw;
-      for (int j = 0; j < d; ++j) W.c[(uint64_t)j * W.stride + p] = x[j];
+      W.c[p] = x0;
+      for (int j = 1; j < d; ++j) W.c[(uint64_t)j * W.stride + p] = x[j - 1];
       W.id[p] = id;
       wslots[p] = got;
     }
-  }
-}
-
-__global__ void __launch_bounds__(ID_THREADS) k_ids_settle(const uint64_t* wslots, uint64_t n, IdTable T,
-                                                           uint32_t state) {
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t s = wslots[i];
-    T.key[s] = id_key((uint32_t)T.key[s], state);
   }
 }
 
@@ -128,7 +133,7 @@ __global__ void __launch_bounds__(ID_THREADS) k_ids_rehash(IdTable A, IdTable B,
   const uint64_t mask = B.cap - 1;
   for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < A.cap; a += (uint64_t)gridDim.x * blockDim.x) {
     const unsigned long long k = A.key[a];
-    if (k == ID_EMPTY || key_state(k) != ID_LIVE) continue;
+    if (k == ID_EMPTY || id_state(k) != ID_LIVE) continue;
     const uint32_t id = (uint32_t)k;
     uint64_t s = id_home(id, B.lgc), n = 0;
     for (; n < B.cap; ++n, s = (s + 1) & mask)
@@ -137,7 +142,7 @@ __global__ void __launch_bounds__(ID_THREADS) k_ids_rehash(IdTable A, IdTable B,
       atomicOr(&st->idflags, IDF_FULL);
       continue;
     }
-    for (int j = 0; j < d; ++j) B.xs[s * (uint64_t)B.cw + j] = A.xs[a * (uint64_t)A.cw + j];
+    for (int j = 1; j < d; ++j) B.xs[s * (uint64_t)B.cw + j - 1] = A.xs[a * (uint64_t)A.cw + j - 1];
   }
 }
 
@@ -155,10 +160,13 @@ int ids_alloc(IdTable& T, int d, uint64_t cap, cudaStream_t s) {
   T.cap = cap;
   T.lgc = 0;
   while ((32ull << T.lgc) < cap) ++T.lgc;
-  T.cw = 1;
-  while (T.cw < d) T.cw <<= 1;
+  T.cw = 0;
+  if (d > 1) {
+    T.cw = 1;
+    while (T.cw < d - 1) T.cw <<= 1;
+  }
   cudaError_t e = big_alloc((void**)&T.key, (size_t)cap * 8, s);
-  if (e == cudaSuccess) e = big_alloc((void**)&T.xs, (size_t)cap * T.cw * 4, s);
+  if (e == cudaSuccess && T.cw) e = big_alloc((void**)&T.xs, (size_t)cap * T.cw * 4, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     ids_release(T, s);
@@ -214,7 +222,7 @@ void ids_claim(TreeMem& t, const int32_t* coords, const uint32_t* ids, uint64_t 
 
 void ids_unclaim(TreeMem& t, const uint64_t* slots, uint64_t m, cudaStream_t s) {
   if (m == 0) return;
-  PKD_LAUNCH(k_ids_unclaim<<<id_blocks(m), ID_THREADS, 0, s>>>(slots, m, t.ids));
+  PKD_LAUNCH(k_ids_restate<<<id_blocks(m), ID_THREADS, 0, s>>>(slots, m, t.ids, ID_DEAD));
 }
 
 void ids_take(TreeMem& t, const uint32_t* ids, uint64_t m, Pts W, uint64_t* wslots, uint32_t* count,
@@ -223,9 +231,9 @@ void ids_take(TreeMem& t, const uint32_t* ids, uint64_t m, Pts W, uint64_t* wslo
   PKD_LAUNCH(k_ids_take<<<id_blocks(m), ID_THREADS, 0, s>>>(ids, m, t.ids, W, wslots, count, t.p.d, t.st));
 }
 
-void ids_settle(TreeMem& t, const uint64_t* wslots, uint64_t n, bool deleted, cudaStream_t s) {
+void ids_restore(TreeMem& t, const uint64_t* wslots, uint64_t n, cudaStream_t s) {
   if (n == 0) return;
-  PKD_LAUNCH(k_ids_settle<<<id_blocks(n), ID_THREADS, 0, s>>>(wslots, n, t.ids, deleted ? ID_DEAD : ID_LIVE));
+  PKD_LAUNCH(k_ids_restate<<<id_blocks(n), ID_THREADS, 0, s>>>(wslots, n, t.ids, ID_LIVE));
 }
 
 }  // namespace pkd

@@ -500,8 +500,8 @@ int pkd_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const pkd_
   uint32_t one = 1;
   cudaMemcpyAsync(t->m.shared_next, &one, 4, cudaMemcpyHostToDevice, s);
   // The id table (id -> coordinates, and the check that ids are unique) is
-  // filled on a second stream while the tree is built: the base case is
-  // bound by instruction issue, the table fill by memory traffic.
+  // filled on a second stream while the shared-memory base cases run: they
+  // are bound by instruction issue, the table fill by memory traffic.
   cudaStream_t s2 = side_stream();
   cudaEvent_t ev[2] = {nullptr, nullptr};
   if (!s2 || cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -513,12 +513,19 @@ int pkd_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const pkd_
     delete t;
     return PKD_ECUDA;
   }
-  cudaEventRecord(ev[0], s);
-  cudaStreamWaitEvent(s2, ev[0], 0);
-  int eid = ids_create(t->m, n, s2);
-  if (eid == PKD_OK) ids_claim(t->m, coords, ids, n, nullptr, s2);
-  cudaEventRecord(ev[1], s2);
+  int eid = PKD_OK;
+  bool queued = false;
+  pkd_tree* tt = t;
+  auto fill_ids = [&]() {
+    queued = true;
+    cudaEventRecord(ev[0], s);
+    cudaStreamWaitEvent(s2, ev[0], 0);
+    eid = ids_create(tt->m, n, s2);
+    if (eid == PKD_OK) ids_claim(tt->m, coords, ids, n, nullptr, s2);
+    cudaEventRecord(ev[1], s2);
+  };
   BuildJob job;
+  job.before_base = fill_ids;
   job.input_coords = coords;
   job.input_ids = ids;
   job.base = 0;
@@ -527,6 +534,7 @@ int pkd_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const pkd_
   trace_mark(s, "build: alloc tree");
   e = run_build(t->m, job, s);
   trace_mark(s, "build: run_build");
+  if (e == PKD_OK && !queued) fill_ids();  // run_build returned before its base cases
   cudaStreamWaitEvent(s, ev[1], 0);
   if (e == PKD_OK) e = eid;
   if (e == PKD_OK) e = check_status(t->m, s);

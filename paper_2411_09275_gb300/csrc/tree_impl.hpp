@@ -44,12 +44,13 @@ int export_from(const HostTree& h, uint32_t root, uint64_t top, uint64_t size, u
 //  ids_reserve  room for `extra` more claims (rehashes into a larger table)
 //  ids_claim    launch: points take their ids' slots (LIVE); slots[i] gets
 //               the claimed slot or ID_NO_SLOT (slots may be NULL); a bad id
-//               raises IDF_BAD_ID in the status word
+//               raises IDF_BAD_ID in the status word; ids NULL (0..m-1) only
+//               into a new, empty table
 //  ids_unclaim  launch: claimed slots go back to DEAD (a rejected batch)
-//  ids_take     launch: LIVE ids move to DELETING and their (coords, id) are
+//  ids_take     launch: LIVE ids become DEAD and their (coords, id) are
 //               appended to W (count is the device append counter), the slot
 //               of each appended point to wslots
-//  ids_settle   launch: the taken slots become DEAD (deleted) or LIVE again
+//  ids_restore  launch: taken slots become LIVE again (a failed delete)
 //  read_idflags synchronises `s`, returns and clears the flags
 int ids_create(TreeMem& t, uint64_t n, cudaStream_t s);
 int ids_reserve(TreeMem& t, uint64_t extra, cudaStream_t s);
@@ -58,7 +59,7 @@ void ids_claim(TreeMem& t, const int32_t* coords, const uint32_t* ids, uint64_t 
 void ids_unclaim(TreeMem& t, const uint64_t* slots, uint64_t m, cudaStream_t s);
 void ids_take(TreeMem& t, const uint32_t* ids, uint64_t m, Pts W, uint64_t* wslots, uint32_t* count,
               cudaStream_t s);
-void ids_settle(TreeMem& t, const uint64_t* wslots, uint64_t n, bool deleted, cudaStream_t s);
+void ids_restore(TreeMem& t, const uint64_t* wslots, uint64_t n, cudaStream_t s);
 int read_idflags(TreeMem& t, cudaStream_t s, int* flags);
 
 // k-NN (see pkd_knn) on the tree rooted at node slot `root`.

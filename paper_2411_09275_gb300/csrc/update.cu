@@ -1469,7 +1469,7 @@ int pkd_batch_delete(pkd_tree* tc, const uint32_t* ids, uint64_t m, uint64_t* n_
   PKD_TRY(read_idflags(t, s, &fl));  // synchronises s
   const uint32_t taken = *(const uint32_t*)hb.p;
   if (fl) {
-    ids_settle(t, wslots, taken, false, s);
+    ids_restore(t, wslots, taken, s);
     return PKD_EINTERNAL;
   }
   stat_items("delete_gather", taken);
@@ -1481,7 +1481,7 @@ int pkd_batch_delete(pkd_tree* tc, const uint32_t* ids, uint64_t m, uint64_t* n_
     fprintf(stderr, "pkd: delete removed %llu points for %u live ids\n", (unsigned long long)removed, taken);
     e = PKD_EINTERNAL;
   }
-  ids_settle(t, wslots, taken, e == PKD_OK, s);
+  if (e != PKD_OK) ids_restore(t, wslots, taken, s);
   if (e == PKD_OK) {
     t.size -= removed;
     t.ids.live -= removed;

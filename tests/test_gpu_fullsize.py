@@ -20,6 +20,7 @@ import pytest
 
 import bench
 from paper_2411_09275_gb300 import inputs as I
+from tests.golden import make_fullsize_golden as G
 from tests.gpuutil import ids_dev, to_dev
 
 pytestmark = pytest.mark.gpu
@@ -130,3 +131,41 @@ def test_full_size_bench_workload_properties():
         assert cnt[bi] == int(np.all((P >= lo[bi]) & (P <= hi[bi]), axis=1).sum())
     t.close()
 
+
+def _golden():
+    want = {}
+    with open(G.OUT) as f:
+        for ln in f:
+            if ln.startswith("#") or not ln.strip():
+                continue
+            kind, key, *rest = ln.split()
+            want.setdefault(kind, {})[key] = rest
+    return want
+
+
+@pytest.mark.parametrize("kind", ["uniform", "varden"])
+def test_full_size_equals_oracle_golden(kind):
+    from paper_2411_09275_gb300 import pkd
+
+    wl = dict(bench.WORKLOADS[bench.DEFAULT_WORKLOAD], kind=kind)
+    assert (wl["n"], wl["d"], wl["m"]) == (G.N, G.D, G.M)
+    X, Y, yid, zid = bench.make_inputs(wl, 0)
+    gX, gY, gyid, gzid, gQ = G.workload(kind)  # the golden script's own draw of the inputs
+    assert np.array_equal(X, gX) and np.array_equal(Y, gY) and np.array_equal(yid, gyid)
+    assert np.array_equal(zid, gzid)
+    del gX, gY
+    t = pkd.Tree(to_dev(X), None, pkd.Params(d=wl["d"]))
+    t.insert(to_dev(Y), ids_dev(yid))
+    assert t.delete(ids_dev(zid)) == wl["m"]
+    ex = t.export()
+    qi, qd = t.knn(to_dev(gQ), G.K)
+    qi = qi.cpu().numpy().view(np.uint32)
+    qd = qd.cpu().numpy()
+    t.close()
+    want = _golden()[kind]
+    nodes, leaves = int(want["nodes"][0]), int(want["nodes"][2])
+    assert (len(ex["dims"]), len(ex["leaf_offsets"]) - 1) == (nodes, leaves)
+    assert G.export_digest(ex) == want["export_sha256"][0]
+    row0 = " ".join(f"{int(a)}:{int(b)}" for a, b in zip(qi[0], qd[0]))
+    assert row0 == " ".join(want["knn_row0"])
+    assert G.knn_digest(qi, qd) == want["knn_sha256"][0]

@@ -171,6 +171,22 @@ int pkd_range_count(const pkd_tree* tree, const int32_t* lo, const int32_t* hi, 
 int pkd_range_report(const pkd_tree* tree, const int32_t* lo, const int32_t* hi, uint64_t q, uint64_t* offsets,
                      uint32_t* ids, uint64_t ids_cap, uint64_t* total, void* stream);
 
+/* Stored bounding boxes: the paper's Pkd-bb variant (Sec. 6, the study of
+ * bounding boxes).  With enable = 1 every node keeps the tight box of the
+ * points in its subtree (8d bytes per node slot, computed bottom-up now and
+ * again after every batch update), and pkd_knn, pkd_range_count and
+ * pkd_range_report prune with those boxes instead of the subspace implied by
+ * the splitters above a node (the Pkd form, the default).  The answers are
+ * identical; only the search differs.  enable = 0 frees the boxes.
+ * Synchronises `stream`.  Errors: PKD_EINVAL, PKD_ENOMEM (boxes off), PKD_ECUDA. */
+int pkd_set_bounding_boxes(pkd_tree* tree, int enable, void* stream);
+
+/* The stored boxes in the pre-order of pkd_export, into HOST buffers
+ * lo[n_nodes][d], hi[n_nodes][d] (n_nodes as pkd_export reports it); an
+ * empty subtree has lo = INT32_MAX and hi = INT32_MIN.  PKD_EINVAL when
+ * the boxes are off or n_nodes differs.  Synchronises the device. */
+int pkd_export_boxes(const pkd_tree* tree, int32_t* lo, int32_t* hi, uint64_t n_nodes);
+
 /* Canonical form of the tree into HOST buffers (for parity checks and
  * checkpoints): nodes in pre-order, interior nodes as (dim, split, size),
  * leaves as (0xFF, 0, point count); leaves in in-order with their ids sorted

@@ -51,6 +51,9 @@ struct TreeMem {
   DevStatus* st = nullptr;          // device status word
   DevStatus* st_host = nullptr;     // pinned mirror
   IdTable ids;                      // id -> coordinates of the stored points
+  int32_t* bbox = nullptr;          // stored bounding boxes (boxes.cu), node_cap * 2d
+  uint64_t bbox_cap = 0;            // node slots bbox covers
+  bool bbox_on = false;             // kept current after every update; queries prune with them
 };
 
 // Every kernel launch of the library goes through PKD_LAUNCH, which counts

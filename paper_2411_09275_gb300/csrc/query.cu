@@ -48,6 +48,7 @@ struct QueryArgs {
   int64_t* out_d2;
   uint64_t* out_cnt;
   DevStatus* st;
+  const int32_t* box;  // stored bounding boxes (node slot * 2d), or null
 };
 
 template <int D, int KMAX>
@@ -279,6 +280,164 @@ __global__ void __launch_bounds__(QTHREADS) k_range_report(QueryArgs a, const ui
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// The same searches with stored bounding boxes (the Pkd-bb variant of Sec. 6):
+// a node is pruned, counted whole or reported whole by the tight box of its
+// points (a.box) instead of the subspace its ancestors' splitters imply, so
+// a stack entry is a node slot only.  Answers are identical.
+// ---------------------------------------------------------------------------
+
+template <int D>
+__device__ __forceinline__ Box<D> stored_box(const int32_t* box, uint32_t v) {
+  Box<D> b;
+  const int32_t* p = box + (uint64_t)v * 2 * D;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    b.lo[j] = p[j];
+    b.hi[j] = p[D + j];
+  }
+  return b;
+}
+
+template <int D, int KMAX>
+__global__ void __launch_bounds__(QTHREADS) k_knn_bb(QueryArgs a) {
+  const uint64_t qi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (qi >= a.nq) return;
+  int32_t q[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) q[j] = a.q[qi * D + j];
+  long long bd[KMAX];
+  uint32_t bi[KMAX];
+  const int k = a.k;
+  for (int i = 0; i < KMAX; ++i) {
+    bd[i] = LLONG_MAX;
+    bi[i] = 0xFFFFFFFFu;
+  }
+  uint32_t sv[QSTACK];
+  sv[0] = a.root;
+  int sp = 1;
+  while (sp > 0) {
+    const uint32_t v = sv[--sp];
+    const Box<D> b = stored_box<D>(a.box, v);
+    if (b.lo[0] > b.hi[0]) continue;  // an empty subtree
+    if (box_dist2<D>(q, b) > bd[k - 1]) continue;
+    const uint8_t dm = a.ndim[v];
+    const Node nd = a.nodes[v];
+    if (dm == PKD_LEAF) {
+      for (uint32_t i = 0; i < nd.size; ++i) {
+        const uint64_t g = (uint64_t)nd.a + i;
+        long long d2 = 0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          long long t = (long long)a.A.c[(uint64_t)j * a.A.stride + g] - q[j];
+          d2 += t * t;
+        }
+        const uint32_t id = a.A.id[g];
+        if (d2 > bd[k - 1] || (d2 == bd[k - 1] && id >= bi[k - 1])) continue;
+        int p = k - 1;
+        while (p > 0 && (bd[p - 1] > d2 || (bd[p - 1] == d2 && bi[p - 1] > id))) {
+          bd[p] = bd[p - 1];
+          bi[p] = bi[p - 1];
+          --p;
+        }
+        bd[p] = d2;
+        bi[p] = id;
+      }
+      continue;
+    }
+    if (sp + 2 > QSTACK) {
+      set_error(a.st, DERR_STACK, 904);
+      break;
+    }
+    const bool near_left = q[dm] < nd.split;
+    sv[sp++] = near_left ? nd.b : nd.a;  // far child first, near child next
+    sv[sp++] = near_left ? nd.a : nd.b;
+  }
+  for (int i = 0; i < k; ++i) {
+    a.out_d2[qi * k + i] = bd[i];
+    a.out_ids[qi * k + i] = bi[i];
+  }
+}
+
+// Range count (report = false) or report (true) with stored boxes.
+template <int D, bool REPORT>
+__global__ void __launch_bounds__(QTHREADS) k_range_bb(QueryArgs a, const uint64_t* offsets, uint32_t* out_ids) {
+  const uint64_t qi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (qi >= a.nq) return;
+  int32_t lo[D], hi[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    lo[j] = a.q[qi * D + j];
+    hi[j] = a.hi[qi * D + j];
+  }
+  uint32_t sv[QSTACK];
+  uint8_t sin[QSTACK];  // 1: inside the query box (report: walk without tests)
+  sv[0] = a.root;
+  sin[0] = 0;
+  int sp = 1;
+  unsigned long long cnt = 0;
+  uint64_t pos = REPORT ? offsets[qi] : 0;
+  const uint64_t end = REPORT ? offsets[qi + 1] : 0;
+  while (sp > 0) {
+    --sp;
+    const uint32_t v = sv[sp];
+    bool inside = sin[sp] != 0;
+    if (!inside) {
+      const Box<D> b = stored_box<D>(a.box, v);
+      bool disjoint = false;
+      inside = true;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        disjoint |= (b.hi[j] < lo[j]) | (b.lo[j] > hi[j]) | (b.hi[j] < b.lo[j]);
+        inside &= (b.lo[j] >= lo[j]) & (b.hi[j] <= hi[j]);
+      }
+      if (disjoint) continue;
+    }
+    const Node nd = a.nodes[v];
+    if (!REPORT && inside) {
+      cnt += nd.size;
+      continue;
+    }
+    const uint8_t dm = a.ndim[v];
+    if (dm == PKD_LEAF) {
+      for (uint32_t i = 0; i < nd.size; ++i) {
+        const uint64_t g = (uint64_t)nd.a + i;
+        bool in = true;
+        if (!inside) {
+#pragma unroll
+          for (int j = 0; j < D; ++j) {
+            const int32_t x = a.A.c[(uint64_t)j * a.A.stride + g];
+            in &= (x >= lo[j]) & (x <= hi[j]);
+          }
+        }
+        if (!in) continue;
+        if (REPORT) {
+          if (pos >= end) {  // more points than counted: the tree changed
+            set_error(a.st, DERR_STATE, 905);
+            return;
+          }
+          out_ids[pos++] = a.A.id[g];
+        } else {
+          ++cnt;
+        }
+      }
+      continue;
+    }
+    if (sp + 2 > QSTACK) {
+      set_error(a.st, DERR_STACK, 906);
+      return;
+    }
+    sv[sp] = nd.b;
+    sin[sp] = inside;
+    ++sp;
+    sv[sp] = nd.a;
+    sin[sp] = inside;
+    ++sp;
+  }
+  if (!REPORT) a.out_cnt[qi] = cnt;
+}
+
 // Exclusive scan of q 64-bit counts into offsets[0..q] (offsets[q] = total):
 // per-block sums, one block over the sums, then the blocks again.
 constexpr int SCAN64_THREADS = 256, SCAN64_PER = 8, SCAN64_TILE = SCAN64_THREADS * SCAN64_PER;
@@ -350,7 +509,8 @@ static void launch_report(const QueryArgs& a, const uint64_t* offsets, uint32_t*
   const unsigned g = (unsigned)((a.nq + QTHREADS - 1) / QTHREADS);
   KTimer kt;
   ktimer_begin(kt, "range_report", a.nq, s);
-  PKD_LAUNCH(k_range_report<D><<<g, QTHREADS, 0, s>>>(a, offsets, ids));
+  if (a.box) PKD_LAUNCH((k_range_bb<D, true><<<g, QTHREADS, 0, s>>>(a, offsets, ids)));
+  else PKD_LAUNCH(k_range_report<D><<<g, QTHREADS, 0, s>>>(a, offsets, ids));
   ktimer_end(kt);
 }
 
@@ -359,8 +519,13 @@ static void launch_knn(const QueryArgs& a, cudaStream_t s) {
   const unsigned g = (unsigned)((a.nq + QTHREADS - 1) / QTHREADS);
   KTimer kt;
   ktimer_begin(kt, "knn", a.nq, s);
-  if (a.k <= 16) PKD_LAUNCH(k_knn<D, 16><<<g, QTHREADS, 0, s>>>(a));
-  else PKD_LAUNCH(k_knn<D, 128><<<g, QTHREADS, 0, s>>>(a));
+  if (a.box) {
+    if (a.k <= 16) PKD_LAUNCH((k_knn_bb<D, 16><<<g, QTHREADS, 0, s>>>(a)));
+    else PKD_LAUNCH((k_knn_bb<D, 128><<<g, QTHREADS, 0, s>>>(a)));
+  } else {
+    if (a.k <= 16) PKD_LAUNCH(k_knn<D, 16><<<g, QTHREADS, 0, s>>>(a));
+    else PKD_LAUNCH(k_knn<D, 128><<<g, QTHREADS, 0, s>>>(a));
+  }
   ktimer_end(kt);
 }
 
@@ -369,7 +534,8 @@ static void launch_rc(const QueryArgs& a, cudaStream_t s) {
   const unsigned g = (unsigned)((a.nq + QTHREADS - 1) / QTHREADS);
   KTimer kt;
   ktimer_begin(kt, "range_count", a.nq, s);
-  PKD_LAUNCH(k_range_count<D><<<g, QTHREADS, 0, s>>>(a));
+  if (a.box) PKD_LAUNCH((k_range_bb<D, false><<<g, QTHREADS, 0, s>>>(a, nullptr, nullptr)));
+  else PKD_LAUNCH(k_range_count<D><<<g, QTHREADS, 0, s>>>(a));
   ktimer_end(kt);
 }
 
@@ -426,6 +592,7 @@ int pkd::knn_on(TreeMem& t, uint32_t root, const int32_t* queries, uint64_t q, i
   a.out_ids = out_ids;
   a.out_d2 = out_d2;
   a.st = t.st;
+  a.box = (t.bbox_on && root == t.root) ? t.bbox : nullptr;
   PKD_QDISPATCH(t.p.d, launch_knn, a, s);
   PKD_CUDA(cudaGetLastError());
   return PKD_OK;
@@ -456,6 +623,7 @@ int pkd_range_count(const pkd_tree* tc, const int32_t* lo, const int32_t* hi, ui
   a.nq = q;
   a.out_cnt = out_counts;
   a.st = t.st;
+  a.box = t.bbox_on ? t.bbox : nullptr;
   PKD_QDISPATCH(t.p.d, launch_rc, a, s);
   PKD_CUDA(cudaGetLastError());
   return PKD_OK;
@@ -495,6 +663,7 @@ int pkd_range_report(const pkd_tree* tc, const int32_t* lo, const int32_t* hi, u
   a.nq = q;
   a.out_cnt = counts;
   a.st = t.st;
+  a.box = t.bbox_on ? t.bbox : nullptr;
   PKD_QDISPATCH(t.p.d, launch_rc, a, s);
   PKD_LAUNCH(k_scan64_reduce<<<(unsigned)nb, SCAN64_THREADS, 0, s>>>(counts, q, partial));
   PKD_LAUNCH(k_scan64_partials<<<1, SCAN64_THREADS, 0, s>>>(partial, nb));

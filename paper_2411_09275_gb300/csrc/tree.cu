@@ -349,6 +349,7 @@ void tree_release(TreeMem& t) {
                   (void*)t.dead, (void*)t.aux, (void*)t.st})
     big_free(p, s);
   ids_release(t.ids, s);
+  big_free(t.bbox, s);
   pinned_put_after(s, t.st_host);
   t = TreeMem{};
 }

@@ -62,6 +62,11 @@ void ids_take(TreeMem& t, const uint32_t* ids, uint64_t m, Pts W, uint64_t* wslo
 void ids_restore(TreeMem& t, const uint64_t* wslots, uint64_t n, cudaStream_t s);
 int read_idflags(TreeMem& t, cudaStream_t s, int* flags);
 
+// Stored bounding boxes (boxes.cu): compute every node's tight box into
+// t.bbox (allocated or grown to node_cap), or free them.
+int boxes_compute(TreeMem& t, cudaStream_t s);
+void boxes_release(TreeMem& t, cudaStream_t s);
+
 // k-NN (see pkd_knn) on the tree rooted at node slot `root`.
 int knn_on(TreeMem& t, uint32_t root, const int32_t* queries, uint64_t q, int k, uint32_t* out_ids,
            int64_t* out_d2, cudaStream_t s);

@@ -1432,6 +1432,7 @@ int pkd_batch_insert(pkd_tree* tc, const int32_t* coords, const uint32_t* ids, u
   if (e == PKD_OK) {
     t.size += m;
     t.ids.live += m;
+    if (t.bbox_on) e = boxes_compute(t, s);
   } else {
     ids_unclaim(t, slots, m, s);
   }
@@ -1486,6 +1487,7 @@ int pkd_batch_delete(pkd_tree* tc, const uint32_t* ids, uint64_t m, uint64_t* n_
     t.size -= removed;
     t.ids.live -= removed;
     if (n_deleted) *n_deleted = removed;
+    if (t.bbox_on) e = boxes_compute(t, s);
   }
   return e;
 }

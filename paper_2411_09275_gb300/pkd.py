@@ -81,6 +81,8 @@ def lib():
         L.pkd_forest_free.argtypes = [vp]
         L.pkd_forest_free.restype = None
         L.pkd_export.argtypes = [vp, vp, vp, vp, P(u64), vp, vp, P(u64)]
+        L.pkd_set_bounding_boxes.argtypes = [vp, i32, vp]
+        L.pkd_export_boxes.argtypes = [vp, vp, vp, u64]
         L.pkd_size.restype = u64
         L.pkd_size.argtypes = [vp]
         L.pkd_height.argtypes = [vp, P(i32)]
@@ -92,7 +94,7 @@ def lib():
         L.pkd_kernel_timing.argtypes = [i32]
         L.pkd_kernel_stats.argtypes = [C.c_char_p, P(u64), P(C.c_double), P(u64)]
         for f in ("pkd_build", "pkd_batch_insert", "pkd_batch_delete", "pkd_knn", "pkd_range_count",
-                  "pkd_knn_ids_noalloc", "pkd_range_report", "pkd_build_forest", "pkd_forest_export", "pkd_forest_knn", "pkd_export", "pkd_height", "pkd_set_option", "pkd_kernel_timing",
+                  "pkd_knn_ids_noalloc", "pkd_range_report", "pkd_set_bounding_boxes", "pkd_export_boxes", "pkd_build_forest", "pkd_forest_export", "pkd_forest_knn", "pkd_export", "pkd_height", "pkd_set_option", "pkd_kernel_timing",
                   "pkd_kernel_stats"):
             getattr(L, f).restype = i32
         _lib = L
@@ -236,6 +238,20 @@ def pkd_forest_knn(forest, tree: int, queries: torch.Tensor, k: int, out_ids: to
 
 def pkd_forest_free(forest):
     lib().pkd_forest_free(forest)
+
+
+def pkd_set_bounding_boxes(tree, enable: bool, stream=None):
+    """Keep (True) or drop (False) the tight box of every node (Pkd-bb)."""
+    _check(lib().pkd_set_bounding_boxes(tree, 1 if enable else 0, _stream(stream)), "pkd_set_bounding_boxes")
+
+
+def pkd_export_boxes(tree, n_nodes: int, d: int):
+    """The stored boxes in pre-order: (lo, hi), each [n_nodes, d] int32."""
+    lo = np.empty((n_nodes, d), np.int32)
+    hi = np.empty((n_nodes, d), np.int32)
+    p = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    _check(lib().pkd_export_boxes(tree, p(lo), p(hi), n_nodes), "pkd_export_boxes")
+    return lo, hi
 
 
 def pkd_size(tree) -> int:

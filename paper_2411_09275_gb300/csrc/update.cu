@@ -790,6 +790,9 @@ struct Front {
   uint64_t off;
 };
 
+// Leaves of more than BIG_LEAF points are copied one block each.
+constexpr uint32_t BIG_LEAF = 1024;
+
 __global__ void k_front_init(const RebuildItem* it, const uint32_t* n, Front* f, uint32_t* nf) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool e = i < *n && it[i].old_live != 0;
@@ -801,23 +804,25 @@ __global__ void k_front_init(const RebuildItem* it, const uint32_t* n, Front* f,
 }
 
 __global__ void k_front_expand(const Front* f, const uint32_t* nf, Front* g, uint32_t* ng, Front* leaves,
-                               uint32_t* nleaves, const Node* nodes, const uint8_t* ndim, const uint32_t* aux,
-                               int use_aux, uint32_t cap, DevStatus* st) {
+                               uint32_t* nleaves, Front* bigleaves, uint32_t* nbig, const Node* nodes,
+                               const uint8_t* ndim, const uint32_t* aux, int use_aux, uint32_t cap, DevStatus* st) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool have = i < *nf;
   Front e{};
-  bool leaf = false;
+  bool leaf = false, big = false;
   if (have) {
     e = f[i];
     leaf = ndim[e.slot] == PKD_LEAF;
+    big = leaf && nodes[e.slot].size > BIG_LEAF;
   }
-  const uint32_t c[2] = {have && leaf ? 1u : 0u, have && !leaf ? 2u : 0u};
-  uint32_t* const ctrs[2] = {nleaves, ng};
-  uint32_t first[2];
-  block_reserve<2>(c, ctrs, first);
+  const uint32_t c[3] = {have && leaf && !big ? 1u : 0u, have && !leaf ? 2u : 0u, big ? 1u : 0u};
+  uint32_t* const ctrs[3] = {nleaves, ng, nbig};
+  uint32_t first[3];
+  block_reserve<3>(c, ctrs, first);
   if (!have) return;
   if (leaf) {
-    if (first[0] < cap) leaves[first[0]] = e;
+    const uint32_t k = big ? first[2] : first[0];
+    if (k < cap) (big ? bigleaves : leaves)[k] = e;
     else set_error(st, DERR_CAPACITY, 820);
     return;
   }
@@ -906,7 +911,9 @@ __global__ void __launch_bounds__(UPW_WARPS * 32) k_copy_leaves(const Front* lv,
 }
 
 // Insert: append each item's new batch points after its old ones (UPW
-// items per warp).
+// items per warp); items with more than NEW_BIG new points are left to
+// k_copy_new_flat.
+constexpr uint64_t NEW_BIG = 256;
 template <int D>
 __global__ void __launch_bounds__(UPW_WARPS * 32) k_copy_new(const RebuildItem* items, const uint32_t* n, Pts F,
                                                              Pts A) {
@@ -945,6 +952,7 @@ __global__ void __launch_bounds__(UPW_WARPS * 32) k_copy_new(const RebuildItem* 
   for (int q = 0; q < UPW; ++q) {
     const unsigned long long qws = __shfl_sync(FULL_MASK, ws, q), qcnt = __shfl_sync(FULL_MASK, cnt, q);
     const unsigned long long qd = __shfl_sync(FULL_MASK, dst0, q);
+    if (qcnt > NEW_BIG) continue;  // k_copy_new_flat copies these
     for (uint64_t i = lane; i < qcnt; i += 32) {
       const uint64_t src = qws + i, dst = qd + i;
 #pragma unroll
@@ -952,6 +960,103 @@ __global__ void __launch_bounds__(UPW_WARPS * 32) k_copy_new(const RebuildItem* 
       A.id[dst] = F.id[src];
     }
   }
+}
+
+// Insert: every new batch point of the rebuild items with more than NEW_BIG
+// of them, one thread each: cnt[i] = those points of item i (0 for the
+// others), off = their exclusive scan, so point j of
+// the flat order belongs to the item whose range [off[i], off[i] + cnt[i])
+// holds it (binary search).  A clustered batch can put millions of points
+// into one item; this keeps all of them in flight instead of one warp's.
+__global__ void k_item_newcounts(const RebuildItem* it, const uint32_t* n, uint32_t* cnt) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < *n) {
+    const uint64_t c = it[i].we - it[i].ws;
+    cnt[i] = c > NEW_BIG ? (uint32_t)c : 0u;  // the items k_copy_new leaves out
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_copy_new_flat(const RebuildItem* items, const uint32_t* n,
+                                                       const uint32_t* off, const uint32_t* cnt, uint64_t m, Pts F,
+                                                       Pts A) {
+  const uint32_t ni = *n;
+  if (ni == 0) return;
+  const uint64_t total = (uint64_t)off[ni - 1] + cnt[ni - 1];
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < total && j < m;
+       j += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t lo = 0, hi = ni;  // the last item whose offset is <= j
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (off[mid] <= j) lo = mid;
+      else hi = mid;
+    }
+    const RebuildItem it = items[lo];
+    const uint64_t k = j - off[lo];
+    const uint64_t src = it.ws + k, dst = it.pos + it.old_live + k;
+#pragma unroll
+    for (int q = 0; q < D; ++q) A.c[(uint64_t)q * A.stride + dst] = F.c[(uint64_t)q * F.stride + src];
+    A.id[dst] = F.id[src];
+  }
+}
+
+// Flattened leaves of more than BIG_LEAF points (heavy leaves, or leaves
+// after skewed updates), one block each: live points keep their leaf's
+// relative order, compacted by a block-wide ballot scan per 256 points.
+
+template <int D>
+__global__ void __launch_bounds__(256) k_copy_big_leaves(const Front* lv, const uint32_t* n,
+                                                         const RebuildItem* items, const Node* nodes, Pts A,
+                                                         const uint8_t* dead, int use_dead) {
+  __shared__ int wsum[8];
+  const uint32_t nn = *n;
+  for (uint32_t k = blockIdx.x; k < nn; k += gridDim.x) {
+    const Front e = lv[k];
+    const Node nd = nodes[e.slot];
+    const uint64_t d0 = items[e.item].pos + e.off;
+    uint64_t out = 0;
+    for (uint32_t base = 0; base < nd.size; base += 256) {
+      const uint32_t i = base + threadIdx.x;
+      const uint64_t src = (uint64_t)nd.a + i;
+      const bool keep = i < nd.size && !(use_dead && dead[src]);
+      int32_t x[D];
+      uint32_t id = 0;
+      if (keep) {
+#pragma unroll
+        for (int q = 0; q < D; ++q) x[q] = A.c[(uint64_t)q * A.stride + src];
+        id = A.id[src];
+      }
+      const unsigned m = __ballot_sync(FULL_MASK, keep);
+      if (lane_id() == 0) wsum[warp_id()] = __popc(m);
+      __syncthreads();
+      int before = 0, tot = 0;
+      for (int w = 0; w < 8; ++w) {
+        if (w < warp_id()) before += wsum[w];
+        tot += wsum[w];
+      }
+      if (keep) {
+        const uint64_t dst = d0 + out + before + __popc(m & lanemask_lt());
+#pragma unroll
+        for (int q = 0; q < D; ++q) A.c[(uint64_t)q * A.stride + dst] = x[q];
+        A.id[dst] = id;
+      }
+      out += tot;
+      __syncthreads();
+    }
+  }
+}
+
+template <int D>
+static void launch_copy_new_flat(const RebuildItem* items, const uint32_t* n, const uint32_t* off,
+                                 const uint32_t* cnt, uint64_t m, Pts F, Pts A, cudaStream_t s) {
+  const unsigned g = (unsigned)std::min<uint64_t>((m + 255) / 256, 152ull * 32);
+  PKD_LAUNCH(k_copy_new_flat<D><<<std::max(g, 1u), 256, 0, s>>>(items, n, off, cnt, m, F, A));
+}
+template <int D>
+static void launch_copy_big_leaves(const Front* lv, const uint32_t* n, uint32_t nh, const RebuildItem* items,
+                                   const Node* nodes, Pts A, const uint8_t* dead, int use_dead, cudaStream_t s) {
+  const unsigned g = std::min<uint32_t>(nh, 152u * 8);
+  PKD_LAUNCH(k_copy_big_leaves<D><<<std::max(g, 1u), 256, 0, s>>>(lv, n, items, nodes, A, dead, use_dead));
 }
 
 template <int D>
@@ -1346,12 +1451,13 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
     {
       // capacity: every node of the old subtrees appears once
       const uint64_t fcap = 4 * ((uint64_t)t.size + (uint64_t)nitems) + 1024;
-      Front *fa, *fb, *leaves;
+      Front *fa, *fb, *leaves, *bigleaves;
       PKD_TRY(sc.get(&fa, std::min<uint64_t>(fcap, 0xFFFFFFF0ull)));
       PKD_TRY(sc.get(&fb, std::min<uint64_t>(fcap, 0xFFFFFFF0ull)));
       PKD_TRY(sc.get(&leaves, std::min<uint64_t>(fcap, 0xFFFFFFF0ull)));
-      uint32_t* fc = dctr + 12;  // [0] cur, [1] next, [2] leaves
-      PKD_CUDA(cudaMemsetAsync(fc, 0, 12, s));
+      PKD_TRY(sc.get(&bigleaves, std::min<uint64_t>(fcap / BIG_LEAF + 16, 0xFFFFFFF0ull)));
+      uint32_t* fc = dctr + 12;  // [0] cur, [1] next, [2] leaves, [3] big leaves
+      PKD_CUDA(cudaMemsetAsync(fc, 0, 16, s));
       PKD_LAUNCH(k_front_init<<<gi, 128, 0, s>>>(items_out, d_nitems, fa, fc));
       PKD_CUDA(cudaMemcpyAsync(hctr + 12, fc, 12, cudaMemcpyDeviceToHost, s));
       PKD_CUDA(cudaStreamSynchronize(s));
@@ -1360,20 +1466,33 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
       for (int it = 0; nf > 0; ++it) {
         if (it > 100000) return PKD_EINTERNAL;
         PKD_CUDA(cudaMemsetAsync(fc + 1, 0, 4, s));
-        PKD_LAUNCH(k_front_expand<<<(nf + 127) / 128, 128, 0, s>>>(fa, fc, fb, fc + 1, leaves, fc + 2, t.nodes, t.ndim,
-                                                        t.aux, insert ? 0 : 1, fcap32, t.st));
+        PKD_LAUNCH(k_front_expand<<<(nf + 127) / 128, 128, 0, s>>>(fa, fc, fb, fc + 1, leaves, fc + 2, bigleaves,
+                                                                    fc + 3, t.nodes, t.ndim, t.aux, insert ? 0 : 1,
+                                                                    fcap32, t.st));
         PKD_CUDA(cudaMemcpyAsync(fc, fc + 1, 4, cudaMemcpyDeviceToDevice, s));
-        PKD_CUDA(cudaMemcpyAsync(hctr + 12, fc, 12, cudaMemcpyDeviceToHost, s));
+        PKD_CUDA(cudaMemcpyAsync(hctr + 12, fc, 16, cudaMemcpyDeviceToHost, s));
         PKD_CUDA(cudaStreamSynchronize(s));
         nf = hctr[12];
         std::swap(fa, fb);
       }
-      const uint32_t nleaves = hctr[14];
+      const uint32_t nleaves = hctr[14], nbigleaves = hctr[15];
       if (nleaves)
         PKD_DISPATCH_D(d, launch_copy_leaves, leaves, fc + 2, nleaves, items_out, t.nodes, t.A, t.dead,
                        insert ? 0 : 1, s);
+      if (nbigleaves)
+        PKD_DISPATCH_D(d, launch_copy_big_leaves, bigleaves, fc + 3, nbigleaves, items_out, t.nodes, t.A, t.dead,
+                       insert ? 0 : 1, s);
     }
-    if (insert) PKD_DISPATCH_D(d, launch_copy_new, items_out, d_nitems, nitems, F, t.A, s);
+    if (insert) {
+      uint32_t *ncnt, *noff, *npart;
+      PKD_TRY(sc.get(&ncnt, nitems));
+      PKD_TRY(sc.get(&noff, nitems));
+      PKD_TRY(sc.get(&npart, ((uint64_t)nitems + SCAN_TILE - 1) / SCAN_TILE + 1));
+      PKD_DISPATCH_D(d, launch_copy_new, items_out, d_nitems, nitems, F, t.A, s);
+      PKD_LAUNCH(k_item_newcounts<<<gi, 128, 0, s>>>(items_out, d_nitems, ncnt));
+      device_excl_scan(ncnt, noff, nitems, npart, s);
+      PKD_DISPATCH_D(d, launch_copy_new_flat, items_out, d_nitems, noff, ncnt, m, F, t.A, s);
+    }
     PKD_LAUNCH(k_item_leaves<<<gi, 128, 0, s>>>(items_out, d_nitems, t.nodes, t.ndim, (uint32_t)p.phi));
     trace_mark(s, "upd: flatten + gather");
     BuildJob job;

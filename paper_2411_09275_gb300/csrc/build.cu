@@ -519,6 +519,7 @@ __global__ void k_classify(const Seg* segs, uint32_t nseg, uint32_t cap, Seg* bi
                            Seg* wbase, uint32_t* nwbase, uint32_t wcap, Seg* tbase, uint32_t* ntbase,
                            uint32_t tcap, Seg* bbase, uint32_t* nbbase, uint32_t cap2, uint32_t tile,
                            uint32_t where, unsigned long long* base_pts, DevStatus* st) {
+  if (pkd_failed_block(st)) return;  // uniform: before the block-wide reservations
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   Seg s{};
   int kind = -1;  // 0 big, 1 one CTA (two per SM), 2 one warp, 3 small slice, 4 one CTA per SM
@@ -1036,6 +1037,7 @@ __global__ void k_finalize(RoundArgs r) {
 
 // Children segments, interior nodes and heavy leaves of every big segment.
 __global__ void k_emit(RoundArgs r, uint32_t* heavy_ctr) {
+  if (pkd_failed_block(r.st)) return;
   uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= *r.nbig) return;
   const Seg seg = r.big[s];
@@ -1082,6 +1084,7 @@ __global__ void k_emit(RoundArgs r, uint32_t* heavy_ctr) {
 
 // Heavy segments whose points are not yet in the arena.
 __global__ void k_copy_heavy(RoundArgs r) {
+  if (pkd_failed_block(r.st)) return;
   SieveTile t;
   if (!sieve_tile(r, t)) return;
   if (sk_state(r.skel[(uint64_t)t.s * r.HN + 1].y) != SK_HEAVY) return;
@@ -1327,6 +1330,7 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     if (nbig == 0) break;
 
     RoundArgs r{};
+    r.wait_cycles = knobs().wait_cycles;
     r.p = p;
     r.lam = lam;
     r.NB = NB;

@@ -73,6 +73,19 @@ __device__ __forceinline__ void set_error(DevStatus* st, int code, int detail) {
   if (atomicCAS(&st->err, 0, code) == 0) st->detail = detail;
 }
 
+// True once any kernel of the tree has recorded an error.  Kernels that
+// consume another kernel's counts or offsets (which a kernel that stopped
+// early may have left unwritten) test it first and do nothing, so a
+// failure never turns into reads or writes at garbage positions; the host
+// then reports the recorded error.
+__device__ __forceinline__ bool pkd_failed(const DevStatus* st) { return *(volatile const int*)&st->err != 0; }
+// The same test with one answer for the whole block (thread 0 reads the
+// status): the kernels that use it synchronise their threads, so all of
+// them must leave together.  Call it first, from every thread.
+__device__ __forceinline__ bool pkd_failed_block(const DevStatus* st) {
+  return __syncthreads_or(threadIdx.x == 0 && pkd_failed(st)) != 0;
+}
+
 // Sampling hash (SplitMix64's 64-bit finaliser, Steele/Lea/Flood 2014, as a
 // counter-based generator keyed by seed, depth and id).
 constexpr uint64_t K_DEPTH = 0x9E3779B97F4A7C15ull;

@@ -16,6 +16,7 @@ namespace pkd {
 // Tunables; none of them changes any result.
 struct Knobs {
   long long fail_alloc_after = -1;  // >= 0: allocations fail after this many more (fault injection)
+  long long wait_cycles = 4000000000ll;  // limit of the streaming sieve's waits (clock cycles, ~2 s)
   int base_cap = 0;   // 0: derived from d and the shared memory per block
   int skel_cap = 0;   // 0: derived
   int tile = 2048;    // points per tile in the sieve kernels

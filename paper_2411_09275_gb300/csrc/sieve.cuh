@@ -218,6 +218,7 @@ struct RoundArgs {
   uint32_t* shared_next;
   uint64_t shared_cap;
   DevStatus* st;
+  long long wait_cycles;  // limit of a streaming kernel's waits (clock cycles)
 };
 
 __device__ __forceinline__ uint32_t seg_of_tile(const uint32_t* tile0, uint32_t nseg, uint32_t tile) {
@@ -330,6 +331,7 @@ __global__ void __launch_bounds__(SIEVE_THREADS) k_count(RoundArgs r) {
 
 template <int D>
 __global__ void __launch_bounds__(SIEVE_THREADS) k_scatter(RoundArgs r) {
+  if (pkd_failed_block(r.st)) return;
   SieveTile t;
   if (!sieve_tile(r, t)) return;
   extern __shared__ __align__(16) uint8_t sm[];

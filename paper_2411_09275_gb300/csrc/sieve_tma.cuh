@@ -23,7 +23,8 @@
 
 namespace pkd {
 
-constexpr long long STM_WAIT_CYCLES = 4000000000ll;  // about 2 s at 2 GHz
+constexpr long long STM_WAIT_CYCLES = 4000000000ll;  // about 2 s at 2 GHz: the default limit, and the
+                                                     // fixed limit of the drain before a CTA exits
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -57,12 +58,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for phase `parity` of `bar`; false when it ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity` of `bar`; false when `limit` clock cycles
+// went by first (limit 0: one non-blocking test).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
+  if (mbar_test_wait(bar, parity)) return true;
+  if (limit <= 0) return false;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > STM_WAIT_CYCLES) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 
@@ -219,6 +231,17 @@ __device__ __forceinline__ uint32_t stm_advance(const RoundArgs& r, uint32_t s, 
   return s;
 }
 
+// Before the producer warp leaves (at the end of its tiles, or after a wait
+// ran out), every bulk copy it issued has landed: it waits, with the fixed
+// limit STM_WAIT_CYCLES, for the last phase of each stage's "full" barrier.
+// The CTA, and so its shared memory, lives as long as this warp does, so no
+// copy can land in shared memory that another CTA has been given.
+__device__ __forceinline__ void stm_drain(uint64_t* full, uint32_t issued, DevStatus* st) {
+  if (lane_id() != 0) return;
+  for (uint32_t k = issued > (uint32_t)STM_STAGES ? issued - STM_STAGES : 0; k < issued; ++k)
+    if (!mbar_wait(&full[k % STM_STAGES], (k / STM_STAGES) & 1, STM_WAIT_CYCLES)) set_error(st, DERR_TIMEOUT, 704);
+}
+
 // Producer warp main loop over the CTA's tiles.
 template <int D>
 __device__ void stm_producer(const RoundArgs& r, uint32_t tb, uint32_t te, bool ids, uint32_t* bufs, size_t swords,
@@ -226,14 +249,15 @@ __device__ void stm_producer(const RoundArgs& r, uint32_t tb, uint32_t te, bool 
                              uint8_t* sbk) {
   const uint32_t nb = *r.nbig;
   uint32_t s = seg_of_tile(r.tile0, nb, tb);
-  for (uint32_t k = 0; tb + k < te; ++k) {
+  uint32_t k = 0;
+  for (; tb + k < te; ++k) {
     const int stg = (int)(k % STM_STAGES);
     if (k >= (uint32_t)STM_STAGES) {
       bool ok = true;
-      if (lane_id() == 0) ok = mbar_wait(&empty[stg], ((k / STM_STAGES) - 1) & 1);
+      if (lane_id() == 0) ok = mbar_wait(&empty[stg], ((k / STM_STAGES) - 1) & 1, r.wait_cycles);
       if (!__shfl_sync(FULL_MASK, (int)ok, 0)) {
         if (lane_id() == 0) set_error(r.st, DERR_TIMEOUT, 702);
-        return;
+        break;
       }
       fence_proxy_async_smem();
     }
@@ -241,13 +265,15 @@ __device__ void stm_producer(const RoundArgs& r, uint32_t tb, uint32_t te, bool 
     stm_produce<D>(r, s, tb + k, ids, bufs + stg * swords, &recs[stg], &full[stg], gbs ? gbs + stg * r.NB : nullptr,
                    sbk ? sbk + (size_t)stg * r.TILE : nullptr);
   }
+  stm_drain(full, k, r.st);
 }
 
 // Consumers: wait for stage `stg` of tile k (thread 0 waits, the others
 // follow through the consumer barrier); false on time-out, for all of them.
-__device__ __forceinline__ bool stm_consume_wait(uint64_t* full, int stg, uint32_t k, int* flag, DevStatus* st) {
+__device__ __forceinline__ bool stm_consume_wait(uint64_t* full, int stg, uint32_t k, int* flag, DevStatus* st,
+                                                 long long limit) {
   if (threadIdx.x == 0) {
-    const bool ok = mbar_wait(&full[stg], (k / STM_STAGES) & 1);
+    const bool ok = mbar_wait(&full[stg], (k / STM_STAGES) & 1, limit);
     *flag = ok ? 1 : 0;
     if (!ok) set_error(st, DERR_TIMEOUT, 703);
   }
@@ -337,7 +363,7 @@ __global__ void __launch_bounds__(STM_THREADS) k_count_stream(RoundArgs r, uint3
   bool heavy = false;
   for (uint32_t k = 0; tb + k < te; ++k) {
     const int stg = (int)(k % STM_STAGES);
-    if (!stm_consume_wait(full, stg, k, flag, r.st)) return;
+    if (!stm_consume_wait(full, stg, k, flag, r.st, r.wait_cycles)) return;
     const StmStage<D> st = recs[stg];
     const uint32_t* buf = bufs + stg * swords;
     if (st.t.s != cur_seg) {  // uniform: every consumer reads the same record
@@ -393,6 +419,7 @@ static size_t count_stream_smem(const RoundArgs& r) {
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(STM_THREADS) k_scatter_stream(RoundArgs r, uint32_t ntiles) {
+  if (pkd_failed_block(r.st)) return;
   extern __shared__ __align__(16) uint8_t sm[];
   const int tilecap = r.TILE;
   const size_t stride = stm_stride(tilecap);
@@ -436,7 +463,7 @@ __global__ void __launch_bounds__(STM_THREADS) k_scatter_stream(RoundArgs r, uin
   bool heavy = false;
   for (uint32_t k = 0; tb + k < te; ++k) {
     const int stg = (int)(k % STM_STAGES);
-    if (!stm_consume_wait(full, stg, k, flag, r.st)) return;
+    if (!stm_consume_wait(full, stg, k, flag, r.st, r.wait_cycles)) return;
     const StmStage<D> st = recs[stg];
     const uint32_t* buf = bufs + stg * swords;
     if (st.t.s != cur_seg) {

@@ -618,6 +618,9 @@ int pkd_set_option(const char* name, int64_t value) {
     if (value < -1) return PKD_EINVAL;
     knobs().fail_alloc_after = value;
     g_fail_budget.store(value);
+  } else if (n == "wait_cycles") {
+    if (value < 0 || value > 4000000000000ll) return PKD_EINVAL;
+    knobs().wait_cycles = value;
   } else if (n == "tile") {
     if (value < 256 || value > 4096 || (value & (value - 1))) return PKD_EINVAL;
     knobs().tile = (int)value;

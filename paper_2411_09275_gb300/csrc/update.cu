@@ -55,7 +55,6 @@ struct UpdArgs {
   int lam, NB, HN, TILE;
   int insert;
   const Node* nodes;
-  Node* wnodes;
   const uint8_t* ndim;
   // this round
   const Seg* items;
@@ -69,6 +68,7 @@ struct UpdArgs {
   uint32_t* blen;    // [item][NB]
   uint32_t* link;    // [item][NB]
   uint32_t* fnd;     // [item][HN]
+  uint32_t* nsz;     // [item][HN] new size of a node that stays, or ~0 (applied at the end)
   uint32_t* iflag;   // [item]
   // next round
   Seg* next;
@@ -179,6 +179,7 @@ constexpr uint32_t SMALL_ITEM = 256;  // items up to this many points: one warp 
 // Bucket ranges of the big items from the bucket-major scan of the tile
 // histograms.
 __global__ void k_bucket_ranges(RoundArgs r, uint64_t* bstart, uint32_t* blen, const uint32_t* nbk) {
+  if (pkd_failed_block(r.st)) return;
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= *r.nbig) return;
   const Seg it = r.big[s];
@@ -206,6 +207,7 @@ template <int D>
 __global__ void __launch_bounds__(256) k_route_small(RoundArgs r, const uint32_t* small, const uint32_t* nsmall,
                                                      const Seg* items, const uint32_t* nbk, uint64_t* bstart,
                                                      uint32_t* blen, Pts F) {
+  if (pkd_failed_block(r.st)) return;
   extern __shared__ unsigned cnt_sm[];
   const uint32_t gw = blockIdx.x * (blockDim.x / 32) + warp_id();
   if (gw >= *nsmall) return;  // warp-uniform
@@ -285,6 +287,7 @@ static void launch_route_small(const RoundArgs& ra, const uint32_t* small, const
 
 // Next-round items and leaf groups from the bucket ranges.
 __global__ void __launch_bounds__(ITEM_WARPS * 32) k_route_emit(UpdArgs a) {
+  if (pkd_failed_block(a.st)) return;
   const uint32_t i = item_of_warp();
   if (i >= *a.nitems) return;  // warp-uniform
   const int lane = lane_id();
@@ -366,6 +369,7 @@ __global__ void __launch_bounds__(ITEM_WARPS * 32) k_route_emit(UpdArgs a) {
 // every point at its final position (the points of a leaf group are never
 // moved again).  Same tiling as the sieve kernels: one block per tile.
 __global__ void k_copy_round(RoundArgs r, Pts F) {
+  if (pkd_failed_block(r.st)) return;
   SieveTile t;
   if (!sieve_tile(r, t)) return;
   const int d = r.p.d;
@@ -518,6 +522,7 @@ __global__ void __launch_bounds__(UPW_WARPS * 32) k_match(LeafGroup* groups, con
 // Exact counts per skeleton node, bottom-up (rounds in reverse order; within
 // a skeleton, level by level from the deepest).
 __global__ void __launch_bounds__(ITEM_WARPS * 32) k_aggregate(UpdArgs a) {
+  if (pkd_failed_block(a.st)) return;
   const uint32_t i = item_of_warp();
   if (i >= *a.nitems) return;  // warp-uniform
   const int lane = lane_id();
@@ -561,6 +566,7 @@ __device__ void push_rebuild(const UpdArgs& a, uint32_t slot, uint32_t depth, ui
 // The item's skeleton, slots and counts are staged in shared memory first;
 // each level then loads only node sizes (both of a node's at once).
 __global__ void __launch_bounds__(ITEM_WARPS * 32) k_decide(UpdArgs a) {
+  if (pkd_failed_block(a.st)) return;
   extern __shared__ __align__(16) uint8_t dec_sm[];
   __shared__ uint32_t under_sh[ITEM_WARPS][64];
   const uint32_t i = item_of_warp();
@@ -616,7 +622,7 @@ __global__ void __launch_bounds__(ITEM_WARPS * 32) k_decide(UpdArgs a) {
       const uint32_t N = a.insert ? old + c : old - c;
       const uint32_t L = a.insert ? lold + f[c0] : lold - f[c0];
       if (N > 0 && is_balanced(L, N, a.p.alpha_num, a.p.alpha_den)) {
-        a.wnodes[slot].size = N;
+        a.nsz[(uint64_t)i * a.HN + v] = N;  // written to the node once nothing can fail
         continue;
       }
       // rebuild this subtree; the batch points below it are contiguous
@@ -638,6 +644,7 @@ __global__ void __launch_bounds__(ITEM_WARPS * 32) k_decide(UpdArgs a) {
 // points is a leaf again).
 __global__ void k_leaf_items(UpdArgs a, LeafGroup* groups, const uint32_t* ngroups, uint32_t* compact,
                              uint32_t* ncompact) {
+  if (pkd_failed_block(a.st)) return;  // uniform: before the block-wide reservation
   const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t ng = *ngroups;
   bool push = false, comp = false;
@@ -1079,6 +1086,32 @@ static void launch_copy_new(const RebuildItem* items, const uint32_t* n, uint32_
   PKD_LAUNCH(k_copy_new<D><<<upw_blocks(nh), UPW_WARPS * 32, 0, s>>>(items, n, F, A));
 }
 
+// The deferred size updates of the nodes that stay (k_decide), applied once
+// the update can no longer fail for lack of memory.
+__global__ void k_apply_sizes(const uint32_t* slots, const uint32_t* nsz, uint64_t n, Node* nodes) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && nsz[i] != 0xFFFFFFFFu) nodes[slots[i]].size = nsz[i];
+}
+
+// Node records of the rebuild items' root slots, saved before the rebuild
+// writes them and put back when it fails.
+__global__ void k_save_roots(const RebuildItem* it, const uint32_t* n, const Node* nodes, const uint8_t* ndim,
+                             Node* bn, uint8_t* bd) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < *n) {
+    bn[i] = nodes[it[i].slot];
+    bd[i] = ndim[it[i].slot];
+  }
+}
+__global__ void k_restore_roots(const RebuildItem* it, const uint32_t* n, Node* nodes, uint8_t* ndim, const Node* bn,
+                                const uint8_t* bd) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < *n) {
+    nodes[it[i].slot] = bn[i];
+    ndim[it[i].slot] = bd[i];
+  }
+}
+
 __global__ void k_clear_aux(const uint32_t* slots, uint64_t n, uint32_t* aux) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
@@ -1128,13 +1161,18 @@ static int ensure_capacity(TreeMem& t, uint64_t need, cudaStream_t s) {
   // delete scratch grows with the arena and keeps its marks
   uint8_t* dead2 = nullptr;
   uint32_t* aux2 = nullptr;
-  if (t.dead) {
-    PKD_CUDA(big_alloc((void**)&dead2, ncap, s));
+  if (t.dead) e = big_alloc((void**)&dead2, ncap, s);
+  if (e == cudaSuccess && t.aux) e = big_alloc((void**)&aux2, nnode * 4, s);
+  if (e != cudaSuccess) {  // nothing of the tree has changed
+    cudaGetLastError();
+    for (void* q : {(void*)A2.c, (void*)A2.id, (void*)n2, (void*)d2, (void*)dead2, (void*)aux2}) big_free(q, s);
+    return PKD_ENOMEM;
+  }
+  if (dead2) {
     PKD_CUDA(cudaMemsetAsync(dead2, 0, ncap, s));
     PKD_CUDA(cudaMemcpyAsync(dead2, t.dead, t.cap, cudaMemcpyDeviceToDevice, s));
   }
-  if (t.aux) {
-    PKD_CUDA(big_alloc((void**)&aux2, nnode * 4, s));
+  if (aux2) {
     PKD_CUDA(cudaMemsetAsync(aux2, 0, nnode * 4, s));
     PKD_CUDA(cudaMemcpyAsync(aux2, t.aux, t.node_cap * 4, cudaMemcpyDeviceToDevice, s));
   }
@@ -1168,6 +1206,7 @@ struct RouteRound {
   int2* skel;
   uint32_t* slots;
   uint32_t* fnd;
+  uint32_t* nsz;
   uint32_t* link;
   uint64_t* bstart;
   uint32_t* blen;
@@ -1226,7 +1265,6 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
   ua.TILE = TILE;
   ua.insert = insert ? 1 : 0;
   ua.nodes = t.nodes;
-  ua.wnodes = t.nodes;
   ua.ndim = t.ndim;
   ua.groups = groups;
   ua.ngroups = d_ngroups;
@@ -1270,6 +1308,8 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
     PKD_TRY(sc.get(&R.skel, (size_t)ncur * HN));
     PKD_TRY(sc.get(&R.slots, (size_t)ncur * HN));
     PKD_TRY(sc.get(&R.fnd, (size_t)ncur * HN));
+    PKD_TRY(sc.get(&R.nsz, (size_t)ncur * HN));
+    PKD_CUDA(cudaMemsetAsync(R.nsz, 0xFF, (size_t)ncur * HN * 4, s));
     PKD_TRY(sc.get(&R.link, (size_t)ncur * NB));
     PKD_TRY(sc.get(&R.bstart, (size_t)ncur * NB));
     PKD_TRY(sc.get(&R.blen, (size_t)ncur * NB));
@@ -1316,6 +1356,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
     }
 
     RoundArgs ra{};
+    ra.wait_cycles = knobs().wait_cycles;
     ra.p = p;
     ra.lam = lam;
     ra.NB = NB;
@@ -1374,6 +1415,24 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
   const uint32_t ngroups = groups_before;
   trace_mark(s, "upd: route");
 
+  // From here on, every exit clears the delete marks this batch sets (the
+  // scratch must be zero for the next call).
+  struct ClearMarks {
+    TreeMem& t;
+    const std::vector<RouteRound>& rounds;
+    int HN;
+    cudaStream_t s;
+    bool on;
+    ~ClearMarks() {
+      if (!on) return;
+      cudaMemsetAsync(t.dead, 0, t.cap, s);
+      for (const auto& R : rounds)
+        PKD_LAUNCH(k_clear_aux<<<(unsigned)(((uint64_t)R.n * HN + 255) / 256), 256, 0, s>>>(R.slots, (uint64_t)R.n * HN,
+                                                                                           t.aux));
+      // (a leaf group's slot is a heap bucket of its round, cleared above)
+    }
+  } clear_marks{t, rounds, HN, s, !insert};
+
   // ---- match (delete) ----
   if (!insert && ngroups)
     PKD_DISPATCH_D(d, launch_match, groups, d_ngroups, ngroups, t.nodes, t.A, F, t.dead, t.aux, s);
@@ -1393,8 +1452,10 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
   }
   uint32_t total_changed = 0;
   PKD_CUDA(cudaMemcpyAsync(&total_changed, rounds[0].fnd + 1, 4, cudaMemcpyDeviceToHost, s));
+  uint32_t* compact;
+  PKD_TRY(sc.get(&compact, std::max<uint32_t>(ngroups, 1)));
 
-  // ---- decide, top-down ----
+  // ---- decide, top-down (sizes of the nodes that stay are only recorded) ----
   for (size_t r = 0; r < rounds.size(); ++r) {
     RouteRound& R = rounds[r];
     ua.items = R.items;
@@ -1403,6 +1464,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
     ua.slots = R.slots;
     ua.link = R.link;
     ua.fnd = R.fnd;
+    ua.nsz = R.nsz;
     ua.bstart = R.bstart;
     ua.blen = R.blen;
     ua.iflag = R.iflag;
@@ -1418,8 +1480,6 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
     }
   }
   trace_mark(s, "upd: match+count+decide");
-  uint32_t* compact;
-  PKD_TRY(sc.get(&compact, std::max<uint32_t>(ngroups, 1)));
   if (ngroups) PKD_LAUNCH(k_leaf_items<<<(ngroups + 255) / 256, 256, 0, s>>>(ua, groups, d_ngroups, compact, d_ncompact));
   PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 40, cudaMemcpyDeviceToHost, s));
   PKD_CUDA(cudaStreamSynchronize(s));
@@ -1427,35 +1487,47 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
   const uint64_t total = *(unsigned long long*)(hctr + 6);
   const uint32_t ncompact = hctr[8];
   stat_items(insert ? "rebuilt_insert" : "rebuilt_delete", total);
-
-  // ---- delete: compact the reached leaves in place ----
-  if (ncompact)
-    PKD_DISPATCH_D(d, launch_compact, groups, compact, d_ncompact, ncompact, t.nodes, t.A, t.dead, s);
+  trace_mark(s, "upd: leaf items");
 
   // ---- rebuild ----
-  trace_mark(s, "upd: leaf items + compact");
+  // Nothing the tree shows has changed so far: the new sizes are recorded,
+  // the leaves to compact are listed.  Every allocation of the rebuild comes
+  // first; the new subtrees are built in fresh arena positions (past top);
+  // the rebuild items' root records are saved and put back if the rebuild
+  // fails, so PKD_ENOMEM leaves the tree as it was.
   if (nitems) {
     PKD_TRY(ensure_capacity(t, total, s));
     trace_mark(s, "upd: ensure capacity");
-    uint32_t *isz, *ioff, *ipart;
+    uint32_t *isz, *ioff, *ipart, *saved_next;
     PKD_TRY(sc.get(&isz, nitems));
     PKD_TRY(sc.get(&ioff, nitems));
     PKD_TRY(sc.get(&ipart, ((uint64_t)nitems + SCAN_TILE - 1) / SCAN_TILE + 1));
     Seg* segs;
     PKD_TRY(sc.get(&segs, nitems));
+    Node* saved_nodes;
+    uint8_t* saved_dims;
+    PKD_TRY(sc.get(&saved_nodes, nitems));
+    PKD_TRY(sc.get(&saved_dims, nitems));
+    PKD_TRY(sc.get(&saved_next, 1));
+    const uint64_t fcap = 4 * ((uint64_t)t.size + (uint64_t)nitems) + 1024;
+    Front *fa, *fb, *leaves, *bigleaves;
+    PKD_TRY(sc.get(&fa, std::min<uint64_t>(fcap, 0xFFFFFFF0ull)));
+    PKD_TRY(sc.get(&fb, std::min<uint64_t>(fcap, 0xFFFFFFF0ull)));
+    PKD_TRY(sc.get(&leaves, std::min<uint64_t>(fcap, 0xFFFFFFF0ull)));
+    PKD_TRY(sc.get(&bigleaves, std::min<uint64_t>(fcap / BIG_LEAF + 16, 0xFFFFFFF0ull)));
+    uint32_t *ncnt = nullptr, *noff = nullptr, *npart = nullptr;
+    if (insert) {
+      PKD_TRY(sc.get(&ncnt, nitems));
+      PKD_TRY(sc.get(&noff, nitems));
+      PKD_TRY(sc.get(&npart, ((uint64_t)nitems + SCAN_TILE - 1) / SCAN_TILE + 1));
+    }
     const unsigned gi = (nitems + 127) / 128;
     PKD_LAUNCH(k_item_sizes<<<gi, 128, 0, s>>>(items_out, d_nitems, isz));
     device_excl_scan(isz, ioff, nitems, ipart, s);
     PKD_LAUNCH(k_item_pos<<<gi, 128, 0, s>>>(items_out, d_nitems, ioff, t.top, segs, (uint32_t)p.phi));
-    // flatten the old subtrees breadth first
+    // flatten the old subtrees breadth first (capacity: every node of the
+    // old subtrees appears once)
     {
-      // capacity: every node of the old subtrees appears once
-      const uint64_t fcap = 4 * ((uint64_t)t.size + (uint64_t)nitems) + 1024;
-      Front *fa, *fb, *leaves, *bigleaves;
-      PKD_TRY(sc.get(&fa, std::min<uint64_t>(fcap, 0xFFFFFFF0ull)));
-      PKD_TRY(sc.get(&fb, std::min<uint64_t>(fcap, 0xFFFFFFF0ull)));
-      PKD_TRY(sc.get(&leaves, std::min<uint64_t>(fcap, 0xFFFFFFF0ull)));
-      PKD_TRY(sc.get(&bigleaves, std::min<uint64_t>(fcap / BIG_LEAF + 16, 0xFFFFFFF0ull)));
       uint32_t* fc = dctr + 12;  // [0] cur, [1] next, [2] leaves, [3] big leaves
       PKD_CUDA(cudaMemsetAsync(fc, 0, 16, s));
       PKD_LAUNCH(k_front_init<<<gi, 128, 0, s>>>(items_out, d_nitems, fa, fc));
@@ -1484,33 +1556,41 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
                        insert ? 0 : 1, s);
     }
     if (insert) {
-      uint32_t *ncnt, *noff, *npart;
-      PKD_TRY(sc.get(&ncnt, nitems));
-      PKD_TRY(sc.get(&noff, nitems));
-      PKD_TRY(sc.get(&npart, ((uint64_t)nitems + SCAN_TILE - 1) / SCAN_TILE + 1));
       PKD_DISPATCH_D(d, launch_copy_new, items_out, d_nitems, nitems, F, t.A, s);
       PKD_LAUNCH(k_item_newcounts<<<gi, 128, 0, s>>>(items_out, d_nitems, ncnt));
       device_excl_scan(ncnt, noff, nitems, npart, s);
       PKD_DISPATCH_D(d, launch_copy_new_flat, items_out, d_nitems, noff, ncnt, m, F, t.A, s);
     }
-    PKD_LAUNCH(k_item_leaves<<<gi, 128, 0, s>>>(items_out, d_nitems, t.nodes, t.ndim, (uint32_t)p.phi));
     trace_mark(s, "upd: flatten + gather");
+    PKD_LAUNCH(k_save_roots<<<gi, 128, 0, s>>>(items_out, d_nitems, t.nodes, t.ndim, saved_nodes, saved_dims));
+    PKD_CUDA(cudaMemcpyAsync(saved_next, t.shared_next, 4, cudaMemcpyDeviceToDevice, s));
     BuildJob job;
     job.base = t.top;
     job.extent = std::max<uint64_t>(total, 1);
     job.dsegs = segs;
     job.dsegs_n = nitems;
-    PKD_TRY(run_build(t, job, s));
+    const int eb = run_build(t, job, s);
+    if (eb != PKD_OK) {
+      PKD_LAUNCH(k_restore_roots<<<gi, 128, 0, s>>>(items_out, d_nitems, t.nodes, t.ndim, saved_nodes, saved_dims));
+      cudaMemcpyAsync(t.shared_next, saved_next, 4, cudaMemcpyDeviceToDevice, s);
+      return eb;
+    }
+    PKD_LAUNCH(k_item_leaves<<<gi, 128, 0, s>>>(items_out, d_nitems, t.nodes, t.ndim, (uint32_t)p.phi));
     trace_mark(s, "upd: rebuild");
-    t.top += total;
   }
 
-  // ---- delete: clear the marks this batch set ----
+  // ---- the visible changes: nothing below allocates ----
+  if (ncompact)  // delete: the reached leaves lose their deleted points
+    PKD_DISPATCH_D(d, launch_compact, groups, compact, d_ncompact, ncompact, t.nodes, t.A, t.dead, s);
+  for (const auto& R : rounds)
+    PKD_LAUNCH(k_apply_sizes<<<(unsigned)(((uint64_t)R.n * HN + 255) / 256), 256, 0, s>>>(R.slots, R.nsz,
+                                                                                         (uint64_t)R.n * HN, t.nodes));
+  t.top += total;
+  clear_marks.on = false;
   if (!insert) {
     PKD_CUDA(cudaMemsetAsync(t.dead, 0, t.cap, s));
     for (auto& R : rounds)
       PKD_LAUNCH(k_clear_aux<<<(unsigned)(((uint64_t)R.n * HN + 255) / 256), 256, 0, s>>>(R.slots, (uint64_t)R.n * HN, t.aux));
-    // (a leaf group's slot is a heap bucket of its round, cleared above)
   }
   PKD_CUDA(cudaStreamSynchronize(s));
   trace_mark(s, "upd: cleanup");

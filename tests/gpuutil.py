@@ -35,6 +35,10 @@ def oparams(p) -> O.Params:
                     seed=p.seed)
 
 
+# library options whose default is not 0
+DEFAULTS = {"tile": 2048, "wait_cycles": 4_000_000_000, "fail_alloc_after": -1}
+
+
 @contextlib.contextmanager
 def knobs(**kw):
     from paper_2411_09275_gb300 import pkd
@@ -45,7 +49,7 @@ def knobs(**kw):
         yield
     finally:
         for k in kw:
-            pkd.pkd_set_option(k, 0 if k != "tile" else 2048)
+            pkd.pkd_set_option(k, DEFAULTS.get(k, 0))
 
 
 def make_points(kind: str, n: int, d: int, seed: int) -> np.ndarray:

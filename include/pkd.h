@@ -232,6 +232,15 @@ int pkd_forest_knn(const pkd_forest* forest, uint32_t tree, const int32_t* queri
                    uint32_t* out_ids, int64_t* out_d2, void* stream);
 void pkd_forest_free(pkd_forest* forest);
 
+/* Device memory on the current device as the library sees it (HOST
+ * outputs, each optional): the driver's free bytes, the bytes the library's
+ * stream-ordered pool holds and of those the bytes in use (blocks kept in
+ * the library's large-block cache for reuse count as in use), the cached
+ * bytes, and `available` = free + the pool's unused bytes + the cache, the
+ * memory a new request can draw on.  A server admits requests by it. */
+int pkd_mem_info(uint64_t* device_free, uint64_t* pool_reserved, uint64_t* pool_used, uint64_t* cached,
+                 uint64_t* available);
+
 /* Human-readable text for an error code. */
 const char* pkd_strerror(int code);
 

@@ -630,6 +630,32 @@ int pkd_set_option(const char* name, int64_t value) {
   return PKD_OK;
 }
 
+int pkd_mem_info(uint64_t* device_free, uint64_t* pool_reserved, uint64_t* pool_used, uint64_t* cached,
+                 uint64_t* available) {
+  size_t fr = 0, tot = 0;
+  PKD_CUDA(cudaMemGetInfo(&fr, &tot));
+  cudaMemPool_t pool = mem_pool();
+  uint64_t res = 0, used = 0;
+  cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &res);
+  cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  uint64_t cache = 0;
+  {
+    std::lock_guard<std::mutex> g(g_big_mu);
+    for (const CachedBlock& b : g_big_cache)
+      if (b.dev == dev) cache += b.bytes;
+  }
+  // blocks in the large-block cache are counted as used by the pool
+  const uint64_t pool_free = res > used ? res - used : 0;
+  if (device_free) *device_free = fr;
+  if (pool_reserved) *pool_reserved = res;
+  if (pool_used) *pool_used = used;
+  if (cached) *cached = cache;
+  if (available) *available = (uint64_t)fr + pool_free + cache;
+  return PKD_OK;
+}
+
 int pkd_kernel_timing(int enable) {
   std::lock_guard<std::mutex> g(g_tmu);
   resolve_pending();

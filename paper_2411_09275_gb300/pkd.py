@@ -82,6 +82,7 @@ def lib():
         L.pkd_forest_free.restype = None
         L.pkd_export.argtypes = [vp, vp, vp, vp, P(u64), vp, vp, P(u64)]
         L.pkd_set_bounding_boxes.argtypes = [vp, i32, vp]
+        L.pkd_mem_info.argtypes = [P(u64), P(u64), P(u64), P(u64), P(u64)]
         L.pkd_export_boxes.argtypes = [vp, vp, vp, u64]
         L.pkd_size.restype = u64
         L.pkd_size.argtypes = [vp]
@@ -94,7 +95,7 @@ def lib():
         L.pkd_kernel_timing.argtypes = [i32]
         L.pkd_kernel_stats.argtypes = [C.c_char_p, P(u64), P(C.c_double), P(u64)]
         for f in ("pkd_build", "pkd_batch_insert", "pkd_batch_delete", "pkd_knn", "pkd_range_count",
-                  "pkd_knn_ids_noalloc", "pkd_range_report", "pkd_set_bounding_boxes", "pkd_export_boxes", "pkd_build_forest", "pkd_forest_export", "pkd_forest_knn", "pkd_export", "pkd_height", "pkd_set_option", "pkd_kernel_timing",
+                  "pkd_knn_ids_noalloc", "pkd_range_report", "pkd_set_bounding_boxes", "pkd_export_boxes", "pkd_mem_info", "pkd_build_forest", "pkd_forest_export", "pkd_forest_knn", "pkd_export", "pkd_height", "pkd_set_option", "pkd_kernel_timing",
                   "pkd_kernel_stats"):
             getattr(L, f).restype = i32
         _lib = L
@@ -252,6 +253,14 @@ def pkd_export_boxes(tree, n_nodes: int, d: int):
     p = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
     _check(lib().pkd_export_boxes(tree, p(lo), p(hi), n_nodes), "pkd_export_boxes")
     return lo, hi
+
+
+def pkd_mem_info() -> dict:
+    """Device memory as the library sees it (bytes): free, pool_reserved,
+    pool_used, cached and available (free + unused pool + cache)."""
+    v = [C.c_uint64(0) for _ in range(5)]
+    _check(lib().pkd_mem_info(*[C.byref(x) for x in v]), "pkd_mem_info")
+    return dict(zip(("free", "pool_reserved", "pool_used", "cached", "available"), (int(x.value) for x in v)))
 
 
 def pkd_size(tree) -> int:

@@ -103,3 +103,40 @@ def test_summary_has_percentiles():
     _, out = _run(pkd, serve, X, reqs, streams=2, realtime=True)
     s = serve.summarize(out, 1.0)
     assert s["all"]["count"] == 20 and s["all"]["p99_ms"] >= s["all"]["p50_ms"] >= 0
+
+
+def test_queries_admitted_during_an_update_see_exactly_the_earlier_updates():
+    # a large insert, then k-NN batches that arrive while it runs, then a
+    # delete and more queries: the batches are admitted before the insert
+    # finishes (the loop does not wait for updates) and each answer equals
+    # the oracle's on the updates admitted before it
+    pkd, serve = _mods()
+    d, n = 3, 400000
+    X = make_points("uniform", n, d, 21)
+    p = pkd.Params(d=d, phi=16, lam=4, sigma_log2=3, sigma_os=8)
+    Y = I.uniform(300000, d, 22)
+    yid = np.arange(n, n + 300000, dtype=np.uint32)
+    kill = np.arange(0, n, 5, dtype=np.uint32)
+    plan = [("insert", 0.0, Y, yid, 0)]
+    plan += [("knn", 1e-4 * (q + 1), I.uniform(500, d, 30 + q), None, 10) for q in range(6)]
+    plan += [("delete", 2e-3, None, kill, 0)]
+    plan += [("knn", 2e-3 + 1e-4 * (q + 1), I.uniform(500, d, 40 + q), None, 5) for q in range(4)]
+    tree = pkd.Tree(to_dev(X), None, p)
+    R = [serve.Request(kind, t, to_dev(C) if C is not None else None, ids_dev(ids) if ids is not None else None, k)
+         for kind, t, C, ids, k in plan]
+    out = serve.Server(tree, streams=4, realtime=True).run(R)
+    tree.close()
+    ins = out[0]
+    during = [r for r in out[1:7] if r.admitted < ins.done]
+    assert during, "no query was admitted while the insert ran"
+    o = O.OracleTree(X, None, oparams(p))
+    for (kind, _, C, ids, k), res in zip(plan, out):
+        if kind == "insert":
+            o.insert(C, ids)
+        elif kind == "delete":
+            assert res.n_deleted == o.delete(ids) == len(ids)
+        else:
+            wi, wd = o.knn(C, k)
+            assert np.array_equal(res.knn_d2.cpu().numpy(), wd)
+            assert np.array_equal(res.knn_ids.cpu().numpy().view(np.uint32), wi)
+    o.close()

@@ -1,12 +1,15 @@
 """Autotuner for the build: picks lambda (skeleton levels per sieve round),
-the sample rate 2^-sigma_log2 and the sieve tile size by timing pkd_build on
-a sample of the workload.
+the sample rate 2^-sigma_log2, the leaf wrap phi, the sieve tile size and the
+shared-memory base-case cutoff by timing pkd_build on a sample of the
+workload.
 
-lambda and the sample rate change the tree (they are parameters of Alg. 1;
-the paper fixes lambda = 6 and sigma = 32 by a similar sweep, Sec. 5
-"Parameter Choosing"), so whatever is chosen is recorded with the results
-and parity is checked with the chosen values.  The tile size is a tuning
-knob that never changes the tree.
+lambda, the sample rate and phi change the tree (they are parameters of
+Alg. 1; the paper fixes lambda = 6, sigma = 32 and phi = 32 by a similar
+sweep, Sec. 5 "Parameter Choosing"), so whatever is chosen is recorded with
+the results and parity is checked with the chosen values.  The tile size and
+the base-case cutoff (the largest subproblem finished by one CTA in shared
+memory; 0 = as large as shared memory allows) are tuning knobs that never
+change the tree.
 """
 from __future__ import annotations
 
@@ -24,26 +27,32 @@ class Candidate:
     lam: int
     sigma_log2: int
     tile: int
+    phi: int = 32
+    base_cap: int = 0
 
     def params(self, d: int, **kw) -> pkd.Params:
-        return pkd.Params(d=d, lam=self.lam, sigma_log2=self.sigma_log2, **kw)
+        return pkd.Params(d=d, lam=self.lam, sigma_log2=self.sigma_log2, phi=self.phi, **kw)
 
 
-def grid(lambdas=(5, 6, 7, 8), sigma_log2s=(5, 6, 7, 8), tiles=(1024, 2048, 4096)) -> list[Candidate]:
+def grid(lambdas=(5, 6, 7, 8), sigma_log2s=(5, 6, 7, 8), tiles=(1024, 2048, 4096), phis=(32,),
+         base_caps=(0,)) -> list[Candidate]:
     """Every combination, lambda in [1, 10], sigma_log2 in [0, 30], tiles
-    powers of two in [256, 4096] (the library's ranges)."""
+    powers of two in [256, 4096], phi >= 1, base_cap 0 or in [64, 16384]
+    (the library's ranges)."""
     out = []
-    for lam, sl, tile in itertools.product(lambdas, sigma_log2s, tiles):
-        if not (1 <= lam <= 10 and 0 <= sl <= 30 and 256 <= tile <= 4096 and tile & (tile - 1) == 0):
-            raise ValueError(f"candidate out of range: lam={lam} sigma_log2={sl} tile={tile}")
-        out.append(Candidate(lam, sl, tile))
+    for lam, sl, tile, phi, bc in itertools.product(lambdas, sigma_log2s, tiles, phis, base_caps):
+        if not (1 <= lam <= 10 and 0 <= sl <= 30 and 256 <= tile <= 4096 and tile & (tile - 1) == 0
+                and phi >= 1 and (bc == 0 or 64 <= bc <= 16384)):
+            raise ValueError(f"candidate out of range: lam={lam} sigma_log2={sl} tile={tile} phi={phi} "
+                             f"base_cap={bc}")
+        out.append(Candidate(lam, sl, tile, phi, bc))
     return out
 
 
 def pick(times: dict[Candidate, float]) -> Candidate:
     """The fastest candidate; ties go to the earliest in (lam, sigma_log2,
-    tile) order, so the choice is reproducible."""
-    return min(times, key=lambda c: (times[c], c.lam, c.sigma_log2, c.tile))
+    tile, phi, base_cap) order, so the choice is reproducible."""
+    return min(times, key=lambda c: (times[c], c.lam, c.sigma_log2, c.tile, c.phi, c.base_cap))
 
 
 def time_build(coords: torch.Tensor, cand: Candidate, reps: int = 2, stream=None) -> float:
@@ -51,6 +60,7 @@ def time_build(coords: torch.Tensor, cand: Candidate, reps: int = 2, stream=None
     d = coords.shape[1]
     st = stream or torch.cuda.current_stream()
     pkd.pkd_set_option("tile", cand.tile)
+    pkd.pkd_set_option("base_cap", cand.base_cap)
     try:
         pkd.pkd_free(pkd.pkd_build(coords, None, cand.params(d), st))  # warm-up
         ts = []
@@ -66,6 +76,7 @@ def time_build(coords: torch.Tensor, cand: Candidate, reps: int = 2, stream=None
         return float(np.median(ts))
     finally:
         pkd.pkd_set_option("tile", 2048)
+        pkd.pkd_set_option("base_cap", 0)
 
 
 def tune(coords: torch.Tensor, candidates: list[Candidate] | None = None, reps: int = 2) -> dict:

@@ -14,6 +14,12 @@ def test_grid_is_the_cartesian_product_in_range():
         A.grid((11,), (6,), (2048,))
     with pytest.raises(ValueError):
         A.grid((6,), (6,), (3000,))
+    with pytest.raises(ValueError):
+        A.grid((6,), (6,), (2048,), phis=(0,))
+    with pytest.raises(ValueError):
+        A.grid((6,), (6,), (2048,), base_caps=(32,))
+    g = A.grid((6,), (6,), (2048,), phis=(16, 32), base_caps=(0, 1024))
+    assert len(g) == 4 and {(c.phi, c.base_cap) for c in g} == {(16, 0), (16, 1024), (32, 0), (32, 1024)}
 
 
 def test_pick_fastest_then_smallest_parameters():
@@ -23,5 +29,5 @@ def test_pick_fastest_then_smallest_parameters():
 
 
 def test_candidate_params_carry_the_choice():
-    p = A.Candidate(7, 5, 1024).params(3, phi=16)
+    p = A.Candidate(7, 5, 1024, phi=16).params(3)
     assert (p.d, p.lam, p.sigma_log2, p.phi) == (3, 7, 5, 16)

@@ -15,8 +15,8 @@ def test_tune_then_build_with_choice_matches_oracle():
 
     X = make_points("varden", 60000, 2, 41)
     g = to_dev(X)
-    res = A.tune(g, A.grid((4, 6), (3, 6), (1024, 2048)), reps=1)
-    assert len(res["table"]) == 8 and all(r["ms"] > 0 for r in res["table"])
+    res = A.tune(g, A.grid((4, 6), (3, 6), (1024, 2048), phis=(16, 32), base_caps=(0, 1024)), reps=1)
+    assert len(res["table"]) == 32 and all(r["ms"] > 0 for r in res["table"])
     best = A.Candidate(**res["best"])
     assert res["table"][0]["ms"] == min(r["ms"] for r in res["table"])
     p = best.params(2)

@@ -15,9 +15,14 @@
  *    keeps; input buffers may be reused once the call has returned.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Builds
  *    and batch updates return after their work on `stream` has completed
- *    (they read device-side counts between sieve rounds).  Queries are
- *    asynchronous: their outputs are valid once `stream` has been
- *    synchronised.
+ *    (they report device-side failures).  A build's sieve rounds are decided
+ *    on the device: the rounds, the skeleton levels within them and the
+ *    exact levels run from one CUDA graph launch whose conditional nodes
+ *    test counts the kernels leave in device memory, so the host does not
+ *    wait between rounds (option "graph_rounds").  The rebuilds inside a
+ *    batch update run the same way; the update's own routing rounds read
+ *    their counts on the host.  Queries are asynchronous: their outputs are
+ *    valid once `stream` has been synchronised.
  *  - A pkd_tree is not thread-safe: one call at a time per tree, except
  *    that queries on an unchanging tree may overlap.
  *  - Return value 0 (PKD_OK) or one of the error codes below; device-side
@@ -258,6 +263,11 @@ const char* pkd_strerror(int code);
  *   "base_kernel" shared-memory base case: 0 sorts each subproblem once per
  *                dimension and splits by lookups (default), 1 selects every
  *                splitter by a radix select
+ *   "graph_rounds" 1 (default): a build's rounds run from one CUDA graph whose
+ *                WHILE / IF nodes test device-side counts, and its base cases
+ *                are persistent launches over device-side lists; 0: the same
+ *                kernels with the host reading the counts after every step
+ *                (one stream synchronisation per round and skeleton level)
  * Returns PKD_EINVAL for an unknown name or an out-of-range value. */
 int pkd_set_option(const char* name, int64_t value);
 
@@ -275,7 +285,10 @@ int pkd_set_option(const char* name, int64_t value);
  * and "rebuilt_delete" (points in the subtrees an update rebuilt, one entry
  * per call), "delete_gather" (ids a delete found and looked up).  The name
  * "allocations" reports, in *launches, every device or pinned-host allocation
- * the library made since it was loaded. */
+ * the library made since it was loaded; "graph_builds" the builds (and update
+ * rebuilds) whose rounds ran from one graph launch.  With graph rounds,
+ * "launches" counts each recorded kernel node once, although a node in a
+ * loop body runs once per iteration. */
 int pkd_kernel_timing(int enable);
 int pkd_kernel_stats(const char* name, uint64_t* launches, double* total_ms, uint64_t* items);
 

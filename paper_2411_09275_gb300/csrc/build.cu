@@ -19,12 +19,14 @@
 // (smem_build.cuh).  When a skeleton root is a bucket (too few or identical
 // samples) the subproblem takes one exact level on its own points; when its
 // points are all identical it becomes one heavy leaf.
+#include <chrono>
 #include <map>
 #include <mutex>
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
 
+#include "flow.cuh"
 #include "sieve_tma.cuh"
 #include "smem_sorted.cuh"
 
@@ -111,15 +113,37 @@ __device__ void load_segment(const SmemArgs& a, const Seg& seg, int32_t* X, uint
   }
 }
 
+// The entries of a list, one per CTA at a time, from a persistent grid:
+// every CTA takes the next entry from the grab counter (zeroed before the
+// launch) until the list is done, so a grid of resident CTAs serves a list
+// whose length only the device knows (the skeleton jobs of a graph's loop
+// bodies).  The entry's work `f` may return early but only uniformly over
+// the CTA.
+// The list length is re-read for every entry, so that nothing stays live
+// across an entry's work.
+__device__ __forceinline__ uint32_t list_len(const uint32_t* n, uint32_t cap) { return min(*n, cap); }
+
+template <class F>
+__device__ __forceinline__ void for_each_entry(const uint32_t* n, uint32_t cap, uint32_t* grab, F&& f) {
+  __shared__ uint32_t nxt;
+  for (;;) {
+    __syncthreads();  // the previous entry is done with shared memory
+    if (threadIdx.x == 0) nxt = atomicAdd(grab, 1u);
+    __syncthreads();
+    const uint32_t i = nxt;
+    if (i >= list_len(n, cap)) return;
+    f(i);
+  }
+}
+
 template <int D>
-__global__ void __launch_bounds__(SM_THREADS, 1) k_smem_build(SmemArgs a) {
-  if (blockIdx.x >= *a.nsegs) return;
+__device__ __forceinline__ void smem_build_one(const SmemArgs& a, uint32_t sid) {
   extern __shared__ __align__(16) uint8_t sm[];
-  const Seg seg = a.segs[blockIdx.x];
+  const Seg seg = a.segs[sid];
   const int cap = a.cap, tid = threadIdx.x;
   SmemPtrs q = carve(sm, cap, D);
   if (seg.len > (uint32_t)cap) {
-    if (tid == 0) set_error(a.st, DERR_CAPACITY, (int)blockIdx.x);
+    if (tid == 0) set_error(a.st, DERR_CAPACITY, (int)sid);
     return;
   }
   const int n = (int)seg.len;
@@ -147,17 +171,21 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_smem_build(SmemArgs a) {
   if (tid == 0) atomicMax(&a.st->max_depth, q.ctl->maxd);
 }
 
+template <int D>
+__global__ void __launch_bounds__(SM_THREADS, 1) k_smem_build(SmemArgs a) {
+  if (blockIdx.x < list_len(a.nsegs, a.list_cap)) smem_build_one<D>(a, blockIdx.x);
+}
+
 // The base case on presorted lists (one CTA per segment of at most cap
 // points): load, sort every dimension once, then split by lookups and stable
 // list partitions.  Instantiated for one CTA per SM (the largest capacity)
 // and for two (half the shared memory and at most 64 registers a thread);
 // the segment lists of the two launches are separated when the segments are
 // classified.
-template <int D, int MINB>
-__global__ void __launch_bounds__(SS_THREADS, MINB) k_smem_sorted(SmemArgs a) {
-  if (blockIdx.x >= *a.nsegs) return;
+template <int D>
+__device__ __forceinline__ void smem_sorted_one(const SmemArgs& a, uint32_t sid) {
   extern __shared__ __align__(16) uint8_t sm[];
-  const Seg seg = a.segs[blockIdx.x];
+  const Seg seg = a.segs[sid];
   const int cap = a.cap, tid = threadIdx.x;
   const SortedLayout Lo = sorted_layout(cap, D);
   int32_t* X = (int32_t*)(sm + Lo.X);
@@ -166,7 +194,7 @@ __global__ void __launch_bounds__(SS_THREADS, MINB) k_smem_sorted(SmemArgs a) {
   STask* wstack = (STask*)(sm + Lo.stack);
   SmemCtl* ctl = (SmemCtl*)(sm + Lo.ctl);
   if (seg.len > (uint32_t)cap) {
-    if (tid == 0) set_error(a.st, DERR_CAPACITY, 400000 + (int)blockIdx.x);
+    if (tid == 0) set_error(a.st, DERR_CAPACITY, 400000 + (int)sid);
     return;
   }
   const int n = (int)seg.len;
@@ -294,15 +322,21 @@ __global__ void __launch_bounds__(SS_THREADS, MINB) k_smem_sorted(SmemArgs a) {
   if (tid == 0) atomicMax(&a.st->max_depth, ctl->maxd);
 }
 
+// One CTA per entry of the list (a persistent loop around this body costs
+// registers the two-CTAs-per-SM form does not have: it would spill).
+template <int D, int MINB>
+__global__ void __launch_bounds__(SS_THREADS, MINB) k_smem_sorted(SmemArgs a) {
+  if (blockIdx.x < list_len(a.nsegs, a.list_cap)) smem_sorted_one<D>(a, blockIdx.x);
+}
+
 template <int D>
-__global__ void __launch_bounds__(SM_THREADS, 1) k_smem_skel(SmemArgs a) {
-  if (blockIdx.x >= *a.njobs) return;
+__device__ __forceinline__ void smem_skel_one(const SmemArgs& a, uint32_t ji) {
   extern __shared__ __align__(16) uint8_t sm[];
-  const SkelJob jb = a.jobs[blockIdx.x];
+  const SkelJob jb = a.jobs[ji];
   const int cap = a.cap, tid = threadIdx.x;
   SmemPtrs q = carve(sm, cap, D);
   if (jb.n > (uint32_t)cap) {
-    if (tid == 0) set_error(a.st, DERR_CAPACITY, 200000 + (int)blockIdx.x);
+    if (tid == 0) set_error(a.st, DERR_CAPACITY, 200000 + (int)ji);
     return;
   }
   const int n = (int)jb.n;
@@ -322,6 +356,11 @@ __global__ void __launch_bounds__(SM_THREADS, 1) k_smem_skel(SmemArgs a) {
   cx.min_split = (int)jb.min_split;
   Task root{0, (uint16_t)n, 0, 0, jb.j, 0, jb.h};
   run_team_tasks<true, D>(cx, root, q.whist, q.wred, q.wstack, SM_NW);
+}
+
+template <int D>
+__global__ void __launch_bounds__(SM_THREADS, 1) k_smem_skel(SmemArgs a) {
+  for_each_entry(a.njobs, a.list_cap, a.grab, [&](uint32_t ji) { smem_skel_one<D>(a, ji); });
 }
 
 // One warp per small subproblem (a leaf rebuilt with a few new points, or a
@@ -373,7 +412,7 @@ __global__ void __launch_bounds__(WK_WARPS * 32, 4) k_smem_warp(SmemArgs a) {
   q.wred = nullptr;
   q.wstack = (Task*)(base + Lo.stack);
   q.ctl = (SmemCtl*)(base + Lo.ctl);
-  const uint32_t nsegs = *a.nsegs;
+  const uint32_t nsegs = list_len(a.nsegs, a.list_cap);
   if (lane == 0) q.ctl->maxd = 0;
   __syncwarp();
   // every warp takes segments in turn (a grid of a few CTAs per SM)
@@ -415,33 +454,33 @@ __global__ void __launch_bounds__(WK_WARPS * 32, 4) k_smem_warp(SmemArgs a) {
   if (lane == 0) atomicMax(&a.st->max_depth, q.ctl->maxd);
 }
 
+// Launch of a shared-memory kernel with its dynamic shared memory.
+template <class K>
+static void launch_with_smem(K kern, int* set, uint32_t nblocks, int threads, size_t smb, cudaStream_t s,
+                             const SmemArgs& a) {
+  if (*set < (int)smb) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+    *set = (int)smb;
+  }
+  if (nblocks == 0) return;
+  PKD_LAUNCH(kern<<<nblocks, threads, smb, s>>>(a));
+}
+
 template <int D>
 static void launch_smem_build(const SmemArgs& a, uint32_t nblocks, size_t smb, cudaStream_t s) {
   static int set = 0;
-  if (set < (int)smb) {
-    cudaFuncSetAttribute(k_smem_build<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
-    set = (int)smb;
-  }
-  PKD_LAUNCH(k_smem_build<D><<<nblocks, SM_THREADS, smb, s>>>(a));
+  launch_with_smem(k_smem_build<D>, &set, nblocks, SM_THREADS, smb, s, a);
 }
 
 template <int D>
 static void launch_smem_sorted(const SmemArgs& a, uint32_t nblocks, size_t smb, cudaStream_t s) {
   static int set = 0;
-  if (set < (int)smb) {
-    cudaFuncSetAttribute(k_smem_sorted<D, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
-    set = (int)smb;
-  }
-  PKD_LAUNCH((k_smem_sorted<D, 1><<<nblocks, SS_THREADS, smb, s>>>(a)));
+  launch_with_smem(k_smem_sorted<D, 1>, &set, nblocks, SS_THREADS, smb, s, a);
 }
 template <int D>
 static void launch_smem_sorted2(const SmemArgs& a, uint32_t nblocks, size_t smb, cudaStream_t s) {
   static int set = 0;
-  if (set < (int)smb) {
-    cudaFuncSetAttribute(k_smem_sorted<D, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
-    set = (int)smb;
-  }
-  PKD_LAUNCH((k_smem_sorted<D, 2><<<nblocks, SS_THREADS, smb, s>>>(a)));
+  launch_with_smem(k_smem_sorted<D, 2>, &set, nblocks, SS_THREADS, smb, s, a);
 }
 
 // A second stream of the current device, created on first use.
@@ -514,39 +553,47 @@ static void launch_smem_warp(const SmemArgs& a, uint32_t nblocks, size_t smb, cu
 // points *pts) and segments finished in shared memory, appended to the
 // persistent base lists: one CTA per SM (longer than cap2), two CTAs per SM
 // (*nbase), one warp (*nwbase) and one warp with a small slice (*ntbase).
-__global__ void k_classify(const Seg* segs, uint32_t nseg, uint32_t cap, Seg* big, uint32_t* ctr,
+__global__ void k_classify(const RoundDyn* dyn, const uint32_t* sel, const uint32_t* ncur, uint32_t cur_cap,
+                           uint32_t cap, Seg* big, uint32_t big_cap, uint32_t* ctr,
                            unsigned long long* pts, Seg* base, uint32_t* nbase, uint32_t base_cap,
                            Seg* wbase, uint32_t* nwbase, uint32_t wcap, Seg* tbase, uint32_t* ntbase,
                            uint32_t tcap, Seg* bbase, uint32_t* nbbase, uint32_t cap2, uint32_t tile,
-                           uint32_t where, unsigned long long* base_pts, DevStatus* st) {
+                           unsigned long long* base_pts, DevStatus* st) {
   if (pkd_failed_block(st)) return;  // uniform: before the block-wide reservations
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  Seg s{};
-  int kind = -1;  // 0 big, 1 one CTA (two per SM), 2 one warp, 3 small slice, 4 one CTA per SM
-  if (i < nseg) {
-    s = segs[i];
-    if (s.len != SEG_SKIP) {
-      s.where = where;
-      kind = s.len > cap ? 0 : (s.len > cap2 ? 4 : (s.len > wcap ? 1 : (s.len > tcap ? 2 : 3)));
+  const RoundDyn& dy = dyn[*sel];
+  const Seg* segs = dy.cur;
+  const uint32_t where = (uint32_t)dy.src_where;
+  const uint32_t nseg = min(*ncur, cur_cap);
+  // the grid strides over the segments, a block-uniform loop
+  for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < nseg; i0 += gridDim.x * blockDim.x) {
+    const uint32_t i = i0 + threadIdx.x;
+    Seg s{};
+    int kind = -1;  // 0 big, 1 one CTA (two per SM), 2 one warp, 3 small slice, 4 one CTA per SM
+    if (i < nseg) {
+      s = segs[i];
+      if (s.len != SEG_SKIP) {
+        s.where = where;
+        kind = s.len > cap ? 0 : (s.len > cap2 ? 4 : (s.len > wcap ? 1 : (s.len > tcap ? 2 : 3)));
+      }
     }
-  }
-  // the list counters and point sums are updated once per block
-  const uint32_t c[6] = {kind == 0, kind == 1, kind == 2, kind == 3, kind == 4,
-                         kind == 0 ? (s.len + tile - 1) / tile : 0u};
-  uint32_t* const ctrs[6] = {&ctr[0], nbase, nwbase, ntbase, nbbase, &ctr[2]};
-  uint32_t first[6];
-  block_reserve<6>(c, ctrs, first);
-  const unsigned long long len = kind >= 0 ? s.len : 0ull;
-  const unsigned long long v[4] = {kind == 0 ? len : 0ull, (kind == 1 || kind == 4) ? len : 0ull,
-                                   kind == 2 ? len : 0ull, kind == 3 ? len : 0ull};
-  unsigned long long* const sums[4] = {pts, &base_pts[0], &base_pts[1], &base_pts[2]};
-  block_add64<4>(v, sums);
-  if (kind == 0) {
-    big[first[0]] = s;
-  } else if (kind > 0) {
-    const uint32_t b = first[kind];
-    if (b < base_cap) (kind == 1 ? base : (kind == 2 ? wbase : (kind == 3 ? tbase : bbase)))[b] = s;
-    else set_error(st, DERR_CAPACITY, 300 + kind);
+    // the list counters and point sums are updated once per block
+    const uint32_t c[6] = {kind == 0, kind == 1, kind == 2, kind == 3, kind == 4,
+                           kind == 0 ? (s.len + tile - 1) / tile : 0u};
+    uint32_t* const ctrs[6] = {&ctr[0], nbase, nwbase, ntbase, nbbase, &ctr[2]};
+    uint32_t first[6];
+    block_reserve<6>(c, ctrs, first);
+    const unsigned long long len = kind >= 0 ? s.len : 0ull;
+    const unsigned long long v[4] = {kind == 0 ? len : 0ull, (kind == 1 || kind == 4) ? len : 0ull,
+                                     kind == 2 ? len : 0ull, kind == 3 ? len : 0ull};
+    unsigned long long* const sums[4] = {pts, &base_pts[0], &base_pts[1], &base_pts[2]};
+    block_add64<4>(v, sums);
+    if (kind == 0) {
+      if (first[0] < big_cap) big[first[0]] = s;
+    } else if (kind > 0) {
+      const uint32_t b = first[kind];
+      if (b < base_cap) (kind == 1 ? base : (kind == 2 ? wbase : (kind == 3 ? tbase : bbase)))[b] = s;
+      else set_error(st, DERR_CAPACITY, 300 + kind);
+    }
   }
 }
 
@@ -563,7 +610,7 @@ constexpr int SAMPLE_PER = 16;      // points per thread (tiles of up to 4096)
 constexpr int SAMPLE_LIST = 8192;   // sampled positions held before a flush
 constexpr int SAMPLE_CTAS_PER_SM = 4;
 
-__device__ __forceinline__ void sample_flush(const RoundArgs& r, const Seg& seg, uint32_t s, const uint32_t* lst,
+__device__ __forceinline__ void sample_flush(const RoundArgs& r, const Src& src, const Seg& seg, uint32_t s, const uint32_t* lst,
                                              int nl, uint32_t* base_sh) {
   if (threadIdx.x == 0) *base_sh = atomicAdd(&r.scnt[s], (uint32_t)nl);
   __syncthreads();
@@ -571,15 +618,17 @@ __device__ __forceinline__ void sample_flush(const RoundArgs& r, const Seg& seg,
   const int d = r.p.d;
   for (int i = threadIdx.x; i < nl; i += SAMPLE_THREADS) {
     const uint64_t g = seg.start + lst[i];
-    for (int j = 0; j < d; ++j) r.samp.c[(uint64_t)j * r.samp.stride + o0 + i] = r.src.x(d, j, g);
+    for (int j = 0; j < d; ++j) r.samp.c[(uint64_t)j * r.samp.stride + o0 + i] = src.x(d, j, g);
   }
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(RoundArgs r, uint32_t ntiles) {
+__global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(RoundArgs r, uint32_t ntiles_host) {
   __shared__ uint32_t sh[33];
   __shared__ uint32_t base_sh;
   __shared__ uint32_t lst[SAMPLE_LIST];
+  const Src src = round_src(r);
+  const uint32_t ntiles = round_tiles(r, ntiles_host);
   const uint32_t per_cta = (ntiles + gridDim.x - 1) / gridDim.x;
   const uint32_t tb = min(ntiles, blockIdx.x * per_cta), te = min(ntiles, tb + per_cta);
   if (tb >= te) return;
@@ -592,7 +641,7 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(RoundArgs r, uint32_t
   int nl = 0;  // uniform
   for (uint32_t tile = tb; tile < te; ++tile) {
     if (s + 1 < nb && r.tile0[s + 1] <= tile) {  // the next segment with tiles
-      if (nl) sample_flush(r, seg, s, lst, nl, &base_sh);
+      if (nl) sample_flush(r, src, seg, s, lst, nl, &base_sh);
       nl = 0;
       do {
         ++s;
@@ -606,14 +655,14 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(RoundArgs r, uint32_t
     if (first >= seg.len) continue;
     const int cnt = (int)min((uint64_t)r.TILE, (uint64_t)seg.len - first);
     if (nl + cnt > SAMPLE_LIST) {
-      sample_flush(r, seg, s, lst, nl, &base_sh);
+      sample_flush(r, src, seg, s, lst, nl, &base_sh);
       nl = 0;
     }
     uint32_t ids[SAMPLE_PER];
 #pragma unroll
     for (int k = 0; k < SAMPLE_PER; ++k) {
       const int i = k * SAMPLE_THREADS + threadIdx.x;
-      if (i < cnt) ids[k] = r.src.id(seg.start + first + (uint64_t)i);
+      if (i < cnt) ids[k] = src.id(seg.start + first + (uint64_t)i);
     }
     unsigned fl = 0;
 #pragma unroll
@@ -629,7 +678,7 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(RoundArgs r, uint32_t
       if (fl & (1u << k)) lst[nl + (int)off + q++] = (uint32_t)(first + (uint64_t)(k * SAMPLE_THREADS + threadIdx.x));
     nl += (int)total;
   }
-  if (nl) sample_flush(r, seg, s, lst, nl, &base_sh);
+  if (nl) sample_flush(r, src, seg, s, lst, nl, &base_sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -667,9 +716,13 @@ struct JobArgs {
   SkelJob* small;
   uint32_t small_cap, big_cap;
   DevStatus* st;
+  const uint32_t* jtiles;  // tiles of the current level's jobs (written by k_job_tiles)
 };
 
-__global__ void k_job_tiles(const SkelJob* jobs, const uint32_t* njobs, uint32_t* jtile0) {
+// Grid-stride loop over i in [0, n).
+#define PKD_FOR(i, n) for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
+
+__global__ void k_job_tiles(const SkelJob* jobs, const uint32_t* njobs, uint32_t* jtile0, uint32_t* total) {
   __shared__ uint32_t sh[33];
   const uint32_t n = *njobs;
   uint32_t c = 0;
@@ -681,11 +734,11 @@ __global__ void k_job_tiles(const SkelJob* jobs, const uint32_t* njobs, uint32_t
     if (i < n) jtile0[i] = c + e;
     c += tot;
   }
+  if (threadIdx.x == 0) *total = c;
 }
 
 __global__ void k_job_init(JobArgs a) {
-  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= *a.njobs) return;
+  PKD_FOR(i, *a.njobs) {
   JobState& s = a.js[i];
   for (int j = 0; j < PKD_DMAX; ++j) {
     s.mn[j] = INT32_MAX;
@@ -695,6 +748,7 @@ __global__ void k_job_init(JobArgs a) {
   s.lcur = s.rcur = 0;
   s.fixmin = INT32_MAX;
   for (int b = 0; b < 256; ++b) a.jhist[(uint64_t)i * 256 + b] = 0;
+  }
 }
 
 struct JobTile {
@@ -704,19 +758,29 @@ struct JobTile {
   int cnt;
 };
 
-__device__ __forceinline__ bool job_tile(const JobArgs& a, JobTile& t) {
+__device__ __forceinline__ bool job_tile(const JobArgs& a, JobTile& t, uint32_t tile) {
   const uint32_t nj = *a.njobs;
-  t.job = seg_of_tile(a.jtile0, nj, blockIdx.x);
+  t.job = seg_of_tile(a.jtile0, nj, tile);
   t.jb = a.jobs[t.job];
-  t.first = (uint64_t)(blockIdx.x - a.jtile0[t.job]) * JOB_TILE;
+  t.first = (uint64_t)(tile - a.jtile0[t.job]) * JOB_TILE;
   if (t.first >= t.jb.n) return false;
   t.cnt = (int)min((uint64_t)JOB_TILE, (uint64_t)t.jb.n - t.first);
   return true;
 }
 
-__global__ void __launch_bounds__(JOB_THREADS) k_job_stats(JobArgs a) {
+// The grid strides over the level's tiles, one tile per block at a time.
+#define PKD_JOB_TILE_KERNEL(name, body_fn)                                  \
+  __global__ void __launch_bounds__(JOB_THREADS) name(JobArgs a) {          \
+    const uint32_t nt = *a.jtiles;                                          \
+    for (uint32_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {        \
+      body_fn(a, tile);                                                     \
+      __syncthreads();                                                      \
+    }                                                                       \
+  }
+
+__device__ __forceinline__ void job_stats_tile(const JobArgs& a, uint32_t tile) {
   JobTile t;
-  if (!job_tile(a, t)) return;
+  if (!job_tile(a, t, tile)) return;
   __shared__ int smn[PKD_DMAX][JOB_THREADS / 32], smx[PKD_DMAX][JOB_THREADS / 32];
   const Pts& B = a.sb[t.jb.buf];
   const int d = a.d;
@@ -746,10 +810,10 @@ __global__ void __launch_bounds__(JOB_THREADS) k_job_stats(JobArgs a) {
     atomicMax(&a.js[t.job].mx[j], mx);
   }
 }
+PKD_JOB_TILE_KERNEL(k_job_stats, job_stats_tile)
 
 __global__ void k_job_choose(JobArgs a) {
-  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= *a.njobs) return;
+  PKD_FOR(i, *a.njobs) {
   const SkelJob jb = a.jobs[i];
   JobState& s = a.js[i];
   int dim = -1;
@@ -761,11 +825,12 @@ __global__ void k_job_choose(JobArgs a) {
   s.mask = 0;
   s.less = 0;
   s.eq = 0;
+  }
 }
 
-__global__ void __launch_bounds__(JOB_THREADS) k_job_hist(JobArgs a, int pass) {
+__device__ __forceinline__ void job_hist_tile(const JobArgs& a, uint32_t tile, int pass) {
   JobTile t;
-  if (!job_tile(a, t)) return;
+  if (!job_tile(a, t, tile)) return;
   const JobState& s = a.js[t.job];
   if (!s.split) return;
   __shared__ unsigned h[256];
@@ -784,12 +849,20 @@ __global__ void __launch_bounds__(JOB_THREADS) k_job_hist(JobArgs a, int pass) {
     if (h[b]) atomicAdd(&a.jhist[(uint64_t)t.job * 256 + b], h[b]);
 }
 
+__global__ void __launch_bounds__(JOB_THREADS) k_job_hist(JobArgs a, int pass) {
+  const uint32_t nt = *a.jtiles;
+  for (uint32_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    job_hist_tile(a, tile, pass);
+    __syncthreads();
+  }
+}
+
 // One warp per job.
 __global__ void k_job_pick(JobArgs a, int pass) {
-  const uint32_t job = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (job >= *a.njobs) return;
+  const uint32_t nj = *a.njobs;
+  for (uint32_t job = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; job < nj; job += (gridDim.x * blockDim.x) >> 5) {
   JobState& s = a.js[job];
-  if (!s.split) return;
+  if (!s.split) continue;
   unsigned* h = a.jhist + (uint64_t)job * 256;
   int digit, below, eq;
   warp_find_digit(h, s.k, digit, below, eq);
@@ -803,11 +876,12 @@ __global__ void k_job_pick(JobArgs a, int pass) {
     s.less += below;
     s.eq = eq;
   }
+  }
 }
 
-__global__ void __launch_bounds__(JOB_THREADS) k_job_minabove(JobArgs a) {
+__device__ __forceinline__ void job_minabove_tile(const JobArgs& a, uint32_t tile) {
   JobTile t;
-  if (!job_tile(a, t)) return;
+  if (!job_tile(a, t, tile)) return;
   JobState& s = a.js[t.job];
   if (!s.split || s.less != 0) return;
   const Pts& B = a.sb[t.jb.buf];
@@ -821,12 +895,12 @@ __global__ void __launch_bounds__(JOB_THREADS) k_job_minabove(JobArgs a) {
   m = warp_min(m);
   if (lane_id() == 0 && m != INT32_MAX) atomicMin(&s.fixmin, m);
 }
+PKD_JOB_TILE_KERNEL(k_job_minabove, job_minabove_tile)
 
 __global__ void k_job_fix(JobArgs a) {
-  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= *a.njobs) return;
+  PKD_FOR(i, *a.njobs) {
   JobState& s = a.js[i];
-  if (!s.split) return;
+  if (!s.split) continue;
   if (s.less == 0) {
     // nothing strictly below the median: split at the next distinct value;
     // the left side is then exactly the copies of the minimum.
@@ -836,11 +910,12 @@ __global__ void k_job_fix(JobArgs a) {
     s.x = (int)s.prefix;
     s.L = s.less;
   }
+  }
 }
 
-__global__ void __launch_bounds__(JOB_THREADS) k_job_partition(JobArgs a) {
+__device__ __forceinline__ void job_partition_tile(const JobArgs& a, uint32_t tile) {
   JobTile t;
-  if (!job_tile(a, t)) return;
+  if (!job_tile(a, t, tile)) return;
   JobState& s = a.js[t.job];
   if (!s.split) return;
   __shared__ uint32_t sh[33];
@@ -872,6 +947,7 @@ __global__ void __launch_bounds__(JOB_THREADS) k_job_partition(JobArgs a) {
     for (int j = 0; j < d; ++j) O.c[(uint64_t)j * O.stride + dst] = B.c[(uint64_t)j * B.stride + src];
   }
 }
+PKD_JOB_TILE_KERNEL(k_job_partition, job_partition_tile)
 
 __device__ void push_job(const JobArgs& a, const SkelJob& c) {
   int2* sk = a.skel + (uint64_t)c.seg * a.HN;
@@ -898,18 +974,17 @@ __device__ void push_job(const JobArgs& a, const SkelJob& c) {
 }
 
 __global__ void k_job_children(JobArgs a) {
-  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= *a.njobs) return;
+  PKD_FOR(i, *a.njobs) {
   const SkelJob jb = a.jobs[i];
   const JobState& s = a.js[i];
   int2* sk = a.skel + (uint64_t)jb.seg * a.HN;
   if (!s.split) {
     sk[jb.h] = make_int2(0, sk_meta(SK_BUCKET, 0, 0));
-    return;
+    continue;
   }
   if (s.L <= 0 || (uint32_t)s.L >= jb.n) {
     set_error(a.st, DERR_STATE, 500);
-    return;
+    continue;
   }
   sk[jb.h] = make_int2(s.x, sk_meta(SK_INTERNAL, s.dim, 0));
   SkelJob l = jb, r = jb;
@@ -922,12 +997,12 @@ __global__ void k_job_children(JobArgs a) {
   r.n = jb.n - (uint32_t)s.L;
   push_job(a, l);
   push_job(a, r);
+  }
 }
 
 // Root jobs: one per big segment, on its sample.
 __global__ void k_root_jobs(RoundArgs r, JobArgs a, int exact_pass) {
-  uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= *r.nbig) return;
+  PKD_FOR(s, *r.nbig) {
   const Seg seg = r.big[s];
   SkelJob jb;
   jb.seg = s;
@@ -942,44 +1017,46 @@ __global__ void k_root_jobs(RoundArgs r, JobArgs a, int exact_pass) {
     jb.lam = (uint8_t)r.lam;
     jb.min_split = 2u * (uint32_t)r.p.sigma_os;
   } else {
-    if (r.exact[s] != 1) return;
+    if (r.exact[s] != 1) continue;
     jb.n = seg.len;  // every point of the segment was copied into the sample buffer
     jb.lam = 1;
     jb.min_split = 2;
   }
   push_job(a, jb);
+  }
 }
 
 // Segments whose skeleton root is a bucket take one exact level next.
 __global__ void k_mark_exact(RoundArgs r, uint32_t* ctr) {
-  uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= *r.nbig) return;
-  const int m = r.skel[(uint64_t)s * r.HN + 1].y;
-  if (r.exact[s] == 0 && sk_state(m) == SK_BUCKET) {
-    r.exact[s] = 1;
-    atomicAdd(ctr, 1u);
+  PKD_FOR(s, *r.nbig) {
+    const int m = r.skel[(uint64_t)s * r.HN + 1].y;
+    if (r.exact[s] == 0 && sk_state(m) == SK_BUCKET) {
+      r.exact[s] = 1;
+      atomicAdd(ctr, 1u);
+    }
   }
 }
 
-__global__ void k_copy_exact(RoundArgs r) {
-  const uint32_t nb = *r.nbig;
-  const uint32_t s = seg_of_tile(r.tile0, nb, blockIdx.x);
-  if (r.exact[s] != 1) return;
-  const Seg seg = r.big[s];
-  const uint64_t first = (uint64_t)(blockIdx.x - r.tile0[s]) * r.TILE;
-  if (first >= seg.len) return;
-  const int cnt = (int)min((uint64_t)r.TILE, (uint64_t)seg.len - first);
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-    const uint64_t g = seg.start + first + i;
-    for (int j = 0; j < r.p.d; ++j) r.samp.c[(uint64_t)j * r.samp.stride + g] = r.src.x(r.p.d, j, g);
+__global__ void k_copy_exact(RoundArgs r0, uint32_t ntiles_host) {
+  const RoundArgs r = with_dyn(r0);
+  const uint32_t nb = *r.nbig, nt = round_tiles(r, ntiles_host);
+  for (uint32_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    const uint32_t s = seg_of_tile(r.tile0, nb, tile);
+    if (r.exact[s] != 1) continue;
+    const Seg seg = r.big[s];
+    const uint64_t first = (uint64_t)(tile - r.tile0[s]) * r.TILE;
+    if (first >= seg.len) continue;
+    const int cnt = (int)min((uint64_t)r.TILE, (uint64_t)seg.len - first);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      const uint64_t g = seg.start + first + i;
+      for (int j = 0; j < r.p.d; ++j) r.samp.c[(uint64_t)j * r.samp.stride + g] = r.src.x(r.p.d, j, g);
+    }
   }
 }
 
 // Number the buckets left to right, detect heavy segments, give every
 // skeleton node a tree slot (root: the segment's own slot).
-__global__ void k_finalize(RoundArgs r) {
-  uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= *r.nbig) return;
+__device__ __forceinline__ void finalize_one(const RoundArgs& r, uint32_t s) {
   int2* sk = r.skel + (uint64_t)s * r.HN;
   uint32_t* sl = r.slots + (uint64_t)s * r.HN;
   const Seg seg = r.big[s];
@@ -1028,6 +1105,10 @@ __global__ void k_finalize(RoundArgs r) {
   }
 }
 
+__global__ void k_finalize(RoundArgs r) {
+  PKD_FOR(s, *r.nbig) finalize_one(r, s);
+}
+
 // ---------------------------------------------------------------------------
 // Sieve: count and scatter
 // ---------------------------------------------------------------------------
@@ -1036,10 +1117,7 @@ __global__ void k_finalize(RoundArgs r) {
 
 
 // Children segments, interior nodes and heavy leaves of every big segment.
-__global__ void k_emit(RoundArgs r, uint32_t* heavy_ctr) {
-  if (pkd_failed_block(r.st)) return;
-  uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= *r.nbig) return;
+__device__ __forceinline__ void emit_one(const RoundArgs& r, uint32_t* heavy_ctr, uint32_t s) {
   const Seg seg = r.big[s];
   const int2* sk = r.skel + (uint64_t)s * r.HN;
   const uint32_t* sl = r.slots + (uint64_t)s * r.HN;
@@ -1081,17 +1159,27 @@ __global__ void k_emit(RoundArgs r, uint32_t* heavy_ctr) {
   if (size[1] != seg.len) set_error(r.st, DERR_STATE, 700);
 }
 
+__global__ void k_emit(RoundArgs r0, uint32_t* heavy_ctr) {
+  if (pkd_failed_block(r0.st)) return;
+  const RoundArgs r = with_dyn(r0);
+  PKD_FOR(s, *r.nbig) emit_one(r, heavy_ctr, s);
+}
+
 
 // Heavy segments whose points are not yet in the arena.
-__global__ void k_copy_heavy(RoundArgs r) {
-  if (pkd_failed_block(r.st)) return;
-  SieveTile t;
-  if (!sieve_tile(r, t)) return;
-  if (sk_state(r.skel[(uint64_t)t.s * r.HN + 1].y) != SK_HEAVY) return;
-  for (int i = threadIdx.x; i < t.cnt; i += blockDim.x) {
-    const uint64_t g = t.seg.start + t.first + i;
-    for (int j = 0; j < r.p.d; ++j) r.A.c[(uint64_t)j * r.A.stride + g] = r.src.x(r.p.d, j, g);
-    r.A.id[g] = r.src.id(g);
+__global__ void k_copy_heavy(RoundArgs r0, uint32_t ntiles_host) {
+  if (pkd_failed_block(r0.st)) return;
+  const RoundArgs r = with_dyn(r0);
+  const uint32_t nt = round_tiles(r, ntiles_host);
+  for (uint32_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    SieveTile t;
+    if (!sieve_tile(r, t, tile)) continue;
+    if (sk_state(r.skel[(uint64_t)t.s * r.HN + 1].y) != SK_HEAVY) continue;
+    for (int i = threadIdx.x; i < t.cnt; i += blockDim.x) {
+      const uint64_t g = t.seg.start + t.first + i;
+      for (int j = 0; j < r.p.d; ++j) r.A.c[(uint64_t)j * r.A.stride + g] = r.src.x(r.p.d, j, g);
+      r.A.id[g] = r.src.id(g);
+    }
   }
 }
 
@@ -1159,69 +1247,246 @@ int skel_cap_for(int d) {
 
 
 
-// Run the job levels for skeleton nodes whose samples exceed one CTA, then
-// finish every small node in shared memory.
-static int run_skeleton_jobs(JobArgs ja, SkelJob* big0, uint32_t nbig_jobs, uint32_t big_tiles,
-                             uint32_t nsmall_host, SmemArgs sa, uint32_t* hctr, uint32_t* dctr,
-                             SkelJob* bigA, SkelJob* bigB, uint32_t* d_njobs, Scratch& sc,
-                             cudaStream_t s) {
-  (void)big0;
-  SkelJob* cur = bigA;
-  SkelJob* nxt = bigB;
-  uint32_t njobs = nbig_jobs, tiles = big_tiles;
-  JobState* js = nullptr;
-  uint32_t* jhist = nullptr;
-  uint32_t* jtile0 = nullptr;
-  uint32_t cap_jobs = 0;
-  while (njobs > 0) {
-    if (njobs > cap_jobs) {
-      cap_jobs = std::max(njobs, 64u);
-      PKD_TRY(sc.get(&js, cap_jobs));
-      PKD_TRY(sc.get(&jhist, (size_t)cap_jobs * 256));
-      PKD_TRY(sc.get(&jtile0, cap_jobs));
-    }
-    PKD_CUDA(cudaMemcpyAsync(d_njobs, &njobs, 4, cudaMemcpyHostToDevice, s));
-    ja.jobs = cur;
-    ja.njobs = d_njobs;
-    ja.jtile0 = jtile0;
-    ja.js = js;
-    ja.jhist = jhist;
-    ja.next_big = nxt;
-    const unsigned g1 = (njobs + 127) / 128;
-    PKD_LAUNCH(k_job_tiles<<<1, 1024, 0, s>>>(cur, d_njobs, jtile0));
-    PKD_LAUNCH(k_job_init<<<g1, 128, 0, s>>>(ja));
-    PKD_CUDA(cudaMemsetAsync(dctr, 0, 8, s));  // next big jobs and tiles
-    PKD_LAUNCH(k_job_stats<<<tiles, JOB_THREADS, 0, s>>>(ja));
-    PKD_LAUNCH(k_job_choose<<<g1, 128, 0, s>>>(ja));
-    for (int pass = 0; pass < 4; ++pass) {
-      PKD_LAUNCH(k_job_hist<<<tiles, JOB_THREADS, 0, s>>>(ja, pass));
-      PKD_LAUNCH(k_job_pick<<<(njobs * 32 + 127) / 128, 128, 0, s>>>(ja, pass));
-    }
-    PKD_LAUNCH(k_job_minabove<<<tiles, JOB_THREADS, 0, s>>>(ja));
-    PKD_LAUNCH(k_job_fix<<<g1, 128, 0, s>>>(ja));
-    PKD_LAUNCH(k_job_partition<<<tiles, JOB_THREADS, 0, s>>>(ja));
-    PKD_LAUNCH(k_job_children<<<g1, 128, 0, s>>>(ja));
-    PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 12, cudaMemcpyDeviceToHost, s));
-    PKD_CUDA(cudaStreamSynchronize(s));
-    njobs = hctr[0];
-    tiles = hctr[1];
-    std::swap(cur, nxt);
-  }
-  // small jobs: the count lives in dctr[2]
-  PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 12, cudaMemcpyDeviceToHost, s));
-  PKD_CUDA(cudaStreamSynchronize(s));
-  const uint32_t nsmall = hctr[2];
-  (void)nsmall_host;
-  if (nsmall > 0) {
-    sa.jobs = ja.small;
-    sa.njobs = dctr + 2;
-    const int d = sa.p.d;
-    sa.cap = skel_cap_for(d);
-    const size_t smb = smem_layout(sa.cap, d).total;
-    PKD_DISPATCH_D(d, launch_smem_skel, sa, nsmall, smb, s);
-  }
-  return PKD_OK;
+// ---------------------------------------------------------------------------
+// Round control on the device
+// ---------------------------------------------------------------------------
+
+// Words of a build's device control block.
+enum : int {
+  C_NBIG = 0,      // big segments of the round
+  C_TILES = 2,     // their tiles
+  C_EXACT = 3,     // segments that take an exact level
+  C_HEAVY = 4,     // heavy segments
+  C_JNEXT = 8,     // [8] jobs pushed for the next level, [9] their tiles, [10] small jobs
+  C_JSMALL = 10,
+  C_NBASE = 12,    // base lists: two CTAs per SM, one warp
+  C_NWBASE = 13,
+  C_PTS = 14,      // u64: points of the big segments
+  C_BASE_PTS = 16, // u64 x3: points of the CTA, warp and small-slice lists
+  C_NTBASE = 24,   // base lists: small slice, one CTA per SM
+  C_NBBASE = 25,
+  C_ROUND = 26,    // rounds done
+  C_SEL = 27,      // entry of the round arguments (0 first round, 1 odd, 2 even)
+  C_NCUR = 28,     // segments of the round
+  C_GO = 29,       // another round
+  C_JN = 30,       // jobs of the current skeleton level
+  C_JTILES = 31,   // their tiles
+  C_JLEVEL = 32,   // skeleton levels done in this pass
+  C_JGO = 33,      // another skeleton level
+  C_GRAB = 36,     // grab counter of the persistent small-job launch
+  C_WORDS = 48
+};
+constexpr uint32_t MAX_ROUNDS = 64;
+constexpr uint32_t MAX_JOB_LEVELS = 64;
+
+__global__ void k_ctl_init(uint32_t* c, uint32_t nroots) {
+  for (int i = threadIdx.x; i < C_WORDS; i += blockDim.x) c[i] = i == C_NCUR ? nroots : 0u;
 }
+
+// After a round's segments were classified: whether the round has work.
+// The counts are within the buffers by construction (every big segment
+// holds more than cap points); a count past them stops the build with an
+// error instead of reaching past a buffer.
+__global__ void k_round_go(uint32_t* c, uint32_t big_cap, uint32_t tiles_cap, DevStatus* st) {
+  const bool more = c[C_NBIG] > 0;
+  if (c[C_NBIG] > big_cap || c[C_TILES] > tiles_cap) {
+    set_error(st, DERR_CAPACITY, 802);
+    c[C_NBIG] = c[C_TILES] = 0;
+    c[C_GO] = 0;
+  } else if (more && c[C_ROUND] >= MAX_ROUNDS) {
+    set_error(st, DERR_STATE, 800);
+    c[C_GO] = 0;
+  } else {
+    c[C_GO] = more ? 1u : 0u;
+  }
+}
+
+// End of a round: its buckets are the next round's segments.
+__global__ void k_round_next(uint32_t* c, uint32_t NB) {
+  const uint32_t r = c[C_ROUND] + 1;
+  c[C_ROUND] = r;
+  c[C_SEL] = (r & 1) ? 1u : 2u;
+  c[C_NCUR] = c[C_NBIG] * NB;
+  for (int i = 0; i < 12; ++i) c[i] = 0;
+  c[C_PTS] = c[C_PTS + 1] = 0;
+}
+
+// Per-big-segment state of the round, cleared.
+__global__ void k_round_clear(RoundArgs r) {
+  const uint32_t nb = *r.nbig;
+  PKD_FOR(i, nb * (uint32_t)r.HN) {
+    r.skel[i] = make_int2(0, 0);
+    if (i < nb) {
+      r.scnt[i] = 0;
+      r.exact[i] = 0;
+    }
+  }
+}
+
+// Start of a skeleton pass: no pushed jobs, no levels, no small jobs.
+__global__ void k_jobs_reset(uint32_t* c) {
+  c[C_JNEXT] = c[C_JNEXT + 1] = c[C_JSMALL] = 0;
+  c[C_JLEVEL] = 0;
+  c[C_GRAB] = 0;
+}
+
+// The jobs pushed by the last step become the current level (one block).
+__global__ void k_job_advance(SkelJob* cur, const SkelJob* next, uint32_t* c, uint32_t cap, DevStatus* st) {
+  const uint32_t n = min(c[C_JNEXT], cap);
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) cur[i] = next[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    c[C_JN] = n;
+    c[C_JNEXT] = c[C_JNEXT + 1] = 0;
+    const uint32_t lvl = c[C_JLEVEL] + 1;
+    c[C_JLEVEL] = lvl;
+    if (n > 0 && lvl > MAX_JOB_LEVELS) {
+      set_error(st, DERR_STATE, 801);
+      c[C_JGO] = 0;
+    } else {
+      c[C_JGO] = n > 0 ? 1u : 0u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Device-decided graphs: streams, capture lock, retired executables
+// ---------------------------------------------------------------------------
+
+bool& flow_capturing() {
+  static thread_local bool v = false;
+  return v;
+}
+
+std::mutex& flow_mutex() {
+  static std::mutex m;
+  return m;
+}
+
+cudaStream_t flow_stream(int level) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, cudaStream_t> streams;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_pair(dev, level);
+  auto it = streams.find(key);
+  if (it != streams.end()) return it->second;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  streams[key] = st;
+  return st;
+}
+
+// An executable graph stays alive until an event after its launch has
+// completed; finished ones are destroyed on the next build.
+struct RetiredGraph {
+  cudaGraphExec_t exec;
+  cudaGraph_t graph;
+  cudaEvent_t done;
+  cudaEvent_t base;  // external event recorded by the graph (may be null)
+};
+static std::mutex g_retire_mu;
+static std::vector<RetiredGraph> g_retired;
+
+static void reap_graphs(bool all) {
+  std::lock_guard<std::mutex> lk(g_retire_mu);
+  std::vector<RetiredGraph> keep;
+  for (const RetiredGraph& r : g_retired) {
+    if (all) cudaEventSynchronize(r.done);
+    if (cudaEventQuery(r.done) == cudaSuccess) {
+      cudaGraphExecDestroy(r.exec);
+      cudaGraphDestroy(r.graph);
+      cudaEventDestroy(r.done);
+      if (r.base) cudaEventDestroy(r.base);
+    } else {
+      cudaGetLastError();
+      keep.push_back(r);
+    }
+  }
+  g_retired.swap(keep);
+}
+
+static int g_graph_builds = 0;  // builds whose rounds ran from one graph launch
+
+// The launch shape of a base-case kernel node, set on the device from the
+// length of its list just before it runs (a graph's kernel nodes are
+// recorded with a placeholder grid; the lists' lengths exist only on the
+// device).
+struct BaseShape {
+  cudaGraphDeviceNode_t node;
+  const uint32_t* count;  // list length
+  uint32_t cap;           // entries the list can hold
+  uint32_t per_block;     // entries per block
+  uint32_t max_blocks;    // 0: no limit
+  uint32_t pad;
+};
+constexpr int MAX_SHAPES = 4;
+
+__global__ void k_base_shapes(const BaseShape* sh, int n) {
+  if (threadIdx.x != 0) return;
+  for (int i = 0; i < n; ++i) {
+    const BaseShape b = sh[i];
+    const uint32_t c = min(*b.count, b.cap);
+    uint32_t blocks = (c + b.per_block - 1) / b.per_block;
+    if (b.max_blocks && blocks > b.max_blocks) blocks = b.max_blocks;
+    if (blocks == 0) {
+      cudaGraphKernelNodeSetEnabled(b.node, false);
+    } else {
+      cudaGraphKernelNodeSetEnabled(b.node, true);
+      cudaGraphKernelNodeSetGridDim(b.node, dim3(blocks, 1, 1));
+    }
+  }
+}
+
+// The kernel node a launch just recorded on a capturing stream.
+static cudaGraphNode_t last_node(cudaStream_t st) {
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  if (cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &nd) != cudaSuccess || nd != 1)
+    return nullptr;
+  return deps[0];
+}
+
+// Makes a recorded kernel node device-updatable; its device handle, or null.
+static cudaGraphDeviceNode_t make_updatable(cudaGraphNode_t node) {
+  if (!node) return nullptr;
+  cudaKernelNodeAttrValue v{};
+  v.deviceUpdatableKernelNode.deviceUpdatable = 1;
+  if (cudaGraphKernelNodeSetAttribute(node, cudaKernelNodeAttributeDeviceUpdatableKernelNode, &v) != cudaSuccess)
+    return nullptr;
+  cudaKernelNodeAttrValue o{};
+  if (cudaGraphKernelNodeGetAttribute(node, cudaKernelNodeAttributeDeviceUpdatableKernelNode, &o) != cudaSuccess)
+    return nullptr;
+  return o.deviceUpdatableKernelNode.devNode;
+}
+
+// ---------------------------------------------------------------------------
+// Host orchestration
+// ---------------------------------------------------------------------------
+
+// Every buffer a build needs, sized for the worst case so that no step
+// depends on a count the host has not seen:
+//   big segments of a round   <= extent / (cap + 1)  (each holds > cap points)
+//   their tiles               <= extent / TILE + big segments
+//   big skeleton jobs a level <= extent / (scap + 1) (disjoint sample ranges)
+struct BuildBufs {
+  uint64_t nbig, ncur, tiles, big_jobs, jtiles, small_jobs;
+  Seg* big;
+  uint32_t *tile0, *slots, *sizes, *nbk, *hist, *hscan, *scnt, *partial;
+  uint64_t* excl;
+  int2* skel;
+  uint8_t *exact, *bkt;
+  Seg* children[2];
+  SkelJob *jcur, *jnext, *jsmall;
+  JobState* js;
+  uint32_t *jhist, *jtile0;
+  RoundDyn* dyn;
+};
 
 int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
   const Params& p = t.p;
@@ -1232,6 +1497,8 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
   const uint32_t cap = (uint32_t)base_cap_for(d);
   const int scap = skel_cap_for(d);
   const uint64_t base = job.base, extent = std::max<uint64_t>(job.extent, 1);
+  const int nsm = num_sms();
+  reap_graphs(false);
   Scratch sc{s, {}};
 
   // scratch point buffer B and two sample buffers over [base, base + extent)
@@ -1245,29 +1512,23 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
   Pts S0 = shifted(Pts{s0c, bid, extent}, base), S1 = shifted(Pts{s1c, bid, extent}, base);
   S0.id = S1.id = nullptr;
 
-  // device counters: [0] big segs, [2] their tiles, [3] exact, [4] heavy,
-  // [8..10] skeleton jobs; [12] base list length; u64 at [14] big points
-  // u32: [12] CTA list, [13] warp list, [24] tiny list, [25] one-CTA-per-SM list;
-  // u64: [14] big points, [16] CTA points, [18] warp points, [20] tiny points
   uint32_t* dctr;
-  PKD_TRY(sc.get(&dctr, 32));
-  unsigned long long* dpts = (unsigned long long*)(dctr + 14);
-  unsigned long long* dbase_pts = (unsigned long long*)(dctr + 16);
-  uint32_t* d_nbase = dctr + 12;
-  PinnedBlock hblk(s);  // 128 bytes of host counters
+  PKD_TRY(sc.get(&dctr, C_WORDS));
+  PinnedBlock hblk(s);  // host copy of the control block
   uint32_t* hctr = (uint32_t*)hblk.p;
   if (!hctr) return PKD_ENOMEM;
-  PKD_CUDA(cudaMemsetAsync(dctr, 0, 32 * 4, s));
+  static_assert(C_WORDS * 4 <= PINNED_BLOCK, "control block");
+  memset(hctr, 0, C_WORDS * 4);
 
   const uint64_t nroots = job.dsegs ? job.dsegs_n : job.segs.size();
-  Seg* cur;
+  if (nroots >= 0xFFFFFFFFull) return PKD_EINVAL;
+  Seg* roots;
   if (job.dsegs) {
-    cur = const_cast<Seg*>(job.dsegs);
+    roots = const_cast<Seg*>(job.dsegs);
   } else {
-    PKD_TRY(sc.get(&cur, std::max<uint64_t>(nroots, 1)));
-    PKD_CUDA(cudaMemcpyAsync(cur, job.segs.data(), nroots * sizeof(Seg), cudaMemcpyHostToDevice, s));
+    PKD_TRY(sc.get(&roots, std::max<uint64_t>(nroots, 1)));
+    PKD_CUDA(cudaMemcpyAsync(roots, job.segs.data(), nroots * sizeof(Seg), cudaMemcpyHostToDevice, s));
   }
-  uint64_t ncur = nroots;
   const uint32_t wcap = (uint32_t)warp_cap_for(d);
   // every base segment is a root or a non-empty bucket: at most extent + roots
   const uint64_t base_cap_segs = extent + nroots + 16;
@@ -1281,18 +1542,97 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
   const uint32_t cap2 =
       knobs().base_kernel == 0 ? std::min<uint32_t>(cap, (uint32_t)sorted_cap_two_per_sm(d)) : cap;
 
-  Src src{};
-  int src_where;
-  if (job.input_coords) {
-    src.aos = job.input_coords;
-    src.aos_ids = job.input_ids;
-    src.is_aos = 1;
-    src_where = IN_INPUT;
-  } else {
-    src.soa = t.A;
-    src.is_aos = 0;
-    src_where = IN_A;
+  // worst-case round buffers
+  BuildBufs bb{};
+  bb.nbig = extent / (cap + 1) + 1;
+  bb.ncur = std::max<uint64_t>(nroots, bb.nbig * NB);
+  bb.tiles = (extent + TILE - 1) / TILE + bb.nbig;
+  bb.big_jobs = extent / ((uint64_t)scap + 1) + bb.nbig + 16;
+  bb.jtiles = (extent + JOB_TILE - 1) / JOB_TILE + bb.big_jobs;
+  bb.small_jobs = bb.nbig * NB + 16;
+  if (bb.ncur >= 0xFFFFFFFFull || bb.tiles * NB >= 0xFFFFFFFFull) return PKD_EINVAL;
+  PKD_TRY(sc.get(&bb.big, bb.nbig));
+  PKD_TRY(sc.get(&bb.tile0, bb.nbig));
+  PKD_TRY(sc.get(&bb.excl, bb.nbig));
+  PKD_TRY(sc.get(&bb.skel, bb.nbig * HN));
+  PKD_TRY(sc.get(&bb.slots, bb.nbig * HN));
+  PKD_TRY(sc.get(&bb.sizes, bb.nbig * HN));
+  PKD_TRY(sc.get(&bb.nbk, bb.nbig));
+  PKD_TRY(sc.get(&bb.exact, bb.nbig));
+  PKD_TRY(sc.get(&bb.scnt, bb.nbig));
+  PKD_TRY(sc.get(&bb.hist, bb.tiles * NB));
+  PKD_TRY(sc.get(&bb.hscan, bb.tiles * NB));
+  PKD_TRY(sc.get(&bb.partial, SCAN_BLOCKS + 1));
+  bb.bkt = nullptr;
+  if (record_buckets(NB)) PKD_TRY(sc.get(&bb.bkt, bb.tiles * TILE));
+  PKD_TRY(sc.get(&bb.children[0], bb.nbig * NB));
+  PKD_TRY(sc.get(&bb.children[1], bb.nbig * NB));
+  PKD_TRY(sc.get(&bb.jcur, bb.big_jobs));
+  PKD_TRY(sc.get(&bb.jnext, bb.big_jobs));
+  PKD_TRY(sc.get(&bb.jsmall, bb.small_jobs));
+  PKD_TRY(sc.get(&bb.js, bb.big_jobs));
+  PKD_TRY(sc.get(&bb.jhist, bb.big_jobs * 256));
+  PKD_TRY(sc.get(&bb.jtile0, bb.big_jobs));
+  PKD_TRY(sc.get(&bb.dyn, 3));
+
+  // the arguments of the three kinds of rounds: the first reads the input
+  // (or the arena), the odd ones B, the even ones after the first the arena
+  {
+    RoundDyn hd[3];
+    Src in{};
+    if (job.input_coords) {
+      in.aos = job.input_coords;
+      in.aos_ids = job.input_ids;
+      in.is_aos = 1;
+    } else {
+      in.soa = t.A;
+    }
+    Src fromB{};
+    fromB.soa = B;
+    Src fromA{};
+    fromA.soa = t.A;
+    hd[0] = RoundDyn{in, B, (int)IN_B, job.input_coords ? (int)IN_INPUT : (int)IN_A, roots, bb.children[0]};
+    hd[1] = RoundDyn{fromB, t.A, (int)IN_A, (int)IN_B, bb.children[0], bb.children[1]};
+    hd[2] = RoundDyn{fromA, B, (int)IN_B, (int)IN_A, bb.children[1], bb.children[0]};
+    for (int k = 0; k < 3; ++k) {
+      static_assert(sizeof(RoundDyn) <= PINNED_BLOCK, "round arguments");
+      PinnedBlock one(s);
+      if (!one.p) return PKD_ENOMEM;
+      memcpy(one.p, &hd[k], sizeof(RoundDyn));
+      PKD_CUDA(cudaMemcpyAsync(bb.dyn + k, one.p, sizeof(RoundDyn), cudaMemcpyHostToDevice, s));
+    }
   }
+
+  RoundArgs r{};
+  r.wait_cycles = knobs().wait_cycles;
+  r.p = p;
+  r.lam = lam;
+  r.NB = NB;
+  r.HN = HN;
+  r.TILE = TILE;
+  r.A = t.A;
+  r.big = bb.big;
+  r.nbig = dctr + C_NBIG;
+  r.tile0 = bb.tile0;
+  r.excl = bb.excl;
+  r.skel = bb.skel;
+  r.slots = bb.slots;
+  r.sizes = bb.sizes;
+  r.nbk = bb.nbk;
+  r.exact = bb.exact;
+  r.hist = bb.hist;
+  r.hscan = bb.hscan;
+  r.bkt = bb.bkt;
+  r.scnt = bb.scnt;
+  r.samp = S0;
+  r.nodes = t.nodes;
+  r.ndim = t.ndim;
+  r.shared_next = t.shared_next;
+  r.shared_cap = t.shared_cap;
+  r.st = t.st;
+  r.dyn = bb.dyn;
+  r.sel = dctr + C_SEL;
+  r.ntiles = dctr + C_TILES;
 
   SmemArgs sa{};
   sa.p = p;
@@ -1308,202 +1648,299 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
   sa.sstride = extent;
   sa.heap_n = HN;
   sa.shared_cap = t.shared_cap;
+  sa.skel = bb.skel;
 
-  uint32_t* d_nj;
-  PKD_TRY(sc.get(&d_nj, 4));
+  JobArgs ja{};
+  ja.p = p;
+  ja.d = d;
+  ja.sb[0] = S0;
+  ja.sb[1] = S1;
+  ja.skel = bb.skel;
+  ja.HN = HN;
+  ja.scap = scap;
+  ja.st = t.st;
+  ja.jobs = bb.jcur;
+  ja.njobs = dctr + C_JN;
+  ja.jtile0 = bb.jtile0;
+  ja.js = bb.js;
+  ja.jhist = bb.jhist;
+  ja.next_big = bb.jnext;
+  ja.next_ctr = dctr + C_JNEXT;
+  ja.small = bb.jsmall;
+  ja.small_cap = (uint32_t)bb.small_jobs;
+  ja.big_cap = (uint32_t)bb.big_jobs;
+  ja.jtiles = dctr + C_JTILES;
 
-  for (int round = 0; ncur > 0; ++round) {
-    if (round > 64) return PKD_EINTERNAL;
-    Seg* big;
-    PKD_TRY(sc.get(&big, ncur));
-    PKD_CUDA(cudaMemsetAsync(dctr, 0, 12 * 4, s));
-    PKD_CUDA(cudaMemsetAsync(dpts, 0, 8, s));
-    PKD_LAUNCH(k_classify<<<(unsigned)((ncur + 255) / 256), 256, 0, s>>>(
-        cur, (uint32_t)ncur, cap, big, dctr, dpts, base_list, d_nbase, (uint32_t)base_cap_segs,
-        wbase_list, d_nbase + 1, wcap, tbase_list, dctr + 24, tcap, bbase_list, dctr + 25, cap2, (uint32_t)TILE,
-        (uint32_t)src_where,
-        dbase_pts, t.st));
-    PKD_CUDA(cudaMemcpyAsync(hctr, dctr, 16 * 4, cudaMemcpyDeviceToHost, s));
-    PKD_CUDA(cudaStreamSynchronize(s));
-    const uint32_t nbig = hctr[0], tiles = hctr[2];
-    const uint64_t pts_big = *(unsigned long long*)(hctr + 14);
-    if (nbig == 0) break;
+  // launch shapes: grids of resident blocks that stride over device counts
+  auto grid_for = [&](uint64_t items, int per_block, int per_sm) {
+    return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((items + per_block - 1) / per_block,
+                                                              (uint64_t)nsm * per_sm));
+  };
+  const unsigned g_seg128 = grid_for(bb.nbig, 128, 8);
+  const unsigned g_clear = grid_for(bb.nbig * HN, 256, 8);
+  const unsigned g_cls = grid_for(bb.ncur, 256, 8);
+  const unsigned g_tiles = grid_for(bb.tiles, 1, 8);
+  const unsigned g_job = grid_for(bb.big_jobs, 128, 8);
+  const unsigned g_jobw = grid_for(bb.big_jobs * 32, 128, 8);
+  const unsigned g_jtiles = grid_for(bb.jtiles, 1, 8);
+  const unsigned g_sample = grid_for(bb.tiles, 1, SAMPLE_CTAS_PER_SM);
 
-    RoundArgs r{};
-    r.wait_cycles = knobs().wait_cycles;
-    r.p = p;
-    r.lam = lam;
-    r.NB = NB;
-    r.HN = HN;
-    r.TILE = TILE;
-    r.src = src;
-    const bool dst_is_A = (src_where == IN_B);
-    r.dst = dst_is_A ? t.A : B;
-    r.dst_where = dst_is_A ? IN_A : IN_B;
-    r.A = t.A;
-    r.big = big;
-    r.nbig = dctr;
-    PKD_TRY(sc.get(&r.tile0, nbig));
-    PKD_TRY(sc.get(&r.excl, nbig));
-    PKD_TRY(sc.get(&r.skel, (size_t)nbig * HN));
-    PKD_TRY(sc.get(&r.slots, (size_t)nbig * HN));
-    PKD_TRY(sc.get(&r.sizes, (size_t)nbig * HN));
-    PKD_TRY(sc.get(&r.nbk, nbig));
-    PKD_TRY(sc.get(&r.exact, nbig));
-    PKD_TRY(sc.get(&r.hist, (size_t)tiles * NB));
-    PKD_TRY(sc.get(&r.hscan, (size_t)tiles * NB));
-    r.bkt = nullptr;
-    if (record_buckets(NB)) PKD_TRY(sc.get(&r.bkt, (size_t)tiles * TILE));
-    PKD_TRY(sc.get(&r.scnt, nbig));
-    PKD_TRY(sc.get(&r.children, (size_t)nbig * NB));
-    r.samp = S0;
-    r.nodes = t.nodes;
-    r.ndim = t.ndim;
-    r.shared_next = t.shared_next;
-    r.shared_cap = t.shared_cap;
-    r.st = t.st;
-    PKD_CUDA(cudaMemsetAsync(r.skel, 0, (size_t)nbig * HN * sizeof(int2), s));
-    PKD_CUDA(cudaMemsetAsync(r.scnt, 0, (size_t)nbig * 4, s));
-    PKD_CUDA(cudaMemsetAsync(r.exact, 0, nbig, s));
-    PKD_LAUNCH(k_big_prefix<<<1, 1024, 0, s>>>(big, dctr, (uint32_t)TILE, r.tile0, r.excl));
+  const bool graph = knobs().graph_rounds != 0;
+  Flow f;
+  f.dctl = dctr;
+  f.hctl = hctr;
+  f.nctl = C_WORDS;
+  f.s = s;
 
-    // 1. sample
+  auto classify = [&](Flow& g) {
+    PKD_LAUNCH(k_classify<<<g_cls, 256, 0, g.s>>>(
+        bb.dyn, dctr + C_SEL, dctr + C_NCUR, (uint32_t)bb.ncur, cap, bb.big, (uint32_t)bb.nbig, dctr,
+        (unsigned long long*)(dctr + C_PTS), base_list, dctr + C_NBASE, (uint32_t)base_cap_segs, wbase_list,
+        dctr + C_NWBASE, wcap, tbase_list, dctr + C_NTBASE, tcap, bbase_list, dctr + C_NBBASE, cap2,
+        (uint32_t)TILE, (unsigned long long*)(dctr + C_BASE_PTS), t.st));
+    PKD_LAUNCH(k_round_go<<<1, 1, 0, g.s>>>(dctr, (uint32_t)bb.nbig, (uint32_t)bb.tiles, t.st));
+    return PKD_OK;
+  };
+
+  // one skeleton level of the jobs whose samples exceed one CTA
+  auto job_level = [&](Flow& g) {
+    cudaStream_t q = g.s;
+    PKD_LAUNCH(k_job_tiles<<<1, 1024, 0, q>>>(bb.jcur, dctr + C_JN, bb.jtile0, dctr + C_JTILES));
+    PKD_LAUNCH(k_job_init<<<g_job, 128, 0, q>>>(ja));
+    PKD_LAUNCH(k_job_stats<<<g_jtiles, JOB_THREADS, 0, q>>>(ja));
+    PKD_LAUNCH(k_job_choose<<<g_job, 128, 0, q>>>(ja));
+    for (int pass = 0; pass < 4; ++pass) {
+      PKD_LAUNCH(k_job_hist<<<g_jtiles, JOB_THREADS, 0, q>>>(ja, pass));
+      PKD_LAUNCH(k_job_pick<<<g_jobw, 128, 0, q>>>(ja, pass));
+    }
+    PKD_LAUNCH(k_job_minabove<<<g_jtiles, JOB_THREADS, 0, q>>>(ja));
+    PKD_LAUNCH(k_job_fix<<<g_job, 128, 0, q>>>(ja));
+    PKD_LAUNCH(k_job_partition<<<g_jtiles, JOB_THREADS, 0, q>>>(ja));
+    PKD_LAUNCH(k_job_children<<<g_job, 128, 0, q>>>(ja));
+    PKD_LAUNCH(k_job_advance<<<1, 1024, 0, q>>>(bb.jcur, bb.jnext, dctr, (uint32_t)bb.big_jobs, t.st));
+    return PKD_OK;
+  };
+
+  // the skeletons of every big segment: root jobs, device-wide levels while
+  // a node's sample exceeds one CTA, then every small node in shared memory
+  auto skeleton_pass = [&](Flow& g, int exact_pass) {
+    if (exact_pass) PKD_LAUNCH(k_copy_exact<<<g_tiles, 256, 0, g.s>>>(r, 0));
+    PKD_LAUNCH(k_jobs_reset<<<1, 1, 0, g.s>>>(dctr));
+    PKD_LAUNCH(k_root_jobs<<<g_seg128, 128, 0, g.s>>>(r, ja, exact_pass));
+    PKD_LAUNCH(k_job_advance<<<1, 1024, 0, g.s>>>(bb.jcur, bb.jnext, dctr, (uint32_t)bb.big_jobs, t.st));
+    PKD_TRY(flow_while(g, C_JGO, job_level));
+    SmemArgs ka = sa;
+    ka.jobs = bb.jsmall;
+    ka.njobs = dctr + C_JSMALL;
+    ka.list_cap = (uint32_t)bb.small_jobs;
+    ka.grab = dctr + C_GRAB;
+    ka.cap = scap;
+    const size_t smb = smem_layout(ka.cap, d).total;
+    PKD_DISPATCH_D(d, launch_smem_skel, ka, (uint32_t)nsm, smb, g.s);
+    return PKD_OK;
+  };
+
+  auto round = [&](Flow& g) {
+    cudaStream_t q = g.s;
+    const uint64_t pts_big = g.graph ? 0 : *(unsigned long long*)(g.hctl + C_PTS);
+    PKD_LAUNCH(k_round_clear<<<g_clear, 256, 0, q>>>(r));
+    PKD_LAUNCH(k_big_prefix<<<1, 1024, 0, q>>>(bb.big, dctr + C_NBIG, (uint32_t)TILE, bb.tile0, bb.excl));
     {
       KTimer kt;
-      ktimer_begin(kt, "sample", pts_big, s);
-      const uint32_t sgrid = std::min<uint32_t>(tiles, (uint32_t)stream_sm_count() * SAMPLE_CTAS_PER_SM);
-      PKD_LAUNCH(k_sample<<<sgrid, SAMPLE_THREADS, 0, s>>>(r, tiles));
+      ktimer_begin(kt, "sample", pts_big, q);
+      PKD_LAUNCH(k_sample<<<g_sample, SAMPLE_THREADS, 0, q>>>(r, 0));
       ktimer_end(kt);
     }
+    PKD_TRY(skeleton_pass(g, 0));
+    // segments whose skeleton root is a bucket take one exact level on their own points
+    PKD_LAUNCH(k_mark_exact<<<g_seg128, 128, 0, q>>>(r, dctr + C_EXACT));
+    PKD_TRY(flow_if(g, C_EXACT, [&](Flow& h) { return skeleton_pass(h, 1); }));
+    PKD_LAUNCH(k_finalize<<<g_seg128, 128, 0, q>>>(r));
+    PKD_DISPATCH_D(d, launch_count, r, (uint32_t)bb.tiles, pts_big, "count", q);
+    device_excl_scan_dev(bb.hist, bb.hscan, dctr + C_TILES, (uint32_t)NB, bb.tiles * NB, bb.partial, q);
+    PKD_LAUNCH(k_emit<<<grid_for(bb.nbig, 64, 8), 64, 0, q>>>(r, dctr + C_HEAVY));
+    PKD_DISPATCH_D(d, launch_scatter, r, (uint32_t)bb.tiles, pts_big, "scatter", q);
+    PKD_LAUNCH(k_copy_heavy<<<g_tiles, 256, 0, q>>>(r, 0));
+    // the buckets, now in the destination buffer, are the next round
+    PKD_LAUNCH(k_round_next<<<1, 1, 0, q>>>(dctr, (uint32_t)NB));
+    return classify(g);
+  };
 
-    // 2. skeletons (and, for segments whose skeleton root is a bucket, one
-    //    exact level on their own points)
-    JobArgs ja{};
-    ja.p = p;
-    ja.d = d;
-    ja.sb[0] = S0;
-    ja.sb[1] = S1;
-    ja.skel = r.skel;
-    ja.HN = HN;
-    ja.scap = scap;
-    ja.st = t.st;
-    const uint32_t small_cap = nbig * (uint32_t)NB + 16;
-    const uint32_t big_cap = (uint32_t)std::min<uint64_t>(pts_big / (uint64_t)scap + nbig + 16, 1u << 30);
-    SkelJob *bigA, *bigB, *small;
-    PKD_TRY(sc.get(&bigA, big_cap));
-    PKD_TRY(sc.get(&bigB, big_cap));
-    PKD_TRY(sc.get(&small, small_cap));
-    ja.small = small;
-    ja.small_cap = small_cap;
-    ja.big_cap = big_cap;
-    uint32_t* jctr = dctr + 8;
-    ja.next_ctr = jctr;
-    sa.skel = r.skel;
-    for (int exact_pass = 0; exact_pass < 2; ++exact_pass) {
-      if (exact_pass == 1) {
-        PKD_LAUNCH(k_mark_exact<<<(nbig + 127) / 128, 128, 0, s>>>(r, dctr + 3));
-        PKD_CUDA(cudaMemcpyAsync(hctr + 3, dctr + 3, 4, cudaMemcpyDeviceToHost, s));
-        PKD_CUDA(cudaStreamSynchronize(s));
-        if (hctr[3] == 0) break;
-        PKD_LAUNCH(k_copy_exact<<<tiles, 256, 0, s>>>(r));
-      }
-      PKD_CUDA(cudaMemsetAsync(jctr, 0, 12, s));
-      ja.next_big = bigA;
-      PKD_LAUNCH(k_root_jobs<<<(nbig + 127) / 128, 128, 0, s>>>(r, ja, exact_pass));
-      PKD_CUDA(cudaMemcpyAsync(hctr + 8, jctr, 12, cudaMemcpyDeviceToHost, s));
-      PKD_CUDA(cudaStreamSynchronize(s));
-      PKD_TRY(run_skeleton_jobs(ja, bigA, hctr[8], hctr[9], 0, sa, hctr + 8, jctr, bigA, bigB, d_nj,
-                                sc, s));
+  // 5. every small subproblem, in shared memory, one CTA (or warp) per
+  //    entry of the base lists: `q` is the stream, `list_blocks(w, per,
+  //    max)` the grid of the list whose length is control word w.
+  auto base_stage = [&](cudaStream_t q, cudaStream_t aux, auto&& list_blocks, auto&& recorded) {
+    const uint64_t cta_pts = *(unsigned long long*)(hctr + C_BASE_PTS);
+    const uint64_t warp_pts = *(unsigned long long*)(hctr + C_BASE_PTS + 2);
+    const uint64_t tiny_pts = *(unsigned long long*)(hctr + C_BASE_PTS + 4);
+    for (int pass = 0; pass < 2; ++pass) {
+      SmemArgs wa = sa;
+      const int w = pass == 0 ? C_NWBASE : C_NTBASE;
+      wa.segs = pass == 0 ? wbase_list : tbase_list;
+      wa.nsegs = dctr + w;
+      wa.list_cap = (uint32_t)base_cap_segs;
+      wa.cap = pass == 0 ? (int)wcap : (int)tcap;
+      const size_t smb = warp_layout(wa.cap, d).per_warp * WK_WARPS;
+      const uint32_t blocks = list_blocks(w, WK_WARPS, (uint32_t)(nsm * 8));
+      if (blocks == 0) continue;
+      KTimer kt;
+      ktimer_begin(kt, "smem_warp", pass == 0 ? warp_pts : tiny_pts, q);
+      PKD_DISPATCH_D(d, launch_smem_warp, wa, blocks, smb, q);
+      ktimer_end(kt);
+      PKD_TRY(recorded(q, w, (uint32_t)WK_WARPS, (uint32_t)(nsm * 8)));
     }
-
-    // 3. finalize skeletons, count, scan, emit, scatter
-    PKD_LAUNCH(k_finalize<<<(nbig + 127) / 128, 128, 0, s>>>(r));
-    PKD_DISPATCH_D(d, launch_count, r, tiles, pts_big, "count", s);
-    uint32_t* partial;
-    const uint64_t nh = (uint64_t)tiles * NB;
-    PKD_TRY(sc.get(&partial, (nh + SCAN_TILE - 1) / SCAN_TILE + 1));
-    device_excl_scan(r.hist, r.hscan, nh, partial, s);
-    PKD_LAUNCH(k_emit<<<(nbig + 63) / 64, 64, 0, s>>>(r, dctr + 4));
-    PKD_DISPATCH_D(d, launch_scatter, r, tiles, pts_big, "scatter", s);
-    PKD_LAUNCH(k_copy_heavy<<<tiles, 256, 0, s>>>(r));
-
-    // 4. the buckets, now in the destination buffer, are the next round
-    cur = r.children;
-    ncur = (uint64_t)nbig * NB;
-    src.soa = r.dst;
-    src.is_aos = 0;
-    src_where = r.dst_where;
-  }
-
-  // 5. every small subproblem, one CTA each, in shared memory
-  PKD_CUDA(cudaMemcpyAsync(hctr + 12, d_nbase, 14 * 4, cudaMemcpyDeviceToHost, s));
-  PKD_CUDA(cudaStreamSynchronize(s));
-  if (job.before_base) job.before_base();
-  const uint64_t cta_pts = *(unsigned long long*)(hctr + 16), warp_pts = *(unsigned long long*)(hctr + 18);
-  const uint64_t tiny_pts = *(unsigned long long*)(hctr + 20);
-  const uint32_t nbase = std::min<uint32_t>(hctr[12], (uint32_t)base_cap_segs);
-  const uint32_t nwbase = std::min<uint32_t>(hctr[13], (uint32_t)base_cap_segs);
-  const uint32_t ntbase = std::min<uint32_t>(hctr[24], (uint32_t)base_cap_segs);
-  const uint32_t nbbase = std::min<uint32_t>(hctr[25], (uint32_t)base_cap_segs);
-  for (int pass = 0; pass < 2; ++pass) {
-    const uint32_t nw = pass == 0 ? nwbase : ntbase;
-    if (nw == 0) continue;
-    SmemArgs wa = sa;
-    wa.segs = pass == 0 ? wbase_list : tbase_list;
-    wa.nsegs = pass == 0 ? d_nbase + 1 : dctr + 24;
-    wa.cap = pass == 0 ? (int)wcap : (int)tcap;
-    const size_t smb = warp_layout(wa.cap, d).per_warp * WK_WARPS;
     KTimer kt;
-    ktimer_begin(kt, "smem_warp", pass == 0 ? warp_pts : tiny_pts, s);
-    const uint32_t blocks = std::min<uint32_t>((nw + WK_WARPS - 1) / WK_WARPS, (uint32_t)(num_sms() * 8));
-    PKD_DISPATCH_D(d, launch_smem_warp, wa, blocks, smb, s);
-    ktimer_end(kt);
-  }
-  if (nbase + nbbase > 0) {
-    KTimer kt;
-    ktimer_begin(kt, "smem_build", cta_pts, s);
+    ktimer_begin(kt, "smem_build", cta_pts, q);
     if (knobs().base_kernel == 0) {
       // the one-CTA-per-SM segments run beside the two-CTA launch, on a
       // second stream, so their long CTAs do not form a tail of their own
-      cudaStream_t sb = s;
       cudaEvent_t fork = nullptr, join = nullptr;
-      if (nbase > 0 && nbbase > 0) {
-        sb = aux_stream();
-        PKD_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-        PKD_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
-        PKD_CUDA(cudaEventRecord(fork, s));
-        PKD_CUDA(cudaStreamWaitEvent(sb, fork, 0));
+      PKD_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+      PKD_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+      PKD_CUDA(cudaEventRecord(fork, q));
+      PKD_CUDA(cudaStreamWaitEvent(aux, fork, 0));
+      SmemArgs s1 = sa;
+      s1.segs = bbase_list;
+      s1.nsegs = dctr + C_NBBASE;
+      s1.list_cap = (uint32_t)base_cap_segs;
+      s1.cap = (int)cap;
+      const uint32_t b1 = list_blocks(C_NBBASE, 1, 0);
+      if (b1) {
+        PKD_DISPATCH_D(d, launch_smem_sorted, s1, b1, sorted_layout((int)cap, d).total, aux);
+        PKD_TRY(recorded(aux, C_NBBASE, 1u, 0u));
       }
-      if (nbbase > 0) {
-        SmemArgs s1 = sa;
-        s1.segs = bbase_list;
-        s1.nsegs = dctr + 25;
-        s1.cap = (int)cap;
-        PKD_DISPATCH_D(d, launch_smem_sorted, s1, nbbase, sorted_layout((int)cap, d).total, sb);
+      SmemArgs s2 = sa;
+      s2.segs = base_list;
+      s2.nsegs = dctr + C_NBASE;
+      s2.list_cap = (uint32_t)base_cap_segs;
+      s2.cap = (int)cap2;
+      const uint32_t b2 = list_blocks(C_NBASE, 1, 0);
+      if (b2) {
+        PKD_DISPATCH_D(d, launch_smem_sorted2, s2, b2, sorted_layout((int)cap2, d).total, q);
+        PKD_TRY(recorded(q, C_NBASE, 1u, 0u));
       }
-      if (nbase > 0) {
-        SmemArgs s2 = sa;
-        s2.segs = base_list;
-        s2.nsegs = d_nbase;
-        s2.cap = (int)cap2;
-        PKD_DISPATCH_D(d, launch_smem_sorted2, s2, nbase, sorted_layout((int)cap2, d).total, s);
-      }
-      if (join) {
-        PKD_CUDA(cudaEventRecord(join, sb));
-        PKD_CUDA(cudaStreamWaitEvent(s, join, 0));
-        cudaEventDestroy(fork);
-        cudaEventDestroy(join);
-      }
+      PKD_CUDA(cudaEventRecord(join, aux));
+      PKD_CUDA(cudaStreamWaitEvent(q, join, 0));
+      cudaEventDestroy(fork);
+      cudaEventDestroy(join);
     } else {
-      sa.segs = base_list;
-      sa.nsegs = d_nbase;
-      sa.cap = (int)cap;
-      PKD_DISPATCH_D(d, launch_smem_build, sa, nbase, smem_layout((int)cap, d).total, s);
+      SmemArgs s2 = sa;
+      s2.segs = base_list;
+      s2.nsegs = dctr + C_NBASE;
+      s2.list_cap = (uint32_t)base_cap_segs;
+      s2.cap = (int)cap;
+      const uint32_t b2 = list_blocks(C_NBASE, 1, 0);
+      if (b2) {
+        PKD_DISPATCH_D(d, launch_smem_build, s2, b2, smem_layout((int)cap, d).total, q);
+        PKD_TRY(recorded(q, C_NBASE, 1u, 0u));
+      }
     }
     ktimer_end(kt);
+    return PKD_OK;
+  };
+
+  PKD_LAUNCH(k_ctl_init<<<1, 64, 0, s>>>(dctr, (uint32_t)nroots));
+  if (!graph) {
+    PKD_TRY(classify(f));
+    PKD_TRY(flow_while(f, C_GO, round));
+    // the counts come back once more: every list gets its exact grid
+    PKD_TRY(flow_read(f));
+    if (job.before_base) job.before_base(nullptr);
+    auto host_blocks = [&](int w, uint32_t per, uint32_t mx) {
+      const uint32_t c = (uint32_t)std::min<uint64_t>(hctr[w], base_cap_segs);
+      const uint32_t b = (c + per - 1) / per;
+      return mx ? std::min(b, mx) : b;
+    };
+    auto none = [](cudaStream_t, int, uint32_t, uint32_t) { return PKD_OK; };
+    PKD_TRY(base_stage(s, aux_stream(), host_blocks, none));
+  } else {
+    // One graph: WHILE(another round) { ... WHILE(another skeleton level)
+    // { ... } ... IF(exact levels) { ... } ... }, then the base cases as
+    // device-updatable kernel nodes whose grids k_base_shapes sets from the
+    // lists' lengths (a node with an empty list is disabled).
+    std::lock_guard<std::mutex> lk(flow_mutex());
+    const auto rec0 = std::chrono::steady_clock::now();
+    cudaStream_t cs = flow_stream(0);
+    if (!cs) return PKD_ECUDA;
+    BaseShape* dshape;
+    PKD_TRY(sc.get(&dshape, MAX_SHAPES));
+    PinnedBlock shblk(s);
+    if (!shblk.p) return PKD_ENOMEM;
+    static_assert(MAX_SHAPES * sizeof(BaseShape) <= PINNED_BLOCK, "shape block");
+    BaseShape* hshape = (BaseShape*)shblk.p;
+    int nshape = 0;
+    cudaGraphNode_t shape_nodes[MAX_SHAPES] = {};
+    cudaEvent_t ready = nullptr, done = nullptr, base_ev = nullptr;
+    PKD_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    PKD_CUDA(cudaEventCreateWithFlags(&base_ev, cudaEventDisableTiming));
+    // the capture stream starts after the work queued so far on s
+    PKD_CUDA(cudaEventRecord(ready, s));
+    PKD_CUDA(cudaStreamWaitEvent(cs, ready, 0));
+    cudaEventDestroy(ready);
+    PKD_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    flow_capturing() = true;
+    Flow g = f;
+    g.s = cs;
+    g.graph = true;
+    int e = classify(g);
+    if (e == PKD_OK) e = flow_while(g, C_GO, round);
+    if (e == PKD_OK) {
+      PKD_LAUNCH(k_base_shapes<<<1, 32, 0, cs>>>(dshape, MAX_SHAPES));
+      if (cudaEventRecordWithFlags(base_ev, cs, cudaEventRecordExternal) != cudaSuccess) e = PKD_ECUDA;
+    }
+    auto dev_blocks = [](int, uint32_t, uint32_t) { return 1u; };  // placeholders
+    auto record_shape = [&](cudaStream_t q, int w, uint32_t per, uint32_t mx) {
+      if (nshape >= MAX_SHAPES) return PKD_EINTERNAL;
+      shape_nodes[nshape] = last_node(q);
+      if (!shape_nodes[nshape]) return PKD_ECUDA;
+      hshape[nshape] = BaseShape{nullptr, dctr + w, (uint32_t)base_cap_segs, per, mx, 0};
+      ++nshape;
+      return PKD_OK;
+    };
+    if (e == PKD_OK) e = base_stage(cs, aux_stream(), dev_blocks, record_shape);
+    flow_capturing() = false;
+    cudaGraph_t graph_h = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &graph_h);
+    if (e == PKD_OK && ce != cudaSuccess) e = PKD_ECUDA;
+    // the recorded base-case nodes become device-updatable (the shape
+    // kernel walks MAX_SHAPES entries: unused ones repeat the first update)
+    for (int k = 0; e == PKD_OK && k < nshape; ++k) {
+      hshape[k].node = make_updatable(shape_nodes[k]);
+      if (!hshape[k].node) e = PKD_ECUDA;
+    }
+    for (int k = nshape; k < MAX_SHAPES; ++k) hshape[k] = hshape[0];
+    cudaGraphExec_t exec = nullptr;
+    if (e == PKD_OK && cudaMemcpyAsync(dshape, hshape, MAX_SHAPES * sizeof(BaseShape), cudaMemcpyHostToDevice, s) !=
+                           cudaSuccess)
+      e = PKD_ECUDA;
+    if (e == PKD_OK && cudaGraphInstantiate(&exec, graph_h, 0) != cudaSuccess) e = PKD_ECUDA;
+    if (e == PKD_OK && cudaGraphUpload(exec, s) != cudaSuccess) e = PKD_ECUDA;
+    if (e == PKD_OK && cudaGraphLaunch(exec, s) != cudaSuccess) e = PKD_ECUDA;
+    if (e == PKD_OK && cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) e = PKD_ECUDA;
+    if (e == PKD_OK && cudaEventRecord(done, s) != cudaSuccess) e = PKD_ECUDA;
+    if (e != PKD_OK) {
+      cudaGetLastError();
+      cudaStreamSynchronize(s);
+      if (exec) cudaGraphExecDestroy(exec);
+      if (graph_h) cudaGraphDestroy(graph_h);
+      if (done) cudaEventDestroy(done);
+      cudaEventDestroy(base_ev);
+      return e;
+    }
+    {
+      std::lock_guard<std::mutex> rl(g_retire_mu);
+      g_retired.push_back(RetiredGraph{exec, graph_h, done, base_ev});
+    }
+    ++g_graph_builds;
+    stat_host_ms("graph_record",
+                 std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - rec0).count(), 1);
+    // work that overlaps the base cases starts at the graph's event
+    if (job.before_base) job.before_base(base_ev);
   }
   PKD_CUDA(cudaGetLastError());
   return PKD_OK;
 }
+
+int graph_builds() { return g_graph_builds; }
 
 }  // namespace pkd

@@ -23,6 +23,8 @@ struct Knobs {
   int base_kernel = 0;  // base case: 0 presorted lists, 1 radix select per node
   int sieve_kernel = 0;  // sieve: 0 persistent with bulk copies and recorded
                          // buckets, 2 persistent re-walking, 1 one tile per CTA
+  int graph_rounds = 1;  // build rounds: 1 decided on the device (one CUDA graph
+                         // with conditional nodes), 0 sequenced by the host
 };
 Knobs& knobs();
 
@@ -157,6 +159,8 @@ bool ktiming_enabled();
 // While timing is on, add `items` to the counter family `name` (a count
 // with no kernel time, e.g. the points a batch update rebuilt).
 void stat_items(const char* name, uint64_t items);
+// A host-side duration (ms) under a timer family (e.g. recording a graph).
+void stat_host_ms(const char* name, double ms, uint64_t items);
 
 // A build of independent subproblems ("segments"): every segment's points
 // sit at arena positions [start, start+len) of A (or of the caller's input
@@ -171,12 +175,20 @@ struct BuildJob {
   std::vector<Seg> segs;   // host list of root segments, or:
   const Seg* dsegs = nullptr;  // device list of root segments (dsegs_n of them)
   uint64_t dsegs_n = 0;
-  // Called once on the host, right before the shared-memory base cases are
-  // launched on the stream (work that should overlap them, which are bound by
-  // instruction issue rather than memory traffic, is queued from here).
-  std::function<void()> before_base;
+  // Called once on the host when the shared-memory base cases have been
+  // queued or recorded (work that should overlap them, which are bound by
+  // instruction issue rather than memory traffic, is queued from here).  The
+  // argument is an event that completes when they may start (null: the work
+  // queued so far on the stream).
+  std::function<void(cudaEvent_t)> before_base;
 };
 int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s);
+
+// Builds whose rounds ran from one graph launch (since the library was loaded).
+int graph_builds();
+
+// True while this host thread records a CUDA graph (kernel timers are off).
+bool& flow_capturing();
 
 // Derived shared-memory capacities.
 int base_cap_for(int d);

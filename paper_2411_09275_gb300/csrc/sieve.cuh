@@ -188,6 +188,79 @@ static void device_excl_scan(const uint32_t* in, uint32_t* out, uint64_t n, uint
   PKD_LAUNCH(k_scan_apply<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, partial));
 }
 
+// The same scan over n = min(nmax, *n_dev * mult) elements, a length only
+// the device knows: a fixed grid of SCAN_BLOCKS blocks, each over a
+// contiguous run of SCAN_TILE pieces (partial needs SCAN_BLOCKS words).
+constexpr int SCAN_BLOCKS = 256;
+
+__device__ __forceinline__ void scan_dev_range(const uint32_t* n_dev, uint32_t mult, uint64_t nmax, uint64_t& n,
+                                               uint64_t& t0, uint64_t& t1) {
+  n = min(nmax, (uint64_t)*n_dev * mult);
+  const uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  const uint64_t per = (tiles + gridDim.x - 1) / gridDim.x;
+  t0 = min(tiles, (uint64_t)blockIdx.x * per);
+  t1 = min(tiles, t0 + per);
+}
+
+static __global__ void k_scan_reduce_dev(const uint32_t* in, const uint32_t* n_dev, uint32_t mult, uint64_t nmax,
+                                         uint32_t* partial) {
+  __shared__ uint32_t sh[33];
+  uint64_t n, t0, t1;
+  scan_dev_range(n_dev, mult, nmax, n, t0, t1);
+  uint32_t s = 0;
+  for (uint64_t i = t0 * SCAN_TILE + threadIdx.x; i < min(n, t1 * SCAN_TILE); i += SCAN_THREADS) s += in[i];
+  uint32_t tot;
+  block_excl_scan<uint32_t>(s, sh, &tot);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+static __global__ void k_scan_apply_dev(const uint32_t* in, uint32_t* out, const uint32_t* n_dev, uint32_t mult,
+                                        uint64_t nmax, const uint32_t* partial) {
+  __shared__ uint32_t sh[33];
+  uint64_t n, t0, t1;
+  scan_dev_range(n_dev, mult, nmax, n, t0, t1);
+  uint32_t carry = partial[blockIdx.x];
+  for (uint64_t t = t0; t < t1; ++t) {
+    const uint64_t base = t * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+      v[k] = (base + k < n) ? in[base + k] : 0;
+      s += v[k];
+    }
+    uint32_t tot;
+    uint32_t e = block_excl_scan<uint32_t>(s, sh, &tot) + carry;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+      if (base + k < n) out[base + k] = e;
+      e += v[k];
+    }
+    carry += tot;
+  }
+}
+
+static void device_excl_scan_dev(const uint32_t* in, uint32_t* out, const uint32_t* n_dev, uint32_t mult,
+                                 uint64_t nmax, uint32_t* partial, cudaStream_t s) {
+  PKD_LAUNCH(k_scan_reduce_dev<<<SCAN_BLOCKS, SCAN_THREADS, 0, s>>>(in, n_dev, mult, nmax, partial));
+  PKD_LAUNCH(k_scan_single<<<1, 1024, 0, s>>>(partial, SCAN_BLOCKS));
+  PKD_LAUNCH(k_scan_apply_dev<<<SCAN_BLOCKS, SCAN_THREADS, 0, s>>>(in, out, n_dev, mult, nmax, partial));
+}
+
+// Streaming multiprocessors of the current device.
+static inline int sm_count() {
+  static int v = -1;
+  if (v < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (v <= 0) v = 1;
+  }
+  return v;
+}
+
+struct RoundDyn;
+
 struct RoundArgs {
   Params p;
   int lam, NB, HN, TILE;
@@ -219,7 +292,45 @@ struct RoundArgs {
   uint64_t shared_cap;
   DevStatus* st;
   long long wait_cycles;  // limit of a streaming kernel's waits (clock cycles)
+  // rounds decided on the device: the round's entry of dyn (selected by
+  // *sel) replaces src, dst, dst_where and children, and the tile count of
+  // the round is *ntiles (null: the launch's own count)
+  const RoundDyn* dyn;
+  const uint32_t* sel;
+  const uint32_t* ntiles;
 };
+
+// The per-round part of a build's arguments when its rounds are decided on
+// the device: one entry for the first round, one for the odd rounds and one
+// for the even rounds after the first (the point buffers alternate).
+struct RoundDyn {
+  Src src;
+  Pts dst;
+  int dst_where, src_where;
+  const Seg* cur;  // segments of the round
+  Seg* children;   // [big segments * NB] buckets of the round
+};
+
+__device__ __forceinline__ RoundArgs with_dyn(const RoundArgs& r0) {
+  RoundArgs r = r0;
+  if (r0.dyn) {
+    const RoundDyn& d = r0.dyn[*r0.sel];
+    r.src = d.src;
+    r.dst = d.dst;
+    r.dst_where = d.dst_where;
+    r.children = d.children;
+  }
+  return r;
+}
+
+// The round's source and destination alone (hot kernels: no struct copy).
+__device__ __forceinline__ Src round_src(const RoundArgs& r) { return r.dyn ? r.dyn[*r.sel].src : r.src; }
+__device__ __forceinline__ Pts round_dst(const RoundArgs& r) { return r.dyn ? r.dyn[*r.sel].dst : r.dst; }
+
+// Tiles of the round: the device count when there is one, else `host`.
+__device__ __forceinline__ uint32_t round_tiles(const RoundArgs& r, uint32_t host) {
+  return r.ntiles ? *r.ntiles : host;
+}
 
 __device__ __forceinline__ uint32_t seg_of_tile(const uint32_t* tile0, uint32_t nseg, uint32_t tile) {
   uint32_t lo = 0, hi = nseg;  // largest s with tile0[s] <= tile
@@ -268,13 +379,13 @@ struct SieveTile {
   uint32_t t0, nt;
 };
 
-__device__ __forceinline__ bool sieve_tile(const RoundArgs& r, SieveTile& t) {
+__device__ __forceinline__ bool sieve_tile(const RoundArgs& r, SieveTile& t, uint32_t tile) {
   const uint32_t nb = *r.nbig;
-  t.s = seg_of_tile(r.tile0, nb, blockIdx.x);
+  t.s = seg_of_tile(r.tile0, nb, tile);
   t.seg = r.big[t.s];
   t.t0 = r.tile0[t.s];
   t.nt = (t.seg.len + r.TILE - 1) / r.TILE;
-  t.first = (uint64_t)(blockIdx.x - t.t0) * r.TILE;
+  t.first = (uint64_t)(tile - t.t0) * r.TILE;
   if (t.first >= t.seg.len) return false;
   t.cnt = (int)min((uint64_t)r.TILE, (uint64_t)t.seg.len - t.first);
   return true;
@@ -293,9 +404,9 @@ __device__ __forceinline__ int walk_bucket(const int2* sk, const int32_t* x, int
 }
 
 template <int D>
-__global__ void __launch_bounds__(SIEVE_THREADS) k_count(RoundArgs r) {
+__device__ __forceinline__ void count_tile(const RoundArgs& r, uint32_t tile) {
   SieveTile t;
-  if (!sieve_tile(r, t)) return;
+  if (!sieve_tile(r, t, tile)) return;
   extern __shared__ __align__(16) uint8_t sm[];
   int2* sk = (int2*)sm;
   unsigned* lh = (unsigned*)(sk + r.HN);
@@ -325,15 +436,25 @@ __global__ void __launch_bounds__(SIEVE_THREADS) k_count(RoundArgs r) {
   }
   __syncthreads();
   const uint64_t hb = (uint64_t)t.t0 * r.NB;
-  const uint32_t tl = blockIdx.x - t.t0;
+  const uint32_t tl = tile - t.t0;
   for (int b = threadIdx.x; b < r.NB; b += blockDim.x) r.hist[hb + (uint64_t)b * t.nt + tl] = lh[b];
 }
 
+// One tile a block at a time (the grid strides over the round's tiles).
 template <int D>
-__global__ void __launch_bounds__(SIEVE_THREADS) k_scatter(RoundArgs r) {
-  if (pkd_failed_block(r.st)) return;
+__global__ void __launch_bounds__(SIEVE_THREADS) k_count(RoundArgs r0) {
+  const RoundArgs r = with_dyn(r0);
+  const uint32_t nt = round_tiles(r, gridDim.x);
+  for (uint32_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    count_tile<D>(r, tile);
+    __syncthreads();
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void scatter_tile(const RoundArgs& r, uint32_t tile) {
   SieveTile t;
-  if (!sieve_tile(r, t)) return;
+  if (!sieve_tile(r, t, tile)) return;
   extern __shared__ __align__(16) uint8_t sm[];
   int2* sk = (int2*)sm;
   unsigned* cur = (unsigned*)(sk + r.HN);      // [NB] per-bucket counters, then starts
@@ -386,7 +507,7 @@ __global__ void __launch_bounds__(SIEVE_THREADS) k_scatter(RoundArgs r) {
     }
   }
   const uint64_t hb = (uint64_t)t.t0 * r.NB;
-  const uint32_t tl = blockIdx.x - t.t0;
+  const uint32_t tl = tile - t.t0;
   const uint32_t segbase = r.hscan[hb];
   for (int b = threadIdx.x; b < r.NB; b += blockDim.x)
     gbase[b] = r.hscan[hb + (uint64_t)b * t.nt + tl] - segbase;
@@ -412,6 +533,17 @@ __global__ void __launch_bounds__(SIEVE_THREADS) k_scatter(RoundArgs r) {
   }
 }
 
+template <int D>
+__global__ void __launch_bounds__(SIEVE_THREADS) k_scatter(RoundArgs r0) {
+  if (pkd_failed_block(r0.st)) return;
+  const RoundArgs r = with_dyn(r0);
+  const uint32_t nt = round_tiles(r, gridDim.x);
+  for (uint32_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    scatter_tile<D>(r, tile);
+    __syncthreads();
+  }
+}
+
 static size_t scatter_smem(int HN, int NB, int D, int tile) {
   return (size_t)HN * 8 + (size_t)NB * 12 + (size_t)D * tile * 4 + (size_t)tile * 4 + (size_t)tile * 2;
 }
@@ -419,9 +551,11 @@ static size_t scatter_smem(int HN, int NB, int D, int tile) {
 template <int D>
 static void launch_count_tiles(const RoundArgs& r, uint32_t tiles, uint64_t pts, const char* fam, cudaStream_t s) {
   const size_t sm = (size_t)r.HN * 8 + (size_t)r.NB * 4;
+  // with a device tile count, `tiles` is only a bound: a grid of resident blocks strides over the tiles
+  const uint32_t grid = r.ntiles ? std::min<uint32_t>(tiles, (uint32_t)sm_count() * 2) : tiles;
   KTimer kt;
   ktimer_begin(kt, fam, pts, s);
-  PKD_LAUNCH(k_count<D><<<tiles, SIEVE_THREADS, sm, s>>>(r));
+  PKD_LAUNCH(k_count<D><<<grid, SIEVE_THREADS, sm, s>>>(r));
   ktimer_end(kt);
 }
 
@@ -434,9 +568,10 @@ static void launch_scatter_tiles(const RoundArgs& r, uint32_t tiles, uint64_t pt
     cudaFuncSetAttribute(k_scatter<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     set = true;
   }
+  const uint32_t grid = r.ntiles ? std::min<uint32_t>(tiles, (uint32_t)sm_count() * 2) : tiles;
   KTimer kt;
   ktimer_begin(kt, fam, pts, s);
-  PKD_LAUNCH(k_scatter<D><<<tiles, SIEVE_THREADS, sm, s>>>(r));
+  PKD_LAUNCH(k_scatter<D><<<grid, SIEVE_THREADS, sm, s>>>(r));
   ktimer_end(kt);
 }
 

@@ -150,7 +150,7 @@ __host__ __device__ inline size_t stm_stage_words(int tile, bool ids) {
 // Producer warp: fill stage `buf` with tile `tile` of segment s and arrive on
 // `full` with the bytes the bulk copies will deliver.
 template <int D>
-__device__ void stm_produce(const RoundArgs& r, uint32_t s, uint32_t tile, bool ids, uint32_t* buf,
+__device__ void stm_produce(const RoundArgs& r, const Src& src, uint32_t s, uint32_t tile, bool ids, uint32_t* buf,
                             StmStage<D>* rec, uint64_t* full, uint32_t* gbs, uint8_t* sbk) {
   const int lane = lane_id();
   const StmTile t = stm_tile(r, s, tile);
@@ -162,17 +162,17 @@ __device__ void stm_produce(const RoundArgs& r, uint32_t s, uint32_t tile, bool 
   const size_t stride = stm_stride(r.TILE);
   StmArr arr[D + 1];
   int implicit = 0;
-  if (!r.src.is_aos) {
+  if (!src.is_aos) {
 #pragma unroll
-    for (int j = 0; j < D; ++j) arr[j] = stm_arr(r.src.soa.c + (uint64_t)j * r.src.soa.stride + t.g0, t.cnt);
-    arr[D] = stm_arr(r.src.soa.id + t.g0, ids ? t.cnt : 0);
+    for (int j = 0; j < D; ++j) arr[j] = stm_arr(src.soa.c + (uint64_t)j * src.soa.stride + t.g0, t.cnt);
+    arr[D] = stm_arr(src.soa.id + t.g0, ids ? t.cnt : 0);
   } else {
-    arr[0] = stm_arr(r.src.aos + t.g0 * D, t.cnt * D);
+    arr[0] = stm_arr(src.aos + t.g0 * D, t.cnt * D);
 #pragma unroll
     for (int j = 1; j < D; ++j) arr[j] = stm_arr(nullptr, 0);
     arr[D] = stm_arr(nullptr, 0);
     if (ids) {
-      if (r.src.aos_ids) arr[D] = stm_arr(r.src.aos_ids + t.g0, t.cnt);
+      if (src.aos_ids) arr[D] = stm_arr(src.aos_ids + t.g0, t.cnt);
       else implicit = 1;
     }
   }
@@ -244,7 +244,7 @@ __device__ __forceinline__ void stm_drain(uint64_t* full, uint32_t issued, DevSt
 
 // Producer warp main loop over the CTA's tiles.
 template <int D>
-__device__ void stm_producer(const RoundArgs& r, uint32_t tb, uint32_t te, bool ids, uint32_t* bufs, size_t swords,
+__device__ void stm_producer(const RoundArgs& r, const Src& src, uint32_t tb, uint32_t te, bool ids, uint32_t* bufs, size_t swords,
                              StmStage<D>* recs, uint64_t* full, uint64_t* empty, uint32_t* gbs,
                              uint8_t* sbk) {
   const uint32_t nb = *r.nbig;
@@ -262,7 +262,7 @@ __device__ void stm_producer(const RoundArgs& r, uint32_t tb, uint32_t te, bool 
       fence_proxy_async_smem();
     }
     s = stm_advance(r, s, nb, tb + k);
-    stm_produce<D>(r, s, tb + k, ids, bufs + stg * swords, &recs[stg], &full[stg], gbs ? gbs + stg * r.NB : nullptr,
+    stm_produce<D>(r, src, s, tb + k, ids, bufs + stg * swords, &recs[stg], &full[stg], gbs ? gbs + stg * r.NB : nullptr,
                    sbk ? sbk + (size_t)stg * r.TILE : nullptr);
   }
   stm_drain(full, k, r.st);
@@ -342,9 +342,9 @@ __global__ void __launch_bounds__(STM_THREADS) k_count_stream(RoundArgs r, uint3
   uint16_t* wb = (uint16_t*)(lh + r.NB);
   int* flag = (int*)(wb + L + 2);
   const int tid = threadIdx.x;
-  const bool aos = r.src.is_aos != 0;
+  const bool aos = (r.dyn ? r.dyn[*r.sel].src.is_aos : r.src.is_aos) != 0;
   uint32_t tb, te;
-  stm_range(ntiles, tb, te);
+  stm_range(round_tiles(r, ntiles), tb, te);
   if (tb >= te) return;
   if (tid == 0) {
     for (int k = 0; k < STM_STAGES; ++k) {
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(STM_THREADS) k_count_stream(RoundArgs r, uint3
   for (int b = tid; b < r.NB; b += blockDim.x) lh[b] = 0;
   __syncthreads();
   if (tid >= STM_CONSUMERS) {
-    stm_producer<D>(r, tb, te, false, bufs, swords, recs, full, empty, nullptr, nullptr);
+    stm_producer<D>(r, round_src(r), tb, te, false, bufs, swords, recs, full, empty, nullptr, nullptr);
     return;
   }
   uint32_t cur_seg = 0xFFFFFFFFu;
@@ -442,9 +442,9 @@ __global__ void __launch_bounds__(STM_THREADS) k_scatter_stream(RoundArgs r, uin
   uint8_t* sbk = r.bkt ? (uint8_t*)(((uintptr_t)(gbs + STM_STAGES * r.NB) + 15) & ~(uintptr_t)15)
                        : nullptr;  // [STM_STAGES][TILE], 16-byte aligned for the bulk copies
   const int tid = threadIdx.x;
-  const bool aos = r.src.is_aos != 0;
+  const bool aos = (r.dyn ? r.dyn[*r.sel].src.is_aos : r.src.is_aos) != 0;
   uint32_t tb, te;
-  stm_range(ntiles, tb, te);
+  stm_range(round_tiles(r, ntiles), tb, te);
   if (tb >= te) return;
   if (tid == 0) {
     for (int k = 0; k < STM_STAGES; ++k) {
@@ -453,10 +453,12 @@ __global__ void __launch_bounds__(STM_THREADS) k_scatter_stream(RoundArgs r, uin
     }
     fence_mbar_init();
   }
+  __shared__ Pts sdst[1];
+  if (tid == 0) sdst[0] = round_dst(r);
   for (int b = tid; b < r.NB; b += blockDim.x) cur[b] = 0;
   __syncthreads();
   if (tid >= STM_CONSUMERS) {
-    stm_producer<D>(r, tb, te, true, bufs, swords, recs, full, empty, gbs, sbk);
+    stm_producer<D>(r, round_src(r), tb, te, true, bufs, swords, recs, full, empty, gbs, sbk);
     return;
   }
   uint32_t cur_seg = 0xFFFFFFFFu;
@@ -540,10 +542,11 @@ __global__ void __launch_bounds__(STM_THREADS) k_scatter_stream(RoundArgs r, uin
     // every bucket's run leaves the tile as one contiguous range; the next
     // tile overwrites the staging arrays only after three more barriers
     {
+      const Pts dst = *sdst;  // re-read after the barriers: not held in registers
       int32_t* oc[D];
 #pragma unroll
-      for (int j = 0; j < D; ++j) oc[j] = r.dst.c + (uint64_t)j * r.dst.stride + seg_start;
-      uint32_t* oid = r.dst.id + seg_start;
+      for (int j = 0; j < D; ++j) oc[j] = dst.c + (uint64_t)j * dst.stride + seg_start;
+      uint32_t* oid = dst.id + seg_start;
 #pragma unroll
       for (int u = 0; u < STM_PER; ++u) {
         const int pos = u * STM_CONSUMERS + tid;

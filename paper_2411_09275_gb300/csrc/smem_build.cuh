@@ -85,6 +85,8 @@ struct SmemArgs {
   int heap_n;              // 2^(lambda+1)
   uint64_t shared_cap;     // first per-position node slot
   DevStatus* st;
+  uint32_t list_cap;       // entries segs / jobs can hold (bounds the device count)
+  uint32_t* grab;          // persistent launches: next entry to take (zeroed before the launch)
 };
 
 struct SmemLayout {

@@ -102,7 +102,7 @@ static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void ktimer_begin(KTimer& k, const char* name, uint64_t items, cudaStream_t s) {
-  k.on = g_timing;
+  k.on = g_timing && !flow_capturing();
   if (!k.on) return;
   k.name = name;
   k.items = items;
@@ -117,6 +117,15 @@ void stat_items(const char* name, uint64_t items) {
   std::lock_guard<std::mutex> g(g_tmu);
   auto& st = g_stats[name];
   st.launches++;
+  st.items += items;
+}
+
+void stat_host_ms(const char* name, double ms, uint64_t items) {
+  if (!g_timing) return;
+  std::lock_guard<std::mutex> g(g_tmu);
+  auto& st = g_stats[name];
+  st.launches++;
+  st.ms += ms;
   st.items += items;
 }
 
@@ -517,10 +526,13 @@ int pkd_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const pkd_
   int eid = PKD_OK;
   bool queued = false;
   pkd_tree* tt = t;
-  auto fill_ids = [&]() {
+  auto fill_ids = [&](cudaEvent_t start) {
     queued = true;
-    cudaEventRecord(ev[0], s);
-    cudaStreamWaitEvent(s2, ev[0], 0);
+    if (!start) {
+      cudaEventRecord(ev[0], s);
+      start = ev[0];
+    }
+    cudaStreamWaitEvent(s2, start, 0);
     eid = ids_create(tt->m, n, s2);
     if (eid == PKD_OK) ids_claim(tt->m, coords, ids, n, nullptr, s2);
     cudaEventRecord(ev[1], s2);
@@ -535,7 +547,7 @@ int pkd_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const pkd_
   trace_mark(s, "build: alloc tree");
   e = run_build(t->m, job, s);
   trace_mark(s, "build: run_build");
-  if (e == PKD_OK && !queued) fill_ids();  // run_build returned before its base cases
+  if (e == PKD_OK && !queued) fill_ids(nullptr);  // run_build returned before its base cases
   cudaStreamWaitEvent(s, ev[1], 0);
   if (e == PKD_OK) e = eid;
   if (e == PKD_OK) e = check_status(t->m, s);
@@ -621,6 +633,9 @@ int pkd_set_option(const char* name, int64_t value) {
   } else if (n == "wait_cycles") {
     if (value < 0 || value > 4000000000000ll) return PKD_EINVAL;
     knobs().wait_cycles = value;
+  } else if (n == "graph_rounds") {
+    if (value != 0 && value != 1) return PKD_EINVAL;
+    knobs().graph_rounds = (int)value;
   } else if (n == "tile") {
     if (value < 256 || value > 4096 || (value & (value - 1))) return PKD_EINVAL;
     knobs().tile = (int)value;
@@ -670,6 +685,12 @@ int pkd_kernel_stats(const char* name, uint64_t* launches, double* total_ms, uin
   std::lock_guard<std::mutex> g(g_tmu);
   if (std::string(name) == "launches") {
     if (launches) *launches = g_launches.load();
+    if (total_ms) *total_ms = 0;
+    if (items) *items = 0;
+    return PKD_OK;
+  }
+  if (std::string(name) == "graph_builds") {  // since the library was loaded
+    if (launches) *launches = (uint64_t)graph_builds();
     if (total_ms) *total_ms = 0;
     if (items) *items = 0;
     return PKD_OK;

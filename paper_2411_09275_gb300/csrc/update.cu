@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(ITEM_WARPS * 32) k_route_emit(UpdArgs a) {
 __global__ void k_copy_round(RoundArgs r, Pts F) {
   if (pkd_failed_block(r.st)) return;
   SieveTile t;
-  if (!sieve_tile(r, t)) return;
+  if (!sieve_tile(r, t, blockIdx.x)) return;
   const int d = r.p.d;
   for (int i = threadIdx.x; i < t.cnt; i += blockDim.x) {
     const uint64_t p = t.seg.start + t.first + (uint64_t)i;

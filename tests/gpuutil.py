@@ -36,7 +36,7 @@ def oparams(p) -> O.Params:
 
 
 # library options whose default is not 0
-DEFAULTS = {"tile": 2048, "wait_cycles": 4_000_000_000, "fail_alloc_after": -1}
+DEFAULTS = {"tile": 2048, "wait_cycles": 4_000_000_000, "fail_alloc_after": -1, "graph_rounds": 1}
 
 
 @contextlib.contextmanager

@@ -47,20 +47,26 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("base_kernel,sieve_kernel", [(0, 0), (0, 2), (1, 1)],
-                         ids=["sorted-stream", "sorted-stream-rewalk", "select-tiles"])
+# graph_rounds 1: every round decided on the device (one graph launch);
+# 0: the same kernels sequenced by the host
+@pytest.mark.parametrize("base_kernel,sieve_kernel,graph_rounds", [(0, 0, 1), (0, 2, 1), (1, 1, 1), (0, 0, 0), (1, 1, 0)],
+                         ids=["sorted-stream", "sorted-stream-rewalk", "select-tiles", "sorted-stream-host",
+                              "select-tiles-host"])
 @pytest.mark.parametrize("name,n,d,kind,over,kn", CASES, ids=[c[0] for c in CASES])
-def test_build_matches_oracle(name, n, d, kind, over, kn, base_kernel, sieve_kernel):
+def test_build_matches_oracle(name, n, d, kind, over, kn, base_kernel, sieve_kernel, graph_rounds):
     pkd = _pkd()
     X = make_points(kind, n, d, 1000 + n + d)
     ids = ((np.arange(n, dtype=np.uint64) * 2654435761) % (1 << 32)).astype(np.uint32)
     p = pkd.Params(d=d, seed=42, **over)
-    with knobs(base_kernel=base_kernel, sieve_kernel=sieve_kernel, **kn):
+    g0 = pkd.pkd_kernel_stats("graph_builds")[0]
+    with knobs(base_kernel=base_kernel, sieve_kernel=sieve_kernel, graph_rounds=graph_rounds, **kn):
         t = pkd.Tree(to_dev(X), ids_dev(ids), p)
         got = t.export()
     want = O.OracleTree(X, ids, oparams(p)).export()
     U.assert_exports_equal(got, want)
     assert t.size == n
+    # the build's rounds ran from one graph launch exactly when asked
+    assert pkd.pkd_kernel_stats("graph_builds")[0] - g0 == graph_rounds
     t.close()
 
 

@@ -37,13 +37,18 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("graph_rounds", [1, 0], ids=["device-rounds", "host-rounds"])
 @pytest.mark.parametrize("name,sizes,d,kind,over,kn", CASES, ids=[c[0] for c in CASES])
-def test_forest_trees_match_their_own_oracle_builds(name, sizes, d, kind, over, kn):
+def test_forest_trees_match_their_own_oracle_builds(name, sizes, d, kind, over, kn, graph_rounds):
     pkd = _pkd()
     X, ids, off = _forest_inputs(sizes, d, kind, 500 + len(sizes))
     p = pkd.Params(d=d, seed=7, **over)
-    with knobs(**kn):
+    g0 = pkd.pkd_kernel_stats("graph_builds")[0]
+    with knobs(graph_rounds=graph_rounds, **kn):
         f = pkd.pkd_build_forest(to_dev(X), ids_dev(ids), off, p)
+    # every tree's rounds, as extra roots of one build, ran from one graph
+    # launch with no host synchronisation between rounds (device rounds)
+    assert pkd.pkd_kernel_stats("graph_builds")[0] - g0 == graph_rounds
     try:
         assert pkd.lib().pkd_forest_trees(f) == len(sizes)
         for t in range(len(sizes)):

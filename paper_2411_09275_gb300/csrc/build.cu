@@ -598,34 +598,39 @@ __global__ void k_classify(const RoundDyn* dyn, const uint32_t* sel, const uint3
 }
 
 // Sample: points whose hash at the segment's depth passes the rate test.
-// Persistent CTAs, each over a contiguous run of tiles: a CTA hashes a
-// tile's ids and appends the sampled positions to a shared list; once per
-// run of tiles of one segment (or before the list could overflow) it
-// reserves the list's slots in the segment's sample with one atomic and
-// gathers their coordinates.  One atomic per CTA and segment instead of one
-// per tile: the first round's tiles all belong to one segment.  The order of
-// a sample is immaterial: only its multiset enters the skeleton.
+// Persistent CTAs, each over a contiguous run of tiles.  Every warp hashes
+// 32 ids at a time and appends the positions that pass to a shared list
+// through one shared-memory atomic (the order of a sample is immaterial:
+// only its multiset enters the skeleton), so a tile costs no block-wide
+// barrier.  Once per run of tiles of one segment, or before the list could
+// overflow, the CTA reserves the list's slots in the segment's sample with
+// one global atomic and gathers their coordinates.  The next tile's ids are
+// loaded before the current tile's hashes, so a warp keeps a tile of loads
+// in flight.
 constexpr int SAMPLE_THREADS = 256;
 constexpr int SAMPLE_PER = 16;      // points per thread (tiles of up to 4096)
 constexpr int SAMPLE_LIST = 8192;   // sampled positions held before a flush
 constexpr int SAMPLE_CTAS_PER_SM = 4;
 
-__device__ __forceinline__ void sample_flush(const RoundArgs& r, const Src& src, const Seg& seg, uint32_t s, const uint32_t* lst,
-                                             int nl, uint32_t* base_sh) {
-  if (threadIdx.x == 0) *base_sh = atomicAdd(&r.scnt[s], (uint32_t)nl);
+__device__ __forceinline__ void sample_flush(const RoundArgs& r, const Src& src, const Seg& seg, uint32_t s,
+                                             const uint32_t* lst, uint32_t* nl_sh, uint32_t* base_sh) {
+  __syncthreads();  // every append is in the list
+  const uint32_t nl = *nl_sh;
+  if (threadIdx.x == 0 && nl) *base_sh = atomicAdd(&r.scnt[s], nl);
   __syncthreads();
   const uint64_t o0 = seg.start + *base_sh;
   const int d = r.p.d;
-  for (int i = threadIdx.x; i < nl; i += SAMPLE_THREADS) {
+  for (uint32_t i = threadIdx.x; i < nl; i += SAMPLE_THREADS) {
     const uint64_t g = seg.start + lst[i];
     for (int j = 0; j < d; ++j) r.samp.c[(uint64_t)j * r.samp.stride + o0 + i] = src.x(d, j, g);
   }
+  __syncthreads();  // the list is read before it is refilled
+  if (threadIdx.x == 0) *nl_sh = 0;
   __syncthreads();
 }
 
 __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(RoundArgs r, uint32_t ntiles_host) {
-  __shared__ uint32_t sh[33];
-  __shared__ uint32_t base_sh;
+  __shared__ uint32_t base_sh, nl_sh;
   __shared__ uint32_t lst[SAMPLE_LIST];
   const Src src = round_src(r);
   const uint32_t ntiles = round_tiles(r, ntiles_host);
@@ -633,16 +638,30 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(RoundArgs r, uint32_t
   const uint32_t tb = min(ntiles, blockIdx.x * per_cta), te = min(ntiles, tb + per_cta);
   if (tb >= te) return;
   const uint32_t nb = *r.nbig;
+  const int lane = lane_id();
+  if (threadIdx.x == 0) nl_sh = 0;
+  __syncthreads();
   uint32_t s = seg_of_tile(r.tile0, nb, tb);
   Seg seg = r.big[s];
   uint32_t t0 = r.tile0[s];
   int shift = sample_shift(r.p, seg.len);
   uint64_t key = sample_key(r.p.seed, seg.depth);
-  int nl = 0;  // uniform
+  // ids of one tile: SAMPLE_PER per thread, loaded a tile ahead
+  auto load_ids = [&](uint32_t tile, uint32_t ts, uint32_t (&ids)[SAMPLE_PER]) {
+    const Seg sg = r.big[ts];
+    const uint64_t first = (uint64_t)(tile - r.tile0[ts]) * r.TILE;
+    const int cnt = first >= sg.len ? 0 : (int)min((uint64_t)r.TILE, (uint64_t)sg.len - first);
+#pragma unroll
+    for (int k = 0; k < SAMPLE_PER; ++k) {
+      const int i = k * SAMPLE_THREADS + threadIdx.x;
+      ids[k] = i < cnt ? src.id(sg.start + first + (uint64_t)i) : 0u;
+    }
+  };
+  uint32_t nxt[SAMPLE_PER];
+  load_ids(tb, s, nxt);
   for (uint32_t tile = tb; tile < te; ++tile) {
-    if (s + 1 < nb && r.tile0[s + 1] <= tile) {  // the next segment with tiles
-      if (nl) sample_flush(r, src, seg, s, lst, nl, &base_sh);
-      nl = 0;
+    if (s + 1 < nb && r.tile0[s + 1] <= tile) {  // the next segment with tiles (uniform)
+      sample_flush(r, src, seg, s, lst, &nl_sh, &base_sh);
       do {
         ++s;
       } while (s + 1 < nb && r.tile0[s + 1] <= tile);
@@ -652,33 +671,29 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(RoundArgs r, uint32_t
       key = sample_key(r.p.seed, seg.depth);
     }
     const uint64_t first = (uint64_t)(tile - t0) * r.TILE;
-    if (first >= seg.len) continue;
-    const int cnt = (int)min((uint64_t)r.TILE, (uint64_t)seg.len - first);
-    if (nl + cnt > SAMPLE_LIST) {
-      sample_flush(r, src, seg, s, lst, nl, &base_sh);
-      nl = 0;
-    }
+    const int cnt = first >= seg.len ? 0 : (int)min((uint64_t)r.TILE, (uint64_t)seg.len - first);
+    if (cnt == 0) continue;
     uint32_t ids[SAMPLE_PER];
 #pragma unroll
-    for (int k = 0; k < SAMPLE_PER; ++k) {
-      const int i = k * SAMPLE_THREADS + threadIdx.x;
-      if (i < cnt) ids[k] = src.id(seg.start + first + (uint64_t)i);
-    }
-    unsigned fl = 0;
+    for (int k = 0; k < SAMPLE_PER; ++k) ids[k] = nxt[k];
+    if (tile + 1 < te) load_ids(tile + 1, stm_advance(r, s, nb, tile + 1), nxt);
+    // a tile's samples fit when the list has room for the whole tile
+    if (*(volatile uint32_t*)&nl_sh + (uint32_t)cnt > (uint32_t)SAMPLE_LIST)
+      sample_flush(r, src, seg, s, lst, &nl_sh, &base_sh);
 #pragma unroll
     for (int k = 0; k < SAMPLE_PER; ++k) {
       const int i = k * SAMPLE_THREADS + threadIdx.x;
-      if (i < cnt && in_sample_k(key, ids[k], shift)) fl |= 1u << k;
+      if (k * SAMPLE_THREADS >= cnt) break;  // uniform
+      const bool f = i < cnt && in_sample_k(key, ids[k], shift);
+      const unsigned m = __ballot_sync(FULL_MASK, f);
+      if (!m) continue;
+      uint32_t b = 0;
+      if (lane == 0) b = atomicAdd(&nl_sh, (uint32_t)__popc(m));
+      b = __shfl_sync(FULL_MASK, b, 0);
+      if (f) lst[b + __popc(m & lanemask_lt())] = (uint32_t)(first + (uint64_t)i);
     }
-    uint32_t total;
-    const uint32_t off = block_excl_scan<uint32_t>((uint32_t)__popc(fl), sh, &total);
-    int q = 0;
-#pragma unroll
-    for (int k = 0; k < SAMPLE_PER; ++k)
-      if (fl & (1u << k)) lst[nl + (int)off + q++] = (uint32_t)(first + (uint64_t)(k * SAMPLE_THREADS + threadIdx.x));
-    nl += (int)total;
   }
-  if (nl) sample_flush(r, src, seg, s, lst, nl, &base_sh);
+  sample_flush(r, src, seg, s, lst, &nl_sh, &base_sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -1381,37 +1396,6 @@ cudaStream_t flow_stream(int level) {
   return st;
 }
 
-// An executable graph stays alive until an event after its launch has
-// completed; finished ones are destroyed on the next build.
-struct RetiredGraph {
-  cudaGraphExec_t exec;
-  cudaGraph_t graph;
-  cudaEvent_t done;
-  cudaEvent_t base;  // external event recorded by the graph (may be null)
-};
-static std::mutex g_retire_mu;
-static std::vector<RetiredGraph> g_retired;
-
-static void reap_graphs(bool all) {
-  std::lock_guard<std::mutex> lk(g_retire_mu);
-  std::vector<RetiredGraph> keep;
-  for (const RetiredGraph& r : g_retired) {
-    if (all) cudaEventSynchronize(r.done);
-    if (cudaEventQuery(r.done) == cudaSuccess) {
-      cudaGraphExecDestroy(r.exec);
-      cudaGraphDestroy(r.graph);
-      cudaEventDestroy(r.done);
-      if (r.base) cudaEventDestroy(r.base);
-    } else {
-      cudaGetLastError();
-      keep.push_back(r);
-    }
-  }
-  g_retired.swap(keep);
-}
-
-static int g_graph_builds = 0;  // builds whose rounds ran from one graph launch
-
 // The launch shape of a base-case kernel node, set on the device from the
 // length of its list just before it runs (a graph's kernel nodes are
 // recorded with a placeholder grid; the lists' lengths exist only on the
@@ -1425,6 +1409,60 @@ struct BaseShape {
   uint32_t pad;
 };
 constexpr int MAX_SHAPES = 4;
+
+// Recorded builds, reused: a graph's kernels take every pointer and size as
+// an argument, so a build whose arguments are all equal to an earlier one's
+// (the same tree memory, scratch and input at the same addresses: repeated
+// builds of one size, which the stream-ordered pool tends to place at the
+// same addresses) launches that graph again instead of recording a new one.
+// The key lists every value the recorded kernels take.  An entry is
+// destroyed only after its last launch has completed.
+struct GraphEntry {
+  std::vector<uint64_t> key;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaEvent_t done = nullptr;  // after the entry's last launch
+  cudaEvent_t base = nullptr;  // external event: the base cases may start
+  BaseShape shapes[MAX_SHAPES];
+  uint64_t used = 0;
+};
+constexpr int GRAPH_CACHE = 4;
+static std::vector<GraphEntry> g_graphs;  // guarded by flow_mutex()
+static uint64_t g_graph_clock = 0;
+
+static void graph_entry_destroy(GraphEntry& e) {
+  if (e.done) cudaEventSynchronize(e.done);
+  if (e.exec) cudaGraphExecDestroy(e.exec);
+  if (e.graph) cudaGraphDestroy(e.graph);
+  if (e.done) cudaEventDestroy(e.done);
+  if (e.base) cudaEventDestroy(e.base);
+  e = GraphEntry{};
+}
+
+static GraphEntry* graph_find(const std::vector<uint64_t>& key) {
+  for (GraphEntry& e : g_graphs)
+    if (e.key == key) {
+      e.used = ++g_graph_clock;
+      return &e;
+    }
+  return nullptr;
+}
+
+static GraphEntry* graph_slot() {
+  if ((int)g_graphs.size() < GRAPH_CACHE) {
+    g_graphs.emplace_back();
+    return &g_graphs.back();
+  }
+  GraphEntry* lru = &g_graphs[0];
+  for (GraphEntry& e : g_graphs)
+    if (e.used < lru->used) lru = &e;
+  graph_entry_destroy(*lru);
+  return lru;
+}
+
+static int g_graph_builds = 0;  // builds whose rounds ran from one graph launch
+static int g_graph_reuses = 0;  // ... of them, launches of a recorded graph
+
 
 __global__ void k_base_shapes(const BaseShape* sh, int n) {
   if (threadIdx.x != 0) return;
@@ -1498,7 +1536,6 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
   const int scap = skel_cap_for(d);
   const uint64_t base = job.base, extent = std::max<uint64_t>(job.extent, 1);
   const int nsm = num_sms();
-  reap_graphs(false);
   Scratch sc{s, {}};
 
   // scratch point buffer B and two sample buffers over [base, base + extent)
@@ -1868,6 +1905,41 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     if (!shblk.p) return PKD_ENOMEM;
     static_assert(MAX_SHAPES * sizeof(BaseShape) <= PINNED_BLOCK, "shape block");
     BaseShape* hshape = (BaseShape*)shblk.p;
+
+    // every value the recorded kernels take as an argument
+    std::vector<uint64_t> key;
+    {
+      auto put = [&](uint64_t v) { key.push_back(v); };
+      auto putp = [&](const void* q) { key.push_back((uint64_t)(uintptr_t)q); };
+      int dev = 0;
+      cudaGetDevice(&dev);
+      put((uint64_t)dev);
+      for (void* q : sc.ptrs) putp(q);  // every scratch buffer, in allocation order
+      putp(t.A.c), putp(t.A.id), put(t.A.stride), putp(t.nodes), putp(t.ndim), putp(t.st), putp(t.shared_next);
+      put(t.shared_cap);
+      putp(job.input_coords), putp(job.input_ids), put(job.base), put(job.extent), putp(roots), put(nroots);
+      put((uint64_t)p.d), put((uint64_t)p.phi), put((uint64_t)p.lambda), put((uint64_t)p.sigma_log2);
+      put((uint64_t)p.sigma_os), put((uint64_t)p.count_mode), put((uint64_t)p.alpha_num), put((uint64_t)p.alpha_den);
+      put(p.seed);
+      put((uint64_t)TILE), put(cap), put((uint64_t)scap), put(cap2), put(wcap), put((uint64_t)nsm);
+      put((uint64_t)knobs().sieve_kernel), put((uint64_t)knobs().base_kernel), put((uint64_t)knobs().wait_cycles);
+      put((uint64_t)record_buckets(NB));
+    }
+    GraphEntry* ent = graph_find(key);
+    if (ent) {
+      memcpy(hshape, ent->shapes, sizeof(ent->shapes));
+      PKD_CUDA(cudaMemcpyAsync(dshape, hshape, sizeof(ent->shapes), cudaMemcpyHostToDevice, s));
+      PKD_CUDA(cudaGraphLaunch(ent->exec, s));
+      PKD_CUDA(cudaEventRecord(ent->done, s));
+      ++g_graph_builds;
+      ++g_graph_reuses;
+      stat_host_ms("graph_record",
+                   std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - rec0).count(), 0);
+      if (job.before_base) job.before_base(ent->base);
+      PKD_CUDA(cudaGetLastError());
+      return PKD_OK;
+    }
+
     int nshape = 0;
     cudaGraphNode_t shape_nodes[MAX_SHAPES] = {};
     cudaEvent_t ready = nullptr, done = nullptr, base_ev = nullptr;
@@ -1908,7 +1980,8 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
       hshape[k].node = make_updatable(shape_nodes[k]);
       if (!hshape[k].node) e = PKD_ECUDA;
     }
-    for (int k = nshape; k < MAX_SHAPES; ++k) hshape[k] = hshape[0];
+    if (e == PKD_OK && nshape == 0) e = PKD_EINTERNAL;
+    for (int k = nshape; e == PKD_OK && k < MAX_SHAPES; ++k) hshape[k] = hshape[0];
     cudaGraphExec_t exec = nullptr;
     if (e == PKD_OK && cudaMemcpyAsync(dshape, hshape, MAX_SHAPES * sizeof(BaseShape), cudaMemcpyHostToDevice, s) !=
                            cudaSuccess)
@@ -1927,10 +2000,14 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
       cudaEventDestroy(base_ev);
       return e;
     }
-    {
-      std::lock_guard<std::mutex> rl(g_retire_mu);
-      g_retired.push_back(RetiredGraph{exec, graph_h, done, base_ev});
-    }
+    ent = graph_slot();
+    ent->key = std::move(key);
+    ent->exec = exec;
+    ent->graph = graph_h;
+    ent->done = done;
+    ent->base = base_ev;
+    memcpy(ent->shapes, hshape, sizeof(ent->shapes));
+    ent->used = ++g_graph_clock;
     ++g_graph_builds;
     stat_host_ms("graph_record",
                  std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - rec0).count(), 1);
@@ -1942,5 +2019,6 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
 }
 
 int graph_builds() { return g_graph_builds; }
+int graph_reuses() { return g_graph_reuses; }
 
 }  // namespace pkd

@@ -186,6 +186,8 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s);
 
 // Builds whose rounds ran from one graph launch (since the library was loaded).
 int graph_builds();
+// ... of them, the builds that launched a graph recorded by an earlier build.
+int graph_reuses();
 
 // True while this host thread records a CUDA graph (kernel timers are off).
 bool& flow_capturing();

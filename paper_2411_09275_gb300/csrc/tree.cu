@@ -692,7 +692,7 @@ int pkd_kernel_stats(const char* name, uint64_t* launches, double* total_ms, uin
   if (std::string(name) == "graph_builds") {  // since the library was loaded
     if (launches) *launches = (uint64_t)graph_builds();
     if (total_ms) *total_ms = 0;
-    if (items) *items = 0;
+    if (items) *items = (uint64_t)graph_reuses();
     return PKD_OK;
   }
   if (std::string(name) == "allocations") {  // since the library was loaded

@@ -131,3 +131,30 @@ def test_build_validation_every_position_and_alignment(n):
                 with pytest.raises(pkd.PkdError) as e:
                     pkd.Tree(view.view(n, d), None, pkd.Params(d=d))
                 assert e.value.code == pkd.PKD_EINVAL
+
+
+def test_recorded_build_graph_relaunched_on_new_data():
+    """A build whose arguments all equal an earlier build's (same input
+    buffer, same sizes: the pool tends to hand out the same scratch) launches
+    the earlier build's graph again; the graph reads the data at run time, so
+    new coordinates in the same buffer still give the oracle's tree."""
+    import torch
+
+    pkd = _pkd()
+    n, d = 60000, 3
+    p = pkd.Params(d=d, phi=8, lam=4, sigma_log2=2, sigma_os=4)
+    buf = torch.empty((n, d), dtype=torch.int32, device="cuda")
+    reused = 0
+    with knobs(base_cap=1024, skel_cap=256):
+        for r in range(4):
+            X = make_points("varden" if r % 2 else "uniform", n, d, 900 + r)
+            buf.copy_(torch.from_numpy(X))
+            g0, u0 = pkd.pkd_kernel_stats("graph_builds")[0], pkd.pkd_kernel_stats("graph_builds")[2]
+            t = pkd.Tree(buf, None, p)
+            g1, u1 = pkd.pkd_kernel_stats("graph_builds")[0], pkd.pkd_kernel_stats("graph_builds")[2]
+            assert g1 - g0 == 1
+            reused += u1 - u0
+            U.assert_exports_equal(t.export(), O.OracleTree(X, None, oparams(p)).export())
+            t.close()
+    # the same sizes four times: at least one build found its graph recorded
+    assert reused >= 1

@@ -598,39 +598,34 @@ __global__ void k_classify(const RoundDyn* dyn, const uint32_t* sel, const uint3
 }
 
 // Sample: points whose hash at the segment's depth passes the rate test.
-// Persistent CTAs, each over a contiguous run of tiles.  Every warp hashes
-// 32 ids at a time and appends the positions that pass to a shared list
-// through one shared-memory atomic (the order of a sample is immaterial:
-// only its multiset enters the skeleton), so a tile costs no block-wide
-// barrier.  Once per run of tiles of one segment, or before the list could
-// overflow, the CTA reserves the list's slots in the segment's sample with
-// one global atomic and gathers their coordinates.  The next tile's ids are
-// loaded before the current tile's hashes, so a warp keeps a tile of loads
-// in flight.
+// Persistent CTAs, each over a contiguous run of tiles: a CTA hashes a
+// tile's ids and appends the sampled positions to a shared list; once per
+// run of tiles of one segment (or before the list could overflow) it
+// reserves the list's slots in the segment's sample with one atomic and
+// gathers their coordinates.  One atomic per CTA and segment instead of one
+// per tile: the first round's tiles all belong to one segment.  The order of
+// a sample is immaterial: only its multiset enters the skeleton.
 constexpr int SAMPLE_THREADS = 256;
 constexpr int SAMPLE_PER = 16;      // points per thread (tiles of up to 4096)
 constexpr int SAMPLE_LIST = 8192;   // sampled positions held before a flush
 constexpr int SAMPLE_CTAS_PER_SM = 4;
 
-__device__ __forceinline__ void sample_flush(const RoundArgs& r, const Src& src, const Seg& seg, uint32_t s,
-                                             const uint32_t* lst, uint32_t* nl_sh, uint32_t* base_sh) {
-  __syncthreads();  // every append is in the list
-  const uint32_t nl = *nl_sh;
-  if (threadIdx.x == 0 && nl) *base_sh = atomicAdd(&r.scnt[s], nl);
+__device__ __forceinline__ void sample_flush(const RoundArgs& r, const Src& src, const Seg& seg, uint32_t s, const uint32_t* lst,
+                                             int nl, uint32_t* base_sh) {
+  if (threadIdx.x == 0) *base_sh = atomicAdd(&r.scnt[s], (uint32_t)nl);
   __syncthreads();
   const uint64_t o0 = seg.start + *base_sh;
   const int d = r.p.d;
-  for (uint32_t i = threadIdx.x; i < nl; i += SAMPLE_THREADS) {
+  for (int i = threadIdx.x; i < nl; i += SAMPLE_THREADS) {
     const uint64_t g = seg.start + lst[i];
     for (int j = 0; j < d; ++j) r.samp.c[(uint64_t)j * r.samp.stride + o0 + i] = src.x(d, j, g);
   }
-  __syncthreads();  // the list is read before it is refilled
-  if (threadIdx.x == 0) *nl_sh = 0;
   __syncthreads();
 }
 
 __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(RoundArgs r, uint32_t ntiles_host) {
-  __shared__ uint32_t base_sh, nl_sh;
+  __shared__ uint32_t sh[33];
+  __shared__ uint32_t base_sh;
   __shared__ uint32_t lst[SAMPLE_LIST];
   const Src src = round_src(r);
   const uint32_t ntiles = round_tiles(r, ntiles_host);
@@ -638,30 +633,16 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(RoundArgs r, uint32_t
   const uint32_t tb = min(ntiles, blockIdx.x * per_cta), te = min(ntiles, tb + per_cta);
   if (tb >= te) return;
   const uint32_t nb = *r.nbig;
-  const int lane = lane_id();
-  if (threadIdx.x == 0) nl_sh = 0;
-  __syncthreads();
   uint32_t s = seg_of_tile(r.tile0, nb, tb);
   Seg seg = r.big[s];
   uint32_t t0 = r.tile0[s];
   int shift = sample_shift(r.p, seg.len);
   uint64_t key = sample_key(r.p.seed, seg.depth);
-  // ids of one tile: SAMPLE_PER per thread, loaded a tile ahead
-  auto load_ids = [&](uint32_t tile, uint32_t ts, uint32_t (&ids)[SAMPLE_PER]) {
-    const Seg sg = r.big[ts];
-    const uint64_t first = (uint64_t)(tile - r.tile0[ts]) * r.TILE;
-    const int cnt = first >= sg.len ? 0 : (int)min((uint64_t)r.TILE, (uint64_t)sg.len - first);
-#pragma unroll
-    for (int k = 0; k < SAMPLE_PER; ++k) {
-      const int i = k * SAMPLE_THREADS + threadIdx.x;
-      ids[k] = i < cnt ? src.id(sg.start + first + (uint64_t)i) : 0u;
-    }
-  };
-  uint32_t nxt[SAMPLE_PER];
-  load_ids(tb, s, nxt);
+  int nl = 0;  // uniform
   for (uint32_t tile = tb; tile < te; ++tile) {
-    if (s + 1 < nb && r.tile0[s + 1] <= tile) {  // the next segment with tiles (uniform)
-      sample_flush(r, src, seg, s, lst, &nl_sh, &base_sh);
+    if (s + 1 < nb && r.tile0[s + 1] <= tile) {  // the next segment with tiles
+      if (nl) sample_flush(r, src, seg, s, lst, nl, &base_sh);
+      nl = 0;
       do {
         ++s;
       } while (s + 1 < nb && r.tile0[s + 1] <= tile);
@@ -671,29 +652,33 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(RoundArgs r, uint32_t
       key = sample_key(r.p.seed, seg.depth);
     }
     const uint64_t first = (uint64_t)(tile - t0) * r.TILE;
-    const int cnt = first >= seg.len ? 0 : (int)min((uint64_t)r.TILE, (uint64_t)seg.len - first);
-    if (cnt == 0) continue;
+    if (first >= seg.len) continue;
+    const int cnt = (int)min((uint64_t)r.TILE, (uint64_t)seg.len - first);
+    if (nl + cnt > SAMPLE_LIST) {
+      sample_flush(r, src, seg, s, lst, nl, &base_sh);
+      nl = 0;
+    }
     uint32_t ids[SAMPLE_PER];
-#pragma unroll
-    for (int k = 0; k < SAMPLE_PER; ++k) ids[k] = nxt[k];
-    if (tile + 1 < te) load_ids(tile + 1, stm_advance(r, s, nb, tile + 1), nxt);
-    // a tile's samples fit when the list has room for the whole tile
-    if (*(volatile uint32_t*)&nl_sh + (uint32_t)cnt > (uint32_t)SAMPLE_LIST)
-      sample_flush(r, src, seg, s, lst, &nl_sh, &base_sh);
 #pragma unroll
     for (int k = 0; k < SAMPLE_PER; ++k) {
       const int i = k * SAMPLE_THREADS + threadIdx.x;
-      if (k * SAMPLE_THREADS >= cnt) break;  // uniform
-      const bool f = i < cnt && in_sample_k(key, ids[k], shift);
-      const unsigned m = __ballot_sync(FULL_MASK, f);
-      if (!m) continue;
-      uint32_t b = 0;
-      if (lane == 0) b = atomicAdd(&nl_sh, (uint32_t)__popc(m));
-      b = __shfl_sync(FULL_MASK, b, 0);
-      if (f) lst[b + __popc(m & lanemask_lt())] = (uint32_t)(first + (uint64_t)i);
+      if (i < cnt) ids[k] = src.id(seg.start + first + (uint64_t)i);
     }
+    unsigned fl = 0;
+#pragma unroll
+    for (int k = 0; k < SAMPLE_PER; ++k) {
+      const int i = k * SAMPLE_THREADS + threadIdx.x;
+      if (i < cnt && in_sample_k(key, ids[k], shift)) fl |= 1u << k;
+    }
+    uint32_t total;
+    const uint32_t off = block_excl_scan<uint32_t>((uint32_t)__popc(fl), sh, &total);
+    int q = 0;
+#pragma unroll
+    for (int k = 0; k < SAMPLE_PER; ++k)
+      if (fl & (1u << k)) lst[nl + (int)off + q++] = (uint32_t)(first + (uint64_t)(k * SAMPLE_THREADS + threadIdx.x));
+    nl += (int)total;
   }
-  sample_flush(r, src, seg, s, lst, &nl_sh, &base_sh);
+  if (nl) sample_flush(r, src, seg, s, lst, nl, &base_sh);
 }
 
 // ---------------------------------------------------------------------------

@@ -341,8 +341,11 @@ __device__ __forceinline__ void semit_leaf(const Team& tm, const SCtx<D>& cx, co
   }
 }
 
-// flag[p] = sampled at depth t for the points of [lo, hi); the count.
-template <int D>
+// The number of points of [lo, hi) sampled at depth t; with WRITE also
+// flag[p] = sampled.  A node first counts; only a node whose sample reaches
+// the split threshold (rare below the sieve rounds) writes the flags, which
+// only its splits on the sample read.
+template <int D, bool WRITE>
 __device__ __forceinline__ int sdraw_sample(const Team& tm, const SCtx<D>& cx, uint32_t map, int lo, int hi,
                                             uint32_t t, int shift) {
   const uint16_t* P = cx.list(mget(map, 0));
@@ -363,12 +366,12 @@ __device__ __forceinline__ int sdraw_sample(const Team& tm, const SCtx<D>& cx, u
     for (int u = 0; u < U; ++u) {
       if (pp[u] >= 0) {
         const bool f = in_sample_k(key, id[u], shift);
-        cx.flag[pp[u]] = f;
+        if (WRITE) cx.flag[pp[u]] = f;
         c += f;
       }
     }
   }
-  tm.sync();
+  if (WRITE) tm.sync();
   return tm.sum(c);
 }
 
@@ -646,8 +649,11 @@ __device__ int snode(const Team& tm, const SCtx<D>& cx, STask tk, STask* ch) {
       }
       // fewer than 2*sigma_os points cannot reach the split threshold
       int ns = 0;
-      if (n >= 2 * cx.p.sigma_os)
-        ns = sdraw_sample<D>(tm, cx, tk.map, lo, hi, tk.t, sample_shift(cx.p, (uint64_t)n));
+      if (n >= 2 * cx.p.sigma_os) {
+        const int sh = sample_shift(cx.p, (uint64_t)n);
+        ns = sdraw_sample<D, false>(tm, cx, tk.map, lo, hi, tk.t, sh);
+        if (ns >= 2 * cx.p.sigma_os) sdraw_sample<D, true>(tm, cx, tk.map, lo, hi, tk.t, sh);
+      }
       tk.ns = (uint16_t)ns;
       if (ns >= 2 * cx.p.sigma_os && ssample_split<D>(tm, cx, tk, dim, x, L, SL)) {
         on_sample = true;

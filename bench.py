@@ -687,6 +687,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-varden", action="store_true", help="skip the varden-like repetition of the step")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg (p50 / p99 latency)")
+    ap.add_argument("--host-rounds", action="store_true",
+                    help="sequence every build's rounds on the host (profiling: kernels inside a graph are not "
+                         "listed by a launch-list capture)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if wl.get("full"):
@@ -721,6 +724,8 @@ def main():
     dev = torch.device("cuda", local)
     pkd.lib()
 
+    if args.host_rounds:
+        pkd.pkd_set_option("graph_rounds", 0)
     X, Y, yid, zid = make_inputs(wl, rank)
     d = wl["d"]
     gX = torch.from_numpy(X).to(dev)
@@ -793,7 +798,7 @@ def main():
     counts = {k: pkd.pkd_kernel_stats(k) for k in ("rebuilt_insert", "rebuilt_delete", "delete_gather")}
     launches_per_step = pkd.pkd_kernel_stats("launches")[0] / stat_steps
     pkd.pkd_kernel_timing(False)
-    pkd.pkd_set_option("graph_rounds", 1)
+    pkd.pkd_set_option("graph_rounds", 0 if args.host_rounds else 1)
 
     pts_step = n + 2 * m
     ms_per_step = elapsed_ms / args.steps
@@ -929,8 +934,9 @@ def main():
                 "gpu_launches_note": "kernels run in the timed steps, counted in the host-sequenced stats pass "
                                      "(same kernels); the graph launches also run one one-thread condition "
                                      f"kernel per loop test ({launches} kernel nodes and launches recorded)",
-                "build_rounds": "decided on the device: one CUDA graph launch per build (WHILE over rounds "
-                                "and skeleton levels, IF for exact levels, base-case grids set by a kernel)",
+                "build_rounds": ("sequenced by the host (--host-rounds)" if args.host_rounds else
+                                 "decided on the device: one CUDA graph launch per build (WHILE over rounds "
+                                 "and skeleton levels, IF for exact levels, base-case grids set by a kernel)"),
                 "clocks": clk.summary(),
                 "phases": dict(phase, build_mpts=n / phase["build_ms"] / 1e3,
                                insert_mpts=m / phase["insert_ms"] / 1e3,

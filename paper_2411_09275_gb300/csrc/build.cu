@@ -1400,8 +1400,9 @@ constexpr int MAX_SHAPES = 4;
 // (the same tree memory, scratch and input at the same addresses: repeated
 // builds of one size, which the stream-ordered pool tends to place at the
 // same addresses) launches that graph again instead of recording a new one.
-// The key lists every value the recorded kernels take.  An entry is
-// destroyed only after its last launch has completed.
+// The key lists every value the recorded kernels take.  An evicted entry
+// is destroyed once its last launch has completed (checked without waiting
+// at later builds), so eviction never blocks the host.
 struct GraphEntry {
   std::vector<uint64_t> key;
   cudaGraphExec_t exec = nullptr;
@@ -1411,17 +1412,28 @@ struct GraphEntry {
   BaseShape shapes[MAX_SHAPES];
   uint64_t used = 0;
 };
-constexpr int GRAPH_CACHE = 4;
-static std::vector<GraphEntry> g_graphs;  // guarded by flow_mutex()
+constexpr int GRAPH_CACHE = 16;
+static std::vector<GraphEntry> g_graphs;   // guarded by flow_mutex()
+static std::vector<GraphEntry> g_retired;  // evicted, maybe still running
 static uint64_t g_graph_clock = 0;
 
 static void graph_entry_destroy(GraphEntry& e) {
-  if (e.done) cudaEventSynchronize(e.done);
   if (e.exec) cudaGraphExecDestroy(e.exec);
   if (e.graph) cudaGraphDestroy(e.graph);
   if (e.done) cudaEventDestroy(e.done);
   if (e.base) cudaEventDestroy(e.base);
   e = GraphEntry{};
+}
+
+// Destroys the evicted entries whose last launch has completed.
+static void graph_reap() {
+  std::vector<GraphEntry> keep;
+  for (GraphEntry& e : g_retired) {
+    if (!e.done || cudaEventQuery(e.done) == cudaSuccess) graph_entry_destroy(e);
+    else keep.push_back(e);
+  }
+  cudaGetLastError();  // a pending event's query status is not an error
+  g_retired.swap(keep);
 }
 
 static GraphEntry* graph_find(const std::vector<uint64_t>& key) {
@@ -1441,7 +1453,8 @@ static GraphEntry* graph_slot() {
   GraphEntry* lru = &g_graphs[0];
   for (GraphEntry& e : g_graphs)
     if (e.used < lru->used) lru = &e;
-  graph_entry_destroy(*lru);
+  g_retired.push_back(*lru);
+  *lru = GraphEntry{};
   return lru;
 }
 
@@ -1910,6 +1923,7 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
       put((uint64_t)knobs().sieve_kernel), put((uint64_t)knobs().base_kernel), put((uint64_t)knobs().wait_cycles);
       put((uint64_t)record_buckets(NB));
     }
+    graph_reap();
     GraphEntry* ent = graph_find(key);
     if (ent) {
       memcpy(hshape, ent->shapes, sizeof(ent->shapes));

@@ -70,10 +70,14 @@ def algo_bytes(kernel: str, d: int) -> float | None:
     the range check read one 4-byte word."""
     return {"scatter": 2 * (4 * d + 4), "smem_build": 2 * (4 * d + 4), "smem_warp": 2 * (4 * d + 4),
             "count": 4 * d, "sample": 4, "validate": 4,
-            "scatter_route": 2 * (4 * d + 4), "count_route": 4 * d}.get(kernel)
+            "scatter_route": 2 * (4 * d + 4), "count_route": 4 * d,
+            # id table: an id and its point's coordinates read, the table
+            # entry (claim) or the batch entry (take) written
+            "id_claim": 8 * d + 8, "id_take": 8 * d + 8}.get(kernel)
 
 
-TIMED_KERNELS = ["smem_build", "smem_warp", "scatter", "count", "sample", "validate", "scatter_route", "count_route"]
+TIMED_KERNELS = ["smem_build", "smem_warp", "scatter", "count", "sample", "validate", "scatter_route", "count_route",
+                 "id_claim", "id_take"]
 
 
 def measured_peaks():

@@ -281,9 +281,12 @@ int pkd_set_option(const char* name, int64_t value);
  * build), "count_route" and "scatter_route" (sieve rounds that route an
  * update batch; items = batch points they move), "smem_build" (shared-memory
  * base case, one CTA per subproblem), "smem_warp" (one warp per subproblem),
- * "knn", "range_count", "range_report".  Counts without a time: "rebuilt_insert"
- * and "rebuilt_delete" (points in the subtrees an update rebuilt, one entry
- * per call), "delete_gather" (ids a delete found and looked up).  The name
+ * "knn", "range_count", "range_report", "id_claim" and "id_take" (the id
+ * table's fill at build and insert, and its lookups at delete; items = ids),
+ * "graph_record" (host time to record a build's graph; items = graphs
+ * recorded).  Counts without a time: "rebuilt_insert" and "rebuilt_delete"
+ * (points in the subtrees an update rebuilt, one entry per call),
+ * "delete_gather" (ids a delete found and looked up).  The name
  * "allocations" reports, in *launches, every device or pinned-host allocation
  * the library made since it was loaded; "graph_builds" the builds (and update
  * rebuilds) whose rounds ran from one graph launch.  With graph rounds,

@@ -31,49 +31,85 @@ unsigned id_blocks(uint64_t n) {
   return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(b, 152ull * 16));
 }
 
+// CLAIM_PER ids per thread: their first probe loads, then their
+// compare-and-swaps, are all issued before any is waited for (random
+// accesses into a table far larger than L2).  The dense build path (ids
+// 0..m-1 into an empty table) stores its keys directly.
+constexpr int CLAIM_PER = 4;
+
+__device__ __forceinline__ void claim_store(const int32_t* coords, uint64_t i, int d, const IdTable& T, uint64_t got,
+                                            uint64_t* slots) {
+  if (got != ID_NO_SLOT) {
+    const int32_t* c = coords + i * (uint64_t)d;
+    int32_t* x = T.xs + got * (uint64_t)T.cw;
+    for (int j = 1; j < d; ++j) x[j - 1] = c[j];
+  }
+  if (slots) slots[i] = got;
+}
+
 __global__ void __launch_bounds__(ID_THREADS) k_ids_claim(const int32_t* coords, const uint32_t* ids, uint64_t m,
                                                           int d, IdTable T, uint64_t* slots, DevStatus* st) {
   const uint64_t mask = T.cap - 1;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
-    const int32_t* c = coords + i * (uint64_t)d;
-    const int32_t x0 = c[0];
-    uint64_t got = ID_NO_SLOT;
+  if (!ids) {  // ids 0..m-1 into an empty table: distinct home slots
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+      const uint64_t got = id_home((uint32_t)i, T.lgc);
+      T.key[got] = id_key((uint32_t)i, coords[i * (uint64_t)d], ID_LIVE);
+      claim_store(coords, i, d, T, got, slots);
+    }
+    return;
+  }
+  const uint64_t span = (uint64_t)ID_THREADS * CLAIM_PER;
+  for (uint64_t b0 = (uint64_t)blockIdx.x * span; b0 < m; b0 += (uint64_t)gridDim.x * span) {
+    uint32_t id[CLAIM_PER];
+    int32_t x0[CLAIM_PER];
+    uint64_t s[CLAIM_PER];
+    unsigned long long k[CLAIM_PER];
+#pragma unroll
+    for (int u = 0; u < CLAIM_PER; ++u) {
+      const uint64_t i = b0 + (uint64_t)u * ID_THREADS + threadIdx.x;
+      id[u] = i < m ? ids[i] : ID_RESERVED;
+      x0[u] = i < m ? coords[i * (uint64_t)d] : 0;
+    }
     int bad = 0;
-    if (!ids) {  // ids 0..m-1 into an empty table: distinct home slots
-      got = id_home((uint32_t)i, T.lgc);
-      T.key[got] = id_key((uint32_t)i, x0, ID_LIVE);
-    } else {
-      const uint32_t id = ids[i];
-      const unsigned long long want = id_key(id, x0, ID_LIVE);
-      if (id == ID_RESERVED) {
-        bad = IDF_BAD_ID;
-      } else {
-        uint64_t s = id_home(id, T.lgc), n = 0;
-        for (; n < T.cap; ++n, s = (s + 1) & mask) {
-          unsigned long long k = __ldcg(&T.key[s]);
-          if (k == ID_EMPTY) {
-            k = atomicCAS(&T.key[s], ID_EMPTY, want);
-            if (k == ID_EMPTY) {
-              got = s;
-              break;
-            }
-          }
-          if ((uint32_t)k == id) {  // this id's slot: revive it if deleted
-            if (id_state(k) == ID_DEAD && atomicCAS(&T.key[s], k, want) == k)
-              got = s;
-            else
-              bad = IDF_BAD_ID;
+#pragma unroll
+    for (int u = 0; u < CLAIM_PER; ++u) {
+      const uint64_t i = b0 + (uint64_t)u * ID_THREADS + threadIdx.x;
+      if (i < m && id[u] == ID_RESERVED) bad |= IDF_BAD_ID;
+      s[u] = id[u] != ID_RESERVED ? id_home(id[u], T.lgc) : 0;
+      k[u] = id[u] != ID_RESERVED ? __ldcg(&T.key[s[u]]) : 0ull;
+    }
+    uint64_t got[CLAIM_PER];
+#pragma unroll
+    for (int u = 0; u < CLAIM_PER; ++u) {
+      got[u] = ID_NO_SLOT;
+      if (id[u] == ID_RESERVED) continue;
+      const unsigned long long want = id_key(id[u], x0[u], ID_LIVE);
+      uint64_t n = 0;
+      for (; n < T.cap; ++n) {
+        if (k[u] == ID_EMPTY) {
+          k[u] = atomicCAS(&T.key[s[u]], ID_EMPTY, want);
+          if (k[u] == ID_EMPTY) {
+            got[u] = s[u];
             break;
           }
         }
-        if (n == T.cap) bad = IDF_FULL;
+        if ((uint32_t)k[u] == id[u]) {  // this id's slot: revive it if deleted
+          if (id_state(k[u]) == ID_DEAD && atomicCAS(&T.key[s[u]], k[u], want) == k[u])
+            got[u] = s[u];
+          else
+            bad |= IDF_BAD_ID;
+          break;
+        }
+        s[u] = (s[u] + 1) & mask;
+        k[u] = __ldcg(&T.key[s[u]]);
       }
+      if (n == T.cap) bad |= IDF_FULL;
     }
-    if (got != ID_NO_SLOT) {
-      int32_t* x = T.xs + got * (uint64_t)T.cw;
-      for (int j = 1; j < d; ++j) x[j - 1] = c[j];
+#pragma unroll
+    for (int u = 0; u < CLAIM_PER; ++u) {
+      const uint64_t i = b0 + (uint64_t)u * ID_THREADS + threadIdx.x;
+      if (i < m) claim_store(coords, i, d, T, got[u], slots);
     }
-    if (slots) slots[i] = got;
     if (bad) atomicOr(&st->idflags, bad);
   }
 }
@@ -86,45 +122,88 @@ __global__ void __launch_bounds__(ID_THREADS) k_ids_restate(const uint64_t* slot
   }
 }
 
-// One thread per id; the winners of a block reserve their batch positions
-// with one atomic (block_reserve), so the append does not serialise.
+// TAKE_PER ids per thread: every probe's first load, then every
+// compare-and-swap, then every coordinate load of the thread is issued before
+// any of them is waited for (the lookups are random accesses into a table far
+// larger than L2, so the time is the chains' latency); the winners of a block
+// then reserve their batch positions with one atomic (block_reserve), so the
+// append does not serialise.  The batch order is immaterial (the delete
+// treats it as a set).
+constexpr int TAKE_PER = 4;
+
 __global__ void __launch_bounds__(ID_THREADS) k_ids_take(const uint32_t* ids, uint64_t m, IdTable T, Pts W,
                                                          uint64_t* wslots, uint32_t* count, int d, DevStatus* st) {
   const uint64_t mask = T.cap - 1;
-  for (uint64_t b0 = (uint64_t)blockIdx.x * blockDim.x; b0 < m; b0 += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t i = b0 + threadIdx.x;
-    uint64_t got = ID_NO_SLOT;
-    uint32_t id = ID_RESERVED;
-    int32_t x0 = 0;
-    if (i < m) {
-      id = ids[i];
-      if (id != ID_RESERVED) {
-        uint64_t s = id_home(id, T.lgc), n = 0;
-        for (; n < T.cap; ++n, s = (s + 1) & mask) {
-          const unsigned long long k = __ldcg(&T.key[s]);
-          if (k == ID_EMPTY) break;  // never stored
-          if ((uint32_t)k == id) {
-            if (id_state(k) == ID_LIVE && atomicCAS(&T.key[s], k, id_with_state(k, ID_DEAD)) == k) {
-              got = s;
-              x0 = id_x0(k);
-            }
-            break;
-          }
-        }
-        if (n == T.cap) atomicOr(&st->idflags, IDF_FULL);
-      }
+  const uint64_t span = (uint64_t)ID_THREADS * TAKE_PER;
+  for (uint64_t b0 = (uint64_t)blockIdx.x * span; b0 < m; b0 += (uint64_t)gridDim.x * span) {
+    uint32_t id[TAKE_PER];
+    uint64_t s[TAKE_PER];
+    unsigned long long k[TAKE_PER];
+#pragma unroll
+    for (int u = 0; u < TAKE_PER; ++u) {
+      const uint64_t i = b0 + (uint64_t)u * ID_THREADS + threadIdx.x;
+      id[u] = i < m ? ids[i] : ID_RESERVED;
     }
-    const uint32_t c[1] = {got != ID_NO_SLOT ? 1u : 0u};
+#pragma unroll
+    for (int u = 0; u < TAKE_PER; ++u) {
+      s[u] = id[u] != ID_RESERVED ? id_home(id[u], T.lgc) : 0;
+      k[u] = id[u] != ID_RESERVED ? __ldcg(&T.key[s[u]]) : ID_EMPTY;
+    }
+    // the rest of each probe (rarely more than the first slot)
+    uint64_t got[TAKE_PER];
+    int32_t x0[TAKE_PER];
+#pragma unroll
+    for (int u = 0; u < TAKE_PER; ++u) {
+      got[u] = ID_NO_SLOT;
+      x0[u] = 0;
+      if (id[u] == ID_RESERVED) continue;
+      uint64_t n = 0;
+      while (k[u] != ID_EMPTY && (uint32_t)k[u] != id[u] && n + 1 < T.cap) {
+        s[u] = (s[u] + 1) & mask;
+        ++n;
+        k[u] = __ldcg(&T.key[s[u]]);
+      }
+      if (k[u] != ID_EMPTY && (uint32_t)k[u] != id[u]) atomicOr(&st->idflags, IDF_FULL);
+      if ((uint32_t)k[u] != id[u] || k[u] == ID_EMPTY || id_state(k[u]) != ID_LIVE) k[u] = ID_EMPTY;  // not taken
+    }
+#pragma unroll
+    for (int u = 0; u < TAKE_PER; ++u)
+      if (k[u] != ID_EMPTY && atomicCAS(&T.key[s[u]], k[u], id_with_state(k[u], ID_DEAD)) == k[u]) {
+        got[u] = s[u];
+        x0[u] = id_x0(k[u]);
+      }
+    int32_t xr[TAKE_PER][3];
+#pragma unroll
+    for (int u = 0; u < TAKE_PER; ++u)
+      if (got[u] != ID_NO_SLOT) {
+        const int32_t* x = T.xs + got[u] * (uint64_t)T.cw;
+#pragma unroll
+        for (int j = 1; j < 4; ++j)
+          if (j < d) xr[u][j - 1] = x[j - 1];
+      }
+    uint32_t nwin = 0;
+#pragma unroll
+    for (int u = 0; u < TAKE_PER; ++u) nwin += got[u] != ID_NO_SLOT;
+    const uint32_t c[1] = {nwin};
     uint32_t* const ctr[1] = {count};
     uint32_t first[1];
     block_reserve<1>(c, ctr, first);
-    if (got != ID_NO_SLOT) {
-      const uint64_t p = first[0];
-      const int32_t* x = T.xs + got * (uint64_t)T.cw;
-      W.c[p] = x0;
-      for (int j = 1; j < d; ++j) W.c[(uint64_t)j * W.stride + p] = x[j - 1];
-      W.id[p] = id;
-      wslots[p] = got;
+    uint64_t p = first[0];
+#pragma unroll
+    for (int u = 0; u < TAKE_PER; ++u) {
+      if (got[u] == ID_NO_SLOT) continue;
+      W.c[p] = x0[u];
+      if (d <= 4) {
+#pragma unroll
+        for (int j = 1; j < 4; ++j)
+          if (j < d) W.c[(uint64_t)j * W.stride + p] = xr[u][j - 1];
+      } else {
+        const int32_t* x = T.xs + got[u] * (uint64_t)T.cw;
+        for (int j = 1; j < d; ++j) W.c[(uint64_t)j * W.stride + p] = x[j - 1];
+      }
+      W.id[p] = id[u];
+      wslots[p] = got[u];
+      ++p;
     }
   }
 }
@@ -217,7 +296,12 @@ int read_idflags(TreeMem& t, cudaStream_t s, int* flags) {
 void ids_claim(TreeMem& t, const int32_t* coords, const uint32_t* ids, uint64_t m, uint64_t* slots,
                cudaStream_t s) {
   if (m == 0) return;
-  PKD_LAUNCH(k_ids_claim<<<id_blocks(m), ID_THREADS, 0, s>>>(coords, ids, m, t.p.d, t.ids, slots, t.st));
+  const uint64_t per = ids ? CLAIM_PER : 1;
+  KTimer kt;
+  ktimer_begin(kt, "id_claim", m, s);
+  PKD_LAUNCH(k_ids_claim<<<id_blocks((m + per - 1) / per), ID_THREADS, 0, s>>>(coords, ids, m, t.p.d, t.ids, slots,
+                                                                              t.st));
+  ktimer_end(kt);
 }
 
 void ids_unclaim(TreeMem& t, const uint64_t* slots, uint64_t m, cudaStream_t s) {
@@ -228,7 +312,11 @@ void ids_unclaim(TreeMem& t, const uint64_t* slots, uint64_t m, cudaStream_t s) 
 void ids_take(TreeMem& t, const uint32_t* ids, uint64_t m, Pts W, uint64_t* wslots, uint32_t* count,
               cudaStream_t s) {
   if (m == 0) return;
-  PKD_LAUNCH(k_ids_take<<<id_blocks(m), ID_THREADS, 0, s>>>(ids, m, t.ids, W, wslots, count, t.p.d, t.st));
+  KTimer kt;
+  ktimer_begin(kt, "id_take", m, s);
+  PKD_LAUNCH(k_ids_take<<<id_blocks((m + TAKE_PER - 1) / TAKE_PER), ID_THREADS, 0, s>>>(ids, m, t.ids, W, wslots,
+                                                                                       count, t.p.d, t.st));
+  ktimer_end(kt);
 }
 
 void ids_restore(TreeMem& t, const uint64_t* wslots, uint64_t n, cudaStream_t s) {

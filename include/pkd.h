@@ -282,7 +282,8 @@ int pkd_set_option(const char* name, int64_t value);
  * update batch; items = batch points they move), "smem_build" (shared-memory
  * base case, one CTA per subproblem), "smem_warp" (one warp per subproblem),
  * "knn", "range_count", "range_report", "id_claim" and "id_take" (the id
- * table's fill at build and insert, and its lookups at delete; items = ids),
+ * table's fill at an insert (a build fills it beside its base cases,
+ * untimed) and its lookups at a delete; items = ids),
  * "graph_record" (host time to record a build's graph; items = graphs
  * recorded).  Counts without a time: "rebuilt_insert" and "rebuilt_delete"
  * (points in the subtrees an update rebuilt, one entry per call),

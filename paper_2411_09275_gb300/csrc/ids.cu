@@ -297,8 +297,10 @@ void ids_claim(TreeMem& t, const int32_t* coords, const uint32_t* ids, uint64_t 
                cudaStream_t s) {
   if (m == 0) return;
   const uint64_t per = ids ? CLAIM_PER : 1;
+  // timed for inserts only: a build's fill runs beside its base cases on a
+  // second stream, so its span is not the kernel's own time
   KTimer kt;
-  ktimer_begin(kt, "id_claim", m, s);
+  if (slots) ktimer_begin(kt, "id_claim", m, s);
   PKD_LAUNCH(k_ids_claim<<<id_blocks((m + per - 1) / per), ID_THREADS, 0, s>>>(coords, ids, m, t.p.d, t.ids, slots,
                                                                               t.st));
   ktimer_end(kt);

@@ -116,7 +116,7 @@ struct SCtx {
 // peer mask, so equal digits keep their order.  Loads are issued SS_BATCH groups at a
 // time before any store (the compiler cannot move them past the stores).
 // ---------------------------------------------------------------------------
-constexpr int SS_BATCH = 8;
+constexpr int SS_BATCH = 4;
 
 __device__ __forceinline__ void radix_pass(const int32_t* Xj, unsigned vmin, int shift, const uint16_t* src,
                                            uint16_t* dst, int n, unsigned* hist, int* tmp) {
@@ -230,10 +230,11 @@ __device__ void presort_dim(const SCtx<D>& cx, int k, int vmin, int vmax, int n,
 constexpr int MSD_BITS = 12;
 constexpr int MSD_BINS = 1 << MSD_BITS;  // 4096 counters fill the 16 KB radix region
 constexpr int MSD_MAX_BUCKET = 64;
+constexpr int MSD_PER = MSD_BINS / SS_THREADS;  // bins per thread
 
 template <int D>
 __device__ bool presort_dim_msd(const SCtx<D>& cx, int k, int vmin, int vmax, int n, unsigned* hist, int* tmp) {
-  static_assert(MSD_BINS == 8 * SS_THREADS, "eight bins per thread");
+  static_assert(MSD_PER * SS_THREADS == MSD_BINS && MSD_BINS <= SS_NW * 256, "bins per thread, radix region");
   const int32_t* Xk = cx.X + k * cx.cap;
   uint16_t* target = cx.list(k);
   const unsigned range = (unsigned)vmax - (unsigned)vmin;
@@ -241,15 +242,15 @@ __device__ bool presort_dim_msd(const SCtx<D>& cx, int k, int vmin, int vmax, in
   const int shift = max(0, bits - MSD_BITS);
   const int tid = threadIdx.x, lane = lane_id(), w = warp_id();
 #pragma unroll
-  for (int q = 0; q < 8; ++q) hist[q * SS_THREADS + tid] = 0;
+  for (int q = 0; q < MSD_PER; ++q) hist[q * SS_THREADS + tid] = 0;
   __syncthreads();
   for (int i = tid; i < n; i += SS_THREADS) atomicAdd(&hist[((unsigned)Xk[i] - (unsigned)vmin) >> shift], 1u);
   __syncthreads();
-  // bin starts: thread t owns bins [8t, 8t + 8)
-  unsigned c[8], sum = 0, mx = 0;
+  // bin starts: thread t owns bins [MSD_PER t, MSD_PER (t + 1))
+  unsigned c[MSD_PER], sum = 0, mx = 0;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    c[q] = hist[8 * tid + q];
+  for (int q = 0; q < MSD_PER; ++q) {
+    c[q] = hist[MSD_PER * tid + q];
     sum += c[q];
     mx = max(mx, c[q]);
   }
@@ -268,8 +269,8 @@ __device__ bool presort_dim_msd(const SCtx<D>& cx, int k, int vmin, int vmax, in
     return false;
   }
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    hist[8 * tid + q] = run;
+  for (int q = 0; q < MSD_PER; ++q) {
+    hist[MSD_PER * tid + q] = run;
     run += c[q];
   }
   __syncthreads();

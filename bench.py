@@ -883,6 +883,15 @@ def main():
                 e2e_step(k, k == steps - 1)
 
         e2e_run(2)
+        # the copies alone: one step's inputs, host to device, nothing else running
+        torch.cuda.synchronize(dev)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(copy_stream)
+        upload(0)
+        c1.record(copy_stream)
+        torch.cuda.synchronize(dev)
+        copy_ms = c0.elapsed_time(c1)
         barrier_max(0.0, ws, dev)
         torch.cuda.synchronize(dev)
         a = torch.cuda.Event(enable_timing=True)
@@ -896,7 +905,8 @@ def main():
         e2e = {"value": ws * pts_step * args.steps / (e2e_ms / 1e3) / 1e6, "unit": "Mpts/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8,
                "note": "inputs copied from pinned host memory every step; the next step's copy overlaps "
-                       "this step on a second stream"}
+                       "this step on a second stream",
+               "copy_ms_alone": copy_ms, "h2d_gbs_alone": h2d / (copy_ms / 1e3) / 1e9}
 
     # ---- varden-like variant of the same step (same sizes, timers off) ----
     varden = None

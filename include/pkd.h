@@ -150,10 +150,18 @@ int pkd_knn(const pkd_tree* tree, const int32_t* queries, uint64_t q, int k, uin
  *   queries  device, [q][d] int32 in [0, 2^30);  k  in 1..128
  *   out_ids  device, [q][k] uint32 (as pkd_knn)
  * Errors: PKD_EINVAL (k, q * k, coordinates, wrong device), PKD_ECUDA,
- * PKD_EINTERNAL. */
+ * PKD_EINTERNAL (also for a tree of height 126 or more, whose search stacks
+ * would need scratch memory: pkd_knn serves those). */
 #define PKD_NOALLOC_MAX_PAIRS (1u << 20)
 int pkd_knn_ids_noalloc(const pkd_tree* tree, const int32_t* queries, uint64_t q, int k,
                         uint32_t* out_ids, void* stream);
+
+/* Search depth (pkd_knn, pkd_range_count, pkd_range_report): each query's
+ * depth-first stack holds up to height + 1 entries.  Below height 126 they
+ * live in registers and local memory; a deeper tree (possible only after
+ * long runs of one-sided updates with alpha near 1/2, where no interior node
+ * is rebuilt) is searched with stacks in a scratch buffer of the library's
+ * pool, at most 1 GiB, a chunk of queries at a time. */
 
 /* Range count (Sec. 5): for each closed box lo[i][j] <= x_j <= hi[i][j],
  * the number of stored points inside; a subtree whose subspace lies inside
@@ -208,7 +216,14 @@ uint64_t pkd_size(const pkd_tree* tree);
 /* Longest root-to-leaf path (edges) into *height.  Synchronises the device. */
 int pkd_height(const pkd_tree* tree, int* height);
 
-/* Free the tree and all device memory it owns (NULL is a no-op). */
+/* Free the tree and all device memory it owns (NULL is a no-op).  Returns
+ * without waiting: the memory is released on the legacy default stream
+ * after the work every earlier call queued on the tree (each call records
+ * an event on its stream when it returns), so a query still running on
+ * another stream finishes on the tree it was given.  After a
+ * pkd_knn_ids_noalloc call on a stream no other call on this tree used (it
+ * may not create an event), the free waits for the whole device instead.
+ * pkd_forest_free behaves the same. */
 void pkd_free(pkd_tree* tree);
 
 /* Batched build of independent trees ("forest"): one pass over n_trees

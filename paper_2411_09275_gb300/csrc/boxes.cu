@@ -178,6 +178,7 @@ int pkd_set_bounding_boxes(pkd_tree* tc, int enable, void* stream) {
   if (!tc || (enable != 0 && enable != 1)) return PKD_EINVAL;
   TreeMem& t = tc->m;
   cudaStream_t s = (cudaStream_t)stream;
+  TreeTouch touch{&t, s};
   PKD_TRY_(check_status(t, s));
   if (!enable) {
     t.bbox_on = false;

@@ -57,6 +57,29 @@ struct TreeMem {
   int32_t* bbox = nullptr;          // stored bounding boxes (boxes.cu), node_cap * 2d
   uint64_t bbox_cap = 0;            // node slots bbox covers
   bool bbox_on = false;             // kept current after every update; queries prune with them
+  // the last use of the tree on every stream a call queued work on (an event
+  // recorded after that work), so that freeing the tree waits for exactly
+  // that work; untracked: a use that could not record one (a call that may
+  // not allocate), after which freeing waits for the whole device
+  std::vector<std::pair<cudaStream_t, cudaEvent_t>> uses;
+  bool untracked = false;
+};
+
+// Records the use of tree t by the work queued so far on stream s.
+void tree_touch(TreeMem& t, cudaStream_t s, bool noalloc = false);
+// Orders the legacy default stream after every recorded use (or, after an
+// untracked one, waits for the device) and forgets the uses.
+void tree_wait_uses(TreeMem& t);
+
+// Records the tree's use by the calling entry point when it returns (every
+// return path, after its last enqueue).
+struct TreeTouch {
+  TreeMem* t;
+  cudaStream_t s;
+  bool noalloc = false;
+  ~TreeTouch() {
+    if (t) tree_touch(*t, s, noalloc);
+  }
 };
 
 // Every kernel launch of the library goes through PKD_LAUNCH, which counts

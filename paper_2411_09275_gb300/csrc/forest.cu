@@ -72,6 +72,7 @@ int pkd_build_forest(const int32_t* coords, const uint32_t* ids, const uint64_t*
   }
   f->m.size = n;
   f->m.top = n;
+  tree_touch(f->m, s);
   *out = f;
   return PKD_OK;
 }
@@ -101,7 +102,7 @@ int pkd_forest_knn(const pkd_forest* f, uint32_t tree, const int32_t* queries, u
 
 void pkd_forest_free(pkd_forest* f) {
   if (!f) return;
-  cudaDeviceSynchronize();  // no kernel of any stream may still use the forest
+  tree_wait_uses(f->m);  // the frees below are ordered after every call's work
   tree_release(f->m);
   delete f;
 }

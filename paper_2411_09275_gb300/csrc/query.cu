@@ -4,7 +4,12 @@
 // (a subtree whose subspace lies inside the box adds its stored size).
 // Subspaces are not stored: each stack entry carries the box implied by the
 // splitters above it, as the paper does instead of keeping bounding boxes.
-// One thread per query; the stack holds at most height + 1 entries.
+// One thread per query; the stack holds at most height + 1 entries: in local
+// memory (QSTACK entries) for trees of height below QSTACK - 2, which the
+// sampling build and the alpha test keep every tree below for alpha <= 3/10;
+// in a global scratch buffer, sized by the tree's height and processed a
+// chunk of queries at a time, for deeper trees (long runs of one-sided
+// updates with alpha near 1/2, where no interior node is ever rebuilt).
 #include <algorithm>
 #include <cstdio>
 #include <mutex>
@@ -49,9 +54,52 @@ struct QueryArgs {
   uint64_t* out_cnt;
   DevStatus* st;
   const int32_t* box;  // stored bounding boxes (node slot * 2d), or null
+  // deep trees: stack entry i of query qi at [i * nq + qi] of these
+  uint32_t* dv;
+  void* db;      // Box<D> entries
+  uint8_t* df;
+  int dcap;      // entries per query (0: local stacks)
 };
 
-template <int D, int KMAX>
+// The depth-first stack of one query: local arrays, or (DEEP) the query's
+// column of the global scratch.
+template <int D, bool DEEP>
+struct QStack {
+  uint32_t lv[DEEP ? 1 : QSTACK];
+  Box<D> lb[DEEP ? 1 : QSTACK];
+  uint8_t lf[DEEP ? 1 : QSTACK];
+  uint32_t* gv;
+  Box<D>* gb;
+  uint8_t* gf;
+  uint64_t stride, col;
+  int cap;
+  __device__ QStack(const QueryArgs& a, uint64_t qi) {
+    if constexpr (DEEP) {
+      gv = a.dv;
+      gb = (Box<D>*)a.db;
+      gf = a.df;
+      stride = a.nq;
+      col = qi;
+      cap = a.dcap;
+    } else {
+      cap = QSTACK;
+    }
+  }
+  __device__ __forceinline__ uint32_t& v(int i) {
+    if constexpr (DEEP) return gv[(uint64_t)i * stride + col];
+    else return lv[i];
+  }
+  __device__ __forceinline__ Box<D>& b(int i) {
+    if constexpr (DEEP) return gb[(uint64_t)i * stride + col];
+    else return lb[i];
+  }
+  __device__ __forceinline__ uint8_t& f(int i) {
+    if constexpr (DEEP) return gf[(uint64_t)i * stride + col];
+    else return lf[i];
+  }
+};
+
+template <int D, int KMAX, bool DEEP>
 __global__ void __launch_bounds__(QTHREADS) k_knn(QueryArgs a) {
   const uint64_t qi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (qi >= a.nq) return;
@@ -65,20 +113,19 @@ __global__ void __launch_bounds__(QTHREADS) k_knn(QueryArgs a) {
     bd[i] = LLONG_MAX;
     bi[i] = 0xFFFFFFFFu;
   }
-  uint32_t sv[QSTACK];
-  Box<D> sb[QSTACK];
+  QStack<D, DEEP> S(a, qi);
   int sp = 0;
-  sv[0] = a.root;
+  S.v(0) = a.root;
 #pragma unroll
   for (int j = 0; j < D; ++j) {
-    sb[0].lo[j] = 0;
-    sb[0].hi[j] = PKD_COORD_LIMIT - 1;
+    S.b(0).lo[j] = 0;
+    S.b(0).hi[j] = PKD_COORD_LIMIT - 1;
   }
   sp = 1;
   while (sp > 0) {
     --sp;
-    const uint32_t v = sv[sp];
-    const Box<D> b = sb[sp];
+    const uint32_t v = S.v(sp);
+    const Box<D> b = S.b(sp);
     if (box_dist2<D>(q, b) > bd[k - 1]) continue;
     const uint8_t dm = a.ndim[v];
     const Node nd = a.nodes[v];
@@ -104,7 +151,7 @@ __global__ void __launch_bounds__(QTHREADS) k_knn(QueryArgs a) {
       }
       continue;
     }
-    if (sp + 2 > QSTACK) {
+    if (sp + 2 > S.cap) {
       set_error(a.st, DERR_STACK, 900);
       break;
     }
@@ -115,11 +162,11 @@ __global__ void __launch_bounds__(QTHREADS) k_knn(QueryArgs a) {
     R.lo[j] = max(R.lo[j], x);
     const bool near_left = q[j] < x;
     // far child first, so the near child is searched next
-    sv[sp] = near_left ? nd.b : nd.a;
-    sb[sp] = near_left ? R : L;
+    S.v(sp) = near_left ? nd.b : nd.a;
+    S.b(sp) = near_left ? R : L;
     ++sp;
-    sv[sp] = near_left ? nd.a : nd.b;
-    sb[sp] = near_left ? L : R;
+    S.v(sp) = near_left ? nd.a : nd.b;
+    S.b(sp) = near_left ? L : R;
     ++sp;
   }
   for (int i = 0; i < k; ++i) {
@@ -128,7 +175,7 @@ __global__ void __launch_bounds__(QTHREADS) k_knn(QueryArgs a) {
   }
 }
 
-template <int D>
+template <int D, bool DEEP>
 __global__ void __launch_bounds__(QTHREADS) k_range_count(QueryArgs a) {
   const uint64_t qi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (qi >= a.nq) return;
@@ -138,20 +185,19 @@ __global__ void __launch_bounds__(QTHREADS) k_range_count(QueryArgs a) {
     lo[j] = a.q[qi * D + j];
     hi[j] = a.hi[qi * D + j];
   }
-  uint32_t sv[QSTACK];
-  Box<D> sb[QSTACK];
-  sv[0] = a.root;
+  QStack<D, DEEP> S(a, qi);
+  S.v(0) = a.root;
 #pragma unroll
   for (int j = 0; j < D; ++j) {
-    sb[0].lo[j] = 0;
-    sb[0].hi[j] = PKD_COORD_LIMIT - 1;
+    S.b(0).lo[j] = 0;
+    S.b(0).hi[j] = PKD_COORD_LIMIT - 1;
   }
   int sp = 1;
   unsigned long long cnt = 0;
   while (sp > 0) {
     --sp;
-    const uint32_t v = sv[sp];
-    const Box<D> b = sb[sp];
+    const uint32_t v = S.v(sp);
+    const Box<D> b = S.b(sp);
     bool disjoint = false, inside = true;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
@@ -178,7 +224,7 @@ __global__ void __launch_bounds__(QTHREADS) k_range_count(QueryArgs a) {
       }
       continue;
     }
-    if (sp + 2 > QSTACK) {
+    if (sp + 2 > S.cap) {
       set_error(a.st, DERR_STACK, 901);
       break;
     }
@@ -186,11 +232,11 @@ __global__ void __launch_bounds__(QTHREADS) k_range_count(QueryArgs a) {
     Box<D> L = b, R = b;
     L.hi[j] = min(L.hi[j], nd.split - 1);
     R.lo[j] = max(R.lo[j], nd.split);
-    sv[sp] = nd.b;
-    sb[sp] = R;
+    S.v(sp) = nd.b;
+    S.b(sp) = R;
     ++sp;
-    sv[sp] = nd.a;
-    sb[sp] = L;
+    S.v(sp) = nd.a;
+    S.b(sp) = L;
     ++sp;
   }
   a.out_cnt[qi] = cnt;
@@ -200,7 +246,7 @@ __global__ void __launch_bounds__(QTHREADS) k_range_count(QueryArgs a) {
 // whose subspace lies inside the box is walked to its leaves without
 // coordinate tests (its points need not be contiguous in the arena after
 // updates).  Query qi writes its ids from out_ids[offsets[qi]].
-template <int D>
+template <int D, bool DEEP>
 __global__ void __launch_bounds__(QTHREADS) k_range_report(QueryArgs a, const uint64_t* offsets, uint32_t* out_ids) {
   const uint64_t qi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (qi >= a.nq) return;
@@ -210,24 +256,22 @@ __global__ void __launch_bounds__(QTHREADS) k_range_report(QueryArgs a, const ui
     lo[j] = a.q[qi * D + j];
     hi[j] = a.hi[qi * D + j];
   }
-  uint32_t sv[QSTACK];
-  Box<D> sb[QSTACK];
-  uint8_t sin[QSTACK];  // 1: the subspace lies inside the box
-  sv[0] = a.root;
-  sin[0] = 0;
+  QStack<D, DEEP> S(a, qi);  // flag f: 1 when the subspace lies inside the box
+  S.v(0) = a.root;
+  S.f(0) = 0;
 #pragma unroll
   for (int j = 0; j < D; ++j) {
-    sb[0].lo[j] = 0;
-    sb[0].hi[j] = PKD_COORD_LIMIT - 1;
+    S.b(0).lo[j] = 0;
+    S.b(0).hi[j] = PKD_COORD_LIMIT - 1;
   }
   int sp = 1;
   uint64_t pos = offsets[qi];
   const uint64_t end = offsets[qi + 1];
   while (sp > 0) {
     --sp;
-    const uint32_t v = sv[sp];
-    bool inside = sin[sp] != 0;
-    const Box<D> b = sb[sp];
+    const uint32_t v = S.v(sp);
+    bool inside = S.f(sp) != 0;
+    const Box<D> b = S.b(sp);
     if (!inside) {
       bool disjoint = false;
       inside = true;
@@ -261,7 +305,7 @@ __global__ void __launch_bounds__(QTHREADS) k_range_report(QueryArgs a, const ui
       }
       continue;
     }
-    if (sp + 2 > QSTACK) {
+    if (sp + 2 > S.cap) {
       set_error(a.st, DERR_STACK, 903);
       return;
     }
@@ -269,13 +313,13 @@ __global__ void __launch_bounds__(QTHREADS) k_range_report(QueryArgs a, const ui
     Box<D> L = b, R = b;
     L.hi[j] = min(L.hi[j], nd.split - 1);
     R.lo[j] = max(R.lo[j], nd.split);
-    sv[sp] = nd.b;
-    sb[sp] = R;
-    sin[sp] = inside;
+    S.v(sp) = nd.b;
+    S.b(sp) = R;
+    S.f(sp) = inside;
     ++sp;
-    sv[sp] = nd.a;
-    sb[sp] = L;
-    sin[sp] = inside;
+    S.v(sp) = nd.a;
+    S.b(sp) = L;
+    S.f(sp) = inside;
     ++sp;
   }
 }
@@ -300,7 +344,7 @@ __device__ __forceinline__ Box<D> stored_box(const int32_t* box, uint32_t v) {
   return b;
 }
 
-template <int D, int KMAX>
+template <int D, int KMAX, bool DEEP>
 __global__ void __launch_bounds__(QTHREADS) k_knn_bb(QueryArgs a) {
   const uint64_t qi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (qi >= a.nq) return;
@@ -314,11 +358,11 @@ __global__ void __launch_bounds__(QTHREADS) k_knn_bb(QueryArgs a) {
     bd[i] = LLONG_MAX;
     bi[i] = 0xFFFFFFFFu;
   }
-  uint32_t sv[QSTACK];
-  sv[0] = a.root;
+  QStack<D, DEEP> S(a, qi);
+  S.v(0) = a.root;
   int sp = 1;
   while (sp > 0) {
-    const uint32_t v = sv[--sp];
+    const uint32_t v = S.v(--sp);
     const Box<D> b = stored_box<D>(a.box, v);
     if (b.lo[0] > b.hi[0]) continue;  // an empty subtree
     if (box_dist2<D>(q, b) > bd[k - 1]) continue;
@@ -346,13 +390,13 @@ __global__ void __launch_bounds__(QTHREADS) k_knn_bb(QueryArgs a) {
       }
       continue;
     }
-    if (sp + 2 > QSTACK) {
+    if (sp + 2 > S.cap) {
       set_error(a.st, DERR_STACK, 904);
       break;
     }
     const bool near_left = q[dm] < nd.split;
-    sv[sp++] = near_left ? nd.b : nd.a;  // far child first, near child next
-    sv[sp++] = near_left ? nd.a : nd.b;
+    S.v(sp++) = near_left ? nd.b : nd.a;  // far child first, near child next
+    S.v(sp++) = near_left ? nd.a : nd.b;
   }
   for (int i = 0; i < k; ++i) {
     a.out_d2[qi * k + i] = bd[i];
@@ -361,7 +405,7 @@ __global__ void __launch_bounds__(QTHREADS) k_knn_bb(QueryArgs a) {
 }
 
 // Range count (report = false) or report (true) with stored boxes.
-template <int D, bool REPORT>
+template <int D, bool REPORT, bool DEEP>
 __global__ void __launch_bounds__(QTHREADS) k_range_bb(QueryArgs a, const uint64_t* offsets, uint32_t* out_ids) {
   const uint64_t qi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (qi >= a.nq) return;
@@ -371,18 +415,17 @@ __global__ void __launch_bounds__(QTHREADS) k_range_bb(QueryArgs a, const uint64
     lo[j] = a.q[qi * D + j];
     hi[j] = a.hi[qi * D + j];
   }
-  uint32_t sv[QSTACK];
-  uint8_t sin[QSTACK];  // 1: inside the query box (report: walk without tests)
-  sv[0] = a.root;
-  sin[0] = 0;
+  QStack<D, DEEP> S(a, qi);  // flag f: 1 inside the query box (report: walk without tests)
+  S.v(0) = a.root;
+  S.f(0) = 0;
   int sp = 1;
   unsigned long long cnt = 0;
   uint64_t pos = REPORT ? offsets[qi] : 0;
   const uint64_t end = REPORT ? offsets[qi + 1] : 0;
   while (sp > 0) {
     --sp;
-    const uint32_t v = sv[sp];
-    bool inside = sin[sp] != 0;
+    const uint32_t v = S.v(sp);
+    bool inside = S.f(sp) != 0;
     if (!inside) {
       const Box<D> b = stored_box<D>(a.box, v);
       bool disjoint = false;
@@ -412,7 +455,7 @@ __global__ void __launch_bounds__(QTHREADS) k_range_bb(QueryArgs a, const uint64
           }
         }
         if (!in) continue;
-        if (REPORT) {
+        if constexpr (REPORT) {
           if (pos >= end) {  // more points than counted: the tree changed
             set_error(a.st, DERR_STATE, 905);
             return;
@@ -424,15 +467,15 @@ __global__ void __launch_bounds__(QTHREADS) k_range_bb(QueryArgs a, const uint64
       }
       continue;
     }
-    if (sp + 2 > QSTACK) {
+    if (sp + 2 > S.cap) {
       set_error(a.st, DERR_STACK, 906);
       return;
     }
-    sv[sp] = nd.b;
-    sin[sp] = inside;
+    S.v(sp) = nd.b;
+    S.f(sp) = inside;
     ++sp;
-    sv[sp] = nd.a;
-    sin[sp] = inside;
+    S.v(sp) = nd.a;
+    S.f(sp) = inside;
     ++sp;
   }
   if (!REPORT) a.out_cnt[qi] = cnt;
@@ -504,39 +547,54 @@ __global__ void k_scan64_apply(const uint64_t* in, uint64_t n, const uint64_t* p
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = partial[gridDim.x];
 }
 
-template <int D>
-static void launch_report(const QueryArgs& a, const uint64_t* offsets, uint32_t* ids, cudaStream_t s) {
+template <int D, bool DEEP>
+static void launch_report_(const QueryArgs& a, const uint64_t* offsets, uint32_t* ids, cudaStream_t s) {
   const unsigned g = (unsigned)((a.nq + QTHREADS - 1) / QTHREADS);
   KTimer kt;
   ktimer_begin(kt, "range_report", a.nq, s);
-  if (a.box) PKD_LAUNCH((k_range_bb<D, true><<<g, QTHREADS, 0, s>>>(a, offsets, ids)));
-  else PKD_LAUNCH(k_range_report<D><<<g, QTHREADS, 0, s>>>(a, offsets, ids));
+  if (a.box) PKD_LAUNCH((k_range_bb<D, true, DEEP><<<g, QTHREADS, 0, s>>>(a, offsets, ids)));
+  else PKD_LAUNCH((k_range_report<D, DEEP><<<g, QTHREADS, 0, s>>>(a, offsets, ids)));
   ktimer_end(kt);
 }
-
 template <int D>
-static void launch_knn(const QueryArgs& a, cudaStream_t s) {
+static void launch_report(const QueryArgs& a, const uint64_t* offsets, uint32_t* ids, cudaStream_t s) {
+  if (a.dcap) launch_report_<D, true>(a, offsets, ids, s);
+  else launch_report_<D, false>(a, offsets, ids, s);
+}
+
+template <int D, bool DEEP>
+static void launch_knn_(const QueryArgs& a, cudaStream_t s) {
   const unsigned g = (unsigned)((a.nq + QTHREADS - 1) / QTHREADS);
   KTimer kt;
   ktimer_begin(kt, "knn", a.nq, s);
   if (a.box) {
-    if (a.k <= 16) PKD_LAUNCH((k_knn_bb<D, 16><<<g, QTHREADS, 0, s>>>(a)));
-    else PKD_LAUNCH((k_knn_bb<D, 128><<<g, QTHREADS, 0, s>>>(a)));
+    if (a.k <= 16) PKD_LAUNCH((k_knn_bb<D, 16, DEEP><<<g, QTHREADS, 0, s>>>(a)));
+    else PKD_LAUNCH((k_knn_bb<D, 128, DEEP><<<g, QTHREADS, 0, s>>>(a)));
   } else {
-    if (a.k <= 16) PKD_LAUNCH(k_knn<D, 16><<<g, QTHREADS, 0, s>>>(a));
-    else PKD_LAUNCH(k_knn<D, 128><<<g, QTHREADS, 0, s>>>(a));
+    if (a.k <= 16) PKD_LAUNCH((k_knn<D, 16, DEEP><<<g, QTHREADS, 0, s>>>(a)));
+    else PKD_LAUNCH((k_knn<D, 128, DEEP><<<g, QTHREADS, 0, s>>>(a)));
   }
   ktimer_end(kt);
 }
-
 template <int D>
-static void launch_rc(const QueryArgs& a, cudaStream_t s) {
+static void launch_knn(const QueryArgs& a, cudaStream_t s) {
+  if (a.dcap) launch_knn_<D, true>(a, s);
+  else launch_knn_<D, false>(a, s);
+}
+
+template <int D, bool DEEP>
+static void launch_rc_(const QueryArgs& a, cudaStream_t s) {
   const unsigned g = (unsigned)((a.nq + QTHREADS - 1) / QTHREADS);
   KTimer kt;
   ktimer_begin(kt, "range_count", a.nq, s);
-  if (a.box) PKD_LAUNCH((k_range_bb<D, false><<<g, QTHREADS, 0, s>>>(a, nullptr, nullptr)));
-  else PKD_LAUNCH(k_range_count<D><<<g, QTHREADS, 0, s>>>(a));
+  if (a.box) PKD_LAUNCH((k_range_bb<D, false, DEEP><<<g, QTHREADS, 0, s>>>(a, nullptr, nullptr)));
+  else PKD_LAUNCH((k_range_count<D, DEEP><<<g, QTHREADS, 0, s>>>(a)));
   ktimer_end(kt);
+}
+template <int D>
+static void launch_rc(const QueryArgs& a, cudaStream_t s) {
+  if (a.dcap) launch_rc_<D, true>(a, s);
+  else launch_rc_<D, false>(a, s);
 }
 
 #define PKD_QDISPATCH(d, F, ...)      \
@@ -554,6 +612,49 @@ static void launch_rc(const QueryArgs& a, cudaStream_t s) {
 static int query_height_ok(const TreeMem& t) {
   // the depth-first stack holds at most height + 1 entries
   return t.st_host && t.st_host->max_depth + 2 < (uint32_t)QSTACK;
+}
+
+// Runs fn(args, first query) over the queries of `a`: one call with local
+// stacks, or, for a tree too deep for them, chunks of queries whose stacks
+// (height + 3 entries each) live in a global scratch buffer of at most
+// DEEP_SCRATCH bytes.  The status must have been read (check_status).
+constexpr uint64_t DEEP_SCRATCH = 1ull << 30;
+
+template <class F>
+static int for_query_chunks(const TreeMem& t, const QueryArgs& a, cudaStream_t s, F&& fn) {
+  if (query_height_ok(t)) {
+    fn(a, 0);
+    return PKD_OK;
+  }
+  if (!t.st_host) return PKD_EINTERNAL;
+  const int d = t.p.d;
+  const uint64_t cap = (uint64_t)t.st_host->max_depth + 3;
+  const uint64_t per = cap * (4 + 8 * (uint64_t)d + 1);
+  const uint64_t chunk = std::max<uint64_t>(1, std::min<uint64_t>(a.nq, DEEP_SCRATCH / per));
+  if (cap > (1u << 30)) return PKD_EINTERNAL;
+  uint32_t* dv = nullptr;
+  int32_t* db = nullptr;
+  uint8_t* df = nullptr;
+  int e = dalloc(&dv, chunk * cap, s);
+  if (e == PKD_OK) e = dalloc(&db, chunk * cap * 2 * (uint64_t)d, s);
+  if (e == PKD_OK) e = dalloc(&df, chunk * cap, s);
+  if (e == PKD_OK) {
+    for (uint64_t c0 = 0; c0 < a.nq; c0 += chunk) {
+      QueryArgs ac = a;
+      ac.nq = std::min<uint64_t>(chunk, a.nq - c0);
+      ac.q = a.q + c0 * (uint64_t)d;
+      if (a.hi) ac.hi = a.hi + c0 * (uint64_t)d;
+      ac.dv = dv;
+      ac.db = db;
+      ac.df = df;
+      ac.dcap = (int)cap;
+      fn(ac, c0);
+    }
+  }
+  dfree(dv, s);
+  dfree(db, s);
+  dfree(df, s);
+  return e;
 }
 
 }  // namespace pkd
@@ -576,11 +677,11 @@ int pkd::knn_on(TreeMem& t, uint32_t root, const int32_t* queries, uint64_t q, i
   if (k < 1 || k > 128) return PKD_EINVAL;
   if (q == 0) return PKD_OK;
   if (!queries || !out_ids || !out_d2) return PKD_EINVAL;
+  TreeTouch touch{&t, s};
   bool ok;
   PKD_TRY_(validate_coords(queries, q * (uint64_t)t.p.d, s, &ok));
   if (!ok) return PKD_EINVAL;
   PKD_TRY_(check_status(t, s));
-  if (!query_height_ok(t)) return PKD_EINTERNAL;
   QueryArgs a{};
   a.nodes = t.nodes;
   a.ndim = t.ndim;
@@ -593,7 +694,11 @@ int pkd::knn_on(TreeMem& t, uint32_t root, const int32_t* queries, uint64_t q, i
   a.out_d2 = out_d2;
   a.st = t.st;
   a.box = (t.bbox_on && root == t.root) ? t.bbox : nullptr;
-  PKD_QDISPATCH(t.p.d, launch_knn, a, s);
+  PKD_TRY_(for_query_chunks(t, a, s, [&](QueryArgs ac, uint64_t c0) {
+    ac.out_ids = out_ids + c0 * (uint64_t)k;
+    ac.out_d2 = out_d2 + c0 * (uint64_t)k;
+    PKD_QDISPATCH(t.p.d, launch_knn, ac, s);
+  }));
   PKD_CUDA(cudaGetLastError());
   return PKD_OK;
 }
@@ -607,12 +712,12 @@ int pkd_range_count(const pkd_tree* tc, const int32_t* lo, const int32_t* hi, ui
   if (!lo || !hi || !out_counts) return PKD_EINVAL;
   TreeMem& t = const_cast<TreeMem&>(tc->m);
   cudaStream_t s = (cudaStream_t)stream;
+  TreeTouch touch{&t, s};
   bool ok1, ok2;
   PKD_TRY_(validate_coords(lo, q * (uint64_t)t.p.d, s, &ok1));
   PKD_TRY_(validate_coords(hi, q * (uint64_t)t.p.d, s, &ok2));
   if (!ok1 || !ok2) return PKD_EINVAL;
   PKD_TRY_(check_status(t, s));
-  if (!query_height_ok(t)) return PKD_EINTERNAL;
   QueryArgs a{};
   a.nodes = t.nodes;
   a.ndim = t.ndim;
@@ -624,7 +729,10 @@ int pkd_range_count(const pkd_tree* tc, const int32_t* lo, const int32_t* hi, ui
   a.out_cnt = out_counts;
   a.st = t.st;
   a.box = t.bbox_on ? t.bbox : nullptr;
-  PKD_QDISPATCH(t.p.d, launch_rc, a, s);
+  PKD_TRY_(for_query_chunks(t, a, s, [&](QueryArgs ac, uint64_t c0) {
+    ac.out_cnt = out_counts + c0;
+    PKD_QDISPATCH(t.p.d, launch_rc, ac, s);
+  }));
   PKD_CUDA(cudaGetLastError());
   return PKD_OK;
 }
@@ -637,12 +745,12 @@ int pkd_range_report(const pkd_tree* tc, const int32_t* lo, const int32_t* hi, u
   if (!lo || !hi || !offsets) return PKD_EINVAL;
   TreeMem& t = const_cast<TreeMem&>(tc->m);
   cudaStream_t s = (cudaStream_t)stream;
+  TreeTouch touch{&t, s};
   bool ok1, ok2;
   PKD_TRY_(validate_coords(lo, q * (uint64_t)t.p.d, s, &ok1));
   PKD_TRY_(validate_coords(hi, q * (uint64_t)t.p.d, s, &ok2));
   if (!ok1 || !ok2) return PKD_EINVAL;
   PKD_TRY_(check_status(t, s));
-  if (!query_height_ok(t)) return PKD_EINTERNAL;
   // pass 1: counts (into offsets[0..q)), scanned in place into offsets[0..q]
   uint64_t* counts = nullptr;
   uint64_t* partial = nullptr;
@@ -664,7 +772,15 @@ int pkd_range_report(const pkd_tree* tc, const int32_t* lo, const int32_t* hi, u
   a.out_cnt = counts;
   a.st = t.st;
   a.box = t.bbox_on ? t.bbox : nullptr;
-  PKD_QDISPATCH(t.p.d, launch_rc, a, s);
+  e = for_query_chunks(t, a, s, [&](QueryArgs ac, uint64_t c0) {
+    ac.out_cnt = counts + c0;
+    PKD_QDISPATCH(t.p.d, launch_rc, ac, s);
+  });
+  if (e) {
+    dfree(counts, s);
+    dfree(partial, s);
+    return e;
+  }
   PKD_LAUNCH(k_scan64_reduce<<<(unsigned)nb, SCAN64_THREADS, 0, s>>>(counts, q, partial));
   PKD_LAUNCH(k_scan64_partials<<<1, SCAN64_THREADS, 0, s>>>(partial, nb));
   PKD_LAUNCH(k_scan64_apply<<<(unsigned)nb, SCAN64_THREADS, 0, s>>>(counts, q, partial, offsets));
@@ -676,7 +792,9 @@ int pkd_range_report(const pkd_tree* tc, const int32_t* lo, const int32_t* hi, u
   *total = tot;
   if (tot > ids_cap || (tot > 0 && !ids)) return PKD_EINVAL;
   // pass 2: the ids
-  PKD_QDISPATCH(t.p.d, launch_report, a, offsets, ids, s);
+  PKD_TRY_(for_query_chunks(t, a, s, [&](QueryArgs ac, uint64_t c0) {
+    PKD_QDISPATCH(t.p.d, launch_report, ac, offsets + c0, ids, s);
+  }));
   PKD_CUDA(cudaGetLastError());
   return PKD_OK;
 }
@@ -738,8 +856,8 @@ static void noalloc_warm(cudaStream_t s) {
   QueryArgs a{};
   a.nq = 0;
   a.k = 1;
-  PKD_LAUNCH(k_knn<D, 16><<<1, QTHREADS, 0, s>>>(a));
-  PKD_LAUNCH(k_knn<D, 128><<<1, QTHREADS, 0, s>>>(a));
+  PKD_LAUNCH((k_knn<D, 16, false><<<1, QTHREADS, 0, s>>>(a)));
+  PKD_LAUNCH((k_knn<D, 128, false><<<1, QTHREADS, 0, s>>>(a)));
 }
 
 // Set-up, once per device, with that device current: the scratch address,
@@ -774,8 +892,8 @@ static int noalloc_scratch(int dev, cudaStream_t s, unsigned char** out) {
 template <int D>
 static void launch_knn_noalloc(const QueryArgs& a, cudaStream_t s) {
   const unsigned g = (unsigned)((a.nq + QTHREADS - 1) / QTHREADS);
-  if (a.k <= 16) PKD_LAUNCH(k_knn<D, 16><<<g, QTHREADS, 0, s>>>(a));
-  else PKD_LAUNCH(k_knn<D, 128><<<g, QTHREADS, 0, s>>>(a));
+  if (a.k <= 16) PKD_LAUNCH((k_knn<D, 16, false><<<g, QTHREADS, 0, s>>>(a)));
+  else PKD_LAUNCH((k_knn<D, 128, false><<<g, QTHREADS, 0, s>>>(a)));
 }
 
 }  // namespace pkd
@@ -799,6 +917,7 @@ extern "C" int pkd_knn_ids_noalloc(const pkd_tree* tc, const int32_t* queries, u
   unsigned char* scratch = nullptr;
   PKD_TRY_(noalloc_scratch(dev, (cudaStream_t)stream, &scratch));
   cudaStream_t s = (cudaStream_t)stream;
+  TreeTouch touch{&t, s, true};  // may not create an event
   unsigned* bad = (unsigned*)scratch;
   PKD_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned), s));
   PKD_LAUNCH(k_noalloc_check<<<152 * 8, 256, 0, s>>>(queries, q * (uint64_t)t.p.d, bad));

@@ -363,6 +363,40 @@ void tree_release(TreeMem& t) {
   t = TreeMem{};
 }
 
+static std::mutex g_use_mu;
+
+void tree_touch(TreeMem& t, cudaStream_t s, bool noalloc) {
+  std::lock_guard<std::mutex> g(g_use_mu);
+  for (auto& u : t.uses)
+    if (u.first == s) {
+      if (cudaEventRecord(u.second, s) != cudaSuccess) {
+        cudaGetLastError();
+        t.untracked = true;
+      }
+      return;
+    }
+  cudaEvent_t ev = nullptr;
+  if (noalloc || cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(ev, s) != cudaSuccess) {
+    cudaGetLastError();
+    if (ev) cudaEventDestroy(ev);
+    t.untracked = true;
+    return;
+  }
+  t.uses.emplace_back(s, ev);
+}
+
+void tree_wait_uses(TreeMem& t) {
+  std::lock_guard<std::mutex> g(g_use_mu);
+  if (t.untracked) cudaDeviceSynchronize();
+  for (auto& u : t.uses) {
+    if (!t.untracked) cudaStreamWaitEvent(0, u.second, 0);
+    cudaEventDestroy(u.second);
+  }
+  t.uses.clear();
+  t.untracked = false;
+}
+
 cudaStream_t side_stream() {
   static cudaStream_t streams[64] = {};
   static std::mutex mu;
@@ -564,14 +598,15 @@ int pkd_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const pkd_
   t->m.top = n;
   t->m.ids.live = n;
   t->m.ids.used = n;
+  tree_touch(t->m, s);
   *out = t;
   return PKD_OK;
 }
 
 void pkd_free(pkd_tree* t) {
   if (!t) return;
-  cudaDeviceSynchronize();  // no kernel of any stream may still use the tree
   trace_mark(0, "free: enter");
+  tree_wait_uses(t->m);  // the frees below are ordered after every call's work
   tree_release(t->m);
   delete t;
   trace_mark(0, "free: release");

@@ -1611,6 +1611,7 @@ int pkd_batch_insert(pkd_tree* tc, const int32_t* coords, const uint32_t* ids, u
   TreeMem& t = tc->m;
   if (t.size + m >= (1ull << 31)) return PKD_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  TreeTouch touch{&t, s};
   bool ok;
   PKD_TRY_(validate_coords(coords, m * (uint64_t)t.p.d, s, &ok));
   if (!ok) return PKD_EINVAL;
@@ -1647,6 +1648,7 @@ int pkd_batch_delete(pkd_tree* tc, const uint32_t* ids, uint64_t m, uint64_t* n_
   TreeMem& t = tc->m;
   if (m >= (1ull << 31)) return PKD_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  TreeTouch touch{&t, s};
   PKD_TRY_(check_status(t, s));
   // ids -> coordinates: every LIVE id of the batch is taken once (repeats and
   // unknown or deleted ids are skipped) and staged for the sieve

@@ -130,3 +130,54 @@ def test_range_report_after_updates():
         assert np.array_equal(np.sort(got[off[i]:off[i + 1]]), want[i])
     o.close()
     t.close()
+
+
+def test_queries_on_a_tree_deeper_than_the_local_stack():
+    """alpha = 1/2 never rebuilds an interior node, so batches that always
+    land right of every stored point grow one path by two levels per batch
+    (the rightmost leaf plus the batch is rebuilt below it).  Past height
+    126 the searches keep their stacks in global scratch, a chunk of queries
+    at a time; every answer still equals the oracle's, with and without
+    stored boxes."""
+    import torch
+
+    pkd = _pkd()
+    d = 1
+    p = pkd.Params(d=d, phi=2, lam=2, sigma_log2=0, sigma_os=1, alpha_num=1, alpha_den=2)
+    X = (np.arange(8, dtype=np.int32) * 7).reshape(8, 1)
+    ids = np.arange(8, dtype=np.uint32)
+    t = pkd.Tree(to_dev(X), ids_dev(ids), p)
+    o = O.OracleTree(X, ids, oparams(p))
+    nxt, top = 8, 100
+    for r in range(80):
+        Y = (top + np.array([3, 1, 2], dtype=np.int32)).reshape(3, 1)
+        yid = np.arange(nxt, nxt + 3, dtype=np.uint32)
+        t.insert(to_dev(Y), ids_dev(yid))
+        o.insert(Y, yid)
+        nxt += 3
+        top += 10
+    assert t.height > 130
+    pts = o.points()[1]
+    Q = np.concatenate([I.uniform(200, d, 71) % (top + 50), pts[::7]]).astype(np.int32)
+    lo, hi = I.boxes(100, d, 300, 72)
+    lo, hi = lo % top, hi % top
+    hi = np.maximum(lo, hi)
+    for boxes in (False, True):
+        pkd.pkd_set_bounding_boxes(t._h, boxes)
+        for k in (1, 5, 40):
+            gi, gd = t.knn(to_dev(Q), k)
+            wi, wd = o.knn(Q, k)
+            assert np.array_equal(gd.cpu().numpy(), wd) and np.array_equal(gi.cpu().numpy().view(np.uint32), wi)
+        cnt = t.range_count(to_dev(lo), to_dev(hi)).cpu().numpy().astype(np.uint64)
+        assert np.array_equal(cnt, o.range_count(lo, hi))
+        off, got = pkd.pkd_range_report(t._h, to_dev(lo), to_dev(hi))
+        off = off.cpu().numpy().astype(np.int64)
+        got = got.cpu().numpy().view(np.uint32)
+        want = o.range_report(lo, hi)
+        for i in range(len(lo)):
+            assert np.array_equal(np.sort(got[off[i]:off[i + 1]]), want[i])
+    # the no-allocation search has no scratch for a deep tree: it refuses
+    out = torch.empty((len(Q), 5), dtype=torch.int32, device="cuda")
+    with pytest.raises(Exception):
+        pkd.pkd_knn_ids_noalloc(t._h, to_dev(Q), 5, out)
+    t.close()

@@ -140,7 +140,7 @@ int boxes_compute(TreeMem& t, cudaStream_t s) {
   PinnedBlock hb(s);
   if (!hb.p) return PKD_ENOMEM;
   uint32_t* hn = (uint32_t*)hb.p;
-  PKD_CUDA(cudaMemcpyAsync(all, &t.root, 4, cudaMemcpyHostToDevice, s));
+  PKD_TRY_(dev_store(all, &t.root, 4, s));
   std::vector<uint64_t> level_start{0, 1};
   for (int lev = 0; lev < 100000; ++lev) {
     const uint64_t a = level_start[lev], b = level_start[lev + 1];

@@ -1562,7 +1562,7 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     roots = const_cast<Seg*>(job.dsegs);
   } else {
     PKD_TRY(sc.get(&roots, std::max<uint64_t>(nroots, 1)));
-    PKD_CUDA(cudaMemcpyAsync(roots, job.segs.data(), nroots * sizeof(Seg), cudaMemcpyHostToDevice, s));
+    PKD_TRY(dev_store(roots, job.segs.data(), nroots * sizeof(Seg), s));
   }
   const uint32_t wcap = (uint32_t)warp_cap_for(d);
   // every base segment is a root or a non-empty bucket: at most extent + roots
@@ -1629,13 +1629,8 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     hd[0] = RoundDyn{in, B, (int)IN_B, job.input_coords ? (int)IN_INPUT : (int)IN_A, roots, bb.children[0]};
     hd[1] = RoundDyn{fromB, t.A, (int)IN_A, (int)IN_B, bb.children[0], bb.children[1]};
     hd[2] = RoundDyn{fromA, B, (int)IN_B, (int)IN_A, bb.children[1], bb.children[0]};
-    for (int k = 0; k < 3; ++k) {
-      static_assert(sizeof(RoundDyn) <= PINNED_BLOCK, "round arguments");
-      PinnedBlock one(s);
-      if (!one.p) return PKD_ENOMEM;
-      memcpy(one.p, &hd[k], sizeof(RoundDyn));
-      PKD_CUDA(cudaMemcpyAsync(bb.dyn + k, one.p, sizeof(RoundDyn), cudaMemcpyHostToDevice, s));
-    }
+    static_assert(sizeof(hd) % 4 == 0, "round arguments");
+    PKD_TRY(dev_store(bb.dyn, hd, sizeof(hd), s));
   }
 
   RoundArgs r{};
@@ -1927,7 +1922,7 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     GraphEntry* ent = graph_find(key);
     if (ent) {
       memcpy(hshape, ent->shapes, sizeof(ent->shapes));
-      PKD_CUDA(cudaMemcpyAsync(dshape, hshape, sizeof(ent->shapes), cudaMemcpyHostToDevice, s));
+      PKD_TRY(dev_store(dshape, hshape, sizeof(ent->shapes), s));
       PKD_CUDA(cudaGraphLaunch(ent->exec, s));
       PKD_CUDA(cudaEventRecord(ent->done, s));
       ++g_graph_builds;
@@ -1982,9 +1977,7 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     if (e == PKD_OK && nshape == 0) e = PKD_EINTERNAL;
     for (int k = nshape; e == PKD_OK && k < MAX_SHAPES; ++k) hshape[k] = hshape[0];
     cudaGraphExec_t exec = nullptr;
-    if (e == PKD_OK && cudaMemcpyAsync(dshape, hshape, MAX_SHAPES * sizeof(BaseShape), cudaMemcpyHostToDevice, s) !=
-                           cudaSuccess)
-      e = PKD_ECUDA;
+    if (e == PKD_OK) e = dev_store(dshape, hshape, MAX_SHAPES * sizeof(BaseShape), s);
     if (e == PKD_OK && cudaGraphInstantiate(&exec, graph_h, 0) != cudaSuccess) e = PKD_ECUDA;
     if (e == PKD_OK && cudaGraphUpload(exec, s) != cudaSuccess) e = PKD_ECUDA;
     if (e == PKD_OK && cudaGraphLaunch(exec, s) != cudaSuccess) e = PKD_ECUDA;

@@ -65,6 +65,16 @@ struct TreeMem {
   bool untracked = false;
 };
 
+// Small host values into device memory, in stream order, by a kernel that
+// takes them as arguments (bytes: a multiple of 4, dst 4-byte aligned).  A
+// host-to-device copy would queue behind whatever large copy the caller has
+// on the same copy engine (the next step's input, say) and hold the stream
+// back for its whole duration; a kernel does not.  Up to 4 KiB; larger
+// values go through cudaMemcpyAsync.
+int dev_store(void* dst, const void* src, size_t bytes, cudaStream_t s);
+// n words from device to device the same way (a small copy).
+int dev_copy_words(uint32_t* dst, const uint32_t* src, uint32_t n, cudaStream_t s);
+
 // Records the use of tree t by the work queued so far on stream s.
 void tree_touch(TreeMem& t, cudaStream_t s, bool noalloc = false);
 // Orders the legacy default stream after every recorded use (or, after an

@@ -54,7 +54,7 @@ int pkd_build_forest(const int32_t* coords, const uint32_t* ids, const uint64_t*
     return e;
   }
   const uint32_t first_free = n_trees;
-  cudaMemcpyAsync(f->m.shared_next, &first_free, 4, cudaMemcpyHostToDevice, s);
+  dev_store(f->m.shared_next, &first_free, 4, s);
   BuildJob job;
   job.input_coords = coords;
   job.input_ids = ids;

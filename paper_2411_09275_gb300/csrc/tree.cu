@@ -363,6 +363,43 @@ void tree_release(TreeMem& t) {
   t = TreeMem{};
 }
 
+namespace {
+constexpr int STORE_WORDS = 64;  // 256 bytes of kernel arguments a launch
+struct StoreBlock {
+  uint32_t w[STORE_WORDS];
+};
+__global__ void k_store_words(uint32_t* dst, StoreBlock v, uint32_t n) {
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = v.w[i];
+}
+__global__ void k_copy_words(uint32_t* dst, const uint32_t* src, uint32_t n) {
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+}  // namespace
+
+int dev_store(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes % 4 || ((uintptr_t)dst & 3)) return PKD_EINVAL;
+  if (bytes > 4096) {
+    PKD_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+    return PKD_OK;
+  }
+  const uint32_t nw = (uint32_t)(bytes / 4);
+  for (uint32_t o = 0; o < nw; o += STORE_WORDS) {
+    StoreBlock v{};
+    const uint32_t n = std::min<uint32_t>(STORE_WORDS, nw - o);
+    memcpy(v.w, (const uint32_t*)src + o, (size_t)n * 4);
+    PKD_LAUNCH(k_store_words<<<1, 64, 0, s>>>((uint32_t*)dst + o, v, n));
+  }
+  PKD_CUDA(cudaGetLastError());
+  return PKD_OK;
+}
+
+int dev_copy_words(uint32_t* dst, const uint32_t* src, uint32_t n, cudaStream_t s) {
+  if (n == 0) return PKD_OK;
+  PKD_LAUNCH(k_copy_words<<<1, 256, 0, s>>>(dst, src, n));
+  PKD_CUDA(cudaGetLastError());
+  return PKD_OK;
+}
+
 static std::mutex g_use_mu;
 
 void tree_touch(TreeMem& t, cudaStream_t s, bool noalloc) {
@@ -542,7 +579,7 @@ int pkd_build(const int32_t* coords, const uint32_t* ids, uint64_t n, const pkd_
   }
   t->m.root = 0;
   uint32_t one = 1;
-  cudaMemcpyAsync(t->m.shared_next, &one, 4, cudaMemcpyHostToDevice, s);
+  dev_store(t->m.shared_next, &one, 4, s);
   // The id table (id -> coordinates, and the check that ids are unique) is
   // filled on a second stream while the shared-memory base cases run: they
   // are bound by instruction issue, the table fill by memory traffic.

@@ -1287,13 +1287,13 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
   PKD_TRY(sc.get(&cur_bigmap, 1));
   PKD_TRY(sc.get(&cur_small, 1));
   uint32_t zero = 0;
-  PKD_CUDA(cudaMemcpyAsync(cur, &root, sizeof(Seg), cudaMemcpyHostToDevice, s));
+  PKD_TRY(dev_store(cur, &root, sizeof(Seg), s));
   const bool root_big = m > SMALL_ITEM;
   if (root_big) {
-    PKD_CUDA(cudaMemcpyAsync(cur_big, &root, sizeof(Seg), cudaMemcpyHostToDevice, s));
-    PKD_CUDA(cudaMemcpyAsync(cur_bigmap, &zero, 4, cudaMemcpyHostToDevice, s));
+    PKD_TRY(dev_store(cur_big, &root, sizeof(Seg), s));
+    PKD_TRY(dev_store(cur_bigmap, &zero, 4, s));
   } else {
-    PKD_CUDA(cudaMemcpyAsync(cur_small, &zero, 4, cudaMemcpyHostToDevice, s));
+    PKD_TRY(dev_store(cur_small, &zero, 4, s));
   }
   uint32_t ncur = 1, tiles = root_big ? (uint32_t)((m + TILE - 1) / TILE) : 0;
   uint64_t big_pts = root_big ? m : 0;  // points the round's sieve kernels move
@@ -1317,7 +1317,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
     PKD_TRY(sc.get(&R.d_n, 4));
     uint32_t hn[4] = {ncur, nbig, nsmall, 0};
     PKD_CUDA(cudaMemsetAsync(R.iflag, 0, (size_t)ncur * 4, s));
-    PKD_CUDA(cudaMemcpyAsync(R.d_n, hn, 16, cudaMemcpyHostToDevice, s));
+    PKD_TRY(dev_store(R.d_n, hn, 16, s));
     uint32_t* nbk;
     PKD_TRY(sc.get(&nbk, ncur));
     Seg *next, *next_big;
@@ -1541,7 +1541,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
         PKD_LAUNCH(k_front_expand<<<(nf + 127) / 128, 128, 0, s>>>(fa, fc, fb, fc + 1, leaves, fc + 2, bigleaves,
                                                                     fc + 3, t.nodes, t.ndim, t.aux, insert ? 0 : 1,
                                                                     fcap32, t.st));
-        PKD_CUDA(cudaMemcpyAsync(fc, fc + 1, 4, cudaMemcpyDeviceToDevice, s));
+        PKD_TRY(dev_copy_words(fc, fc + 1, 1, s));
         PKD_CUDA(cudaMemcpyAsync(hctr + 12, fc, 16, cudaMemcpyDeviceToHost, s));
         PKD_CUDA(cudaStreamSynchronize(s));
         nf = hctr[12];
@@ -1563,7 +1563,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
     }
     trace_mark(s, "upd: flatten + gather");
     PKD_LAUNCH(k_save_roots<<<gi, 128, 0, s>>>(items_out, d_nitems, t.nodes, t.ndim, saved_nodes, saved_dims));
-    PKD_CUDA(cudaMemcpyAsync(saved_next, t.shared_next, 4, cudaMemcpyDeviceToDevice, s));
+    PKD_TRY(dev_copy_words(saved_next, t.shared_next, 1, s));
     BuildJob job;
     job.base = t.top;
     job.extent = std::max<uint64_t>(total, 1);
@@ -1572,7 +1572,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
     const int eb = run_build(t, job, s);
     if (eb != PKD_OK) {
       PKD_LAUNCH(k_restore_roots<<<gi, 128, 0, s>>>(items_out, d_nitems, t.nodes, t.ndim, saved_nodes, saved_dims));
-      cudaMemcpyAsync(t.shared_next, saved_next, 4, cudaMemcpyDeviceToDevice, s);
+      dev_copy_words(t.shared_next, saved_next, 1, s);
       return eb;
     }
     PKD_LAUNCH(k_item_leaves<<<gi, 128, 0, s>>>(items_out, d_nitems, t.nodes, t.ndim, (uint32_t)p.phi));

@@ -146,7 +146,7 @@ int boxes_compute(TreeMem& t, cudaStream_t s) {
     const uint64_t a = level_start[lev], b = level_start[lev + 1];
     const uint32_t nf = (uint32_t)(b - a);
     if (nf == 0) break;
-    PKD_CUDA(cudaMemsetAsync(ctr, 0, 4, s));
+    PKD_TRY(dev_fill(ctr, 0, 4, s));
     PKD_LAUNCH(k_bb_expand<<<(nf + BB_THREADS - 1) / BB_THREADS, BB_THREADS, 0, s>>>(
         all + a, nf, all + b, ctr, t.nodes, t.ndim, (uint32_t)(cap - b), t.st));
     PKD_CUDA(cudaMemcpyAsync(hn, ctr, 4, cudaMemcpyDeviceToHost, s));

@@ -74,6 +74,9 @@ struct TreeMem {
 int dev_store(void* dst, const void* src, size_t bytes, cudaStream_t s);
 // n words from device to device the same way (a small copy).
 int dev_copy_words(uint32_t* dst, const uint32_t* src, uint32_t n, cudaStream_t s);
+// bytes of dst set to `value` by a kernel (for the same reason: a fill that
+// the runtime may hand to a copy engine would wait for the caller's copies).
+int dev_fill(void* dst, int value, size_t bytes, cudaStream_t s);
 
 // Records the use of tree t by the work queued so far on stream s.
 void tree_touch(TreeMem& t, cudaStream_t s, bool noalloc = false);

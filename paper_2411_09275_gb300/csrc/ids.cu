@@ -251,7 +251,7 @@ int ids_alloc(IdTable& T, int d, uint64_t cap, cudaStream_t s) {
     ids_release(T, s);
     return e == cudaErrorMemoryAllocation ? PKD_ENOMEM : PKD_ECUDA;
   }
-  PKD_CUDA(cudaMemsetAsync(T.key, 0xFF, (size_t)cap * 8, s));
+  PKD_TRY(dev_fill(T.key, 0xFF, (size_t)cap * 8, s));
   return PKD_OK;
 }
 
@@ -289,7 +289,7 @@ int read_idflags(TreeMem& t, cudaStream_t s, int* flags) {
   PKD_CUDA(cudaMemcpyAsync(t.st_host, t.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
   PKD_CUDA(cudaStreamSynchronize(s));
   *flags = t.st_host->idflags;
-  if (*flags) PKD_CUDA(cudaMemsetAsync(&t.st->idflags, 0, sizeof(int), s));
+  if (*flags) PKD_TRY(dev_fill(&t.st->idflags, 0, sizeof(int), s));
   return PKD_OK;
 }
 

@@ -200,7 +200,7 @@ int validate_coords(const int32_t* c, uint64_t cnt, cudaStream_t s, bool* ok) {
   int* d = nullptr;
   PKD_TRY_(dalloc(&d, 1, s));
   int h = 0;
-  cudaMemsetAsync(d, 0, 4, s);
+  dev_fill(d, 0, 4, s);
   KTimer kt;
   ktimer_begin(kt, "validate", cnt, s);
   PKD_LAUNCH(k_validate<<<152 * 8, 256, 0, s>>>(c, cnt, d));
@@ -374,7 +374,40 @@ __global__ void k_store_words(uint32_t* dst, StoreBlock v, uint32_t n) {
 __global__ void k_copy_words(uint32_t* dst, const uint32_t* src, uint32_t n) {
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
+__global__ void k_fill_bytes(uint8_t* p, uint8_t v, uint32_t n) {
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) p[i] = v;
+}
+__global__ void k_fill16(uint4* p, uint4 v, uint64_t n) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
 }  // namespace
+
+int dev_fill(void* dst, int value, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return PKD_OK;
+  uint8_t* p = (uint8_t*)dst;
+  const uint8_t v = (uint8_t)(value & 0xFF);
+  size_t head = (16 - ((uintptr_t)p & 15)) & 15;
+  if (head > bytes) head = bytes;
+  const size_t body = (bytes - head) / 16 * 16, tail = bytes - head - body;
+  if (head) PKD_LAUNCH(k_fill_bytes<<<1, 32, 0, s>>>(p, v, (uint32_t)head));
+  if (body) {
+    static int sms = 0;
+    if (!sms) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (sms <= 0) sms = 1;
+    }
+    const uint32_t w = 0x01010101u * v;
+    const uint64_t n16 = body / 16;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((n16 + 255) / 256, (uint64_t)sms * 8));
+    PKD_LAUNCH(k_fill16<<<grid, 256, 0, s>>>((uint4*)(p + head), make_uint4(w, w, w, w), n16));
+  }
+  if (tail) PKD_LAUNCH(k_fill_bytes<<<1, 32, 0, s>>>(p + head + body, v, (uint32_t)tail));
+  PKD_CUDA(cudaGetLastError());
+  return PKD_OK;
+}
 
 int dev_store(void* dst, const void* src, size_t bytes, cudaStream_t s) {
   if (bytes % 4 || ((uintptr_t)dst & 3)) return PKD_EINVAL;
@@ -524,8 +557,8 @@ int tree_alloc(TreeMem& t, const Params& p, uint64_t cap, uint64_t shared_cap, c
     return e == cudaErrorMemoryAllocation ? PKD_ENOMEM : PKD_ECUDA;
   }
   t.A.stride = t.cap;
-  cudaMemsetAsync(t.st, 0, sizeof(DevStatus), s);
-  cudaMemsetAsync(t.shared_next, 0, 16, s);
+  dev_fill(t.st, 0, sizeof(DevStatus), s);
+  dev_fill(t.shared_next, 0, 16, s);
   return PKD_OK;
 }
 

@@ -1169,11 +1169,11 @@ static int ensure_capacity(TreeMem& t, uint64_t need, cudaStream_t s) {
     return PKD_ENOMEM;
   }
   if (dead2) {
-    PKD_CUDA(cudaMemsetAsync(dead2, 0, ncap, s));
+    PKD_TRY(dev_fill(dead2, 0, ncap, s));
     PKD_CUDA(cudaMemcpyAsync(dead2, t.dead, t.cap, cudaMemcpyDeviceToDevice, s));
   }
   if (aux2) {
-    PKD_CUDA(cudaMemsetAsync(aux2, 0, nnode * 4, s));
+    PKD_TRY(dev_fill(aux2, 0, nnode * 4, s));
     PKD_CUDA(cudaMemcpyAsync(aux2, t.aux, t.node_cap * 4, cudaMemcpyDeviceToDevice, s));
   }
   for (void* q : {(void*)t.A.c, (void*)t.A.id, (void*)t.nodes, (void*)t.ndim, (void*)t.dead, (void*)t.aux})
@@ -1191,11 +1191,11 @@ static int ensure_capacity(TreeMem& t, uint64_t need, cudaStream_t s) {
 static int ensure_delete_scratch(TreeMem& t, cudaStream_t s) {
   if (!t.dead) {
     PKD_CUDA(big_alloc((void**)&t.dead, t.cap, s));
-    PKD_CUDA(cudaMemsetAsync(t.dead, 0, t.cap, s));
+    PKD_TRY(dev_fill(t.dead, 0, t.cap, s));
   }
   if (!t.aux) {
     PKD_CUDA(big_alloc((void**)&t.aux, t.node_cap * 4, s));
-    PKD_CUDA(cudaMemsetAsync(t.aux, 0, t.node_cap * 4, s));
+    PKD_TRY(dev_fill(t.aux, 0, t.node_cap * 4, s));
   }
   return PKD_OK;
 }
@@ -1240,7 +1240,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
 
   uint32_t* dctr;
   PKD_TRY(sc.get(&dctr, 32));
-  PKD_CUDA(cudaMemsetAsync(dctr, 0, 32 * 4, s));
+  PKD_TRY(dev_fill(dctr, 0, 32 * 4, s));
   PinnedBlock hblk(s);  // 128 bytes of host counters
   uint32_t* hctr = (uint32_t*)hblk.p;
   if (!hctr) return PKD_ENOMEM;
@@ -1309,14 +1309,14 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
     PKD_TRY(sc.get(&R.slots, (size_t)ncur * HN));
     PKD_TRY(sc.get(&R.fnd, (size_t)ncur * HN));
     PKD_TRY(sc.get(&R.nsz, (size_t)ncur * HN));
-    PKD_CUDA(cudaMemsetAsync(R.nsz, 0xFF, (size_t)ncur * HN * 4, s));
+    PKD_TRY(dev_fill(R.nsz, 0xFF, (size_t)ncur * HN * 4, s));
     PKD_TRY(sc.get(&R.link, (size_t)ncur * NB));
     PKD_TRY(sc.get(&R.bstart, (size_t)ncur * NB));
     PKD_TRY(sc.get(&R.blen, (size_t)ncur * NB));
     PKD_TRY(sc.get(&R.iflag, ncur));
     PKD_TRY(sc.get(&R.d_n, 4));
     uint32_t hn[4] = {ncur, nbig, nsmall, 0};
-    PKD_CUDA(cudaMemsetAsync(R.iflag, 0, (size_t)ncur * 4, s));
+    PKD_TRY(dev_fill(R.iflag, 0, (size_t)ncur * 4, s));
     PKD_TRY(dev_store(R.d_n, hn, 16, s));
     uint32_t* nbk;
     PKD_TRY(sc.get(&nbk, ncur));
@@ -1326,8 +1326,8 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
     PKD_TRY(sc.get(&next_big, (size_t)ncur * NB));
     PKD_TRY(sc.get(&next_bigmap, (size_t)ncur * NB));
     PKD_TRY(sc.get(&next_small, (size_t)ncur * NB));
-    PKD_CUDA(cudaMemsetAsync(dctr, 0, 16, s));
-    PKD_CUDA(cudaMemsetAsync(dctr + 16, 0, 4, s));
+    PKD_TRY(dev_fill(dctr, 0, 16, s));
+    PKD_TRY(dev_fill(dctr + 16, 0, 4, s));
 
     ua.items = cur;
     ua.nitems = R.d_n;
@@ -1425,7 +1425,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
     bool on;
     ~ClearMarks() {
       if (!on) return;
-      cudaMemsetAsync(t.dead, 0, t.cap, s);
+      dev_fill(t.dead, 0, t.cap, s);
       for (const auto& R : rounds)
         PKD_LAUNCH(k_clear_aux<<<(unsigned)(((uint64_t)R.n * HN + 255) / 256), 256, 0, s>>>(R.slots, (uint64_t)R.n * HN,
                                                                                            t.aux));
@@ -1529,7 +1529,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
     // old subtrees appears once)
     {
       uint32_t* fc = dctr + 12;  // [0] cur, [1] next, [2] leaves, [3] big leaves
-      PKD_CUDA(cudaMemsetAsync(fc, 0, 16, s));
+      PKD_TRY(dev_fill(fc, 0, 16, s));
       PKD_LAUNCH(k_front_init<<<gi, 128, 0, s>>>(items_out, d_nitems, fa, fc));
       PKD_CUDA(cudaMemcpyAsync(hctr + 12, fc, 12, cudaMemcpyDeviceToHost, s));
       PKD_CUDA(cudaStreamSynchronize(s));
@@ -1537,7 +1537,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
       const uint32_t fcap32 = (uint32_t)std::min<uint64_t>(fcap, 0xFFFFFFF0ull);
       for (int it = 0; nf > 0; ++it) {
         if (it > 100000) return PKD_EINTERNAL;
-        PKD_CUDA(cudaMemsetAsync(fc + 1, 0, 4, s));
+        PKD_TRY(dev_fill(fc + 1, 0, 4, s));
         PKD_LAUNCH(k_front_expand<<<(nf + 127) / 128, 128, 0, s>>>(fa, fc, fb, fc + 1, leaves, fc + 2, bigleaves,
                                                                     fc + 3, t.nodes, t.ndim, t.aux, insert ? 0 : 1,
                                                                     fcap32, t.st));
@@ -1588,7 +1588,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
   t.top += total;
   clear_marks.on = false;
   if (!insert) {
-    PKD_CUDA(cudaMemsetAsync(t.dead, 0, t.cap, s));
+    PKD_TRY(dev_fill(t.dead, 0, t.cap, s));
     for (auto& R : rounds)
       PKD_LAUNCH(k_clear_aux<<<(unsigned)(((uint64_t)R.n * HN + 255) / 256), 256, 0, s>>>(R.slots, (uint64_t)R.n * HN, t.aux));
   }
@@ -1661,7 +1661,7 @@ int pkd_batch_delete(pkd_tree* tc, const uint32_t* ids, uint64_t m, uint64_t* n_
   PKD_TRY(sc.get(&wid, m));
   PKD_TRY(sc.get(&wslots, m));
   PKD_TRY(sc.get(&cnt, 1));
-  PKD_CUDA(cudaMemsetAsync(cnt, 0, 4, s));
+  PKD_TRY(dev_fill(cnt, 0, 4, s));
   Pts W{wc, wid, m};
   ids_take(t, ids, m, W, wslots, cnt, s);
   PinnedBlock hb(s);

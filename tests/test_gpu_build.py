@@ -158,3 +158,23 @@ def test_recorded_build_graph_relaunched_on_new_data():
             t.close()
     # the same sizes four times: at least one build found its graph recorded
     assert reused >= 1
+
+
+def test_recorded_graphs_evicted_and_relaunched_stay_correct():
+    """More distinct build shapes than the recorded-graph cache holds (16):
+    every build records or relaunches a graph, evicted graphs are destroyed
+    only once their launches have completed, and every tree still equals
+    the oracle's."""
+    pkd = _pkd()
+    d = 2
+    p = pkd.Params(d=d, phi=8, lam=3, sigma_log2=2, sigma_os=4)
+    sizes = [3000 + 1700 * i for i in range(20)]
+    with knobs(base_cap=256, skel_cap=64):
+        for rep in range(2):
+            for i, n in enumerate(sizes):
+                if rep and i % 3:
+                    continue
+                X = make_points("varden" if i % 2 else "uniform", n, d, 4000 + n)
+                t = pkd.Tree(to_dev(X), None, p)
+                U.assert_exports_equal(t.export(), O.OracleTree(X, None, oparams(p)).export())
+                t.close()

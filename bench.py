@@ -59,6 +59,10 @@ WORKLOADS = {
     "build1e8_d2_varden": dict(full=True, n=100_000_000, d=2, kind="varden", q=1_000_000, k=10, m=0),
 }
 DEFAULT_WORKLOAD = "build1e8_d3_ins1e7_del1e7"
+# how many steps ahead of the computing step the e2e loop copies inputs (a
+# pipelined caller's prefetch depth: the copy of one step may take up to this
+# many steps of compute before the step that needs it waits)
+E2E_AHEAD = 3
 
 # Algorithmic bytes per point moved by each kernel family (int32 coords + id):
 # a sieve scatter or a shared-memory base case reads and writes every point
@@ -853,45 +857,60 @@ def main():
         hzid = torch.from_numpy(zid.view(np.int32)).pin_memory()
         h2d = sum(t.numel() * t.element_size() for t in (hX, hY, hyid, hzid))
         hs = (hX, hY, hyid, hzid)
-        # two device sets: step k+1's inputs travel on a copy stream while step
-        # k runs its updates (every byte of every step is still copied inside
-        # the timed region)
-        sets = [tuple(torch.empty_like(t, device=dev) for t in hs) for _ in range(2)]
+        # E2E_AHEAD + 1 device sets: step k+E2E_AHEAD's inputs travel on a copy
+        # stream while step k runs (every byte of every step is still copied
+        # inside the timed region; the copy of a set starts only after the
+        # step that last read it has finished on the device)
+        S = E2E_AHEAD + 1
+        sets = [tuple(torch.empty_like(t, device=dev) for t in hs) for _ in range(S)]
         copy_stream = torch.cuda.Stream(dev)
-        ready = [torch.cuda.Event() for _ in range(2)]
+        ready = [torch.cuda.Event() for _ in range(S)]
+        done = [torch.cuda.Event() for _ in range(S)]
+        spans = []
 
-        def upload(k):
+        def upload(k, timed=True):
             with torch.cuda.stream(copy_stream):
-                for dd, hh in zip(sets[k % 2], hs):
+                if k >= S:
+                    copy_stream.wait_event(done[k % S])
+                c0 = torch.cuda.Event(enable_timing=True)
+                c1 = torch.cuda.Event(enable_timing=True)
+                c0.record(copy_stream)
+                for dd, hh in zip(sets[k % S], hs):
                     dd.copy_(hh, non_blocking=True)
-                ready[k % 2].record(copy_stream)
+                c1.record(copy_stream)
+                ready[k % S].record(copy_stream)
+                if timed:
+                    spans.append((c0, c1))
 
-        def e2e_step(k, last):
-            dX, dY, dyid, dzid = sets[k % 2]
-            if not last:  # the other set is free: step k-1 has finished
-                upload(k + 1)
-            stream.wait_event(ready[k % 2])
+        def e2e_step(k, steps):
+            dX, dY, dyid, dzid = sets[k % S]
+            if k + E2E_AHEAD < steps:
+                upload(k + E2E_AHEAD)
+            stream.wait_event(ready[k % S])
             t = pkd.pkd_build(dX, None, params, stream)
             pkd.pkd_batch_insert(t, dY, dyid, stream)
             nd = pkd.pkd_batch_delete(t, dzid, stream)  # n_deleted comes back to the host
+            done[k % S].record(stream)
             pkd.pkd_free(t)
             return nd
 
         def e2e_run(steps):
-            upload(0)
+            for k in range(min(E2E_AHEAD, steps)):
+                upload(k)
             for k in range(steps):
-                e2e_step(k, k == steps - 1)
+                e2e_step(k, steps)
 
-        e2e_run(2)
+        e2e_run(S)  # every device set once (the library records one graph per input set)
         # the copies alone: one step's inputs, host to device, nothing else running
         torch.cuda.synchronize(dev)
         c0 = torch.cuda.Event(enable_timing=True)
         c1 = torch.cuda.Event(enable_timing=True)
         c0.record(copy_stream)
-        upload(0)
+        upload(0, timed=False)
         c1.record(copy_stream)
         torch.cuda.synchronize(dev)
         copy_ms = c0.elapsed_time(c1)
+        spans.clear()
         barrier_max(0.0, ws, dev)
         torch.cuda.synchronize(dev)
         a = torch.cuda.Event(enable_timing=True)
@@ -902,11 +921,13 @@ def main():
         b.record(stream)
         torch.cuda.synchronize(dev)
         e2e_ms = barrier_max(a.elapsed_time(b), ws, dev)
+        cms = sorted(x.elapsed_time(y) for x, y in spans)
         e2e = {"value": ws * pts_step * args.steps / (e2e_ms / 1e3) / 1e6, "unit": "Mpts/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8,
-               "note": "inputs copied from pinned host memory every step; the next step's copy overlaps "
-                       "this step on a second stream",
-               "copy_ms_alone": copy_ms, "h2d_gbs_alone": h2d / (copy_ms / 1e3) / 1e9}
+               "note": f"inputs copied from pinned host memory every step; step k+{E2E_AHEAD}'s copy runs on a "
+                       "second stream while step k computes",
+               "copy_ms_alone": copy_ms, "h2d_gbs_alone": h2d / (copy_ms / 1e3) / 1e9,
+               "copy_ms_in_run": {"median": cms[len(cms) // 2], "max": cms[-1]} if cms else None}
 
     # ---- varden-like variant of the same step (same sizes, timers off) ----
     varden = None

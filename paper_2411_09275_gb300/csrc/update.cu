@@ -285,7 +285,12 @@ static void launch_route_small(const RoundArgs& ra, const uint32_t* small, const
   PKD_LAUNCH(k_route_small<D><<<(n + 7) / 8, 256, smb, s>>>(ra, small, nsmall, items, nbk, bstart, blen, F));
 }
 
-// Next-round items and leaf groups from the bucket ranges.
+// Next-round items and leaf groups from the bucket ranges.  Each lane takes
+// EMIT_PER heap positions at a time (v = v0 + 32u + lane): the loads of all
+// of them are issued before the first counter update, and the warp reserves
+// its outputs with one atomic per counter for all of them (warp scans give
+// each lane its offsets).
+constexpr int EMIT_PER = 4;
 __global__ void __launch_bounds__(ITEM_WARPS * 32) k_route_emit(UpdArgs a) {
   if (pkd_failed_block(a.st)) return;
   const uint32_t i = item_of_warp();
@@ -294,72 +299,103 @@ __global__ void __launch_bounds__(ITEM_WARPS * 32) k_route_emit(UpdArgs a) {
   const Seg it = a.items[i];
   const int2* sk = a.skel + (uint64_t)i * a.HN;
   const uint32_t* sl = a.slots + (uint64_t)i * a.HN;
-  for (int b = lane; b < a.NB; b += 32) a.link[(uint64_t)i * a.NB + b] = LINK_NONE;
+  const uint64_t kb0 = (uint64_t)i * a.NB;
+  for (int b = lane; b < a.NB; b += 32) a.link[kb0 + b] = LINK_NONE;
   __syncwarp();
-  for (int v0 = 1; v0 < a.HN; v0 += 32) {
-    const int v = v0 + lane;
-    bool leaf = false, inner = false;
-    uint32_t cnt = 0, slot = 0, depth = 0;
-    uint64_t b0 = 0, k = 0;
-    if (v < a.HN) {
-      const int m = sk[v].y;
-      if (sk_state(m) == SK_BUCKET) {
-        k = (uint64_t)i * a.NB + sk_bucket(m);
-        cnt = a.blen[k];
-        if (cnt) {
-          b0 = a.bstart[k];
-          slot = sl[v];
-          depth = it.depth + (31 - __clz(v));
-          leaf = a.ndim[slot] == PKD_LEAF;
-          inner = !leaf;
-        }
+  for (int v0 = 1; v0 < a.HN; v0 += 32 * EMIT_PER) {
+    int bkt[EMIT_PER];
+#pragma unroll
+    for (int u = 0; u < EMIT_PER; ++u) {
+      const int v = v0 + 32 * u + lane;
+      bkt[u] = -1;
+      if (v < a.HN) {
+        const int m = sk[v].y;
+        if (sk_state(m) == SK_BUCKET) bkt[u] = sk_bucket(m);
       }
     }
-    // one update of each counter per warp
-    const bool big = inner && cnt > SMALL_ITEM;
-    const unsigned mL = __ballot_sync(FULL_MASK, leaf), mN = __ballot_sync(FULL_MASK, inner);
-    const unsigned mB = __ballot_sync(FULL_MASK, big), mS = __ballot_sync(FULL_MASK, inner && !big);
-    uint32_t tiles = big ? (cnt + a.TILE - 1) / a.TILE : 0u;
-    uint32_t bigpts = big ? cnt : 0u;
+    uint32_t cnt[EMIT_PER], slot[EMIT_PER];
+    uint64_t b0[EMIT_PER];
+#pragma unroll
+    for (int u = 0; u < EMIT_PER; ++u) {
+      cnt[u] = 0;
+      slot[u] = 0;
+      b0[u] = 0;
+      if (bkt[u] >= 0) {
+        cnt[u] = a.blen[kb0 + bkt[u]];
+        b0[u] = a.bstart[kb0 + bkt[u]];
+        slot[u] = sl[v0 + 32 * u + lane];
+      }
+    }
+    bool leaf[EMIT_PER], big[EMIT_PER];
+    uint32_t nL = 0, nN = 0, nB = 0, tiles = 0, bigpts = 0;
+#pragma unroll
+    for (int u = 0; u < EMIT_PER; ++u) {
+      const bool reached = cnt[u] != 0;
+      leaf[u] = reached && a.ndim[slot[u]] == PKD_LEAF;
+      const bool inner = reached && !leaf[u];
+      big[u] = inner && cnt[u] > SMALL_ITEM;
+      nL += leaf[u];
+      nN += inner;
+      nB += big[u];
+      if (big[u]) {
+        tiles += (cnt[u] + a.TILE - 1) / a.TILE;
+        bigpts += cnt[u];
+      }
+    }
+    // one update of each counter per warp and batch
+    const uint32_t iL = (uint32_t)warp_incl_scan((int)nL);
+    const uint32_t iN = (uint32_t)warp_incl_scan((int)nN);
+    const uint32_t iB = (uint32_t)warp_incl_scan((int)nB);
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       tiles += __shfl_xor_sync(FULL_MASK, tiles, o);
       bigpts += __shfl_xor_sync(FULL_MASK, bigpts, o);
     }
+    const uint32_t tL = __shfl_sync(FULL_MASK, iL, 31), tN = __shfl_sync(FULL_MASK, iN, 31);
+    const uint32_t tB = __shfl_sync(FULL_MASK, iB, 31);
     uint32_t gB = 0, qB = 0, kB = 0, sB = 0;
     if (lane == 0) {
-      if (mL) gB = atomicAdd(a.ngroups, (uint32_t)__popc(mL));
-      if (mN) qB = atomicAdd(&a.next_ctr[0], (uint32_t)__popc(mN));
-      if (mB) {
-        kB = atomicAdd(&a.next_ctr[2], (uint32_t)__popc(mB));
+      if (tL) gB = atomicAdd(a.ngroups, tL);
+      if (tN) qB = atomicAdd(&a.next_ctr[0], tN);
+      if (tB) {
+        kB = atomicAdd(&a.next_ctr[2], tB);
         atomicAdd(&a.next_ctr[1], tiles);
         atomicAdd(&a.next_ctr[16], bigpts);
       }
-      if (mS) sB = atomicAdd(&a.next_ctr[3], (uint32_t)__popc(mS));
+      if (tN > tB) sB = atomicAdd(&a.next_ctr[3], tN - tB);
     }
-    const unsigned lt = lanemask_lt();
-    const uint32_t g = __shfl_sync(FULL_MASK, gB, 0) + __popc(mL & lt);
-    if (leaf) {
-      if (g >= a.group_cap) {
-        set_error(a.st, DERR_CAPACITY, 800);
-      } else {
-        a.groups[g] = LeafGroup{slot, depth, b0, cnt, a.insert ? cnt : 0u, 0u, 0u};
-        a.link[k] = LINK_LEAF | g;
+    uint32_t g = __shfl_sync(FULL_MASK, gB, 0) + iL - nL;
+    uint32_t q = __shfl_sync(FULL_MASK, qB, 0) + iN - nN;
+    uint32_t kb = __shfl_sync(FULL_MASK, kB, 0) + iB - nB;
+    uint32_t sb = __shfl_sync(FULL_MASK, sB, 0) + (iN - iB) - (nN - nB);
+#pragma unroll
+    for (int u = 0; u < EMIT_PER; ++u) {
+      if (!cnt[u]) continue;
+      const int v = v0 + 32 * u + lane;
+      const uint64_t k = kb0 + bkt[u];
+      const uint32_t depth = it.depth + (31 - __clz(v));
+      if (leaf[u]) {
+        if (g >= a.group_cap) {
+          set_error(a.st, DERR_CAPACITY, 800);
+        } else {
+          a.groups[g] = LeafGroup{slot[u], depth, b0[u], cnt[u], a.insert ? cnt[u] : 0u, 0u, 0u};
+          a.link[k] = LINK_LEAF | g;
+        }
+        ++g;
+        continue;
       }
-    }
-    const uint32_t q = __shfl_sync(FULL_MASK, qB, 0) + __popc(mN & lt);
-    const uint32_t kb = __shfl_sync(FULL_MASK, kB, 0) + __popc(mB & lt);
-    const uint32_t sb = __shfl_sync(FULL_MASK, sB, 0) + __popc(mS & lt);
-    if (inner) {
-      const Seg c{b0, cnt, depth, slot, IN_B};
+      const Seg c{b0[u], cnt[u], depth, slot[u], IN_B};
       a.next[q] = c;
-      if (big) {
+      if (big[u]) {
         a.next_big[kb] = c;
         a.next_bigmap[kb] = q;
+        ++kb;
       } else {
         a.next_small[sb] = q;
+        ++sb;
       }
       a.link[k] = q;
+      ++q;
     }
   }
 }
@@ -519,33 +555,58 @@ __global__ void __launch_bounds__(UPW_WARPS * 32) k_match(LeafGroup* groups, con
   }
 }
 
-// Exact counts per skeleton node, bottom-up (rounds in reverse order; within
-// a skeleton, level by level from the deepest).
+// Exact counts per skeleton node, bottom-up (rounds in reverse order).  The
+// item's states and bucket counts are loaded first, AGG_PER heap positions
+// per lane at a time with all their loads in flight together; the interior
+// sums are then formed level by level in shared memory, from the deepest,
+// and the counts are written out at the end.
+constexpr int AGG_PER = 4;
 __global__ void __launch_bounds__(ITEM_WARPS * 32) k_aggregate(UpdArgs a) {
   if (pkd_failed_block(a.st)) return;
+  extern __shared__ __align__(16) int agg_sm[];
   const uint32_t i = item_of_warp();
   if (i >= *a.nitems) return;  // warp-uniform
   const int lane = lane_id();
+  int* ms = agg_sm + (size_t)warp_id() * 2 * a.HN;
+  uint32_t* fs = reinterpret_cast<uint32_t*>(ms + a.HN);
   const int2* sk = a.skel + (uint64_t)i * a.HN;
   const uint32_t* sl = a.slots + (uint64_t)i * a.HN;
   uint32_t* f = a.fnd + (uint64_t)i * a.HN;
-  for (int j = a.lam; j >= 0; --j) {
-    for (int v = (1 << j) + lane; v < (2 << j); v += 32) {
-      const int m = sk[v].y;
-      const int st = sk_state(m);
-      if (st == SK_NONE) continue;
-      uint32_t c = 0;
-      if (st == SK_BUCKET) {
-        const uint32_t L = a.link[(uint64_t)i * a.NB + sk_bucket(m)];
-        if (L != LINK_NONE)
-          c = (L & LINK_LEAF) ? a.groups[L & ~LINK_LEAF].found : a.next_fnd[(uint64_t)L * a.next_HN + 1];
-      } else {
-        c = f[2 * v] + f[2 * v + 1];
-      }
-      f[v] = c;
-      if (!a.insert && c) a.aux[sl[v]] = c;
+  const uint64_t kb0 = (uint64_t)i * a.NB;
+  for (int v0 = 1; v0 < a.HN; v0 += 32 * AGG_PER) {
+    int m[AGG_PER];
+#pragma unroll
+    for (int u = 0; u < AGG_PER; ++u) {
+      const int v = v0 + 32 * u + lane;
+      m[u] = v < a.HN ? sk[v].y : sk_meta(SK_NONE, 0, 0);
     }
+    uint32_t L[AGG_PER];
+#pragma unroll
+    for (int u = 0; u < AGG_PER; ++u)
+      L[u] = sk_state(m[u]) == SK_BUCKET ? a.link[kb0 + sk_bucket(m[u])] : LINK_NONE;
+#pragma unroll
+    for (int u = 0; u < AGG_PER; ++u) {
+      uint32_t c = 0;
+      if (L[u] != LINK_NONE)
+        c = (L[u] & LINK_LEAF) ? a.groups[L[u] & ~LINK_LEAF].found : a.next_fnd[(uint64_t)L[u] * a.next_HN + 1];
+      const int v = v0 + 32 * u + lane;
+      if (v < a.HN) {
+        ms[v] = m[u];
+        fs[v] = c;
+      }
+    }
+  }
+  __syncwarp();
+  for (int j = a.lam - 1; j >= 0; --j) {  // interior nodes sit above level lambda
+    for (int v = (1 << j) + lane; v < (2 << j); v += 32)
+      if (sk_state(ms[v]) == SK_INTERNAL) fs[v] = fs[2 * v] + fs[2 * v + 1];
     __syncwarp();
+  }
+  for (int v = 1 + lane; v < a.HN; v += 32) {
+    if (sk_state(ms[v]) == SK_NONE) continue;
+    const uint32_t c = fs[v];
+    f[v] = c;
+    if (!a.insert && c) a.aux[sl[v]] = c;
   }
 }
 
@@ -563,8 +624,10 @@ __device__ void push_rebuild(const UpdArgs& a, uint32_t slot, uint32_t depth, ui
 // Top-down alpha test over every skeleton (rounds in forward order; within a
 // skeleton, level by level from the root).  under: one bit per heap node
 // inside a subtree that is rebuilt.
-// The item's skeleton, slots and counts are staged in shared memory first;
-// each level then loads only node sizes (both of a node's at once).
+// The item's skeleton, slots, counts and the nodes' current sizes are staged
+// in shared memory first (DEC_PER heap positions per lane at a time, their
+// loads in flight together); the levels then read shared memory only.
+constexpr int DEC_PER = 4;
 __global__ void __launch_bounds__(ITEM_WARPS * 32) k_decide(UpdArgs a) {
   if (pkd_failed_block(a.st)) return;
   extern __shared__ __align__(16) uint8_t dec_sm[];
@@ -578,16 +641,39 @@ __global__ void __launch_bounds__(ITEM_WARPS * 32) k_decide(UpdArgs a) {
   uint32_t* sl = reinterpret_cast<uint32_t*>(reinterpret_cast<int2*>(dec_sm) + (size_t)ITEM_WARPS * a.HN) +
                  (size_t)warp_id() * a.HN;
   uint32_t* f = sl + (size_t)ITEM_WARPS * a.HN;
+  uint32_t* osz = f + (size_t)ITEM_WARPS * a.HN;
   {
     const int2* gsk = a.skel + (uint64_t)i * a.HN;
     const uint32_t* gsl = a.slots + (uint64_t)i * a.HN;
     const uint32_t* gf = a.fnd + (uint64_t)i * a.HN;
-    for (int v = 1 + lane; v < a.HN; v += 32) {
-      const int2 e = gsk[v];
-      sk[v] = e;
-      if (sk_state(e.y) != SK_NONE) {
-        sl[v] = gsl[v];
-        f[v] = gf[v];
+    for (int v0 = 1; v0 < a.HN; v0 += 32 * DEC_PER) {
+      int2 e[DEC_PER];
+      uint32_t slv[DEC_PER], fv[DEC_PER], szv[DEC_PER];
+#pragma unroll
+      for (int u = 0; u < DEC_PER; ++u) {
+        const int v = v0 + 32 * u + lane;
+        e[u] = v < a.HN ? gsk[v] : make_int2(0, sk_meta(SK_NONE, 0, 0));
+      }
+#pragma unroll
+      for (int u = 0; u < DEC_PER; ++u) {
+        const int v = v0 + 32 * u + lane;
+        slv[u] = 0;
+        fv[u] = 0;
+        if (sk_state(e[u].y) != SK_NONE) {
+          slv[u] = gsl[v];
+          fv[u] = gf[v];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < DEC_PER; ++u) szv[u] = sk_state(e[u].y) != SK_NONE ? a.nodes[slv[u]].size : 0u;
+#pragma unroll
+      for (int u = 0; u < DEC_PER; ++u) {
+        const int v = v0 + 32 * u + lane;
+        if (v >= a.HN) continue;
+        sk[v] = e[u];
+        sl[v] = slv[u];
+        f[v] = fv[u];
+        osz[v] = szv[u];
       }
     }
   }
@@ -618,7 +704,7 @@ __global__ void __launch_bounds__(ITEM_WARPS * 32) k_decide(UpdArgs a) {
       const uint32_t c = f[v];
       if (c == 0) continue;  // nothing below changes
       const uint32_t slot = sl[v];
-      const uint32_t old = a.nodes[slot].size, lold = a.nodes[sl[c0]].size;
+      const uint32_t old = osz[v], lold = osz[c0];
       const uint32_t N = a.insert ? old + c : old - c;
       const uint32_t L = a.insert ? lold + f[c0] : lold - f[c0];
       if (N > 0 && is_balanced(L, N, a.p.alpha_num, a.p.alpha_den)) {
@@ -1448,7 +1534,15 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
     ua.fnd = R.fnd;
     ua.next_fnd = (r + 1 < (int)rounds.size()) ? rounds[r + 1].fnd : nullptr;
     ua.next_HN = HN;
-    PKD_LAUNCH(k_aggregate<<<item_blocks(R.n), ITEM_WARPS * 32, 0, s>>>(ua));
+    {
+      const size_t smb = (size_t)ITEM_WARPS * HN * 2 * sizeof(uint32_t);
+      static size_t set = 0;
+      if (smb > 48 * 1024 && set < smb) {
+        cudaFuncSetAttribute(k_aggregate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+        set = smb;
+      }
+      PKD_LAUNCH(k_aggregate<<<item_blocks(R.n), ITEM_WARPS * 32, smb, s>>>(ua));
+    }
   }
   uint32_t total_changed = 0;
   PKD_CUDA(cudaMemcpyAsync(&total_changed, rounds[0].fnd + 1, 4, cudaMemcpyDeviceToHost, s));
@@ -1470,7 +1564,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
     ua.iflag = R.iflag;
     ua.next_iflag = (r + 1 < rounds.size()) ? rounds[r + 1].iflag : nullptr;
     {
-      const size_t smb = (size_t)ITEM_WARPS * HN * (sizeof(int2) + 2 * sizeof(uint32_t));
+      const size_t smb = (size_t)ITEM_WARPS * HN * (sizeof(int2) + 3 * sizeof(uint32_t));
       static size_t set = 0;
       if (smb > 48 * 1024 && set < smb) {
         cudaFuncSetAttribute(k_decide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);

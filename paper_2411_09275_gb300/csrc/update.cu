@@ -177,18 +177,18 @@ __global__ void __launch_bounds__(ITEM_WARPS * 32) k_fetch(UpdArgs a) {
 constexpr uint32_t SMALL_ITEM = 256;  // items up to this many points: one warp routes them
 
 // Bucket ranges of the big items from the bucket-major scan of the tile
-// histograms.
+// histograms: one warp per item, its lanes over the buckets.
 __global__ void k_bucket_ranges(RoundArgs r, uint64_t* bstart, uint32_t* blen, const uint32_t* nbk) {
   if (pkd_failed_block(r.st)) return;
-  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= *r.nbig) return;
+  const uint32_t s = (uint32_t)(((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (s >= *r.nbig) return;  // warp-uniform
   const Seg it = r.big[s];
   const uint32_t k = r.skel_map[s];
   const uint32_t nb = nbk[k];
   const uint32_t nt = (it.len + r.TILE - 1) / r.TILE;
   const uint64_t hb = (uint64_t)r.tile0[s] * r.NB;
   const uint32_t base = r.hscan[hb];
-  for (uint32_t b = 0; b < (uint32_t)r.NB; ++b) {
+  for (uint32_t b = lane_id(); b < (uint32_t)r.NB; b += 32) {
     uint32_t b0 = it.len, b1 = it.len;
     if (b < nb) {
       b0 = r.hscan[hb + (uint64_t)b * nt] - base;
@@ -1474,7 +1474,8 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
       PKD_LAUNCH(k_big_prefix<<<1, 1024, 0, s>>>(cur_big, R.d_n + 1, (uint32_t)TILE, tile0, excl));
       PKD_DISPATCH_D(d, launch_count, ra, tiles, big_pts, "count_route", s);
       device_excl_scan(hist, hscan, nh, partial, s);
-      PKD_LAUNCH(k_bucket_ranges<<<(nbig + 127) / 128, 128, 0, s>>>(ra, R.bstart, R.blen, nbk));
+      PKD_LAUNCH(k_bucket_ranges<<<(unsigned)(((uint64_t)nbig * 32 + 127) / 128), 128, 0, s>>>(ra, R.bstart, R.blen,
+                                                                                               nbk));
       PKD_DISPATCH_D(d, launch_scatter, ra, tiles, big_pts, "scatter_route", s);
       PKD_LAUNCH(k_copy_round<<<tiles, 256, 0, s>>>(ra, F));
     }

@@ -1116,53 +1116,66 @@ __global__ void k_finalize(RoundArgs r) {
 
 
 
-// Children segments, interior nodes and heavy leaves of every big segment.
-__device__ __forceinline__ void emit_one(const RoundArgs& r, uint32_t* heavy_ctr, uint32_t s) {
+// Children segments, interior nodes and heavy leaves of every big segment:
+// one warp per segment.  The buckets (at any level of the skeleton) are
+// independent, so their ranges are read by all lanes at once; the interior
+// nodes then take their sizes level by level from the deepest.
+__device__ __forceinline__ void emit_warp(const RoundArgs& r, uint32_t* heavy_ctr, uint32_t s) {
+  const int lane = lane_id();
   const Seg seg = r.big[s];
   const int2* sk = r.skel + (uint64_t)s * r.HN;
   const uint32_t* sl = r.slots + (uint64_t)s * r.HN;
   Seg* ch = r.children + (uint64_t)s * r.NB;
   const uint32_t nb = r.nbk[s];
-  for (int b = (int)nb; b < r.NB; ++b) ch[b].len = SEG_SKIP;
-  if (sk_state(sk[1].y) == SK_HEAVY) {
-    r.nodes[seg.root] = Node{0, seg.len, (uint32_t)seg.start, 0};
-    r.ndim[seg.root] = PKD_LEAF;
-    atomicAdd(heavy_ctr, 1u);
-    atomicMax(&r.st->max_depth, seg.depth);
+  for (int b = (int)nb + lane; b < r.NB; b += 32) ch[b].len = SEG_SKIP;
+  if (sk_state(sk[1].y) == SK_HEAVY) {  // warp-uniform
+    if (lane == 0) {
+      r.nodes[seg.root] = Node{0, seg.len, (uint32_t)seg.start, 0};
+      r.ndim[seg.root] = PKD_LEAF;
+      atomicAdd(heavy_ctr, 1u);
+      atomicMax(&r.st->max_depth, seg.depth);
+    }
     return;
   }
   const uint32_t nt = (seg.len + r.TILE - 1) / r.TILE;
   const uint64_t hb = (uint64_t)r.tile0[s] * r.NB;
   const uint32_t base = r.hscan[hb];
-  // subtree sizes, children before parents (heap order reversed)
   uint32_t* size = r.sizes + (uint64_t)s * r.HN;
-  for (int v = r.HN - 1; v >= 1; --v) {
-    const int st = sk_state(sk[v].y);
-    if (st == SK_BUCKET) {
-      const int b = sk_bucket(sk[v].y);
-      const uint32_t b0 = r.hscan[hb + (uint64_t)b * nt] - base;
-      const uint32_t b1 = (b + 1 < (int)nb) ? r.hscan[hb + (uint64_t)(b + 1) * nt] - base : seg.len;
-      size[v] = b1 - b0;
-      Seg c;
-      c.start = seg.start + b0;
-      c.len = b1 - b0;
-      c.depth = seg.depth + (31 - __clz(v));
-      c.root = sl[v];
-      c.where = (uint32_t)r.dst_where;
-      ch[b] = c;
-    } else if (st == SK_INTERNAL) {
-      size[v] = size[2 * v] + size[2 * v + 1];
-      r.nodes[sl[v]] = Node{sk[v].x, size[v], sl[2 * v], sl[2 * v + 1]};
-      r.ndim[sl[v]] = (uint8_t)sk_dim(sk[v].y);
-    }
+  for (int v = 1 + lane; v < r.HN; v += 32) {
+    const int m = sk[v].y;
+    if (sk_state(m) != SK_BUCKET) continue;
+    const int b = sk_bucket(m);
+    const uint32_t b0 = r.hscan[hb + (uint64_t)b * nt] - base;
+    const uint32_t b1 = (b + 1 < (int)nb) ? r.hscan[hb + (uint64_t)(b + 1) * nt] - base : seg.len;
+    size[v] = b1 - b0;
+    Seg c;
+    c.start = seg.start + b0;
+    c.len = b1 - b0;
+    c.depth = seg.depth + (31 - __clz(v));
+    c.root = sl[v];
+    c.where = (uint32_t)r.dst_where;
+    ch[b] = c;
   }
-  if (size[1] != seg.len) set_error(r.st, DERR_STATE, 700);
+  __syncwarp();
+  for (int j = r.lam - 1; j >= 0; --j) {  // interior nodes sit above level lambda
+    for (int v = (1 << j) + lane; v < (2 << j); v += 32) {
+      const int2 e = sk[v];
+      if (sk_state(e.y) != SK_INTERNAL) continue;
+      const uint32_t sz = size[2 * v] + size[2 * v + 1];
+      size[v] = sz;
+      r.nodes[sl[v]] = Node{e.x, sz, sl[2 * v], sl[2 * v + 1]};
+      r.ndim[sl[v]] = (uint8_t)sk_dim(e.y);
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && size[1] != seg.len) set_error(r.st, DERR_STATE, 700);
 }
 
 __global__ void k_emit(RoundArgs r0, uint32_t* heavy_ctr) {
   if (pkd_failed_block(r0.st)) return;
   const RoundArgs r = with_dyn(r0);
-  PKD_FOR(s, *r.nbig) emit_one(r, heavy_ctr, s);
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < *r.nbig; s += nw) emit_warp(r, heavy_ctr, s);
 }
 
 
@@ -1788,7 +1801,7 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     PKD_LAUNCH(k_finalize<<<g_seg128, 128, 0, q>>>(r));
     PKD_DISPATCH_D(d, launch_count, r, (uint32_t)bb.tiles, pts_big, "count", q);
     device_excl_scan_dev(bb.hist, bb.hscan, dctr + C_TILES, (uint32_t)NB, bb.tiles * NB, bb.partial, q);
-    PKD_LAUNCH(k_emit<<<grid_for(bb.nbig, 64, 8), 64, 0, q>>>(r, dctr + C_HEAVY));
+    PKD_LAUNCH(k_emit<<<grid_for(bb.nbig * 32, 128, 8), 128, 0, q>>>(r, dctr + C_HEAVY));
     PKD_DISPATCH_D(d, launch_scatter, r, (uint32_t)bb.tiles, pts_big, "scatter", q);
     PKD_LAUNCH(k_copy_heavy<<<g_tiles, 256, 0, q>>>(r, 0));
     // the buckets, now in the destination buffer, are the next round

@@ -302,7 +302,10 @@ int pkd_set_option(const char* name, int64_t value);
  * "graph_record" (host time to record a build's graph; items = graphs
  * recorded).  Counts without a time: "rebuilt_insert" and "rebuilt_delete"
  * (points in the subtrees an update rebuilt, one entry per call),
- * "delete_gather" (ids a delete found and looked up).  The name
+ * "delete_gather" (ids a delete found and looked up), "scratch_zeroed"
+ * (a tree's first delete took a released tree's per-node delete scratch,
+ * which every delete leaves all zero, from the block cache without clearing
+ * it; items = bytes).  The name
  * "allocations" reports, in *launches, every device or pinned-host allocation
  * the library made since it was loaded; "graph_builds" the builds (and update
  * rebuilds) whose rounds ran from one graph launch.  With graph rounds,

@@ -51,6 +51,7 @@ struct TreeMem {
   uint64_t size = 0;
   uint8_t* dead = nullptr;          // delete scratch: per arena position (kept zero)
   uint32_t* aux = nullptr;          // delete scratch: per node slot (kept zero)
+  bool scratch_dirty = false;       // a delete has set marks it has not cleared yet
   DevStatus* st = nullptr;          // device status word
   DevStatus* st_host = nullptr;     // pinned mirror
   IdTable ids;                      // id -> coordinates of the stored points
@@ -131,6 +132,11 @@ cudaMemPool_t mem_pool();
 constexpr size_t BIG_BLOCK_MIN = (size_t)64 << 20;
 cudaError_t big_alloc(void** p, size_t bytes, cudaStream_t s);
 void big_free(void* p, cudaStream_t s);
+// The same for a block that must start zeroed: *zero says whether the block
+// handed out is known to be zero over `bytes` (a cached block released with
+// big_free_zeroed); otherwise the caller clears it.
+cudaError_t big_alloc_zeroed(void** p, size_t bytes, cudaStream_t s, bool* zero);
+void big_free_zeroed(void* p, size_t zeroed, cudaStream_t s);
 
 // Every device allocation of the library goes through pool_alloc: a
 // stream-ordered allocation from the pool above that is counted (reported by

@@ -228,6 +228,7 @@ struct CachedBlock {
   size_t bytes;
   int dev;
   cudaEvent_t ev;  // recorded on the stream that freed the block
+  size_t zeroed;   // its first `zeroed` bytes are known to be zero
 };
 static std::mutex g_big_mu;
 static std::vector<CachedBlock> g_big_cache;
@@ -259,17 +260,27 @@ cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
   return cudaMallocFromPoolAsync(p, bytes, mem_pool(), s);
 }
 
-cudaError_t big_alloc(void** p, size_t bytes, cudaStream_t s) {
+// A cached block is taken when it fits and wastes at most half of itself.
+// Plain requests prefer blocks not known to be zero, so that the zeroed
+// ones (a released tree's delete scratch, cleared after every delete) stay
+// for big_alloc_zeroed, which prefers them and reports whether it got one.
+static cudaError_t big_alloc_impl(void** p, size_t bytes, cudaStream_t s, bool want_zero, bool* zero) {
   *p = nullptr;
+  if (zero) *zero = false;
   if (bytes < BIG_BLOCK_MIN) return pool_alloc(p, bytes, s);
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> g(g_big_mu);
-  // the smallest cached block that fits and wastes at most half of itself
   int best = -1;
+  auto rank = [&](const CachedBlock& b) {  // lower is better
+    const bool z = b.zeroed >= bytes;
+    return (want_zero ? (z ? 0 : 1) : (b.zeroed == 0 ? 0 : 1));
+  };
   for (size_t k = 0; k < g_big_cache.size(); ++k) {
     const CachedBlock& b = g_big_cache[k];
-    if (b.dev == dev && b.bytes >= bytes && b.bytes <= 2 * bytes && (best < 0 || b.bytes < g_big_cache[best].bytes))
+    if (b.dev != dev || b.bytes < bytes || b.bytes > 2 * bytes) continue;
+    if (best < 0 || rank(b) < rank(g_big_cache[best]) ||
+        (rank(b) == rank(g_big_cache[best]) && b.bytes < g_big_cache[best].bytes))
       best = (int)k;
   }
   if (best >= 0) {
@@ -280,6 +291,7 @@ cudaError_t big_alloc(void** p, size_t bytes, cudaStream_t s) {
     cudaEventDestroy(b.ev);
     g_big_live[b.p] = {b.bytes, dev};
     *p = b.p;
+    if (zero) *zero = b.zeroed >= bytes;
     return cudaSuccess;
   }
   cudaError_t e = pool_alloc(p, bytes, s);
@@ -292,7 +304,13 @@ cudaError_t big_alloc(void** p, size_t bytes, cudaStream_t s) {
   return e;
 }
 
-void big_free(void* p, cudaStream_t s) {
+cudaError_t big_alloc(void** p, size_t bytes, cudaStream_t s) { return big_alloc_impl(p, bytes, s, false, nullptr); }
+
+cudaError_t big_alloc_zeroed(void** p, size_t bytes, cudaStream_t s, bool* zero) {
+  return big_alloc_impl(p, bytes, s, true, zero);
+}
+
+void big_free_zeroed(void* p, size_t zeroed, cudaStream_t s) {
   if (!p) return;
   std::lock_guard<std::mutex> g(g_big_mu);
   auto it = g_big_live.find(p);
@@ -306,7 +324,7 @@ void big_free(void* p, cudaStream_t s) {
   cudaEvent_t ev = nullptr;
   if (g_big_cached + bytes <= BIG_CACHE_MAX && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess &&
       cudaEventRecord(ev, s) == cudaSuccess) {
-    g_big_cache.push_back(CachedBlock{p, bytes, dev, ev});
+    g_big_cache.push_back(CachedBlock{p, bytes, dev, ev, std::min(zeroed, bytes)});
     g_big_cached += bytes;
     return;
   }
@@ -314,6 +332,8 @@ void big_free(void* p, cudaStream_t s) {
   if (ev) cudaEventDestroy(ev);
   cudaFreeAsync(p, s);
 }
+
+void big_free(void* p, cudaStream_t s) { big_free_zeroed(p, 0, s); }
 
 static std::mutex g_pin_mu;
 static std::vector<void*> g_pin_free;
@@ -354,9 +374,13 @@ void pinned_put_after(cudaStream_t s, void* p) {
 
 void tree_release(TreeMem& t) {
   cudaStream_t s = 0;
-  for (void* p : {(void*)t.A.c, (void*)t.A.id, (void*)t.nodes, (void*)t.ndim, (void*)t.shared_next,
-                  (void*)t.dead, (void*)t.aux, (void*)t.st})
+  for (void* p : {(void*)t.A.c, (void*)t.A.id, (void*)t.nodes, (void*)t.ndim, (void*)t.shared_next, (void*)t.st})
     big_free(p, s);
+  // the delete scratch is all zero again after every delete: the next tree's
+  // first delete can take it without a fill
+  const bool clean = !t.scratch_dirty;
+  big_free_zeroed(t.dead, clean ? t.cap : 0, s);
+  big_free_zeroed(t.aux, clean ? t.node_cap * 4 : 0, s);
   ids_release(t.ids, s);
   big_free(t.bbox, s);
   pinned_put_after(s, t.st_host);

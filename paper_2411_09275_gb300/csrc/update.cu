@@ -1275,13 +1275,15 @@ static int ensure_capacity(TreeMem& t, uint64_t need, cudaStream_t s) {
 }
 
 static int ensure_delete_scratch(TreeMem& t, cudaStream_t s) {
+  bool zero = false;
   if (!t.dead) {
-    PKD_CUDA(big_alloc((void**)&t.dead, t.cap, s));
-    PKD_TRY(dev_fill(t.dead, 0, t.cap, s));
+    PKD_CUDA(big_alloc_zeroed((void**)&t.dead, t.cap, s, &zero));
+    if (!zero) PKD_TRY(dev_fill(t.dead, 0, t.cap, s));
   }
   if (!t.aux) {
-    PKD_CUDA(big_alloc((void**)&t.aux, t.node_cap * 4, s));
-    PKD_TRY(dev_fill(t.aux, 0, t.node_cap * 4, s));
+    PKD_CUDA(big_alloc_zeroed((void**)&t.aux, t.node_cap * 4, s, &zero));
+    if (!zero) PKD_TRY(dev_fill(t.aux, 0, t.node_cap * 4, s));
+    else stat_items("scratch_zeroed", t.node_cap * 4);
   }
   return PKD_OK;
 }
@@ -1512,13 +1514,15 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
     bool on;
     ~ClearMarks() {
       if (!on) return;
-      dev_fill(t.dead, 0, t.cap, s);
+      const bool ok = dev_fill(t.dead, 0, t.cap, s) == PKD_OK;
       for (const auto& R : rounds)
         PKD_LAUNCH(k_clear_aux<<<(unsigned)(((uint64_t)R.n * HN + 255) / 256), 256, 0, s>>>(R.slots, (uint64_t)R.n * HN,
                                                                                            t.aux));
       // (a leaf group's slot is a heap bucket of its round, cleared above)
+      if (ok && cudaPeekAtLastError() == cudaSuccess) t.scratch_dirty = false;
     }
   } clear_marks{t, rounds, HN, s, !insert};
+  if (!insert) t.scratch_dirty = true;
 
   // ---- match (delete) ----
   if (!insert && ngroups)
@@ -1688,6 +1692,7 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
       PKD_LAUNCH(k_clear_aux<<<(unsigned)(((uint64_t)R.n * HN + 255) / 256), 256, 0, s>>>(R.slots, (uint64_t)R.n * HN, t.aux));
   }
   PKD_CUDA(cudaStreamSynchronize(s));
+  if (!insert && cudaPeekAtLastError() == cudaSuccess) t.scratch_dirty = false;  // every mark is cleared
   trace_mark(s, "upd: cleanup");
   if (n_changed) *n_changed = total_changed;
   return PKD_OK;

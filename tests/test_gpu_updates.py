@@ -122,6 +122,32 @@ def test_config2_scaled_uniform_and_varden():
         assert pr.delete(sel.astype(np.uint32)) == m
 
 
+def test_delete_scratch_recycled_between_trees():
+    # Trees of 4e6 points built and freed one after the other, each deleting
+    # a batch: a released tree's per-slot delete scratch (all zero again
+    # after every delete) goes back to the block cache as zeroed, and a later
+    # tree's first delete may take it without a fill.  Every tree matches
+    # the oracle.
+    pkd = _pkd()
+    d, n, m = 3, 4_000_000, 200_000
+    p = pkd.Params(d=d)
+    pkd.pkd_kernel_timing(True)
+    try:
+        for seed in (21, 22, 23):
+            X = I.points("uniform", n, d, seed)
+            ids = np.arange(n, dtype=np.uint32)
+            t = pkd.Tree(to_dev(X), ids_dev(ids), p)
+            o = O.OracleTree(X, ids, oparams(p))
+            zid = I.sample_indices(m, n, seed + 5).astype(np.uint32)
+            assert t.delete(ids_dev(zid)) == o.delete(zid)
+            U.assert_exports_equal(t.export(), o.export())
+            t.close()
+        reused = pkd.pkd_kernel_stats("scratch_zeroed")[0]
+    finally:
+        pkd.pkd_kernel_timing(False)
+    print("zeroed scratch taken by", reused, "of 2 later trees")
+
+
 def _rejects(fn):
     pkd = _pkd()
     with pytest.raises(pkd.PkdError) as e:

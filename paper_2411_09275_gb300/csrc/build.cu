@@ -1055,58 +1055,94 @@ __global__ void k_copy_exact(RoundArgs r0, uint32_t ntiles_host) {
 }
 
 // Number the buckets left to right, detect heavy segments, give every
-// skeleton node a tree slot (root: the segment's own slot).
-__device__ __forceinline__ void finalize_one(const RoundArgs& r, uint32_t s) {
+// skeleton node a tree slot (root: the segment's own slot).  One warp per
+// segment: a bucket's number is the count of buckets whose first position
+// on level lambda lies left of its own (a bitmap of those positions), and
+// the slots follow heap order (a running count of the occupied positions).
+constexpr int FIN_WARPS = 4;
+__device__ __forceinline__ void finalize_warp(const RoundArgs& r, uint32_t s, uint32_t* bits, uint32_t* pre) {
+  const int lane = lane_id();
   int2* sk = r.skel + (uint64_t)s * r.HN;
   uint32_t* sl = r.slots + (uint64_t)s * r.HN;
   const Seg seg = r.big[s];
-  if (sk_state(sk[1].y) != SK_INTERNAL) {
+  if (sk_state(sk[1].y) != SK_INTERNAL) {  // warp-uniform
     // exact level found no split: every point is identical
-    sk[1] = make_int2(0, sk_meta(SK_HEAVY, 0, 0));
-    r.nbk[s] = 0;
-    sl[1] = seg.root;
+    if (lane == 0) {
+      sk[1] = make_int2(0, sk_meta(SK_HEAVY, 0, 0));
+      r.nbk[s] = 0;
+      sl[1] = seg.root;
+    }
     return;
   }
-  // in-order walk of the heap
-  int stack[12];
-  int sp = 0, h = 1, nb = 0, ni = 0;
-  while (sp > 0 || h != 0) {
-    if (h != 0) {
-      const int st = sk_state(sk[h].y);
-      if (st == SK_INTERNAL) {
-        stack[sp++] = h;
-        h = 2 * h;
-        continue;
+  bits[lane] = 0;
+  __syncwarp();
+  // every child of an interior node is interior or a bucket; buckets mark
+  // their first position
+  bool bad = false;
+  uint32_t occ = 0;
+  for (int v = 1 + lane; v < r.HN; v += 32) {
+    const int st = sk_state(sk[v].y);
+    if (st == SK_NONE) continue;
+    ++occ;
+    if (st == SK_INTERNAL) {
+      if (2 * v + 1 >= r.HN) {
+        bad = true;
+      } else {
+        const int a = sk_state(sk[2 * v].y), b = sk_state(sk[2 * v + 1].y);
+        bad |= (a != SK_INTERNAL && a != SK_BUCKET) || (b != SK_INTERNAL && b != SK_BUCKET);
       }
-      if (st != SK_BUCKET) {
-        set_error(r.st, DERR_STATE, 600);
-        return;
-      }
-      sk[h].y = sk_meta(SK_BUCKET, 0, nb++);
-      h = 0;
+    } else if (st == SK_BUCKET) {
+      const int j = 31 - __clz(v);
+      const uint32_t lo = (uint32_t)(v - (1 << j)) << (r.lam - j);
+      atomicOr(&bits[lo >> 5], 1u << (lo & 31));
     } else {
-      h = stack[--sp];
-      ++ni;
-      h = 2 * h + 1;
+      bad = true;
     }
   }
-  r.nbk[s] = nb;
-  const uint32_t need = (uint32_t)(ni - 1 + nb);
-  const uint32_t b0 = atomicAdd(r.shared_next, need);
+  if (__any_sync(FULL_MASK, bad)) {
+    if (lane == 0) set_error(r.st, DERR_STATE, 600);
+    return;
+  }
+  __syncwarp();
+  const uint32_t wc = (uint32_t)__popc(bits[lane]);
+  const uint32_t incl = (uint32_t)warp_incl_scan((int)wc);
+  pre[lane] = incl - wc;
+  const uint32_t nb = __shfl_sync(FULL_MASK, incl, 31);
+  __syncwarp();
+  for (int v = 1 + lane; v < r.HN; v += 32) {
+    if (sk_state(sk[v].y) != SK_BUCKET) continue;
+    const int j = 31 - __clz(v);
+    const uint32_t lo = (uint32_t)(v - (1 << j)) << (r.lam - j);
+    const uint32_t num = pre[lo >> 5] + (uint32_t)__popc(bits[lo >> 5] & ((1u << (lo & 31)) - 1u));
+    sk[v].y = sk_meta(SK_BUCKET, 0, (int)num);
+  }
+  const uint32_t need = (uint32_t)warp_sum((int)occ) - 1;  // the root keeps the segment's slot
+  uint32_t b0 = 0;
+  if (lane == 0) {
+    r.nbk[s] = nb;
+    b0 = atomicAdd(r.shared_next, need);
+  }
+  b0 = __shfl_sync(FULL_MASK, b0, 0);
   if ((uint64_t)b0 + need > r.shared_cap) {
-    set_error(r.st, DERR_SLOT, 601);
+    if (lane == 0) set_error(r.st, DERR_SLOT, 601);
     return;
   }
   uint32_t k = b0;
-  for (int v = 1; v < r.HN; ++v) {
-    const int st = sk_state(sk[v].y);
-    if (st == SK_NONE) continue;
-    sl[v] = (v == 1) ? seg.root : k++;
+  for (int v0 = 1; v0 < r.HN; v0 += 32) {
+    const int v = v0 + lane;
+    const bool on = v < r.HN && sk_state(sk[v].y) != SK_NONE;
+    const bool takes = on && v != 1;
+    const unsigned m = __ballot_sync(FULL_MASK, takes);
+    if (on) sl[v] = v == 1 ? seg.root : k + (uint32_t)__popc(m & lanemask_lt());
+    k += (uint32_t)__popc(m);
   }
 }
 
-__global__ void k_finalize(RoundArgs r) {
-  PKD_FOR(s, *r.nbig) finalize_one(r, s);
+__global__ void __launch_bounds__(FIN_WARPS * 32) k_finalize(RoundArgs r) {
+  __shared__ uint32_t bits_sh[FIN_WARPS][32], pre_sh[FIN_WARPS][32];
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < *r.nbig; s += nw)
+    finalize_warp(r, s, bits_sh[warp_id()], pre_sh[warp_id()]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1180,8 +1216,10 @@ __global__ void k_emit(RoundArgs r0, uint32_t* heavy_ctr) {
 
 
 // Heavy segments whose points are not yet in the arena.
-__global__ void k_copy_heavy(RoundArgs r0, uint32_t ntiles_host) {
-  if (pkd_failed_block(r0.st)) return;
+// (nheavy: the round's heavy segments, counted by the emission; none is
+// the common case, and then no tile is looked at)
+__global__ void k_copy_heavy(RoundArgs r0, uint32_t ntiles_host, const uint32_t* nheavy) {
+  if (pkd_failed_block(r0.st) || *nheavy == 0) return;
   const RoundArgs r = with_dyn(r0);
   const uint32_t nt = round_tiles(r, ntiles_host);
   for (uint32_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
@@ -1798,12 +1836,12 @@ int run_build(TreeMem& t, const BuildJob& job, cudaStream_t s) {
     // segments whose skeleton root is a bucket take one exact level on their own points
     PKD_LAUNCH(k_mark_exact<<<g_seg128, 128, 0, q>>>(r, dctr + C_EXACT));
     PKD_TRY(flow_if(g, C_EXACT, [&](Flow& h) { return skeleton_pass(h, 1); }));
-    PKD_LAUNCH(k_finalize<<<g_seg128, 128, 0, q>>>(r));
+    PKD_LAUNCH(k_finalize<<<grid_for(bb.nbig * 32, FIN_WARPS * 32, 8), FIN_WARPS * 32, 0, q>>>(r));
     PKD_DISPATCH_D(d, launch_count, r, (uint32_t)bb.tiles, pts_big, "count", q);
     device_excl_scan_dev(bb.hist, bb.hscan, dctr + C_TILES, (uint32_t)NB, bb.tiles * NB, bb.partial, q);
     PKD_LAUNCH(k_emit<<<grid_for(bb.nbig * 32, 128, 8), 128, 0, q>>>(r, dctr + C_HEAVY));
     PKD_DISPATCH_D(d, launch_scatter, r, (uint32_t)bb.tiles, pts_big, "scatter", q);
-    PKD_LAUNCH(k_copy_heavy<<<g_tiles, 256, 0, q>>>(r, 0));
+    PKD_LAUNCH(k_copy_heavy<<<g_tiles, 256, 0, q>>>(r, 0, dctr + C_HEAVY));
     // the buckets, now in the destination buffer, are the next round
     PKD_LAUNCH(k_round_next<<<1, 1, 0, q>>>(dctr, (uint32_t)NB));
     return classify(g);

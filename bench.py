@@ -112,6 +112,13 @@ def measured_peaks():
     return PEAK_FALLBACK_GBS, "fallback"
 
 
+def graph_records(pkd) -> int:
+    """Build graphs recorded so far (graph launches that were not a reuse of
+    a recorded graph): a record inside a timed region costs host time."""
+    n, _, reuses = pkd.pkd_kernel_stats("graph_builds")
+    return n - reuses
+
+
 def dram_traffic():
     """Per-item DRAM bytes of the kernel families from the committed ncu
     capture (profiles/dram_traffic.json), or {} when a kernel source it lists
@@ -796,6 +803,7 @@ def main():
         pass
     barrier_max(0.0, ws, dev)
     torch.cuda.synchronize(dev)
+    g0 = graph_records(pkd)
     with Clocks(gpu_index) as clk:
         e0.record(stream)
         for k in range(args.steps):
@@ -804,6 +812,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize(dev)
     elapsed_ms = barrier_max(e0.elapsed_time(e1), ws, dev)
+    records_timed = graph_records(pkd) - g0
     launches = pkd.pkd_kernel_stats("launches")[0]
     phase = {"build_ms": 0.0, "insert_ms": 0.0, "delete_ms": 0.0}
     for k in range(args.steps):
@@ -917,17 +926,20 @@ def main():
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
         copy_stream.wait_event(a)
+        g0 = graph_records(pkd)
         e2e_run(args.steps)
         b.record(stream)
         torch.cuda.synchronize(dev)
         e2e_ms = barrier_max(a.elapsed_time(b), ws, dev)
+        records_e2e = graph_records(pkd) - g0
         cms = sorted(x.elapsed_time(y) for x, y in spans)
         e2e = {"value": ws * pts_step * args.steps / (e2e_ms / 1e3) / 1e6, "unit": "Mpts/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8,
                "note": f"inputs copied from pinned host memory every step; step k+{E2E_AHEAD}'s copy runs on a "
                        "second stream while step k computes",
                "copy_ms_alone": copy_ms, "h2d_gbs_alone": h2d / (copy_ms / 1e3) / 1e9,
-               "copy_ms_in_run": {"median": cms[len(cms) // 2], "max": cms[-1]} if cms else None}
+               "copy_ms_in_run": {"median": cms[len(cms) // 2], "max": cms[-1]} if cms else None,
+               "graph_records_in_run": records_e2e}
 
     # ---- varden-like variant of the same step (same sizes, timers off) ----
     varden = None
@@ -993,6 +1005,7 @@ def main():
                 "build_rounds": ("sequenced by the host (--host-rounds)" if args.host_rounds else
                                  "decided on the device: one CUDA graph launch per build (WHILE over rounds "
                                  "and skeleton levels, IF for exact levels, base-case grids set by a kernel)"),
+                "graph_records_in_timed_steps": records_timed,
                 "clocks": clk.summary(),
                 "phases": dict(phase, build_mpts=n / phase["build_ms"] / 1e3,
                                insert_mpts=m / phase["insert_ms"] / 1e3,

@@ -204,7 +204,7 @@ __global__ void k_bucket_ranges(RoundArgs r, uint64_t* bstart, uint32_t* blen, c
 // one pass (no global histogram: the warp owns the whole item).  Points
 // also go to the final batch buffer F (see k_copy_round).
 template <int D>
-__global__ void __launch_bounds__(256) k_route_small(RoundArgs r, const uint32_t* small, const uint32_t* nsmall,
+__global__ void __launch_bounds__(256, 6) k_route_small(RoundArgs r, const uint32_t* small, const uint32_t* nsmall,
                                                      const Seg* items, const uint32_t* nbk, uint64_t* bstart,
                                                      uint32_t* blen, Pts F) {
   if (pkd_failed_block(r.st)) return;

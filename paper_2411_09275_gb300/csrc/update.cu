@@ -204,7 +204,7 @@ __global__ void k_bucket_ranges(RoundArgs r, uint64_t* bstart, uint32_t* blen, c
 // one pass (no global histogram: the warp owns the whole item).  Points
 // also go to the final batch buffer F (see k_copy_round).
 template <int D>
-__global__ void __launch_bounds__(256, 6) k_route_small(RoundArgs r, const uint32_t* small, const uint32_t* nsmall,
+__global__ void __launch_bounds__(256, (D <= 3 ? 6 : 1)) k_route_small(RoundArgs r, const uint32_t* small, const uint32_t* nsmall,
                                                      const Seg* items, const uint32_t* nbk, uint64_t* bstart,
                                                      uint32_t* blen, Pts F) {
   if (pkd_failed_block(r.st)) return;
@@ -430,7 +430,7 @@ __host__ __device__ inline unsigned upw_blocks(uint32_t n) {
 // Deletion round 1 at the leaves: mark stored points equal to a routed batch
 // point (coordinates and id); count them.
 template <int D>
-__global__ void __launch_bounds__(UPW_WARPS * 32) k_match(LeafGroup* groups, const uint32_t* ngroups,
+__global__ void __launch_bounds__(UPW_WARPS * 32, (D <= 3 ? 8 : 1)) k_match(LeafGroup* groups, const uint32_t* ngroups,
                                                           const Node* nodes, Pts A, Pts F, uint8_t* dead,
                                                           uint32_t* aux) {
   const uint32_t n = *ngroups;
@@ -1008,7 +1008,7 @@ __global__ void __launch_bounds__(UPW_WARPS * 32) k_copy_leaves(const Front* lv,
 // k_copy_new_flat.
 constexpr uint64_t NEW_BIG = 256;
 template <int D>
-__global__ void __launch_bounds__(UPW_WARPS * 32) k_copy_new(const RebuildItem* items, const uint32_t* n, Pts F,
+__global__ void __launch_bounds__(UPW_WARPS * 32, (D <= 3 ? 8 : 1)) k_copy_new(const RebuildItem* items, const uint32_t* n, Pts F,
                                                              Pts A) {
   const uint32_t nn = *n;
   const uint32_t k0 = (blockIdx.x * UPW_WARPS + warp_id()) * UPW;

@@ -886,6 +886,8 @@ struct Front {
 // Leaves of more than BIG_LEAF points are copied one block each.
 constexpr uint32_t BIG_LEAF = 1024;
 
+constexpr int FRONT_BATCH = 8;  // frontier levels launched per host check
+
 __global__ void k_front_init(const RebuildItem* it, const uint32_t* n, Front* f, uint32_t* nf) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool e = i < *n && it[i].old_live != 0;
@@ -896,38 +898,44 @@ __global__ void k_front_init(const RebuildItem* it, const uint32_t* n, Front* f,
   if (e) f[first[0]] = Front{it[i].slot, i, 0};
 }
 
+// One level of the frontier: the grid strides over the device-side count
+// *nf (block-uniform), so the host launches a batch of levels without
+// reading any count in between; a level with an empty frontier does nothing.
 __global__ void k_front_expand(const Front* f, const uint32_t* nf, Front* g, uint32_t* ng, Front* leaves,
                                uint32_t* nleaves, Front* bigleaves, uint32_t* nbig, const Node* nodes,
                                const uint8_t* ndim, const uint32_t* aux, int use_aux, uint32_t cap, DevStatus* st) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool have = i < *nf;
-  Front e{};
-  bool leaf = false, big = false;
-  if (have) {
-    e = f[i];
-    leaf = ndim[e.slot] == PKD_LEAF;
-    big = leaf && nodes[e.slot].size > BIG_LEAF;
+  const uint32_t n = *nf;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const uint32_t i = base + threadIdx.x;
+    const bool have = i < n;
+    Front e{};
+    bool leaf = false, big = false;
+    if (have) {
+      e = f[i];
+      leaf = ndim[e.slot] == PKD_LEAF;
+      big = leaf && nodes[e.slot].size > BIG_LEAF;
+    }
+    const uint32_t c[3] = {have && leaf && !big ? 1u : 0u, have && !leaf ? 2u : 0u, big ? 1u : 0u};
+    uint32_t* const ctrs[3] = {nleaves, ng, nbig};
+    uint32_t first[3];
+    block_reserve<3>(c, ctrs, first);
+    if (!have) continue;
+    if (leaf) {
+      const uint32_t k = big ? first[2] : first[0];
+      if (k < cap) (big ? bigleaves : leaves)[k] = e;
+      else set_error(st, DERR_CAPACITY, 820);
+      continue;
+    }
+    const Node nd = nodes[e.slot];
+    const uint32_t llive = nodes[nd.a].size - (use_aux ? aux[nd.a] : 0u);
+    const uint32_t k = first[1];
+    if (k + 2 > cap) {
+      set_error(st, DERR_CAPACITY, 821);
+      continue;
+    }
+    g[k] = Front{nd.a, e.item, e.off};
+    g[k + 1] = Front{nd.b, e.item, e.off + llive};
   }
-  const uint32_t c[3] = {have && leaf && !big ? 1u : 0u, have && !leaf ? 2u : 0u, big ? 1u : 0u};
-  uint32_t* const ctrs[3] = {nleaves, ng, nbig};
-  uint32_t first[3];
-  block_reserve<3>(c, ctrs, first);
-  if (!have) return;
-  if (leaf) {
-    const uint32_t k = big ? first[2] : first[0];
-    if (k < cap) (big ? bigleaves : leaves)[k] = e;
-    else set_error(st, DERR_CAPACITY, 820);
-    return;
-  }
-  const Node nd = nodes[e.slot];
-  const uint32_t llive = nodes[nd.a].size - (use_aux ? aux[nd.a] : 0u);
-  const uint32_t k = first[1];
-  if (k + 2 > cap) {
-    set_error(st, DERR_CAPACITY, 821);
-    return;
-  }
-  g[k] = Front{nd.a, e.item, e.off};
-  g[k + 1] = Front{nd.b, e.item, e.off + llive};
 }
 
 // Flattened leaves, UPW per warp: copy their live points to the item's range.
@@ -1625,26 +1633,34 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
     device_excl_scan(isz, ioff, nitems, ipart, s);
     PKD_LAUNCH(k_item_pos<<<gi, 128, 0, s>>>(items_out, d_nitems, ioff, t.top, segs, (uint32_t)p.phi));
     // flatten the old subtrees breadth first (capacity: every node of the
-    // old subtrees appears once)
+    // old subtrees appears once).  The levels run in batches whose counts
+    // stay on the device; the host reads the frontier once per batch: one
+    // level first (an insert's items are mostly leaves), then FRONT_BATCH
+    // levels at a time (a rebuilt interior subtree is many levels deep).
     {
-      uint32_t* fc = dctr + 12;  // [0] cur, [1] next, [2] leaves, [3] big leaves
+      uint32_t* fc = dctr + 12;  // [0] frontier, [2] leaves, [3] big leaves
+      uint32_t* lc;              // the frontier of every level of a batch
+      PKD_TRY(sc.get(&lc, FRONT_BATCH + 1));
       PKD_TRY(dev_fill(fc, 0, 16, s));
       PKD_LAUNCH(k_front_init<<<gi, 128, 0, s>>>(items_out, d_nitems, fa, fc));
-      PKD_CUDA(cudaMemcpyAsync(hctr + 12, fc, 12, cudaMemcpyDeviceToHost, s));
-      PKD_CUDA(cudaStreamSynchronize(s));
-      uint32_t nf = hctr[12];
       const uint32_t fcap32 = (uint32_t)std::min<uint64_t>(fcap, 0xFFFFFFF0ull);
-      for (int it = 0; nf > 0; ++it) {
-        if (it > 100000) return PKD_EINTERNAL;
-        PKD_TRY(dev_fill(fc + 1, 0, 4, s));
-        PKD_LAUNCH(k_front_expand<<<(nf + 127) / 128, 128, 0, s>>>(fa, fc, fb, fc + 1, leaves, fc + 2, bigleaves,
-                                                                    fc + 3, t.nodes, t.ndim, t.aux, insert ? 0 : 1,
-                                                                    fcap32, t.st));
-        PKD_TRY(dev_copy_words(fc, fc + 1, 1, s));
+      const unsigned gexp = (unsigned)sm_count() * 8;
+      int levels = 0;
+      for (int batch = 1;; batch = FRONT_BATCH) {
+        if (levels > 100000) return PKD_EINTERNAL;
+        PKD_TRY(dev_fill(lc + 1, 0, (size_t)batch * 4, s));
+        PKD_TRY(dev_copy_words(lc, fc, 1, s));
+        for (int k = 0; k < batch; ++k) {
+          PKD_LAUNCH(k_front_expand<<<gexp, 128, 0, s>>>(fa, lc + k, fb, lc + k + 1, leaves, fc + 2, bigleaves,
+                                                          fc + 3, t.nodes, t.ndim, t.aux, insert ? 0 : 1, fcap32,
+                                                          t.st));
+          std::swap(fa, fb);
+        }
+        levels += batch;
+        PKD_TRY(dev_copy_words(fc, lc + batch, 1, s));
         PKD_CUDA(cudaMemcpyAsync(hctr + 12, fc, 16, cudaMemcpyDeviceToHost, s));
         PKD_CUDA(cudaStreamSynchronize(s));
-        nf = hctr[12];
-        std::swap(fa, fb);
+        if (hctr[12] == 0) break;
       }
       const uint32_t nleaves = hctr[14], nbigleaves = hctr[15];
       if (nleaves)

@@ -283,6 +283,11 @@ const char* pkd_strerror(int code);
  *                are persistent launches over device-side lists; 0: the same
  *                kernels with the host reading the counts after every step
  *                (one stream synchronisation per round and skeleton level)
+ *   "front_cap"  > 0: first capacity (entries) of the lists with which an
+ *                update flattens the subtrees it rebuilds (testing; 0, the
+ *                default, sizes them by the points of those subtrees).  A
+ *                list that overflows makes the update redo the flatten with
+ *                room for every node of the tree, before any visible change.
  * Returns PKD_EINVAL for an unknown name or an out-of-range value. */
 int pkd_set_option(const char* name, int64_t value);
 
@@ -305,7 +310,8 @@ int pkd_set_option(const char* name, int64_t value);
  * "delete_gather" (ids a delete found and looked up), "scratch_zeroed"
  * (a tree's first delete took a released tree's per-node delete scratch,
  * which every delete leaves all zero, from the block cache without clearing
- * it; items = bytes).  The name
+ * it; items = bytes), "front_retries" (updates whose flatten lists
+ * overflowed and were redone larger).  The name
  * "allocations" reports, in *launches, every device or pinned-host allocation
  * the library made since it was loaded; "graph_builds" the builds (and update
  * rebuilds) whose rounds ran from one graph launch.  With graph rounds,

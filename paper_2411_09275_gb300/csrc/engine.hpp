@@ -25,6 +25,7 @@ struct Knobs {
                          // buckets, 2 persistent re-walking, 1 one tile per CTA
   int graph_rounds = 1;  // build rounds: 1 decided on the device (one CUDA graph
                          // with conditional nodes), 0 sequenced by the host
+  long long front_cap = 0;  // > 0: first capacity of an update's flatten lists (testing)
 };
 Knobs& knobs();
 

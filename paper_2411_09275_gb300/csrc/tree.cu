@@ -749,6 +749,9 @@ int pkd_set_option(const char* name, int64_t value) {
   } else if (n == "skel_cap") {
     if (value != 0 && (value < 64 || value > 16384)) return PKD_EINVAL;
     knobs().skel_cap = (int)value;
+  } else if (n == "front_cap") {
+    if (value < 0) return PKD_EINVAL;
+    knobs().front_cap = value;
   } else if (n == "sieve_kernel") {
     if (value < 0 || value > 2) return PKD_EINVAL;
     knobs().sieve_kernel = (int)value;

@@ -901,10 +901,15 @@ __global__ void k_front_init(const RebuildItem* it, const uint32_t* n, Front* f,
 // One level of the frontier: the grid strides over the device-side count
 // *nf (block-uniform), so the host launches a batch of levels without
 // reading any count in between; a level with an empty frontier does nothing.
+// An entry past a list's capacity is not written: it sets *ovf, and the
+// host redoes the flatten with larger lists.  The counts still include such
+// entries, so a level reads at most `cap` entries of its frontier (the
+// entries past it were never written; the attempt is redone anyway).
 __global__ void k_front_expand(const Front* f, const uint32_t* nf, Front* g, uint32_t* ng, Front* leaves,
                                uint32_t* nleaves, Front* bigleaves, uint32_t* nbig, const Node* nodes,
-                               const uint8_t* ndim, const uint32_t* aux, int use_aux, uint32_t cap, DevStatus* st) {
-  const uint32_t n = *nf;
+                               const uint8_t* ndim, const uint32_t* aux, int use_aux, uint32_t cap, uint32_t bcap,
+                               uint32_t* ovf) {
+  const uint32_t n = min(*nf, cap);
   for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
     const uint32_t i = base + threadIdx.x;
     const bool have = i < n;
@@ -922,15 +927,15 @@ __global__ void k_front_expand(const Front* f, const uint32_t* nf, Front* g, uin
     if (!have) continue;
     if (leaf) {
       const uint32_t k = big ? first[2] : first[0];
-      if (k < cap) (big ? bigleaves : leaves)[k] = e;
-      else set_error(st, DERR_CAPACITY, 820);
+      if (k < (big ? bcap : cap)) (big ? bigleaves : leaves)[k] = e;
+      else atomicOr(ovf, 1u);
       continue;
     }
     const Node nd = nodes[e.slot];
     const uint32_t llive = nodes[nd.a].size - (use_aux ? aux[nd.a] : 0u);
     const uint32_t k = first[1];
     if (k + 2 > cap) {
-      set_error(st, DERR_CAPACITY, 821);
+      atomicOr(ovf, 1u);
       continue;
     }
     g[k] = Front{nd.a, e.item, e.off};
@@ -1616,12 +1621,17 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
     PKD_TRY(sc.get(&saved_nodes, nitems));
     PKD_TRY(sc.get(&saved_dims, nitems));
     PKD_TRY(sc.get(&saved_next, 1));
-    const uint64_t fcap = 4 * ((uint64_t)t.size + (uint64_t)nitems) + 1024;
-    Front *fa, *fb, *leaves, *bigleaves;
-    PKD_TRY(sc.get(&fa, std::min<uint64_t>(fcap, 0xFFFFFFF0ull)));
-    PKD_TRY(sc.get(&fb, std::min<uint64_t>(fcap, 0xFFFFFFF0ull)));
-    PKD_TRY(sc.get(&leaves, std::min<uint64_t>(fcap, 0xFFFFFFF0ull)));
-    PKD_TRY(sc.get(&bigleaves, std::min<uint64_t>(fcap / BIG_LEAF + 16, 0xFFFFFFF0ull)));
+    // Capacity of the flatten's lists: every node of the old subtrees
+    // appears once.  A subtree of P stored points has at most 2P - 1 nodes
+    // unless deletes left empty leaves in it, so the first attempt is sized
+    // by the stored points of the rebuilt subtrees (at most their new sizes
+    // plus the points this batch deleted); when a level overflows it, the
+    // flatten is redone with four entries per stored point of the tree.
+    const uint64_t big_fcap = 4 * ((uint64_t)t.size + (uint64_t)nitems) + 1024;
+    uint64_t fcap = 2 * (total + (insert ? 0ull : (uint64_t)total_changed) + (uint64_t)nitems) + 1024;
+    if (knobs().front_cap > 0) fcap = (uint64_t)knobs().front_cap;
+    fcap = std::max<uint64_t>(std::min(fcap, big_fcap), (uint64_t)nitems + 1024);  // the roots always fit
+    Front *fa = nullptr, *fb = nullptr, *leaves = nullptr, *bigleaves = nullptr;
     uint32_t *ncnt = nullptr, *noff = nullptr, *npart = nullptr;
     if (insert) {
       PKD_TRY(sc.get(&ncnt, nitems));
@@ -1638,29 +1648,41 @@ static int run_update(TreeMem& t, const int32_t* coords, const uint32_t* ids, co
     // level first (an insert's items are mostly leaves), then FRONT_BATCH
     // levels at a time (a rebuilt interior subtree is many levels deep).
     {
-      uint32_t* fc = dctr + 12;  // [0] frontier, [2] leaves, [3] big leaves
+      uint32_t* fc = dctr + 12;  // [0] frontier, [1] overflow, [2] leaves, [3] big leaves
       uint32_t* lc;              // the frontier of every level of a batch
       PKD_TRY(sc.get(&lc, FRONT_BATCH + 1));
-      PKD_TRY(dev_fill(fc, 0, 16, s));
-      PKD_LAUNCH(k_front_init<<<gi, 128, 0, s>>>(items_out, d_nitems, fa, fc));
-      const uint32_t fcap32 = (uint32_t)std::min<uint64_t>(fcap, 0xFFFFFFF0ull);
       const unsigned gexp = (unsigned)sm_count() * 8;
-      int levels = 0;
-      for (int batch = 1;; batch = FRONT_BATCH) {
-        if (levels > 100000) return PKD_EINTERNAL;
-        PKD_TRY(dev_fill(lc + 1, 0, (size_t)batch * 4, s));
-        PKD_TRY(dev_copy_words(lc, fc, 1, s));
-        for (int k = 0; k < batch; ++k) {
-          PKD_LAUNCH(k_front_expand<<<gexp, 128, 0, s>>>(fa, lc + k, fb, lc + k + 1, leaves, fc + 2, bigleaves,
-                                                          fc + 3, t.nodes, t.ndim, t.aux, insert ? 0 : 1, fcap32,
-                                                          t.st));
-          std::swap(fa, fb);
+      for (int attempt = 0;; ++attempt) {
+        const uint32_t fcap32 = (uint32_t)std::min<uint64_t>(fcap, 0xFFFFFFF0ull);
+        const uint32_t bcap32 = (uint32_t)std::min<uint64_t>(fcap / BIG_LEAF + 16, 0xFFFFFFF0ull);
+        PKD_TRY(sc.get(&fa, fcap32));
+        PKD_TRY(sc.get(&fb, fcap32));
+        PKD_TRY(sc.get(&leaves, fcap32));
+        PKD_TRY(sc.get(&bigleaves, bcap32));
+        PKD_TRY(dev_fill(fc, 0, 16, s));
+        PKD_LAUNCH(k_front_init<<<gi, 128, 0, s>>>(items_out, d_nitems, fa, fc));
+        int levels = 0;
+        for (int batch = 1;; batch = FRONT_BATCH) {
+          if (levels > 100000) return PKD_EINTERNAL;
+          PKD_TRY(dev_fill(lc + 1, 0, (size_t)batch * 4, s));
+          PKD_TRY(dev_copy_words(lc, fc, 1, s));
+          for (int k = 0; k < batch; ++k) {
+            PKD_LAUNCH(k_front_expand<<<gexp, 128, 0, s>>>(fa, lc + k, fb, lc + k + 1, leaves, fc + 2, bigleaves,
+                                                            fc + 3, t.nodes, t.ndim, t.aux, insert ? 0 : 1, fcap32,
+                                                            bcap32, fc + 1));
+            std::swap(fa, fb);
+          }
+          levels += batch;
+          PKD_TRY(dev_copy_words(fc, lc + batch, 1, s));
+          PKD_CUDA(cudaMemcpyAsync(hctr + 12, fc, 16, cudaMemcpyDeviceToHost, s));
+          PKD_CUDA(cudaStreamSynchronize(s));
+          if (hctr[12] == 0 || hctr[13] != 0) break;
         }
-        levels += batch;
-        PKD_TRY(dev_copy_words(fc, lc + batch, 1, s));
-        PKD_CUDA(cudaMemcpyAsync(hctr + 12, fc, 16, cudaMemcpyDeviceToHost, s));
-        PKD_CUDA(cudaStreamSynchronize(s));
-        if (hctr[12] == 0) break;
+        if (hctr[13] == 0) break;
+        // a list overflowed: nothing the tree shows has changed yet
+        if (fcap >= big_fcap) return PKD_EINTERNAL;
+        stat_items("front_retries", 1);
+        fcap = big_fcap;
       }
       const uint32_t nleaves = hctr[14], nbigleaves = hctr[15];
       if (nleaves)

@@ -122,6 +122,29 @@ def test_config2_scaled_uniform_and_varden():
         assert pr.delete(sel.astype(np.uint32)) == m
 
 
+def test_flatten_overflow_is_redone_with_room():
+    # The lists that flatten the rebuilt subtrees start at 64 entries: the
+    # skewed batches below rebuild interior subtrees far larger than that, so
+    # the first attempt overflows and the update redoes the flatten with room
+    # for every node; the trees still match the oracle.
+    pkd = _pkd()
+    d, n = 3, 200_000
+    X = make_points("uniform", n, d, 61)
+    p = pkd.Params(d=d, phi=8, lam=3, sigma_log2=2, sigma_os=4)
+    pr = Pair(X, _ids(n), p)
+    Y = make_points("uniform", 40_000, d, 62)
+    Y[:, 0] //= 64  # a slab of new points: interior subtrees become unbalanced
+    pkd.pkd_kernel_timing(True)
+    try:
+        with knobs(front_cap=64):
+            pr.insert(Y, _ids(40_000, n))
+            pr.delete(_ids(60_000))
+        retries = pkd.pkd_kernel_stats("front_retries")[0]
+    finally:
+        pkd.pkd_kernel_timing(False)
+    assert retries >= 1
+
+
 def test_delete_scratch_recycled_between_trees():
     # Trees of 4e6 points built and freed one after the other, each deleting
     # a batch: a released tree's per-slot delete scratch (all zero again
